@@ -1,0 +1,200 @@
+/*
+ * he.h -- C ABI of the GB300 library for the encrypted FFConv layer (arXiv 2102.03494).
+ *
+ * The library evaluates, on one GPU, the homomorphic FFConv layer of the paper's Sec. 4.2
+ * (FFConv packing, DP-HI2C-CP): a d x d low-rank convolution W1 under DensePack (Sec. 3.2,
+ * Fig. 1) followed by a 1 x 1 restoring convolution W2 under ConvPack (Sec. 3.2, Fig. 2a),
+ * on RNS-BFV ciphertexts (Sec. 2.1: plaintext modulus t, ciphertext modulus Q, ring
+ * dimension N).  Every step runs in the library's own CUDA kernels.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: HE_OK (0) or a negative HE_E* code; he_last_error() gives the message.
+ *     Nothing throws across the ABI.
+ *   - "device" pointers are CUDA device memory owned by the caller; "host" pointers are
+ *     ordinary host memory owned by the caller.  The context owns its tables, its resident
+ *     Galois keys and its scratch memory.
+ *   - Work is enqueued on the context's CUDA stream and is asynchronous unless stated;
+ *     entry points that return data in host memory synchronise that stream.
+ *   - A context is not thread-safe; use one per host thread.
+ *   - Ring elements are stored limb-major: a ciphertext is [2][n_limbs][N] uint64 residues,
+ *     limb i reduced modulo the i-th ciphertext prime.  Slot vectors are N int64 values
+ *     (slot j < N/2 is row 0, slot N/2 + j is row 1).
+ */
+#ifndef HE_H
+#define HE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    HE_OK = 0,
+    HE_EINVAL = -1,   /* bad argument: shape, size, domain, level or parameter */
+    HE_ENOMEM = -2,   /* device allocation failed */
+    HE_ENOKEY = -3,   /* a rotation needs a Galois key that is not loaded */
+    HE_ECUDA = -4,    /* a CUDA call or kernel launch failed */
+    HE_ETIMEOUT = -5  /* reserved for bounded device waits */
+};
+
+enum { HE_COEFF = 0, HE_NTT = 1 };            /* representation of a ciphertext's limbs */
+enum { HE_DP_DOT = 0, HE_DP_SHIFT = 1 };      /* W1 schedule, see he_ffconv_layer */
+
+/* Rotation step that swaps the two rows of slots (Galois element 2N - 1). */
+#define HE_ROW_SWAP ((int32_t)0x7fffffff)
+
+typedef struct he_ctx he_ctx;
+
+/* BFV parameters (Sec. 2.1 fixes t, Q, N; the RNS split and key switching are readings).
+ * The ciphertext primes q_0 > ... > q_{n_q-1} are the largest primes below 2^q_bits with
+ * q = 1 mod 2N; the special primes p_0 > ... the largest below 2^p_bits with the same
+ * congruence.  alpha primes form one key-switching digit (dnum = ceil(n_q / alpha)).
+ * Limits: 6 <= log_n <= 16, 1 <= n_q <= 32, 1 <= n_p <= 8, 20 <= q_bits, p_bits <= 60,
+ * 1 <= alpha <= n_q, alpha <= n_p (key-switching noise), t an odd prime < 2^62. */
+typedef struct {
+    uint32_t log_n;
+    uint32_t n_q;
+    uint32_t q_bits;
+    uint32_t n_p;
+    uint32_t p_bits;
+    uint32_t alpha;
+    uint64_t t;
+} he_params;
+
+/* A ciphertext in caller-owned device memory: data is [n_polys][n_limbs][N] uint64,
+ * contiguous.  n_polys is 2; n_limbs is the level (n_q for fresh ciphertexts, one less
+ * after he_rescale); domain is HE_COEFF or HE_NTT. */
+typedef struct {
+    uint64_t* data;
+    uint32_t n_polys;
+    uint32_t n_limbs;
+    int32_t domain;
+} he_ct;
+
+/* Shape of one FFConv layer (Sec. 3.1 notation): input I_c x I_h x I_w, low-rank filters
+ * W1 of d x d x I_c x r (r = O'_c of Eq. 2), restoring filters W2 of 1 x 1 x r x O_c,
+ * stride and zero padding of W1, pack = HE_DP_DOT or HE_DP_SHIFT, modswitch != 0 drops the
+ * last ciphertext prime at the end of the layer. */
+typedef struct {
+    int32_t I_c, I_h, I_w, d, stride, pad, r, O_c;
+    int32_t pack;
+    int32_t modswitch;
+} he_layout;
+
+/* ---- context ---------------------------------------------------------------------- */
+
+/* Create a context for `params` on the current CUDA device; `cuda_stream` is a
+ * cudaStream_t (NULL = default stream).  Builds primes, twiddle and base-conversion
+ * tables on the host and uploads them.  Errors: HE_EINVAL (parameters out of range or too
+ * few primes), HE_ENOMEM, HE_ECUDA.  *out is NULL on error. */
+int he_ctx_create(const he_params* params, void* cuda_stream, he_ctx** out);
+void he_ctx_destroy(he_ctx* ctx);
+/* Message of the last error on this context (never NULL; empty when none). */
+const char* he_last_error(const he_ctx* ctx);
+/* Change the stream later work is enqueued on. */
+int he_set_stream(he_ctx* ctx, void* cuda_stream);
+/* Copy the moduli to host memory: out[0..n_q) = q_i, out[n_q..n_q+n_p) = p_k, then t.
+ * `cap` is the capacity of out; returns the count written or HE_EINVAL. */
+int he_get_moduli(const he_ctx* ctx, uint64_t* out, int cap);
+/* Operation counters since creation or the last reset: out[0] MulPC, out[1] AddCC,
+ * out[2] rotations, out[3] key switches (Table I's counted operations). */
+void he_op_counts(const he_ctx* ctx, uint64_t out[4]);
+void he_reset_op_counts(he_ctx* ctx);
+/* Number of CUDA kernels this context has launched since creation (a diagnostic). */
+uint64_t he_launch_count(const he_ctx* ctx);
+/* The 20 cumulative thresholds of the error sampler (sigma = 3.2, |e| <= 19), as
+ * computed by the library: T[m] = floor(2^63 Pr(|e| <= m)), T[19] = 2^63. */
+void he_gaussian_table(uint64_t out[20]);
+
+/* ---- client side: keys, encryption, decryption (Sec. 1: the client holds the secret) */
+
+/* Ternary secret key from `seed` (SplitMix64 stream 1): sk_out is host int64[N] in
+ * {-1, 0, 1}.  Synchronous. */
+int he_keygen_secret(he_ctx* ctx, uint64_t seed, int64_t* sk_out);
+/* Generate Galois keys for the rotation `steps` (host int32[n_steps]; HE_ROW_SWAP allowed)
+ * from the host secret `sk` (int64[N]) and `seed`, and keep them resident on the device.
+ * Steps with the same Galois element share one key. */
+int he_keygen_galois(he_ctx* ctx, const int64_t* sk, uint64_t seed, const int32_t* steps,
+                     int n_steps);
+/* Copy the resident key of `step` to host memory in the interchange layout
+ * [dnum][2][n_q + n_p][N] uint64, coefficient domain, index 0 = b, 1 = a.  Synchronous.
+ * HE_ENOKEY if absent. */
+int he_export_galois(he_ctx* ctx, int32_t step, uint64_t* blob_out);
+/* Load n_steps keys from the host blob (n_steps consecutive keys in the layout of
+ * he_export_galois) and keep them resident; replaces a key with the same Galois element. */
+int he_load_keys(he_ctx* ctx, const uint64_t* galois_blob, const int32_t* steps, int n_steps);
+/* Encrypt the slot vector `slots` (host int64[N], taken mod t) under the host secret sk
+ * with randomness from `seed` (streams 2 and 3).  out->data must hold [2][n_q][N]; the
+ * result is in out->domain (HE_COEFF or HE_NTT, chosen by the caller). */
+int he_encrypt(he_ctx* ctx, const int64_t* sk, const int64_t* slots, uint64_t seed, he_ct* out);
+/* Decrypt `ct` (any level, either domain) under sk and decode: slots_out is host
+ * int64[N] with values in [0, t).  Synchronous. */
+int he_decrypt(he_ctx* ctx, const int64_t* sk, const he_ct* ct, int64_t* slots_out);
+
+/* ---- server side: evaluation ---------------------------------------------------------- */
+
+/* In-place change of representation (negacyclic NTT per limb, or its inverse). */
+int he_to_ntt(he_ctx* ctx, he_ct* ct);
+int he_to_coeff(he_ctx* ctx, he_ct* ct);
+/* Encode slot values (host int64[N]) as a plaintext for he_mul_plain_acc: pt_out is device
+ * [n_q][N], the centred lift of the encoding, NTT domain. */
+int he_encode(he_ctx* ctx, const int64_t* slots, uint64_t* pt_out);
+/* Rotation by `step` slots (Sec. 3.2, Fig. 1b): decrypt(out)[row][j] = decrypt(in)[row][j+step]
+ * within each row of N/2 slots.  Automorphism X -> X^(5^step), then hybrid key switching.
+ * in/out: NTT domain, same level, in may equal out.  HE_ENOKEY without the key. */
+int he_rotate(he_ctx* ctx, const he_ct* in, int32_t step, he_ct* out);
+/* The same rotation applied to n ciphertexts in one batch (one key read per launch). */
+int he_rotate_batch(he_ctx* ctx, const he_ct* in, int n, int32_t step, he_ct* out);
+/* h rotations of one ciphertext sharing one ModUp of c1 (hoisting): outs[i] = rotation by
+ * steps[i].  Its ciphertext bits differ from he_rotate's (the lift happens before the
+ * automorphism); both decrypt identically. */
+int he_rotate_hoisted(he_ctx* ctx, const he_ct* in, const int32_t* steps, int h, he_ct* outs);
+/* MulPC + AddCC (Table I): acc += sum_i cts[i] * pts[i], pts device [n][level][N] NTT domain
+ * (e.g. from he_encode).  acc and cts in the NTT domain, same level. */
+int he_mul_plain_acc(he_ctx* ctx, const he_ct* cts, const uint64_t* pts, int n, he_ct* acc);
+/* AddCC: out = a + b (same level and domain; out may alias an input). */
+int he_add(he_ctx* ctx, const he_ct* a, const he_ct* b, he_ct* out);
+/* Modulus switch: out = round(in / q_last), one limb fewer.  NTT domain in and out. */
+int he_rescale(he_ctx* ctx, const he_ct* in, he_ct* out);
+
+/* Encrypted FFConv layer, FFConv packing DP-HI2C-CP (Sec. 4.2, Fig. 4; Tables I-III).
+ *   ct_in      one ciphertext (NTT domain, level n_q) holding the input image packed as the
+ *              layout requires: HE_DP_DOT slot ci*I_h*I_w + h*I_w + w;
+ *              HE_DP_SHIFT slot ci*B_c + h*I_w + w with B_c = I_h*I_w for I_c = 1, else the
+ *              next power of two.
+ *   lowrank_w  host int32 [r][I_c][d][d] (W1), restore_w host int32 [O_c][r] (W2); weights
+ *              are taken mod t.
+ *   ct_out     O_c caller-owned ciphertexts (NTT domain; level n_q, or n_q - 1 with
+ *              modswitch).  Output channel c holds y2[c, oh, ow] (mod t) at slot
+ *              oh*O_w + ow (HE_DP_DOT) or (stride*oh)*I_w + stride*ow (HE_DP_SHIFT).
+ * HE_DP_DOT is the paper's DensePack: per output (c', o) a zero-padded filter product and
+ * rotate-and-sum over ceil(log2(occupied slots)) steps (plus a row swap when the input fills
+ * both rows), then one-hot masks move the r*S dot products into r ciphertexts.
+ * HE_DP_SHIFT rotates the input once per filter tap (hoisted) and accumulates tap
+ * plaintexts, then folds channels with rotations by B_c*2^k.  Both finish with W2 under
+ * ConvPack (scalar products, no rotation).  Needs the Galois keys of the schedule. */
+int he_ffconv_layer(he_ctx* ctx, const he_ct* ct_in, const int32_t* lowrank_w,
+                    const int32_t* restore_w, const he_layout* layout, he_ct* ct_out);
+/* The same layer on B independent ciphertexts with shared weights: ct_in[B],
+ * ct_out[B * O_c] (image b's channel c at b * O_c + c).  Rotations of all B images by one
+ * Galois element share each key read. */
+int he_ffconv_layer_batch(he_ctx* ctx, const he_ct* ct_in, int B, const int32_t* lowrank_w,
+                          const int32_t* restore_w, const he_layout* layout, he_ct* ct_out);
+/* Rotation steps the layer needs keys for; writes at most `cap` steps into steps_out and
+ * returns the count (or HE_EINVAL for a layout that does not fit the ring). */
+int he_ffconv_required_steps(const he_ctx* ctx, const he_layout* layout, int32_t* steps_out,
+                             int cap);
+
+/* ---- primitives for measurement --------------------------------------------------- */
+
+/* Negacyclic NTT (inverse = 0) or inverse NTT (inverse = 1) in place on `n_items` blocks of
+ * n_limbs limbs each (device [n_items][n_limbs][N]); limb i uses the i-th ciphertext prime
+ * (i < n_q) or the (i - n_q)-th special prime. */
+int he_ntt(he_ctx* ctx, uint64_t* data, int n_items, int n_limbs, int inverse);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HE_H */

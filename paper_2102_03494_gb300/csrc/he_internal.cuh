@@ -1,0 +1,177 @@
+// he_internal.cuh -- shared declarations of the GB300 RNS-BFV library (not part of the ABI).
+//
+// Modular arithmetic on 64-bit residues (moduli below 2^62), built from the 64-bit integer
+// multiply of the SM (lowered to 32-bit IMAD):
+//   * Shoup products x*w mod q for a constant w with companion w' = floor(w 2^64 / q):
+//     r = x w - floor(x w' / 2^64) q lies in [0, 2q) for any 64-bit x;
+//   * Montgomery reduction REDC(x) = x 2^-64 mod q for a 128-bit x < q 2^64, used to reduce
+//     sums of products once (key-switch inner products, plaintext MACs); constants stored in
+//     Montgomery form (w 2^64 mod q) make REDC return plain residues.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "he.h"
+
+#define HE_MAX_MODS 48
+
+struct ModConst {
+    uint64_t q;
+    uint64_t qinv_neg;   // -q^-1 mod 2^64
+    uint64_t r2;         // 2^128 mod q (to Montgomery form via REDC(x r2))
+    uint64_t n_inv;      // N^-1 mod q
+    uint64_t n_inv_sh;   // its Shoup companion
+};
+
+struct ShoupPair {
+    uint64_t w, ws;
+};
+
+// ------------------------------------------------------------------ device arithmetic
+
+__device__ __forceinline__ uint64_t add_mod(uint64_t a, uint64_t b, uint64_t q) {
+    uint64_t s = a + b;
+    return s >= q ? s - q : s;
+}
+
+__device__ __forceinline__ uint64_t sub_mod(uint64_t a, uint64_t b, uint64_t q) {
+    return a >= b ? a - b : a + q - b;
+}
+
+__device__ __forceinline__ uint64_t neg_mod(uint64_t a, uint64_t q) { return a ? q - a : 0; }
+
+// x * w mod q, x any 64-bit value, w < q, ws = floor(w 2^64 / q).
+__device__ __forceinline__ uint64_t mul_shoup(uint64_t x, uint64_t w, uint64_t ws, uint64_t q) {
+    uint64_t h = __umul64hi(x, ws);
+    uint64_t r = x * w - h * q;
+    return r >= q ? r - q : r;
+}
+
+// Same, result left in [0, 2q).
+__device__ __forceinline__ uint64_t mul_shoup_lazy(uint64_t x, uint64_t w, uint64_t ws,
+                                                   uint64_t q) {
+    uint64_t h = __umul64hi(x, ws);
+    return x * w - h * q;
+}
+
+struct U128 {
+    uint64_t lo, hi;
+};
+
+__device__ __forceinline__ void mac128(U128& acc, uint64_t a, uint64_t b) {
+    uint64_t lo = a * b;
+    uint64_t hi = __umul64hi(a, b);
+    acc.lo += lo;
+    acc.hi += hi + (acc.lo < lo ? 1u : 0u);
+}
+
+// REDC: x 2^-64 mod q for x < q 2^64, result in [0, q).
+__device__ __forceinline__ uint64_t redc(U128 x, uint64_t q, uint64_t qinv_neg) {
+    uint64_t m = x.lo * qinv_neg;
+    uint64_t t = x.hi + __umul64hi(m, q) + (x.lo != 0 ? 1u : 0u);
+    return t >= q ? t - q : t;
+}
+
+__device__ __forceinline__ uint64_t to_mont(uint64_t a, const ModConst& M) {
+    U128 x{0, 0};
+    mac128(x, a, M.r2);
+    return redc(x, M.q, M.qinv_neg);
+}
+
+// ------------------------------------------------------------------ host-side context
+
+struct Arena {
+    // Grow-only device scratch.  take() hands out 256-byte aligned slices of one buffer;
+    // reset() frees every slice at once.  Growing synchronises the stream first.
+    char* base = nullptr;
+    size_t cap = 0, used = 0;
+};
+
+struct Staging {
+    // Pinned host slots + device slots for small uploads (pointer tables, weights).
+    static constexpr int kSlots = 64;
+    size_t slot_bytes = 1 << 18;
+    int n_slots = kSlots;
+    int next = 0;
+    char* host = nullptr;
+    char* dev = nullptr;
+    cudaEvent_t ev[kSlots] = {};
+};
+
+struct GaloisKey {
+    uint64_t* dev = nullptr;     // [dnum][2][L+K][N], NTT domain, Montgomery form
+};
+
+struct he_ctx {
+    he_params prm{};
+    int N = 0, logN = 0, L = 0, K = 0, alpha = 0, dnum = 0;
+    int n_mod = 0;               // L + K + 1 (the last one is t)
+    bool batching = false;       // t = 1 mod 2N: slot encoding available
+    std::vector<uint64_t> mods;  // q_0..q_{L-1}, p_0..p_{K-1}, t
+    cudaStream_t stream = nullptr;
+
+    ModConst* d_mod = nullptr;          // [n_mod]
+    ShoupPair* d_tw_fwd = nullptr;      // [n_mod][N]: psi^brv(k)
+    ShoupPair* d_tw_inv = nullptr;      // [n_mod][N]: psi^-brv(k)
+    int32_t* d_slot_pos = nullptr;      // [N]: NTT position of each slot (mod t, root zeta)
+    uint64_t* d_cdt = nullptr;          // [20] sampler thresholds
+    // ModUp: y_i = x_i [(Q_j/q_i)^-1]_{q_i};  then sum_i y_i [Q_j/q_i]_{p_l}
+    ShoupPair* d_modup_inv = nullptr;   // [L]
+    ShoupPair* d_modup_c = nullptr;     // [dnum][alpha][L+K]
+    // ModDown: y_k = u_k [(P/p_k)^-1]_{p_k}; v_i = sum_k y_k [P/p_k]_{q_i}; (u_i - v_i) P^-1
+    ShoupPair* d_md_inv = nullptr;      // [K]
+    ShoupPair* d_md_c = nullptr;        // [K][L]
+    ShoupPair* d_md_pinv = nullptr;     // [L]
+    ShoupPair* d_rs_inv = nullptr;      // [L][L]: row lv = q_lv^-1 mod q_i (rescale at level lv+1)
+    uint64_t* d_pmodq = nullptr;        // [L] P mod q_i (Montgomery form) for key generation
+
+    std::map<uint32_t, GaloisKey> keys; // by Galois element
+    Arena arena;
+    Staging staging;
+    uint64_t ops[4] = {0, 0, 0, 0};     // MulPC, AddCC, Rot, KeySwitch
+    uint64_t launches = 0;              // kernels launched by this context
+    std::string err;
+};
+
+// ------------------------------------------------------------------ internal helpers
+
+#define HE_CHECK_CUDA(ctx, call)                                                       \
+    do {                                                                               \
+        cudaError_t _e = (call);                                                       \
+        if (_e != cudaSuccess) return he_fail((ctx), HE_ECUDA, cudaGetErrorString(_e)); \
+    } while (0)
+
+int he_fail(he_ctx* ctx, int code, const std::string& msg);
+int he_launch_check(he_ctx* ctx, const char* what);
+
+uint64_t* arena_take(he_ctx* ctx, size_t n_u64);
+void arena_reset(he_ctx* ctx);
+int arena_reserve(he_ctx* ctx, size_t n_u64);
+
+uint32_t galois_elt(const he_ctx* ctx, int32_t step);
+const void* upload_small(he_ctx* ctx, const void* src, size_t bytes);
+int check_ct(he_ctx* ctx, const he_ct* ct, int need_limbs, int need_domain, const char* what);
+void encode_device(he_ctx* ctx, const int64_t* d_slots, int items, uint64_t* tmp, uint64_t* out,
+                   int mont);
+int he_get_key(he_ctx* ctx, uint32_t g, const uint64_t** key);
+
+// host arithmetic (api.cu)
+uint64_t h_mulmod(uint64_t a, uint64_t b, uint64_t q);
+uint64_t h_powmod(uint64_t a, uint64_t e, uint64_t q);
+uint64_t h_inv(uint64_t a, uint64_t q);
+ShoupPair h_shoup(uint64_t w, uint64_t q);
+uint64_t h_to_mont(uint64_t x, uint64_t q);
+uint64_t he_stream_state(uint64_t seed, uint64_t stream);
+void he_cdt_compute(uint64_t out[20]);
+
+// NTT launchers (ntt.cu).  A launch covers `items` blocks (stride `item_stride` u64) of
+// `rows` consecutive limbs; limb r of a block uses modulus index mod_off + r.
+void ntt_forward(he_ctx* ctx, uint64_t* data, int items, size_t item_stride, int rows,
+                 int mod_off);
+void ntt_inverse(he_ctx* ctx, uint64_t* data, int items, size_t item_stride, int rows,
+                 int mod_off);

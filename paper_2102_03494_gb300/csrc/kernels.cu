@@ -1,0 +1,723 @@
+// kernels.cu -- element-wise and base-conversion kernels of the RNS-BFV path.
+//
+// Layout: a ring element is [limbs][N] uint64 residues; a ciphertext [2][limbs][N].  Grids
+// put the "item" (ciphertext / output) index in blockIdx.x so that CTAs running together
+// touch the same coefficient tile of shared operands (keys, plaintexts) and find it in L2.
+#include "he_internal.cuh"
+#include "kernels.cuh"
+
+namespace {
+
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
+
+__device__ __forceinline__ uint32_t brv_bits(uint32_t x, int bits) {
+    return bits ? (__brev(x) >> (32 - bits)) : 0u;
+}
+
+}  // namespace
+
+// NTT-domain automorphism X -> X^g: position p holds a(psi^(2 brv(p) + 1)); the image takes
+// the value at exponent (2 brv(p) + 1) g mod 2N.
+__device__ __forceinline__ uint32_t perm_src(uint32_t p, uint32_t g, int logN) {
+    uint32_t e = (2u * brv_bits(p, logN) + 1u) * g & ((2u << logN) - 1u);
+    return brv_bits((e - 1u) >> 1, logN);
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t draw(uint64_t state0, uint64_t ctr) {
+    return mix64(state0 + (ctr + 1ull) * kGamma);
+}
+
+// ------------------------------------------------------------------ automorphism
+
+// out[item][r][p] = in[item][r][perm_g(p)] for `rows` limbs per item.
+__global__ void k_automorph(const uint64_t* __restrict__ in, size_t in_stride,
+                            uint64_t* __restrict__ out, size_t out_stride, int rows, int logN,
+                            uint32_t g) {
+    const int N = 1 << logN;
+    const int n = blockIdx.y * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const uint32_t src = perm_src(n, g, logN);
+    const uint64_t* a = in + blockIdx.x * in_stride;
+    uint64_t* b = out + blockIdx.x * out_stride;
+    for (int r = 0; r < rows; ++r) b[(size_t)r * N + n] = a[(size_t)r * N + src];
+}
+
+// ------------------------------------------------------------------ key switching
+
+// ModUp.  x_coeff: [item][L][N] coefficient form of the polynomial being switched;
+// x_ntt: [item][L][N] its NTT form (read at perm_g positions for the digit's own limbs);
+// out: [item][dnum][L+K][N].  Rows outside digit j get the fast base conversion
+//   y_l = sum_{i in digit j} [x_i (Q_j/q_i)^-1]_{q_i} [Q_j/q_i]_{m_l}  mod m_l
+// (coefficient form, transformed afterwards); the digit's own rows get the NTT form.
+__global__ void k_modup(const uint64_t* __restrict__ x_coeff, size_t xc_stride,
+                        const uint64_t* __restrict__ x_ntt, size_t xn_stride, uint32_t g_own,
+                        uint64_t* __restrict__ out, size_t out_stride, int L, int K, int alpha,
+                        int logN, const ModConst* __restrict__ mods,
+                        const ShoupPair* __restrict__ inv, const ShoupPair* __restrict__ cst) {
+    const int N = 1 << logN;
+    const int n = blockIdx.y * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int j = blockIdx.z;
+    const int LK = L + K;
+    const int i0 = j * alpha;
+    const int i1 = min(i0 + alpha, L);
+    const uint64_t* xc = x_coeff + blockIdx.x * xc_stride;
+    const uint64_t* xn = x_ntt + blockIdx.x * xn_stride;
+    uint64_t* o = out + blockIdx.x * out_stride + (size_t)j * LK * N;
+    uint64_t y[8];
+    for (int i = i0; i < i1; ++i) {
+        ShoupPair w = inv[i];
+        y[i - i0] = mul_shoup(xc[(size_t)i * N + n], w.w, w.ws, mods[i].q);
+    }
+    const uint32_t src = perm_src(n, g_own, logN);
+    for (int l = 0; l < LK; ++l) {
+        if (l >= i0 && l < i1) {
+            o[(size_t)l * N + n] = xn[(size_t)l * N + src];
+            continue;
+        }
+        const uint64_t ql = mods[l].q;
+        uint64_t acc = 0;
+        for (int i = i0; i < i1; ++i) {
+            ShoupPair c = cst[((size_t)j * alpha + (i - i0)) * LK + l];
+            acc = add_mod(acc, mul_shoup(y[i - i0], c.w, c.ws, ql), ql);
+        }
+        o[(size_t)l * N + n] = acc;
+    }
+}
+
+// Inner product with a key in Montgomery form: u_k[l][p] = sum_j D_j[l][perm_g(p)] * key_j,k[l][p]
+// D: [item][dnum][L+K][N]; key: [dnum][2][L+K][N]; u: [item][2][L+K][N].
+__global__ void k_ks_inner(const uint64_t* __restrict__ D, size_t d_stride,
+                           const uint64_t* __restrict__ key, uint64_t* __restrict__ u,
+                           size_t u_stride, int LK, int dnum, int logN, uint32_t g,
+                           const ModConst* __restrict__ mods) {
+    const int N = 1 << logN;
+    const int n = blockIdx.y * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int l = blockIdx.z;
+    const ModConst M = mods[l];
+    const uint32_t src = perm_src(n, g, logN);
+    const uint64_t* d = D + blockIdx.x * d_stride + (size_t)l * N;
+    const uint64_t* kb = key + (size_t)l * N + n;
+    U128 a0{0, 0}, a1{0, 0};
+    for (int j = 0; j < dnum; ++j) {
+        uint64_t x = d[(size_t)j * LK * N + src];
+        mac128(a0, x, kb[(size_t)(2 * j) * LK * N]);
+        mac128(a1, x, kb[(size_t)(2 * j + 1) * LK * N]);
+    }
+    uint64_t* ub = u + blockIdx.x * u_stride + (size_t)l * N + n;
+    ub[0] = redc(a0, M.q, M.qinv_neg);
+    ub[(size_t)LK * N] = redc(a1, M.q, M.qinv_neg);
+}
+
+// ModDown base conversion.  u: [item][2][L+K][N] with the K special rows in coefficient form;
+// v: [item][2][L][N] coefficient form, v_i = sum_k [u_{p_k} (P/p_k)^-1]_{p_k} [P/p_k]_{q_i}.
+__global__ void k_moddown_conv(const uint64_t* __restrict__ u, size_t u_stride,
+                               uint64_t* __restrict__ v, size_t v_stride, int L, int K,
+                               int logN, const ModConst* __restrict__ mods,
+                               const ShoupPair* __restrict__ inv,
+                               const ShoupPair* __restrict__ cst) {
+    const int N = 1 << logN;
+    const int n = blockIdx.y * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int k = blockIdx.z;  // polynomial 0 or 1
+    const int LK = L + K;
+    const uint64_t* ub = u + blockIdx.x * u_stride + (size_t)k * LK * N + (size_t)L * N;
+    uint64_t y[8];
+    for (int kk = 0; kk < K; ++kk) {
+        ShoupPair w = inv[kk];
+        y[kk] = mul_shoup(ub[(size_t)kk * N + n], w.w, w.ws, mods[L + kk].q);
+    }
+    uint64_t* vb = v + blockIdx.x * v_stride + (size_t)k * L * N;
+    for (int i = 0; i < L; ++i) {
+        const uint64_t qi = mods[i].q;
+        uint64_t acc = 0;
+        for (int kk = 0; kk < K; ++kk) {
+            ShoupPair c = cst[(size_t)kk * L + i];
+            acc = add_mod(acc, mul_shoup(y[kk], c.w, c.ws, qi), qi);
+        }
+        vb[(size_t)i * N + n] = acc;
+    }
+}
+
+// Rotation result: out_k[i] = (u_k[i] - v_k[i]) P^-1 (+ c0[i][perm_g] for k = 0)
+// (+ base_k[i] when base != null).  All NTT domain.  out/base/c0 addressed through pointer
+// tables (one pointer per item, each a [2][L][N] ciphertext).
+__global__ void k_ks_combine(const uint64_t* __restrict__ u, size_t u_stride,
+                             const uint64_t* __restrict__ v, size_t v_stride,
+                             const uint64_t* const* __restrict__ c0p,
+                             const uint64_t* const* __restrict__ basep, uint64_t* const* outp,
+                             int L, int K, int logN, uint32_t g,
+                             const ModConst* __restrict__ mods,
+                             const ShoupPair* __restrict__ pinv) {
+    const int N = 1 << logN;
+    const int n = blockIdx.y * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int i = blockIdx.z;
+    const int LK = L + K;
+    const uint64_t q = mods[i].q;
+    const ShoupPair w = pinv[i];
+    const uint32_t src = perm_src(n, g, logN);
+    const int it = blockIdx.x;
+    const uint64_t* ub = u + it * u_stride + (size_t)i * N + n;
+    const uint64_t* vb = v + it * v_stride + (size_t)i * N + n;
+    uint64_t r0 = mul_shoup(sub_mod(ub[0], vb[0], q), w.w, w.ws, q);
+    uint64_t r1 = mul_shoup(sub_mod(ub[(size_t)LK * N], vb[(size_t)L * N], q), w.w, w.ws, q);
+    r0 = add_mod(r0, c0p[it][(size_t)i * N + src], q);
+    if (basep) {
+        const uint64_t* bb = basep[it] + (size_t)i * N + n;
+        r0 = add_mod(r0, bb[0], q);
+        r1 = add_mod(r1, bb[(size_t)L * N], q);
+    }
+    uint64_t* ob = outp[it] + (size_t)i * N + n;
+    ob[0] = r0;
+    ob[(size_t)L * N] = r1;
+}
+
+// ------------------------------------------------------------------ MulPC / AddCC
+
+// out[o] = (accin[o] or 0) + sum_{t < T} X[o*T + t] * P[o*T + t]   (per poly and limb)
+// X entries are [2][L][N] ciphertexts, P entries [L][N] plaintexts in Montgomery form.
+// The products of one output are summed in 128 bits and reduced once (T < 2^64 / q_max).
+__global__ void k_mac(const uint64_t* const* __restrict__ X, const uint64_t* const* __restrict__ P,
+                      int T, const uint64_t* const* __restrict__ accin, uint64_t* const* outp,
+                      int L, int logN, const ModConst* __restrict__ mods) {
+    const int N = 1 << logN;
+    const int n = blockIdx.y * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int i = blockIdx.z;
+    const int o = blockIdx.x;
+    const ModConst M = mods[i];
+    const size_t off = (size_t)i * N + n;
+    U128 a0{0, 0}, a1{0, 0};
+    for (int t = 0; t < T; ++t) {
+        const uint64_t* x = X[(size_t)o * T + t];
+        uint64_t p = P[(size_t)o * T + t][off];
+        mac128(a0, x[off], p);
+        mac128(a1, x[off + (size_t)L * N], p);
+    }
+    uint64_t r0 = redc(a0, M.q, M.qinv_neg);
+    uint64_t r1 = redc(a1, M.q, M.qinv_neg);
+    if (accin && accin[o]) {
+        r0 = add_mod(r0, accin[o][off], M.q);
+        r1 = add_mod(r1, accin[o][off + (size_t)L * N], M.q);
+    }
+    outp[o][off] = r0;
+    outp[o][off + (size_t)L * N] = r1;
+}
+
+// ConvPack with scalar weights (Table II): out[b][c] = sum_{c'} w[c][c'] x[b][c'], weights in
+// Montgomery form per limb: wm[(c * r + c') * L + i].  x: [B][r][2][L][N] contiguous.
+__global__ void k_convpack(const uint64_t* __restrict__ x, int r, int O_c,
+                           const uint64_t* __restrict__ wm, uint64_t* const* outp, int L,
+                           int logN, const ModConst* __restrict__ mods) {
+    const int N = 1 << logN;
+    const int n = blockIdx.y * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int i = blockIdx.z;
+    const int b = blockIdx.x / O_c, c = blockIdx.x - b * O_c;
+    const ModConst M = mods[i];
+    const size_t ct = (size_t)2 * L * N;
+    const uint64_t* xb = x + (size_t)b * r * ct + (size_t)i * N + n;
+    U128 a0{0, 0}, a1{0, 0};
+    for (int cp = 0; cp < r; ++cp) {
+        uint64_t w = wm[((size_t)c * r + cp) * L + i];
+        mac128(a0, xb[cp * ct], w);
+        mac128(a1, xb[cp * ct + (size_t)L * N], w);
+    }
+    uint64_t* ob = outp[blockIdx.x] + (size_t)i * N + n;
+    ob[0] = redc(a0, M.q, M.qinv_neg);
+    ob[(size_t)L * N] = redc(a1, M.q, M.qinv_neg);
+}
+
+// out = a + b for `rows` limbs (pointer tables, each entry rows*N contiguous)
+__global__ void k_add(const uint64_t* const* ap, const uint64_t* const* bp, uint64_t* const* op,
+                      int rows_per_poly, int polys, int logN, const ModConst* __restrict__ mods) {
+    const int N = 1 << logN;
+    const int n = blockIdx.y * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int row = blockIdx.z;
+    const uint64_t q = mods[row % rows_per_poly].q;
+    const size_t off = (size_t)row * N + n;
+    op[blockIdx.x][off] = add_mod(ap[blockIdx.x][off], bp[blockIdx.x][off], q);
+    (void)polys;
+}
+
+// Convert rows to Montgomery form in place (x -> x 2^64 mod q); row r uses mods[mod_off + r % period].
+__global__ void k_to_mont(uint64_t* data, int rows, int period, int mod_off, int logN,
+                          const ModConst* __restrict__ mods) {
+    const int N = 1 << logN;
+    const int n = blockIdx.y * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int r = blockIdx.z;
+    uint64_t* p = data + (size_t)blockIdx.x * rows * N + (size_t)r * N + n;
+    *p = to_mont(*p, mods[mod_off + r % period]);
+}
+
+// Back from Montgomery form (x -> x 2^-64 mod q) in place.
+__global__ void k_from_mont(uint64_t* data, int rows, int period, int mod_off, int logN,
+                            const ModConst* __restrict__ mods) {
+    const int N = 1 << logN;
+    const int n = blockIdx.y * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int r = blockIdx.z;
+    uint64_t* p = data + (size_t)blockIdx.x * rows * N + (size_t)r * N + n;
+    const ModConst M = mods[mod_off + r % period];
+    *p = redc(U128{*p, 0}, M.q, M.qinv_neg);
+}
+
+// ------------------------------------------------------------------ rescale (mod switch)
+
+// s[item][k][i][n] = ([last_k[n] + h]_{q_last}) mod q_i, coefficient form, i < L-1.
+// last: [item][2][N] coefficient form of the last limb of each polynomial.
+__global__ void k_rescale_spread(const uint64_t* __restrict__ last, uint64_t* __restrict__ s,
+                                 int L, int logN, const ModConst* __restrict__ mods) {
+    const int N = 1 << logN;
+    const int n = blockIdx.y * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int k = blockIdx.z;
+    const uint64_t ql = mods[L - 1].q;
+    const uint64_t h = (ql - 1) >> 1;
+    const uint64_t r = add_mod(last[((size_t)blockIdx.x * 2 + k) * N + n], h, ql);
+    uint64_t* sb = s + ((size_t)blockIdx.x * 2 + k) * (L - 1) * N + n;
+    for (int i = 0; i < L - 1; ++i) sb[(size_t)i * N] = r % mods[i].q;
+}
+
+// last[item][k][n] = x[item][k][L-1][n] (the limb a modulus switch drops).
+__global__ void k_gather_last(const uint64_t* const* xp, uint64_t* __restrict__ last, int L,
+                              int logN) {
+    const int N = 1 << logN;
+    const int n = blockIdx.y * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int k = blockIdx.z;
+    last[((size_t)blockIdx.x * 2 + k) * N + n] = xp[blockIdx.x][((size_t)k * L + L - 1) * N + n];
+}
+
+// out_k[i] = (x_k[i] + h - s_k[i]) q_last^-1 mod q_i   (NTT domain; h is a constant polynomial)
+__global__ void k_rescale_combine(const uint64_t* const* xp, const uint64_t* __restrict__ s,
+                                  uint64_t* const* outp, int L, int logN,
+                                  const ModConst* __restrict__ mods,
+                                  const ShoupPair* __restrict__ qinv_row) {
+    const int N = 1 << logN;
+    const int n = blockIdx.y * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int i = blockIdx.z % (L - 1), k = blockIdx.z / (L - 1);
+    const uint64_t q = mods[i].q;
+    const uint64_t h = ((mods[L - 1].q - 1) >> 1) % q;
+    const ShoupPair w = qinv_row[i];
+    uint64_t x = xp[blockIdx.x][((size_t)k * L + i) * N + n];
+    uint64_t sv = s[(((size_t)blockIdx.x * 2 + k) * (L - 1) + i) * N + n];
+    uint64_t y = sub_mod(add_mod(x, h, q), sv, q);
+    outp[blockIdx.x][((size_t)k * (L - 1) + i) * N + n] = mul_shoup(y, w.w, w.ws, q);
+}
+
+// ------------------------------------------------------------------ encoder
+
+// Slot values (int64, taken mod t) -> NTT-order buffer mod t: buf[item][slot_pos[s]] = v[s].
+__global__ void k_slots_to_ntt(const int64_t* __restrict__ v, uint64_t* __restrict__ buf,
+                               const int32_t* __restrict__ slot_pos, int logN, uint64_t t) {
+    const int N = 1 << logN;
+    const int s = blockIdx.y * blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    int64_t x = v[(size_t)blockIdx.x * N + s];
+    int64_t m = x % (int64_t)t;
+    if (m < 0) m += (int64_t)t;
+    buf[(size_t)blockIdx.x * N + slot_pos[s]] = (uint64_t)m;
+}
+
+// NTT-order buffer mod t -> slot values: v[item][s] = buf[item][slot_pos[s]].
+__global__ void k_ntt_to_slots(const uint64_t* __restrict__ buf, int64_t* __restrict__ v,
+                               const int32_t* __restrict__ slot_pos, int logN) {
+    const int N = 1 << logN;
+    const int s = blockIdx.y * blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    v[(size_t)blockIdx.x * N + s] = (int64_t)buf[(size_t)blockIdx.x * N + slot_pos[s]];
+}
+
+// m (coefficients mod t) -> centred lift mod q_i for L limbs; Montgomery form if mont != 0.
+__global__ void k_lift(const uint64_t* __restrict__ m, uint64_t* __restrict__ out, int L,
+                       int logN, uint64_t t, int mont, const ModConst* __restrict__ mods) {
+    const int N = 1 << logN;
+    const int n = blockIdx.y * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const uint64_t x = m[(size_t)blockIdx.x * N + n];
+    uint64_t* o = out + (size_t)blockIdx.x * L * N + n;
+    const bool neg = x > (t - 1) / 2;
+    for (int i = 0; i < L; ++i) {
+        const ModConst M = mods[i];
+        uint64_t r = neg ? M.q - ((t - x) % M.q) : x % M.q;
+        if (r == M.q) r = 0;
+        o[(size_t)i * N] = mont ? to_mont(r, M) : r;
+    }
+}
+
+// ------------------------------------------------------------------ client side
+
+// Signed coefficients -> residues for `rows` moduli starting at mod_off: out[r][n].
+__global__ void k_from_signed(const int64_t* __restrict__ c, uint64_t* __restrict__ out,
+                              int rows, int mod_off, int logN, const ModConst* __restrict__ mods) {
+    const int N = 1 << logN;
+    const int n = blockIdx.y * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int64_t x = c[n];
+    const int r = blockIdx.z;
+    const uint64_t q = mods[mod_off + r].q;
+    uint64_t v;
+    if (x >= 0) v = (uint64_t)x % q;
+    else {
+        uint64_t m = ((uint64_t)(-(x + 1)) + 1u) % q;
+        v = m ? q - m : 0;
+    }
+    out[(size_t)r * N + n] = v;
+    (void)rows;
+}
+
+// Uniform residues: out[r][n] for limb index (limb0 + r) of the generator's counter space.
+__global__ void k_uniform(uint64_t state0, uint64_t* __restrict__ out, int limb0, int mod_off,
+                          int logN, const ModConst* __restrict__ mods) {
+    const int N = 1 << logN;
+    const int n = blockIdx.y * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int r = blockIdx.z;
+    const uint64_t q = mods[mod_off + r].q;
+    const uint64_t ctr = 2ull * ((uint64_t)(limb0 + r) * N + n);
+    const uint64_t hi = draw(state0, ctr), lo = draw(state0, ctr + 1);
+    const uint64_t a_lo = hi * q, a_hi = __umul64hi(hi, q);
+    const uint64_t b_hi = __umul64hi(lo, q);
+    const uint64_t mid = a_lo + b_hi;
+    out[(size_t)r * N + n] = a_hi + (mid < a_lo ? 1u : 0u);
+}
+
+// Discrete Gaussian coefficients (int64) by the cumulative table T[0..19].
+__global__ void k_gaussian(uint64_t state0, int64_t* __restrict__ out, int logN,
+                           const uint64_t* __restrict__ cdt) {
+    const int N = 1 << logN;
+    const int n = blockIdx.y * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const uint64_t u = draw(state0, (uint64_t)n);
+    const uint64_t x = u >> 1;
+    int64_t mag = 0;
+    for (int m = 0; m < 20; ++m) mag += (x >= cdt[m]) ? 1 : 0;
+    out[n] = (u & 1ull) ? -mag : mag;
+}
+
+// Ternary coefficients: v = floor(3u / 2^64) in {0, 1, 2} -> {0, +1, -1}.
+__global__ void k_ternary(uint64_t state0, int64_t* __restrict__ out, int logN) {
+    const int N = 1 << logN;
+    const int n = blockIdx.y * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const uint64_t v = __umul64hi(draw(state0, (uint64_t)n), 3ull);
+    out[n] = v == 2 ? -1 : (int64_t)v;
+}
+
+// Fresh ciphertext, coefficient form: c0 = e + Delta_i m - as_i, where as holds a*s.
+__global__ void k_enc_c0(const int64_t* __restrict__ e, const uint64_t* __restrict__ m,
+                         const uint64_t* __restrict__ as, const ShoupPair* __restrict__ delta,
+                         uint64_t* __restrict__ c0, int L, int logN,
+                         const ModConst* __restrict__ mods) {
+    const int N = 1 << logN;
+    const int n = blockIdx.y * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int i = blockIdx.z;
+    const uint64_t q = mods[i].q;
+    const int64_t x = e[n];
+    uint64_t ev = x >= 0 ? (uint64_t)x % q : (q - ((uint64_t)(-x) % q)) % q;
+    uint64_t dm = mul_shoup(m[n], delta[i].w, delta[i].ws, q);
+    c0[(size_t)i * N + n] = sub_mod(add_mod(ev, dm, q), as[(size_t)i * N + n], q);
+    (void)L;
+}
+
+// x = c0 + c1 * s (NTT domain, s in Montgomery form), rows limbs.
+__global__ void k_dec_phase(const uint64_t* __restrict__ ct, const uint64_t* __restrict__ s_m,
+                            uint64_t* __restrict__ x, int rows, int logN,
+                            const ModConst* __restrict__ mods) {
+    const int N = 1 << logN;
+    const int n = blockIdx.y * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int i = blockIdx.z;
+    const ModConst M = mods[i];
+    const size_t off = (size_t)i * N + n;
+    U128 p{0, 0};
+    mac128(p, ct[off + (size_t)rows * N], s_m[off]);
+    x[off] = add_mod(ct[off], redc(p, M.q, M.qinv_neg), M.q);
+}
+
+// x <- x * s (NTT domain, s in Montgomery form), rows limbs.
+__global__ void k_mul_mont(uint64_t* __restrict__ x, const uint64_t* __restrict__ s_m, int logN,
+                           const ModConst* __restrict__ mods) {
+    const int N = 1 << logN;
+    const int n = blockIdx.y * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int i = blockIdx.z;
+    const ModConst M = mods[i];
+    const size_t off = (size_t)i * N + n;
+    U128 p{0, 0};
+    mac128(p, x[off], s_m[off]);
+    x[off] = redc(p, M.q, M.qinv_neg);
+}
+
+// Galois key digit: b_l = e_l - a_l s_l + [l in digit] (P mod q_l) s(X^g)_l, NTT domain over
+// Q u P (s in Montgomery form; pmodq in Montgomery form).
+__global__ void k_keygen_b(const uint64_t* __restrict__ a, const uint64_t* __restrict__ s_m,
+                           const uint64_t* __restrict__ e, const uint64_t* __restrict__ sg,
+                           uint64_t* __restrict__ b, int i0, int i1, int logN,
+                           const ModConst* __restrict__ mods, const uint64_t* __restrict__ pmodq) {
+    const int N = 1 << logN;
+    const int n = blockIdx.y * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int l = blockIdx.z;
+    const ModConst M = mods[l];
+    const size_t off = (size_t)l * N + n;
+    U128 p{0, 0};
+    mac128(p, a[off], s_m[off]);
+    uint64_t v = sub_mod(e[off], redc(p, M.q, M.qinv_neg), M.q);
+    if (l >= i0 && l < i1) {
+        U128 g{0, 0};
+        mac128(g, sg[off], pmodq[l]);
+        v = add_mod(v, redc(g, M.q, M.qinv_neg), M.q);
+    }
+    b[off] = v;
+}
+
+// Exact BFV decryption rounding, one coefficient per thread:
+//   t x / Q = sum_i y_i t / q_i - v t with y_i = [x_i (Q/q_i)^-1]_{q_i};
+//   write y_i t = a_i q_i + b_i; then m = (sum_i a_i + round(sum_i b_i (Q/q_i) / Q)) mod t,
+// the rounding decided exactly on multi-word integers.
+// cst layout: qhat_inv[L] (ShoupPair as 2 u64) | Qhat[L][W] | Q[W]
+__global__ void k_dec_round(const uint64_t* __restrict__ x, uint64_t* __restrict__ m, int L,
+                            int W, int logN, uint64_t t, const ModConst* __restrict__ mods,
+                            const uint64_t* __restrict__ cst) {
+    const int N = 1 << logN;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const uint64_t* qhinv = cst;
+    const uint64_t* qhat = cst + 2 * L;
+    const uint64_t* Qw = qhat + (size_t)L * W;
+    uint64_t R[HE_DEC_MAX_WORDS + 1];
+    for (int w = 0; w <= W; ++w) R[w] = 0;
+    uint64_t asum = 0;
+    for (int i = 0; i < L; ++i) {
+        const uint64_t q = mods[i].q;
+        uint64_t y = mul_shoup(x[(size_t)i * N + n], qhinv[2 * i], qhinv[2 * i + 1], q);
+        unsigned __int128 yt = (unsigned __int128)y * t;
+        uint64_t a = (uint64_t)(yt / q);
+        uint64_t b = (uint64_t)(yt % q);
+        asum = (asum + a % t) % t;
+        // R += b * Qhat_i
+        uint64_t carry = 0;
+        for (int w = 0; w < W; ++w) {
+            unsigned __int128 p = (unsigned __int128)b * qhat[(size_t)i * W + w] + R[w] + carry;
+            R[w] = (uint64_t)p;
+            carry = (uint64_t)(p >> 64);
+        }
+        R[W] += carry;
+    }
+    // 2R
+    uint64_t R2[HE_DEC_MAX_WORDS + 2];
+    uint64_t c = 0;
+    for (int w = 0; w <= W; ++w) {
+        R2[w] = (R[w] << 1) | c;
+        c = R[w] >> 63;
+    }
+    R2[W + 1] = c;
+    // smallest k with 2R < (2k+1) Q
+    uint64_t T[HE_DEC_MAX_WORDS + 2];
+    for (int w = 0; w < W; ++w) T[w] = Qw[w];
+    T[W] = 0;
+    T[W + 1] = 0;
+    uint64_t k = 0;
+    for (int iter = 0; iter <= L + 1; ++iter) {
+        // compare R2 >= T
+        int ge = 1;
+        for (int w = W + 1; w >= 0; --w) {
+            if (R2[w] != T[w]) {
+                ge = R2[w] > T[w];
+                break;
+            }
+        }
+        if (!ge) break;
+        ++k;
+        // T += 2Q
+        uint64_t cy = 0;
+        for (int w = 0; w <= W + 1; ++w) {
+            uint64_t q2 = w < W ? (Qw[w] << 1) | (w > 0 ? Qw[w - 1] >> 63 : 0)
+                                : (w == W ? Qw[W - 1] >> 63 : 0);
+            unsigned __int128 s = (unsigned __int128)T[w] + q2 + cy;
+            T[w] = (uint64_t)s;
+            cy = (uint64_t)(s >> 64);
+        }
+    }
+    m[n] = (asum + k % t) % t;
+}
+
+// ------------------------------------------------------------------ launch helpers
+
+static inline dim3 grid_nx(int items, int N, int z) {
+    return dim3(items, (N + 255) / 256, z);
+}
+
+void launch_automorph(he_ctx* c, const uint64_t* in, size_t in_stride, uint64_t* out,
+                      size_t out_stride, int items, int rows, uint32_t g) {
+    ++c->launches;
+    k_automorph<<<grid_nx(items, c->N, 1), 256, 0, c->stream>>>(in, in_stride, out, out_stride,
+                                                                 rows, c->logN, g);
+}
+
+void launch_modup(he_ctx* c, const uint64_t* x_coeff, size_t xc_stride, const uint64_t* x_ntt,
+                  size_t xn_stride, uint32_t g_own, uint64_t* out, size_t out_stride, int items) {
+    ++c->launches;
+    k_modup<<<grid_nx(items, c->N, c->dnum), 256, 0, c->stream>>>(
+        x_coeff, xc_stride, x_ntt, xn_stride, g_own, out, out_stride, c->L, c->K, c->alpha,
+        c->logN, c->d_mod, c->d_modup_inv, c->d_modup_c);
+}
+
+void launch_ks_inner(he_ctx* c, const uint64_t* D, size_t d_stride, const uint64_t* key,
+                     uint64_t* u, size_t u_stride, int items, uint32_t g) {
+    ++c->launches;
+    k_ks_inner<<<grid_nx(items, c->N, c->L + c->K), 256, 0, c->stream>>>(
+        D, d_stride, key, u, u_stride, c->L + c->K, c->dnum, c->logN, g, c->d_mod);
+}
+
+void launch_moddown_conv(he_ctx* c, const uint64_t* u, size_t u_stride, uint64_t* v,
+                         size_t v_stride, int items) {
+    ++c->launches;
+    k_moddown_conv<<<grid_nx(items, c->N, 2), 256, 0, c->stream>>>(
+        u, u_stride, v, v_stride, c->L, c->K, c->logN, c->d_mod, c->d_md_inv, c->d_md_c);
+}
+
+void launch_ks_combine(he_ctx* c, const uint64_t* u, size_t u_stride, const uint64_t* v,
+                       size_t v_stride, const uint64_t* const* c0p, const uint64_t* const* basep,
+                       uint64_t* const* outp, int items, uint32_t g) {
+    ++c->launches;
+    k_ks_combine<<<grid_nx(items, c->N, c->L), 256, 0, c->stream>>>(
+        u, u_stride, v, v_stride, c0p, basep, outp, c->L, c->K, c->logN, g, c->d_mod,
+        c->d_md_pinv);
+}
+
+void launch_mac(he_ctx* c, const uint64_t* const* X, const uint64_t* const* P, int T,
+                const uint64_t* const* accin, uint64_t* const* outp, int n_out, int L) {
+    ++c->launches;
+    k_mac<<<grid_nx(n_out, c->N, L), 256, 0, c->stream>>>(X, P, T, accin, outp, L, c->logN,
+                                                          c->d_mod);
+}
+
+void launch_convpack(he_ctx* c, const uint64_t* x, int B, int r, int O_c, const uint64_t* wm,
+                     uint64_t* const* outp, int L) {
+    ++c->launches;
+    k_convpack<<<grid_nx(B * O_c, c->N, L), 256, 0, c->stream>>>(x, r, O_c, wm, outp, L,
+                                                                 c->logN, c->d_mod);
+}
+
+void launch_add(he_ctx* c, const uint64_t* const* a, const uint64_t* const* b,
+                uint64_t* const* o, int items, int L) {
+    ++c->launches;
+    k_add<<<grid_nx(items, c->N, 2 * L), 256, 0, c->stream>>>(a, b, o, L, 2, c->logN, c->d_mod);
+}
+
+void launch_to_mont(he_ctx* c, uint64_t* data, int items, int rows, int period, int mod_off) {
+    ++c->launches;
+    k_to_mont<<<grid_nx(items, c->N, rows), 256, 0, c->stream>>>(data, rows, period, mod_off,
+                                                                 c->logN, c->d_mod);
+}
+
+void launch_from_mont(he_ctx* c, uint64_t* data, int items, int rows, int period, int mod_off) {
+    ++c->launches;
+    k_from_mont<<<grid_nx(items, c->N, rows), 256, 0, c->stream>>>(data, rows, period, mod_off,
+                                                                   c->logN, c->d_mod);
+}
+
+void launch_rescale_spread(he_ctx* c, const uint64_t* last, uint64_t* s, int items, int L) {
+    ++c->launches;
+    k_rescale_spread<<<grid_nx(items, c->N, 2), 256, 0, c->stream>>>(last, s, L, c->logN,
+                                                                     c->d_mod);
+}
+
+void launch_rescale_combine(he_ctx* c, const uint64_t* const* xp, const uint64_t* s,
+                            uint64_t* const* outp, int items, int L) {
+    ++c->launches;
+    k_rescale_combine<<<grid_nx(items, c->N, 2 * (L - 1)), 256, 0, c->stream>>>(
+        xp, s, outp, L, c->logN, c->d_mod, c->d_rs_inv + (size_t)(L - 1) * c->L);
+}
+
+void launch_slots_to_ntt(he_ctx* c, const int64_t* v, uint64_t* buf, int items) {
+    ++c->launches;
+    k_slots_to_ntt<<<grid_nx(items, c->N, 1), 256, 0, c->stream>>>(v, buf, c->d_slot_pos,
+                                                                    c->logN, c->prm.t);
+}
+
+void launch_ntt_to_slots(he_ctx* c, const uint64_t* buf, int64_t* v, int items) {
+    ++c->launches;
+    k_ntt_to_slots<<<grid_nx(items, c->N, 1), 256, 0, c->stream>>>(buf, v, c->d_slot_pos,
+                                                                    c->logN);
+}
+
+void launch_lift(he_ctx* c, const uint64_t* m, uint64_t* out, int items, int L, int mont) {
+    ++c->launches;
+    k_lift<<<grid_nx(items, c->N, 1), 256, 0, c->stream>>>(m, out, L, c->logN, c->prm.t, mont,
+                                                           c->d_mod);
+}
+
+void launch_from_signed(he_ctx* c, const int64_t* v, uint64_t* out, int rows, int mod_off) {
+    ++c->launches;
+    k_from_signed<<<grid_nx(1, c->N, rows), 256, 0, c->stream>>>(v, out, rows, mod_off, c->logN,
+                                                                 c->d_mod);
+}
+
+void launch_uniform(he_ctx* c, uint64_t state0, uint64_t* out, int rows, int limb0, int mod_off) {
+    ++c->launches;
+    k_uniform<<<grid_nx(1, c->N, rows), 256, 0, c->stream>>>(state0, out, limb0, mod_off,
+                                                             c->logN, c->d_mod);
+}
+
+void launch_gaussian(he_ctx* c, uint64_t state0, int64_t* out) {
+    ++c->launches;
+    k_gaussian<<<grid_nx(1, c->N, 1), 256, 0, c->stream>>>(state0, out, c->logN, c->d_cdt);
+}
+
+void launch_ternary(he_ctx* c, uint64_t state0, int64_t* out) {
+    ++c->launches;
+    k_ternary<<<grid_nx(1, c->N, 1), 256, 0, c->stream>>>(state0, out, c->logN);
+}
+
+void launch_enc_c0(he_ctx* c, const int64_t* e, const uint64_t* m, const uint64_t* as,
+                   const ShoupPair* delta, uint64_t* c0) {
+    ++c->launches;
+    k_enc_c0<<<grid_nx(1, c->N, c->L), 256, 0, c->stream>>>(e, m, as, delta, c0, c->L, c->logN,
+                                                            c->d_mod);
+}
+
+void launch_dec_phase(he_ctx* c, const uint64_t* ct, const uint64_t* s_m, uint64_t* x, int rows) {
+    ++c->launches;
+    k_dec_phase<<<grid_nx(1, c->N, rows), 256, 0, c->stream>>>(ct, s_m, x, rows, c->logN,
+                                                               c->d_mod);
+}
+
+void launch_dec_round(he_ctx* c, const uint64_t* x, uint64_t* m, int L, int W,
+                      const uint64_t* cst) {
+    ++c->launches;
+    k_dec_round<<<(c->N + 127) / 128, 128, 0, c->stream>>>(x, m, L, W, c->logN, c->prm.t,
+                                                           c->d_mod, cst);
+}
+
+void launch_dec_phase_mul(he_ctx* c, uint64_t* x, const uint64_t* s_m, int rows) {
+    ++c->launches;
+    k_mul_mont<<<grid_nx(1, c->N, rows), 256, 0, c->stream>>>(x, s_m, c->logN, c->d_mod);
+}
+
+void launch_keygen_b(he_ctx* c, const uint64_t* a, const uint64_t* s_m, const uint64_t* e,
+                     const uint64_t* sg, uint64_t* b, int i0, int i1) {
+    ++c->launches;
+    k_keygen_b<<<grid_nx(1, c->N, c->L + c->K), 256, 0, c->stream>>>(a, s_m, e, sg, b, i0, i1,
+                                                                     c->logN, c->d_mod, c->d_pmodq);
+}
+
+void launch_gather_last(he_ctx* c, const uint64_t* const* xp, uint64_t* last, int items, int L) {
+    ++c->launches;
+    k_gather_last<<<grid_nx(items, c->N, 2), 256, 0, c->stream>>>(xp, last, L, c->logN);
+}

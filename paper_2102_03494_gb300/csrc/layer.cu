@@ -1,0 +1,388 @@
+// layer.cu -- the encrypted FFConv layer, FFConv packing DP-HI2C-CP (Sec. 4.2, Fig. 4).
+//
+// W1 (d x d, r = O'_c low-rank filters) under DensePack (Sec. 3.2, Fig. 1), the DP -> CP
+// transition for a 1 x 1 kernel (Table III), W2 (1 x 1, r -> O_c) under ConvPack (Table II).
+//
+// HE_DP_DOT (the paper's DensePack dot products, Fig. 1a-c): for every low-rank channel c'
+// and output position o the filter, zero-padded to the input size at its shifted location,
+// multiplies the input; rotate-and-sum prod += rot(prod, 2^e), e < k, accumulates it, where
+// 2^k covers the occupied slots (k = log2(N/2) and a final row swap when the input fills both
+// rows; Table VIII's 7000 = 500 x 14 and 120 = 10 x 12).  One-hot masks then gather the r*S
+// dot products into r ciphertexts (no rotation: Table III, DP-HI2C-CP, d = 1).
+//
+// HE_DP_SHIFT (hoisted taps): one hoisted rotation of the input per filter tap
+// delta = (i - pad) I_w + (j - pad) and a plaintext per (c', tap) holding W1[c', ci, i, j] at
+// the output base slots; channels folded with rotations by B_c 2^e.
+#include <algorithm>
+#include <vector>
+
+#include "eval.cuh"
+#include "kernels.cuh"
+
+namespace {
+
+struct LayoutInfo {
+    int O_h, O_w, S, hw, B_c, taps, fold;
+    int sum_depth;        // DP_DOT rotate-and-sum steps within a row
+    bool both_rows;       // DP_DOT input spills into row 1 (adds the row swap)
+};
+
+int ceil_log2(long long x) {
+    int k = 0;
+    while ((1ll << k) < x) ++k;
+    return k;
+}
+
+// After k rotate-and-sum steps slot o holds sum_{m < 2^k} prod[o + m]; valid when every
+// output's zero-padded filter lies inside [o, o + 2^k).
+bool window_covers(const he_layout& y, const LayoutInfo& li, int k) {
+    for (int oh = 0; oh < li.O_h; ++oh)
+        for (int ow = 0; ow < li.O_w; ++ow) {
+            int o = oh * li.O_w + ow;
+            int hmin = 1 << 30, hmax = -1, wmin = 1 << 30, wmax = -1;
+            for (int i = 0; i < y.d; ++i) {
+                int h = y.stride * oh + i - y.pad;
+                if (h >= 0 && h < y.I_h) hmin = std::min(hmin, h), hmax = std::max(hmax, h);
+                int w = y.stride * ow + i - y.pad;
+                if (w >= 0 && w < y.I_w) wmin = std::min(wmin, w), wmax = std::max(wmax, w);
+            }
+            if (hmax < 0 || wmax < 0) continue;
+            long long lo = (long long)hmin * y.I_w + wmin;
+            long long hi = (long long)(y.I_c - 1) * li.hw + (long long)hmax * y.I_w + wmax;
+            if (lo < o || hi >= o + (1ll << k)) return false;
+        }
+    return true;
+}
+
+int layout_info(const he_ctx* c, const he_layout* y, LayoutInfo* li, std::string* why) {
+    if (y->I_c < 1 || y->I_h < 1 || y->I_w < 1 || y->d < 1 || y->stride < 1 || y->pad < 0 ||
+        y->r < 1 || y->O_c < 1 || (y->pack != HE_DP_DOT && y->pack != HE_DP_SHIFT)) {
+        *why = "layout fields out of range";
+        return HE_EINVAL;
+    }
+    li->O_h = (y->I_h + 2 * y->pad - y->d) / y->stride + 1;
+    li->O_w = (y->I_w + 2 * y->pad - y->d) / y->stride + 1;
+    if (y->I_h + 2 * y->pad < y->d || y->I_w + 2 * y->pad < y->d || li->O_h < 1 || li->O_w < 1) {
+        *why = "filter larger than the padded input";
+        return HE_EINVAL;
+    }
+    li->S = li->O_h * li->O_w;
+    li->hw = y->I_h * y->I_w;
+    li->B_c = y->I_c == 1 ? li->hw : (1 << ceil_log2(li->hw));
+    li->taps = y->d * y->d;
+    li->fold = ceil_log2(y->I_c);
+    const long long half = c->N / 2;
+    li->sum_depth = 0;
+    li->both_rows = false;
+    if (y->pack == HE_DP_DOT) {
+        long long span = (long long)y->I_c * li->hw;
+        if (span > c->N || li->S > half) {
+            *why = "DP_DOT input must fit in N slots and its output in N/2";
+            return HE_EINVAL;
+        }
+        const int full = ceil_log2(half);
+        if (span > half) {
+            li->sum_depth = full;
+            li->both_rows = true;
+        } else {
+            int k = ceil_log2(span);
+            li->sum_depth = (k < full && window_covers(*y, *li, k)) ? k : full;
+        }
+    } else {
+        if ((long long)li->B_c * (1ll << li->fold) > half) {
+            *why = "DP_SHIFT channel blocks must fit in one row of N/2 slots";
+            return HE_EINVAL;
+        }
+    }
+    return HE_OK;
+}
+
+std::vector<int32_t> layer_steps(const he_layout& y, const LayoutInfo& li) {
+    std::vector<int32_t> st;
+    if (y.pack == HE_DP_DOT) {
+        for (int e = 0; e < li.sum_depth; ++e) st.push_back(1 << e);
+        if (li.both_rows) st.push_back(HE_ROW_SWAP);
+    } else {
+        for (int i = 0; i < y.d; ++i)
+            for (int j = 0; j < y.d; ++j) {
+                int dl = (i - y.pad) * y.I_w + (j - y.pad);
+                if (dl != 0) st.push_back(dl);
+            }
+        for (int e = 0; e < li.fold; ++e) st.push_back(li.B_c << e);
+    }
+    return st;
+}
+
+// ---- slot vectors of the schedules' plaintexts (zeroed beforehand)
+
+// DP_SHIFT: plaintext (c', i, j) holds W1[c', ci, i, j] at slot ci*B_c + (s oh) I_w + s ow for
+// every output position whose input pixel (s oh + i - pad, s ow + j - pad) is inside.
+__global__ void k_dp_shift_slots(const int32_t* __restrict__ w1, int I_c, int I_h, int I_w, int d,
+                                 int s, int pad, int r, int O_h, int O_w, int B_c, int logN,
+                                 int64_t* __restrict__ out) {
+    const int N = 1 << logN;
+    const int pt = blockIdx.x;  // (c' * d + i) * d + j
+    const int j = pt % d, i = (pt / d) % d, cp = pt / (d * d);
+    const int per = I_c * O_h * O_w;
+    for (int idx = threadIdx.x + blockIdx.y * blockDim.x; idx < per; idx += blockDim.x * gridDim.y) {
+        int ow = idx % O_w, oh = (idx / O_w) % O_h, ci = idx / (O_w * O_h);
+        int h = s * oh + i - pad, w = s * ow + j - pad;
+        if (h < 0 || h >= I_h || w < 0 || w >= I_w) continue;
+        int slot = ci * B_c + (s * oh) * I_w + s * ow;
+        out[(size_t)pt * N + slot] = w1[((cp * I_c + ci) * d + i) * d + j];
+    }
+    (void)r;
+}
+
+// DP_DOT: plaintext (c', o) (index c' S + o) is filter c' zero-padded at output o; plaintext
+// r S + o is the one-hot mask of slot o.
+__global__ void k_dp_dot_slots(const int32_t* __restrict__ w1, int I_c, int I_h, int I_w, int d,
+                               int s, int pad, int r, int O_w, int S, int logN,
+                               int64_t* __restrict__ out) {
+    const int N = 1 << logN;
+    const int pt = blockIdx.x;
+    if (pt >= r * S) {
+        if (threadIdx.x == 0 && blockIdx.y == 0) out[(size_t)pt * N + (pt - r * S)] = 1;
+        return;
+    }
+    const int cp = pt / S, o = pt % S;
+    const int oh = o / O_w, ow = o % O_w;
+    const int per = I_c * d * d;
+    const int hw = I_h * I_w;
+    for (int idx = threadIdx.x + blockIdx.y * blockDim.x; idx < per; idx += blockDim.x * gridDim.y) {
+        int j = idx % d, i = (idx / d) % d, ci = idx / (d * d);
+        int h = s * oh + i - pad, w = s * ow + j - pad;
+        if (h < 0 || h >= I_h || w < 0 || w >= I_w) continue;
+        out[(size_t)pt * N + ci * hw + h * I_w + w] = w1[((cp * I_c + ci) * d + i) * d + j];
+    }
+}
+
+}  // namespace
+
+extern "C" int he_ffconv_required_steps(const he_ctx* ctx, const he_layout* layout,
+                                        int32_t* steps_out, int cap) {
+    if (!ctx || !layout) return HE_EINVAL;
+    LayoutInfo li;
+    std::string why;
+    if (layout_info(ctx, layout, &li, &why)) return HE_EINVAL;
+    std::vector<int32_t> st = layer_steps(*layout, li);
+    for (int i = 0; i < (int)st.size() && i < cap && steps_out; ++i) steps_out[i] = st[i];
+    return (int)st.size();
+}
+
+extern "C" int he_ffconv_layer_batch(he_ctx* ctx, const he_ct* ct_in, int B,
+                                     const int32_t* lowrank_w, const int32_t* restore_w,
+                                     const he_layout* layout, he_ct* ct_out) {
+    if (!ctx) return HE_EINVAL;
+    if (!ct_in || !lowrank_w || !restore_w || !layout || !ct_out || B < 1)
+        return he_fail(ctx, HE_EINVAL, "he_ffconv_layer: null argument");
+    if (!ctx->batching) return he_fail(ctx, HE_EINVAL, "he_ffconv_layer: t is not 1 mod 2N");
+    LayoutInfo li;
+    std::string why;
+    int rc = layout_info(ctx, layout, &li, &why);
+    if (rc) return he_fail(ctx, rc, "he_ffconv_layer: " + why);
+    const he_layout& y = *layout;
+    const int L = ctx->L, Lout = y.modswitch ? L - 1 : L;
+    if (y.modswitch && L < 2) return he_fail(ctx, HE_EINVAL, "he_ffconv_layer: modswitch needs two primes");
+    for (int b = 0; b < B; ++b)
+        if ((rc = check_ct(ctx, &ct_in[b], L, HE_NTT, "he_ffconv_layer input"))) return rc;
+    for (int o = 0; o < B * y.O_c; ++o)
+        if ((rc = check_ct(ctx, &ct_out[o], Lout, -1, "he_ffconv_layer output"))) return rc;
+    const std::vector<int32_t> steps = layer_steps(y, li);
+    std::vector<uint32_t> gs;
+    for (int32_t st : steps) {
+        uint32_t g = galois_elt(ctx, st);
+        const uint64_t* k = nullptr;
+        if ((rc = he_get_key(ctx, g, &k))) return rc;
+        gs.push_back(g);
+    }
+
+    const size_t N = ctx->N, ct = 2 * (size_t)L * N;
+    const int r = y.r, O_c = y.O_c;
+    const bool dot = y.pack == HE_DP_DOT;
+    const int n_pt = dot ? r * li.S + li.S : r * li.taps;
+    const int n_prod = dot ? B * r * li.S : B * li.taps;      // ciphertexts fed to the MAC
+    // ciphertexts key-switched per launch: all of them when the scratch allows
+    const int chunk = std::min(dot ? n_prod : (li.fold ? B * r : B), rotation_chunk(ctx));
+    const int rot_items = chunk;
+    size_t need = (size_t)B * ct                              // X
+                  + (size_t)n_pt * (2 * N + (size_t)L * N)     // slots, tmp, plaintexts
+                  + (size_t)n_prod * ct * (dot ? 2 : 1)        // products (double buffer for DP_DOT)
+                  + (size_t)2 * B * r * ct                     // accumulators (double buffer)
+                  + (size_t)rot_items * rot_scratch_per_item(ctx)
+                  + (y.modswitch ? (size_t)B * O_c * (ct + 2 * N + 2 * (L - 1) * N) : 0) + 1024;
+    if ((rc = arena_reserve(ctx, need))) return rc;
+    arena_reset(ctx);
+    uint64_t* X = arena_take(ctx, (size_t)B * ct);
+    int64_t* slots = (int64_t*)arena_take(ctx, (size_t)n_pt * N);
+    uint64_t* tmp = arena_take(ctx, (size_t)n_pt * N);
+    uint64_t* pts = arena_take(ctx, (size_t)n_pt * L * N);
+    uint64_t* PR = arena_take(ctx, (size_t)n_prod * ct);
+    uint64_t* PR2 = dot ? arena_take(ctx, (size_t)n_prod * ct) : nullptr;
+    uint64_t* A = arena_take(ctx, (size_t)B * r * ct);
+    uint64_t* A2 = arena_take(ctx, (size_t)B * r * ct);
+    RotBufs rb = rot_bufs_take(ctx, rot_items);
+    uint64_t* Y = y.modswitch ? arena_take(ctx, (size_t)B * O_c * ct) : nullptr;
+    uint64_t* last = y.modswitch ? arena_take(ctx, (size_t)B * O_c * 2 * N) : nullptr;
+    uint64_t* sprd = y.modswitch ? arena_take(ctx, (size_t)B * O_c * 2 * (L - 1) * N) : nullptr;
+    if (!rb.v || (y.modswitch && !sprd)) return he_fail(ctx, HE_ENOMEM, "he_ffconv_layer: scratch");
+
+    // inputs -> contiguous X
+    for (int b = 0; b < B; ++b)
+        HE_CHECK_CUDA(ctx, cudaMemcpyAsync(X + b * ct, ct_in[b].data, ct * 8, cudaMemcpyDeviceToDevice,
+                                           ctx->stream));
+    // (a1) plaintexts: slot vectors from the integer weights, encoded in Montgomery form
+    const size_t w1n = (size_t)r * y.I_c * y.d * y.d;
+    const int32_t* d_w1 = (const int32_t*)upload_small(ctx, lowrank_w, w1n * 4);
+    if (!d_w1) return he_fail(ctx, HE_EINVAL, "he_ffconv_layer: W1 too large for staging");
+    HE_CHECK_CUDA(ctx, cudaMemsetAsync(slots, 0, (size_t)n_pt * N * 8, ctx->stream));
+    ++ctx->launches;
+    if (dot)
+        k_dp_dot_slots<<<dim3(n_pt, 1), 256, 0, ctx->stream>>>(d_w1, y.I_c, y.I_h, y.I_w, y.d, y.stride,
+                                                               y.pad, r, li.O_w, li.S, ctx->logN, slots);
+    else
+        k_dp_shift_slots<<<dim3(n_pt, 4), 256, 0, ctx->stream>>>(d_w1, y.I_c, y.I_h, y.I_w, y.d,
+                                                                 y.stride, y.pad, r, li.O_h, li.O_w,
+                                                                 li.B_c, ctx->logN, slots);
+    encode_device(ctx, slots, n_pt, tmp, pts, 1);
+
+    if (dot) {
+        // prod[b][c'][o] = X[b] * filter(c', o)
+        std::vector<const uint64_t*> xs(n_prod), ps(n_prod);
+        std::vector<uint64_t*> os(n_prod);
+        for (int b = 0; b < B; ++b)
+            for (int q = 0; q < r * li.S; ++q) {
+                int it = b * r * li.S + q;
+                xs[it] = X + b * ct;
+                ps[it] = pts + (size_t)q * L * N;
+                os[it] = PR + (size_t)it * ct;
+            }
+        auto xp = upload_ptrs(ctx, xs);
+        auto pp = upload_ptrs(ctx, ps);
+        auto op = upload_out_ptrs(ctx, os);
+        if (!xp || !pp || !op) return he_fail(ctx, HE_ECUDA, "pointer table upload failed");
+        launch_mac(ctx, xp, pp, 1, nullptr, op, n_prod, L);
+        ctx->ops[0] += n_prod;
+        // rotate-and-sum: PR2 = PR + rot(PR, step), then swap
+        for (size_t si = 0; si < steps.size(); ++si) {
+            std::vector<uint64_t*> outs(n_prod);
+            for (int it = 0; it < n_prod; ++it) outs[it] = PR2 + (size_t)it * ct;
+            if ((rc = rotate_contig(ctx, PR, n_prod, gs[si], PR, outs, rb, chunk))) return rc;
+            std::swap(PR, PR2);
+        }
+        // DP -> CP: ct_w1[b][c'] = sum_o prod[b][c'][o] * mask_o
+        const int tmax = max_mac_terms(ctx);
+        for (int o0 = 0; o0 < li.S; o0 += tmax) {
+            int T = std::min(tmax, li.S - o0);
+            std::vector<const uint64_t*> mx((size_t)B * r * T), mp((size_t)B * r * T), ai;
+            std::vector<uint64_t*> ao(B * r);
+            for (int q = 0; q < B * r; ++q) {
+                for (int t = 0; t < T; ++t) {
+                    mx[(size_t)q * T + t] = PR + ((size_t)q * li.S + o0 + t) * ct;
+                    mp[(size_t)q * T + t] = pts + (size_t)(r * li.S + o0 + t) * L * N;
+                }
+                ao[q] = A + (size_t)q * ct;
+                ai.push_back(o0 ? A + (size_t)q * ct : nullptr);
+            }
+            auto a1 = upload_ptrs(ctx, mx);
+            auto a2 = upload_ptrs(ctx, mp);
+            auto a3 = o0 ? upload_ptrs(ctx, ai) : nullptr;
+            auto a4 = upload_out_ptrs(ctx, ao);
+            if (!a1 || !a2 || !a4 || (o0 && !a3)) return he_fail(ctx, HE_ECUDA, "pointer table upload failed");
+            launch_mac(ctx, a1, a2, T, a3, a4, B * r, L);
+        }
+        ctx->ops[0] += (uint64_t)B * r * li.S;
+        ctx->ops[1] += (uint64_t)B * r * (li.S - 1);
+    } else {
+        // hoisted rotations of every input by every non-zero tap offset
+        std::vector<uint32_t> hg;
+        std::vector<int> tap_of;
+        std::vector<uint64_t*> outs;
+        int tap = 0;
+        for (int i = 0; i < y.d; ++i)
+            for (int j = 0; j < y.d; ++j, ++tap) {
+                int dl = (i - y.pad) * y.I_w + (j - y.pad);
+                if (dl == 0) {
+                    for (int b = 0; b < B; ++b)
+                        HE_CHECK_CUDA(ctx, cudaMemcpyAsync(PR + ((size_t)b * li.taps + tap) * ct, X + b * ct,
+                                                           ct * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+                    continue;
+                }
+                hg.push_back(galois_elt(ctx, dl));
+                for (int b = 0; b < B; ++b) outs.push_back(PR + ((size_t)b * li.taps + tap) * ct);
+            }
+        for (int b0 = 0; b0 < B; b0 += rot_items) {
+            int nb = std::min(rot_items, B - b0);
+            std::vector<uint64_t*> o2;
+            for (size_t s = 0; s < hg.size(); ++s)
+                for (int b = 0; b < nb; ++b) o2.push_back(outs[s * B + b0 + b]);
+            if ((rc = rotate_hoisted_contig(ctx, X + (size_t)b0 * ct, nb, hg, o2, rb))) return rc;
+        }
+        // acc[b][c'] = sum_tap R[b][tap] * pt[c'][tap]
+        std::vector<const uint64_t*> mx((size_t)B * r * li.taps), mp((size_t)B * r * li.taps);
+        std::vector<uint64_t*> ao(B * r);
+        for (int b = 0; b < B; ++b)
+            for (int cp = 0; cp < r; ++cp) {
+                int q = b * r + cp;
+                for (int t = 0; t < li.taps; ++t) {
+                    mx[(size_t)q * li.taps + t] = PR + ((size_t)b * li.taps + t) * ct;
+                    mp[(size_t)q * li.taps + t] = pts + ((size_t)cp * li.taps + t) * L * N;
+                }
+                ao[q] = A + (size_t)q * ct;
+            }
+        auto a1 = upload_ptrs(ctx, mx);
+        auto a2 = upload_ptrs(ctx, mp);
+        auto a4 = upload_out_ptrs(ctx, ao);
+        if (!a1 || !a2 || !a4) return he_fail(ctx, HE_ECUDA, "pointer table upload failed");
+        launch_mac(ctx, a1, a2, li.taps, nullptr, a4, B * r, L);
+        ctx->ops[0] += (uint64_t)B * r * li.taps;
+        ctx->ops[1] += (uint64_t)B * r * (li.taps - 1);
+        // channel fold: acc += rot(acc, B_c 2^e)
+        for (int e = 0; e < li.fold; ++e) {
+            std::vector<uint64_t*> o(B * r);
+            for (int q = 0; q < B * r; ++q) o[q] = A2 + (size_t)q * ct;
+            if ((rc = rotate_contig(ctx, A, B * r, galois_elt(ctx, li.B_c << e), A, o, rb, rot_items)))
+                return rc;
+            std::swap(A, A2);
+        }
+    }
+
+    // W2 under ConvPack: ct_out[b][c] = sum_c' W2[c][c'] ct_w1[b][c'] (scalar plaintexts)
+    std::vector<uint64_t> wm((size_t)O_c * r * L);
+    for (int c = 0; c < O_c; ++c)
+        for (int cp = 0; cp < r; ++cp)
+            for (int i = 0; i < L; ++i) {
+                uint64_t q = ctx->mods[i];
+                int64_t w = restore_w[c * r + cp];
+                uint64_t wr = w >= 0 ? (uint64_t)w % q : (q - ((uint64_t)(-w) % q)) % q;
+                wm[((size_t)c * r + cp) * L + i] = h_to_mont(wr, q);
+            }
+    const uint64_t* d_wm = (const uint64_t*)upload_small(ctx, wm.data(), wm.size() * 8);
+    if (!d_wm) return he_fail(ctx, HE_EINVAL, "he_ffconv_layer: W2 too large for staging");
+    std::vector<uint64_t*> dst(B * O_c);
+    for (int o = 0; o < B * O_c; ++o) {
+        dst[o] = y.modswitch ? Y + (size_t)o * ct : ct_out[o].data;
+        ct_out[o].domain = HE_NTT;
+    }
+    auto dp = upload_out_ptrs(ctx, dst);
+    if (!dp) return he_fail(ctx, HE_ECUDA, "pointer table upload failed");
+    launch_convpack(ctx, A, B, r, O_c, d_wm, dp, L);
+    ctx->ops[0] += (uint64_t)B * O_c * r;
+    ctx->ops[1] += (uint64_t)B * O_c * (r - 1);
+    if ((rc = he_launch_check(ctx, "he_ffconv_layer"))) return rc;
+    if (y.modswitch) {
+        std::vector<const uint64_t*> xs(B * O_c);
+        std::vector<uint64_t*> os(B * O_c);
+        for (int o = 0; o < B * O_c; ++o) {
+            xs[o] = Y + (size_t)o * ct;
+            os[o] = ct_out[o].data;
+        }
+        if ((rc = rescale_items(ctx, xs, os, L, last, sprd))) return rc;
+    }
+    return HE_OK;
+}
+
+extern "C" int he_ffconv_layer(he_ctx* ctx, const he_ct* ct_in, const int32_t* lowrank_w,
+                               const int32_t* restore_w, const he_layout* layout, he_ct* ct_out) {
+    return he_ffconv_layer_batch(ctx, ct_in, 1, lowrank_w, restore_w, layout, ct_out);
+}

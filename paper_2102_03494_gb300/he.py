@@ -1,0 +1,338 @@
+"""Thin Python binding of libhe.so (include/he.h): argument marshalling only.
+
+Every function here forwards to the C entry point of the same name; all arithmetic runs in the
+library's CUDA kernels.  Device buffers are torch tensors (dtype int64 used as a container for
+uint64 residues) on the current CUDA device; host arrays are numpy.  There is no CPU fallback:
+if the library is missing or fails to load, `lib()` raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HE_OK, HE_EINVAL, HE_ENOMEM, HE_ENOKEY, HE_ECUDA, HE_ETIMEOUT = 0, -1, -2, -3, -4, -5
+HE_COEFF, HE_NTT = 0, 1
+HE_DP_DOT, HE_DP_SHIFT = 0, 1
+HE_ROW_SWAP = 0x7FFFFFFF
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhe.so")
+
+
+class HeParams(ctypes.Structure):
+    _fields_ = [("log_n", ctypes.c_uint32), ("n_q", ctypes.c_uint32), ("q_bits", ctypes.c_uint32),
+                ("n_p", ctypes.c_uint32), ("p_bits", ctypes.c_uint32), ("alpha", ctypes.c_uint32),
+                ("t", ctypes.c_uint64)]
+
+
+class HeCt(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("n_polys", ctypes.c_uint32),
+                ("n_limbs", ctypes.c_uint32), ("domain", ctypes.c_int32)]
+
+
+class HeLayout(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in
+                ("I_c", "I_h", "I_w", "d", "stride", "pad", "r", "O_c", "pack", "modswitch")]
+
+
+class HeError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+_P = ctypes.c_void_p
+_U64P = ctypes.POINTER(ctypes.c_uint64)
+_I64P = ctypes.POINTER(ctypes.c_int64)
+_I32P = ctypes.POINTER(ctypes.c_int32)
+_CTP = ctypes.POINTER(HeCt)
+_SIGS = {
+    "he_ctx_create": ([ctypes.POINTER(HeParams), _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "he_ctx_destroy": ([_P], None),
+    "he_last_error": ([_P], ctypes.c_char_p),
+    "he_set_stream": ([_P, _P], ctypes.c_int),
+    "he_get_moduli": ([_P, _U64P, ctypes.c_int], ctypes.c_int),
+    "he_op_counts": ([_P, _U64P], None),
+    "he_reset_op_counts": ([_P], None),
+    "he_launch_count": ([_P], ctypes.c_uint64),
+    "he_gaussian_table": ([_U64P], None),
+    "he_keygen_secret": ([_P, ctypes.c_uint64, _I64P], ctypes.c_int),
+    "he_keygen_galois": ([_P, _I64P, ctypes.c_uint64, _I32P, ctypes.c_int], ctypes.c_int),
+    "he_export_galois": ([_P, ctypes.c_int32, _U64P], ctypes.c_int),
+    "he_load_keys": ([_P, _U64P, _I32P, ctypes.c_int], ctypes.c_int),
+    "he_encrypt": ([_P, _I64P, _I64P, ctypes.c_uint64, _CTP], ctypes.c_int),
+    "he_decrypt": ([_P, _I64P, _CTP, _I64P], ctypes.c_int),
+    "he_to_ntt": ([_P, _CTP], ctypes.c_int),
+    "he_to_coeff": ([_P, _CTP], ctypes.c_int),
+    "he_encode": ([_P, _I64P, _P], ctypes.c_int),
+    "he_rotate": ([_P, _CTP, ctypes.c_int32, _CTP], ctypes.c_int),
+    "he_rotate_batch": ([_P, _CTP, ctypes.c_int, ctypes.c_int32, _CTP], ctypes.c_int),
+    "he_rotate_hoisted": ([_P, _CTP, _I32P, ctypes.c_int, _CTP], ctypes.c_int),
+    "he_mul_plain_acc": ([_P, _CTP, _P, ctypes.c_int, _CTP], ctypes.c_int),
+    "he_add": ([_P, _CTP, _CTP, _CTP], ctypes.c_int),
+    "he_rescale": ([_P, _CTP, _CTP], ctypes.c_int),
+    "he_ffconv_layer": ([_P, _CTP, _I32P, _I32P, ctypes.POINTER(HeLayout), _CTP], ctypes.c_int),
+    "he_ffconv_layer_batch": ([_P, _CTP, ctypes.c_int, _I32P, _I32P, ctypes.POINTER(HeLayout), _CTP],
+                              ctypes.c_int),
+    "he_ffconv_required_steps": ([_P, ctypes.POINTER(HeLayout), _I32P, ctypes.c_int], ctypes.c_int),
+    "he_ntt": ([_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+}
+_lib = None
+
+
+def lib():
+    """Load libhe.so (build it first with __graft_entry__.build() or build_ext.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return sorted(_SIGS)
+
+
+def _i64(a):
+    a = np.ascontiguousarray(a, dtype=np.int64)
+    return a, a.ctypes.data_as(_I64P)
+
+
+def _i32(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(_I32P)
+
+
+def _u64(a):
+    a = np.ascontiguousarray(a, dtype=np.uint64)
+    return a, a.ctypes.data_as(_U64P)
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("no CUDA device: the library has no CPU path")
+    return torch
+
+
+class Context:
+    """An he_ctx plus the marshalling helpers; methods are named after the C entry points."""
+
+    def __init__(self, log_n, n_q, n_p, alpha, t=65537, q_bits=50, p_bits=60, stream=None):
+        torch = _torch()
+        self.N = 1 << log_n
+        self.L, self.K, self.alpha = n_q, n_p, alpha
+        self.dnum = -(-n_q // alpha)
+        prm = HeParams(log_n, n_q, q_bits, n_p, p_bits, alpha, t)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = _P()
+        rc = lib().he_ctx_create(ctypes.byref(prm), ctypes.c_void_p(self.stream.cuda_stream),
+                                 ctypes.byref(h))
+        if rc != HE_OK:
+            raise HeError(rc, "he_ctx_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().he_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ck(self, rc, what):
+        if rc != HE_OK:
+            raise HeError(rc, f"{what}: {lib().he_last_error(self.h).decode()}")
+
+    # ---- buffers
+    def new_ct(self, level=None, count=None):
+        torch = _torch()
+        lv = self.L if level is None else level
+        shape = (2, lv, self.N) if count is None else (count, 2, lv, self.N)
+        return torch.zeros(shape, dtype=torch.int64, device="cuda")
+
+    @staticmethod
+    def ct_struct(t, domain=HE_NTT):
+        return HeCt(t.data_ptr(), 2, t.shape[-2], domain)
+
+    def ct_array(self, ts, domain=HE_NTT):
+        arr = (HeCt * len(ts))()
+        for i, t in enumerate(ts):
+            arr[i] = self.ct_struct(t, domain)
+        return arr
+
+    @staticmethod
+    def to_numpy(t):
+        return t.detach().cpu().numpy().view(np.uint64)
+
+    def from_numpy(self, a):
+        torch = _torch()
+        return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint64).view(np.int64)).cuda()
+
+    # ---- context
+    def he_get_moduli(self):
+        out = np.zeros(64, dtype=np.uint64)
+        n = lib().he_get_moduli(self.h, out.ctypes.data_as(_U64P), 64)
+        return [int(x) for x in out[:n]]
+
+    def he_op_counts(self):
+        out = np.zeros(4, dtype=np.uint64)
+        lib().he_op_counts(self.h, out.ctypes.data_as(_U64P))
+        return {"mulpc": int(out[0]), "addcc": int(out[1]), "rot": int(out[2]), "ks": int(out[3])}
+
+    def he_launch_count(self):
+        return int(lib().he_launch_count(self.h))
+
+    def he_reset_op_counts(self):
+        lib().he_reset_op_counts(self.h)
+
+    # ---- client side
+    def he_keygen_secret(self, seed):
+        out = np.zeros(self.N, dtype=np.int64)
+        self._ck(lib().he_keygen_secret(self.h, seed, out.ctypes.data_as(_I64P)), "he_keygen_secret")
+        return out
+
+    def he_keygen_galois(self, sk, seed, steps):
+        sk, psk = _i64(sk)
+        st, pst = _i32(steps)
+        self._ck(lib().he_keygen_galois(self.h, psk, seed, pst, len(st)), "he_keygen_galois")
+
+    def key_words(self):
+        return self.dnum * 2 * (self.L + self.K) * self.N
+
+    def he_export_galois(self, step):
+        out = np.zeros(self.key_words(), dtype=np.uint64)
+        self._ck(lib().he_export_galois(self.h, step, out.ctypes.data_as(_U64P)), "he_export_galois")
+        return out.reshape(self.dnum, 2, self.L + self.K, self.N)
+
+    def he_load_keys(self, blob, steps):
+        b, pb = _u64(blob)
+        st, pst = _i32(steps)
+        self._ck(lib().he_load_keys(self.h, pb, pst, len(st)), "he_load_keys")
+
+    def he_encrypt(self, sk, slots, seed, domain=HE_NTT, out=None):
+        out = self.new_ct() if out is None else out
+        sk, psk = _i64(sk)
+        sl, psl = _i64(slots)
+        c = self.ct_struct(out, domain)
+        self._ck(lib().he_encrypt(self.h, psk, psl, seed, ctypes.byref(c)), "he_encrypt")
+        return out
+
+    def he_decrypt(self, sk, ct, domain=HE_NTT):
+        sk, psk = _i64(sk)
+        out = np.zeros(self.N, dtype=np.int64)
+        c = self.ct_struct(ct, domain)
+        self._ck(lib().he_decrypt(self.h, psk, ctypes.byref(c), out.ctypes.data_as(_I64P)), "he_decrypt")
+        return out
+
+    # ---- evaluation
+    def he_to_ntt(self, ct):
+        c = self.ct_struct(ct, HE_COEFF)
+        self._ck(lib().he_to_ntt(self.h, ctypes.byref(c)), "he_to_ntt")
+        return ct
+
+    def he_to_coeff(self, ct):
+        c = self.ct_struct(ct, HE_NTT)
+        self._ck(lib().he_to_coeff(self.h, ctypes.byref(c)), "he_to_coeff")
+        return ct
+
+    def he_encode(self, slots):
+        torch = _torch()
+        out = torch.zeros((self.L, self.N), dtype=torch.int64, device="cuda")
+        sl, psl = _i64(slots)
+        self._ck(lib().he_encode(self.h, psl, ctypes.c_void_p(out.data_ptr())), "he_encode")
+        return out
+
+    def he_rotate(self, ct, step, out=None):
+        out = self.new_ct() if out is None else out
+        a, b = self.ct_struct(ct), self.ct_struct(out)
+        self._ck(lib().he_rotate(self.h, ctypes.byref(a), step, ctypes.byref(b)), "he_rotate")
+        return out
+
+    def he_rotate_batch(self, cts, step, outs=None):
+        outs = [self.new_ct() for _ in cts] if outs is None else outs
+        ia, oa = self.ct_array(cts), self.ct_array(outs)
+        self._ck(lib().he_rotate_batch(self.h, ia, len(cts), step, oa), "he_rotate_batch")
+        return outs
+
+    def he_rotate_hoisted(self, ct, steps, outs=None):
+        outs = [self.new_ct() for _ in steps] if outs is None else outs
+        a = self.ct_struct(ct)
+        st, pst = _i32(steps)
+        oa = self.ct_array(outs)
+        self._ck(lib().he_rotate_hoisted(self.h, ctypes.byref(a), pst, len(st), oa), "he_rotate_hoisted")
+        return outs
+
+    def he_mul_plain_acc(self, cts, pts, acc):
+        ia = self.ct_array(cts)
+        c = self.ct_struct(acc)
+        self._ck(lib().he_mul_plain_acc(self.h, ia, ctypes.c_void_p(pts.data_ptr()), len(cts),
+                                        ctypes.byref(c)), "he_mul_plain_acc")
+        return acc
+
+    def he_add(self, a, b, out=None, domain=HE_NTT):
+        out = self.new_ct(level=a.shape[-2]) if out is None else out
+        x, y, z = self.ct_struct(a, domain), self.ct_struct(b, domain), self.ct_struct(out, domain)
+        self._ck(lib().he_add(self.h, ctypes.byref(x), ctypes.byref(y), ctypes.byref(z)), "he_add")
+        return out
+
+    def he_rescale(self, ct, out=None):
+        out = self.new_ct(level=ct.shape[-2] - 1) if out is None else out
+        a, b = self.ct_struct(ct), self.ct_struct(out)
+        self._ck(lib().he_rescale(self.h, ctypes.byref(a), ctypes.byref(b)), "he_rescale")
+        return out
+
+    @staticmethod
+    def layout(I_c, I_h, I_w, d, stride, pad, r, O_c, pack="dp_shift", modswitch=False):
+        return HeLayout(I_c, I_h, I_w, d, stride, pad, r, O_c,
+                        HE_DP_DOT if pack == "dp_dot" else HE_DP_SHIFT, int(bool(modswitch)))
+
+    def he_ffconv_required_steps(self, lay):
+        out = np.zeros(4096, dtype=np.int32)
+        n = lib().he_ffconv_required_steps(self.h, ctypes.byref(lay), out.ctypes.data_as(_I32P), 4096)
+        if n < 0:
+            raise HeError(n, "he_ffconv_required_steps: layout does not fit the ring")
+        return [int(x) for x in out[:n]]
+
+    def he_ffconv_layer_batch(self, cts_in, W1, W2, lay, outs=None):
+        B = len(cts_in)
+        lv = self.L - 1 if lay.modswitch else self.L
+        outs = [self.new_ct(level=lv) for _ in range(B * lay.O_c)] if outs is None else outs
+        ia, oa = self.ct_array(cts_in), self.ct_array(outs)
+        w1, pw1 = _i32(W1)
+        w2, pw2 = _i32(W2)
+        self._ck(lib().he_ffconv_layer_batch(self.h, ia, B, pw1, pw2, ctypes.byref(lay), oa),
+                 "he_ffconv_layer_batch")
+        return outs
+
+    def he_ffconv_layer(self, ct_in, W1, W2, lay, outs=None):
+        lv = self.L - 1 if lay.modswitch else self.L
+        outs = [self.new_ct(level=lv) for _ in range(lay.O_c)] if outs is None else outs
+        a = self.ct_struct(ct_in)
+        oa = self.ct_array(outs)
+        w1, pw1 = _i32(W1)
+        w2, pw2 = _i32(W2)
+        self._ck(lib().he_ffconv_layer(self.h, ctypes.byref(a), pw1, pw2, ctypes.byref(lay), oa),
+                 "he_ffconv_layer")
+        return outs
+
+    def he_ntt(self, data, n_items, n_limbs, inverse=False):
+        self._ck(lib().he_ntt(self.h, ctypes.c_void_p(data.data_ptr()), n_items, n_limbs, int(inverse)),
+                 "he_ntt")
+        return data
+
+
+def he_gaussian_table():
+    out = np.zeros(20, dtype=np.uint64)
+    lib().he_gaussian_table(out.ctypes.data_as(_U64P))
+    return [int(x) for x in out]

@@ -1,0 +1,133 @@
+"""GPU parity of the encrypted FFConv layer (Sec. 4.2) against the CPU oracle.
+
+Bit-exact on every output ciphertext coefficient where the oracle finishes in seconds (small
+rings, and the 1 x 28 x 28 layer at N = 8192 under DP_SHIFT); at the benchmark's N = 2^15
+configuration and for DP_DOT at N = 8192, the decrypted outputs are compared with the plain
+integer convolution mod t (exact), and operation counts with the schedule's formulas."""
+import numpy as np
+import pytest
+
+from oracle import bfv, encoder, ffconv, params
+from paper_2102_03494_gb300 import workloads
+from tests.gpu_common import download_coeff, gpu_steps, make_ctx, oracle_keys, upload_ntt
+
+pytestmark = pytest.mark.gpu
+
+
+def setup_layer(prm, shape, pack, seed=0, modswitch=False, B=1):
+    lay_o = ffconv.Layout(*shape.astuple(), pack=pack, modswitch=modswitch)
+    s = bfv.keygen_secret(prm, seed + 1)
+    steps = ffconv.required_steps(lay_o, prm.n)
+    keys, blob = oracle_keys(prm, s, steps, seed + 2)
+    xs = workloads.images(seed, shape, B)
+    W1, W2 = workloads.weights(seed, shape)
+    cts = [bfv.encrypt(prm, s, encoder.encode(ffconv.input_slots(x, lay_o, prm.n), prm), seed + 3 + b)
+           for b, x in enumerate(xs)]
+    return lay_o, s, steps, keys, blob, xs, W1, W2, cts
+
+
+def check_decrypted(ctx, prm, s, lay_o, outs, x, W1, W2):
+    _, y2 = ffconv.plain_layer(x, W1, W2, lay_o)
+    for c, o in enumerate(outs):
+        v = ctx.he_decrypt(s, o)
+        for oh in range(lay_o.O_h):
+            for ow in range(lay_o.O_w):
+                assert v[ffconv.output_slot(lay_o, oh, ow)] == y2[c, oh, ow] % prm.t
+
+
+SMALL = [workloads.LayerShape(1, 8, 8, 3, 2, 1, 2, 3), workloads.LayerShape(2, 6, 6, 3, 1, 1, 2, 2),
+         workloads.LayerShape(3, 5, 7, 3, 2, 1, 3, 4), workloads.LayerShape(1, 9, 9, 5, 2, 2, 1, 2)]
+
+
+@pytest.mark.parametrize("pack", ["dp_shift", "dp_dot"])
+@pytest.mark.parametrize("si", range(len(SMALL)))
+def test_small_layers_are_bit_exact(pack, si):
+    prm = params.Params(log_n=9, n_q=3, n_p=1, alpha=1)
+    shape = SMALL[si]
+    lay_o, s, steps, keys, blob, xs, W1, W2, cts = setup_layer(prm, shape, pack, seed=si)
+    ctx = make_ctx(prm)
+    ctx.he_load_keys(blob, gpu_steps(steps))
+    lay = ctx.layout(*shape.astuple(), pack=pack)
+    assert ctx.he_ffconv_required_steps(lay) == gpu_steps(steps)
+    ops = ffconv.OpCount()
+    want = ffconv.he_layer(prm, cts[0], W1, W2, lay_o, keys, ops)
+    ctx.he_reset_op_counts()
+    outs = ctx.he_ffconv_layer(upload_ntt(ctx, cts[0]), W1, W2, lay)
+    for o, w in zip(outs, want):
+        assert (download_coeff(ctx, o) == w.stack()).all()
+    got_ops = ctx.he_op_counts()
+    assert {k: got_ops[k] for k in ("mulpc", "addcc", "rot")} == ops.as_dict() == \
+        ffconv.expected_ops(lay_o, prm.n)
+    check_decrypted(ctx, prm, s, lay_o, outs, xs[0], W1, W2)
+
+
+@pytest.mark.parametrize("pack", ["dp_shift", "dp_dot"])
+def test_batched_layer_with_modswitch_and_wide_digits(pack):
+    prm = params.Params(log_n=10, n_q=4, n_p=2, alpha=2)
+    shape = workloads.LayerShape(2, 6, 6, 3, 2, 1, 2, 3)
+    B = 3
+    lay_o, s, steps, keys, blob, xs, W1, W2, cts = setup_layer(prm, shape, pack, seed=7,
+                                                                modswitch=True, B=B)
+    ctx = make_ctx(prm)
+    ctx.he_load_keys(blob, gpu_steps(steps))
+    lay = ctx.layout(*shape.astuple(), pack=pack, modswitch=True)
+    outs = ctx.he_ffconv_layer_batch([upload_ntt(ctx, c) for c in cts], W1, W2, lay)
+    for b in range(B):
+        want = ffconv.he_layer(prm, cts[b], W1, W2, lay_o, keys)
+        for c in range(shape.O_c):
+            assert (download_coeff(ctx, outs[b * shape.O_c + c]) == want[c].stack()).all()
+        single = ctx.he_ffconv_layer(upload_ntt(ctx, cts[b]), W1, W2, lay)
+        for c in range(shape.O_c):
+            assert (ctx.to_numpy(single[c]) == ctx.to_numpy(outs[b * shape.O_c + c])).all()
+
+
+def test_mnist_layer_dp_shift_n8192_is_bit_exact():
+    """The 1 x 28 x 28, 5 x 5 stride-2, r = 2 -> 5 channel layer at N = 8192 (3 x 50-bit q)."""
+    prm = params.cfg_small_layer()
+    shape = workloads.MNIST_LAYER
+    lay_o, s, steps, keys, blob, xs, W1, W2, cts = setup_layer(prm, shape, "dp_shift")
+    ctx = make_ctx(prm)
+    ctx.he_load_keys(blob, gpu_steps(steps))
+    lay = ctx.layout(*shape.astuple(), pack="dp_shift")
+    want = ffconv.he_layer(prm, cts[0], W1, W2, lay_o, keys)
+    outs = ctx.he_ffconv_layer(upload_ntt(ctx, cts[0]), W1, W2, lay)
+    for o, w in zip(outs, want):
+        assert (download_coeff(ctx, o) == w.stack()).all()
+    check_decrypted(ctx, prm, s, lay_o, outs, xs[0], W1, W2)
+
+
+def test_mnist_layer_dp_dot_n8192_decrypts_to_the_convolution():
+    prm = params.cfg_small_layer()
+    shape = workloads.MNIST_LAYER
+    ctx = make_ctx(prm)
+    lay_o = ffconv.Layout(*shape.astuple(), pack="dp_dot")
+    lay = ctx.layout(*shape.astuple(), pack="dp_dot")
+    sk = ctx.he_keygen_secret(1)
+    ctx.he_keygen_galois(sk, 2, ctx.he_ffconv_required_steps(lay))
+    x = workloads.image(0, shape)
+    W1, W2 = workloads.weights(0, shape)
+    ct = ctx.he_encrypt(sk, ffconv.input_slots(x, lay_o, prm.n), 3)
+    ctx.he_reset_op_counts()
+    outs = ctx.he_ffconv_layer(ct, W1, W2, lay)
+    check_decrypted(ctx, prm, sk, lay_o, outs, x, W1, W2)
+    got = ctx.he_op_counts()
+    assert {k: got[k] for k in ("mulpc", "addcc", "rot")} == ffconv.expected_ops(lay_o, prm.n)
+    assert got["rot"] == 2 * 169 * 10
+
+
+@pytest.mark.parametrize("B", [1, 4])
+def test_bench_layer_n15_decrypts_to_the_convolution(B):
+    """The benchmark configuration: N = 2^15, 12 x 50-bit q, 3 x 60-bit p, digits of 3."""
+    prm = params.cfg_n15()
+    shape = workloads.MNIST_LAYER
+    ctx = make_ctx(prm)
+    lay_o = ffconv.Layout(*shape.astuple(), pack="dp_shift")
+    lay = ctx.layout(*shape.astuple(), pack="dp_shift")
+    sk = ctx.he_keygen_secret(1)
+    ctx.he_keygen_galois(sk, 2, ctx.he_ffconv_required_steps(lay))
+    xs = workloads.images(0, shape, B)
+    W1, W2 = workloads.weights(0, shape)
+    cts = [ctx.he_encrypt(sk, ffconv.input_slots(x, lay_o, prm.n), 3 + b) for b, x in enumerate(xs)]
+    outs = ctx.he_ffconv_layer_batch(cts, W1, W2, lay)
+    for b in range(B):
+        check_decrypted(ctx, prm, sk, lay_o, outs[b * 5:(b + 1) * 5], xs[b], W1, W2)

@@ -1,0 +1,193 @@
+"""GPU parity of the RNS-BFV primitives against the CPU oracle, bit for bit.
+
+Covers the NTT (against the oracle's evaluation at the odd powers of the same root), key and
+encryption randomness, Galois keys, decryption, plain / batched / hoisted rotations, MulPC,
+AddCC and modulus switching, at several ring sizes including N = 2^15 with 12 primes."""
+import numpy as np
+import pytest
+
+from oracle import bfv, encoder, params, prng, ring
+from tests.gpu_common import (download_coeff, encrypt_slots, gpu_steps, make_ctx, oracle_keys,
+                              upload_ntt)
+
+pytestmark = pytest.mark.gpu
+
+CONFIGS = {"n512": (9, 3, 1, 1), "n1024_a2": (10, 4, 2, 2), "n1024_partial": (10, 5, 2, 2),
+           "n8192": (13, 3, 1, 1)}
+
+
+def brv(x, bits):
+    return int(format(x, f"0{bits}b")[::-1], 2)
+
+
+@pytest.mark.parametrize("cfg", [(6, 2, 1, 1), (9, 3, 1, 1), (13, 3, 1, 1), (14, 6, 2, 2),
+                                 (15, 12, 3, 3), (16, 24, 6, 6)])
+def test_ntt_matches_oracle_evaluation(cfg):
+    import torch
+    prm = params.Params(log_n=cfg[0], n_q=cfg[1], n_p=cfg[2], alpha=cfg[3])
+    ctx = make_ctx(prm)
+    items = 2
+    a = np.stack([np.stack([np.random.default_rng(100 * i + l).integers(0, q, prm.n, dtype=np.uint64)
+                            for l, q in enumerate(prm.qp)]) for i in range(items)])
+    d = ctx.from_numpy(a)
+    ctx.he_ntt(d, items, len(prm.qp), inverse=False)
+    got = ctx.to_numpy(d)
+    perm = np.array([brv(p, prm.log_n) for p in range(prm.n)])
+    for i in range(items):
+        for l in [0, len(prm.qp) - 1] + ([prm.n_q] if prm.n_q < len(prm.qp) else []):
+            q = prm.qp[l]
+            ev = ring.neg_eval(a[i, l], q, prm.psi[q])
+            assert (got[i, l] == ev[perm]).all(), (i, l)
+    ctx.he_ntt(d, items, len(prm.qp), inverse=True)
+    assert (ctx.to_numpy(d) == a).all()
+    torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("name", ["n512", "n1024_partial", "n8192"])
+def test_secret_encryption_and_keys_are_bit_exact(name):
+    prm = params.Params(*CONFIGS[name][:1], n_q=CONFIGS[name][1], n_p=CONFIGS[name][2],
+                        alpha=CONFIGS[name][3])
+    ctx = make_ctx(prm)
+    sk = ctx.he_keygen_secret(77)
+    s = bfv.keygen_secret(prm, 77)
+    assert (sk == s).all()
+    v = np.random.default_rng(5).integers(0, prm.t, prm.n)
+    want = encrypt_slots(prm, s, v, 123)
+    from paper_2102_03494_gb300 import he
+    got = ctx.he_encrypt(sk, v, 123, domain=he.HE_COEFF)
+    assert (ctx.to_numpy(got) == want.stack()).all()
+    got_ntt = ctx.he_encrypt(sk, v, 123, domain=he.HE_NTT)
+    assert (download_coeff(ctx, got_ntt) == want.stack()).all()
+    steps = [1, -3, bfv.ROW_SWAP]
+    ctx.he_keygen_galois(sk, 9, gpu_steps(steps))
+    for st in steps:
+        g = bfv.galois_of(st, prm.n)
+        assert (ctx.he_export_galois(gpu_steps([st])[0]) == bfv.galois_key(prm, s, g, 9)).all()
+
+
+def test_keys_at_n15_are_bit_exact():
+    prm = params.cfg_n15()
+    ctx = make_ctx(prm)
+    s = bfv.keygen_secret(prm, 3)
+    ctx.he_keygen_galois(s, 4, [7])
+    want = bfv.galois_key(prm, s, bfv.galois_of(7, prm.n), 4)
+    assert (ctx.he_export_galois(7) == want).all()
+
+
+@pytest.mark.parametrize("name", list(CONFIGS))
+def test_decrypt_matches_oracle(name):
+    prm = params.Params(log_n=CONFIGS[name][0], n_q=CONFIGS[name][1], n_p=CONFIGS[name][2],
+                        alpha=CONFIGS[name][3])
+    ctx = make_ctx(prm)
+    s = bfv.keygen_secret(prm, 1)
+    v = np.random.default_rng(2).integers(0, prm.t, prm.n)
+    ct = encrypt_slots(prm, s, v, 3)
+    d = upload_ntt(ctx, ct)
+    assert (ctx.he_decrypt(s, d) == v).all()
+    from paper_2102_03494_gb300 import he
+    assert (ctx.he_decrypt(s, ctx.from_numpy(ct.stack()), domain=he.HE_COEFF) == v).all()
+    low = bfv.rescale(prm, ct)
+    dl = ctx.from_numpy(low.stack())
+    assert (ctx.he_decrypt(s, dl, domain=he.HE_COEFF) == v).all()
+
+
+@pytest.mark.parametrize("name", list(CONFIGS))
+def test_rotations_are_bit_exact(name):
+    prm = params.Params(log_n=CONFIGS[name][0], n_q=CONFIGS[name][1], n_p=CONFIGS[name][2],
+                        alpha=CONFIGS[name][3])
+    ctx = make_ctx(prm)
+    s = bfv.keygen_secret(prm, 11)
+    steps = [1, 5, -3, bfv.ROW_SWAP]
+    keys, blob = oracle_keys(prm, s, steps)
+    ctx.he_load_keys(blob, gpu_steps(steps))
+    cts = [encrypt_slots(prm, s, np.random.default_rng(i).integers(0, prm.t, prm.n), 40 + i)
+           for i in range(3)]
+    ds = [upload_ntt(ctx, c) for c in cts]
+    # plain rotation, single and batched
+    for st in steps:
+        want = bfv.rotate(prm, cts[0], st, keys)
+        got = ctx.he_rotate(ds[0], gpu_steps([st])[0])
+        assert (download_coeff(ctx, got) == want.stack()).all(), st
+    outs = ctx.he_rotate_batch(ds, 5)
+    for c, o in zip(cts, outs):
+        assert (download_coeff(ctx, o) == bfv.rotate(prm, c, 5, keys).stack()).all()
+    # hoisted
+    hs = ctx.he_rotate_hoisted(ds[1], gpu_steps(steps))
+    for o, w in zip(hs, bfv.rotate_hoisted(prm, cts[1], steps, keys)):
+        assert (download_coeff(ctx, o) == w.stack()).all()
+    # decrypted slots shift as the paper's rotation does
+    half = prm.n // 2
+    v = encoder.decode(bfv.decrypt(prm, s, cts[1]), prm)
+    got = ctx.he_decrypt(s, hs[0])
+    assert (got[:half] == np.roll(v[:half], -1)).all() and (got[half:] == np.roll(v[half:], -1)).all()
+    # in-place rotation (input and output alias)
+    x = ds[2].clone()
+    ctx.he_rotate(x, 1, out=x)
+    assert (download_coeff(ctx, x) == bfv.rotate(prm, cts[2], 1, keys).stack()).all()
+
+
+def test_rotations_at_n15_are_bit_exact():
+    prm = params.cfg_n15()
+    ctx = make_ctx(prm)
+    s = bfv.keygen_secret(prm, 5)
+    steps = [3, -29]
+    keys, blob = oracle_keys(prm, s, steps)
+    ctx.he_load_keys(blob, steps)
+    ct = encrypt_slots(prm, s, np.random.default_rng(9).integers(0, prm.t, prm.n), 6)
+    d = upload_ntt(ctx, ct)
+    got = ctx.he_rotate(d, 3)
+    assert (download_coeff(ctx, got) == bfv.rotate(prm, ct, 3, keys).stack()).all()
+    hs = ctx.he_rotate_hoisted(d, steps)
+    for o, w in zip(hs, bfv.rotate_hoisted(prm, ct, steps, keys)):
+        assert (download_coeff(ctx, o) == w.stack()).all()
+
+
+@pytest.mark.parametrize("name", ["n512", "n8192"])
+def test_encode_mulpc_addcc_rescale_are_bit_exact(name):
+    import torch
+    prm = params.Params(log_n=CONFIGS[name][0], n_q=CONFIGS[name][1], n_p=CONFIGS[name][2],
+                        alpha=CONFIGS[name][3])
+    ctx = make_ctx(prm)
+    s = bfv.keygen_secret(prm, 2)
+    rng = np.random.default_rng(8)
+    vs = [rng.integers(0, prm.t, prm.n) for _ in range(3)]
+    ws = [rng.integers(-prm.t // 2, prm.t // 2, prm.n) for _ in range(3)]
+    cts = [encrypt_slots(prm, s, v, 70 + i) for i, v in enumerate(vs)]
+    pts_o = [bfv.pt_rns(encoder.encode(w, prm), prm) for w in ws]
+    pts = torch.stack([ctx.he_encode(w) for w in ws])
+    for p, po in zip(pts, pts_o):     # encoder: centred lift, NTT domain
+        c = p.clone()
+        ctx.he_ntt(c, 1, prm.n_q, inverse=True)
+        assert (ctx.to_numpy(c) == po).all()
+    ds = [upload_ntt(ctx, c) for c in cts]
+    acc = upload_ntt(ctx, cts[0])
+    ctx.he_mul_plain_acc(ds, pts, acc)
+    want = cts[0]
+    for c, po in zip(cts, pts_o):
+        want = bfv.add(prm, want, bfv.mul_plain(prm, c, po))
+    assert (download_coeff(ctx, acc) == want.stack()).all()
+    got = ctx.he_add(ds[0], ds[1])
+    assert (download_coeff(ctx, got) == bfv.add(prm, cts[0], cts[1]).stack()).all()
+    r = ctx.he_rescale(ds[2])
+    assert (download_coeff(ctx, r) == bfv.rescale(prm, cts[2]).stack()).all()
+    assert (ctx.he_decrypt(s, r) == vs[2]).all()
+
+
+def test_error_paths():
+    from paper_2102_03494_gb300 import he
+    prm = params.Params(log_n=9, n_q=3, n_p=1, alpha=1)
+    ctx = make_ctx(prm)
+    s = bfv.keygen_secret(prm, 1)
+    d = upload_ntt(ctx, encrypt_slots(prm, s, np.zeros(prm.n, np.int64), 1))
+    with pytest.raises(he.HeError) as e:
+        ctx.he_rotate(d, 3)
+    assert e.value.code == he.HE_ENOKEY
+    with pytest.raises(he.HeError) as e:
+        ctx.he_rescale(d, out=ctx.new_ct(level=3))     # wrong output level
+    assert e.value.code == he.HE_EINVAL
+    bad = ctx.layout(1, 40, 40, 5, 2, 1, 2, 5)          # 1600 slots > N/2 = 256
+    with pytest.raises(he.HeError):
+        ctx.he_ffconv_required_steps(bad)
+    with pytest.raises(he.HeError) as e:
+        ctx.he_ffconv_layer(d, np.ones((2, 1, 5, 5)), np.ones((5, 2)), bad)
+    assert e.value.code == he.HE_EINVAL

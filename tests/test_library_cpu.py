@@ -1,0 +1,44 @@
+"""CPU checks of the C-ABI library: it builds, loads, exports every entry point declared in
+include/he.h, and its host-side sampler table equals the oracle's (no GPU calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from oracle import prng
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libhe():
+    from paper_2102_03494_gb300 import build_ext, he
+    build_ext.build()
+    return he
+
+
+def declared_entry_points():
+    text = open(os.path.join(ROOT, "include", "he.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:int|void|uint64_t|const char\*)\s+(he_[a-z0-9_]+)\(", text, re.M)))
+
+
+def test_library_exports_every_declared_symbol(libhe):
+    lib = ctypes.CDLL(libhe.LIB_PATH)
+    names = declared_entry_points()
+    assert len(names) >= 25
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(libhe.exported_symbols())
+
+
+def test_sampler_table_matches_oracle(libhe):
+    assert libhe.he_gaussian_table() == prng.cdt_table()
+
+
+def test_binding_refuses_to_run_without_gpu(libhe):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(RuntimeError):
+        libhe.Context(log_n=10, n_q=2, n_p=1, alpha=1)
