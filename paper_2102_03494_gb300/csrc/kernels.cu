@@ -274,7 +274,8 @@ __global__ void k_from_mont(uint64_t* data, int rows, int period, int mod_off, i
 
 // ------------------------------------------------------------------ rescale (mod switch)
 
-// s[item][k][i][n] = ([last_k[n] + h]_{q_last}) mod q_i, coefficient form, i < L-1.
+// s[item][k][i][n] = ([last_k[n] + h]_{q_last} - h) mod q_i, coefficient form, i < L-1,
+// h = (q_last - 1) / 2 added to every coefficient (rounding, not truncation).
 // last: [item][2][N] coefficient form of the last limb of each polynomial.
 __global__ void k_rescale_spread(const uint64_t* __restrict__ last, uint64_t* __restrict__ s,
                                  int L, int logN, const ModConst* __restrict__ mods) {
@@ -286,7 +287,10 @@ __global__ void k_rescale_spread(const uint64_t* __restrict__ last, uint64_t* __
     const uint64_t h = (ql - 1) >> 1;
     const uint64_t r = add_mod(last[((size_t)blockIdx.x * 2 + k) * N + n], h, ql);
     uint64_t* sb = s + ((size_t)blockIdx.x * 2 + k) * (L - 1) * N + n;
-    for (int i = 0; i < L - 1; ++i) sb[(size_t)i * N] = r % mods[i].q;
+    for (int i = 0; i < L - 1; ++i) {
+        const uint64_t qi = mods[i].q;
+        sb[(size_t)i * N] = sub_mod(r % qi, h % qi, qi);   // r - h: c~_i - r = c_i - (r - h)
+    }
 }
 
 // last[item][k][n] = x[item][k][L-1][n] (the limb a modulus switch drops).
@@ -299,7 +303,7 @@ __global__ void k_gather_last(const uint64_t* const* xp, uint64_t* __restrict__ 
     last[((size_t)blockIdx.x * 2 + k) * N + n] = xp[blockIdx.x][((size_t)k * L + L - 1) * N + n];
 }
 
-// out_k[i] = (x_k[i] + h - s_k[i]) q_last^-1 mod q_i   (NTT domain; h is a constant polynomial)
+// out_k[i] = (x_k[i] - s_k[i]) q_last^-1 mod q_i   (NTT domain)
 __global__ void k_rescale_combine(const uint64_t* const* xp, const uint64_t* __restrict__ s,
                                   uint64_t* const* outp, int L, int logN,
                                   const ModConst* __restrict__ mods,
@@ -309,11 +313,10 @@ __global__ void k_rescale_combine(const uint64_t* const* xp, const uint64_t* __r
     if (n >= N) return;
     const int i = blockIdx.z % (L - 1), k = blockIdx.z / (L - 1);
     const uint64_t q = mods[i].q;
-    const uint64_t h = ((mods[L - 1].q - 1) >> 1) % q;
     const ShoupPair w = qinv_row[i];
     uint64_t x = xp[blockIdx.x][((size_t)k * L + i) * N + n];
     uint64_t sv = s[(((size_t)blockIdx.x * 2 + k) * (L - 1) + i) * N + n];
-    uint64_t y = sub_mod(add_mod(x, h, q), sv, q);
+    uint64_t y = sub_mod(x, sv, q);
     outp[blockIdx.x][((size_t)k * (L - 1) + i) * N + n] = mul_shoup(y, w.w, w.ws, q);
 }
 
