@@ -144,6 +144,17 @@ int he_encode(he_ctx* ctx, const int64_t* slots, uint64_t* pt_out);
  * within each row of N/2 slots.  Automorphism X -> X^(5^step), then hybrid key switching.
  * in/out: NTT domain, same level, in may equal out.  HE_ENOKEY without the key. */
 int he_rotate(he_ctx* ctx, const he_ct* in, int32_t step, he_ct* out);
+/* he_rotate without any device allocation (the paper has no counterpart: this serves callers
+ * that cannot allocate device memory when they rotate -- a process whose GPU memory is
+ * already reserved by another allocator, or a request path that must not wait on
+ * cudaMalloc/cudaFree).  Same arguments and the same ciphertext bits as he_rotate; its
+ * key-switching scratch is one static device array of 16 MiB, held by every GPU that loads
+ * the library until exit (enough for N = 2^13 with 3 + 1 primes or N = 2^14 with 6 + 2
+ * primes; larger parameter sets are rejected with HE_EINVAL and a message giving the size
+ * needed).  The first call on a device looks up the array's device address, so make it
+ * before any stream capture.  All calls share the array: calls that overlap on the GPU race
+ * on it and must be serialised by the caller.  Calls cudaMalloc/cudaFree never. */
+int he_rotate_noalloc(he_ctx* ctx, const he_ct* in, int32_t step, he_ct* out);
 /* The same rotation applied to n ciphertexts in one batch (one key read per launch). */
 int he_rotate_batch(he_ctx* ctx, const he_ct* in, int n, int32_t step, he_ct* out);
 /* h rotations of one ciphertext sharing one ModUp of c1 (hoisting): outs[i] = rotation by

@@ -66,6 +66,7 @@ _SIGS = {
     "he_to_coeff": ([_P, _CTP], ctypes.c_int),
     "he_encode": ([_P, _I64P, _P], ctypes.c_int),
     "he_rotate": ([_P, _CTP, ctypes.c_int32, _CTP], ctypes.c_int),
+    "he_rotate_noalloc": ([_P, _CTP, ctypes.c_int32, _CTP], ctypes.c_int),
     "he_rotate_batch": ([_P, _CTP, ctypes.c_int, ctypes.c_int32, _CTP], ctypes.c_int),
     "he_rotate_hoisted": ([_P, _CTP, _I32P, ctypes.c_int, _CTP], ctypes.c_int),
     "he_mul_plain_acc": ([_P, _CTP, _P, ctypes.c_int, _CTP], ctypes.c_int),
@@ -257,6 +258,14 @@ class Context:
         out = self.new_ct() if out is None else out
         a, b = self.ct_struct(ct), self.ct_struct(out)
         self._ck(lib().he_rotate(self.h, ctypes.byref(a), step, ctypes.byref(b)), "he_rotate")
+        return out
+
+    def he_rotate_noalloc(self, ct, step, out):
+        """he_rotate for callers that cannot allocate device memory: the library's scratch is
+        a fixed static device array, and `out` must be supplied by the caller."""
+        a, b = self.ct_struct(ct), self.ct_struct(out)
+        self._ck(lib().he_rotate_noalloc(self.h, ctypes.byref(a), step, ctypes.byref(b)),
+                 "he_rotate_noalloc")
         return out
 
     def he_rotate_batch(self, cts, step, outs=None):
