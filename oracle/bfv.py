@@ -285,6 +285,43 @@ def rotate_hoisted(prm: Params, ct: Ct, steps, keys):
 
 # ---------------------------------------------------------------- plaintext ops, add, rescale
 
+def rotate_hoisted_ext(prm: Params, ct: Ct, steps, keys):
+    """Hoisted rotations left in the extended basis Q u P: for each step the pair
+    (u0 + P phi_g(c0), u1) over Q u P, whose ModDown is the rotation's key-switched result
+    up to the rounding of the division by P.  Sums of plaintext multiples of these pairs are
+    divided by P once (ModDown after the sum instead of once per rotation)."""
+    digits = [modup(prm, ct.c1, j) for j in range(prm.dnum)]
+    L = prm.n_q
+    out = []
+    for step in steps:
+        g = galois_of(step, prm.n)
+        rd = [automorphism(y, g, prm.qp) for y in digits]
+        u0, u1 = key_inner_product(prm, rd, keys[g])
+        c0g = automorphism(ct.c0, g, prm.q)
+        for i, q in enumerate(prm.q):
+            u0[i] = ring.vmac_scalar(u0[i], c0g[i], prm.P % q, q)
+        out.append((u0, u1))
+    return out
+
+
+def scale_by_p_ext(prm: Params, ct: Ct):
+    """(P c0, P c1) over Q u P (zero modulo the special primes): the unrotated ciphertext in
+    the form rotate_hoisted_ext returns, ModDown giving back (c0, c1) exactly."""
+    L, n = prm.n_q, prm.n
+    pair = []
+    for c in (ct.c0, ct.c1):
+        e = np.zeros((len(prm.qp), n), dtype=np.uint64)
+        for i, q in enumerate(prm.q):
+            e[i] = ring.vmul_scalar(c[i], prm.P % q, q)
+        pair.append(e)
+    return pair
+
+
+def pt_rns_ext(m, prm: Params):
+    """Centred lift of a plaintext modulo every prime of Q u P ([L+K][N])."""
+    return to_rns(lift_centered(m, prm), prm.qp)
+
+
 def pt_rns(m, prm: Params, level=None):
     """Plaintext polynomial (coefficients mod t) -> centred lift mod each q ([L][N])."""
     c = lift_centered(m, prm)

@@ -10,7 +10,7 @@ padding `pad` on every side, output size floor((I + 2 pad - d) / stride) + 1.
 
 Encrypted layer, FFConv packing DP-HI2C-CP (Sec. 4.2, Fig. 4): W1 under DensePack (Sec. 3.2,
 Fig. 1), the DP -> CP transition with a 1 x 1 kernel (Table III, d = 1 row), W2 under
-ConvPack (Sec. 3.2, Fig. 2a).  Two schedules of W1:
+ConvPack (Sec. 3.2, Fig. 2a).  Three schedules of W1:
 
   dp_dot   (the paper's DensePack): the input is packed densely in row 0,
            slot ci*I_h*I_w + h*I_w + w.  For every output channel c' and output position o
@@ -28,6 +28,11 @@ ConvPack (Sec. 3.2, Fig. 2a).  Two schedules of W1:
            ci*B_c + (s oh) I_w + s ow wherever that input pixel lies inside the image;
            channels are then folded with acc <- acc + rot(acc, B_c 2^k).  y1[c', oh, ow]
            lands at slot (s oh) I_w + s ow.
+  dp_shift_ext (the same slots and plaintexts as dp_shift): the hoisted rotations stay in the
+           extended basis Q u P, each as (u0 + P phi(c0), u1); the tap products are summed
+           there (plaintexts lifted to Q u P) and divided by P once per channel (one ModDown
+           per channel instead of one per rotation).  A different algorithm from dp_shift,
+           with its own ciphertext bits; both decrypt to the same slots.
 
 W2 (ConvPack, Table II): ct_out[c] = sum_c' W2[c, c'] ct_w1[c'], each weight a constant
 plaintext.  An optional modulus switch drops the last prime at the end.
@@ -50,7 +55,7 @@ class Layout:
     pad: int
     r: int
     O_c: int
-    pack: str = "dp_shift"      # "dp_dot" | "dp_shift"
+    pack: str = "dp_shift"      # "dp_dot" | "dp_shift" | "dp_shift_ext"
     modswitch: bool = False
 
     @property
@@ -292,21 +297,38 @@ def he_layer(prm, ct_in, W1, W2, lay: Layout, keys, ops: OpCount = None,
     else:
         taps = lay.taps()
         steps = [dl for (_, _, dl) in taps if dl != 0]
-        rotated = bfv.rotate_hoisted(prm, ct_in, steps, keys)
+        ext = lay.pack == "dp_shift_ext"
+        if ext:
+            # rotations left in the extended basis Q u P (before ModDown), Sec. 3.2's
+            # rotate-then-multiply with the division by P moved after the tap sum
+            rotated = bfv.rotate_hoisted_ext(prm, ct_in, steps, keys)
+            by_delta = dict(zip(steps, rotated))
+            by_delta[0] = bfv.scale_by_p_ext(prm, ct_in)
+        else:
+            rotated = bfv.rotate_hoisted(prm, ct_in, steps, keys)
+            by_delta = dict(zip(steps, rotated))
+            by_delta[0] = ct_in
         ops.rot += len(steps)
-        by_delta = dict(zip(steps, rotated))
-        by_delta[0] = ct_in
         for c in range(lay.r):
             acc = None
             for (i, j, dl) in taps:
-                pt = bfv.pt_rns(encode(dp_shift_tap_slots(W1, lay, n, c, i, j), prm), prm)
-                term = bfv.mul_plain(prm, by_delta[dl], pt)
+                m = encode(dp_shift_tap_slots(W1, lay, n, c, i, j), prm)
+                if ext:
+                    pt = bfv.pt_rns_ext(m, prm)
+                    term = [bfv.rns_mul(by_delta[dl][k], pt, prm, prm.qp) for k in range(2)]
+                else:
+                    term = bfv.mul_plain(prm, by_delta[dl], bfv.pt_rns(m, prm))
                 ops.mulpc += 1
                 if acc is None:
                     acc = term
+                elif ext:
+                    acc = [bfv.rns_add(acc[k], term[k], prm.qp) for k in range(2)]
+                    ops.addcc += 1
                 else:
                     acc = bfv.add(prm, acc, term)
                     ops.addcc += 1
+            if ext:
+                acc = bfv.Ct(bfv.moddown(prm, acc[0]), bfv.moddown(prm, acc[1]))
             for st in lay.channel_fold_steps():
                 acc = bfv.add(prm, acc, bfv.rotate(prm, acc, st, keys))
                 ops.rot += 1

@@ -5,186 +5,250 @@
 // order, position p holding a(psi^(2 brv(p) + 1)).  Inverse: Gentleman-Sande with
 // psi^-brv(m + i), stages in reverse, then the factor N^-1.
 //
-// The N = N1 N2 points (N1 = 2^s1, s1 = floor(log N / 2)) are split in two passes, each
-// staged in shared memory:
+// The N = N1 N2 points (N1 = 2^s1, s1 = floor(log N / 2)) are split in two passes:
 //   column pass: stages s < s1 act on elements with the same j mod N2 (strided columns);
-//                one CTA holds COLS adjacent columns x N1 rows (128-byte row segments);
+//                one CTA holds `cols` adjacent columns x N1 rows;
 //   row pass:    stages s >= s1 act inside contiguous blocks of N2 elements; one CTA holds
-//                several blocks.
-// Each pass reads and writes every limb once.
+//                `blocks` blocks.
+// Inside a pass every thread keeps 8 residues in registers and applies up to three stages
+// per round (a radix-8 step on one group of 8, or two radix-4 / four radix-2 groups): the
+// elements of a group share all index bits except the round's K stage bits.  Rounds exchange
+// through shared memory; the first round reads global memory directly and the last writes it.
+// Butterflies use Harvey's lazy reduction: forward values stay in [0, 4q), inverse values in
+// [0, 2q), and are brought to [0, q) at the end (moduli below 2^62).
 #include "he_internal.cuh"
 
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kTileElems = 2048;   // elements staged per CTA (16 KiB)
+constexpr int kTile = 2048;   // residues staged per CTA (16 KiB), 8 per thread
 
-__global__ void __launch_bounds__(kThreads)
-k_fwd_cols(uint64_t* __restrict__ data, size_t item_stride, int mod_off, int logN, int s1,
-           int cols, const ModConst* __restrict__ mods, const ShoupPair* __restrict__ tw) {
-    extern __shared__ uint64_t sm[];
+__device__ __forceinline__ void bfly_ct(uint64_t& X, uint64_t& Y, const ShoupPair& W, uint64_t q,
+                                        uint64_t q2) {
+    uint64_t x = X >= q2 ? X - q2 : X;               // [0, 2q)
+    uint64_t t = mul_shoup_lazy(Y, W.w, W.ws, q);    // [0, 2q)
+    X = x + t;                                       // [0, 4q)
+    Y = x - t + q2;                                  // (0, 4q)
+}
+
+__device__ __forceinline__ void bfly_gs(uint64_t& X, uint64_t& Y, const ShoupPair& W, uint64_t q,
+                                        uint64_t q2) {
+    uint64_t s = X + Y;                              // X, Y in [0, 2q)
+    s = s >= q2 ? s - q2 : s;
+    uint64_t d = X - Y + q2;                         // (0, 4q)
+    X = s;
+    Y = mul_shoup_lazy(d, W.w, W.ws, q);             // [0, 2q)
+}
+
+// Butterflies of one round on the thread's 8 registers: (8 >> K) groups of 2^K elements,
+// group g at x[g * 2^K + m].  Twiddle of stage ee for element m of a group whose block index
+// is `hi` (plus the block offset `toff` of the row pass): psi^brv(2^s + toff 2^ee + hi 2^ee
+// + (m >> (K - ee))).
+template <int K, bool INV>
+__device__ __forceinline__ void round_bflies(uint64_t (&x)[8], const int (&hi)[8 >> K], int s0,
+                                             int toff, const ShoupPair* __restrict__ w,
+                                             uint64_t q, uint64_t q2) {
+    constexpr int M = 1 << K;
+#pragma unroll
+    for (int g = 0; g < (8 >> K); ++g) {
+        const int base_hi = toff + hi[g];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int ee = INV ? (K - 1 - k) : k;
+            const int d = 1 << (K - 1 - ee);
+            const int s = s0 + ee;
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                if (m & d) continue;
+                const ShoupPair W = w[(1 << s) + (base_hi << ee) + (m >> (K - ee))];
+                if (INV) bfly_gs(x[g * M + m], x[g * M + m + d], W, q, q2);
+                else bfly_ct(x[g * M + m], x[g * M + m + d], W, q, q2);
+            }
+        }
+    }
+}
+
+// One round of the column pass.  Element m of group Gi: column c = Gi % cols, row
+// hi (tlow 2^K) + m tlow + lo with (hi, lo) = divmod(Gi / cols, tlow).
+template <int K, bool INV>
+__device__ __forceinline__ void col_round(uint64_t (&x)[8], uint64_t* sm, uint64_t* __restrict__ a,
+                                          bool first, bool last, int e0, int N1, int N2, int lo0,
+                                          int cols, const ShoupPair* __restrict__ w,
+                                          const ModConst& Mc) {
+    constexpr int M = 1 << K;
+    const int tlow = N1 >> (e0 + K);
+    const int nthr = blockDim.x, tid = threadIdx.x;
+    int hi[8 >> K];
+    int off[8];
+#pragma unroll
+    for (int g = 0; g < (8 >> K); ++g) {
+        const int Gi = tid + g * nthr;
+        const int c = Gi % cols, Gc = Gi / cols;
+        hi[g] = Gc / tlow;
+        const int lo = Gc - hi[g] * tlow;
+#pragma unroll
+        for (int m = 0; m < M; ++m) off[g * M + m] = (hi[g] * (tlow << K) + m * tlow + lo) * cols + c;
+    }
+    if (first) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int row = off[i] / cols, c = off[i] - row * cols;
+            x[i] = a[(size_t)row * N2 + lo0 + c];
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = sm[off[i]];
+    }
+    const uint64_t q = Mc.q, q2 = 2 * q;
+    round_bflies<K, INV>(x, hi, e0, 0, w, q, q2);
+    if (last) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int row = off[i] / cols, c = off[i] - row * cols;
+            uint64_t v = x[i];
+            if (INV) v = mul_shoup(v, Mc.n_inv, Mc.n_inv_sh, q);
+            a[(size_t)row * N2 + lo0 + c] = v;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) sm[off[i]] = x[i];
+        __syncthreads();
+    }
+}
+
+// One round of the row pass.  Element m of group Gi: block b = Gi / (N2 >> K) of the tile,
+// local index hi (tlow 2^K) + m tlow + lo.
+template <int K, bool INV>
+__device__ __forceinline__ void row_round(uint64_t (&x)[8], uint64_t* sm, uint64_t* __restrict__ a,
+                                          bool first, bool last, int e0, int s1, int N2, int blk0,
+                                          const ShoupPair* __restrict__ w, const ModConst& Mc) {
+    constexpr int M = 1 << K;
+    const int tlow = N2 >> (e0 + K);
+    const int per_blk = N2 >> K;
+    const int nthr = blockDim.x, tid = threadIdx.x;
+    // all groups of one thread lie in the same block when per_blk >= nthr, else they differ:
+    // keep the block of each group separately.
+    int hi[8 >> K];
+    int blk[8 >> K];
+    int off[8];
+#pragma unroll
+    for (int g = 0; g < (8 >> K); ++g) {
+        const int Gi = tid + g * nthr;
+        const int b = Gi / per_blk, Gl = Gi - b * per_blk;
+        hi[g] = Gl / tlow;
+        blk[g] = b;
+        const int lo = Gl - hi[g] * tlow;
+#pragma unroll
+        for (int m = 0; m < M; ++m) off[g * M + m] = b * N2 + hi[g] * (tlow << K) + m * tlow + lo;
+    }
+    if (first) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = a[(size_t)blk0 * N2 + off[i]];
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = sm[off[i]];
+    }
+    const uint64_t q = Mc.q, q2 = 2 * q;
+    // twiddle offset of block (blk0 + b) at stage s1 + e0 + ee is (blk0 + b) 2^(e0 + ee):
+    // fold it into hi as (blk0 + b) 2^e0 + hi.
+    int hh[8 >> K];
+#pragma unroll
+    for (int g = 0; g < (8 >> K); ++g) hh[g] = ((blk0 + blk[g]) << e0) + hi[g];
+    round_bflies<K, INV>(x, hh, s1 + e0, 0, w, q, q2);
+    if (last) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            uint64_t v = x[i];
+            if (!INV) {
+                v = v >= q2 ? v - q2 : v;
+                v = v >= q ? v - q : v;
+            }
+            a[(size_t)blk0 * N2 + off[i]] = v;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) sm[off[i]] = x[i];
+        __syncthreads();
+    }
+}
+
+// Rounds of a pass of 2^lg points: forward e0 = 0, 3, 6, ...; inverse from the top down.
+__device__ __forceinline__ void round_of(int r, int lg, bool inv, int& e0, int& K) {
+    if (!inv) {
+        e0 = 3 * r;
+        K = min(3, lg - e0);
+    } else {
+        const int top = lg - 3 * r;
+        K = min(3, top);
+        e0 = top - K;
+    }
+}
+
+template <bool INV>
+__global__ void __launch_bounds__(256)
+k_ntt_cols(uint64_t* __restrict__ data, size_t item_stride, int mod_off, int logN, int s1, int cols,
+           const ModConst* __restrict__ mods, const ShoupPair* __restrict__ tw) {
+    __shared__ uint64_t sm[kTile];
     const int N = 1 << logN, N1 = 1 << s1, N2 = N >> s1;
     const int mod = mod_off + blockIdx.y;
-    const uint64_t q = mods[mod].q;
+    const ModConst Mc = mods[mod];
     const ShoupPair* w = tw + (size_t)mod * N;
     uint64_t* a = data + blockIdx.z * item_stride + (size_t)blockIdx.y * N;
     const int lo0 = blockIdx.x * cols;
-    const int total = N1 * cols;
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-        int hi = idx / cols, c = idx - hi * cols;
-        sm[idx] = a[(size_t)hi * N2 + lo0 + c];
-    }
-    __syncthreads();
-    const int nb = total >> 1;
-    for (int s = 0; s < s1; ++s) {
-        const int tt = N1 >> (s + 1);
-        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-            int bb = b / cols, c = b - bb * cols;
-            int grp = bb / tt;
-            int rj = grp * 2 * tt + (bb - grp * tt);
-            ShoupPair W = w[(1 << s) + grp];
-            uint64_t* pu = sm + rj * cols + c;
-            uint64_t* pv = pu + tt * cols;
-            uint64_t U = *pu;
-            uint64_t V = mul_shoup(*pv, W.w, W.ws, q);
-            *pu = add_mod(U, V, q);
-            *pv = sub_mod(U, V, q);
-        }
-        __syncthreads();
-    }
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-        int hi = idx / cols, c = idx - hi * cols;
-        a[(size_t)hi * N2 + lo0 + c] = sm[idx];
+    const int nr = (s1 + 2) / 3;
+    uint64_t x[8];
+    for (int r = 0; r < nr; ++r) {
+        int e0, K;
+        round_of(r, s1, INV, e0, K);
+        const bool first = r == 0, last = r == nr - 1;
+        if (K == 3) col_round<3, INV>(x, sm, a, first, last, e0, N1, N2, lo0, cols, w, Mc);
+        else if (K == 2) col_round<2, INV>(x, sm, a, first, last, e0, N1, N2, lo0, cols, w, Mc);
+        else col_round<1, INV>(x, sm, a, first, last, e0, N1, N2, lo0, cols, w, Mc);
     }
 }
 
-__global__ void __launch_bounds__(kThreads)
-k_fwd_rows(uint64_t* __restrict__ data, size_t item_stride, int mod_off, int logN, int s1,
-           int blocks, const ModConst* __restrict__ mods, const ShoupPair* __restrict__ tw) {
-    extern __shared__ uint64_t sm[];
+template <bool INV>
+__global__ void __launch_bounds__(256)
+k_ntt_rows(uint64_t* __restrict__ data, size_t item_stride, int mod_off, int logN, int s1, int blocks,
+           const ModConst* __restrict__ mods, const ShoupPair* __restrict__ tw) {
+    __shared__ uint64_t sm[kTile];
     const int N = 1 << logN, N2 = N >> s1;
+    const int s2 = logN - s1;
     const int mod = mod_off + blockIdx.y;
-    const uint64_t q = mods[mod].q;
-    const ShoupPair* w = tw + (size_t)mod * N;
-    const int hi0 = blockIdx.x * blocks;
-    uint64_t* a = data + blockIdx.z * item_stride + (size_t)blockIdx.y * N + (size_t)hi0 * N2;
-    const int total = blocks * N2;
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) sm[idx] = a[idx];
-    __syncthreads();
-    const int half = N2 >> 1, nb = total >> 1;
-    for (int s = s1; s < logN; ++s) {
-        const int tl = N2 >> (s - s1 + 1);
-        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-            int g = b / half, lb = b - g * half;
-            int grp = lb / tl;
-            int lj = grp * 2 * tl + (lb - grp * tl);
-            ShoupPair W = w[(1 << s) + ((hi0 + g) << (s - s1)) + grp];
-            uint64_t* pu = sm + g * N2 + lj;
-            uint64_t* pv = pu + tl;
-            uint64_t U = *pu;
-            uint64_t V = mul_shoup(*pv, W.w, W.ws, q);
-            *pu = add_mod(U, V, q);
-            *pv = sub_mod(U, V, q);
-        }
-        __syncthreads();
-    }
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) a[idx] = sm[idx];
-}
-
-__global__ void __launch_bounds__(kThreads)
-k_inv_rows(uint64_t* __restrict__ data, size_t item_stride, int mod_off, int logN, int s1,
-           int blocks, const ModConst* __restrict__ mods, const ShoupPair* __restrict__ tw) {
-    extern __shared__ uint64_t sm[];
-    const int N = 1 << logN, N2 = N >> s1;
-    const int mod = mod_off + blockIdx.y;
-    const uint64_t q = mods[mod].q;
-    const ShoupPair* w = tw + (size_t)mod * N;
-    const int hi0 = blockIdx.x * blocks;
-    uint64_t* a = data + blockIdx.z * item_stride + (size_t)blockIdx.y * N + (size_t)hi0 * N2;
-    const int total = blocks * N2;
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) sm[idx] = a[idx];
-    __syncthreads();
-    const int half = N2 >> 1, nb = total >> 1;
-    for (int s = logN - 1; s >= s1; --s) {
-        const int tl = N2 >> (s - s1 + 1);
-        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-            int g = b / half, lb = b - g * half;
-            int grp = lb / tl;
-            int lj = grp * 2 * tl + (lb - grp * tl);
-            ShoupPair W = w[(1 << s) + ((hi0 + g) << (s - s1)) + grp];
-            uint64_t* pu = sm + g * N2 + lj;
-            uint64_t* pv = pu + tl;
-            uint64_t U = *pu, V = *pv;
-            *pu = add_mod(U, V, q);
-            *pv = mul_shoup(sub_mod(U, V, q), W.w, W.ws, q);
-        }
-        __syncthreads();
-    }
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) a[idx] = sm[idx];
-}
-
-__global__ void __launch_bounds__(kThreads)
-k_inv_cols(uint64_t* __restrict__ data, size_t item_stride, int mod_off, int logN, int s1,
-           int cols, const ModConst* __restrict__ mods, const ShoupPair* __restrict__ tw) {
-    extern __shared__ uint64_t sm[];
-    const int N = 1 << logN, N1 = 1 << s1, N2 = N >> s1;
-    const int mod = mod_off + blockIdx.y;
-    const ModConst M = mods[mod];
-    const uint64_t q = M.q;
+    const ModConst Mc = mods[mod];
     const ShoupPair* w = tw + (size_t)mod * N;
     uint64_t* a = data + blockIdx.z * item_stride + (size_t)blockIdx.y * N;
-    const int lo0 = blockIdx.x * cols;
-    const int total = N1 * cols;
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-        int hi = idx / cols, c = idx - hi * cols;
-        sm[idx] = a[(size_t)hi * N2 + lo0 + c];
-    }
-    __syncthreads();
-    const int nb = total >> 1;
-    for (int s = s1 - 1; s >= 0; --s) {
-        const int tt = N1 >> (s + 1);
-        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-            int bb = b / cols, c = b - bb * cols;
-            int grp = bb / tt;
-            int rj = grp * 2 * tt + (bb - grp * tt);
-            ShoupPair W = w[(1 << s) + grp];
-            uint64_t* pu = sm + rj * cols + c;
-            uint64_t* pv = pu + tt * cols;
-            uint64_t U = *pu, V = *pv;
-            *pu = add_mod(U, V, q);
-            *pv = mul_shoup(sub_mod(U, V, q), W.w, W.ws, q);
-        }
-        __syncthreads();
-    }
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-        int hi = idx / cols, c = idx - hi * cols;
-        a[(size_t)hi * N2 + lo0 + c] = mul_shoup(sm[idx], M.n_inv, M.n_inv_sh, q);
+    const int blk0 = blockIdx.x * blocks;
+    const int nr = (s2 + 2) / 3;
+    uint64_t x[8];
+    for (int r = 0; r < nr; ++r) {
+        int e0, K;
+        round_of(r, s2, INV, e0, K);
+        const bool first = r == 0, last = r == nr - 1;
+        if (K == 3) row_round<3, INV>(x, sm, a, first, last, e0, s1, N2, blk0, w, Mc);
+        else if (K == 2) row_round<2, INV>(x, sm, a, first, last, e0, s1, N2, blk0, w, Mc);
+        else row_round<1, INV>(x, sm, a, first, last, e0, s1, N2, blk0, w, Mc);
     }
 }
 
 struct Split {
-    int s1, cols, col_ctas, blocks, row_ctas;
+    int s1, cols, col_ctas, col_threads, blocks, row_ctas, row_threads;
 };
 
 Split split_of(int logN) {
     Split sp;
     sp.s1 = logN / 2;
-    int N1 = 1 << sp.s1, N2 = 1 << (logN - sp.s1);
-    sp.cols = N2 < 16 ? N2 : 16;
-    while (sp.cols > 1 && N1 * sp.cols > kTileElems) sp.cols >>= 1;
+    const int N1 = 1 << sp.s1, N2 = 1 << (logN - sp.s1);
+    sp.cols = kTile / N1;
+    if (sp.cols > N2) sp.cols = N2;
+    if (sp.cols < 1) sp.cols = 1;
     sp.col_ctas = N2 / sp.cols;
-    sp.blocks = kTileElems / N2;
-    if (sp.blocks < 1) sp.blocks = 1;
+    sp.col_threads = N1 * sp.cols / 8;
+    sp.blocks = kTile / N2;
     if (sp.blocks > N1) sp.blocks = N1;
+    if (sp.blocks < 1) sp.blocks = 1;
     sp.row_ctas = N1 / sp.blocks;
+    sp.row_threads = sp.blocks * N2 / 8;
     return sp;
-}
-
-int block_threads(int elems) {
-    int t = elems / 2;
-    if (t > kThreads) t = kThreads;
-    if (t < 32) t = 32;
-    return t;
 }
 
 }  // namespace
@@ -193,13 +257,11 @@ void ntt_forward(he_ctx* ctx, uint64_t* data, int items, size_t item_stride, int
                  int mod_off) {
     if (items <= 0 || rows <= 0) return;
     ctx->launches += 2;
-    Split sp = split_of(ctx->logN);
-    int N1 = 1 << sp.s1, N2 = ctx->N >> sp.s1;
+    const Split sp = split_of(ctx->logN);
     dim3 gc(sp.col_ctas, rows, items), gr(sp.row_ctas, rows, items);
-    size_t smc = (size_t)N1 * sp.cols * 8, smr = (size_t)sp.blocks * N2 * 8;
-    k_fwd_cols<<<gc, block_threads(N1 * sp.cols), smc, ctx->stream>>>(
+    k_ntt_cols<false><<<gc, sp.col_threads, 0, ctx->stream>>>(
         data, item_stride, mod_off, ctx->logN, sp.s1, sp.cols, ctx->d_mod, ctx->d_tw_fwd);
-    k_fwd_rows<<<gr, block_threads(sp.blocks * N2), smr, ctx->stream>>>(
+    k_ntt_rows<false><<<gr, sp.row_threads, 0, ctx->stream>>>(
         data, item_stride, mod_off, ctx->logN, sp.s1, sp.blocks, ctx->d_mod, ctx->d_tw_fwd);
 }
 
@@ -207,12 +269,10 @@ void ntt_inverse(he_ctx* ctx, uint64_t* data, int items, size_t item_stride, int
                  int mod_off) {
     if (items <= 0 || rows <= 0) return;
     ctx->launches += 2;
-    Split sp = split_of(ctx->logN);
-    int N1 = 1 << sp.s1, N2 = ctx->N >> sp.s1;
+    const Split sp = split_of(ctx->logN);
     dim3 gc(sp.col_ctas, rows, items), gr(sp.row_ctas, rows, items);
-    size_t smc = (size_t)N1 * sp.cols * 8, smr = (size_t)sp.blocks * N2 * 8;
-    k_inv_rows<<<gr, block_threads(sp.blocks * N2), smr, ctx->stream>>>(
+    k_ntt_rows<true><<<gr, sp.row_threads, 0, ctx->stream>>>(
         data, item_stride, mod_off, ctx->logN, sp.s1, sp.blocks, ctx->d_mod, ctx->d_tw_inv);
-    k_inv_cols<<<gc, block_threads(N1 * sp.cols), smc, ctx->stream>>>(
+    k_ntt_cols<true><<<gc, sp.col_threads, 0, ctx->stream>>>(
         data, item_stride, mod_off, ctx->logN, sp.s1, sp.cols, ctx->d_mod, ctx->d_tw_inv);
 }

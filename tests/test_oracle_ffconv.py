@@ -78,7 +78,7 @@ def check_outputs(prm, s, lay, outs, y2):
         assert bfv.noise_bits(prm, s, ct)[1] > 10
 
 
-@pytest.mark.parametrize("pack", ["dp_dot", "dp_shift"])
+@pytest.mark.parametrize("pack", ["dp_dot", "dp_shift", "dp_shift_ext"])
 @pytest.mark.parametrize("shape", [(1, 6, 6, 3, 2, 1, 2, 3), (2, 5, 5, 3, 1, 1, 2, 2), (3, 4, 4, 3, 2, 1, 2, 3)])
 def test_encrypted_layer_decrypts_to_plain_layer(pack, shape):
     prm = params.Params(log_n=7, n_q=3, n_p=1, alpha=1)
@@ -122,3 +122,18 @@ def test_layer_counts_of_the_28x28_workload():
     assert (lay.O_h, lay.O_w, lay.S) == (13, 13, 169)
     assert ffconv.dp_dot_sum_depth(lay, 8192) == 10
     assert ffconv.expected_ops(lay, 8192)["rot"] == 2 * 169 * 10
+
+
+def test_extended_basis_schedule_differs_in_bits_but_not_in_slots():
+    """dp_shift and dp_shift_ext divide by P at different points: different ciphertexts,
+    identical decryptions."""
+    prm = params.Params(log_n=7, n_q=3, n_p=1, alpha=1)
+    outs = {}
+    for pack in ("dp_shift", "dp_shift_ext"):
+        lay = ffconv.Layout(1, 6, 6, 3, 2, 1, 2, 3, pack=pack)
+        outs[pack] = run_he(prm, lay, seed=5)
+    a, b = outs["dp_shift"][3], outs["dp_shift_ext"][3]
+    s = outs["dp_shift"][1]
+    assert not (a[0].stack() == b[0].stack()).all()
+    for x, y in zip(a, b):
+        assert (bfv.decrypt(prm, s, x) == bfv.decrypt(prm, s, y)).all()
