@@ -34,6 +34,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--pack", default="dp_shift_ext", choices=["dp_shift", "dp_shift_ext", "dp_dot"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -153,7 +154,7 @@ def run(args):
     shape = workloads.MNIST_LAYER
     stream = torch.cuda.Stream()
     ctx = he.Context(log_n=LOG_N, n_q=N_Q, n_p=N_P, alpha=ALPHA, stream=stream)
-    lay = ctx.layout(*shape.astuple(), pack="dp_shift")
+    lay = ctx.layout(*shape.astuple(), pack=args.pack)
     steps = ctx.he_ffconv_required_steps(lay)
     n_rot = len(steps)                    # hoisted rotations per image (I_c = 1: no channel fold)
     N = 1 << LOG_N
@@ -229,7 +230,7 @@ def run(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": "FFConv layer 1x28x28 -> 5x5 s2 p1 (r=2) -> 1x1 (5 ch), DP_SHIFT, "
+            "config": {"workload": f"FFConv layer 1x28x28 -> 5x5 s2 p1 (r=2) -> 1x1 (5 ch), {args.pack}, "
                                    "N=2^15, 12x50-bit q, 3x60-bit p, alpha=3",
                        "batch_per_gpu": B, "layer_ms_per_batch": ms / args.steps,
                        "layer_ms_per_image": ms / args.steps / B, "hoisted_rotations_per_image": n_rot,

@@ -39,7 +39,7 @@ enum {
 };
 
 enum { HE_COEFF = 0, HE_NTT = 1 };            /* representation of a ciphertext's limbs */
-enum { HE_DP_DOT = 0, HE_DP_SHIFT = 1 };      /* W1 schedule, see he_ffconv_layer */
+enum { HE_DP_DOT = 0, HE_DP_SHIFT = 1, HE_DP_SHIFT_EXT = 2 };  /* W1 schedule, see he_ffconv_layer */
 
 /* Rotation step that swaps the two rows of slots (Galois element 2N - 1). */
 #define HE_ROW_SWAP ((int32_t)0x7fffffff)
@@ -74,7 +74,8 @@ typedef struct {
 
 /* Shape of one FFConv layer (Sec. 3.1 notation): input I_c x I_h x I_w, low-rank filters
  * W1 of d x d x I_c x r (r = O'_c of Eq. 2), restoring filters W2 of 1 x 1 x r x O_c,
- * stride and zero padding of W1, pack = HE_DP_DOT or HE_DP_SHIFT, modswitch != 0 drops the
+ * stride and zero padding of W1, pack = HE_DP_DOT, HE_DP_SHIFT or HE_DP_SHIFT_EXT, modswitch
+ * != 0 drops the
  * last ciphertext prime at the end of the layer. */
 typedef struct {
     int32_t I_c, I_h, I_w, d, stride, pad, r, O_c;
@@ -172,19 +173,22 @@ int he_rescale(he_ctx* ctx, const he_ct* in, he_ct* out);
 /* Encrypted FFConv layer, FFConv packing DP-HI2C-CP (Sec. 4.2, Fig. 4; Tables I-III).
  *   ct_in      one ciphertext (NTT domain, level n_q) holding the input image packed as the
  *              layout requires: HE_DP_DOT slot ci*I_h*I_w + h*I_w + w;
- *              HE_DP_SHIFT slot ci*B_c + h*I_w + w with B_c = I_h*I_w for I_c = 1, else the
- *              next power of two.
+ *              HE_DP_SHIFT(_EXT) slot ci*B_c + h*I_w + w with B_c = I_h*I_w for I_c = 1,
+ *              else the next power of two.
  *   lowrank_w  host int32 [r][I_c][d][d] (W1), restore_w host int32 [O_c][r] (W2); weights
  *              are taken mod t.
  *   ct_out     O_c caller-owned ciphertexts (NTT domain; level n_q, or n_q - 1 with
  *              modswitch).  Output channel c holds y2[c, oh, ow] (mod t) at slot
- *              oh*O_w + ow (HE_DP_DOT) or (stride*oh)*I_w + stride*ow (HE_DP_SHIFT).
+ *              oh*O_w + ow (HE_DP_DOT) or (stride*oh)*I_w + stride*ow (the shift schedules).
  * HE_DP_DOT is the paper's DensePack: per output (c', o) a zero-padded filter product and
  * rotate-and-sum over ceil(log2(occupied slots)) steps (plus a row swap when the input fills
  * both rows), then one-hot masks move the r*S dot products into r ciphertexts.
  * HE_DP_SHIFT rotates the input once per filter tap (hoisted) and accumulates tap
- * plaintexts, then folds channels with rotations by B_c*2^k.  Both finish with W2 under
- * ConvPack (scalar products, no rotation).  Needs the Galois keys of the schedule. */
+ * plaintexts, then folds channels with rotations by B_c*2^k.  HE_DP_SHIFT_EXT uses the same
+ * slots and plaintexts but keeps the hoisted rotations in the extended basis Q u P: the tap
+ * products are summed there and divided by P once per low-rank channel (different ciphertext
+ * bits from HE_DP_SHIFT, identical decryptions; at most 64 filter taps).  All finish with W2
+ * under ConvPack (scalar products, no rotation).  Needs the Galois keys of the schedule. */
 int he_ffconv_layer(he_ctx* ctx, const he_ct* ct_in, const int32_t* lowrank_w,
                     const int32_t* restore_w, const he_layout* layout, he_ct* ct_out);
 /* The same layer on B independent ciphertexts with shared weights: ct_in[B],

@@ -519,11 +519,11 @@ extern "C" int he_ntt(he_ctx* ctx, uint64_t* data, int n_items, int n_limbs, int
 // Encode slot values already on the device (items x N int64) into plaintexts [items][L][N]
 // (centred lift, NTT domain; Montgomery form when mont != 0).  `tmp` holds items x N u64.
 void encode_device(he_ctx* ctx, const int64_t* d_slots, int items, uint64_t* tmp, uint64_t* out,
-                   int mont) {
+                   int mont, int rows) {
     launch_slots_to_ntt(ctx, d_slots, tmp, items);
     ntt_inverse(ctx, tmp, items, (size_t)ctx->N, 1, ctx->L + ctx->K);
-    launch_lift(ctx, tmp, out, items, ctx->L, mont);
-    ntt_forward(ctx, out, items, (size_t)ctx->L * ctx->N, ctx->L, 0);
+    launch_lift(ctx, tmp, out, items, rows, mont);
+    ntt_forward(ctx, out, items, (size_t)rows * ctx->N, rows, 0);
 }
 
 extern "C" int he_encode(he_ctx* ctx, const int64_t* slots, uint64_t* pt_out) {
@@ -536,7 +536,7 @@ extern "C" int he_encode(he_ctx* ctx, const int64_t* slots, uint64_t* pt_out) {
     int64_t* ds = (int64_t*)arena_take(ctx, N);
     uint64_t* tmp = arena_take(ctx, N);
     HE_CHECK_CUDA(ctx, cudaMemcpyAsync(ds, slots, N * 8, cudaMemcpyHostToDevice, ctx->stream));
-    encode_device(ctx, ds, 1, tmp, pt_out, 0);
+    encode_device(ctx, ds, 1, tmp, pt_out, 0, ctx->L);
     rc = he_launch_check(ctx, "he_encode");
     HE_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return rc;

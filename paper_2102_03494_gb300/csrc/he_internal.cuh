@@ -156,8 +156,10 @@ int arena_reserve(he_ctx* ctx, size_t n_u64);
 uint32_t galois_elt(const he_ctx* ctx, int32_t step);
 const void* upload_small(he_ctx* ctx, const void* src, size_t bytes);
 int check_ct(he_ctx* ctx, const he_ct* ct, int need_limbs, int need_domain, const char* what);
+// Slot values (items x N int64, device) -> plaintexts [items][rows][N]: centred lift modulo
+// the first `rows` moduli (L for Q, L + K for Q u P), NTT domain, Montgomery form if mont.
 void encode_device(he_ctx* ctx, const int64_t* d_slots, int items, uint64_t* tmp, uint64_t* out,
-                   int mont);
+                   int mont, int rows);
 int he_get_key(he_ctx* ctx, uint32_t g, const uint64_t** key);
 
 // host arithmetic (api.cu)

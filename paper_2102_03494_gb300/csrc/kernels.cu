@@ -169,7 +169,7 @@ __global__ void k_ks_combine(const uint64_t* __restrict__ u, size_t u_stride,
     const uint64_t* vb = v + it * v_stride + (size_t)i * N + n;
     uint64_t r0 = mul_shoup(sub_mod(ub[0], vb[0], q), w.w, w.ws, q);
     uint64_t r1 = mul_shoup(sub_mod(ub[(size_t)LK * N], vb[(size_t)L * N], q), w.w, w.ws, q);
-    r0 = add_mod(r0, c0p[it][(size_t)i * N + src], q);
+    if (c0p) r0 = add_mod(r0, c0p[it][(size_t)i * N + src], q);
     if (basep) {
         const uint64_t* bb = basep[it] + (size_t)i * N + n;
         r0 = add_mod(r0, bb[0], q);
@@ -178,6 +178,81 @@ __global__ void k_ks_combine(const uint64_t* __restrict__ u, size_t u_stride,
     uint64_t* ob = outp[it] + (size_t)i * N + n;
     ob[0] = r0;
     ob[(size_t)L * N] = r1;
+}
+
+// Extended-basis tap MAC (FFConv W1 under DensePack with hoisted rotations, one ModDown per
+// channel): for coefficient n of limb l of image b,
+//   acc_k[c'] = sum_tap pt[c'][tap] * x_k(tap)   over Q u P, with
+//   x_0(tap) = sum_j D_j[perm_g(n)] key_j,0 + P c0[perm_g(n)],  x_1(tap) = sum_j D_j[perm_g(n)] key_j,1
+// (P c0 / P c1 unrotated for the zero offset; P = 0 modulo the special primes).
+// D: [B][dnum][L+K][N]; X: [B][2][L][N] inputs; pts: [r][taps][L+K][N] Montgomery form;
+// A: [B][r][2][L+K][N].  Channels c_lo .. c_lo + c_cnt - 1 (c_cnt <= 8) per launch.
+__global__ void k_ks_mac_ext(const uint64_t* __restrict__ D, const uint64_t* __restrict__ X,
+                             const uint64_t* __restrict__ pts, TapTable tt, int c_lo, int c_cnt,
+                             uint64_t* __restrict__ A, int L, int K, int dnum, int logN,
+                             const ModConst* __restrict__ mods, const uint64_t* __restrict__ pm) {
+    const int N = 1 << logN;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int b = blockIdx.y, l = blockIdx.z;
+    const int LK = L + K;
+    const ModConst M = mods[l];
+    const uint64_t q = M.q;
+    const bool qlimb = l < L;
+    const uint64_t pmod = qlimb ? pm[l] : 0;   // P mod q_l, Montgomery form
+    const size_t LN = (size_t)LK * N;
+    const uint64_t* Db = D + (size_t)b * dnum * LN + (size_t)l * N;
+    const uint64_t* Xb = X + (size_t)b * 2 * L * N + (size_t)l * N;
+    uint64_t acc[8][2];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c][0] = acc[c][1] = 0;
+    for (int t = 0; t < tt.n; ++t) {
+        uint64_t x0 = 0, x1 = 0;
+        const uint64_t* key = tt.key[t];
+        if (!key) {
+            if (qlimb) {
+                U128 p0{0, 0}, p1{0, 0};
+                mac128(p0, Xb[n], pmod);
+                mac128(p1, Xb[(size_t)L * N + n], pmod);
+                x0 = redc(p0, q, M.qinv_neg);
+                x1 = redc(p1, q, M.qinv_neg);
+            }
+        } else {
+            const uint32_t src = perm_src(n, tt.g[t], logN);
+            U128 a0{0, 0}, a1{0, 0};
+            const uint64_t* kb = key + (size_t)l * N + n;
+            for (int j = 0; j < dnum; ++j) {
+                const uint64_t d = Db[(size_t)j * LN + src];
+                mac128(a0, d, kb[(size_t)(2 * j) * LN]);
+                mac128(a1, d, kb[(size_t)(2 * j + 1) * LN]);
+            }
+            x0 = redc(a0, q, M.qinv_neg);
+            x1 = redc(a1, q, M.qinv_neg);
+            if (qlimb) {
+                U128 p0{0, 0};
+                mac128(p0, Xb[src], pmod);
+                x0 = add_mod(x0, redc(p0, q, M.qinv_neg), q);
+            }
+        }
+        const uint64_t* pt = pts + ((size_t)c_lo * tt.n + t) * LN + (size_t)l * N + n;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            if (c >= c_cnt) break;
+            const uint64_t p = pt[(size_t)c * tt.n * LN];
+            U128 m0{0, 0}, m1{0, 0};
+            mac128(m0, x0, p);
+            mac128(m1, x1, p);
+            acc[c][0] = add_mod(acc[c][0], redc(m0, q, M.qinv_neg), q);
+            acc[c][1] = add_mod(acc[c][1], redc(m1, q, M.qinv_neg), q);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        if (c >= c_cnt) break;
+        uint64_t* ab = A + (((size_t)b * tt.r + c_lo + c) * 2) * LN + (size_t)l * N + n;
+        ab[0] = acc[c][0];
+        ab[LN] = acc[c][1];
+    }
 }
 
 // ------------------------------------------------------------------ MulPC / AddCC
@@ -601,6 +676,16 @@ void launch_ks_combine(he_ctx* c, const uint64_t* u, size_t u_stride, const uint
     k_ks_combine<<<grid_nx(items, c->N, c->L), 256, 0, c->stream>>>(
         u, u_stride, v, v_stride, c0p, basep, outp, c->L, c->K, c->logN, g, c->d_mod,
         c->d_md_pinv);
+}
+
+void launch_ks_mac_ext(he_ctx* c, const uint64_t* D, const uint64_t* X, const uint64_t* pts,
+                       const TapTable& tt, uint64_t* A, int B) {
+    for (int c_lo = 0; c_lo < tt.r; c_lo += 8) {
+        ++c->launches;
+        const int cnt = tt.r - c_lo < 8 ? tt.r - c_lo : 8;
+        k_ks_mac_ext<<<dim3((c->N + 255) / 256, B, c->L + c->K), 256, 0, c->stream>>>(
+            D, X, pts, tt, c_lo, cnt, A, c->L, c->K, c->dnum, c->logN, c->d_mod, c->d_pmodq);
+    }
 }
 
 void launch_mac(he_ctx* c, const uint64_t* const* X, const uint64_t* const* P, int T,

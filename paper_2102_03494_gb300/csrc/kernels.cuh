@@ -4,6 +4,19 @@
 #include "he_internal.cuh"
 
 #define HE_DEC_MAX_WORDS 31
+#define HE_MAX_TAPS 64
+
+// Per-tap rotation data of the extended-basis tap MAC (passed by value as a kernel argument):
+// the key (null for the zero offset) and Galois element of each tap, tap count, channels.
+struct TapTable {
+    const uint64_t* key[HE_MAX_TAPS];
+    uint32_t g[HE_MAX_TAPS];
+    int n;
+    int r;
+};
+
+void launch_ks_mac_ext(he_ctx* c, const uint64_t* D, const uint64_t* X, const uint64_t* pts,
+                       const TapTable& tt, uint64_t* A, int B);
 
 void launch_automorph(he_ctx* c, const uint64_t* in, size_t in_stride, uint64_t* out,
                       size_t out_stride, int items, int rows, uint32_t g);

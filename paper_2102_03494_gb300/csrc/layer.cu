@@ -13,6 +13,13 @@
 // HE_DP_SHIFT (hoisted taps): one hoisted rotation of the input per filter tap
 // delta = (i - pad) I_w + (j - pad) and a plaintext per (c', tap) holding W1[c', ci, i, j] at
 // the output base slots; channels folded with rotations by B_c 2^e.
+//
+// HE_DP_SHIFT_EXT (hoisted taps, extended-basis sums): the same slots and plaintexts, but the
+// key-switched rotations are not divided by P one by one.  For every coefficient, one kernel
+// forms each tap's inner product with its Galois key (plus P times the rotated c0), multiplies
+// it by the tap plaintext lifted to Q u P and sums over taps for every channel in registers;
+// one ModDown per (image, channel) follows.  Per image this replaces d^2 - 1 ModDowns (2K
+// inverse and 2L forward transforms each) with r of them.
 #include <algorithm>
 #include <vector>
 
@@ -56,7 +63,8 @@ bool window_covers(const he_layout& y, const LayoutInfo& li, int k) {
 
 int layout_info(const he_ctx* c, const he_layout* y, LayoutInfo* li, std::string* why) {
     if (y->I_c < 1 || y->I_h < 1 || y->I_w < 1 || y->d < 1 || y->stride < 1 || y->pad < 0 ||
-        y->r < 1 || y->O_c < 1 || (y->pack != HE_DP_DOT && y->pack != HE_DP_SHIFT)) {
+        y->r < 1 || y->O_c < 1 ||
+        (y->pack != HE_DP_DOT && y->pack != HE_DP_SHIFT && y->pack != HE_DP_SHIFT_EXT)) {
         *why = "layout fields out of range";
         return HE_EINVAL;
     }
@@ -157,6 +165,21 @@ __global__ void k_dp_dot_slots(const int32_t* __restrict__ w1, int I_c, int I_h,
     }
 }
 
+// Channel fold (input channels in blocks of B_c slots): acc <- acc + rot(acc, B_c 2^e); the
+// result ends in A (A and A2 are swapped as needed).
+int fold_channels(he_ctx* ctx, uint64_t*& A, uint64_t*& A2, int items, const LayoutInfo& li,
+                  const RotBufs& rb, int chunk) {
+    const size_t ct = 2 * (size_t)ctx->L * ctx->N;
+    for (int e = 0; e < li.fold; ++e) {
+        std::vector<uint64_t*> o(items);
+        for (int q = 0; q < items; ++q) o[q] = A2 + (size_t)q * ct;
+        int rc = rotate_contig(ctx, A, items, galois_elt(ctx, li.B_c << e), A, o, rb, chunk);
+        if (rc) return rc;
+        std::swap(A, A2);
+    }
+    return HE_OK;
+}
+
 }  // namespace
 
 extern "C" int he_ffconv_required_steps(const he_ctx* ctx, const he_layout* layout,
@@ -200,15 +223,22 @@ extern "C" int he_ffconv_layer_batch(he_ctx* ctx, const he_ct* ct_in, int B,
     const size_t N = ctx->N, ct = 2 * (size_t)L * N;
     const int r = y.r, O_c = y.O_c;
     const bool dot = y.pack == HE_DP_DOT;
+    const bool ext = y.pack == HE_DP_SHIFT_EXT;
+    if (ext && li.taps > HE_MAX_TAPS) return he_fail(ctx, HE_EINVAL, "he_ffconv_layer: too many filter taps");
+    const int LK = L + ctx->K;
+    const int pt_rows = ext ? LK : L;                          // extended plaintexts live in Q u P
     const int n_pt = dot ? r * li.S + li.S : r * li.taps;
-    const int n_prod = dot ? B * r * li.S : B * li.taps;      // ciphertexts fed to the MAC
-    // ciphertexts key-switched per launch: all of them when the scratch allows
-    const int chunk = std::min(dot ? n_prod : (li.fold ? B * r : B), rotation_chunk(ctx));
+    const int n_prod = dot ? B * r * li.S : (ext ? 0 : B * li.taps);   // ciphertexts fed to the MAC
+    // ciphertexts key-switched per launch: all of them when the scratch allows (the
+    // extended-basis schedule keeps every image's ModUp digits and channel sums at once)
+    const int chunk = ext ? std::max(B * r, B)
+                          : std::min(dot ? n_prod : (li.fold ? B * r : B), rotation_chunk(ctx));
     const int rot_items = chunk;
+    const size_t ext_acc = ext ? (size_t)B * r * 2 * LK * N : 0;
     size_t need = (size_t)B * ct                              // X
-                  + (size_t)n_pt * (2 * N + (size_t)L * N)     // slots, tmp, plaintexts
+                  + (size_t)n_pt * (2 * N + (size_t)pt_rows * N)  // slots, tmp, plaintexts
                   + (size_t)n_prod * ct * (dot ? 2 : 1)        // products (double buffer for DP_DOT)
-                  + (size_t)2 * B * r * ct                     // accumulators (double buffer)
+                  + (size_t)2 * B * r * ct + ext_acc           // accumulators (double buffer)
                   + (size_t)rot_items * rot_scratch_per_item(ctx)
                   + (y.modswitch ? (size_t)B * O_c * (ct + 2 * N + 2 * (L - 1) * N) : 0) + 1024;
     if ((rc = arena_reserve(ctx, need))) return rc;
@@ -216,8 +246,9 @@ extern "C" int he_ffconv_layer_batch(he_ctx* ctx, const he_ct* ct_in, int B,
     uint64_t* X = arena_take(ctx, (size_t)B * ct);
     int64_t* slots = (int64_t*)arena_take(ctx, (size_t)n_pt * N);
     uint64_t* tmp = arena_take(ctx, (size_t)n_pt * N);
-    uint64_t* pts = arena_take(ctx, (size_t)n_pt * L * N);
-    uint64_t* PR = arena_take(ctx, (size_t)n_prod * ct);
+    uint64_t* pts = arena_take(ctx, (size_t)n_pt * pt_rows * N);
+    uint64_t* PR = n_prod ? arena_take(ctx, (size_t)n_prod * ct) : nullptr;
+    uint64_t* AX = ext ? arena_take(ctx, ext_acc) : nullptr;
     uint64_t* PR2 = dot ? arena_take(ctx, (size_t)n_prod * ct) : nullptr;
     uint64_t* A = arena_take(ctx, (size_t)B * r * ct);
     uint64_t* A2 = arena_take(ctx, (size_t)B * r * ct);
@@ -244,7 +275,7 @@ extern "C" int he_ffconv_layer_batch(he_ctx* ctx, const he_ct* ct_in, int B,
         k_dp_shift_slots<<<dim3(n_pt, 4), 256, 0, ctx->stream>>>(d_w1, y.I_c, y.I_h, y.I_w, y.d,
                                                                  y.stride, y.pad, r, li.O_h, li.O_w,
                                                                  li.B_c, ctx->logN, slots);
-    encode_device(ctx, slots, n_pt, tmp, pts, 1);
+    encode_device(ctx, slots, n_pt, tmp, pts, 1, pt_rows);
 
     if (dot) {
         // prod[b][c'][o] = X[b] * filter(c', o)
@@ -293,6 +324,40 @@ extern "C" int he_ffconv_layer_batch(he_ctx* ctx, const he_ct* ct_in, int B,
         }
         ctx->ops[0] += (uint64_t)B * r * li.S;
         ctx->ops[1] += (uint64_t)B * r * (li.S - 1);
+    } else if (ext) {
+        // one ModUp of every input's c1, then every tap's key switch and plaintext product
+        // summed in Q u P, then one ModDown per (image, channel)
+        modup_items(ctx, X, B, 1u, rb);
+        TapTable tt{};
+        tt.n = li.taps;
+        tt.r = r;
+        int tap = 0, nrot = 0;
+        for (int i = 0; i < y.d; ++i)
+            for (int j = 0; j < y.d; ++j, ++tap) {
+                const int dl = (i - y.pad) * y.I_w + (j - y.pad);
+                tt.key[tap] = nullptr;
+                tt.g[tap] = 1u;
+                if (dl == 0) continue;
+                tt.g[tap] = galois_elt(ctx, dl);
+                if ((rc = he_get_key(ctx, tt.g[tap], &tt.key[tap]))) return rc;
+                ++nrot;
+            }
+        launch_ks_mac_ext(ctx, rb.D, X, pts, tt, AX, B);
+        const int items = B * r;
+        const size_t ext_ct = 2 * (size_t)LK * N;
+        ntt_inverse(ctx, AX + (size_t)L * N, items * 2, (size_t)LK * N, ctx->K, L);
+        launch_moddown_conv(ctx, AX, ext_ct, rb.v, ct, items);
+        ntt_forward(ctx, rb.v, items * 2, (size_t)L * N, L, 0);
+        std::vector<uint64_t*> ao(items);
+        for (int q = 0; q < items; ++q) ao[q] = A + (size_t)q * ct;
+        auto op = upload_out_ptrs(ctx, ao);
+        if (!op) return he_fail(ctx, HE_ECUDA, "pointer table upload failed");
+        launch_ks_combine(ctx, AX, ext_ct, rb.v, ct, nullptr, nullptr, op, items, 1u);
+        ctx->ops[0] += (uint64_t)B * r * li.taps;
+        ctx->ops[1] += (uint64_t)B * r * (li.taps - 1);
+        ctx->ops[2] += (uint64_t)B * nrot;
+        ctx->ops[3] += (uint64_t)B * nrot;
+        if ((rc = fold_channels(ctx, A, A2, B * r, li, rb, rot_items))) return rc;
     } else {
         // hoisted rotations of every input by every non-zero tap offset
         std::vector<uint32_t> hg;
@@ -337,14 +402,7 @@ extern "C" int he_ffconv_layer_batch(he_ctx* ctx, const he_ct* ct_in, int B,
         launch_mac(ctx, a1, a2, li.taps, nullptr, a4, B * r, L);
         ctx->ops[0] += (uint64_t)B * r * li.taps;
         ctx->ops[1] += (uint64_t)B * r * (li.taps - 1);
-        // channel fold: acc += rot(acc, B_c 2^e)
-        for (int e = 0; e < li.fold; ++e) {
-            std::vector<uint64_t*> o(B * r);
-            for (int q = 0; q < B * r; ++q) o[q] = A2 + (size_t)q * ct;
-            if ((rc = rotate_contig(ctx, A, B * r, galois_elt(ctx, li.B_c << e), A, o, rb, rot_items)))
-                return rc;
-            std::swap(A, A2);
-        }
+        if ((rc = fold_channels(ctx, A, A2, B * r, li, rb, rot_items))) return rc;
     }
 
     // W2 under ConvPack: ct_out[b][c] = sum_c' W2[c][c'] ct_w1[b][c'] (scalar plaintexts)

@@ -12,7 +12,7 @@ import numpy as np
 
 HE_OK, HE_EINVAL, HE_ENOMEM, HE_ENOKEY, HE_ECUDA, HE_ETIMEOUT = 0, -1, -2, -3, -4, -5
 HE_COEFF, HE_NTT = 0, 1
-HE_DP_DOT, HE_DP_SHIFT = 0, 1
+HE_DP_DOT, HE_DP_SHIFT, HE_DP_SHIFT_EXT = 0, 1, 2
 HE_ROW_SWAP = 0x7FFFFFFF
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -303,8 +303,8 @@ class Context:
 
     @staticmethod
     def layout(I_c, I_h, I_w, d, stride, pad, r, O_c, pack="dp_shift", modswitch=False):
-        return HeLayout(I_c, I_h, I_w, d, stride, pad, r, O_c,
-                        HE_DP_DOT if pack == "dp_dot" else HE_DP_SHIFT, int(bool(modswitch)))
+        packs = {"dp_dot": HE_DP_DOT, "dp_shift": HE_DP_SHIFT, "dp_shift_ext": HE_DP_SHIFT_EXT}
+        return HeLayout(I_c, I_h, I_w, d, stride, pad, r, O_c, packs[pack], int(bool(modswitch)))
 
     def he_ffconv_required_steps(self, lay):
         out = np.zeros(4096, dtype=np.int32)

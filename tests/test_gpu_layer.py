@@ -39,7 +39,7 @@ SMALL = [workloads.LayerShape(1, 8, 8, 3, 2, 1, 2, 3), workloads.LayerShape(2, 6
          workloads.LayerShape(3, 5, 7, 3, 2, 1, 3, 4), workloads.LayerShape(1, 9, 9, 5, 2, 2, 1, 2)]
 
 
-@pytest.mark.parametrize("pack", ["dp_shift", "dp_dot"])
+@pytest.mark.parametrize("pack", ["dp_shift", "dp_shift_ext", "dp_dot"])
 @pytest.mark.parametrize("si", range(len(SMALL)))
 def test_small_layers_are_bit_exact(pack, si):
     prm = params.Params(log_n=9, n_q=3, n_p=1, alpha=1)
@@ -61,7 +61,7 @@ def test_small_layers_are_bit_exact(pack, si):
     check_decrypted(ctx, prm, s, lay_o, outs, xs[0], W1, W2)
 
 
-@pytest.mark.parametrize("pack", ["dp_shift", "dp_dot"])
+@pytest.mark.parametrize("pack", ["dp_shift", "dp_shift_ext", "dp_dot"])
 def test_batched_layer_with_modswitch_and_wide_digits(pack):
     prm = params.Params(log_n=10, n_q=4, n_p=2, alpha=2)
     shape = workloads.LayerShape(2, 6, 6, 3, 2, 1, 2, 3)
@@ -81,14 +81,15 @@ def test_batched_layer_with_modswitch_and_wide_digits(pack):
             assert (ctx.to_numpy(single[c]) == ctx.to_numpy(outs[b * shape.O_c + c])).all()
 
 
-def test_mnist_layer_dp_shift_n8192_is_bit_exact():
+@pytest.mark.parametrize("pack", ["dp_shift", "dp_shift_ext"])
+def test_mnist_layer_n8192_is_bit_exact(pack):
     """The 1 x 28 x 28, 5 x 5 stride-2, r = 2 -> 5 channel layer at N = 8192 (3 x 50-bit q)."""
     prm = params.cfg_small_layer()
     shape = workloads.MNIST_LAYER
-    lay_o, s, steps, keys, blob, xs, W1, W2, cts = setup_layer(prm, shape, "dp_shift")
+    lay_o, s, steps, keys, blob, xs, W1, W2, cts = setup_layer(prm, shape, pack)
     ctx = make_ctx(prm)
     ctx.he_load_keys(blob, gpu_steps(steps))
-    lay = ctx.layout(*shape.astuple(), pack="dp_shift")
+    lay = ctx.layout(*shape.astuple(), pack=pack)
     want = ffconv.he_layer(prm, cts[0], W1, W2, lay_o, keys)
     outs = ctx.he_ffconv_layer(upload_ntt(ctx, cts[0]), W1, W2, lay)
     for o, w in zip(outs, want):
@@ -115,14 +116,16 @@ def test_mnist_layer_dp_dot_n8192_decrypts_to_the_convolution():
     assert got["rot"] == 2 * 169 * 10
 
 
-@pytest.mark.parametrize("B", [1, 4])
-def test_bench_layer_n15_decrypts_to_the_convolution(B):
-    """The benchmark configuration: N = 2^15, 12 x 50-bit q, 3 x 60-bit p, digits of 3."""
+@pytest.mark.parametrize("pack,B", [("dp_shift", 1), ("dp_shift", 4), ("dp_shift_ext", 1),
+                                    ("dp_shift_ext", 16)])
+def test_bench_layer_n15_decrypts_to_the_convolution(pack, B):
+    """The benchmark configuration: N = 2^15, 12 x 50-bit q, 3 x 60-bit p, digits of 3, in the
+    launch configuration the benchmark times (batch of 16 under dp_shift_ext)."""
     prm = params.cfg_n15()
     shape = workloads.MNIST_LAYER
     ctx = make_ctx(prm)
-    lay_o = ffconv.Layout(*shape.astuple(), pack="dp_shift")
-    lay = ctx.layout(*shape.astuple(), pack="dp_shift")
+    lay_o = ffconv.Layout(*shape.astuple(), pack=pack)
+    lay = ctx.layout(*shape.astuple(), pack=pack)
     sk = ctx.he_keygen_secret(1)
     ctx.he_keygen_galois(sk, 2, ctx.he_ffconv_required_steps(lay))
     xs = workloads.images(0, shape, B)
