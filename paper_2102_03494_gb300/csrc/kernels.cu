@@ -180,78 +180,143 @@ __global__ void k_ks_combine(const uint64_t* __restrict__ u, size_t u_stride,
     ob[(size_t)L * N] = r1;
 }
 
+// REDC for x < 2q 2^64 (a sum of products plus one residue times 2^64): result in [0, q).
+__device__ __forceinline__ uint64_t redc_wide(U128 x, uint64_t q, uint64_t qinv_neg) {
+    uint64_t m = x.lo * qinv_neg;
+    uint64_t t = x.hi + __umul64hi(m, q) + (x.lo != 0 ? 1u : 0u);   // < 3q
+    t = t >= q ? t - q : t;
+    return t >= q ? t - q : t;
+}
+
+// XP[b][k][l][n] = P * x_k[l][n] mod q_l for the ciphertext limbs (P c0, P c1 of each input).
+__global__ void k_scale_p(const uint64_t* __restrict__ X, uint64_t* __restrict__ XP, int L, int logN,
+                          const ModConst* __restrict__ mods, const uint64_t* __restrict__ pm) {
+    const int N = 1 << logN;
+    const int n = blockIdx.y * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int kl = blockIdx.z, l = kl % L;
+    const ModConst M = mods[l];
+    const size_t off = ((size_t)blockIdx.x * 2 * L + kl) * N + n;
+    U128 p{0, 0};
+    mac128(p, X[off], pm[l]);
+    XP[off] = redc(p, M.q, M.qinv_neg);
+}
+
 // Extended-basis tap MAC (FFConv W1 under DensePack with hoisted rotations, one ModDown per
 // channel): for coefficient n of limb l of image b,
 //   acc_k[c'] = sum_tap pt[c'][tap] * x_k(tap)   over Q u P, with
-//   x_0(tap) = sum_j D_j[perm_g(n)] key_j,0 + P c0[perm_g(n)],  x_1(tap) = sum_j D_j[perm_g(n)] key_j,1
-// (P c0 / P c1 unrotated for the zero offset; P = 0 modulo the special primes).
-// D: [B][dnum][L+K][N]; X: [B][2][L][N] inputs; pts: [r][taps][L+K][N] Montgomery form;
-// A: [B][r][2][L+K][N].  Channels c_lo .. c_lo + c_cnt - 1 (c_cnt <= 8) per launch.
-__global__ void k_ks_mac_ext(const uint64_t* __restrict__ D, const uint64_t* __restrict__ X,
-                             const uint64_t* __restrict__ pts, TapTable tt, int c_lo, int c_cnt,
-                             uint64_t* __restrict__ A, int L, int K, int dnum, int logN,
-                             const ModConst* __restrict__ mods, const uint64_t* __restrict__ pm) {
+//   x_0(tap) = sum_j D_j[perm_g(n)] key_j,0 + (P c0)[perm_g(n)],  x_1(tap) = sum_j D_j[perm_g(n)] key_j,1
+// ((P c0, P c1) unrotated for the zero offset; P = 0 modulo the special primes).
+// D: [B][DNUM][L+K][N]; XP: [B][2][L][N] (P times the inputs); pts: [r][taps][L+K][N]
+// Montgomery form; A: [B][r][2][L+K][N].  One thread handles two images and two channels
+// (c_lo, c_lo + 1 when c_cnt = 2), so each key and plaintext value it loads serves four
+// products; the grid's x dimension walks image pairs so that CTAs sharing a key tile run
+// together.  Plaintext products are summed unreduced in 128 bits and reduced every 8 taps.
+template <int DNUM>
+__global__ void __launch_bounds__(256)
+k_ks_mac_ext(const uint64_t* __restrict__ D, const uint64_t* __restrict__ XP,
+             const uint64_t* __restrict__ pts, TapTable tt, int c_lo, int c_cnt, int B,
+             uint64_t* __restrict__ A, int L, int K, int logN, const ModConst* __restrict__ mods) {
     const int N = 1 << logN;
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.y * blockDim.x + threadIdx.x;
     if (n >= N) return;
-    const int b = blockIdx.y, l = blockIdx.z;
+    const int l = blockIdx.z;
+    const int b0 = blockIdx.x * 2;
+    const int nb = B - b0 < 2 ? B - b0 : 2;
     const int LK = L + K;
     const ModConst M = mods[l];
-    const uint64_t q = M.q;
+    const uint64_t q = M.q, qi = M.qinv_neg;
     const bool qlimb = l < L;
-    const uint64_t pmod = qlimb ? pm[l] : 0;   // P mod q_l, Montgomery form
     const size_t LN = (size_t)LK * N;
-    const uint64_t* Db = D + (size_t)b * dnum * LN + (size_t)l * N;
-    const uint64_t* Xb = X + (size_t)b * 2 * L * N + (size_t)l * N;
-    uint64_t acc[8][2];
+    const uint64_t* Db[2];
+    const uint64_t* Xb[2];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) acc[c][0] = acc[c][1] = 0;
+    for (int ib = 0; ib < 2; ++ib) {
+        const int b = b0 + (ib < nb ? ib : 0);
+        Db[ib] = D + (size_t)b * DNUM * LN + (size_t)l * N;
+        Xb[ib] = XP + (size_t)b * 2 * L * N + (size_t)(qlimb ? l : 0) * N;
+    }
+    U128 a128[2][2][2];       // [image][channel][poly], unreduced
+    uint64_t acc[2][2][2];    // reduced running sums
+#pragma unroll
+    for (int ib = 0; ib < 2; ++ib)
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                a128[ib][c][k] = U128{0, 0};
+                acc[ib][c][k] = 0;
+            }
+    const uint64_t* pt0 = pts + ((size_t)c_lo * tt.n) * LN + (size_t)l * N + n;
+    const size_t pstride = (size_t)tt.n * LN;
+    int pending = 0;
     for (int t = 0; t < tt.n; ++t) {
-        uint64_t x0 = 0, x1 = 0;
+        const uint64_t p0 = pt0[(size_t)t * LN];
+        const uint64_t p1 = c_cnt > 1 ? pt0[pstride + (size_t)t * LN] : 0;
         const uint64_t* key = tt.key[t];
+        uint64_t x[2][2];
         if (!key) {
-            if (qlimb) {
-                U128 p0{0, 0}, p1{0, 0};
-                mac128(p0, Xb[n], pmod);
-                mac128(p1, Xb[(size_t)L * N + n], pmod);
-                x0 = redc(p0, q, M.qinv_neg);
-                x1 = redc(p1, q, M.qinv_neg);
+#pragma unroll
+            for (int ib = 0; ib < 2; ++ib) {
+                x[ib][0] = qlimb ? Xb[ib][n] : 0;
+                x[ib][1] = qlimb ? Xb[ib][(size_t)L * N + n] : 0;
             }
         } else {
             const uint32_t src = perm_src(n, tt.g[t], logN);
-            U128 a0{0, 0}, a1{0, 0};
             const uint64_t* kb = key + (size_t)l * N + n;
-            for (int j = 0; j < dnum; ++j) {
-                const uint64_t d = Db[(size_t)j * LN + src];
-                mac128(a0, d, kb[(size_t)(2 * j) * LN]);
-                mac128(a1, d, kb[(size_t)(2 * j + 1) * LN]);
+            uint64_t kv[DNUM][2];
+#pragma unroll
+            for (int j = 0; j < DNUM; ++j) {
+                kv[j][0] = kb[(size_t)(2 * j) * LN];
+                kv[j][1] = kb[(size_t)(2 * j + 1) * LN];
             }
-            x0 = redc(a0, q, M.qinv_neg);
-            x1 = redc(a1, q, M.qinv_neg);
-            if (qlimb) {
-                U128 p0{0, 0};
-                mac128(p0, Xb[src], pmod);
-                x0 = add_mod(x0, redc(p0, q, M.qinv_neg), q);
+#pragma unroll
+            for (int ib = 0; ib < 2; ++ib) {
+                uint64_t dv[DNUM];
+#pragma unroll
+                for (int j = 0; j < DNUM; ++j) dv[j] = Db[ib][(size_t)j * LN + src];
+                const uint64_t c0p = qlimb ? Xb[ib][src] : 0;
+                U128 s0{0, 0}, s1{0, 0};
+#pragma unroll
+                for (int j = 0; j < DNUM; ++j) {
+                    mac128(s0, dv[j], kv[j][0]);
+                    mac128(s1, dv[j], kv[j][1]);
+                }
+                s0.hi += c0p;   // + (P c0) 2^64 before the division by 2^64
+                x[ib][0] = redc_wide(s0, q, qi);
+                x[ib][1] = redc(s1, q, qi);
             }
         }
-        const uint64_t* pt = pts + ((size_t)c_lo * tt.n + t) * LN + (size_t)l * N + n;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            if (c >= c_cnt) break;
-            const uint64_t p = pt[(size_t)c * tt.n * LN];
-            U128 m0{0, 0}, m1{0, 0};
-            mac128(m0, x0, p);
-            mac128(m1, x1, p);
-            acc[c][0] = add_mod(acc[c][0], redc(m0, q, M.qinv_neg), q);
-            acc[c][1] = add_mod(acc[c][1], redc(m1, q, M.qinv_neg), q);
+        for (int ib = 0; ib < 2; ++ib)
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                mac128(a128[ib][0][k], x[ib][k], p0);
+                mac128(a128[ib][1][k], x[ib][k], p1);
+            }
+        if (++pending == 8 || t == tt.n - 1) {
+            pending = 0;
+#pragma unroll
+            for (int ib = 0; ib < 2; ++ib)
+#pragma unroll
+                for (int c = 0; c < 2; ++c)
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        acc[ib][c][k] = add_mod(acc[ib][c][k], redc(a128[ib][c][k], q, qi), q);
+                        a128[ib][c][k] = U128{0, 0};
+                    }
         }
     }
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        if (c >= c_cnt) break;
-        uint64_t* ab = A + (((size_t)b * tt.r + c_lo + c) * 2) * LN + (size_t)l * N + n;
-        ab[0] = acc[c][0];
-        ab[LN] = acc[c][1];
+    for (int ib = 0; ib < 2; ++ib) {
+        if (ib >= nb) break;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            if (c >= c_cnt) break;
+            uint64_t* ab = A + (((size_t)(b0 + ib) * tt.r + c_lo + c) * 2) * LN + (size_t)l * N + n;
+            ab[0] = acc[ib][c][0];
+            ab[LN] = acc[ib][c][1];
+        }
     }
 }
 
@@ -429,8 +494,9 @@ __global__ void k_lift(const uint64_t* __restrict__ m, uint64_t* __restrict__ ou
     const bool neg = x > (t - 1) / 2;
     for (int i = 0; i < L; ++i) {
         const ModConst M = mods[i];
-        uint64_t r = neg ? M.q - ((t - x) % M.q) : x % M.q;
-        if (r == M.q) r = 0;
+        uint64_t r;
+        if (t <= M.q) r = neg ? M.q - (t - x) : x;          // x, t - x < q: no reduction
+        else r = neg ? (M.q - ((t - x) % M.q)) % M.q : x % M.q;
         o[(size_t)i * N] = mont ? to_mont(r, M) : r;
     }
 }
@@ -678,13 +744,29 @@ void launch_ks_combine(he_ctx* c, const uint64_t* u, size_t u_stride, const uint
         c->d_md_pinv);
 }
 
-void launch_ks_mac_ext(he_ctx* c, const uint64_t* D, const uint64_t* X, const uint64_t* pts,
-                       const TapTable& tt, uint64_t* A, int B) {
-    for (int c_lo = 0; c_lo < tt.r; c_lo += 8) {
+void launch_ks_mac_ext(he_ctx* c, const uint64_t* D, const uint64_t* X, uint64_t* XP,
+                       const uint64_t* pts, const TapTable& tt, uint64_t* A, int B) {
+    ++c->launches;
+    k_scale_p<<<grid_nx(B, c->N, 2 * c->L), 256, 0, c->stream>>>(X, XP, c->L, c->logN, c->d_mod,
+                                                                 c->d_pmodq);
+    const dim3 grid((B + 1) / 2, (c->N + 255) / 256, c->L + c->K);
+    for (int c_lo = 0; c_lo < tt.r; c_lo += 2) {
         ++c->launches;
-        const int cnt = tt.r - c_lo < 8 ? tt.r - c_lo : 8;
-        k_ks_mac_ext<<<dim3((c->N + 255) / 256, B, c->L + c->K), 256, 0, c->stream>>>(
-            D, X, pts, tt, c_lo, cnt, A, c->L, c->K, c->dnum, c->logN, c->d_mod, c->d_pmodq);
+        const int cnt = tt.r - c_lo < 2 ? tt.r - c_lo : 2;
+#define HE_KS_MAC(DN)                                                                         \
+    k_ks_mac_ext<DN><<<grid, 256, 0, c->stream>>>(D, XP, pts, tt, c_lo, cnt, B, A, c->L, c->K,  \
+                                                  c->logN, c->d_mod)
+        switch (c->dnum) {
+            case 1: HE_KS_MAC(1); break;
+            case 2: HE_KS_MAC(2); break;
+            case 3: HE_KS_MAC(3); break;
+            case 4: HE_KS_MAC(4); break;
+            case 5: HE_KS_MAC(5); break;
+            case 6: HE_KS_MAC(6); break;
+            case 7: HE_KS_MAC(7); break;
+            default: HE_KS_MAC(8); break;
+        }
+#undef HE_KS_MAC
     }
 }
 

@@ -234,7 +234,7 @@ extern "C" int he_ffconv_layer_batch(he_ctx* ctx, const he_ct* ct_in, int B,
     const int chunk = ext ? std::max(B * r, B)
                           : std::min(dot ? n_prod : (li.fold ? B * r : B), rotation_chunk(ctx));
     const int rot_items = chunk;
-    const size_t ext_acc = ext ? (size_t)B * r * 2 * LK * N : 0;
+    const size_t ext_acc = ext ? (size_t)B * r * 2 * LK * N + (size_t)B * ct : 0;  // sums, P x
     size_t need = (size_t)B * ct                              // X
                   + (size_t)n_pt * (2 * N + (size_t)pt_rows * N)  // slots, tmp, plaintexts
                   + (size_t)n_prod * ct * (dot ? 2 : 1)        // products (double buffer for DP_DOT)
@@ -248,7 +248,8 @@ extern "C" int he_ffconv_layer_batch(he_ctx* ctx, const he_ct* ct_in, int B,
     uint64_t* tmp = arena_take(ctx, (size_t)n_pt * N);
     uint64_t* pts = arena_take(ctx, (size_t)n_pt * pt_rows * N);
     uint64_t* PR = n_prod ? arena_take(ctx, (size_t)n_prod * ct) : nullptr;
-    uint64_t* AX = ext ? arena_take(ctx, ext_acc) : nullptr;
+    uint64_t* AX = ext ? arena_take(ctx, (size_t)B * r * 2 * LK * N) : nullptr;
+    uint64_t* XP = ext ? arena_take(ctx, (size_t)B * ct) : nullptr;
     uint64_t* PR2 = dot ? arena_take(ctx, (size_t)n_prod * ct) : nullptr;
     uint64_t* A = arena_take(ctx, (size_t)B * r * ct);
     uint64_t* A2 = arena_take(ctx, (size_t)B * r * ct);
@@ -342,7 +343,7 @@ extern "C" int he_ffconv_layer_batch(he_ctx* ctx, const he_ct* ct_in, int B,
                 if ((rc = he_get_key(ctx, tt.g[tap], &tt.key[tap]))) return rc;
                 ++nrot;
             }
-        launch_ks_mac_ext(ctx, rb.D, X, pts, tt, AX, B);
+        launch_ks_mac_ext(ctx, rb.D, X, XP, pts, tt, AX, B);
         const int items = B * r;
         const size_t ext_ct = 2 * (size_t)LK * N;
         ntt_inverse(ctx, AX + (size_t)L * N, items * 2, (size_t)LK * N, ctx->K, L);
