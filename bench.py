@@ -30,7 +30,7 @@ LOG_N, N_Q, N_P, ALPHA = 15, 12, 3, 3
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -106,7 +106,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -186,6 +186,8 @@ def run(args):
     time.sleep(0.3)
     l0 = ctx.he_launch_count()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.he_phase_times()                  # clear, then time every phase of the timed layers
+    ctx.he_set_phase_timing(True)
     torch.cuda.synchronize()
     ev0.record(stream)
     for _ in range(args.steps):
@@ -193,6 +195,8 @@ def run(args):
     ev1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
+    phases = ctx.he_phase_times()
+    ctx.he_set_phase_timing(False)
     launches = ctx.he_launch_count() - l0
     ms = ev0.elapsed_time(ev1)
 
@@ -216,8 +220,9 @@ def run(args):
     torch.cuda.synchronize()
     ms_e2e = e0.elapsed_time(e1)
 
-    # roofline of the dominant kernel, timed alone on the same stream
-    roof = kernel_roofline(ctx, stream, B)
+    roof = taps_roofline(phases, args, B, n_rot)
+    layer_bytes = layer_algorithmic_bytes(B, shape.O_c, n_rot)
+    peaks = measured_peaks()
 
     if dist:
         t = torch.tensor([ms, ms_e2e], device="cuda")
@@ -238,7 +243,14 @@ def run(args):
                        "l2": "inputs larger than L2 (keys 377 MB + ModUp digits per step)"},
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": B * ct_bytes,
                     "d2h_bytes_per_step": B * shape.O_c * ct_bytes, "ms_per_step": ms_e2e / args.steps},
-            "gpu_launches": launches, "clocks": clk, "roofline": roof}
+            "gpu_launches": launches, "clocks": clk, "roofline": roof,
+            "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items() if v[1]},
+            "layer_hbm": {"algorithmic_bytes_per_step": layer_bytes,
+                          "achieved_gbs": layer_bytes / (ms / args.steps / 1000.0) / 1e9,
+                          "peak_gbs": peaks["hbm_gbs"],
+                          "frac": layer_bytes / (ms / args.steps / 1000.0) / 1e9 / peaks["hbm_gbs"],
+                          "note": "keys read once per batch + input and output ciphertexts; "
+                                  "the layer is bound by 64-bit modular products, not HBM"}}
     if world == 1 and not args.no_cpu_baseline:
         dt, n, desc = oracle_sample(n_steps=2)
         line["cpu_baseline"] = {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -246,32 +258,48 @@ def run(args):
     print(json.dumps(line))
 
 
-def kernel_roofline(ctx, stream, B):
-    """Average duration of the NTT launch pair the layer issues most (the ModDown transforms of
-    B ciphertexts: 2 x 12 limbs forward), from CUDA events around repeated launches."""
-    import torch
-    N, L = 1 << LOG_N, N_Q
-    items = 2 * B
-    buf = torch.randint(0, 1 << 40, (items, L, N), dtype=torch.int64, device="cuda")
-    reps = 20
-    torch.cuda.synchronize()
-    for _ in range(3):
-        ctx.he_ntt(buf, items, L)
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for _ in range(reps):
-        ctx.he_ntt(buf, items, L)
-    b.record(stream)
-    torch.cuda.synchronize()
-    sec = a.elapsed_time(b) / 1000.0 / reps
-    limbs = items * L
-    byts = limbs * N * 8 * 2           # each limb read and written once
-    peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
-        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
-    gbs = byts / sec / 1e9
-    return {"kernel": "ntt forward (column + row pass)", "bound": "hbm", "achieved": gbs,
-            "peak": peak, "unit": "GB/s", "frac": gbs / peak, "traffic": None,
-            "launch_us": sec * 1e6, "limbs_per_launch": limbs}
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return {"hbm_gbs": d["hbm_gbs"], "sm_max_mhz": d.get("sm_max_mhz", 2070.0), "src": "measured"}
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "src": "fallback"}
+
+
+# 64 x 64 -> 128-bit products per second of the GPU's integer multiplier: 152 SMs x 64 32-bit
+# multiply-adds per clock x clock / 4 (a 64 x 64-bit product takes four 32 x 32-bit ones).
+def mul64_peak_per_s(sm_mhz):
+    return 152 * 64 / 4 * sm_mhz * 1e6
+
+
+def taps_roofline(phases, args, B, n_rot):
+    """Roofline of the dominant kernel, the extended-basis tap MAC (k_ks_mac_ext), from its
+    CUDA-event time inside the timed region.  Algorithmic work: per image, ciphertext-basis
+    limb and coefficient, 2 dnum products for the key inner product of each rotated tap and
+    2 r products for the plaintext product of every tap."""
+    ms, spans = phases["taps"]
+    if not spans or args.pack != "dp_shift_ext":
+        return None
+    N, LK, dnum, r, taps = 1 << LOG_N, N_Q + N_P, -(-N_Q // ALPHA), 2, 25
+    products = B * N * LK * (n_rot * 2 * dnum + taps * 2 * r)
+    sec = ms / 1000.0 / spans
+    pk = measured_peaks()
+    peak = mul64_peak_per_s(pk["sm_max_mhz"]) / 1e12
+    achieved = products / sec / 1e12
+    return {"kernel": "k_ks_mac_ext", "bound": "alu", "achieved": achieved, "peak": peak,
+            "unit": "T mul64/s", "frac": achieved / peak, "traffic": None,
+            "launch_us": sec * 1e6, "products_per_launch": products,
+            "peak_note": "152 SMs x 64 IMAD/clk / 4 per 64x64-bit product x max SM clock of "
+                         f"MEASURED_PEAKS ({pk['src']})"}
+
+
+def layer_algorithmic_bytes(B, O_c, n_rot):
+    """Bytes a layer must move at least: its Galois keys once per batch, the input ciphertexts
+    and the output ciphertexts (plaintexts are derived from the integer weights)."""
+    N, L, LK, dnum = 1 << LOG_N, N_Q, N_Q + N_P, -(-N_Q // ALPHA)
+    ct = 2 * L * N * 8
+    keys = n_rot * dnum * 2 * LK * N * 8
+    return keys + B * ct + B * O_c * ct
 
 
 def main():

@@ -104,6 +104,19 @@ void he_op_counts(const he_ctx* ctx, uint64_t out[4]);
 void he_reset_op_counts(he_ctx* ctx);
 /* Number of CUDA kernels this context has launched since creation (a diagnostic). */
 uint64_t he_launch_count(const he_ctx* ctx);
+/* Phase timing (a diagnostic).  While enabled, he_ffconv_layer(_batch) brackets each phase
+ * with CUDA events on the context stream: HE_PHASE_ENCODE (plaintexts from the weights),
+ * HE_PHASE_MODUP (hoisting: inverse NTT of c1, ModUp, NTT of the digits), HE_PHASE_TAPS
+ * (key switches and tap products: the fused extended-basis kernel, or the per-tap rotations
+ * and MACs), HE_PHASE_MODDOWN (ModDown of the channel sums), HE_PHASE_ROTATE (DP_DOT
+ * rotate-and-sum and channel folds), HE_PHASE_RESTORE (W2 ConvPack and modulus switch).
+ * he_phase_times synchronises the stream, writes the summed milliseconds of each phase to
+ * ms_out[0..HE_N_PHASES) and the number of timed spans to calls_out (either may be NULL), and
+ * clears the sums.  Enabling adds two event records per phase per call. */
+enum { HE_PHASE_ENCODE = 0, HE_PHASE_MODUP = 1, HE_PHASE_TAPS = 2, HE_PHASE_MODDOWN = 3,
+       HE_PHASE_ROTATE = 4, HE_PHASE_RESTORE = 5, HE_N_PHASES = 8 };
+int he_set_phase_timing(he_ctx* ctx, int enable);
+int he_phase_times(he_ctx* ctx, double* ms_out, uint64_t* calls_out);
 /* The 20 cumulative thresholds of the error sampler (sigma = 3.2, |e| <= 19), as
  * computed by the library: T[m] = floor(2^63 Pr(|e| <= m)), T[19] = 2^63. */
 void he_gaussian_table(uint64_t out[20]);

@@ -309,6 +309,11 @@ static void free_ctx(he_ctx* c) {
     if (c->staging.host) cudaFreeHost(c->staging.host);
     for (auto e : c->staging.ev)
         if (e) cudaEventDestroy(e);
+    for (auto& sp : c->spans) {
+        cudaEventDestroy(sp.a);
+        cudaEventDestroy(sp.b);
+    }
+    for (auto e : c->event_pool) cudaEventDestroy(e);
     delete c;
 }
 
@@ -473,6 +478,57 @@ extern "C" void he_reset_op_counts(he_ctx* ctx) {
 extern "C" void he_gaussian_table(uint64_t out[20]) { he_cdt_compute(out); }
 
 extern "C" uint64_t he_launch_count(const he_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+void phase_begin(he_ctx* ctx, int phase) {
+    if (!ctx->timing) return;
+    he_ctx::PhaseSpan sp{phase, nullptr, nullptr};
+    for (cudaEvent_t* e : {&sp.a, &sp.b}) {
+        if (!ctx->event_pool.empty()) {
+            *e = ctx->event_pool.back();
+            ctx->event_pool.pop_back();
+        } else if (cudaEventCreate(e) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+    }
+    cudaEventRecord(sp.a, ctx->stream);
+    ctx->spans.push_back(sp);
+}
+
+void phase_end(he_ctx* ctx) {
+    if (!ctx->timing || ctx->spans.empty()) return;
+    cudaEventRecord(ctx->spans.back().b, ctx->stream);
+}
+
+extern "C" int he_set_phase_timing(he_ctx* ctx, int enable) {
+    if (!ctx) return HE_EINVAL;
+    ctx->timing = enable != 0;
+    return HE_OK;
+}
+
+extern "C" int he_phase_times(he_ctx* ctx, double* ms_out, uint64_t* calls_out) {
+    if (!ctx) return HE_EINVAL;
+    HE_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (auto& sp : ctx->spans) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, sp.a, sp.b) == cudaSuccess && sp.phase >= 0 &&
+            sp.phase < HE_N_PHASES) {
+            ctx->phase_ms[sp.phase] += ms;
+            ctx->phase_calls[sp.phase] += 1;
+        }
+        cudaGetLastError();
+        ctx->event_pool.push_back(sp.a);
+        ctx->event_pool.push_back(sp.b);
+    }
+    ctx->spans.clear();
+    for (int i = 0; i < HE_N_PHASES; ++i) {
+        if (ms_out) ms_out[i] = ctx->phase_ms[i];
+        if (calls_out) calls_out[i] = ctx->phase_calls[i];
+        ctx->phase_ms[i] = 0;
+        ctx->phase_calls[i] = 0;
+    }
+    return HE_OK;
+}
 
 // ------------------------------------------------------------------ validation helpers
 

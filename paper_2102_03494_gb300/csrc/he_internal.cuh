@@ -135,6 +135,16 @@ struct he_ctx {
     Staging staging;
     uint64_t ops[4] = {0, 0, 0, 0};     // MulPC, AddCC, Rot, KeySwitch
     uint64_t launches = 0;              // kernels launched by this context
+    // optional per-phase timing (CUDA events on the context stream, summed on request)
+    bool timing = false;
+    struct PhaseSpan {
+        int phase;
+        cudaEvent_t a, b;
+    };
+    std::vector<PhaseSpan> spans;
+    std::vector<cudaEvent_t> event_pool;
+    double phase_ms[HE_N_PHASES] = {};
+    uint64_t phase_calls[HE_N_PHASES] = {};
     std::string err;
 };
 
@@ -154,6 +164,10 @@ void arena_reset(he_ctx* ctx);
 int arena_reserve(he_ctx* ctx, size_t n_u64);
 
 uint32_t galois_elt(const he_ctx* ctx, int32_t step);
+// Phase timing: phase_begin/phase_end bracket work of one phase (HE_PHASE_*) with events on
+// the context stream when timing is enabled; no-ops otherwise.
+void phase_begin(he_ctx* ctx, int phase);
+void phase_end(he_ctx* ctx);
 const void* upload_small(he_ctx* ctx, const void* src, size_t bytes);
 int check_ct(he_ctx* ctx, const he_ct* ct, int need_limbs, int need_domain, const char* what);
 // Slot values (items x N int64, device) -> plaintexts [items][rows][N]: centred lift modulo

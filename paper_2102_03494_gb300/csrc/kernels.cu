@@ -744,11 +744,14 @@ void launch_ks_combine(he_ctx* c, const uint64_t* u, size_t u_stride, const uint
         c->d_md_pinv);
 }
 
-void launch_ks_mac_ext(he_ctx* c, const uint64_t* D, const uint64_t* X, uint64_t* XP,
-                       const uint64_t* pts, const TapTable& tt, uint64_t* A, int B) {
+void launch_scale_p(he_ctx* c, const uint64_t* X, uint64_t* XP, int B) {
     ++c->launches;
     k_scale_p<<<grid_nx(B, c->N, 2 * c->L), 256, 0, c->stream>>>(X, XP, c->L, c->logN, c->d_mod,
                                                                  c->d_pmodq);
+}
+
+void launch_ks_mac_ext(he_ctx* c, const uint64_t* D, const uint64_t* XP, const uint64_t* pts,
+                       const TapTable& tt, uint64_t* A, int B) {
     const dim3 grid((B + 1) / 2, (c->N + 255) / 256, c->L + c->K);
     for (int c_lo = 0; c_lo < tt.r; c_lo += 2) {
         ++c->launches;

@@ -15,9 +15,11 @@ struct TapTable {
     int r;
 };
 
-// XP ([B][2][L][N] scratch) receives P times the inputs; dnum <= 8.
-void launch_ks_mac_ext(he_ctx* c, const uint64_t* D, const uint64_t* X, uint64_t* XP,
-                       const uint64_t* pts, const TapTable& tt, uint64_t* A, int B);
+// XP ([B][2][L][N]) <- P times the inputs X, per ciphertext limb.
+void launch_scale_p(he_ctx* c, const uint64_t* X, uint64_t* XP, int B);
+// Extended-basis tap MAC over B images (dnum <= 8); XP from launch_scale_p.
+void launch_ks_mac_ext(he_ctx* c, const uint64_t* D, const uint64_t* XP, const uint64_t* pts,
+                       const TapTable& tt, uint64_t* A, int B);
 
 void launch_automorph(he_ctx* c, const uint64_t* in, size_t in_stride, uint64_t* out,
                       size_t out_stride, int items, int rows, uint32_t g);

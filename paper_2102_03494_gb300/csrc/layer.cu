@@ -264,6 +264,7 @@ extern "C" int he_ffconv_layer_batch(he_ctx* ctx, const he_ct* ct_in, int B,
         HE_CHECK_CUDA(ctx, cudaMemcpyAsync(X + b * ct, ct_in[b].data, ct * 8, cudaMemcpyDeviceToDevice,
                                            ctx->stream));
     // (a1) plaintexts: slot vectors from the integer weights, encoded in Montgomery form
+    phase_begin(ctx, HE_PHASE_ENCODE);
     const size_t w1n = (size_t)r * y.I_c * y.d * y.d;
     const int32_t* d_w1 = (const int32_t*)upload_small(ctx, lowrank_w, w1n * 4);
     if (!d_w1) return he_fail(ctx, HE_EINVAL, "he_ffconv_layer: W1 too large for staging");
@@ -277,6 +278,7 @@ extern "C" int he_ffconv_layer_batch(he_ctx* ctx, const he_ct* ct_in, int B,
                                                                  y.stride, y.pad, r, li.O_h, li.O_w,
                                                                  li.B_c, ctx->logN, slots);
     encode_device(ctx, slots, n_pt, tmp, pts, 1, pt_rows);
+    phase_end(ctx);
 
     if (dot) {
         // prod[b][c'][o] = X[b] * filter(c', o)
@@ -293,16 +295,21 @@ extern "C" int he_ffconv_layer_batch(he_ctx* ctx, const he_ct* ct_in, int B,
         auto pp = upload_ptrs(ctx, ps);
         auto op = upload_out_ptrs(ctx, os);
         if (!xp || !pp || !op) return he_fail(ctx, HE_ECUDA, "pointer table upload failed");
+        phase_begin(ctx, HE_PHASE_TAPS);
         launch_mac(ctx, xp, pp, 1, nullptr, op, n_prod, L);
+        phase_end(ctx);
         ctx->ops[0] += n_prod;
         // rotate-and-sum: PR2 = PR + rot(PR, step), then swap
+        phase_begin(ctx, HE_PHASE_ROTATE);
         for (size_t si = 0; si < steps.size(); ++si) {
             std::vector<uint64_t*> outs(n_prod);
             for (int it = 0; it < n_prod; ++it) outs[it] = PR2 + (size_t)it * ct;
             if ((rc = rotate_contig(ctx, PR, n_prod, gs[si], PR, outs, rb, chunk))) return rc;
             std::swap(PR, PR2);
         }
+        phase_end(ctx);
         // DP -> CP: ct_w1[b][c'] = sum_o prod[b][c'][o] * mask_o
+        phase_begin(ctx, HE_PHASE_TAPS);
         const int tmax = max_mac_terms(ctx);
         for (int o0 = 0; o0 < li.S; o0 += tmax) {
             int T = std::min(tmax, li.S - o0);
@@ -323,12 +330,16 @@ extern "C" int he_ffconv_layer_batch(he_ctx* ctx, const he_ct* ct_in, int B,
             if (!a1 || !a2 || !a4 || (o0 && !a3)) return he_fail(ctx, HE_ECUDA, "pointer table upload failed");
             launch_mac(ctx, a1, a2, T, a3, a4, B * r, L);
         }
+        phase_end(ctx);
         ctx->ops[0] += (uint64_t)B * r * li.S;
         ctx->ops[1] += (uint64_t)B * r * (li.S - 1);
     } else if (ext) {
         // one ModUp of every input's c1, then every tap's key switch and plaintext product
         // summed in Q u P, then one ModDown per (image, channel)
+        phase_begin(ctx, HE_PHASE_MODUP);
         modup_items(ctx, X, B, 1u, rb);
+        launch_scale_p(ctx, X, XP, B);
+        phase_end(ctx);
         TapTable tt{};
         tt.n = li.taps;
         tt.r = r;
@@ -343,8 +354,11 @@ extern "C" int he_ffconv_layer_batch(he_ctx* ctx, const he_ct* ct_in, int B,
                 if ((rc = he_get_key(ctx, tt.g[tap], &tt.key[tap]))) return rc;
                 ++nrot;
             }
-        launch_ks_mac_ext(ctx, rb.D, X, XP, pts, tt, AX, B);
+        phase_begin(ctx, HE_PHASE_TAPS);
+        launch_ks_mac_ext(ctx, rb.D, XP, pts, tt, AX, B);
+        phase_end(ctx);
         const int items = B * r;
+        phase_begin(ctx, HE_PHASE_MODDOWN);
         const size_t ext_ct = 2 * (size_t)LK * N;
         ntt_inverse(ctx, AX + (size_t)L * N, items * 2, (size_t)LK * N, ctx->K, L);
         launch_moddown_conv(ctx, AX, ext_ct, rb.v, ct, items);
@@ -354,11 +368,14 @@ extern "C" int he_ffconv_layer_batch(he_ctx* ctx, const he_ct* ct_in, int B,
         auto op = upload_out_ptrs(ctx, ao);
         if (!op) return he_fail(ctx, HE_ECUDA, "pointer table upload failed");
         launch_ks_combine(ctx, AX, ext_ct, rb.v, ct, nullptr, nullptr, op, items, 1u);
+        phase_end(ctx);
         ctx->ops[0] += (uint64_t)B * r * li.taps;
         ctx->ops[1] += (uint64_t)B * r * (li.taps - 1);
         ctx->ops[2] += (uint64_t)B * nrot;
         ctx->ops[3] += (uint64_t)B * nrot;
+        phase_begin(ctx, HE_PHASE_ROTATE);
         if ((rc = fold_channels(ctx, A, A2, B * r, li, rb, rot_items))) return rc;
+        phase_end(ctx);
     } else {
         // hoisted rotations of every input by every non-zero tap offset
         std::vector<uint32_t> hg;
@@ -377,6 +394,7 @@ extern "C" int he_ffconv_layer_batch(he_ctx* ctx, const he_ct* ct_in, int B,
                 hg.push_back(galois_elt(ctx, dl));
                 for (int b = 0; b < B; ++b) outs.push_back(PR + ((size_t)b * li.taps + tap) * ct);
             }
+        phase_begin(ctx, HE_PHASE_TAPS);
         for (int b0 = 0; b0 < B; b0 += rot_items) {
             int nb = std::min(rot_items, B - b0);
             std::vector<uint64_t*> o2;
@@ -401,9 +419,12 @@ extern "C" int he_ffconv_layer_batch(he_ctx* ctx, const he_ct* ct_in, int B,
         auto a4 = upload_out_ptrs(ctx, ao);
         if (!a1 || !a2 || !a4) return he_fail(ctx, HE_ECUDA, "pointer table upload failed");
         launch_mac(ctx, a1, a2, li.taps, nullptr, a4, B * r, L);
+        phase_end(ctx);
         ctx->ops[0] += (uint64_t)B * r * li.taps;
         ctx->ops[1] += (uint64_t)B * r * (li.taps - 1);
+        phase_begin(ctx, HE_PHASE_ROTATE);
         if ((rc = fold_channels(ctx, A, A2, B * r, li, rb, rot_items))) return rc;
+        phase_end(ctx);
     }
 
     // W2 under ConvPack: ct_out[b][c] = sum_c' W2[c][c'] ct_w1[b][c'] (scalar plaintexts)
@@ -425,6 +446,7 @@ extern "C" int he_ffconv_layer_batch(he_ctx* ctx, const he_ct* ct_in, int B,
     }
     auto dp = upload_out_ptrs(ctx, dst);
     if (!dp) return he_fail(ctx, HE_ECUDA, "pointer table upload failed");
+    phase_begin(ctx, HE_PHASE_RESTORE);
     launch_convpack(ctx, A, B, r, O_c, d_wm, dp, L);
     ctx->ops[0] += (uint64_t)B * O_c * r;
     ctx->ops[1] += (uint64_t)B * O_c * (r - 1);
@@ -438,6 +460,7 @@ extern "C" int he_ffconv_layer_batch(he_ctx* ctx, const he_ct* ct_in, int B,
         }
         if ((rc = rescale_items(ctx, xs, os, L, last, sprd))) return rc;
     }
+    phase_end(ctx);
     return HE_OK;
 }
 

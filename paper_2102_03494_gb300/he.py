@@ -55,6 +55,8 @@ _SIGS = {
     "he_op_counts": ([_P, _U64P], None),
     "he_reset_op_counts": ([_P], None),
     "he_launch_count": ([_P], ctypes.c_uint64),
+    "he_set_phase_timing": ([_P, ctypes.c_int], ctypes.c_int),
+    "he_phase_times": ([_P, ctypes.POINTER(ctypes.c_double), _U64P], ctypes.c_int),
     "he_gaussian_table": ([_U64P], None),
     "he_keygen_secret": ([_P, ctypes.c_uint64, _I64P], ctypes.c_int),
     "he_keygen_galois": ([_P, _I64P, ctypes.c_uint64, _I32P, ctypes.c_int], ctypes.c_int),
@@ -193,6 +195,18 @@ class Context:
 
     def he_launch_count(self):
         return int(lib().he_launch_count(self.h))
+
+    PHASES = ("encode", "modup", "taps", "moddown", "rotate", "restore")
+
+    def he_set_phase_timing(self, enable):
+        self._ck(lib().he_set_phase_timing(self.h, int(enable)), "he_set_phase_timing")
+
+    def he_phase_times(self):
+        """{phase: (milliseconds, spans)} summed since the last call (synchronises the stream)."""
+        ms = (ctypes.c_double * 8)()
+        calls = np.zeros(8, dtype=np.uint64)
+        self._ck(lib().he_phase_times(self.h, ms, calls.ctypes.data_as(_U64P)), "he_phase_times")
+        return {name: (ms[i], int(calls[i])) for i, name in enumerate(self.PHASES)}
 
     def he_reset_op_counts(self):
         lib().he_reset_op_counts(self.h)
