@@ -266,6 +266,12 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "src": "fallback"}
 
 
+# DRAM bytes (read + write) of one k_ks_mac_ext launch, from one ncu capture of the current
+# kernel version at the bench shape (profiles/k_ks_mac_ext_n15.md); cleared when the kernel
+# changes and until it is captured again.
+KS_MAC_EXT_TRAFFIC = {16: 1310630400 + 241354752}
+
+
 # 64 x 64 -> 128-bit products per second of the GPU's integer multiplier: 152 SMs x 64 32-bit
 # multiply-adds per clock x clock / 4 (a 64 x 64-bit product takes four 32 x 32-bit ones).
 def mul64_peak_per_s(sm_mhz):
@@ -287,7 +293,8 @@ def taps_roofline(phases, args, B, n_rot):
     peak = mul64_peak_per_s(pk["sm_max_mhz"]) / 1e12
     achieved = products / sec / 1e12
     return {"kernel": "k_ks_mac_ext", "bound": "alu", "achieved": achieved, "peak": peak,
-            "unit": "T mul64/s", "frac": achieved / peak, "traffic": None,
+            "unit": "T mul64/s", "frac": achieved / peak,
+            "traffic": KS_MAC_EXT_TRAFFIC.get(B) if args.pack == "dp_shift_ext" else None,
             "launch_us": sec * 1e6, "products_per_launch": products,
             "peak_note": "152 SMs x 64 IMAD/clk / 4 per 64x64-bit product x max SM clock of "
                          f"MEASURED_PEAKS ({pk['src']})"}
