@@ -221,6 +221,18 @@ int he_fail(he_ctx* ctx, int code, const std::string& msg) {
     return code;
 }
 
+int check_device_error(he_ctx* ctx) {
+    int word = 0;
+    HE_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    HE_CHECK_CUDA(ctx, cudaMemcpy(&word, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (word) {
+        cudaMemset(ctx->d_err, 0, sizeof(int));
+        return he_fail(ctx, HE_ETIMEOUT, "a bounded device wait ran out: results since the last "
+                                         "check are unusable");
+    }
+    return HE_OK;
+}
+
 int he_launch_check(he_ctx* ctx, const char* what) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
@@ -301,7 +313,7 @@ static void free_ctx(he_ctx* c) {
     if (c->stream || true) cudaStreamSynchronize(c->stream);
     void* ptrs[] = {c->d_mod, c->d_tw_fwd, c->d_tw_inv, c->d_slot_pos, c->d_cdt,
                     c->d_modup_inv, c->d_modup_c, c->d_md_inv, c->d_md_c, c->d_md_pinv,
-                    c->d_rs_inv, c->d_pmodq, c->arena.base, c->staging.dev};
+                    c->d_rs_inv, c->d_pmodq, c->arena.base, c->staging.dev, c->d_err};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& kv : c->keys)
@@ -438,6 +450,12 @@ extern "C" int he_ctx_create(const he_params* p, void* stream, he_ctx** out) {
         free_ctx(c);
         return rc;
     }
+    if (cudaMalloc((void**)&c->d_err, sizeof(int)) != cudaSuccess ||
+        cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        free_ctx(c);
+        return HE_ENOMEM;
+    }
     Staging& st = c->staging;
     if (cudaMallocHost((void**)&st.host, st.slot_bytes * st.n_slots) != cudaSuccess ||
         cudaMalloc((void**)&st.dev, st.slot_bytes * st.n_slots) != cudaSuccess) {
@@ -508,7 +526,8 @@ extern "C" int he_set_phase_timing(he_ctx* ctx, int enable) {
 
 extern "C" int he_phase_times(he_ctx* ctx, double* ms_out, uint64_t* calls_out) {
     if (!ctx) return HE_EINVAL;
-    HE_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    int rc = check_device_error(ctx);
+    if (rc) return rc;
     for (auto& sp : ctx->spans) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, sp.a, sp.b) == cudaSuccess && sp.phase >= 0 &&
@@ -719,6 +738,7 @@ extern "C" int he_decrypt(he_ctx* ctx, const int64_t* sk, const he_ct* ct, int64
     ntt_forward(ctx, m, 1, 0, 1, ctx->L + ctx->K);
     launch_ntt_to_slots(ctx, m, d_out, 1);
     if ((rc = he_launch_check(ctx, "he_decrypt"))) return rc;
+    if ((rc = check_device_error(ctx))) return rc;
     HE_CHECK_CUDA(ctx, cudaMemcpyAsync(slots_out, d_out, N * 8, cudaMemcpyDeviceToHost, ctx->stream));
     HE_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return HE_OK;

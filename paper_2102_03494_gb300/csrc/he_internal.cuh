@@ -63,17 +63,35 @@ struct U128 {
     uint64_t lo, hi;
 };
 
+// acc += a * b (128-bit accumulator, 64 x 64-bit product): the four 32 x 32-bit partial
+// products are added in one carry chain of 32-bit multiply-adds (ten instructions).
 __device__ __forceinline__ void mac128(U128& acc, uint64_t a, uint64_t b) {
-    uint64_t lo = a * b;
-    uint64_t hi = __umul64hi(a, b);
-    acc.lo += lo;
-    acc.hi += hi + (acc.lo < lo ? 1u : 0u);
+    uint32_t c0 = (uint32_t)acc.lo, c1 = (uint32_t)(acc.lo >> 32);
+    uint32_t c2 = (uint32_t)acc.hi, c3 = (uint32_t)(acc.hi >> 32);
+    const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32);
+    const uint32_t b0 = (uint32_t)b, b1 = (uint32_t)(b >> 32);
+    asm("mad.lo.cc.u32 %0, %4, %6, %0;\n\t"
+        "madc.hi.cc.u32 %1, %4, %6, %1;\n\t"
+        "madc.lo.cc.u32 %2, %5, %7, %2;\n\t"
+        "madc.hi.u32 %3, %5, %7, %3;\n\t"
+        "mad.lo.cc.u32 %1, %4, %7, %1;\n\t"
+        "madc.hi.cc.u32 %2, %4, %7, %2;\n\t"
+        "addc.u32 %3, %3, 0;\n\t"
+        "mad.lo.cc.u32 %1, %5, %6, %1;\n\t"
+        "madc.hi.cc.u32 %2, %5, %6, %2;\n\t"
+        "addc.u32 %3, %3, 0;"
+        : "+r"(c0), "+r"(c1), "+r"(c2), "+r"(c3)
+        : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
+    acc.lo = ((uint64_t)c1 << 32) | c0;
+    acc.hi = ((uint64_t)c3 << 32) | c2;
 }
 
-// REDC: x 2^-64 mod q for x < q 2^64, result in [0, q).
+// REDC: x 2^-64 mod q for x < q 2^64, result in [0, q).  With m = x q' mod 2^64 the sum
+// x + m q is divisible by 2^64 and its top half is x 2^-64 mod q, in [0, 2q).
 __device__ __forceinline__ uint64_t redc(U128 x, uint64_t q, uint64_t qinv_neg) {
-    uint64_t m = x.lo * qinv_neg;
-    uint64_t t = x.hi + __umul64hi(m, q) + (x.lo != 0 ? 1u : 0u);
+    const uint64_t m = x.lo * qinv_neg;
+    mac128(x, m, q);
+    const uint64_t t = x.hi;
     return t >= q ? t - q : t;
 }
 
@@ -129,6 +147,7 @@ struct he_ctx {
     ShoupPair* d_md_pinv = nullptr;     // [L]
     ShoupPair* d_rs_inv = nullptr;      // [L][L]: row lv = q_lv^-1 mod q_i (rescale at level lv+1)
     uint64_t* d_pmodq = nullptr;        // [L] P mod q_i (Montgomery form) for key generation
+    int* d_err = nullptr;               // device error word: bit 0 = a bounded wait ran out
 
     std::map<uint32_t, GaloisKey> keys; // by Galois element
     Arena arena;
@@ -157,6 +176,8 @@ struct he_ctx {
     } while (0)
 
 int he_fail(he_ctx* ctx, int code, const std::string& msg);
+// Synchronise the stream and report HE_ETIMEOUT if a kernel's bounded wait ran out.
+int check_device_error(he_ctx* ctx);
 int he_launch_check(he_ctx* ctx, const char* what);
 
 uint64_t* arena_take(he_ctx* ctx, size_t n_u64);

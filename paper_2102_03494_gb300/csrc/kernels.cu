@@ -182,8 +182,9 @@ __global__ void k_ks_combine(const uint64_t* __restrict__ u, size_t u_stride,
 
 // REDC for x < 2q 2^64 (a sum of products plus one residue times 2^64): result in [0, q).
 __device__ __forceinline__ uint64_t redc_wide(U128 x, uint64_t q, uint64_t qinv_neg) {
-    uint64_t m = x.lo * qinv_neg;
-    uint64_t t = x.hi + __umul64hi(m, q) + (x.lo != 0 ? 1u : 0u);   // < 3q
+    const uint64_t m = x.lo * qinv_neg;
+    mac128(x, m, q);
+    uint64_t t = x.hi;   // < 3q
     t = t >= q ? t - q : t;
     return t >= q ? t - q : t;
 }
@@ -752,6 +753,10 @@ void launch_scale_p(he_ctx* c, const uint64_t* X, uint64_t* XP, int B) {
 
 void launch_ks_mac_ext(he_ctx* c, const uint64_t* D, const uint64_t* XP, const uint64_t* pts,
                        const TapTable& tt, uint64_t* A, int B) {
+    if (tapmac_bulk_supported(c)) {   // operands staged by bulk copies (tapmac.cu)
+        launch_ks_mac_ext_bulk(c, D, XP, pts, tt, A, B);
+        return;
+    }
     const dim3 grid((B + 1) / 2, (c->N + 255) / 256, c->L + c->K);
     for (int c_lo = 0; c_lo < tt.r; c_lo += 2) {
         ++c->launches;

@@ -17,9 +17,13 @@ struct TapTable {
 
 // XP ([B][2][L][N]) <- P times the inputs X, per ciphertext limb.
 void launch_scale_p(he_ctx* c, const uint64_t* X, uint64_t* XP, int B);
-// Extended-basis tap MAC over B images (dnum <= 8); XP from launch_scale_p.
+// Extended-basis tap MAC over B images (dnum <= 8); XP from launch_scale_p.  Uses the
+// bulk-copy pipelined kernel (tapmac.cu) when N >= 256, else the register-only kernel.
 void launch_ks_mac_ext(he_ctx* c, const uint64_t* D, const uint64_t* XP, const uint64_t* pts,
                        const TapTable& tt, uint64_t* A, int B);
+bool tapmac_bulk_supported(const he_ctx* c);
+void launch_ks_mac_ext_bulk(he_ctx* c, const uint64_t* D, const uint64_t* XP, const uint64_t* pts,
+                            const TapTable& tt, uint64_t* A, int B);
 
 void launch_automorph(he_ctx* c, const uint64_t* in, size_t in_stride, uint64_t* out,
                       size_t out_stride, int items, int rows, uint32_t g);

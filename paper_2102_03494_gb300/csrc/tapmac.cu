@@ -1,0 +1,311 @@
+// tapmac.cu -- the extended-basis tap MAC with its operands staged by bulk asynchronous copies.
+//
+// Same arithmetic as k_ks_mac_ext (kernels.cu): for coefficient n of limb l of image b,
+//   acc_k[c'] = sum_tap pt[c'][tap] * x_k(tap)   over Q u P,
+//   x_0(tap) = sum_j D_j[perm_g(n)] key_j,0 + (P c0)[perm_g(n)],  x_1(tap) = sum_j D_j[perm_g(n)] key_j,1.
+// A CTA owns an aligned tile of 256 coefficients of one limb for two images.  For every tap the
+// operands the tile needs are contiguous 2 KiB rows: the 2 dnum key rows and the channel
+// plaintext rows at the tile, and -- because the NTT-domain automorphism maps every aligned
+// block of 2^k positions onto an aligned block of 2^k positions (the bits of p above bit k only
+// feed the bits of perm(p) above bit k) -- the ModUp digit rows and the P c0 row of the one
+// aligned 256-block that holds perm_g of the tile.  Warp 0 copies them with cp.async.bulk into
+// one of two shared-memory stages, completed on an mbarrier, while all warps compute on the
+// other stage.  Every wait is bounded: on expiry the kernel sets a bit in the context's device
+// error word, waits (again bounded) for its own copies and returns.
+#include "he_internal.cuh"
+#include "kernels.cuh"
+
+namespace {
+
+constexpr int kTile = 256;
+constexpr uint32_t kWaitSpins = 1u << 20;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kWaitSpins; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void bulk_copy(void* dst_smem, const void* src_gmem, uint32_t bytes,
+                                          uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst_smem)),
+        "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t brv_bits(uint32_t x, int bits) {
+    return bits ? (__brev(x) >> (32 - bits)) : 0u;
+}
+
+__device__ __forceinline__ uint32_t perm_of(uint32_t p, uint32_t g, int logN) {
+    uint32_t e = (2u * brv_bits(p, logN) + 1u) * g & ((2u << logN) - 1u);
+    return brv_bits((e - 1u) >> 1, logN);
+}
+
+__device__ __forceinline__ uint64_t redc_w(U128 x, uint64_t q, uint64_t qinv_neg) {
+    const uint64_t m = x.lo * qinv_neg;   // x < 2q 2^64: (x + m q) / 2^64 < 3q
+    mac128(x, m, q);
+    uint64_t t = x.hi;
+    t = t >= q ? t - q : t;
+    return t >= q ? t - q : t;
+}
+
+// Shared-memory stage (uint64 words): keys [DNUM][2][T] | pts [2][T] | digits [2 img][DNUM][T]
+// | P x [2 img][2 poly][T].
+template <int DNUM>
+struct Stage {
+    static constexpr int KEYS = 0;
+    static constexpr int PTS = DNUM * 2 * kTile;
+    static constexpr int DIG = PTS + 2 * kTile;
+    static constexpr int XP = DIG + 2 * DNUM * kTile;
+    static constexpr int WORDS = XP + 4 * kTile;
+};
+
+// Warp 0 stages tap t into stage buffer `st`, completing on `bar`.
+template <int DNUM>
+__device__ __forceinline__ void issue_tap(uint64_t* st, uint64_t* bar, int t, const TapTable& tt,
+                                         const uint64_t* __restrict__ D,
+                                         const uint64_t* __restrict__ XPg,
+                                         const uint64_t* __restrict__ pts, int c_lo, int c_cnt,
+                                         int b0, int nb, int l, int L, int n0, size_t LN, int N,
+                                         int logN) {
+    using S = Stage<DNUM>;
+    const int lane = threadIdx.x & 31;
+    const uint64_t* key = tt.key[t];
+    const bool qlimb = l < L;
+    const uint32_t row = kTile * 8;
+    const int src0 = key ? (int)(perm_of((uint32_t)n0, tt.g[t], logN) & ~(uint32_t)(kTile - 1)) : n0;
+    // copy list: index -> (dst, src)
+    const int nkeys = key ? 2 * DNUM : 0;
+    const int npts = c_cnt;
+    const int ndig = key ? nb * DNUM : 0;
+    const int nxp = qlimb ? (key ? nb : 2 * nb) : 0;
+    const int total = nkeys + npts + ndig + nxp;
+    if (lane == 0) mbar_expect_tx(bar, (uint32_t)total * row);
+    __syncwarp();
+    for (int i = lane; i < total; i += 32) {
+        uint64_t* dst;
+        const uint64_t* src;
+        if (i < nkeys) {
+            dst = st + S::KEYS + i * kTile;                          // i = 2 j + k
+            src = key + (size_t)i * LN + (size_t)l * N + n0;
+        } else if (i < nkeys + npts) {
+            const int c = i - nkeys;
+            dst = st + S::PTS + c * kTile;
+            src = pts + ((size_t)(c_lo + c) * tt.n + t) * LN + (size_t)l * N + n0;
+        } else if (i < nkeys + npts + ndig) {
+            const int q = i - nkeys - npts, ib = q / DNUM, j = q - ib * DNUM;
+            dst = st + S::DIG + (ib * DNUM + j) * kTile;
+            src = D + ((size_t)(b0 + ib) * DNUM + j) * LN + (size_t)l * N + src0;
+        } else {
+            const int q = i - nkeys - npts - ndig;
+            const int ib = key ? q : q >> 1, k = key ? 0 : (q & 1);
+            dst = st + S::XP + (ib * 2 + k) * kTile;
+            src = XPg + ((size_t)(b0 + ib) * 2 + k) * L * N + (size_t)l * N + src0;
+        }
+        bulk_copy(dst, src, row, bar);
+    }
+}
+
+template <int DNUM>
+__global__ void __launch_bounds__(256)
+k_ks_mac_ext_bulk(const uint64_t* __restrict__ D, const uint64_t* __restrict__ XPg,
+                  const uint64_t* __restrict__ pts, TapTable tt, int c_lo, int c_cnt, int B,
+                  uint64_t* __restrict__ A, int L, int K, int logN,
+                  const ModConst* __restrict__ mods, int* __restrict__ err) {
+    using S = Stage<DNUM>;
+    extern __shared__ __align__(128) uint64_t smem[];
+    __shared__ __align__(8) uint64_t bars[2];    // stage filled (1 arrival + copied bytes)
+    const int N = 1 << logN;
+    const int tid = threadIdx.x;
+    const int n0 = blockIdx.y * kTile;
+    const int n = n0 + tid;
+    const int l = blockIdx.z;
+    const int b0 = blockIdx.x * 2;
+    const int nb = B - b0 < 2 ? B - b0 : 2;
+    const int LK = L + K;
+    const ModConst M = mods[l];
+    const uint64_t q = M.q, qi = M.qinv_neg;
+    const bool qlimb = l < L;
+    const size_t LN = (size_t)LK * N;
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid < 32) {
+        issue_tap<DNUM>(smem, &bars[0], 0, tt, D, XPg, pts, c_lo, c_cnt, b0, nb, l, L, n0, LN, N, logN);
+        if (tt.n > 1)
+            issue_tap<DNUM>(smem + S::WORDS, &bars[1], 1, tt, D, XPg, pts, c_lo, c_cnt, b0, nb, l, L,
+                            n0, LN, N, logN);
+    }
+    U128 a128[2][2][2];
+    uint64_t acc[2][2][2];
+#pragma unroll
+    for (int ib = 0; ib < 2; ++ib)
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                a128[ib][c][k] = U128{0, 0};
+                acc[ib][c][k] = 0;
+            }
+    uint32_t parity[2] = {0u, 0u};
+    int pending = 0;
+    bool ok = true;
+    for (int t = 0; t < tt.n; ++t) {
+        const int s = t & 1;
+        uint64_t* st = smem + s * S::WORDS;
+        // a wait that runs out does not leave the loop (the other warps would then wait at
+        // the barrier below): the thread goes on with whatever the stage holds and the
+        // error bit makes the result unusable
+        ok &= mbar_wait(&bars[s], parity[s]);
+        parity[s] ^= 1u;
+        const uint64_t p0 = st[S::PTS + tid];
+        const uint64_t p1 = c_cnt > 1 ? st[S::PTS + kTile + tid] : 0;
+        uint64_t x[2][2];
+        if (!tt.key[t]) {
+#pragma unroll
+            for (int ib = 0; ib < 2; ++ib) {
+                x[ib][0] = (qlimb && ib < nb) ? st[S::XP + (ib * 2) * kTile + tid] : 0;
+                x[ib][1] = (qlimb && ib < nb) ? st[S::XP + (ib * 2 + 1) * kTile + tid] : 0;
+            }
+        } else {
+            const int loc = (int)(perm_of((uint32_t)n, tt.g[t], logN) & (kTile - 1));
+            uint64_t kv[DNUM][2];
+#pragma unroll
+            for (int j = 0; j < DNUM; ++j) {
+                kv[j][0] = st[S::KEYS + (2 * j) * kTile + tid];
+                kv[j][1] = st[S::KEYS + (2 * j + 1) * kTile + tid];
+            }
+#pragma unroll
+            for (int ib = 0; ib < 2; ++ib) {
+                if (ib >= nb) {
+                    x[ib][0] = x[ib][1] = 0;
+                    continue;
+                }
+                U128 s0{0, 0}, s1{0, 0};
+#pragma unroll
+                for (int j = 0; j < DNUM; ++j) {
+                    const uint64_t d = st[S::DIG + (ib * DNUM + j) * kTile + loc];
+                    mac128(s0, d, kv[j][0]);
+                    mac128(s1, d, kv[j][1]);
+                }
+                if (qlimb) s0.hi += st[S::XP + (ib * 2) * kTile + loc];   // + (P c0) 2^64
+                x[ib][0] = redc_w(s0, q, qi);
+                x[ib][1] = redc(s1, q, qi);
+            }
+        }
+#pragma unroll
+        for (int ib = 0; ib < 2; ++ib)
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                mac128(a128[ib][0][k], x[ib][k], p0);
+                mac128(a128[ib][1][k], x[ib][k], p1);
+            }
+        if (++pending == 8 || t == tt.n - 1) {
+            pending = 0;
+#pragma unroll
+            for (int ib = 0; ib < 2; ++ib)
+#pragma unroll
+                for (int c = 0; c < 2; ++c)
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        acc[ib][c][k] = add_mod(acc[ib][c][k], redc(a128[ib][c][k], q, qi), q);
+                        a128[ib][c][k] = U128{0, 0};
+                    }
+        }
+        __syncthreads();   // every warp is done with stage s before it is refilled
+        if (tid < 32 && t + 2 < tt.n) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue_tap<DNUM>(st, &bars[s], t + 2, tt, D, XPg, pts, c_lo, c_cnt, b0, nb, l, L, n0, LN,
+                            N, logN);
+        }
+    }
+    if (!ok) {
+        atomicOr(err, 1);
+        // let this CTA's copies land before its shared memory is released (bounded)
+        for (int s = 0; s < 2; ++s) mbar_wait(&bars[s], parity[s]);
+        return;
+    }
+#pragma unroll
+    for (int ib = 0; ib < 2; ++ib) {
+        if (ib >= nb) break;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            if (c >= c_cnt) break;
+            uint64_t* ab = A + (((size_t)(b0 + ib) * tt.r + c_lo + c) * 2) * LN + (size_t)l * N + n;
+            ab[0] = acc[ib][c][0];
+            ab[LN] = acc[ib][c][1];
+        }
+    }
+}
+
+template <int DNUM>
+void launch_bulk(he_ctx* c, const uint64_t* D, const uint64_t* XP, const uint64_t* pts,
+                 const TapTable& tt, uint64_t* A, int B, int c_lo, int cnt) {
+    const size_t smem = 2 * (size_t)Stage<DNUM>::WORDS * 8;
+    static bool attr_set[64] = {};   // per template instance and device
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        cudaFuncSetAttribute(k_ks_mac_ext_bulk<DNUM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    const dim3 grid((B + 1) / 2, c->N / kTile, c->L + c->K);
+    k_ks_mac_ext_bulk<DNUM><<<grid, kTile, smem, c->stream>>>(D, XP, pts, tt, c_lo, cnt, B, A, c->L,
+                                                            c->K, c->logN, c->d_mod, c->d_err);
+}
+
+}  // namespace
+
+bool tapmac_bulk_supported(const he_ctx* c) { return c->N >= kTile && c->dnum <= 8; }
+
+void launch_ks_mac_ext_bulk(he_ctx* c, const uint64_t* D, const uint64_t* XP, const uint64_t* pts,
+                            const TapTable& tt, uint64_t* A, int B) {
+    for (int c_lo = 0; c_lo < tt.r; c_lo += 2) {
+        ++c->launches;
+        const int cnt = tt.r - c_lo < 2 ? tt.r - c_lo : 2;
+        switch (c->dnum) {
+            case 1: launch_bulk<1>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
+            case 2: launch_bulk<2>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
+            case 3: launch_bulk<3>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
+            case 4: launch_bulk<4>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
+            case 5: launch_bulk<5>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
+            case 6: launch_bulk<6>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
+            case 7: launch_bulk<7>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
+            default: launch_bulk<8>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
+        }
+    }
+}
