@@ -45,9 +45,29 @@ __device__ __forceinline__ uint64_t sub_mod(uint64_t a, uint64_t b, uint64_t q) 
 
 __device__ __forceinline__ uint64_t neg_mod(uint64_t a, uint64_t q) { return a ? q - a : 0; }
 
+// High 64 bits of a 64 x 64-bit product from 32-bit partial products in one carry chain (the
+// low word of a0 b0 cannot carry: it is never added to).
+__device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) {
+    const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32);
+    const uint32_t b0 = (uint32_t)b, b1 = (uint32_t)(b >> 32);
+    uint32_t c1, c2, c3;
+    asm("mul.hi.u32 %0, %3, %5;\n\t"
+        "mul.lo.u32 %1, %4, %6;\n\t"
+        "mul.hi.u32 %2, %4, %6;\n\t"
+        "mad.lo.cc.u32 %0, %3, %6, %0;\n\t"
+        "madc.hi.cc.u32 %1, %3, %6, %1;\n\t"
+        "addc.u32 %2, %2, 0;\n\t"
+        "mad.lo.cc.u32 %0, %4, %5, %0;\n\t"
+        "madc.hi.cc.u32 %1, %4, %5, %1;\n\t"
+        "addc.u32 %2, %2, 0;"
+        : "=&r"(c1), "=&r"(c2), "=&r"(c3)
+        : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
+    return ((uint64_t)c3 << 32) | c2;
+}
+
 // x * w mod q, x any 64-bit value, w < q, ws = floor(w 2^64 / q).
 __device__ __forceinline__ uint64_t mul_shoup(uint64_t x, uint64_t w, uint64_t ws, uint64_t q) {
-    uint64_t h = __umul64hi(x, ws);
+    uint64_t h = mulhi64(x, ws);
     uint64_t r = x * w - h * q;
     return r >= q ? r - q : r;
 }
@@ -55,7 +75,7 @@ __device__ __forceinline__ uint64_t mul_shoup(uint64_t x, uint64_t w, uint64_t w
 // Same, result left in [0, 2q).
 __device__ __forceinline__ uint64_t mul_shoup_lazy(uint64_t x, uint64_t w, uint64_t ws,
                                                    uint64_t q) {
-    uint64_t h = __umul64hi(x, ws);
+    uint64_t h = mulhi64(x, ws);
     return x * w - h * q;
 }
 
