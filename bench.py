@@ -39,6 +39,20 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(values, device):
+    """Element-wise maximum of `values` over all ranks (the slowest replica sets the time)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_rate(units_per_rank, world, ms_max):
+    """Units processed by all replicas per second, timed by the slowest replica."""
+    return world * units_per_rank / (ms_max / 1000.0)
+
+
 def dist_env():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
             int(os.environ.get("WORLD_SIZE", 1)))
@@ -225,11 +239,9 @@ def run(args):
     peaks = measured_peaks()
 
     if dist:
-        t = torch.tensor([ms, ms_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_e2e = (float(v) for v in t.tolist())
-    value = world * B * n_rot * args.steps / (ms / 1000.0)
-    e2e = world * B * n_rot * args.steps / (ms_e2e / 1000.0)
+        ms, ms_e2e = max_over_ranks([ms, ms_e2e], "cuda")
+    value = whole_job_rate(B * n_rot * args.steps, world, ms)
+    e2e = whole_job_rate(B * n_rot * args.steps, world, ms_e2e)
     if rank != 0:
         return
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
