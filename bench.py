@@ -234,6 +234,22 @@ def run(args):
     torch.cuda.synchronize()
     ms_e2e = e0.elapsed_time(e1)
 
+    # the plain one-request-at-a-time form: the same layer on one image per call (outputs are
+    # bit-identical to the batched call's; tests/test_gpu_layer.py checks it)
+    one = [cts[0]]
+    one_out = outs[: shape.O_c]
+    for _ in range(3):
+        ctx.he_ffconv_layer_batch(one, W1, W2, lay, one_out)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_single = max(8, min(64, args.steps))
+    torch.cuda.synchronize()
+    s0.record(stream)
+    for _ in range(n_single):
+        ctx.he_ffconv_layer_batch(one, W1, W2, lay, one_out)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    ms_single = s0.elapsed_time(s1) / n_single
+
     roof = taps_roofline(phases, args, B, n_rot)
     layer_bytes = layer_algorithmic_bytes(B, shape.O_c, n_rot)
     peaks = measured_peaks()
@@ -257,6 +273,10 @@ def run(args):
                     "d2h_bytes_per_step": B * shape.O_c * ct_bytes, "ms_per_step": ms_e2e / args.steps},
             "gpu_launches": launches, "clocks": clk, "roofline": roof,
             "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items() if v[1]},
+            "batching": {"one_at_a_time_ms_per_image": ms_single,
+                         "batched_ms_per_image": ms / args.steps / B,
+                         "factor": ms_single / (ms / args.steps / B),
+                         "note": "same layer, same outputs; one image per call vs the batch"},
             "layer_hbm": {"algorithmic_bytes_per_step": layer_bytes,
                           "achieved_gbs": layer_bytes / (ms / args.steps / 1000.0) / 1e9,
                           "peak_gbs": peaks["hbm_gbs"],

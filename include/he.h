@@ -39,7 +39,7 @@ enum {
 };
 
 enum { HE_COEFF = 0, HE_NTT = 1 };            /* representation of a ciphertext's limbs */
-enum { HE_DP_DOT = 0, HE_DP_SHIFT = 1, HE_DP_SHIFT_EXT = 2 };  /* W1 schedule, see he_ffconv_layer */
+enum { HE_DP_DOT = 0, HE_DP_SHIFT = 1, HE_DP_SHIFT_EXT = 2, HE_CP_CP = 3 };  /* W1 schedule */
 
 /* Rotation step that swaps the two rows of slots (Galois element 2N - 1). */
 #define HE_ROW_SWAP ((int32_t)0x7fffffff)
@@ -74,7 +74,8 @@ typedef struct {
 
 /* Shape of one FFConv layer (Sec. 3.1 notation): input I_c x I_h x I_w, low-rank filters
  * W1 of d x d x I_c x r (r = O'_c of Eq. 2), restoring filters W2 of 1 x 1 x r x O_c,
- * stride and zero padding of W1, pack = HE_DP_DOT, HE_DP_SHIFT or HE_DP_SHIFT_EXT, modswitch
+ * stride and zero padding of W1, pack = HE_DP_DOT, HE_DP_SHIFT, HE_DP_SHIFT_EXT or HE_CP_CP,
+ * modswitch
  * != 0 drops the
  * last ciphertext prime at the end of the layer. */
 typedef struct {
@@ -201,7 +202,13 @@ int he_rescale(he_ctx* ctx, const he_ct* in, he_ct* out);
  * slots and plaintexts but keeps the hoisted rotations in the extended basis Q u P: the tap
  * products are summed there and divided by P once per low-rank channel (different ciphertext
  * bits from HE_DP_SHIFT, identical decryptions; at most 64 filter taps).  All finish with W2
- * under ConvPack (scalar products, no rotation).  Needs the Galois keys of the schedule. */
+ * under ConvPack (scalar products, no rotation).  Needs the Galois keys of the schedule.
+ * HE_CP_CP is FFConv packing CP-HI2C-CP (Sec. 4.2 'ConvPack for W1', Fig. 5; the TinyNet
+ * layer of Table VI): the client performs the Im2Col and ct_in holds K = d*d*I_c column
+ * ciphertexts per image (image b's column k = (ci, i, j) at index b*K + k, holding the input
+ * pixel under tap (i, j) of output o at slot o = oh*O_w + ow); W1 and W2 are both ConvPack
+ * scalar products (MulPC r (K + O_c), Table II), no Galois key is needed, and output channel
+ * c holds y2[c, oh, ow] at slot oh*O_w + ow. */
 int he_ffconv_layer(he_ctx* ctx, const he_ct* ct_in, const int32_t* lowrank_w,
                     const int32_t* restore_w, const he_layout* layout, he_ct* ct_out);
 /* The same layer on B independent ciphertexts with shared weights: ct_in[B],

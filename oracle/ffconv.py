@@ -10,7 +10,7 @@ padding `pad` on every side, output size floor((I + 2 pad - d) / stride) + 1.
 
 Encrypted layer, FFConv packing DP-HI2C-CP (Sec. 4.2, Fig. 4): W1 under DensePack (Sec. 3.2,
 Fig. 1), the DP -> CP transition with a 1 x 1 kernel (Table III, d = 1 row), W2 under
-ConvPack (Sec. 3.2, Fig. 2a).  Three schedules of W1:
+ConvPack (Sec. 3.2, Fig. 2a).  Schedules of W1:
 
   dp_dot   (the paper's DensePack): the input is packed densely in row 0,
            slot ci*I_h*I_w + h*I_w + w.  For every output channel c' and output position o
@@ -28,6 +28,9 @@ ConvPack (Sec. 3.2, Fig. 2a).  Three schedules of W1:
            ci*B_c + (s oh) I_w + s ow wherever that input pixel lies inside the image;
            channels are then folded with acc <- acc + rot(acc, B_c 2^k).  y1[c', oh, ow]
            lands at slot (s oh) I_w + s ow.
+  cp_cp    (CP-HI2C-CP, Sec. 4.2 'ConvPack for W1', Fig. 5): the client packs the Im2Col
+           columns of the input (one ciphertext per column, I[o, k] at slot o); W1 and W2 are
+           both ConvPack scalar products and the layer needs no rotation.
   dp_shift_ext (the same slots and plaintexts as dp_shift): the hoisted rotations stay in the
            extended basis Q u P, each as (u0 + P phi(c0), u1); the tap products are summed
            there (plaintexts lifted to Q u P) and divided by P once per channel (one ModDown
@@ -55,7 +58,7 @@ class Layout:
     pad: int
     r: int
     O_c: int
-    pack: str = "dp_shift"      # "dp_dot" | "dp_shift" | "dp_shift_ext"
+    pack: str = "dp_shift"      # "dp_dot" | "dp_shift" | "dp_shift_ext" | "cp_cp"
     modswitch: bool = False
 
     @property
@@ -129,13 +132,17 @@ def input_slots(x, lay: Layout, n: int):
 
 
 def output_slot(lay: Layout, oh: int, ow: int) -> int:
-    if lay.pack == "dp_dot":
+    if lay.pack in ("dp_dot", "cp_cp"):
         return oh * lay.O_w + ow
     return (lay.stride * oh) * lay.I_w + lay.stride * ow
 
 
 def check_fits(lay: Layout, n: int):
     half = n // 2
+    if lay.pack == "cp_cp":
+        if lay.S > n:
+            raise ValueError("cp_cp output positions must fit in N slots")
+        return
     if lay.pack == "dp_dot":
         if lay.I_c * lay.I_h * lay.I_w > n or lay.S > half:
             raise ValueError("dp_dot input must fit in N slots and its output in N/2")
@@ -191,6 +198,8 @@ def dp_dot_steps(lay: Layout, n: int):
 
 def required_steps(lay: Layout, n: int):
     """Rotation steps (slots) whose Galois keys the layer needs."""
+    if lay.pack == "cp_cp":
+        return []
     if lay.pack == "dp_dot":
         return dp_dot_steps(lay, n)
     steps = [dl for (_, _, dl) in lay.taps() if dl != 0]
@@ -263,9 +272,47 @@ def _restore(prm, cts_w1, W2, lay: Layout, ops: OpCount):
     return outs
 
 
+def im2col_slots(x, lay: Layout, n: int):
+    """Client-side plaintext Im2Col (Sec. 3.1 Eq. 1, Table VI's 64 x 144 input): one slot
+    vector per column k = (ci, i, j) of I, holding I[o, k] at slot o = oh O_w + ow."""
+    I = im2col(np.asarray(x), lay)
+    out = []
+    for k in range(I.shape[1]):
+        v = np.zeros(n, dtype=np.int64)
+        v[: lay.S] = I[:, k]
+        out.append(v)
+    return out
+
+
+def he_layer_cp_cp(prm, cts_in, W1, W2, lay: Layout, ops: OpCount = None):
+    """FFConv packing CP-HI2C-CP (Sec. 4.2 'ConvPack for W1', Fig. 5): the K = d^2 I_c input
+    ciphertexts hold the Im2Col columns; W1 under ConvPack is ct_w1[c'] = sum_k W1[c', k] ct_k
+    (Table II), HGrouping for the 1 x 1 W2 is free (Table III, CP-HI2C-CP, d = 1: the r
+    results already hold one channel each), W2 under ConvPack as in the other schedules."""
+    check_fits(lay, prm.n)
+    ops = ops if ops is not None else OpCount()
+    W1m = np.asarray(W1, dtype=np.int64).reshape(lay.r, -1)
+    cts_w1 = []
+    for c in range(lay.r):
+        acc = None
+        for k, ct in enumerate(cts_in):
+            term = bfv.mul_scalar(prm, ct, int(W1m[c, k]))
+            ops.mulpc += 1
+            if acc is None:
+                acc = term
+            else:
+                acc = bfv.add(prm, acc, term)
+                ops.addcc += 1
+        cts_w1.append(acc)
+    return _restore(prm, cts_w1, W2, lay, ops)
+
+
 def he_layer(prm, ct_in, W1, W2, lay: Layout, keys, ops: OpCount = None,
              channels=None):
-    """Encrypted FFConv layer; returns the O_c output ciphertexts (coefficient domain)."""
+    """Encrypted FFConv layer; returns the O_c output ciphertexts (coefficient domain).
+    For the cp_cp schedule ct_in is the list of K Im2Col column ciphertexts."""
+    if lay.pack == "cp_cp":
+        return he_layer_cp_cp(prm, ct_in, W1, W2, lay, ops)
     check_fits(lay, prm.n)
     ops = ops if ops is not None else OpCount()
     n = prm.n
@@ -342,6 +389,9 @@ def expected_ops(lay: Layout, n: int):
     n_sum = len(dp_dot_steps(lay, n)) if lay.pack == "dp_dot" else 0
     r, S, O_c = lay.r, lay.S, lay.O_c
     restore_mul, restore_add = O_c * r, O_c * (r - 1)
+    if lay.pack == "cp_cp":
+        K = lay.d * lay.d * lay.I_c     # Table II, FFConv row: MulPC O'_c (K + O_c)
+        return {"mulpc": r * (K + O_c), "addcc": r * (K - 1) + restore_add, "rot": 0}
     if lay.pack == "dp_dot":
         return {"mulpc": 2 * r * S + restore_mul,
                 "addcc": r * S * n_sum + r * (S - 1) + restore_add,

@@ -64,7 +64,8 @@ bool window_covers(const he_layout& y, const LayoutInfo& li, int k) {
 int layout_info(const he_ctx* c, const he_layout* y, LayoutInfo* li, std::string* why) {
     if (y->I_c < 1 || y->I_h < 1 || y->I_w < 1 || y->d < 1 || y->stride < 1 || y->pad < 0 ||
         y->r < 1 || y->O_c < 1 ||
-        (y->pack != HE_DP_DOT && y->pack != HE_DP_SHIFT && y->pack != HE_DP_SHIFT_EXT)) {
+        (y->pack != HE_DP_DOT && y->pack != HE_DP_SHIFT && y->pack != HE_DP_SHIFT_EXT &&
+         y->pack != HE_CP_CP)) {
         *why = "layout fields out of range";
         return HE_EINVAL;
     }
@@ -82,7 +83,12 @@ int layout_info(const he_ctx* c, const he_layout* y, LayoutInfo* li, std::string
     const long long half = c->N / 2;
     li->sum_depth = 0;
     li->both_rows = false;
-    if (y->pack == HE_DP_DOT) {
+    if (y->pack == HE_CP_CP) {
+        if (li->S > c->N) {
+            *why = "CP_CP output positions must fit in N slots";
+            return HE_EINVAL;
+        }
+    } else if (y->pack == HE_DP_DOT) {
         long long span = (long long)y->I_c * li->hw;
         if (span > c->N || li->S > half) {
             *why = "DP_DOT input must fit in N slots and its output in N/2";
@@ -107,6 +113,7 @@ int layout_info(const he_ctx* c, const he_layout* y, LayoutInfo* li, std::string
 
 std::vector<int32_t> layer_steps(const he_layout& y, const LayoutInfo& li) {
     std::vector<int32_t> st;
+    if (y.pack == HE_CP_CP) return st;   // ConvPack throughout: no rotation
     if (y.pack == HE_DP_DOT) {
         for (int e = 0; e < li.sum_depth; ++e) st.push_back(1 << e);
         if (li.both_rows) st.push_back(HE_ROW_SWAP);
@@ -193,6 +200,100 @@ extern "C" int he_ffconv_required_steps(const he_ctx* ctx, const he_layout* layo
     return (int)st.size();
 }
 
+// Integer weights w[o][i] (o < n_out, i < n_in) -> Montgomery residues wm[(o n_in + i) L + l].
+static std::vector<uint64_t> weights_mont(const he_ctx* ctx, const int32_t* w, int n_out, int n_in) {
+    const int L = ctx->L;
+    std::vector<uint64_t> wm((size_t)n_out * n_in * L);
+    for (int o = 0; o < n_out; ++o)
+        for (int i = 0; i < n_in; ++i)
+            for (int l = 0; l < L; ++l) {
+                const uint64_t q = ctx->mods[l];
+                const int64_t v = w[(size_t)o * n_in + i];
+                const uint64_t wr = v >= 0 ? (uint64_t)v % q : (q - ((uint64_t)(-v) % q)) % q;
+                wm[((size_t)o * n_in + i) * L + l] = h_to_mont(wr, q);
+            }
+    return wm;
+}
+
+// W2 under ConvPack (Table II): ct_out[b][c] = sum_c' W2[c][c'] ct_w1[b][c'] with scalar
+// plaintexts, from the channel results A [B][r][2][L][N]; then the optional modulus switch.
+static int restore_layer(he_ctx* ctx, const uint64_t* A, int B, const he_layout& y,
+                         const int32_t* restore_w, he_ct* ct_out, uint64_t* Y, uint64_t* last,
+                         uint64_t* sprd) {
+    const int L = ctx->L, r = y.r, O_c = y.O_c;
+    const size_t ct = 2 * (size_t)L * ctx->N;
+    const std::vector<uint64_t> wm = weights_mont(ctx, restore_w, O_c, r);
+    const uint64_t* d_wm = (const uint64_t*)upload_small(ctx, wm.data(), wm.size() * 8);
+    if (!d_wm) return he_fail(ctx, HE_EINVAL, "he_ffconv_layer: W2 too large for staging");
+    std::vector<uint64_t*> dst(B * O_c);
+    for (int o = 0; o < B * O_c; ++o) {
+        dst[o] = y.modswitch ? Y + (size_t)o * ct : ct_out[o].data;
+        ct_out[o].domain = HE_NTT;
+    }
+    auto dp = upload_out_ptrs(ctx, dst);
+    if (!dp) return he_fail(ctx, HE_ECUDA, "pointer table upload failed");
+    phase_begin(ctx, HE_PHASE_RESTORE);
+    launch_convpack(ctx, A, B, r, O_c, d_wm, dp, L);
+    ctx->ops[0] += (uint64_t)B * O_c * r;
+    ctx->ops[1] += (uint64_t)B * O_c * (r - 1);
+    int rc = he_launch_check(ctx, "he_ffconv_layer");
+    if (rc) return rc;
+    if (y.modswitch) {
+        std::vector<const uint64_t*> xs(B * O_c);
+        std::vector<uint64_t*> os(B * O_c);
+        for (int o = 0; o < B * O_c; ++o) {
+            xs[o] = Y + (size_t)o * ct;
+            os[o] = ct_out[o].data;
+        }
+        if ((rc = rescale_items(ctx, xs, os, L, last, sprd))) return rc;
+    }
+    phase_end(ctx);
+    return HE_OK;
+}
+
+// CP-HI2C-CP (Sec. 4.2 'ConvPack for W1', Fig. 5): ct_in holds K = d^2 I_c Im2Col column
+// ciphertexts per image (image b's column k at b K + k).  W1 under ConvPack:
+// ct_w1[b][c'] = sum_k W1[c'][k] ct_in[b][k]; the 1 x 1 W2 needs no regrouping (Table III,
+// CP-HI2C-CP with d = 1: zero rotations).
+static int cp_cp_layer(he_ctx* ctx, const he_ct* ct_in, int B, const int32_t* lowrank_w,
+                       const int32_t* restore_w, const he_layout& y, const LayoutInfo& li,
+                       he_ct* ct_out) {
+    const int L = ctx->L, Lout = y.modswitch ? L - 1 : L;
+    const int K = li.taps * y.I_c, r = y.r, O_c = y.O_c;
+    int rc;
+    for (int i = 0; i < B * K; ++i)
+        if ((rc = check_ct(ctx, &ct_in[i], L, HE_NTT, "he_ffconv_layer input column"))) return rc;
+    for (int o = 0; o < B * O_c; ++o)
+        if ((rc = check_ct(ctx, &ct_out[o], Lout, -1, "he_ffconv_layer output"))) return rc;
+    if (K > max_mac_terms(ctx)) return he_fail(ctx, HE_EINVAL, "he_ffconv_layer: too many columns");
+    const size_t N = ctx->N, ct = 2 * (size_t)L * N;
+    size_t need = (size_t)B * K * ct + (size_t)B * r * ct +
+                  (y.modswitch ? (size_t)B * O_c * (ct + 2 * N + 2 * (L - 1) * N) : 0) + 1024;
+    if ((rc = arena_reserve(ctx, need))) return rc;
+    arena_reset(ctx);
+    uint64_t* X = arena_take(ctx, (size_t)B * K * ct);
+    uint64_t* A = arena_take(ctx, (size_t)B * r * ct);
+    uint64_t* Y = y.modswitch ? arena_take(ctx, (size_t)B * O_c * ct) : nullptr;
+    uint64_t* last = y.modswitch ? arena_take(ctx, (size_t)B * O_c * 2 * N) : nullptr;
+    uint64_t* sprd = y.modswitch ? arena_take(ctx, (size_t)B * O_c * 2 * (L - 1) * N) : nullptr;
+    for (int i = 0; i < B * K; ++i)
+        HE_CHECK_CUDA(ctx, cudaMemcpyAsync(X + (size_t)i * ct, ct_in[i].data, ct * 8,
+                                           cudaMemcpyDeviceToDevice, ctx->stream));
+    const std::vector<uint64_t> wm = weights_mont(ctx, lowrank_w, r, K);
+    const uint64_t* d_wm = (const uint64_t*)upload_small(ctx, wm.data(), wm.size() * 8);
+    if (!d_wm) return he_fail(ctx, HE_EINVAL, "he_ffconv_layer: W1 too large for staging");
+    std::vector<uint64_t*> ao(B * r);
+    for (int q = 0; q < B * r; ++q) ao[q] = A + (size_t)q * ct;
+    auto op = upload_out_ptrs(ctx, ao);
+    if (!op) return he_fail(ctx, HE_ECUDA, "pointer table upload failed");
+    phase_begin(ctx, HE_PHASE_TAPS);
+    launch_convpack(ctx, X, B, K, r, d_wm, op, L);
+    phase_end(ctx);
+    ctx->ops[0] += (uint64_t)B * r * K;
+    ctx->ops[1] += (uint64_t)B * r * (K - 1);
+    return restore_layer(ctx, A, B, y, restore_w, ct_out, Y, last, sprd);
+}
+
 extern "C" int he_ffconv_layer_batch(he_ctx* ctx, const he_ct* ct_in, int B,
                                      const int32_t* lowrank_w, const int32_t* restore_w,
                                      const he_layout* layout, he_ct* ct_out) {
@@ -207,6 +308,7 @@ extern "C" int he_ffconv_layer_batch(he_ctx* ctx, const he_ct* ct_in, int B,
     const he_layout& y = *layout;
     const int L = ctx->L, Lout = y.modswitch ? L - 1 : L;
     if (y.modswitch && L < 2) return he_fail(ctx, HE_EINVAL, "he_ffconv_layer: modswitch needs two primes");
+    if (y.pack == HE_CP_CP) return cp_cp_layer(ctx, ct_in, B, lowrank_w, restore_w, y, li, ct_out);
     for (int b = 0; b < B; ++b)
         if ((rc = check_ct(ctx, &ct_in[b], L, HE_NTT, "he_ffconv_layer input"))) return rc;
     for (int o = 0; o < B * y.O_c; ++o)
@@ -427,41 +529,7 @@ extern "C" int he_ffconv_layer_batch(he_ctx* ctx, const he_ct* ct_in, int B,
         phase_end(ctx);
     }
 
-    // W2 under ConvPack: ct_out[b][c] = sum_c' W2[c][c'] ct_w1[b][c'] (scalar plaintexts)
-    std::vector<uint64_t> wm((size_t)O_c * r * L);
-    for (int c = 0; c < O_c; ++c)
-        for (int cp = 0; cp < r; ++cp)
-            for (int i = 0; i < L; ++i) {
-                uint64_t q = ctx->mods[i];
-                int64_t w = restore_w[c * r + cp];
-                uint64_t wr = w >= 0 ? (uint64_t)w % q : (q - ((uint64_t)(-w) % q)) % q;
-                wm[((size_t)c * r + cp) * L + i] = h_to_mont(wr, q);
-            }
-    const uint64_t* d_wm = (const uint64_t*)upload_small(ctx, wm.data(), wm.size() * 8);
-    if (!d_wm) return he_fail(ctx, HE_EINVAL, "he_ffconv_layer: W2 too large for staging");
-    std::vector<uint64_t*> dst(B * O_c);
-    for (int o = 0; o < B * O_c; ++o) {
-        dst[o] = y.modswitch ? Y + (size_t)o * ct : ct_out[o].data;
-        ct_out[o].domain = HE_NTT;
-    }
-    auto dp = upload_out_ptrs(ctx, dst);
-    if (!dp) return he_fail(ctx, HE_ECUDA, "pointer table upload failed");
-    phase_begin(ctx, HE_PHASE_RESTORE);
-    launch_convpack(ctx, A, B, r, O_c, d_wm, dp, L);
-    ctx->ops[0] += (uint64_t)B * O_c * r;
-    ctx->ops[1] += (uint64_t)B * O_c * (r - 1);
-    if ((rc = he_launch_check(ctx, "he_ffconv_layer"))) return rc;
-    if (y.modswitch) {
-        std::vector<const uint64_t*> xs(B * O_c);
-        std::vector<uint64_t*> os(B * O_c);
-        for (int o = 0; o < B * O_c; ++o) {
-            xs[o] = Y + (size_t)o * ct;
-            os[o] = ct_out[o].data;
-        }
-        if ((rc = rescale_items(ctx, xs, os, L, last, sprd))) return rc;
-    }
-    phase_end(ctx);
-    return HE_OK;
+    return restore_layer(ctx, A, B, y, restore_w, ct_out, Y, last, sprd);
 }
 
 extern "C" int he_ffconv_layer(he_ctx* ctx, const he_ct* ct_in, const int32_t* lowrank_w,

@@ -12,7 +12,7 @@ import numpy as np
 
 HE_OK, HE_EINVAL, HE_ENOMEM, HE_ENOKEY, HE_ECUDA, HE_ETIMEOUT = 0, -1, -2, -3, -4, -5
 HE_COEFF, HE_NTT = 0, 1
-HE_DP_DOT, HE_DP_SHIFT, HE_DP_SHIFT_EXT = 0, 1, 2
+HE_DP_DOT, HE_DP_SHIFT, HE_DP_SHIFT_EXT, HE_CP_CP = 0, 1, 2, 3
 HE_ROW_SWAP = 0x7FFFFFFF
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -317,7 +317,8 @@ class Context:
 
     @staticmethod
     def layout(I_c, I_h, I_w, d, stride, pad, r, O_c, pack="dp_shift", modswitch=False):
-        packs = {"dp_dot": HE_DP_DOT, "dp_shift": HE_DP_SHIFT, "dp_shift_ext": HE_DP_SHIFT_EXT}
+        packs = {"dp_dot": HE_DP_DOT, "dp_shift": HE_DP_SHIFT, "dp_shift_ext": HE_DP_SHIFT_EXT,
+                 "cp_cp": HE_CP_CP}
         return HeLayout(I_c, I_h, I_w, d, stride, pad, r, O_c, packs[pack], int(bool(modswitch)))
 
     def he_ffconv_required_steps(self, lay):
@@ -328,7 +329,10 @@ class Context:
         return [int(x) for x in out[:n]]
 
     def he_ffconv_layer_batch(self, cts_in, W1, W2, lay, outs=None):
+        """cts_in: B ciphertexts, or for HE_CP_CP B * K Im2Col column ciphertexts."""
         B = len(cts_in)
+        if lay.pack == HE_CP_CP:
+            B //= lay.d * lay.d * lay.I_c
         lv = self.L - 1 if lay.modswitch else self.L
         outs = [self.new_ct(level=lv) for _ in range(B * lay.O_c)] if outs is None else outs
         ia, oa = self.ct_array(cts_in), self.ct_array(outs)

@@ -24,7 +24,7 @@ def oracle_keys(prm, s, steps, seed=2):
         if g not in keys:
             keys[g] = bfv.galois_key(prm, s, g, seed)
         blob.append(keys[g].reshape(-1))
-    return keys, np.concatenate(blob)
+    return keys, (np.concatenate(blob) if blob else np.zeros(0, dtype=np.uint64))
 
 
 def gpu_steps(steps):

@@ -21,8 +21,12 @@ def setup_layer(prm, shape, pack, seed=0, modswitch=False, B=1):
     keys, blob = oracle_keys(prm, s, steps, seed + 2)
     xs = workloads.images(seed, shape, B)
     W1, W2 = workloads.weights(seed, shape)
-    cts = [bfv.encrypt(prm, s, encoder.encode(ffconv.input_slots(x, lay_o, prm.n), prm), seed + 3 + b)
-           for b, x in enumerate(xs)]
+    if pack == "cp_cp":     # B * K Im2Col column ciphertexts
+        cts = [bfv.encrypt(prm, s, encoder.encode(v, prm), seed + 3 + 100 * b + k)
+               for b, x in enumerate(xs) for k, v in enumerate(ffconv.im2col_slots(x, lay_o, prm.n))]
+    else:
+        cts = [bfv.encrypt(prm, s, encoder.encode(ffconv.input_slots(x, lay_o, prm.n), prm), seed + 3 + b)
+               for b, x in enumerate(xs)]
     return lay_o, s, steps, keys, blob, xs, W1, W2, cts
 
 
@@ -134,3 +138,26 @@ def test_bench_layer_n15_decrypts_to_the_convolution(pack, B):
     outs = ctx.he_ffconv_layer_batch(cts, W1, W2, lay)
     for b in range(B):
         check_decrypted(ctx, prm, sk, lay_o, outs[b * 5:(b + 1) * 5], xs[b], W1, W2)
+
+
+@pytest.mark.parametrize("B", [1, 2])
+def test_cp_cp_layers_are_bit_exact(B):
+    """CP-HI2C-CP (Table VI's TinyNet packing) on small rings and at the TinyNet-shaped layer
+    (28 x 28 input, 8 x 8 stride-2 pad-1 filters, 13 -> 56 channels) at N = 8192."""
+    for prm, shape in [(params.Params(log_n=9, n_q=3, n_p=1, alpha=1), workloads.LayerShape(2, 6, 6, 3, 1, 1, 3, 2)),
+                       (params.cfg_small_layer(), workloads.LayerShape(1, 28, 28, 8, 2, 1, 13, 56))]:
+        lay_o, s, steps, keys, blob, xs, W1, W2, cts = setup_layer(prm, shape, "cp_cp", seed=3, B=B)
+        assert steps == []
+        ctx = make_ctx(prm)
+        lay = ctx.layout(*shape.astuple(), pack="cp_cp")
+        ctx.he_reset_op_counts()
+        outs = ctx.he_ffconv_layer_batch([upload_ntt(ctx, c) for c in cts], W1, W2, lay)
+        K = shape.d * shape.d * shape.I_c
+        for b in range(B):
+            ops = ffconv.OpCount()
+            want = ffconv.he_layer(prm, cts[b * K:(b + 1) * K], W1, W2, lay_o, {}, ops)
+            for c in range(shape.O_c):
+                assert (download_coeff(ctx, outs[b * shape.O_c + c]) == want[c].stack()).all()
+            check_decrypted(ctx, prm, s, lay_o, outs[b * shape.O_c:(b + 1) * shape.O_c], xs[b], W1, W2)
+        got = ctx.he_op_counts()
+        assert got["rot"] == 0 and got["mulpc"] == B * ops.mulpc

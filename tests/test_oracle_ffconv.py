@@ -56,7 +56,11 @@ def run_he(prm, lay, seed=0):
     for st in ffconv.required_steps(lay, prm.n):
         g = bfv.galois_of(st, prm.n)
         keys[g] = bfv.galois_key(prm, s, g, seed + 2)
-    ct = bfv.encrypt(prm, s, encoder.encode(ffconv.input_slots(x, lay, prm.n), prm), seed + 3)
+    if lay.pack == "cp_cp":
+        ct = [bfv.encrypt(prm, s, encoder.encode(v, prm), seed + 3 + k)
+              for k, v in enumerate(ffconv.im2col_slots(x, lay, prm.n))]
+    else:
+        ct = bfv.encrypt(prm, s, encoder.encode(ffconv.input_slots(x, lay, prm.n), prm), seed + 3)
     ops = ffconv.OpCount()
     outs = ffconv.he_layer(prm, ct, W1, W2, lay, keys, ops)
     _, y2 = ffconv.plain_layer(x, W1, W2, lay)
@@ -70,7 +74,7 @@ def check_outputs(prm, s, lay, outs, y2):
         for oh in range(lay.O_h):
             for ow in range(lay.O_w):
                 want[ffconv.output_slot(lay, oh, ow)] = y2[c, oh, ow] % prm.t
-        if lay.I_c == 1 or lay.pack == "dp_dot":
+        if lay.I_c == 1 or lay.pack in ("dp_dot", "cp_cp"):
             assert (v == want).all()
         else:   # folded channels leave partial sums in the other channel blocks
             pos = [ffconv.output_slot(lay, oh, ow) for oh in range(lay.O_h) for ow in range(lay.O_w)]
@@ -78,7 +82,7 @@ def check_outputs(prm, s, lay, outs, y2):
         assert bfv.noise_bits(prm, s, ct)[1] > 10
 
 
-@pytest.mark.parametrize("pack", ["dp_dot", "dp_shift", "dp_shift_ext"])
+@pytest.mark.parametrize("pack", ["dp_dot", "dp_shift", "dp_shift_ext", "cp_cp"])
 @pytest.mark.parametrize("shape", [(1, 6, 6, 3, 2, 1, 2, 3), (2, 5, 5, 3, 1, 1, 2, 2), (3, 4, 4, 3, 2, 1, 2, 3)])
 def test_encrypted_layer_decrypts_to_plain_layer(pack, shape):
     prm = params.Params(log_n=7, n_q=3, n_p=1, alpha=1)
@@ -137,3 +141,13 @@ def test_extended_basis_schedule_differs_in_bits_but_not_in_slots():
     assert not (a[0].stack() == b[0].stack()).all()
     for x, y in zip(a, b):
         assert (bfv.decrypt(prm, s, x) == bfv.decrypt(prm, s, y)).all()
+
+
+def test_conv_pack_counts_follow_table_ii():
+    """Table II, FFConv row: MulPC = O'_c (K + O_c) for the factorized pair under ConvPack,
+    here at the TinyNet layer of Table VI (8 x 8 stride-2 conv, 13 low-rank channels, 56
+    restored channels, 144 output positions, K = 64)."""
+    lay = ffconv.Layout(1, 28, 28, 8, 2, 1, 13, 56, pack="cp_cp")
+    assert (lay.S, lay.d * lay.d * lay.I_c) == (144, 64)
+    ops = ffconv.expected_ops(lay, 8192)
+    assert ops["mulpc"] == 13 * (64 + 56) and ops["rot"] == 0
