@@ -36,6 +36,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--pack", default="dp_shift_ext", choices=["dp_shift", "dp_shift_ext", "dp_dot"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving", action="store_true",
+                    help="run the serving loop (mixed rings, Poisson arrivals) instead")
     return ap.parse_args()
 
 
@@ -341,10 +343,84 @@ def layer_algorithmic_bytes(B, O_c, n_rot):
     return keys + B * ct + B * O_c * ct
 
 
+def run_serving(args):
+    """Serving loop: Poisson arrivals of mixed requests -- 60 % the 28 x 28 layer at N = 2^14
+    (6 + 2 primes), 40 % a 3 x 32 x 32 layer (3 x 3 stride 1, r = 8 -> 64 channels) at
+    N = 2^15 (12 + 3 primes) -- continuously batched over two worker streams per ring,
+    against the plain form (one request per call, in arrival order, one stream)."""
+    import numpy as np
+    import torch
+
+    from paper_2102_03494_gb300 import serving, workloads
+
+    specs = {"n14_mnist": serving.RingSpec(14, 6, 2, 2, workloads.MNIST_LAYER.astuple()),
+             "n15_cifar": serving.RingSpec(15, 12, 3, 3, (3, 32, 32, 3, 1, 1, 8, 64))}
+    mix = {"n14_mnist": 0.6, "n15_cifar": 0.4}
+    rings = {}
+    for i, (name, sp) in enumerate(specs.items()):
+        shape = workloads.LayerShape(*sp.shape)
+        W1, W2 = workloads.weights(i, shape, lo=-8, hi=8)
+        rings[name] = serving.GpuRing(sp, workers=2, W1=W1, W2=W2, sk_seed=1 + i, key_seed=11 + i)
+
+    def make_requests(rate, count, seed):
+        reqs = serving.poisson_arrivals(seed=seed, rate=rate, count=count, mix=mix)
+        for r in reqs:
+            sp = specs[r.ring]
+            shape = workloads.LayerShape(*sp.shape)
+            x = workloads.image(r.rid + 1000 * seed, shape)
+            N = 1 << sp.log_n
+            hw = shape.I_h * shape.I_w
+            B_c = hw if shape.I_c == 1 else 1 << (hw - 1).bit_length()
+            slots = np.zeros(N, dtype=np.int64)
+            for ci in range(shape.I_c):
+                slots[ci * B_c: ci * B_c + hw] = x[ci].reshape(-1)
+            r.payload = rings[r.ring].encrypt(slots, 7000 + r.rid)
+        torch.cuda.synchronize()
+        return reqs
+
+    # warm-up of every worker of every ring at the largest batch (scratch sizing, first launches)
+    warm = make_requests(1e9, 64, seed=99)
+    for name, ring in rings.items():
+        mine = [r for r in warm if r.ring == name][:8]
+        for w in range(ring.workers):
+            ring.launch(w, mine)
+    torch.cuda.synchronize()
+    out = {"metric": "serving: mixed-ring encrypted FFConv-layer requests, continuous batching",
+           "unit": "requests/s and ms", "mix": mix, "workers_per_ring": 2, "max_batch": 8,
+           "rates": []}
+    for rate in (100.0, 400.0, 800.0, 1600.0):
+        count = int(min(rate * 1.5, 1200))
+        reqs = make_requests(rate, count, seed=int(rate))
+        sched = serving.Scheduler(rings, max_batch=8, memory_budget=64 << 30,
+                                  clock=time.perf_counter)
+        done = sched.serve(reqs)
+        torch.cuda.synchronize()
+        served = serving.latency_stats(done)
+        # the plain form: one request per call in arrival order on one stream
+        plain_reqs = make_requests(rate, count, seed=int(rate))
+        t_free, lat, t_first = 0.0, [], None
+        for r in plain_reqs:
+            t0 = time.perf_counter()
+            rings[r.ring].run_alone(r.payload)
+            dt = time.perf_counter() - t0
+            start = max(r.t_arrive, t_free)
+            t_free = start + dt
+            lat.append((t_free - r.t_arrive) * 1000.0)
+        span = t_free - plain_reqs[0].t_arrive
+        plain = {"requests": count, "p50_ms": float(np.percentile(lat, 50)),
+                 "p99_ms": float(np.percentile(lat, 99)), "requests_per_s": count / span}
+        out["rates"].append({"offered_per_s": rate, "served": served, "plain": plain,
+                             "p99_factor": plain["p99_ms"] / served["p99_ms"]})
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.serving:
+        run_serving(args)
         return
     run(args)
 

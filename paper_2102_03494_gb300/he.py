@@ -162,7 +162,8 @@ class Context:
         torch = _torch()
         lv = self.L if level is None else level
         shape = (2, lv, self.N) if count is None else (count, 2, lv, self.N)
-        return torch.zeros(shape, dtype=torch.int64, device="cuda")
+        with torch.cuda.stream(self.stream):      # ordered before the library's work on it
+            return torch.zeros(shape, dtype=torch.int64, device="cuda")
 
     @staticmethod
     def ct_struct(t, domain=HE_NTT):
@@ -174,13 +175,14 @@ class Context:
             arr[i] = self.ct_struct(t, domain)
         return arr
 
-    @staticmethod
-    def to_numpy(t):
+    def to_numpy(self, t):
+        self.stream.synchronize()                  # the library may still be writing t
         return t.detach().cpu().numpy().view(np.uint64)
 
     def from_numpy(self, a):
         torch = _torch()
-        return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint64).view(np.int64)).cuda()
+        with torch.cuda.stream(self.stream):
+            return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint64).view(np.int64)).cuda()
 
     # ---- context
     def he_get_moduli(self):
@@ -263,7 +265,8 @@ class Context:
 
     def he_encode(self, slots):
         torch = _torch()
-        out = torch.zeros((self.L, self.N), dtype=torch.int64, device="cuda")
+        with torch.cuda.stream(self.stream):
+            out = torch.zeros((self.L, self.N), dtype=torch.int64, device="cuda")
         sl, psl = _i64(slots)
         self._ck(lib().he_encode(self.h, psl, ctypes.c_void_p(out.data_ptr())), "he_encode")
         return out

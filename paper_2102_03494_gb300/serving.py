@@ -1,0 +1,223 @@
+"""Serving loop: continuous batching of encrypted FFConv-layer requests on one GPU.
+
+Requests for layers on different rings (e.g. the 28 x 28 layer at N = 2^14 and a 3 x 32 x 32
+layer at N = 2^15) arrive over time.  The scheduler
+  * admits a waiting request when its device-memory footprint fits the budget (inputs,
+    outputs and its share of scratch), freeing the footprint when its batch completes;
+  * groups admitted requests of the same ring, oldest first, into batches of up to
+    `max_batch`, and starts a batch as soon as a worker of that ring is idle -- requests
+    that arrive while others run join the next batch (continuous batching);
+  * runs every worker on its own CUDA stream with its own library context (Galois keys
+    resident in each), so batches of different rings and workers overlap on the device.
+Completion is detected with CUDA events; latency = completion - arrival.
+
+The scheduling logic (`Scheduler`) is plain host code that drives an executor interface, so
+it is tested with a fake executor on the CPU; `GpuRing` is the executor over libhe.
+"""
+from dataclasses import dataclass, field
+from typing import Callable, Dict, List, Optional
+
+
+@dataclass
+class Request:
+    rid: int
+    ring: str
+    t_arrive: float
+    payload: object = None          # executor-specific input (device ciphertext(s))
+    footprint: int = 0              # device bytes held from admission to completion
+    t_start: Optional[float] = None
+    t_done: Optional[float] = None
+    result: object = None
+
+
+@dataclass
+class Batch:
+    ring: str
+    worker: int
+    requests: List[Request]
+    handle: object = None           # executor-specific completion handle
+
+
+class Scheduler:
+    """Admission by memory footprint + per-ring FIFO batching over a pool of workers.
+
+    executors: ring -> object with
+        workers: int                                 number of concurrent batches
+        footprint(req) -> int                        device bytes of one request
+        launch(worker, requests) -> handle           enqueue the batch (asynchronous)
+        done(handle) -> bool                         completion poll
+        results(handle, requests)                    fill req.result after completion
+    """
+
+    def __init__(self, executors: Dict[str, object], max_batch: int, memory_budget: int,
+                 clock: Callable[[], float]):
+        self.ex = executors
+        self.max_batch = max_batch
+        self.budget = memory_budget
+        self.clock = clock
+        self.waiting: List[Request] = []          # arrived, not admitted
+        self.admitted: Dict[str, List[Request]] = {r: [] for r in executors}
+        self.in_use = 0
+        self.running: List[Batch] = []
+        self.idle = {r: list(range(e.workers)) for r, e in executors.items()}
+        self.finished: List[Request] = []
+
+    def submit(self, req: Request):
+        req.footprint = self.ex[req.ring].footprint(req)
+        if req.footprint > self.budget:
+            raise ValueError(f"request {req.rid} needs {req.footprint} B, above the whole budget")
+        self.waiting.append(req)
+
+    def _admit(self):
+        keep = []
+        for req in self.waiting:                  # oldest first; later ones may still fit
+            if self.in_use + req.footprint <= self.budget:
+                self.in_use += req.footprint
+                self.admitted[req.ring].append(req)
+            else:
+                keep.append(req)
+        self.waiting = keep
+
+    def _complete(self):
+        still = []
+        for b in self.running:
+            if self.ex[b.ring].done(b.handle):
+                self.ex[b.ring].results(b.handle, b.requests)
+                now = self.clock()
+                for r in b.requests:
+                    r.t_done = now
+                    self.in_use -= r.footprint
+                    self.finished.append(r)
+                self.idle[b.ring].append(b.worker)
+            else:
+                still.append(b)
+        self.running = still
+
+    def _launch(self):
+        for ring, queue in self.admitted.items():
+            while queue and self.idle[ring]:
+                take, self.admitted[ring] = queue[: self.max_batch], queue[self.max_batch:]
+                queue = self.admitted[ring]
+                w = self.idle[ring].pop(0)
+                now = self.clock()
+                for r in take:
+                    r.t_start = now
+                handle = self.ex[ring].launch(w, take)
+                self.running.append(Batch(ring, w, take, handle))
+
+    def step(self):
+        """One pass: retire finished batches, admit, launch.  Returns True while busy."""
+        self._complete()
+        self._admit()
+        self._launch()
+        return bool(self.waiting or self.running or any(self.admitted.values()))
+
+    def serve(self, arrivals: List[Request]):
+        """Feed requests at their arrival times (seconds from start) and run to completion."""
+        t0 = self.clock()
+        pending = sorted(arrivals, key=lambda r: r.t_arrive)
+        i = 0
+        while True:
+            now = self.clock() - t0
+            while i < len(pending) and pending[i].t_arrive <= now:
+                pending[i].t_arrive += t0             # absolute clock from here on
+                self.submit(pending[i])
+                i += 1
+            busy = self.step()
+            if not busy and i == len(pending):
+                break
+        return self.finished
+
+
+def latency_stats(reqs: List[Request]):
+    import numpy as np
+    lat = np.array([r.t_done - r.t_arrive for r in reqs]) * 1000.0
+    span = max(r.t_done for r in reqs) - min(r.t_arrive for r in reqs)
+    return {"requests": len(reqs), "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+            "requests_per_s": len(reqs) / span if span > 0 else float("inf")}
+
+
+def poisson_arrivals(seed: int, rate: float, count: int, mix: Dict[str, float]):
+    """`count` requests with exponential inter-arrival times (rate per second) and rings drawn
+    with the given probabilities."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, count))
+    names = list(mix)
+    probs = np.array([mix[n] for n in names], dtype=float)
+    picks = rng.choice(len(names), size=count, p=probs / probs.sum())
+    return [Request(rid=i, ring=names[picks[i]], t_arrive=float(t[i])) for i in range(count)]
+
+
+# ---------------------------------------------------------------- GPU executor over libhe
+
+@dataclass
+class RingSpec:
+    log_n: int
+    n_q: int
+    n_p: int
+    alpha: int
+    shape: tuple                      # (I_c, I_h, I_w, d, stride, pad, r, O_c)
+    pack: str = "dp_shift_ext"
+
+
+class GpuRing:
+    """One ring's workers: a library context and a CUDA stream each, keys resident in every
+    context, weights fixed per ring."""
+
+    def __init__(self, spec: RingSpec, workers: int, W1, W2, sk_seed: int, key_seed: int):
+        import torch
+        from . import he
+        self.spec, self.workers = spec, workers
+        self.W1, self.W2 = W1, W2
+        self.streams = [torch.cuda.Stream() for _ in range(workers)]
+        self.ctx = [he.Context(spec.log_n, spec.n_q, spec.n_p, spec.alpha, stream=s)
+                    for s in self.streams]
+        self.lay = self.ctx[0].layout(*spec.shape, pack=spec.pack)
+        self.sk = self.ctx[0].he_keygen_secret(sk_seed)
+        steps = self.ctx[0].he_ffconv_required_steps(self.lay)
+        for c in self.ctx:
+            c.he_keygen_galois(self.sk, key_seed, steps)
+        self.N = 1 << spec.log_n
+        self.ct_bytes = 2 * spec.n_q * self.N * 8
+        self.O_c = spec.shape[7]
+
+    def encrypt(self, slots, seed):
+        return self.ctx[0].he_encrypt(self.sk, slots, seed)
+
+    def footprint(self, req):
+        # input + outputs + the per-image share of the layer's scratch (ModUp digits,
+        # extended channel sums, products): bounded by 8 ciphertexts of the extended basis
+        sp = self.spec
+        ext = 2 * (sp.n_q + sp.n_p) * self.N * 8
+        return self.ct_bytes * (1 + self.O_c) + 8 * ext
+
+    def launch(self, worker, requests):
+        import torch
+        ctx = self.ctx[worker]
+        with torch.cuda.stream(self.streams[worker]):
+            # allocated (and zero-filled) on the worker's stream, ordered before the layer
+            outs = [ctx.new_ct() for _ in range(len(requests) * self.O_c)]
+            ctx.he_ffconv_layer_batch([r.payload for r in requests], self.W1, self.W2, self.lay, outs)
+            ev = torch.cuda.Event()
+            ev.record(self.streams[worker])
+        return (ev, outs)
+
+    def done(self, handle):
+        return handle[0].query()
+
+    def results(self, handle, requests):
+        outs = handle[1]
+        for i, r in enumerate(requests):
+            r.result = outs[i * self.O_c:(i + 1) * self.O_c]
+
+    def run_alone(self, payload):
+        """The plain form: one request, one call, waited for."""
+        import torch
+        ctx = self.ctx[0]
+        with torch.cuda.stream(self.streams[0]):
+            outs = [ctx.new_ct() for _ in range(self.O_c)]
+            ctx.he_ffconv_layer_batch([payload], self.W1, self.W2, self.lay, outs)
+        self.streams[0].synchronize()
+        return outs
