@@ -30,7 +30,7 @@ import numpy as np
 
 from . import prng, ring
 from .encoder import lift_centered
-from .params import Params
+from .params import Params, is_prime, root_2n
 
 
 class Ct:
@@ -180,24 +180,99 @@ def noise_bits(prm: Params, s, ct: Ct, m=None):
     return nb, log2(delta / 2) - nb
 
 
-def galois_key(prm: Params, s, g: int, seed: int):
-    """Key for switching from s(X^g) back to s: [dnum][2][L+K][N] (index 0 = b, 1 = a)."""
+def switching_key(prm: Params, s, target_rns, seed: int, stream_a, stream_e):
+    """Key for switching from the secret `target` (residues [L+K][N] over Q u P) back to s:
+    [dnum][2][L+K][N], digit j = (b_j, a_j) with b_j = -a_j s + e_j + G_j target."""
     n, qp = prm.n, prm.qp
-    s_g = automorphism_int(s, g)
     P = prm.P
     out = np.empty((prm.dnum, 2, len(qp), n), dtype=np.uint64)
     for j in range(prm.dnum):
-        a = prng.uniform(seed, prng.stream_key_a(g, j), qp, n)
-        e = prng.gaussian(seed, prng.stream_key_e(g, j), n)
+        a = prng.uniform(seed, stream_a(j), qp, n)
+        e = prng.gaussian(seed, stream_e(j), n)
         digit = prm.digit(j)
         for l, q in enumerate(qp):
             as_ = ring.polymul(a[l], ring.from_signed(s, q), q, prm.psi[q])
             b = ring.vsub(ring.from_signed(e, q), as_, q)
             if l in digit:
-                b = ring.vmac_scalar(b, ring.from_signed(s_g, q), P % q, q)
+                b = ring.vmac_scalar(b, target_rns[l], P % q, q)
             out[j, 0, l] = b
             out[j, 1, l] = a[l]
     return out
+
+
+def galois_key(prm: Params, s, g: int, seed: int):
+    """Key for switching from s(X^g) back to s: [dnum][2][L+K][N] (index 0 = b, 1 = a)."""
+    target = to_rns(automorphism_int(s, g), prm.qp)
+    return switching_key(prm, s, target, seed, lambda j: prng.stream_key_a(g, j),
+                         lambda j: prng.stream_key_e(g, j))
+
+
+def relin_key(prm: Params, s, seed: int):
+    """Relinearisation key: switches s^2 (the secret of the third component of a product)
+    back to s; streams (6 << 48 | j) and (7 << 48 | j)."""
+    s_rns = to_rns(s, prm.qp)
+    target = rns_mul(s_rns, s_rns, prm, prm.qp)
+    return switching_key(prm, s, target, seed, lambda j: (6 << 48) | j, lambda j: (7 << 48) | j)
+
+
+# ---------------------------------------------------------------- ciphertext multiplication
+
+def _aux_primes(prm: Params, bits_needed: int):
+    """The oracle's own NTT primes (61-bit, 1 mod 2N, none of Q u P) for exact integer products."""
+    out, p = [], ((2 ** 61 - 2) // (2 * prm.n)) * (2 * prm.n) + 1
+    while sum(x.bit_length() - 1 for x in out) < bits_needed:
+        if is_prime(p) and p not in prm.qp:
+            out.append(p)
+        p -= 2 * prm.n
+    return out
+
+
+def centered_ints(x_rns, moduli):
+    """Residues [len][N] -> Python ints in (-M/2, M/2] (M = prod moduli) by CRT."""
+    vals, M = crt(x_rns, moduli)
+    return [v - M if v > M // 2 else v for v in vals]
+
+
+def multiply(prm: Params, a: Ct, b: Ct):
+    """BFV multiplication before relinearisation (Sec. 2.1's homomorphic multiplication):
+    d = round(t/Q (a0 + a1 s)(b0 + b1 s)) coefficient-wise, i.e. with a_k, b_k lifted to
+    centred integers, d0 = a0 b0, d1 = a0 b1 + a1 b0, d2 = a1 b1 over Z[X]/(X^N+1), then
+    round(t d_k / Q) mod Q.  Returns (d0, d1, d2) as [L][N] residue arrays."""
+    L = a.level
+    moduli = prm.q[:L]
+    Q = prm.Q(L)
+    n, t = prm.n, prm.t
+    # exact integer products through enough auxiliary primes: |d| <= 2 N (Q/2)^2
+    bound_bits = 2 * Q.bit_length() + (n.bit_length()) + 3
+    aux = _aux_primes(prm, bound_bits)
+    psi = {p: root_2n(p, n) for p in aux}
+    lifted = [centered_ints(x, moduli) for x in (a.c0, a.c1, b.c0, b.c1)]
+    a0, a1, b0, b1 = [np.stack([np.array([c % p for c in v], dtype=np.uint64) for p in aux])
+                      for v in lifted]
+    prods = []
+    for pairs in ([(a0, b0)], [(a0, b1), (a1, b0)], [(a1, b1)]):
+        acc = np.zeros((len(aux), n), dtype=np.uint64)
+        for x, y in pairs:
+            for l, p in enumerate(aux):
+                acc[l] = ring.vadd(acc[l], ring.polymul(x[l], y[l], p, psi[p]), p)
+        prods.append(acc)
+    out = []
+    for d in prods:
+        scaled = scale_round(centered_ints(d, aux), t, Q)
+        out.append(np.stack([np.array([v % q for v in scaled], dtype=np.uint64) for q in moduli]))
+    return out
+
+
+def scale_round(ints, t, Q):
+    """round(t v / Q) for integers v (Q odd, gcd(Q, t) = 1: never a tie)."""
+    return [(2 * t * v + Q) // (2 * Q) for v in ints]
+
+
+def relinearize(prm: Params, d, rlk) -> Ct:
+    """(d0, d1, d2) -> (d0 + u0, d1 + u1) with (u0, u1) the key switch of d2 from s^2 to s."""
+    moduli = prm.q[: d[0].shape[0]]
+    u0, u1 = keyswitch(prm, d[2], rlk)
+    return Ct(rns_add(d[0], u0, moduli), rns_add(d[1], u1, moduli))
 
 
 # ---------------------------------------------------------------- key switching

@@ -16,6 +16,10 @@ def setup(request):
     return prm, s
 
 
+def encrypt_slots(prm, s, v, seed):
+    return bfv.encrypt(prm, s, encoder.encode(v, prm), seed)
+
+
 def rand_slots(prm, seed):
     return np.random.default_rng(seed).integers(0, prm.t, prm.n)
 
@@ -167,3 +171,37 @@ def test_planted_moddown_slip_is_caught(monkeypatch):
     half = prm.n // 2
     want = np.concatenate([np.roll(v[:half], -1), np.roll(v[half:], -1)])
     assert not (encoder.decode(bfv.decrypt(prm, s, out), prm) == want).all()
+
+
+def test_multiply_three_component_decryption_and_relinearisation(setup):
+    """(d0, d1, d2) decrypts under (1, s, s^2) to the slot-wise product; after relinearising
+    with the s^2 -> s key, (c0, c1) decrypts to it under s (Sec. 2.1's homomorphic multiply)."""
+    prm, s = setup
+    rng = np.random.default_rng(12)
+    v, w = rng.integers(0, prm.t, prm.n), rng.integers(0, prm.t, prm.n)
+    a = encrypt_slots(prm, s, v, 21)
+    b = encrypt_slots(prm, s, w, 22)
+    d = bfv.multiply(prm, a, b)
+    # three-component phase d0 + d1 s + d2 s^2
+    sr = bfv.to_rns(s, prm.q)
+    s2 = bfv.rns_mul(sr, sr, prm, prm.q)
+    x = bfv.rns_add(bfv.rns_add(d[0], bfv.rns_mul(d[1], sr, prm, prm.q), prm.q),
+                    bfv.rns_mul(d[2], s2, prm, prm.q), prm.q)
+    vals, Q = bfv.crt(x, prm.q)
+    m = np.array([((prm.t * v_ + (Q - 1) // 2) // Q) % prm.t for v_ in vals], dtype=np.int64)
+    assert (encoder.decode(m, prm) == (v * w) % prm.t).all()
+    c = bfv.relinearize(prm, d, bfv.relin_key(prm, s, 23))
+    assert (encoder.decode(bfv.decrypt(prm, s, c), prm) == (v * w) % prm.t).all()
+    assert bfv.noise_bits(prm, s, c)[1] > 20
+
+
+def test_planted_scaling_slip_in_multiply_is_caught(monkeypatch, setup):
+    """Dropping the t/Q scaling of the tensor product must break the product."""
+    prm, s = setup
+    rng = np.random.default_rng(13)
+    v, w = rng.integers(0, prm.t, prm.n), rng.integers(0, prm.t, prm.n)
+    a, b = encrypt_slots(prm, s, v, 31), encrypt_slots(prm, s, w, 32)
+    rlk = bfv.relin_key(prm, s, 33)
+    monkeypatch.setattr(bfv, "scale_round", lambda ints, t, Q: ints)
+    bad = bfv.relinearize(prm, bfv.multiply(prm, a, b), rlk)
+    assert not (encoder.decode(bfv.decrypt(prm, s, bad), prm) == (v * w) % prm.t).all()
