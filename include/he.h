@@ -43,6 +43,9 @@ enum { HE_DP_DOT = 0, HE_DP_SHIFT = 1, HE_DP_SHIFT_EXT = 2, HE_CP_CP = 3 };  /* 
 
 /* Rotation step that swaps the two rows of slots (Galois element 2N - 1). */
 #define HE_ROW_SWAP ((int32_t)0x7fffffff)
+/* Pseudo-step naming the relinearisation key (switching s^2 back to s) in he_keygen_galois,
+ * he_load_keys and he_export_galois; he_multiply needs it. */
+#define HE_RELIN_KEY ((int32_t)0x80000000)
 
 typedef struct he_ctx he_ctx;
 
@@ -181,6 +184,14 @@ int he_rotate_hoisted(he_ctx* ctx, const he_ct* in, const int32_t* steps, int h,
 int he_mul_plain_acc(he_ctx* ctx, const he_ct* cts, const uint64_t* pts, int n, he_ct* acc);
 /* AddCC: out = a + b (same level and domain; out may alias an input). */
 int he_add(he_ctx* ctx, const he_ct* a, const he_ct* b, he_ct* out);
+/* Ciphertext product with relinearisation (Sec. 2.1's homomorphic multiplication; with a = b
+ * the square x^2 the paper uses as activation, Sec. 3): out decrypts to the slot-wise product.
+ * Exactly round(t/Q (a0 + a1 s)(b0 + b1 s)) coefficient-wise -- the centred lifts are
+ * multiplied over an auxiliary basis B (prod B > N Q, chosen by the context) and the scaling
+ * is decided on multi-word integers -- then the s^2 component is key-switched with the key of
+ * step HE_RELIN_KEY.  a, b, out: NTT domain, full level (out may alias an input).
+ * HE_ENOKEY without the relinearisation key. */
+int he_multiply(he_ctx* ctx, const he_ct* a, const he_ct* b, he_ct* out);
 /* Modulus switch: out = round(in / q_last), one limb fewer.  NTT domain in and out. */
 int he_rescale(he_ctx* ctx, const he_ct* in, he_ct* out);
 

@@ -288,6 +288,7 @@ const void* upload_small(he_ctx* ctx, const void* src, size_t bytes) {
 uint32_t galois_elt(const he_ctx* ctx, int32_t step) {
     const uint64_t two_n = 2ull * ctx->N;
     if (step == HE_ROW_SWAP) return (uint32_t)(two_n - 1);
+    if (step == HE_RELIN_KEY) return 0u;          // the s^2 -> s key lives in slot 0
     int64_t half = ctx->N / 2;
     int64_t k = ((int64_t)step % half + half) % half;
     return (uint32_t)h_powmod(5, (uint64_t)k, two_n);
@@ -313,7 +314,8 @@ static void free_ctx(he_ctx* c) {
     if (c->stream || true) cudaStreamSynchronize(c->stream);
     void* ptrs[] = {c->d_mod, c->d_tw_fwd, c->d_tw_inv, c->d_slot_pos, c->d_cdt,
                     c->d_modup_inv, c->d_modup_c, c->d_md_inv, c->d_md_c, c->d_md_pinv,
-                    c->d_rs_inv, c->d_pmodq, c->arena.base, c->staging.dev, c->d_err};
+                    c->d_rs_inv, c->d_pmodq, c->arena.base, c->staging.dev, c->d_err,
+                    c->d_mult_tab};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& kv : c->keys)
@@ -349,16 +351,28 @@ extern "C" int he_ctx_create(const he_params* p, void* stream, he_ctx** out) {
     c->K = p->n_p;
     c->alpha = p->alpha;
     c->dnum = (c->L + c->alpha - 1) / c->alpha;
-    c->n_mod = c->L + c->K + 1;
+    // auxiliary basis for ciphertext products: prod B > N Q (60-bit primes, ~59.9 bits each)
+    c->n_b = (int)((c->L * p->q_bits + p->log_n + 4 + 58) / 59);
+    c->n_mod = c->L + c->K + 1 + c->n_b;
     const uint64_t two_n = 2ull * c->N;
-    std::vector<uint64_t> qs, ps;
+    std::vector<uint64_t> qs, ps, bs;
     if (!gen_primes(p->q_bits, c->L, two_n, {}, qs) || !gen_primes(p->p_bits, c->K, two_n, qs, ps)) {
         delete c;
         return HE_EINVAL;
     }
+    {
+        std::vector<uint64_t> avoid = qs;
+        avoid.insert(avoid.end(), ps.begin(), ps.end());
+        avoid.push_back(p->t);
+        if (!gen_primes(60, c->n_b, two_n, avoid, bs)) {
+            delete c;
+            return HE_EINVAL;
+        }
+    }
     c->mods = qs;
     c->mods.insert(c->mods.end(), ps.begin(), ps.end());
     c->mods.push_back(p->t);
+    c->mods.insert(c->mods.end(), bs.begin(), bs.end());
     c->batching = ((p->t - 1) % two_n) == 0;
     const int N = c->N, L = c->L, K = c->K, LK = L + K;
 
@@ -374,7 +388,7 @@ extern "C" int he_ctx_create(const he_params* p, void* stream, he_ctx** out) {
         M.r2 = h_mulmod(r1, r1, q);
         M.n_inv = h_inv((uint64_t)N % q, q);
         M.n_inv_sh = h_shoup(M.n_inv, q).ws;
-        if (m == c->n_mod - 1 && !c->batching) continue;
+        if (m == c->L + c->K && !c->batching) continue;   // t without a 2N-th root
         uint64_t psi = root_2n(q, two_n), psi_inv = h_inv(psi, q);
         for (int k = 0; k < N; ++k) {
             uint32_t e = h_brv((uint32_t)k, c->logN);
@@ -479,9 +493,10 @@ extern "C" int he_set_stream(he_ctx* ctx, void* stream) {
 }
 
 extern "C" int he_get_moduli(const he_ctx* ctx, uint64_t* out, int cap) {
-    if (!ctx || !out || cap < ctx->n_mod) return HE_EINVAL;
-    for (int i = 0; i < ctx->n_mod; ++i) out[i] = ctx->mods[i];
-    return ctx->n_mod;
+    const int n = ctx ? ctx->L + ctx->K + 1 : 0;
+    if (!ctx || !out || cap < n) return HE_EINVAL;
+    for (int i = 0; i < n; ++i) out[i] = ctx->mods[i];
+    return n;
 }
 
 extern "C" void he_op_counts(const he_ctx* ctx, uint64_t out[4]) {
@@ -768,14 +783,23 @@ extern "C" int he_keygen_galois(he_ctx* ctx, const int64_t* sk, uint64_t seed,
         uint32_t g = galois_elt(ctx, steps[si]);
         uint64_t* key = nullptr;
         if ((rc = he_key_for_generation(ctx, g, &key))) return rc;
-        launch_automorph(ctx, s_ntt, 0, sg, 0, 1, (int)LK, g);   // s(X^g), NTT domain
+        const bool relin = g == 0u;
+        if (relin) {   // target s^2 (NTT domain: s_ntt * s_ntt)
+            HE_CHECK_CUDA(ctx, cudaMemcpyAsync(sg, s_ntt, LK * N * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+            launch_dec_phase_mul(ctx, sg, s_m, (int)LK);
+        } else {
+            launch_automorph(ctx, s_ntt, 0, sg, 0, 1, (int)LK, g);   // s(X^g), NTT domain
+        }
         for (int j = 0; j < ctx->dnum; ++j) {
             uint64_t* b = key + (size_t)(2 * j) * LK * N;
             uint64_t* a = key + (size_t)(2 * j + 1) * LK * N;
-            launch_uniform(ctx, he_stream_state(seed, (4ull << 48) | ((uint64_t)g << 8) | (uint64_t)j),
-                           a, (int)LK, 0, 0);
+            const uint64_t sa = relin ? (6ull << 48) | (uint64_t)j
+                                      : (4ull << 48) | ((uint64_t)g << 8) | (uint64_t)j;
+            const uint64_t se = relin ? (7ull << 48) | (uint64_t)j
+                                      : (5ull << 48) | ((uint64_t)g << 8) | (uint64_t)j;
+            launch_uniform(ctx, he_stream_state(seed, sa), a, (int)LK, 0, 0);
             ntt_forward(ctx, a, 1, 0, (int)LK, 0);
-            launch_gaussian(ctx, he_stream_state(seed, (5ull << 48) | ((uint64_t)g << 8) | (uint64_t)j), d_e);
+            launch_gaussian(ctx, he_stream_state(seed, se), d_e);
             launch_from_signed(ctx, d_e, E, (int)LK, 0);
             ntt_forward(ctx, E, 1, 0, (int)LK, 0);
             int i0 = j * ctx->alpha, i1 = std::min(i0 + ctx->alpha, ctx->L);

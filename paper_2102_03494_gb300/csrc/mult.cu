@@ -1,0 +1,379 @@
+// mult.cu -- BFV ciphertext multiplication with relinearisation (the x^2 activation's core).
+//
+// out = Relin(round(t/Q (a0 + a1 s)(b0 + b1 s))): with a_k, b_k lifted to centred integers,
+//   d0 = a0 b0, d1 = a0 b1 + a1 b0, d2 = a1 b1   over Z[X]/(X^N+1),
+//   d_k' = round(t d_k / Q) mod Q,  out = (d0' + u0, d1' + u1),  (u0, u1) = KeySwitch_{s^2 -> s}(d2').
+// Exact throughout:
+//   1. the centred lift of a_k to an auxiliary basis B (prod B > N Q) is computed exactly per
+//      coefficient from the multi-word CRT value (k_extend_exact);
+//   2. the products are formed limb-wise over Q u B in the NTT domain (k_tensor), so d_k is
+//      known modulo Q B > 2 |d_k|;
+//   3. k_scale_round rebuilds d_k as a signed multi-word integer and computes round(t d_k / Q)
+//      by long division, then reduces it modulo each q_i.
+// The relinearisation key is the switching key for s^2 (Galois element slot 0).
+#include <vector>
+
+#include "eval.cuh"
+#include "kernels.cuh"
+
+#define HE_MW_MAX 40   // 64-bit words of the largest multi-word value (Q B and its products)
+
+namespace {
+
+__device__ __forceinline__ int mw_cmp(const uint64_t* a, const uint64_t* b, int W) {
+    for (int w = W - 1; w >= 0; --w)
+        if (a[w] != b[w]) return a[w] > b[w] ? 1 : -1;
+    return 0;
+}
+
+__device__ __forceinline__ void mw_sub(uint64_t* a, const uint64_t* b, int W) {   // a -= b
+    uint64_t borrow = 0;
+    for (int w = 0; w < W; ++w) {
+        const uint64_t x = a[w], y = b[w];
+        const uint64_t d = x - y - borrow;
+        borrow = (x < y || (x == y && borrow)) ? 1u : 0u;
+        a[w] = d;
+    }
+}
+
+__device__ __forceinline__ void mw_mac(uint64_t* X, const uint64_t* A, int W, uint64_t s) {
+    uint64_t carry = 0;                                   // X (W + 1 words) += A (W words) * s
+    for (int w = 0; w < W; ++w) {
+        unsigned __int128 p = (unsigned __int128)A[w] * s + X[w] + carry;
+        X[w] = (uint64_t)p;
+        carry = (uint64_t)(p >> 64);
+    }
+    X[W] += carry;
+}
+
+__device__ __forceinline__ uint64_t mw_mod(const uint64_t* A, int W, uint64_t q) {
+    unsigned __int128 r = 0;
+    for (int w = W - 1; w >= 0; --w) r = ((r << 64) | A[w]) % q;
+    return (uint64_t)r;
+}
+
+// Centred lift of a_k (coefficient form over Q, rows 0..L-1 of each item) to B (rows L..):
+// x = sum_i y_i Qhat_i - v Q with y_i = [x_i Qhat_i^-1]_{q_i}, v chosen so that x lies in
+// (-Q/2, Q/2]; then x mod b_j = sum_i y_i [Qhat_i]_{b_j} - v [Q]_{b_j}.
+// Table (u64 words): qhinv[L] pairs | Qhat[L][Wq] | Q[Wq+1] | qhat_b[L][nb] pairs | Q_b[nb] pairs
+__global__ void k_extend_exact(uint64_t* __restrict__ data, size_t item_stride, int L, int nb,
+                               int Wq, int b_off, int logN, const ModConst* __restrict__ mods,
+                               const uint64_t* __restrict__ tab) {
+    const int N = 1 << logN;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    uint64_t* x = data + blockIdx.y * item_stride;
+    const uint64_t* qhinv = tab;
+    const uint64_t* Qhat = qhinv + 2 * L;
+    const uint64_t* Qw = Qhat + (size_t)L * Wq;
+    const uint64_t* qhb = Qw + (Wq + 1);
+    const uint64_t* Qb = qhb + 2 * (size_t)L * nb;
+    uint64_t y[32];
+    uint64_t X[HE_MW_MAX + 1];
+    for (int w = 0; w <= Wq; ++w) X[w] = 0;
+    for (int i = 0; i < L; ++i) {
+        y[i] = mul_shoup(x[(size_t)i * N + n], qhinv[2 * i], qhinv[2 * i + 1], mods[i].q);
+        mw_mac(X, Qhat + (size_t)i * Wq, Wq, y[i]);
+    }
+    uint64_t v = 0;
+    while (mw_cmp(X, Qw, Wq + 1) >= 0) {
+        mw_sub(X, Qw, Wq + 1);
+        ++v;
+    }
+    // centred: x > Q/2 (i.e. 2x > Q) -> x - Q
+    uint64_t X2[HE_MW_MAX + 1];
+    uint64_t c = 0;
+    for (int w = 0; w <= Wq; ++w) {
+        X2[w] = (X[w] << 1) | c;
+        c = X[w] >> 63;
+    }
+    if (mw_cmp(X2, Qw, Wq + 1) > 0) ++v;
+    for (int j = 0; j < nb; ++j) {
+        const uint64_t b = mods[b_off + j].q;
+        uint64_t z = 0;
+        for (int i = 0; i < L; ++i) {
+            const uint64_t* p = qhb + 2 * ((size_t)i * nb + j);
+            z = add_mod(z, mul_shoup(y[i], p[0], p[1], b), b);
+        }
+        z = sub_mod(z, mul_shoup(v, Qb[2 * j], Qb[2 * j + 1], b), b);
+        x[(size_t)(L + j) * N + n] = z;
+    }
+}
+
+// Tensor product over the R = L + nb limbs (NTT domain): D = (a0 b0, a0 b1 + a1 b0, a1 b1).
+__global__ void k_tensor(const uint64_t* __restrict__ A, const uint64_t* __restrict__ Bv,
+                         uint64_t* __restrict__ D, int R, int L, int b_off, int logN,
+                         const ModConst* __restrict__ mods) {
+    const int N = 1 << logN;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int r = blockIdx.y;
+    const ModConst M = mods[r < L ? r : b_off + (r - L)];
+    const size_t off = (size_t)r * N + n, RN = (size_t)R * N;
+    const uint64_t a0 = A[off], a1 = A[RN + off];
+    const uint64_t b0 = to_mont(Bv[off], M), b1 = to_mont(Bv[RN + off], M);
+    U128 p0{0, 0}, p1{0, 0}, p2{0, 0};
+    mac128(p0, a0, b0);
+    mac128(p1, a0, b1);
+    mac128(p1, a1, b0);
+    mac128(p2, a1, b1);
+    D[off] = redc(p0, M.q, M.qinv_neg);
+    D[RN + off] = redc(p1, M.q, M.qinv_neg);
+    D[2 * RN + off] = redc(p2, M.q, M.qinv_neg);
+}
+
+// round(t d / Q) mod q_i for each product polynomial (coefficient form over Q u B in, over Q
+// out).  d = sum_m y_m Mhat_m - v M centred in (-M/2, M/2] (M = Q B); |d| = A, then
+// round(t A / Q) = floor((2 t A + Q) / 2Q) by binary long division (no ties: Q odd, gcd(Q, t)
+// = 1), negated back for negative d.
+// Table: mhinv[R] pairs | Mhat[R][Wm] | M[Wm+1] | Q[Wm+2] | Q2[Wm+2]
+__global__ void k_scale_round(const uint64_t* __restrict__ D, uint64_t* __restrict__ S, int R,
+                              int L, int Wm, int b_off, uint64_t t, int logN,
+                              const ModConst* __restrict__ mods, const uint64_t* __restrict__ tab) {
+    const int N = 1 << logN;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int k = blockIdx.y;
+    const uint64_t* d = D + (size_t)k * R * N;
+    const uint64_t* mhinv = tab;
+    const uint64_t* Mhat = mhinv + 2 * R;
+    const uint64_t* Mw = Mhat + (size_t)R * Wm;
+    const uint64_t* Qw = Mw + (Wm + 1);
+    const uint64_t* Q2w = Qw + (Wm + 2);
+    const int W = Wm + 2;
+    uint64_t X[HE_MW_MAX + 2];
+    for (int w = 0; w < W; ++w) X[w] = 0;
+    for (int m = 0; m < R; ++m) {
+        const uint64_t q = mods[m < L ? m : b_off + (m - L)].q;
+        const uint64_t y = mul_shoup(d[(size_t)m * N + n], mhinv[2 * m], mhinv[2 * m + 1], q);
+        mw_mac(X, Mhat + (size_t)m * Wm, Wm, y);
+    }
+    while (mw_cmp(X, Mw, Wm + 1) >= 0) mw_sub(X, Mw, Wm + 1);
+    // sign: d = X - M when 2X > M
+    uint64_t A[HE_MW_MAX + 2];
+    uint64_t c = 0;
+    for (int w = 0; w < W; ++w) {
+        A[w] = (w <= Wm ? (X[w] << 1) | c : c);
+        c = w <= Wm ? X[w] >> 63 : 0;
+    }
+    uint64_t Mpad[HE_MW_MAX + 2];
+    for (int w = 0; w < W; ++w) Mpad[w] = w <= Wm ? Mw[w] : 0;
+    const bool neg = mw_cmp(A, Mpad, W) > 0;
+    for (int w = 0; w < W; ++w) A[w] = w <= Wm ? X[w] : 0;
+    if (neg) {                               // A = M - X
+        uint64_t T[HE_MW_MAX + 2];
+        for (int w = 0; w < W; ++w) T[w] = Mpad[w];
+        mw_sub(T, A, W);
+        for (int w = 0; w < W; ++w) A[w] = T[w];
+    }
+    // num = 2 t A + Q
+    uint64_t num[HE_MW_MAX + 2];
+    for (int w = 0; w < W; ++w) num[w] = 0;
+    {
+        uint64_t carry = 0;
+        for (int w = 0; w < W; ++w) {
+            unsigned __int128 p = (unsigned __int128)A[w] * (2 * t) + carry;
+            num[w] = (uint64_t)p;
+            carry = (uint64_t)(p >> 64);
+        }
+        unsigned __int128 s = 0;
+        for (int w = 0; w < W; ++w) {
+            s += (unsigned __int128)num[w] + Qw[w];
+            num[w] = (uint64_t)s;
+            s >>= 64;
+        }
+    }
+    // quotient = floor(num / 2Q)
+    int top = W - 1;
+    while (top > 0 && num[top] == 0) --top;
+    uint64_t rem[HE_MW_MAX + 2], quo[HE_MW_MAX + 2];
+    for (int w = 0; w < W; ++w) rem[w] = quo[w] = 0;
+    for (int bit = top * 64 + 63; bit >= 0; --bit) {
+        uint64_t cc = (num[bit >> 6] >> (bit & 63)) & 1u;
+        for (int w = 0; w < W; ++w) {                 // rem = (rem << 1) | bit
+            const uint64_t nx = rem[w] >> 63;
+            rem[w] = (rem[w] << 1) | cc;
+            cc = nx;
+        }
+        if (mw_cmp(rem, Q2w, W) >= 0) {
+            mw_sub(rem, Q2w, W);
+            quo[bit >> 6] |= 1ull << (bit & 63);
+        }
+    }
+    uint64_t* s = S + (size_t)k * L * N;
+    for (int i = 0; i < L; ++i) {
+        const uint64_t q = mods[i].q;
+        const uint64_t r = mw_mod(quo, W, q);
+        s[(size_t)i * N + n] = neg ? (r ? q - r : 0) : r;
+    }
+}
+
+uint64_t h_mulmod_(uint64_t a, uint64_t b, uint64_t q) { return (uint64_t)((unsigned __int128)a * b % q); }
+
+void mw_mul_small_h(std::vector<uint64_t>& a, uint64_t m) {
+    unsigned __int128 carry = 0;
+    for (auto& w : a) {
+        unsigned __int128 p = (unsigned __int128)w * m + carry;
+        w = (uint64_t)p;
+        carry = p >> 64;
+    }
+    if (carry) a.push_back((uint64_t)carry);
+}
+
+std::vector<uint64_t> padded(std::vector<uint64_t> v, size_t W) {
+    v.resize(W, 0);
+    return v;
+}
+
+}  // namespace
+
+// Tables of the exact extension (level L) and of the scale-and-round, built once per context.
+static int mult_tables(he_ctx* ctx) {
+    if (ctx->d_mult_tab) return HE_OK;
+    const int L = ctx->L, nb = ctx->n_b, R = L + nb, b_off = ctx->L + ctx->K + 1;
+    std::vector<uint64_t> mods_r(R);
+    for (int m = 0; m < R; ++m) mods_r[m] = ctx->mods[m < L ? m : b_off + (m - L)];
+    std::vector<uint64_t> Q{1}, M{1};
+    for (int i = 0; i < L; ++i) mw_mul_small_h(Q, ctx->mods[i]);
+    for (int m = 0; m < R; ++m) mw_mul_small_h(M, mods_r[m]);
+    const int Wq = (int)Q.size(), Wm = (int)M.size();
+    if (Wm + 2 > HE_MW_MAX) return he_fail(ctx, HE_EINVAL, "he_multiply: modulus too large");
+    std::vector<uint64_t> ext, sc;
+    // extension table
+    for (int i = 0; i < L; ++i) {
+        const uint64_t qi = ctx->mods[i];
+        uint64_t v = 1;
+        for (int k = 0; k < L; ++k)
+            if (k != i) v = h_mulmod_(v, ctx->mods[k] % qi, qi);
+        ShoupPair p = h_shoup(h_inv(v, qi), qi);
+        ext.push_back(p.w);
+        ext.push_back(p.ws);
+    }
+    for (int i = 0; i < L; ++i) {
+        std::vector<uint64_t> qh{1};
+        for (int k = 0; k < L; ++k)
+            if (k != i) mw_mul_small_h(qh, ctx->mods[k]);
+        qh = padded(qh, Wq);
+        ext.insert(ext.end(), qh.begin(), qh.end());
+    }
+    {
+        std::vector<uint64_t> q1 = padded(Q, Wq + 1);
+        ext.insert(ext.end(), q1.begin(), q1.end());
+    }
+    for (int i = 0; i < L; ++i)
+        for (int j = 0; j < nb; ++j) {
+            const uint64_t b = ctx->mods[b_off + j];
+            uint64_t v = 1;
+            for (int k = 0; k < L; ++k)
+                if (k != i) v = h_mulmod_(v, ctx->mods[k] % b, b);
+            ShoupPair p = h_shoup(v, b);
+            ext.push_back(p.w);
+            ext.push_back(p.ws);
+        }
+    for (int j = 0; j < nb; ++j) {
+        const uint64_t b = ctx->mods[b_off + j];
+        uint64_t v = 1;
+        for (int k = 0; k < L; ++k) v = h_mulmod_(v, ctx->mods[k] % b, b);
+        ShoupPair p = h_shoup(v, b);
+        ext.push_back(p.w);
+        ext.push_back(p.ws);
+    }
+    // scale table
+    for (int m = 0; m < R; ++m) {
+        const uint64_t qm = mods_r[m];
+        uint64_t v = 1;
+        for (int k = 0; k < R; ++k)
+            if (k != m) v = h_mulmod_(v, mods_r[k] % qm, qm);
+        ShoupPair p = h_shoup(h_inv(v, qm), qm);
+        sc.push_back(p.w);
+        sc.push_back(p.ws);
+    }
+    for (int m = 0; m < R; ++m) {
+        std::vector<uint64_t> mh{1};
+        for (int k = 0; k < R; ++k)
+            if (k != m) mw_mul_small_h(mh, mods_r[k]);
+        mh = padded(mh, Wm);
+        sc.insert(sc.end(), mh.begin(), mh.end());
+    }
+    {
+        std::vector<uint64_t> m1 = padded(M, Wm + 1);
+        sc.insert(sc.end(), m1.begin(), m1.end());
+        std::vector<uint64_t> q2 = padded(Q, Wm + 2);
+        sc.insert(sc.end(), q2.begin(), q2.end());
+        std::vector<uint64_t> qq = Q;
+        mw_mul_small_h(qq, 2);
+        qq = padded(qq, Wm + 2);
+        sc.insert(sc.end(), qq.begin(), qq.end());
+    }
+    ctx->mult_ext_words = ext.size();
+    ctx->mult_Wq = Wq;
+    ctx->mult_Wm = Wm;
+    std::vector<uint64_t> all = ext;
+    all.insert(all.end(), sc.begin(), sc.end());
+    if (cudaMalloc((void**)&ctx->d_mult_tab, all.size() * 8) != cudaSuccess) {
+        cudaGetLastError();
+        return he_fail(ctx, HE_ENOMEM, "he_multiply: table allocation failed");
+    }
+    HE_CHECK_CUDA(ctx, cudaMemcpy(ctx->d_mult_tab, all.data(), all.size() * 8, cudaMemcpyHostToDevice));
+    return HE_OK;
+}
+
+extern "C" int he_multiply(he_ctx* ctx, const he_ct* a, const he_ct* b, he_ct* out) {
+    if (!ctx) return HE_EINVAL;
+    int rc = check_ct(ctx, a, ctx->L, HE_NTT, "he_multiply a");
+    if (!rc) rc = check_ct(ctx, b, ctx->L, HE_NTT, "he_multiply b");
+    if (!rc) rc = check_ct(ctx, out, ctx->L, -1, "he_multiply out");
+    if (rc) return rc;
+    if (ctx->L > 32) return he_fail(ctx, HE_EINVAL, "he_multiply: at most 32 primes");
+    const uint64_t* rlk = nullptr;
+    if ((rc = he_get_key(ctx, 0u, &rlk)))
+        return he_fail(ctx, HE_ENOKEY, "he_multiply: no relinearisation key (step HE_RELIN_KEY)");
+    if ((rc = mult_tables(ctx))) return rc;
+    const int L = ctx->L, nb = ctx->n_b, R = L + nb, b_off = ctx->L + ctx->K + 1;
+    const size_t N = ctx->N, ct = 2 * (size_t)L * N, ext = 2 * (size_t)R * N;
+    const bool same = a->data == b->data;
+    if ((rc = arena_reserve(ctx, 2 * ext + 3 * (size_t)R * N + 3 * (size_t)L * N +
+                                       rot_scratch_per_item(ctx) + 256)))
+        return rc;
+    arena_reset(ctx);
+    uint64_t* A = arena_take(ctx, ext);
+    uint64_t* Bx = same ? A : arena_take(ctx, ext);
+    uint64_t* D = arena_take(ctx, 3 * (size_t)R * N);
+    uint64_t* S = arena_take(ctx, 3 * (size_t)L * N);
+    RotBufs rb = rot_bufs_take(ctx, 1);
+    const uint64_t* ext_tab = ctx->d_mult_tab;
+    const uint64_t* sc_tab = ctx->d_mult_tab + ctx->mult_ext_words;
+    const he_ct* ins[2] = {a, b};
+    uint64_t* bufs[2] = {A, Bx};
+    for (int u = 0; u < (same ? 1 : 2); ++u) {
+        uint64_t* X = bufs[u];
+        for (int k = 0; k < 2; ++k)
+            HE_CHECK_CUDA(ctx, cudaMemcpyAsync(X + (size_t)k * R * N, ins[u]->data + (size_t)k * L * N,
+                                               (size_t)L * N * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+        ntt_inverse(ctx, X, 2, (size_t)R * N, L, 0);
+        ++ctx->launches;
+        k_extend_exact<<<dim3((N + 127) / 128, 2), 128, 0, ctx->stream>>>(
+            X, (size_t)R * N, L, nb, ctx->mult_Wq, b_off, ctx->logN, ctx->d_mod, ext_tab);
+        ntt_forward(ctx, X, 2, (size_t)R * N, L, 0);
+        ntt_forward(ctx, X + (size_t)L * N, 2, (size_t)R * N, nb, b_off);
+    }
+    ++ctx->launches;
+    k_tensor<<<dim3((N + 255) / 256, R), 256, 0, ctx->stream>>>(A, Bx, D, R, L, b_off, ctx->logN,
+                                                                ctx->d_mod);
+    ntt_inverse(ctx, D, 3, (size_t)R * N, L, 0);
+    ntt_inverse(ctx, D + (size_t)L * N, 3, (size_t)R * N, nb, b_off);
+    ++ctx->launches;
+    k_scale_round<<<dim3((N + 127) / 128, 3), 128, 0, ctx->stream>>>(
+        D, S, R, L, ctx->mult_Wm, b_off, ctx->prm.t, ctx->logN, ctx->d_mod, sc_tab);
+    ntt_forward(ctx, S, 3, (size_t)L * N, L, 0);
+    // relinearise: (d0, d1) + KeySwitch_{s^2 -> s}(d2); S + L N is a [2][L][N] view (d1, d2)
+    auto bp = upload_ptrs(ctx, {S});
+    auto op = upload_out_ptrs(ctx, {out->data});
+    if (!bp || !op) return he_fail(ctx, HE_ECUDA, "pointer table upload failed");
+    modup_items(ctx, S + (size_t)L * N, 1, 1u, rb);
+    ks_items(ctx, 1, rlk, 1u, 1u, nullptr, bp, op, rb);
+    out->domain = HE_NTT;
+    ctx->ops[3] += 1;
+    (void)ct;
+    return he_launch_check(ctx, "he_multiply");
+}

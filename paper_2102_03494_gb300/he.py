@@ -14,6 +14,7 @@ HE_OK, HE_EINVAL, HE_ENOMEM, HE_ENOKEY, HE_ECUDA, HE_ETIMEOUT = 0, -1, -2, -3, -
 HE_COEFF, HE_NTT = 0, 1
 HE_DP_DOT, HE_DP_SHIFT, HE_DP_SHIFT_EXT, HE_CP_CP = 0, 1, 2, 3
 HE_ROW_SWAP = 0x7FFFFFFF
+HE_RELIN_KEY = -0x80000000
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libhe.so")
@@ -74,6 +75,7 @@ _SIGS = {
     "he_mul_plain_acc": ([_P, _CTP, _P, ctypes.c_int, _CTP], ctypes.c_int),
     "he_add": ([_P, _CTP, _CTP, _CTP], ctypes.c_int),
     "he_rescale": ([_P, _CTP, _CTP], ctypes.c_int),
+    "he_multiply": ([_P, _CTP, _CTP, _CTP], ctypes.c_int),
     "he_ffconv_layer": ([_P, _CTP, _I32P, _I32P, ctypes.POINTER(HeLayout), _CTP], ctypes.c_int),
     "he_ffconv_layer_batch": ([_P, _CTP, ctypes.c_int, _I32P, _I32P, ctypes.POINTER(HeLayout), _CTP],
                               ctypes.c_int),
@@ -310,6 +312,13 @@ class Context:
         out = self.new_ct(level=a.shape[-2]) if out is None else out
         x, y, z = self.ct_struct(a, domain), self.ct_struct(b, domain), self.ct_struct(out, domain)
         self._ck(lib().he_add(self.h, ctypes.byref(x), ctypes.byref(y), ctypes.byref(z)), "he_add")
+        return out
+
+    def he_multiply(self, a, b, out=None):
+        out = self.new_ct() if out is None else out
+        x, y, z = self.ct_struct(a), self.ct_struct(b), self.ct_struct(out)
+        self._ck(lib().he_multiply(self.h, ctypes.byref(x), ctypes.byref(y), ctypes.byref(z)),
+                 "he_multiply")
         return out
 
     def he_rescale(self, ct, out=None):
