@@ -192,6 +192,9 @@ int he_add(he_ctx* ctx, const he_ct* a, const he_ct* b, he_ct* out);
  * step HE_RELIN_KEY.  a, b, out: NTT domain, full level (out may alias an input).
  * HE_ENOKEY without the relinearisation key. */
 int he_multiply(he_ctx* ctx, const he_ct* a, const he_ct* b, he_ct* out);
+/* The same for n pairs: out[i] = a[i] b[i] (out[i] may alias a[i] or b[i]); pairs with
+ * a[i] == b[i] for every i take the square path (one lift instead of two). */
+int he_multiply_batch(he_ctx* ctx, const he_ct* a, const he_ct* b, int n, he_ct* out);
 /* Modulus switch: out = round(in / q_last), one limb fewer.  NTT domain in and out. */
 int he_rescale(he_ctx* ctx, const he_ct* in, he_ct* out);
 
@@ -231,6 +234,48 @@ int he_ffconv_layer_batch(he_ctx* ctx, const he_ct* ct_in, int B, const int32_t*
  * returns the count (or HE_EINVAL for a layout that does not fit the ring). */
 int he_ffconv_required_steps(const he_ctx* ctx, const he_layout* layout, int32_t* steps_out,
                              int cap);
+
+/* ---- three-layer network (Table VIII's pipeline) ---------------------------------- */
+
+/* Fully connected layer as DensePack dot products (Sec. 3: a fully connected layer is a
+ * convolution whose filter covers the whole input), on B ciphertexts with shared weights.
+ * Input value x_i sits at slot pos[i] of row 0 and repeats with period `period` (a power of
+ * two, M <= period <= N/2 with M the smallest power of two >= n_out; period = N/2 for an
+ * input that does not repeat; row 1 and every other slot of a period must be zero).
+ * weights: host int32 [n_out][n_in]; pos: host int32 [n_in], distinct, in [0, period).
+ * Output: y_j = sum_i weights[j][i] x_i (mod t) at every slot p of row 0 with p mod M = j,
+ * zero where p mod M >= n_out (the output repeats with period M).  Schedule: the M diagonal
+ * plaintexts diag_k[p] = weights[p mod M][i] where (p + k) mod period = pos[i]; the M - 1
+ * hoisted rotations of x summed with them in Q u P and divided by P once; then
+ * log2(period / M) rotate-and-sum steps z <- z + rot(z, M 2^e).  Keys: steps 1 .. M-1 and
+ * M 2^e.  in, out: full level, NTT domain (out may alias in). */
+int he_fc_layer_batch(he_ctx* ctx, const he_ct* in, int B, const int32_t* weights,
+                      const int32_t* pos, int n_in, int n_out, int period, he_ct* out);
+/* Channel combine (Table VIII, "combine to one vector"): out[b] = in[b n_ch] +
+ * sum_{c >= 1} rot(in[b n_ch + c], -c block), n_ch - 1 rotations per image.  in: [B][n_ch]
+ * ciphertexts, full level, NTT domain. */
+int he_combine_batch(he_ctx* ctx, const he_ct* in, int B, int n_ch, int block, he_ct* out);
+
+/* Shape of the network: the FFConv layer (modswitch 0, outputs in row 0), then x^2, a fully
+ * connected layer of m1 outputs over the O_c O_h O_w layer outputs (flattened in
+ * (c, oh, ow) order), x^2, and a fully connected layer of m2 outputs. */
+typedef struct {
+    he_layout conv;
+    int32_t m1, m2;
+} he_net;
+/* Steps whose keys the network needs (the layer's, the combine's -c blk mod N/2, both
+ * fully connected layers'), then HE_RELIN_KEY; count returned, at most cap written. */
+int he_net_required_steps(const he_ctx* ctx, const he_net* net, int32_t* steps_out, int cap);
+/* The network on B images: he_ffconv_layer_batch, he_combine_batch with block = the smallest
+ * power of two above every layer output slot, he_multiply_batch (square), he_fc_layer_batch
+ * (positions c block + slot(oh, ow), period N/2), square, he_fc_layer_batch (positions
+ * 0 .. m1-1, period next_pow2(m1)).  in: B ciphertexts (B K Im2Col columns for HE_CP_CP);
+ * lowrank_w / restore_w as for the layer; fc1_w host int32 [m1][O_c O_h O_w]; fc2_w host
+ * int32 [m2][m1]; out[B]: full level, z2_j at slots p of row 0 with p mod next_pow2(m2) = j.
+ * Intermediate ciphertexts live in a context-owned device buffer (grow-only). */
+int he_net_batch(he_ctx* ctx, const he_ct* in, int B, const int32_t* lowrank_w,
+                 const int32_t* restore_w, const int32_t* fc1_w, const int32_t* fc2_w,
+                 const he_net* net, he_ct* out);
 
 /* ---- primitives for measurement --------------------------------------------------- */
 

@@ -315,7 +315,7 @@ static void free_ctx(he_ctx* c) {
     void* ptrs[] = {c->d_mod, c->d_tw_fwd, c->d_tw_inv, c->d_slot_pos, c->d_cdt,
                     c->d_modup_inv, c->d_modup_c, c->d_md_inv, c->d_md_c, c->d_md_pinv,
                     c->d_rs_inv, c->d_pmodq, c->arena.base, c->staging.dev, c->d_err,
-                    c->d_mult_tab};
+                    c->d_mult_tab, c->net.base};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& kv : c->keys)

@@ -798,6 +798,13 @@ void launch_add(he_ctx* c, const uint64_t* const* a, const uint64_t* const* b,
     k_add<<<grid_nx(items, c->N, 2 * L), 256, 0, c->stream>>>(a, b, o, L, 2, c->logN, c->d_mod);
 }
 
+void launch_add_rows(he_ctx* c, const uint64_t* const* a, const uint64_t* const* b,
+                     uint64_t* const* o, int items, int rows_per_poly) {
+    ++c->launches;
+    k_add<<<grid_nx(items, c->N, 2 * rows_per_poly), 256, 0, c->stream>>>(a, b, o, rows_per_poly, 2,
+                                                                          c->logN, c->d_mod);
+}
+
 void launch_to_mont(he_ctx* c, uint64_t* data, int items, int rows, int period, int mod_off) {
     ++c->launches;
     k_to_mont<<<grid_nx(items, c->N, rows), 256, 0, c->stream>>>(data, rows, period, mod_off,

@@ -42,6 +42,9 @@ void launch_convpack(he_ctx* c, const uint64_t* x, int B, int r, int O_c, const 
                      uint64_t* const* outp, int L);
 void launch_add(he_ctx* c, const uint64_t* const* a, const uint64_t* const* b,
                 uint64_t* const* o, int items, int L);
+// Pairs of polynomials over the first rows_per_poly moduli (e.g. Q u P): o = a + b.
+void launch_add_rows(he_ctx* c, const uint64_t* const* a, const uint64_t* const* b,
+                     uint64_t* const* o, int items, int rows_per_poly);
 void launch_to_mont(he_ctx* c, uint64_t* data, int items, int rows, int period, int mod_off);
 void launch_from_mont(he_ctx* c, uint64_t* data, int items, int rows, int period, int mod_off);
 void launch_gather_last(he_ctx* c, const uint64_t* const* xp, uint64_t* last, int items, int L);

@@ -11,6 +11,7 @@
 //   3. k_scale_round rebuilds d_k as a signed multi-word integer and computes round(t d_k / Q)
 //      by long division, then reduces it modulo each q_i.
 // The relinearisation key is the switching key for s^2 (Galois element slot 0).
+#include <algorithm>
 #include <vector>
 
 #include "eval.cuh"
@@ -100,7 +101,8 @@ __global__ void k_extend_exact(uint64_t* __restrict__ data, size_t item_stride, 
     }
 }
 
-// Tensor product over the R = L + nb limbs (NTT domain): D = (a0 b0, a0 b1 + a1 b0, a1 b1).
+// Tensor product over the R = L + nb limbs (NTT domain): D = (a0 b0, a0 b1 + a1 b0, a1 b1);
+// item blockIdx.z, A and Bv [items][2][R][N], D [items][3][R][N].
 __global__ void k_tensor(const uint64_t* __restrict__ A, const uint64_t* __restrict__ Bv,
                          uint64_t* __restrict__ D, int R, int L, int b_off, int logN,
                          const ModConst* __restrict__ mods) {
@@ -109,7 +111,11 @@ __global__ void k_tensor(const uint64_t* __restrict__ A, const uint64_t* __restr
     if (n >= N) return;
     const int r = blockIdx.y;
     const ModConst M = mods[r < L ? r : b_off + (r - L)];
-    const size_t off = (size_t)r * N + n, RN = (size_t)R * N;
+    const size_t RN = (size_t)R * N;
+    const size_t off = (size_t)r * N + n, it = blockIdx.z;
+    A += it * 2 * RN;
+    Bv += it * 2 * RN;
+    D += it * 3 * RN;
     const uint64_t a0 = A[off], a1 = A[RN + off];
     const uint64_t b0 = to_mont(Bv[off], M), b1 = to_mont(Bv[RN + off], M);
     U128 p0{0, 0}, p1{0, 0}, p2{0, 0};
@@ -126,15 +132,18 @@ __global__ void k_tensor(const uint64_t* __restrict__ A, const uint64_t* __restr
 // out).  d = sum_m y_m Mhat_m - v M centred in (-M/2, M/2] (M = Q B); |d| = A, then
 // round(t A / Q) = floor((2 t A + Q) / 2Q) by binary long division (no ties: Q odd, gcd(Q, t)
 // = 1), negated back for negative d.
+// blockIdx.y = 3 item + k; d0, d1 go to S01 [items][2][L][N], d2 to the c1 half of
+// T2 [items][2][L][N] (the layout the key switch reads).
 // Table: mhinv[R] pairs | Mhat[R][Wm] | M[Wm+1] | Q[Wm+2] | Q2[Wm+2]
-__global__ void k_scale_round(const uint64_t* __restrict__ D, uint64_t* __restrict__ S, int R,
-                              int L, int Wm, int b_off, uint64_t t, int logN,
-                              const ModConst* __restrict__ mods, const uint64_t* __restrict__ tab) {
+__global__ void k_scale_round(const uint64_t* __restrict__ D, uint64_t* __restrict__ S01,
+                              uint64_t* __restrict__ T2, int R, int L, int Wm, int b_off,
+                              uint64_t t, int logN, const ModConst* __restrict__ mods,
+                              const uint64_t* __restrict__ tab) {
     const int N = 1 << logN;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
-    const int k = blockIdx.y;
-    const uint64_t* d = D + (size_t)k * R * N;
+    const int it = blockIdx.y / 3, k = blockIdx.y - 3 * it;
+    const uint64_t* d = D + (size_t)blockIdx.y * R * N;
     const uint64_t* mhinv = tab;
     const uint64_t* Mhat = mhinv + 2 * R;
     const uint64_t* Mw = Mhat + (size_t)R * Wm;
@@ -200,7 +209,7 @@ __global__ void k_scale_round(const uint64_t* __restrict__ D, uint64_t* __restri
             quo[bit >> 6] |= 1ull << (bit & 63);
         }
     }
-    uint64_t* s = S + (size_t)k * L * N;
+    uint64_t* s = k < 2 ? S01 + ((size_t)it * 2 + k) * L * N : T2 + ((size_t)it * 2 + 1) * L * N;
     for (int i = 0; i < L; ++i) {
         const uint64_t q = mods[i].q;
         const uint64_t r = mw_mod(quo, W, q);
@@ -318,62 +327,92 @@ static int mult_tables(he_ctx* ctx) {
     return HE_OK;
 }
 
-extern "C" int he_multiply(he_ctx* ctx, const he_ct* a, const he_ct* b, he_ct* out) {
-    if (!ctx) return HE_EINVAL;
-    int rc = check_ct(ctx, a, ctx->L, HE_NTT, "he_multiply a");
-    if (!rc) rc = check_ct(ctx, b, ctx->L, HE_NTT, "he_multiply b");
-    if (!rc) rc = check_ct(ctx, out, ctx->L, -1, "he_multiply out");
-    if (rc) return rc;
-    if (ctx->L > 32) return he_fail(ctx, HE_EINVAL, "he_multiply: at most 32 primes");
-    const uint64_t* rlk = nullptr;
-    if ((rc = he_get_key(ctx, 0u, &rlk)))
-        return he_fail(ctx, HE_ENOKEY, "he_multiply: no relinearisation key (step HE_RELIN_KEY)");
-    if ((rc = mult_tables(ctx))) return rc;
+// Products of n pairs (a[i], b[i]) into out[i], in chunks that bound the scratch.
+static int multiply_items(he_ctx* ctx, const he_ct* a, const he_ct* b, int n, he_ct* out,
+                          const uint64_t* rlk) {
     const int L = ctx->L, nb = ctx->n_b, R = L + nb, b_off = ctx->L + ctx->K + 1;
     const size_t N = ctx->N, ct = 2 * (size_t)L * N, ext = 2 * (size_t)R * N;
-    const bool same = a->data == b->data;
-    if ((rc = arena_reserve(ctx, 2 * ext + 3 * (size_t)R * N + 3 * (size_t)L * N +
-                                       rot_scratch_per_item(ctx) + 256)))
-        return rc;
-    arena_reset(ctx);
-    uint64_t* A = arena_take(ctx, ext);
-    uint64_t* Bx = same ? A : arena_take(ctx, ext);
-    uint64_t* D = arena_take(ctx, 3 * (size_t)R * N);
-    uint64_t* S = arena_take(ctx, 3 * (size_t)L * N);
-    RotBufs rb = rot_bufs_take(ctx, 1);
+    const size_t per_item = 2 * ext + 3 * (size_t)R * N + 2 * ct + rot_scratch_per_item(ctx);
+    const int chunk = (int)std::max<size_t>(1, std::min<size_t>(n, (size_t(3) << 30) / 8 / per_item));
     const uint64_t* ext_tab = ctx->d_mult_tab;
     const uint64_t* sc_tab = ctx->d_mult_tab + ctx->mult_ext_words;
-    const he_ct* ins[2] = {a, b};
-    uint64_t* bufs[2] = {A, Bx};
-    for (int u = 0; u < (same ? 1 : 2); ++u) {
-        uint64_t* X = bufs[u];
-        for (int k = 0; k < 2; ++k)
-            HE_CHECK_CUDA(ctx, cudaMemcpyAsync(X + (size_t)k * R * N, ins[u]->data + (size_t)k * L * N,
-                                               (size_t)L * N * 8, cudaMemcpyDeviceToDevice, ctx->stream));
-        ntt_inverse(ctx, X, 2, (size_t)R * N, L, 0);
+    int rc;
+    for (int i0 = 0; i0 < n; i0 += chunk) {
+        const int m = std::min(chunk, n - i0);
+        bool same = true;
+        for (int i = 0; i < m; ++i) same &= a[i0 + i].data == b[i0 + i].data;
+        if ((rc = arena_reserve(ctx, (size_t)m * per_item + 16 * 32))) return rc;
+        arena_reset(ctx);
+        uint64_t* A = arena_take(ctx, (size_t)m * ext);
+        uint64_t* Bx = same ? A : arena_take(ctx, (size_t)m * ext);
+        uint64_t* D = arena_take(ctx, (size_t)m * 3 * R * N);
+        uint64_t* S01 = arena_take(ctx, (size_t)m * ct);
+        uint64_t* T2 = arena_take(ctx, (size_t)m * ct);
+        RotBufs rb = rot_bufs_take(ctx, m);
+        if (!rb.v) return he_fail(ctx, HE_ENOMEM, "he_multiply: scratch");
+        for (int u = 0; u < (same ? 1 : 2); ++u) {
+            const he_ct* src = u ? b : a;
+            uint64_t* X = u ? Bx : A;
+            for (int i = 0; i < m; ++i)
+                for (int k = 0; k < 2; ++k)
+                    HE_CHECK_CUDA(ctx, cudaMemcpyAsync(X + (size_t)i * ext + (size_t)k * R * N,
+                                                       src[i0 + i].data + (size_t)k * L * N,
+                                                       (size_t)L * N * 8, cudaMemcpyDeviceToDevice,
+                                                       ctx->stream));
+            ntt_inverse(ctx, X, 2 * m, (size_t)R * N, L, 0);
+            ++ctx->launches;
+            k_extend_exact<<<dim3((unsigned)((N + 127) / 128), 2 * m), 128, 0, ctx->stream>>>(
+                X, (size_t)R * N, L, nb, ctx->mult_Wq, b_off, ctx->logN, ctx->d_mod, ext_tab);
+            ntt_forward(ctx, X, 2 * m, (size_t)R * N, L, 0);
+            ntt_forward(ctx, X + (size_t)L * N, 2 * m, (size_t)R * N, nb, b_off);
+        }
         ++ctx->launches;
-        k_extend_exact<<<dim3((N + 127) / 128, 2), 128, 0, ctx->stream>>>(
-            X, (size_t)R * N, L, nb, ctx->mult_Wq, b_off, ctx->logN, ctx->d_mod, ext_tab);
-        ntt_forward(ctx, X, 2, (size_t)R * N, L, 0);
-        ntt_forward(ctx, X + (size_t)L * N, 2, (size_t)R * N, nb, b_off);
+        k_tensor<<<dim3((unsigned)((N + 255) / 256), R, m), 256, 0, ctx->stream>>>(
+            A, Bx, D, R, L, b_off, ctx->logN, ctx->d_mod);
+        ntt_inverse(ctx, D, 3 * m, (size_t)R * N, L, 0);
+        ntt_inverse(ctx, D + (size_t)L * N, 3 * m, (size_t)R * N, nb, b_off);
+        ++ctx->launches;
+        k_scale_round<<<dim3((unsigned)((N + 127) / 128), 3 * m), 128, 0, ctx->stream>>>(
+            D, S01, T2, R, L, ctx->mult_Wm, b_off, ctx->prm.t, ctx->logN, ctx->d_mod, sc_tab);
+        ntt_forward(ctx, S01, 2 * m, (size_t)L * N, L, 0);
+        ntt_forward(ctx, T2 + (size_t)L * N, m, ct, L, 0);
+        // relinearise: out = (d0, d1) + KeySwitch_{s^2 -> s}(d2)
+        std::vector<const uint64_t*> bs(m);
+        std::vector<uint64_t*> os(m);
+        for (int i = 0; i < m; ++i) {
+            bs[i] = S01 + (size_t)i * ct;
+            os[i] = out[i0 + i].data;
+        }
+        auto bp = upload_ptrs(ctx, bs);
+        auto op = upload_out_ptrs(ctx, os);
+        if (!bp || !op) return he_fail(ctx, HE_ECUDA, "pointer table upload failed");
+        modup_items(ctx, T2, m, 1u, rb);
+        ks_items(ctx, m, rlk, 1u, 1u, nullptr, bp, op, rb);
+        for (int i = 0; i < m; ++i) out[i0 + i].domain = HE_NTT;
     }
-    ++ctx->launches;
-    k_tensor<<<dim3((N + 255) / 256, R), 256, 0, ctx->stream>>>(A, Bx, D, R, L, b_off, ctx->logN,
-                                                                ctx->d_mod);
-    ntt_inverse(ctx, D, 3, (size_t)R * N, L, 0);
-    ntt_inverse(ctx, D + (size_t)L * N, 3, (size_t)R * N, nb, b_off);
-    ++ctx->launches;
-    k_scale_round<<<dim3((N + 127) / 128, 3), 128, 0, ctx->stream>>>(
-        D, S, R, L, ctx->mult_Wm, b_off, ctx->prm.t, ctx->logN, ctx->d_mod, sc_tab);
-    ntt_forward(ctx, S, 3, (size_t)L * N, L, 0);
-    // relinearise: (d0, d1) + KeySwitch_{s^2 -> s}(d2); S + L N is a [2][L][N] view (d1, d2)
-    auto bp = upload_ptrs(ctx, {S});
-    auto op = upload_out_ptrs(ctx, {out->data});
-    if (!bp || !op) return he_fail(ctx, HE_ECUDA, "pointer table upload failed");
-    modup_items(ctx, S + (size_t)L * N, 1, 1u, rb);
-    ks_items(ctx, 1, rlk, 1u, 1u, nullptr, bp, op, rb);
-    out->domain = HE_NTT;
-    ctx->ops[3] += 1;
-    (void)ct;
+    ctx->ops[3] += (uint64_t)n;
+    return HE_OK;
+}
+
+extern "C" int he_multiply_batch(he_ctx* ctx, const he_ct* a, const he_ct* b, int n, he_ct* out) {
+    if (!ctx) return HE_EINVAL;
+    if (!a || !b || !out || n < 0) return he_fail(ctx, HE_EINVAL, "he_multiply: null argument");
+    int rc;
+    for (int i = 0; i < n; ++i) {
+        if ((rc = check_ct(ctx, &a[i], ctx->L, HE_NTT, "he_multiply a"))) return rc;
+        if ((rc = check_ct(ctx, &b[i], ctx->L, HE_NTT, "he_multiply b"))) return rc;
+        if ((rc = check_ct(ctx, &out[i], ctx->L, -1, "he_multiply out"))) return rc;
+    }
+    if (ctx->L > 32) return he_fail(ctx, HE_EINVAL, "he_multiply: at most 32 primes");
+    const uint64_t* rlk = nullptr;
+    if (he_get_key(ctx, 0u, &rlk))
+        return he_fail(ctx, HE_ENOKEY, "he_multiply: no relinearisation key (step HE_RELIN_KEY)");
+    if ((rc = mult_tables(ctx))) return rc;
+    if (n == 0) return HE_OK;
+    if ((rc = multiply_items(ctx, a, b, n, out, rlk))) return rc;
     return he_launch_check(ctx, "he_multiply");
+}
+
+extern "C" int he_multiply(he_ctx* ctx, const he_ct* a, const he_ct* b, he_ct* out) {
+    return he_multiply_batch(ctx, a, b, 1, out);
 }

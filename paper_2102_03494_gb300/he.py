@@ -36,6 +36,10 @@ class HeLayout(ctypes.Structure):
                 ("I_c", "I_h", "I_w", "d", "stride", "pad", "r", "O_c", "pack", "modswitch")]
 
 
+class HeNet(ctypes.Structure):
+    _fields_ = [("conv", HeLayout), ("m1", ctypes.c_int32), ("m2", ctypes.c_int32)]
+
+
 class HeError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{msg} (code {code})")
@@ -76,6 +80,13 @@ _SIGS = {
     "he_add": ([_P, _CTP, _CTP, _CTP], ctypes.c_int),
     "he_rescale": ([_P, _CTP, _CTP], ctypes.c_int),
     "he_multiply": ([_P, _CTP, _CTP, _CTP], ctypes.c_int),
+    "he_multiply_batch": ([_P, _CTP, _CTP, ctypes.c_int, _CTP], ctypes.c_int),
+    "he_fc_layer_batch": ([_P, _CTP, ctypes.c_int, _I32P, _I32P, ctypes.c_int, ctypes.c_int,
+                           ctypes.c_int, _CTP], ctypes.c_int),
+    "he_combine_batch": ([_P, _CTP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _CTP], ctypes.c_int),
+    "he_net_required_steps": ([_P, ctypes.POINTER(HeNet), _I32P, ctypes.c_int], ctypes.c_int),
+    "he_net_batch": ([_P, _CTP, ctypes.c_int, _I32P, _I32P, _I32P, _I32P, ctypes.POINTER(HeNet),
+                      _CTP], ctypes.c_int),
     "he_ffconv_layer": ([_P, _CTP, _I32P, _I32P, ctypes.POINTER(HeLayout), _CTP], ctypes.c_int),
     "he_ffconv_layer_batch": ([_P, _CTP, ctypes.c_int, _I32P, _I32P, ctypes.POINTER(HeLayout), _CTP],
                               ctypes.c_int),
@@ -320,6 +331,55 @@ class Context:
         self._ck(lib().he_multiply(self.h, ctypes.byref(x), ctypes.byref(y), ctypes.byref(z)),
                  "he_multiply")
         return out
+
+    def he_multiply_batch(self, a, b, outs=None):
+        outs = [self.new_ct() for _ in a] if outs is None else outs
+        x, y, z = self.ct_array(a), self.ct_array(b), self.ct_array(outs)
+        self._ck(lib().he_multiply_batch(self.h, x, y, len(a), z), "he_multiply_batch")
+        return outs
+
+    def he_fc_layer_batch(self, cts, F, pos, period, outs=None):
+        outs = [self.new_ct() for _ in cts] if outs is None else outs
+        f, pf = _i32(F)
+        ps, pp = _i32(pos)
+        ia, oa = self.ct_array(cts), self.ct_array(outs)
+        self._ck(lib().he_fc_layer_batch(self.h, ia, len(cts), pf, pp, len(ps), f.shape[0], period,
+                                         oa), "he_fc_layer_batch")
+        return outs
+
+    def he_combine_batch(self, cts, n_ch, block, outs=None):
+        """cts: [B][n_ch] ciphertexts flattened image-major."""
+        B = len(cts) // n_ch
+        outs = [self.new_ct() for _ in range(B)] if outs is None else outs
+        ia, oa = self.ct_array(cts), self.ct_array(outs)
+        self._ck(lib().he_combine_batch(self.h, ia, B, n_ch, block, oa), "he_combine_batch")
+        return outs
+
+    @staticmethod
+    def net(lay, m1, m2):
+        return HeNet(lay, m1, m2)
+
+    def he_net_required_steps(self, net):
+        out = np.zeros(8192, dtype=np.int32)
+        n = lib().he_net_required_steps(self.h, ctypes.byref(net), out.ctypes.data_as(_I32P), 8192)
+        if n < 0:
+            raise HeError(n, "he_net_required_steps: shape does not fit the ring")
+        return [int(x) for x in out[:n]]
+
+    def he_net_batch(self, cts_in, W1, W2, F1, F2, net, outs=None):
+        """cts_in: B ciphertexts (B * K Im2Col columns for HE_CP_CP)."""
+        B = len(cts_in)
+        if net.conv.pack == HE_CP_CP:
+            B //= net.conv.d * net.conv.d * net.conv.I_c
+        outs = [self.new_ct() for _ in range(B)] if outs is None else outs
+        ia, oa = self.ct_array(cts_in), self.ct_array(outs)
+        w1, pw1 = _i32(W1)
+        w2, pw2 = _i32(W2)
+        f1, pf1 = _i32(F1)
+        f2, pf2 = _i32(F2)
+        self._ck(lib().he_net_batch(self.h, ia, B, pw1, pw2, pf1, pf2, ctypes.byref(net), oa),
+                 "he_net_batch")
+        return outs
 
     def he_rescale(self, ct, out=None):
         out = self.new_ct(level=ct.shape[-2] - 1) if out is None else out
