@@ -38,6 +38,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", action="store_true",
                     help="run the serving loop (mixed rings, Poisson arrivals) instead")
+    ap.add_argument("--net", action="store_true",
+                    help="time the three-layer network (batch --net-batch, N=2^14) instead")
+    ap.add_argument("--net-batch", type=int, default=64)
     return ap.parse_args()
 
 
@@ -414,6 +417,121 @@ def run_serving(args):
     print(json.dumps(out))
 
 
+NET_LOG_N, NET_N_Q, NET_N_P, NET_ALPHA, NET_M1, NET_M2 = 14, 6, 2, 2, 100, 10
+
+
+def run_net(args):
+    """The three-layer network on a batch of encrypted 1 x 28 x 28 images: FFConv layer
+    (5 x 5 stride 2, r = 2 -> 5 channels, extended-basis schedule), channel combine, x^2,
+    fully connected 845 -> 100, x^2, fully connected 100 -> 10; N = 2^14, 6 x 50-bit q,
+    2 x 60-bit p, alpha = 2.  One step = one batch through the whole network."""
+    import numpy as np
+    import torch
+
+    from paper_2102_03494_gb300 import he, workloads
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    B = args.net_batch
+    shape = workloads.MNIST_LAYER
+    stream = torch.cuda.Stream()
+    ctx = he.Context(log_n=NET_LOG_N, n_q=NET_N_Q, n_p=NET_N_P, alpha=NET_ALPHA, stream=stream)
+    lay = ctx.layout(*shape.astuple(), pack="dp_shift_ext")
+    net = ctx.net(lay, NET_M1, NET_M2)
+    steps = ctx.he_net_required_steps(net)
+    N = 1 << NET_LOG_N
+    ct_bytes = 2 * NET_N_Q * N * 8
+    sk = ctx.he_keygen_secret(1000 + rank)
+    ctx.he_keygen_galois(sk, 2000 + rank, steps)
+    W1, W2 = workloads.weights(0, shape)
+    rng = np.random.default_rng(5)
+    n1 = shape.O_c * ((shape.I_h + 2 * shape.pad - shape.d) // shape.stride + 1) ** 2
+    F1 = rng.integers(-8, 9, (NET_M1, n1))
+    F2 = rng.integers(-8, 9, (NET_M2, NET_M1))
+    xs = workloads.images(rank, shape, B)
+    cts = []
+    for b, x in enumerate(xs):
+        slots = np.zeros(N, dtype=np.int64)
+        slots[: x.size] = x.reshape(-1)
+        cts.append(ctx.he_encrypt(sk, slots, 3000 + b))
+    outs = [ctx.new_ct() for _ in range(B)]
+    torch.cuda.synchronize()
+
+    def step():
+        ctx.he_net_batch(cts, W1, W2, F1, F2, net, outs)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ctx.he_reset_op_counts()
+    l0 = ctx.he_launch_count()
+    ctx.he_phase_times()
+    ctx.he_set_phase_timing(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    phases = ctx.he_phase_times()
+    ctx.he_set_phase_timing(False)
+    launches = ctx.he_launch_count() - l0
+    ops = ctx.he_op_counts()
+    ms = ev0.elapsed_time(ev1)
+
+    h_in = [torch.empty((2, NET_N_Q, N), dtype=torch.int64).pin_memory() for _ in range(B)]
+    for h, c in zip(h_in, cts):
+        h.copy_(c)
+    h_out = [torch.empty((2, NET_N_Q, N), dtype=torch.int64).pin_memory() for _ in range(B)]
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            for h, c in zip(h_in, cts):
+                c.copy_(h, non_blocking=True)
+            step()
+            for h, o in zip(h_out, outs):
+                h.copy_(o, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1)
+    if dist:
+        ms, ms_e2e = max_over_ranks([ms, ms_e2e], "cuda")
+    value = whole_job_rate(B * args.steps, world, ms)
+    if rank != 0:
+        return
+    per_img = {k: v // (B * args.steps) for k, v in ops.items()}
+    line = {"metric": "encrypted 3-layer network throughput (images/s) at N=2^14",
+            "value": value, "unit": "images/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "1x28x28 -> FFConv 5x5 s2 p1 (r=2) -> 5 ch -> combine -> x^2 -> "
+                                   "FC 845->100 -> x^2 -> FC 100->10, N=2^14, 6x50-bit q, "
+                                   "2x60-bit p, alpha=2",
+                       "batch_per_gpu": B, "ms_per_image": ms / args.steps / B,
+                       "galois_keys": len(steps) - 1, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (Galois keys 0.9 GB per step)"},
+            "ops_per_image": per_img,
+            "e2e": {"value": whole_job_rate(B * args.steps, world, ms_e2e), "unit": "images/s",
+                    "h2d_bytes_per_step": B * ct_bytes, "d2h_bytes_per_step": B * ct_bytes,
+                    "ms_per_step": ms_e2e / args.steps},
+            "gpu_launches": launches, "clocks": clk,
+            "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items() if v[1]}}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -421,6 +539,9 @@ def main():
         return
     if args.serving:
         run_serving(args)
+        return
+    if args.net:
+        run_net(args)
         return
     run(args)
 

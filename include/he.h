@@ -113,12 +113,15 @@ uint64_t he_launch_count(const he_ctx* ctx);
  * HE_PHASE_MODUP (hoisting: inverse NTT of c1, ModUp, NTT of the digits), HE_PHASE_TAPS
  * (key switches and tap products: the fused extended-basis kernel, or the per-tap rotations
  * and MACs), HE_PHASE_MODDOWN (ModDown of the channel sums), HE_PHASE_ROTATE (DP_DOT
- * rotate-and-sum and channel folds), HE_PHASE_RESTORE (W2 ConvPack and modulus switch).
+ * rotate-and-sum, channel folds and combines, fully connected rotate-and-sum),
+ * HE_PHASE_RESTORE (W2 ConvPack and modulus switch), HE_PHASE_MULTIPLY (he_multiply(_batch):
+ * lift, tensor, scale and relinearisation).  The fully connected layers time their diagonal
+ * plaintexts, ModUp, tap sums and ModDown under the same phases as the FFConv layer.
  * he_phase_times synchronises the stream, writes the summed milliseconds of each phase to
  * ms_out[0..HE_N_PHASES) and the number of timed spans to calls_out (either may be NULL), and
  * clears the sums.  Enabling adds two event records per phase per call. */
 enum { HE_PHASE_ENCODE = 0, HE_PHASE_MODUP = 1, HE_PHASE_TAPS = 2, HE_PHASE_MODDOWN = 3,
-       HE_PHASE_ROTATE = 4, HE_PHASE_RESTORE = 5, HE_N_PHASES = 8 };
+       HE_PHASE_ROTATE = 4, HE_PHASE_RESTORE = 5, HE_PHASE_MULTIPLY = 6, HE_N_PHASES = 8 };
 int he_set_phase_timing(he_ctx* ctx, int enable);
 int he_phase_times(he_ctx* ctx, double* ms_out, uint64_t* calls_out);
 /* The 20 cumulative thresholds of the error sampler (sigma = 3.2, |e| <= 19), as

@@ -151,7 +151,7 @@ struct he_ctx {
     int n_mod = 0;               // L + K + 1 + n_b: q's, p's, t, then the auxiliary basis B
     int n_b = 0;                 // auxiliary primes for ciphertext multiplication (prod B > N Q)
     uint64_t* d_mult_tab = nullptr;   // exact extension + scale-and-round tables (mult.cu)
-    size_t mult_ext_words = 0;
+    size_t mult_ext_words = 0, mult_extf_off = 0, mult_scf_off = 0;
     int mult_Wq = 0, mult_Wm = 0;
     bool batching = false;       // t = 1 mod 2N: slot encoding available
     std::vector<uint64_t> mods;  // q_0..q_{L-1}, p_0..p_{K-1}, t

@@ -4,14 +4,18 @@
 //   d0 = a0 b0, d1 = a0 b1 + a1 b0, d2 = a1 b1   over Z[X]/(X^N+1),
 //   d_k' = round(t d_k / Q) mod Q,  out = (d0' + u0, d1' + u1),  (u0, u1) = KeySwitch_{s^2 -> s}(d2').
 // Exact throughout:
-//   1. the centred lift of a_k to an auxiliary basis B (prod B > N Q) is computed exactly per
-//      coefficient from the multi-word CRT value (k_extend_exact);
+//   1. the centred lift of a_k to an auxiliary basis B (prod B > 16 N Q) is computed exactly
+//      per coefficient (k_extend_exact): the CRT overflow count v = round(sum_i y_i / q_i)
+//      comes from 128-bit fractions, or from the multi-word CRT value when those cannot
+//      decide it;
 //   2. the products are formed limb-wise over Q u B in the NTT domain (k_tensor), so d_k is
-//      known modulo Q B > 2 |d_k|;
-//   3. k_scale_round rebuilds d_k as a signed multi-word integer and computes round(t d_k / Q)
-//      by long division, then reduces it modulo each q_i.
+//      known modulo Q B > 32 |d_k|;
+//   3. k_scale_round splits t d_k / Q into an integer known modulo each q_i and a small
+//      fraction whose rounding the 128-bit fractions decide (multi-word long division when
+//      they cannot).
 // The relinearisation key is the switching key for s^2 (Galois element slot 0).
 #include <algorithm>
+#include <cstdlib>
 #include <vector>
 
 #include "eval.cuh"
@@ -53,13 +57,40 @@ __device__ __forceinline__ uint64_t mw_mod(const uint64_t* A, int W, uint64_t q)
     return (uint64_t)r;
 }
 
+// 192-bit accumulator (w0 + w1 2^64 + w2 2^128 + w3 2^192) += y (fhi 2^64 + flo).
+__device__ __forceinline__ void acc_mac192(uint64_t& w0, uint64_t& w1, uint64_t& w2, uint64_t& w3,
+                                           uint64_t y, uint64_t fhi, uint64_t flo) {
+    const uint64_t lo0 = y * flo, hi0 = mulhi64(y, flo);
+    const uint64_t lo1 = y * fhi, hi1 = mulhi64(y, fhi);
+    unsigned __int128 s = (unsigned __int128)w0 + lo0;
+    w0 = (uint64_t)s;
+    s >>= 64;
+    s += (unsigned __int128)w1 + hi0 + lo1;
+    w1 = (uint64_t)s;
+    s >>= 64;
+    s += (unsigned __int128)w2 + hi1;
+    w2 = (uint64_t)s;
+    s >>= 64;
+    w3 += (uint64_t)s;
+}
+
+// The rounding of a sum of fractions decided from its fixed-point value: with S the exact sum
+// and (w3, w2, w1, w0) a lower bound of it within 2^-64 (fraction words w1, w0), round(S) is
+// w3 w2 + [w1 >= 2^63] unless w1 = 2^63 - 1, where the bound cannot separate S from 1/2.
+constexpr uint64_t kNearHalf = 0x7fffffffffffffffull;
+
 // Centred lift of a_k (coefficient form over Q, rows 0..L-1 of each item) to B (rows L..):
-// x = sum_i y_i Qhat_i - v Q with y_i = [x_i Qhat_i^-1]_{q_i}, v chosen so that x lies in
-// (-Q/2, Q/2]; then x mod b_j = sum_i y_i [Qhat_i]_{b_j} - v [Q]_{b_j}.
-// Table (u64 words): qhinv[L] pairs | Qhat[L][Wq] | Q[Wq+1] | qhat_b[L][nb] pairs | Q_b[nb] pairs
+// x = sum_i y_i Qhat_i - v Q with y_i = [x_i Qhat_i^-1]_{q_i} and v = round(sum_i y_i / q_i),
+// which puts x in (-Q/2, Q/2] (Q is odd, so the sum is never a half-integer); then
+// x mod b_j = sum_i y_i [Qhat_i]_{b_j} - v [Q]_{b_j}.  v comes from the 128-bit fractions
+// psi_i = floor(2^128 / q_i); when that bound is inconclusive (or force_exact is set) v is
+// taken from the multi-word value of sum_i y_i Qhat_i instead.
+// Tables (u64 words): exact: qhinv[L] pairs | Qhat[L][Wq] | Q[Wq+1] | qhat_b[L][nb] pairs |
+// Q_b[nb] pairs; fast: psi[L] (hi, lo).
 __global__ void k_extend_exact(uint64_t* __restrict__ data, size_t item_stride, int L, int nb,
                                int Wq, int b_off, int logN, const ModConst* __restrict__ mods,
-                               const uint64_t* __restrict__ tab) {
+                               const uint64_t* __restrict__ tab, const uint64_t* __restrict__ fast,
+                               int force_exact) {
     const int N = 1 << logN;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
@@ -70,25 +101,29 @@ __global__ void k_extend_exact(uint64_t* __restrict__ data, size_t item_stride, 
     const uint64_t* qhb = Qw + (Wq + 1);
     const uint64_t* Qb = qhb + 2 * (size_t)L * nb;
     uint64_t y[32];
-    uint64_t X[HE_MW_MAX + 1];
-    for (int w = 0; w <= Wq; ++w) X[w] = 0;
+    uint64_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;
     for (int i = 0; i < L; ++i) {
         y[i] = mul_shoup(x[(size_t)i * N + n], qhinv[2 * i], qhinv[2 * i + 1], mods[i].q);
-        mw_mac(X, Qhat + (size_t)i * Wq, Wq, y[i]);
+        acc_mac192(w0, w1, w2, w3, y[i], fast[2 * i], fast[2 * i + 1]);
     }
-    uint64_t v = 0;
-    while (mw_cmp(X, Qw, Wq + 1) >= 0) {
-        mw_sub(X, Qw, Wq + 1);
-        ++v;
+    uint64_t v = w2 + (w1 >> 63);
+    if (w1 == kNearHalf || force_exact) {
+        uint64_t X[HE_MW_MAX + 1];
+        for (int w = 0; w <= Wq; ++w) X[w] = 0;
+        for (int i = 0; i < L; ++i) mw_mac(X, Qhat + (size_t)i * Wq, Wq, y[i]);
+        v = 0;
+        while (mw_cmp(X, Qw, Wq + 1) >= 0) {
+            mw_sub(X, Qw, Wq + 1);
+            ++v;
+        }
+        uint64_t X2[HE_MW_MAX + 1];   // centred: x > Q/2 (i.e. 2x > Q) -> x - Q
+        uint64_t c = 0;
+        for (int w = 0; w <= Wq; ++w) {
+            X2[w] = (X[w] << 1) | c;
+            c = X[w] >> 63;
+        }
+        if (mw_cmp(X2, Qw, Wq + 1) > 0) ++v;
     }
-    // centred: x > Q/2 (i.e. 2x > Q) -> x - Q
-    uint64_t X2[HE_MW_MAX + 1];
-    uint64_t c = 0;
-    for (int w = 0; w <= Wq; ++w) {
-        X2[w] = (X[w] << 1) | c;
-        c = X[w] >> 63;
-    }
-    if (mw_cmp(X2, Qw, Wq + 1) > 0) ++v;
     for (int j = 0; j < nb; ++j) {
         const uint64_t b = mods[b_off + j].q;
         uint64_t z = 0;
@@ -128,35 +163,21 @@ __global__ void k_tensor(const uint64_t* __restrict__ A, const uint64_t* __restr
     D[2 * RN + off] = redc(p2, M.q, M.qinv_neg);
 }
 
-// round(t d / Q) mod q_i for each product polynomial (coefficient form over Q u B in, over Q
-// out).  d = sum_m y_m Mhat_m - v M centred in (-M/2, M/2] (M = Q B); |d| = A, then
-// round(t A / Q) = floor((2 t A + Q) / 2Q) by binary long division (no ties: Q odd, gcd(Q, t)
-// = 1), negated back for negative d.
-// blockIdx.y = 3 item + k; d0, d1 go to S01 [items][2][L][N], d2 to the c1 half of
-// T2 [items][2][L][N] (the layout the key switch reads).
+// round(t d / Q) by multi-word arithmetic: d = sum_m y_m Mhat_m reduced mod M, centred in
+// (-M/2, M/2]; |d| = A, round(t A / Q) = floor((2 t A + Q) / 2Q) by binary long division (no
+// ties: Q odd, gcd(Q, t) = 1), negated for negative d; written mod each q_i to s[i N].
 // Table: mhinv[R] pairs | Mhat[R][Wm] | M[Wm+1] | Q[Wm+2] | Q2[Wm+2]
-__global__ void k_scale_round(const uint64_t* __restrict__ D, uint64_t* __restrict__ S01,
-                              uint64_t* __restrict__ T2, int R, int L, int Wm, int b_off,
-                              uint64_t t, int logN, const ModConst* __restrict__ mods,
-                              const uint64_t* __restrict__ tab) {
-    const int N = 1 << logN;
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
-    const int it = blockIdx.y / 3, k = blockIdx.y - 3 * it;
-    const uint64_t* d = D + (size_t)blockIdx.y * R * N;
-    const uint64_t* mhinv = tab;
-    const uint64_t* Mhat = mhinv + 2 * R;
+__device__ void scale_round_multiword(const uint64_t* y, uint64_t* s, int n, int N, int R, int L,
+                                      int Wm, uint64_t t, const ModConst* __restrict__ mods,
+                                      const uint64_t* __restrict__ tab) {
+    const uint64_t* Mhat = tab + 2 * R;
     const uint64_t* Mw = Mhat + (size_t)R * Wm;
     const uint64_t* Qw = Mw + (Wm + 1);
     const uint64_t* Q2w = Qw + (Wm + 2);
     const int W = Wm + 2;
     uint64_t X[HE_MW_MAX + 2];
     for (int w = 0; w < W; ++w) X[w] = 0;
-    for (int m = 0; m < R; ++m) {
-        const uint64_t q = mods[m < L ? m : b_off + (m - L)].q;
-        const uint64_t y = mul_shoup(d[(size_t)m * N + n], mhinv[2 * m], mhinv[2 * m + 1], q);
-        mw_mac(X, Mhat + (size_t)m * Wm, Wm, y);
-    }
+    for (int m = 0; m < R; ++m) mw_mac(X, Mhat + (size_t)m * Wm, Wm, y[m]);
     while (mw_cmp(X, Mw, Wm + 1) >= 0) mw_sub(X, Mw, Wm + 1);
     // sign: d = X - M when 2X > M
     uint64_t A[HE_MW_MAX + 2];
@@ -175,9 +196,7 @@ __global__ void k_scale_round(const uint64_t* __restrict__ D, uint64_t* __restri
         mw_sub(T, A, W);
         for (int w = 0; w < W; ++w) A[w] = T[w];
     }
-    // num = 2 t A + Q
-    uint64_t num[HE_MW_MAX + 2];
-    for (int w = 0; w < W; ++w) num[w] = 0;
+    uint64_t num[HE_MW_MAX + 2];             // num = 2 t A + Q
     {
         uint64_t carry = 0;
         for (int w = 0; w < W; ++w) {
@@ -185,21 +204,20 @@ __global__ void k_scale_round(const uint64_t* __restrict__ D, uint64_t* __restri
             num[w] = (uint64_t)p;
             carry = (uint64_t)(p >> 64);
         }
-        unsigned __int128 s = 0;
+        unsigned __int128 sum = 0;
         for (int w = 0; w < W; ++w) {
-            s += (unsigned __int128)num[w] + Qw[w];
-            num[w] = (uint64_t)s;
-            s >>= 64;
+            sum += (unsigned __int128)num[w] + Qw[w];
+            num[w] = (uint64_t)sum;
+            sum >>= 64;
         }
     }
-    // quotient = floor(num / 2Q)
-    int top = W - 1;
+    int top = W - 1;                         // quotient = floor(num / 2Q)
     while (top > 0 && num[top] == 0) --top;
     uint64_t rem[HE_MW_MAX + 2], quo[HE_MW_MAX + 2];
     for (int w = 0; w < W; ++w) rem[w] = quo[w] = 0;
     for (int bit = top * 64 + 63; bit >= 0; --bit) {
         uint64_t cc = (num[bit >> 6] >> (bit & 63)) & 1u;
-        for (int w = 0; w < W; ++w) {                 // rem = (rem << 1) | bit
+        for (int w = 0; w < W; ++w) {        // rem = (rem << 1) | bit
             const uint64_t nx = rem[w] >> 63;
             rem[w] = (rem[w] << 1) | cc;
             cc = nx;
@@ -209,11 +227,77 @@ __global__ void k_scale_round(const uint64_t* __restrict__ D, uint64_t* __restri
             quo[bit >> 6] |= 1ull << (bit & 63);
         }
     }
-    uint64_t* s = k < 2 ? S01 + ((size_t)it * 2 + k) * L * N : T2 + ((size_t)it * 2 + 1) * L * N;
     for (int i = 0; i < L; ++i) {
         const uint64_t q = mods[i].q;
         const uint64_t r = mw_mod(quo, W, q);
         s[(size_t)i * N + n] = neg ? (r ? q - r : 0) : r;
+    }
+}
+
+// round(t d / Q) mod q_i for each product polynomial (coefficient form over Q u B in, over Q
+// out), without multi-word integers.  With d = sum_m y_m Mhat_m - v M (M = Q B), y_m =
+// [d_m Mhat_m^-1]_{m_m}:
+//   t Mhat_i / Q = t B / q_i = a_i + r_i / q_i     (a_i = floor(t B / q_i), r_i = t B mod q_i)
+//   t Mhat_m / Q = t Bhat_j  (m = L + j, an integer),  t M / Q = t B,
+// so t d / Q = I + F with the integer I = sum_i y_i a_i + sum_j y_{L+j} t Bhat_j - v t B and
+// F = sum_i y_i r_i / q_i, and round(t d / Q) = I + round(F) (no ties).  v = round(sum_m
+// y_m / m_m) is unambiguous because |d| <= N Q^2 / 2 < M / 32 (prod B > 16 N Q).  I is formed
+// modulo each q_k from the tables; round(F) from the 128-bit fractions phi_i of r_i / q_i,
+// with the multi-word path when the fixed-point bound is inconclusive (or force_exact).
+// blockIdx.y = 3 item + k; d0, d1 go to S01 [items][2][L][N], d2 to the c1 half of
+// T2 [items][2][L][N] (the layout the key switch reads).
+// Fast table: G[R] (hi, lo) = floor(2^128 / m_m) | phi[L] (hi, lo) | C[L][R + 1] Montgomery:
+// C[k][i] = [a_i]_{q_k}, C[k][L + j] = [t Bhat_j]_{q_k}, C[k][R] = [t B]_{q_k}.
+__global__ void k_scale_round(const uint64_t* __restrict__ D, uint64_t* __restrict__ S01,
+                              uint64_t* __restrict__ T2, int R, int L, int Wm, int b_off,
+                              uint64_t t, int logN, const ModConst* __restrict__ mods,
+                              const uint64_t* __restrict__ tab, const uint64_t* __restrict__ fast,
+                              int force_exact) {
+    const int N = 1 << logN;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int it = blockIdx.y / 3, k = blockIdx.y - 3 * it;
+    const uint64_t* d = D + (size_t)blockIdx.y * R * N;
+    const uint64_t* mhinv = tab;
+    const uint64_t* G = fast;
+    const uint64_t* phi = G + 2 * R;
+    const uint64_t* C = phi + 2 * L;
+    uint64_t* s = k < 2 ? S01 + ((size_t)it * 2 + k) * L * N : T2 + ((size_t)it * 2 + 1) * L * N;
+    uint64_t y[HE_MW_MAX * 2];
+    U128 sv{0, 0};
+    for (int m = 0; m < R; ++m) {
+        const uint64_t q = mods[m < L ? m : b_off + (m - L)].q;
+        y[m] = mul_shoup(d[(size_t)m * N + n], mhinv[2 * m], mhinv[2 * m + 1], q);
+        mac128(sv, y[m], G[2 * m]);                 // y_m / m_m in units of 2^-64
+        const uint64_t h = mulhi64(y[m], G[2 * m + 1]);
+        sv.lo += h;
+        sv.hi += sv.lo < h;
+    }
+    const uint64_t v = sv.hi + (sv.lo >> 63);
+    uint64_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;
+    for (int i = 0; i < L; ++i) acc_mac192(w0, w1, w2, w3, y[i], phi[2 * i], phi[2 * i + 1]);
+    if (w1 == kNearHalf || force_exact) {
+        scale_round_multiword(y, s, n, N, R, L, Wm, t, mods, tab);
+        return;
+    }
+    // round(F) = w3 2^64 + w2 + [w1 >= 2^63] (< 2^66)
+    U128 f{w2 + (w1 >> 63), w3};
+    f.hi += f.lo < (w1 >> 63);
+    for (int kk = 0; kk < L; ++kk) {
+        const ModConst M = mods[kk];
+        const uint64_t* c = C + (size_t)kk * (R + 1);
+        uint64_t acc = 0;
+        for (int m = 0; m < R; ++m) {
+            U128 p{0, 0};
+            mac128(p, y[m], c[m]);
+            acc = add_mod(acc, redc(p, M.q, M.qinv_neg), M.q);
+        }
+        U128 pv{0, 0};
+        mac128(pv, v, c[R]);
+        acc = sub_mod(acc, redc(pv, M.q, M.qinv_neg), M.q);
+        // [round(F)]_{q_k}: f 2^-64 by REDC, then back to f by a Montgomery product with 2^128
+        const uint64_t fr = to_mont(redc(f, M.q, M.qinv_neg), M);
+        s[(size_t)kk * N + n] = add_mod(acc, fr, M.q);
     }
 }
 
@@ -232,6 +316,31 @@ void mw_mul_small_h(std::vector<uint64_t>& a, uint64_t m) {
 std::vector<uint64_t> padded(std::vector<uint64_t> v, size_t W) {
     v.resize(W, 0);
     return v;
+}
+
+// a / d (multi-word by one word): quotient into quo, remainder returned.
+uint64_t mw_divmod_h(const std::vector<uint64_t>& a, uint64_t d, std::vector<uint64_t>& quo) {
+    quo.assign(a.size(), 0);
+    unsigned __int128 r = 0;
+    for (size_t w = a.size(); w-- > 0;) {
+        r = (r << 64) | a[w];
+        quo[w] = (uint64_t)(r / d);
+        r %= d;
+    }
+    return (uint64_t)r;
+}
+
+uint64_t mw_mod_h(const std::vector<uint64_t>& a, uint64_t d) {
+    std::vector<uint64_t> q;
+    return mw_divmod_h(a, d, q);
+}
+
+// floor(x 2^128 / d) for x < d, as (hi, lo)
+void frac128_h(uint64_t x, uint64_t d, std::vector<uint64_t>& out) {
+    unsigned __int128 r = (unsigned __int128)x << 64;
+    out.push_back((uint64_t)(r / d));
+    r = (r % d) << 64;
+    out.push_back((uint64_t)(r / d));
 }
 
 }  // namespace
@@ -314,11 +423,37 @@ static int mult_tables(he_ctx* ctx) {
         qq = padded(qq, Wm + 2);
         sc.insert(sc.end(), qq.begin(), qq.end());
     }
+    // fixed-point tables: psi_i = 2^128 / q_i (extension); G_m = 2^128 / m_m, phi_i =
+    // 2^128 (t B mod q_i) / q_i and the Montgomery constants C[k][.] (scale)
+    std::vector<uint64_t> extf, scf;
+    for (int i = 0; i < L; ++i) frac128_h(1, ctx->mods[i], extf);
+    std::vector<uint64_t> Bw{1}, tB;
+    for (int j = 0; j < nb; ++j) mw_mul_small_h(Bw, ctx->mods[b_off + j]);
+    tB = Bw;
+    mw_mul_small_h(tB, ctx->prm.t);
+    for (int m = 0; m < R; ++m) frac128_h(1, mods_r[m], scf);
+    for (int i = 0; i < L; ++i) frac128_h(mw_mod_h(tB, ctx->mods[i]), ctx->mods[i], scf);
+    std::vector<std::vector<uint64_t>> a(L), tbh(nb);
+    for (int i = 0; i < L; ++i) mw_divmod_h(tB, ctx->mods[i], a[i]);
+    for (int j = 0; j < nb; ++j) {
+        mw_divmod_h(Bw, ctx->mods[b_off + j], tbh[j]);
+        mw_mul_small_h(tbh[j], ctx->prm.t);
+    }
+    for (int k = 0; k < L; ++k) {
+        const uint64_t qk = ctx->mods[k];
+        for (int i = 0; i < L; ++i) scf.push_back(h_to_mont(mw_mod_h(a[i], qk), qk));
+        for (int j = 0; j < nb; ++j) scf.push_back(h_to_mont(mw_mod_h(tbh[j], qk), qk));
+        scf.push_back(h_to_mont(mw_mod_h(tB, qk), qk));
+    }
     ctx->mult_ext_words = ext.size();
+    ctx->mult_extf_off = ext.size() + sc.size();
+    ctx->mult_scf_off = ctx->mult_extf_off + extf.size();
     ctx->mult_Wq = Wq;
     ctx->mult_Wm = Wm;
     std::vector<uint64_t> all = ext;
     all.insert(all.end(), sc.begin(), sc.end());
+    all.insert(all.end(), extf.begin(), extf.end());
+    all.insert(all.end(), scf.begin(), scf.end());
     if (cudaMalloc((void**)&ctx->d_mult_tab, all.size() * 8) != cudaSuccess) {
         cudaGetLastError();
         return he_fail(ctx, HE_ENOMEM, "he_multiply: table allocation failed");
@@ -336,6 +471,12 @@ static int multiply_items(he_ctx* ctx, const he_ct* a, const he_ct* b, int n, he
     const int chunk = (int)std::max<size_t>(1, std::min<size_t>(n, (size_t(3) << 30) / 8 / per_item));
     const uint64_t* ext_tab = ctx->d_mult_tab;
     const uint64_t* sc_tab = ctx->d_mult_tab + ctx->mult_ext_words;
+    const uint64_t* extf_tab = ctx->d_mult_tab + ctx->mult_extf_off;
+    const uint64_t* scf_tab = ctx->d_mult_tab + ctx->mult_scf_off;
+    // HE_MULT_EXACT=1 takes the multi-word rounding path for every coefficient (a check of
+    // that path; the results are the same either way)
+    const char* fe = getenv("HE_MULT_EXACT");
+    const int force_exact = fe && fe[0] == '1';
     int rc;
     for (int i0 = 0; i0 < n; i0 += chunk) {
         const int m = std::min(chunk, n - i0);
@@ -362,7 +503,8 @@ static int multiply_items(he_ctx* ctx, const he_ct* a, const he_ct* b, int n, he
             ntt_inverse(ctx, X, 2 * m, (size_t)R * N, L, 0);
             ++ctx->launches;
             k_extend_exact<<<dim3((unsigned)((N + 127) / 128), 2 * m), 128, 0, ctx->stream>>>(
-                X, (size_t)R * N, L, nb, ctx->mult_Wq, b_off, ctx->logN, ctx->d_mod, ext_tab);
+                X, (size_t)R * N, L, nb, ctx->mult_Wq, b_off, ctx->logN, ctx->d_mod, ext_tab,
+                extf_tab, force_exact);
             ntt_forward(ctx, X, 2 * m, (size_t)R * N, L, 0);
             ntt_forward(ctx, X + (size_t)L * N, 2 * m, (size_t)R * N, nb, b_off);
         }
@@ -373,7 +515,8 @@ static int multiply_items(he_ctx* ctx, const he_ct* a, const he_ct* b, int n, he
         ntt_inverse(ctx, D + (size_t)L * N, 3 * m, (size_t)R * N, nb, b_off);
         ++ctx->launches;
         k_scale_round<<<dim3((unsigned)((N + 127) / 128), 3 * m), 128, 0, ctx->stream>>>(
-            D, S01, T2, R, L, ctx->mult_Wm, b_off, ctx->prm.t, ctx->logN, ctx->d_mod, sc_tab);
+            D, S01, T2, R, L, ctx->mult_Wm, b_off, ctx->prm.t, ctx->logN, ctx->d_mod, sc_tab, scf_tab,
+            force_exact);
         ntt_forward(ctx, S01, 2 * m, (size_t)L * N, L, 0);
         ntt_forward(ctx, T2 + (size_t)L * N, m, ct, L, 0);
         // relinearise: out = (d0, d1) + KeySwitch_{s^2 -> s}(d2)
@@ -409,7 +552,10 @@ extern "C" int he_multiply_batch(he_ctx* ctx, const he_ct* a, const he_ct* b, in
         return he_fail(ctx, HE_ENOKEY, "he_multiply: no relinearisation key (step HE_RELIN_KEY)");
     if ((rc = mult_tables(ctx))) return rc;
     if (n == 0) return HE_OK;
-    if ((rc = multiply_items(ctx, a, b, n, out, rlk))) return rc;
+    phase_begin(ctx, HE_PHASE_MULTIPLY);
+    rc = multiply_items(ctx, a, b, n, out, rlk);
+    phase_end(ctx);
+    if (rc) return rc;
     return he_launch_check(ctx, "he_multiply");
 }
 

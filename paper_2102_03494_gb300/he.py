@@ -211,7 +211,7 @@ class Context:
     def he_launch_count(self):
         return int(lib().he_launch_count(self.h))
 
-    PHASES = ("encode", "modup", "taps", "moddown", "rotate", "restore")
+    PHASES = ("encode", "modup", "taps", "moddown", "rotate", "restore", "multiply")
 
     def he_set_phase_timing(self, enable):
         self._ck(lib().he_set_phase_timing(self.h, int(enable)), "he_set_phase_timing")

@@ -93,3 +93,25 @@ def test_multiply_errors():
     with pytest.raises(he.HeError) as e:
         ctx.he_multiply(low, low)                     # below full level
     assert e.value.code == he.HE_EINVAL
+
+
+def test_multiword_rounding_path_is_bit_exact(monkeypatch):
+    """HE_MULT_EXACT=1 sends every coefficient through the multi-word path (the one the fast
+    fixed-point rounding falls back to); it must give the same bits as the oracle."""
+    from paper_2102_03494_gb300 import he
+    prm = prm_of("n1024_partial")
+    ctx = make_ctx(prm)
+    s = bfv.keygen_secret(prm, 13)
+    rlk = bfv.relin_key(prm, s, 4)
+    ctx.he_load_keys(rlk.reshape(-1), [he.HE_RELIN_KEY])
+    rng = np.random.default_rng(17)
+    a = encrypt_slots(prm, s, rng.integers(0, prm.t, prm.n), 70)
+    b = encrypt_slots(prm, s, rng.integers(0, prm.t, prm.n), 71)
+    want = bfv.relinearize(prm, bfv.multiply(prm, a, b), rlk)
+    da, db = upload_ntt(ctx, a), upload_ntt(ctx, b)
+    monkeypatch.setenv("HE_MULT_EXACT", "1")
+    got = ctx.he_multiply(da, db)
+    assert (download_coeff(ctx, got) == want.stack()).all()
+    monkeypatch.delenv("HE_MULT_EXACT")
+    fast = ctx.he_multiply(da, db)
+    assert (download_coeff(ctx, fast) == want.stack()).all()
