@@ -24,7 +24,12 @@ readings implemented here (each is also listed among the design readings):
   * the hoisted form runs ModUp once on c1 and applies X -> X^g to the extended digits;
     it is a different algorithm from the plain one (the lifts differ), so each has its
     own ciphertext bits and both decrypt to the same slots;
-  * modulus switching drops q_{L-1} with rounding: c' = round(c / q_{L-1}).
+  * modulus switching drops q_{L-1} with rounding: c' = round(c / q_{L-1});
+  * ciphertext multiplication (Sec. 2.1) is the exact textbook product: both ciphertexts'
+    residues lifted to centred integers, the three tensor polynomials formed over Z[X]/(X^N+1)
+    exactly (CRT over auxiliary primes of this module), each coefficient scaled to
+    round(t d / Q) mod Q; relinearisation key-switches the third component with the
+    switching key of s^2 (streams 6 << 48 | j and 7 << 48 | j).
 """
 import numpy as np
 

@@ -205,3 +205,48 @@ def test_planted_scaling_slip_in_multiply_is_caught(monkeypatch, setup):
     monkeypatch.setattr(bfv, "scale_round", lambda ints, t, Q: ints)
     bad = bfv.relinearize(prm, bfv.multiply(prm, a, b), rlk)
     assert not (encoder.decode(bfv.decrypt(prm, s, bad), prm) == (v * w) % prm.t).all()
+
+
+@pytest.mark.parametrize("cfg", [(4, 2, 1, 1), (5, 3, 1, 1)])
+def test_multiply_equals_brute_force_definition(cfg):
+    """On tiny rings, for arbitrary residues (not only encryptions): d_k = round(t D_k / Q)
+    mod q_i with D_k the exact negacyclic products of the centred lifts, written out with
+    Python integers (no CRT over auxiliary primes, no NTT)."""
+    log_n, nq, np_, alpha = cfg
+    prm = params.Params(log_n=log_n, n_q=nq, n_p=np_, alpha=alpha)
+    n, t, Q = prm.n, prm.t, prm.Q(nq)
+    rng = np.random.default_rng(log_n)
+    rand = lambda: np.stack([rng.integers(0, q, n, dtype=np.uint64) for q in prm.q])
+    a, b = bfv.Ct(rand(), rand()), bfv.Ct(rand(), rand())
+
+    def lift(x):
+        out = []
+        for j in range(n):
+            v = 0
+            for i, q in enumerate(prm.q):          # CRT by the textbook formula
+                Qi = Q // q
+                v += int(x[i][j]) * Qi * pow(Qi, -1, q)
+            v %= Q
+            out.append(v - Q if 2 * v > Q else v)
+        return out
+
+    def negacyclic(x, y):
+        z = [0] * n
+        for i in range(n):
+            for j in range(n):
+                if i + j < n:
+                    z[i + j] += x[i] * y[j]
+                else:
+                    z[i + j - n] -= x[i] * y[j]
+        return z
+
+    A0, A1, B0, B1 = lift(a.c0), lift(a.c1), lift(b.c0), lift(b.c1)
+    D = [negacyclic(A0, B0),
+         [u + v for u, v in zip(negacyclic(A0, B1), negacyclic(A1, B0))],
+         negacyclic(A1, B1)]
+    got = bfv.multiply(prm, a, b)
+    for k in range(3):
+        # floor(t D / Q + 1/2); no ties, as 2 t D + Q is odd and 2Q is even
+        want = [(2 * t * v + Q) // (2 * Q) for v in D[k]]
+        for i, q in enumerate(prm.q):
+            assert [int(e) for e in got[k][i]] == [w % q for w in want], (k, i)
