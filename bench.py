@@ -306,7 +306,7 @@ def measured_peaks():
 # DRAM bytes (read + write) of one k_ks_mac_ext launch, from one ncu capture of the current
 # kernel version at the bench shape (profiles/k_ks_mac_ext_n15.md); cleared when the kernel
 # changes and until it is captured again.
-KS_MAC_EXT_TRAFFIC = {16: 1312579584 + 241215744}
+KS_MAC_EXT_TRAFFIC = {}
 
 
 # 64 x 64 -> 128-bit products per second of the GPU's integer multiplier: 152 SMs x 64 32-bit
@@ -363,7 +363,8 @@ def run_serving(args):
     for i, (name, sp) in enumerate(specs.items()):
         shape = workloads.LayerShape(*sp.shape)
         W1, W2 = workloads.weights(i, shape, lo=-8, hi=8)
-        rings[name] = serving.GpuRing(sp, workers=2, W1=W1, W2=W2, sk_seed=1 + i, key_seed=11 + i)
+        rings[name] = serving.GpuRing(sp, workers=2, W1=W1, W2=W2, sk_seed=1 + i, key_seed=11 + i,
+                                      keep_results=False)
 
     def make_requests(rate, count, seed):
         reqs = serving.poisson_arrivals(seed=seed, rate=rate, count=count, mix=mix)
@@ -380,6 +381,10 @@ def run_serving(args):
             r.payload = rings[r.ring].encrypt(slots, 7000 + r.rid)
         torch.cuda.synchronize()
         return reqs
+
+    def release(reqs):
+        for r in reqs:
+            r.payload = r.result = None
 
     # warm-up of every worker of every ring at the largest batch (scratch sizing, first launches)
     warm = make_requests(1e9, 64, seed=99)
@@ -410,6 +415,8 @@ def run_serving(args):
             t_free = start + dt
             lat.append((t_free - r.t_arrive) * 1000.0)
         span = t_free - plain_reqs[0].t_arrive
+        release(reqs)
+        release(plain_reqs)
         plain = {"requests": count, "p50_ms": float(np.percentile(lat, 50)),
                  "p99_ms": float(np.percentile(lat, 99)), "requests_per_s": count / span}
         out["rates"].append({"offered_per_s": rate, "served": served, "plain": plain,

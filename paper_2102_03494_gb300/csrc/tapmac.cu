@@ -79,6 +79,14 @@ __device__ __forceinline__ uint64_t redc_w(U128 x, uint64_t q, uint64_t qinv_neg
     return t >= q ? t - q : t;
 }
 
+// x mod q for an unreduced sum x < 64 q^2 (q < 2^60): the high word drops below q by at most
+// three subtractions of q 2^64 (a multiple of q), then REDC; the tap sums are kept in the
+// Montgomery domain of the plaintexts, so REDC returns the plain residue.
+__device__ __forceinline__ uint64_t reduce_sum(U128 x, uint64_t q, uint64_t qinv_neg) {
+    while (x.hi >= q) x.hi -= q;
+    return redc(x, q, qinv_neg);
+}
+
 // Shared-memory stage (uint64 words): keys [DNUM][2][T] | pts [2][T] | digits [2 img][DNUM][T]
 // | P x [2 img][2 poly][T].
 template <int DNUM>
@@ -169,19 +177,15 @@ k_ks_mac_ext_bulk(const uint64_t* __restrict__ D, const uint64_t* __restrict__ X
             issue_tap<DNUM>(smem + S::WORDS, &bars[1], 1, tt, D, XPg, pts, c_lo, c_cnt, b0, nb, l, L,
                             n0, LN, N, logN);
     }
+    // unreduced sums of at most HE_MAX_TAPS products below q^2 each: < 64 q^2 < 2^126
     U128 a128[2][2][2];
-    uint64_t acc[2][2][2];
 #pragma unroll
     for (int ib = 0; ib < 2; ++ib)
 #pragma unroll
         for (int c = 0; c < 2; ++c)
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                a128[ib][c][k] = U128{0, 0};
-                acc[ib][c][k] = 0;
-            }
+            for (int k = 0; k < 2; ++k) a128[ib][c][k] = U128{0, 0};
     uint32_t parity[2] = {0u, 0u};
-    int pending = 0;
     bool ok = true;
     for (int t = 0; t < tt.n; ++t) {
         const int s = t & 1;
@@ -233,18 +237,6 @@ k_ks_mac_ext_bulk(const uint64_t* __restrict__ D, const uint64_t* __restrict__ X
                 mac128(a128[ib][0][k], x[ib][k], p0);
                 mac128(a128[ib][1][k], x[ib][k], p1);
             }
-        if (++pending == 8 || t == tt.n - 1) {
-            pending = 0;
-#pragma unroll
-            for (int ib = 0; ib < 2; ++ib)
-#pragma unroll
-                for (int c = 0; c < 2; ++c)
-#pragma unroll
-                    for (int k = 0; k < 2; ++k) {
-                        acc[ib][c][k] = add_mod(acc[ib][c][k], redc(a128[ib][c][k], q, qi), q);
-                        a128[ib][c][k] = U128{0, 0};
-                    }
-        }
         __syncthreads();   // every warp is done with stage s before it is refilled
         if (tid < 32 && t + 2 < tt.n) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -265,8 +257,8 @@ k_ks_mac_ext_bulk(const uint64_t* __restrict__ D, const uint64_t* __restrict__ X
         for (int c = 0; c < 2; ++c) {
             if (c >= c_cnt) break;
             uint64_t* ab = A + (((size_t)(b0 + ib) * tt.r + c_lo + c) * 2) * LN + (size_t)l * N + n;
-            ab[0] = acc[ib][c][0];
-            ab[LN] = acc[ib][c][1];
+            ab[0] = reduce_sum(a128[ib][c][0], q, qi);
+            ab[LN] = reduce_sum(a128[ib][c][1], q, qi);
         }
     }
 }

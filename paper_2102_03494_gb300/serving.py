@@ -166,10 +166,12 @@ class GpuRing:
     """One ring's workers: a library context and a CUDA stream each, keys resident in every
     context, weights fixed per ring."""
 
-    def __init__(self, spec: RingSpec, workers: int, W1, W2, sk_seed: int, key_seed: int):
+    def __init__(self, spec: RingSpec, workers: int, W1, W2, sk_seed: int, key_seed: int,
+                 keep_results: bool = True):
         import torch
         from . import he
         self.spec, self.workers = spec, workers
+        self.keep_results = keep_results          # False: outputs are released on completion
         self.W1, self.W2 = W1, W2
         self.streams = [torch.cuda.Stream() for _ in range(workers)]
         self.ctx = [he.Context(spec.log_n, spec.n_q, spec.n_p, spec.alpha, stream=s)
@@ -210,7 +212,7 @@ class GpuRing:
     def results(self, handle, requests):
         outs = handle[1]
         for i, r in enumerate(requests):
-            r.result = outs[i * self.O_c:(i + 1) * self.O_c]
+            r.result = outs[i * self.O_c:(i + 1) * self.O_c] if self.keep_results else None
 
     def run_alone(self, payload):
         """The plain form: one request, one call, waited for."""
