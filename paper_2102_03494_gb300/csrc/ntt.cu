@@ -67,31 +67,34 @@ __device__ __forceinline__ void round_bflies(uint64_t (&x)[8], const int (&hi)[8
     }
 }
 
-// One round of the column pass.  Element m of group Gi: column c = Gi % cols, row
-// hi (tlow 2^K) + m tlow + lo with (hi, lo) = divmod(Gi / cols, tlow).
+// One round of the column pass.  Element m of group Gi: column c = Gi mod cols, row
+// hi (tlow 2^K) + m tlow + lo with (hi, lo) = divmod(Gi / cols, tlow).  cols = 2^lc and
+// tlow = 2^(s1 - e0 - K), so the divisions are shifts.
 template <int K, bool INV>
 __device__ __forceinline__ void col_round(uint64_t (&x)[8], uint64_t* sm, uint64_t* __restrict__ a,
-                                          bool first, bool last, int e0, int N1, int N2, int lo0,
-                                          int cols, const ShoupPair* __restrict__ w,
+                                          bool first, bool last, int e0, int s1, int N2, int lo0,
+                                          int lc, const ShoupPair* __restrict__ w,
                                           const ModConst& Mc) {
     constexpr int M = 1 << K;
-    const int tlow = N1 >> (e0 + K);
+    const int ltl = s1 - e0 - K, tlow = 1 << ltl;
+    const int cmask = (1 << lc) - 1;
     const int nthr = blockDim.x, tid = threadIdx.x;
     int hi[8 >> K];
     int off[8];
 #pragma unroll
     for (int g = 0; g < (8 >> K); ++g) {
         const int Gi = tid + g * nthr;
-        const int c = Gi % cols, Gc = Gi / cols;
-        hi[g] = Gc / tlow;
-        const int lo = Gc - hi[g] * tlow;
+        const int c = Gi & cmask, Gc = Gi >> lc;
+        hi[g] = Gc >> ltl;
+        const int lo = Gc & (tlow - 1);
 #pragma unroll
-        for (int m = 0; m < M; ++m) off[g * M + m] = (hi[g] * (tlow << K) + m * tlow + lo) * cols + c;
+        for (int m = 0; m < M; ++m)
+            off[g * M + m] = ((((hi[g] << K) + m) << ltl) + lo) << lc | c;
     }
     if (first) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            const int row = off[i] / cols, c = off[i] - row * cols;
+            const int row = off[i] >> lc, c = off[i] & cmask;
             x[i] = a[(size_t)row * N2 + lo0 + c];
         }
     } else {
@@ -103,7 +106,7 @@ __device__ __forceinline__ void col_round(uint64_t (&x)[8], uint64_t* sm, uint64
     if (last) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            const int row = off[i] / cols, c = off[i] - row * cols;
+            const int row = off[i] >> lc, c = off[i] & cmask;
             uint64_t v = x[i];
             if (INV) v = mul_shoup(v, Mc.n_inv, Mc.n_inv_sh, q);
             a[(size_t)row * N2 + lo0 + c] = v;
@@ -119,11 +122,12 @@ __device__ __forceinline__ void col_round(uint64_t (&x)[8], uint64_t* sm, uint64
 // local index hi (tlow 2^K) + m tlow + lo.
 template <int K, bool INV>
 __device__ __forceinline__ void row_round(uint64_t (&x)[8], uint64_t* sm, uint64_t* __restrict__ a,
-                                          bool first, bool last, int e0, int s1, int N2, int blk0,
+                                          bool first, bool last, int e0, int s1, int s2, int blk0,
                                           const ShoupPair* __restrict__ w, const ModConst& Mc) {
     constexpr int M = 1 << K;
-    const int tlow = N2 >> (e0 + K);
-    const int per_blk = N2 >> K;
+    const int N2 = 1 << s2;
+    const int ltl = s2 - e0 - K, tlow = 1 << ltl;
+    const int lpb = s2 - K;                       // log2 of the groups per block
     const int nthr = blockDim.x, tid = threadIdx.x;
     // all groups of one thread lie in the same block when per_blk >= nthr, else they differ:
     // keep the block of each group separately.
@@ -133,12 +137,13 @@ __device__ __forceinline__ void row_round(uint64_t (&x)[8], uint64_t* sm, uint64
 #pragma unroll
     for (int g = 0; g < (8 >> K); ++g) {
         const int Gi = tid + g * nthr;
-        const int b = Gi / per_blk, Gl = Gi - b * per_blk;
-        hi[g] = Gl / tlow;
+        const int b = Gi >> lpb, Gl = Gi & ((1 << lpb) - 1);
+        hi[g] = Gl >> ltl;
         blk[g] = b;
-        const int lo = Gl - hi[g] * tlow;
+        const int lo = Gl & (tlow - 1);
 #pragma unroll
-        for (int m = 0; m < M; ++m) off[g * M + m] = b * N2 + hi[g] * (tlow << K) + m * tlow + lo;
+        for (int m = 0; m < M; ++m)
+            off[g * M + m] = (b << s2) + ((((hi[g] << K) + m) << ltl) | lo);
     }
     if (first) {
 #pragma unroll
@@ -184,34 +189,34 @@ __device__ __forceinline__ void round_of(int r, int lg, bool inv, int& e0, int& 
 }
 
 template <bool INV>
-__global__ void __launch_bounds__(256)
-k_ntt_cols(uint64_t* __restrict__ data, size_t item_stride, int mod_off, int logN, int s1, int cols,
+__global__ void __launch_bounds__(256, 4)
+k_ntt_cols(uint64_t* __restrict__ data, size_t item_stride, int mod_off, int logN, int s1, int lc,
            const ModConst* __restrict__ mods, const ShoupPair* __restrict__ tw) {
     __shared__ uint64_t sm[kTile];
-    const int N = 1 << logN, N1 = 1 << s1, N2 = N >> s1;
+    const int N = 1 << logN, N2 = N >> s1;
     const int mod = mod_off + blockIdx.y;
     const ModConst Mc = mods[mod];
     const ShoupPair* w = tw + (size_t)mod * N;
     uint64_t* a = data + blockIdx.z * item_stride + (size_t)blockIdx.y * N;
-    const int lo0 = blockIdx.x * cols;
+    const int lo0 = blockIdx.x << lc;
     const int nr = (s1 + 2) / 3;
     uint64_t x[8];
     for (int r = 0; r < nr; ++r) {
         int e0, K;
         round_of(r, s1, INV, e0, K);
         const bool first = r == 0, last = r == nr - 1;
-        if (K == 3) col_round<3, INV>(x, sm, a, first, last, e0, N1, N2, lo0, cols, w, Mc);
-        else if (K == 2) col_round<2, INV>(x, sm, a, first, last, e0, N1, N2, lo0, cols, w, Mc);
-        else col_round<1, INV>(x, sm, a, first, last, e0, N1, N2, lo0, cols, w, Mc);
+        if (K == 3) col_round<3, INV>(x, sm, a, first, last, e0, s1, N2, lo0, lc, w, Mc);
+        else if (K == 2) col_round<2, INV>(x, sm, a, first, last, e0, s1, N2, lo0, lc, w, Mc);
+        else col_round<1, INV>(x, sm, a, first, last, e0, s1, N2, lo0, lc, w, Mc);
     }
 }
 
 template <bool INV>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_ntt_rows(uint64_t* __restrict__ data, size_t item_stride, int mod_off, int logN, int s1, int blocks,
            const ModConst* __restrict__ mods, const ShoupPair* __restrict__ tw) {
     __shared__ uint64_t sm[kTile];
-    const int N = 1 << logN, N2 = N >> s1;
+    const int N = 1 << logN;
     const int s2 = logN - s1;
     const int mod = mod_off + blockIdx.y;
     const ModConst Mc = mods[mod];
@@ -224,14 +229,14 @@ k_ntt_rows(uint64_t* __restrict__ data, size_t item_stride, int mod_off, int log
         int e0, K;
         round_of(r, s2, INV, e0, K);
         const bool first = r == 0, last = r == nr - 1;
-        if (K == 3) row_round<3, INV>(x, sm, a, first, last, e0, s1, N2, blk0, w, Mc);
-        else if (K == 2) row_round<2, INV>(x, sm, a, first, last, e0, s1, N2, blk0, w, Mc);
-        else row_round<1, INV>(x, sm, a, first, last, e0, s1, N2, blk0, w, Mc);
+        if (K == 3) row_round<3, INV>(x, sm, a, first, last, e0, s1, s2, blk0, w, Mc);
+        else if (K == 2) row_round<2, INV>(x, sm, a, first, last, e0, s1, s2, blk0, w, Mc);
+        else row_round<1, INV>(x, sm, a, first, last, e0, s1, s2, blk0, w, Mc);
     }
 }
 
 struct Split {
-    int s1, cols, col_ctas, col_threads, blocks, row_ctas, row_threads;
+    int s1, cols, lc, col_ctas, col_threads, blocks, row_ctas, row_threads;
 };
 
 Split split_of(int logN) {
@@ -241,6 +246,8 @@ Split split_of(int logN) {
     sp.cols = kTile / N1;
     if (sp.cols > N2) sp.cols = N2;
     if (sp.cols < 1) sp.cols = 1;
+    sp.lc = 0;
+    while ((1 << sp.lc) < sp.cols) ++sp.lc;
     sp.col_ctas = N2 / sp.cols;
     sp.col_threads = N1 * sp.cols / 8;
     sp.blocks = kTile / N2;
@@ -260,7 +267,7 @@ void ntt_forward(he_ctx* ctx, uint64_t* data, int items, size_t item_stride, int
     const Split sp = split_of(ctx->logN);
     dim3 gc(sp.col_ctas, rows, items), gr(sp.row_ctas, rows, items);
     k_ntt_cols<false><<<gc, sp.col_threads, 0, ctx->stream>>>(
-        data, item_stride, mod_off, ctx->logN, sp.s1, sp.cols, ctx->d_mod, ctx->d_tw_fwd);
+        data, item_stride, mod_off, ctx->logN, sp.s1, sp.lc, ctx->d_mod, ctx->d_tw_fwd);
     k_ntt_rows<false><<<gr, sp.row_threads, 0, ctx->stream>>>(
         data, item_stride, mod_off, ctx->logN, sp.s1, sp.blocks, ctx->d_mod, ctx->d_tw_fwd);
 }
@@ -274,5 +281,5 @@ void ntt_inverse(he_ctx* ctx, uint64_t* data, int items, size_t item_stride, int
     k_ntt_rows<true><<<gr, sp.row_threads, 0, ctx->stream>>>(
         data, item_stride, mod_off, ctx->logN, sp.s1, sp.blocks, ctx->d_mod, ctx->d_tw_inv);
     k_ntt_cols<true><<<gc, sp.col_threads, 0, ctx->stream>>>(
-        data, item_stride, mod_off, ctx->logN, sp.s1, sp.cols, ctx->d_mod, ctx->d_tw_inv);
+        data, item_stride, mod_off, ctx->logN, sp.s1, sp.lc, ctx->d_mod, ctx->d_tw_inv);
 }
