@@ -280,6 +280,51 @@ int he_net_batch(he_ctx* ctx, const he_ct* in, int B, const int32_t* lowrank_w,
                  const int32_t* restore_w, const int32_t* fc1_w, const int32_t* fc2_w,
                  const he_net* net, he_ct* out);
 
+/* ---- deeper networks over several ciphertexts per tensor --------------------------- */
+
+/* A stride-1 "same" convolution layer (d odd, pad = (d - 1) / 2) on a C_in x H x W tensor:
+ * factorized (Eq. 2) into r low-rank d x d filters and a 1 x 1 restore to O_c channels, or
+ * unfactorized (r = 0: O_c d x d filters, no restore). */
+typedef struct {
+    int32_t C_in, H, W, d, pad, r, O_c;
+} he_mc_conv;
+/* Tensor layout of these calls: channel c of the H x W map occupies block c mod g of ciphertext
+ * c / g (row 0), block size Bk = next_pow2(H W), g = (N/2) / Bk, pixel (h, w) at offset
+ * h W + w; other slots zero.  Packing (DensePack over several ciphertexts, Sec. 3.2 with the
+ * FFConv factorization of Sec. 4): every input ciphertext is rotated by the d^2 - 1 nonzero tap
+ * offsets (hoisted, summed in Q u P per low-rank channel over all input ciphertexts, one
+ * ModDown each); a rotate-and-sum over the g blocks (steps Bk 2^e) replicates each low-rank
+ * output in every block; output ciphertext G = sum_c' y1[c'] * P[G][c'] with P[G][c'] holding
+ * restore_w[G g + j][c'] on block j (identity when unfactorized) -- no rotation.  in:
+ * [B][ceil(C_in / g)], out: [B][ceil(O_c / g)], full level, NTT domain.  lowrank_w: host int32
+ * [r or O_c][C_in][d][d]; restore_w: host int32 [O_c][r], NULL when r = 0.  Keys: the nonzero
+ * tap offsets (i - pad) W + (j - pad) and the fold steps Bk 2^e < N/2. */
+int he_mc_conv_batch(he_ctx* ctx, const he_ct* in, int B, const int32_t* lowrank_w,
+                     const int32_t* restore_w, const he_mc_conv* conv, he_ct* out);
+/* In place, for each step in order: x <- x + rot(x, step), on n ciphertexts (full level, NTT
+ * domain); e.g. the global sum pooling inside blocks (steps 1, 2, ..., Bk/2). */
+int he_rotate_sum_batch(he_ctx* ctx, he_ct* cts, int n, const int32_t* steps, int n_steps);
+/* he_fc_layer_batch over n_ct input ciphertexts per image (in: [B][n_ct]): feature i at slot
+ * pos[i] of ciphertext ct_of[i]; the taps of all input ciphertexts are summed in Q u P before the
+ * one ModDown.  Keys as for he_fc_layer_batch. */
+int he_fc_mc_batch(he_ctx* ctx, const he_ct* in, int B, int n_ct, const int32_t* weights,
+                   const int32_t* ct_of, const int32_t* pos, int n_feat, int n_out, int period,
+                   he_ct* out);
+/* Steps whose keys he_deep_batch needs (layer taps and folds, pooling, classifier), then
+ * HE_RELIN_KEY; count returned, at most cap written. */
+int he_deep_required_steps(const he_ctx* ctx, const he_mc_conv* convs, int n_layers, int n_cls,
+                           int32_t* steps_out, int cap);
+/* The deeper network on B images: for each layer he_mc_conv_batch then the square
+ * (he_multiply_batch) of every output ciphertext; global sum pooling inside the blocks
+ * (he_rotate_sum_batch); a fully connected layer to n_cls classes over the pooled channel sums
+ * (he_fc_mc_batch, period N/2).  lowrank_w[l] / restore_w[l] as for he_mc_conv_batch
+ * (restore_w[l] NULL for unfactorized layers); fc_w host int32 [n_cls][O_c of the last layer].
+ * in: [B][ceil(C0 / g)] packed as above; out[B]: class j at slots p of row 0 with
+ * p mod next_pow2(n_cls) = j.  Intermediate ciphertexts live in a context-owned buffer. */
+int he_deep_batch(he_ctx* ctx, const he_ct* in, int B, const he_mc_conv* convs, int n_layers,
+                  const int32_t* const* lowrank_w, const int32_t* const* restore_w,
+                  const int32_t* fc_w, int n_cls, he_ct* out);
+
 /* ---- primitives for measurement --------------------------------------------------- */
 
 /* Negacyclic NTT (inverse = 0) or inverse NTT (inverse = 1) in place on `n_items` blocks of

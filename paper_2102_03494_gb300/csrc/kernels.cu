@@ -229,14 +229,7 @@ k_ks_mac_ext(const uint64_t* __restrict__ D, const uint64_t* __restrict__ XP,
     const uint64_t q = M.q, qi = M.qinv_neg;
     const bool qlimb = l < L;
     const size_t LN = (size_t)LK * N;
-    const uint64_t* Db[2];
-    const uint64_t* Xb[2];
-#pragma unroll
-    for (int ib = 0; ib < 2; ++ib) {
-        const int b = b0 + (ib < nb ? ib : 0);
-        Db[ib] = D + (size_t)b * DNUM * LN + (size_t)l * N;
-        Xb[ib] = XP + (size_t)b * 2 * L * N + (size_t)(qlimb ? l : 0) * N;
-    }
+    const int ns = tt.n_sub > 0 ? tt.n_sub : 1;
     U128 a128[2][2][2];       // [image][channel][poly], unreduced
     uint64_t acc[2][2][2];    // reduced running sums
 #pragma unroll
@@ -255,6 +248,14 @@ k_ks_mac_ext(const uint64_t* __restrict__ D, const uint64_t* __restrict__ XP,
         const uint64_t p0 = pt0[(size_t)t * LN];
         const uint64_t p1 = c_cnt > 1 ? pt0[pstride + (size_t)t * LN] : 0;
         const uint64_t* key = tt.key[t];
+        const uint64_t* Db[2];
+        const uint64_t* Xb[2];
+#pragma unroll
+        for (int ib = 0; ib < 2; ++ib) {
+            const size_t it = (size_t)(b0 + (ib < nb ? ib : 0)) * ns + tt.sub[t];
+            Db[ib] = D + it * DNUM * LN + (size_t)l * N;
+            Xb[ib] = XP + it * 2 * L * N + (size_t)(qlimb ? l : 0) * N;
+        }
         uint64_t x[2][2];
         if (!key) {
 #pragma unroll
@@ -752,7 +753,9 @@ void launch_scale_p(he_ctx* c, const uint64_t* X, uint64_t* XP, int B) {
 }
 
 void launch_ks_mac_ext(he_ctx* c, const uint64_t* D, const uint64_t* XP, const uint64_t* pts,
-                       const TapTable& tt, uint64_t* A, int B) {
+                       const TapTable& tt_in, uint64_t* A, int B) {
+    TapTable tt = tt_in;
+    if (tt.n_sub < 1) tt.n_sub = 1;   // one input ciphertext per image
     if (tapmac_bulk_supported(c)) {   // operands staged by bulk copies (tapmac.cu)
         launch_ks_mac_ext_bulk(c, D, XP, pts, tt, A, B);
         return;

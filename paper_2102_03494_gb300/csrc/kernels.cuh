@@ -7,15 +7,19 @@
 #define HE_MAX_TAPS 64
 
 // Per-tap rotation data of the extended-basis tap MAC (passed by value as a kernel argument):
-// the key (null for the zero offset) and Galois element of each tap, tap count, channels.
+// the key (null for the zero offset) and Galois element of each tap, tap count, channels, and
+// for inputs of several ciphertexts per image the one each tap reads: tap t of image b uses
+// the ModUp digits and P x of item b n_sub + sub[t] (n_sub = 1, sub = 0 for one ciphertext).
 struct TapTable {
     const uint64_t* key[HE_MAX_TAPS];
     uint32_t g[HE_MAX_TAPS];
+    uint8_t sub[HE_MAX_TAPS];
     int n;
     int r;
+    int n_sub;
 };
 
-// XP ([B][2][L][N]) <- P times the inputs X, per ciphertext limb.
+// XP ([B][2][L][N]) <- P times the inputs X, per ciphertext limb.  B counts ciphertexts.
 void launch_scale_p(he_ctx* c, const uint64_t* X, uint64_t* XP, int B);
 // Extended-basis tap MAC over B images (dnum <= 8); XP from launch_scale_p.  Uses the
 // bulk-copy pipelined kernel (tapmac.cu) when N >= 256, else the register-only kernel.

@@ -445,6 +445,7 @@ extern "C" int he_ffconv_layer_batch(he_ctx* ctx, const he_ct* ct_in, int B,
         TapTable tt{};
         tt.n = li.taps;
         tt.r = r;
+        tt.n_sub = 1;
         int tap = 0, nrot = 0;
         for (int i = 0; i < y.d; ++i)
             for (int j = 0; j < y.d; ++j, ++tap) {

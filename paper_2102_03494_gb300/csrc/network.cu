@@ -25,23 +25,24 @@
 
 namespace {
 
-// slots[k][p] = F[p mod M][inv[(p + k) mod per]] for p < N/2 with p mod M < m, else 0.
+// slots[G M + k][p] = F[p mod M][inv[G][(p + k) mod per]] for p < N/2 with p mod M < m, else 0
+// (G: input ciphertext, k: diagonal).
 __global__ void k_fc_diag_slots(const int32_t* __restrict__ F, const int32_t* __restrict__ inv,
                                 int m, int n_in, int M, int per, int logN,
                                 int64_t* __restrict__ slots) {
     const int N = 1 << logN;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= N) return;
-    const int k = blockIdx.y;
+    const int G = blockIdx.y / M, k = blockIdx.y - G * M;
     int64_t v = 0;
     if (p < N / 2) {
         const int j = p & (M - 1);
         if (j < m) {
-            const int i = inv[(p + k) & (per - 1)];
+            const int i = inv[(size_t)G * per + ((p + k) & (per - 1))];
             if (i >= 0) v = F[(size_t)j * n_in + i];
         }
     }
-    slots[(size_t)k * N + p] = v;
+    slots[(size_t)blockIdx.y * N + p] = v;
 }
 
 bool is_pow2(long long x) { return x > 0 && (x & (x - 1)) == 0; }
@@ -120,28 +121,33 @@ int check_net(he_ctx* ctx, const he_net* net, ConvGeom* g) {
 
 }  // namespace
 
-extern "C" int he_fc_layer_batch(he_ctx* ctx, const he_ct* in, int B, const int32_t* weights,
-                                 const int32_t* pos, int n_in, int n_out, int period,
-                                 he_ct* out) {
+// Fully connected layer over n_ct input ciphertexts per image (the schedule in the file
+// comment, taps of every input ciphertext summed in Q u P before the one ModDown): feature i
+// sits at slot pos[i] of ciphertext ct_of[i], inside one period.
+static int fc_core(he_ctx* ctx, const he_ct* in, int B, int n_ct, const int32_t* weights,
+                   const int32_t* ct_of, const int32_t* pos, int n_feat, int n_out, int period,
+                   he_ct* out) {
     if (!ctx) return HE_EINVAL;
-    if (!in || !weights || !pos || !out || B < 1 || n_in < 1 || n_out < 1)
+    if (!in || !weights || !pos || !out || B < 1 || n_ct < 1 || n_feat < 1 || n_out < 1)
         return he_fail(ctx, HE_EINVAL, "he_fc_layer: null or empty argument");
     if (!ctx->batching) return he_fail(ctx, HE_EINVAL, "he_fc_layer: t is not 1 mod 2N");
     const int half = ctx->N / 2, M = next_pow2(n_out);
     if (!is_pow2(period) || period > half || M > period)
         return he_fail(ctx, HE_EINVAL, "he_fc_layer: period must be a power of two, M <= period <= N/2");
-    std::vector<int32_t> inv(period, -1);
-    for (int i = 0; i < n_in; ++i) {
-        if (pos[i] < 0 || pos[i] >= period || inv[pos[i]] >= 0)
+    if (n_ct > 255) return he_fail(ctx, HE_EINVAL, "he_fc_layer: at most 255 input ciphertexts");
+    std::vector<int32_t> inv((size_t)n_ct * period, -1);
+    for (int i = 0; i < n_feat; ++i) {
+        const int G = ct_of ? ct_of[i] : 0;
+        if (G < 0 || G >= n_ct || pos[i] < 0 || pos[i] >= period || inv[(size_t)G * period + pos[i]] >= 0)
             return he_fail(ctx, HE_EINVAL, "he_fc_layer: positions must be distinct and inside one period");
-        inv[pos[i]] = i;
+        inv[(size_t)G * period + pos[i]] = i;
     }
     int rc;
     const int L = ctx->L, LK = L + ctx->K;
-    for (int b = 0; b < B; ++b) {
-        if ((rc = check_ct(ctx, &in[b], L, HE_NTT, "he_fc_layer input"))) return rc;
+    for (int i = 0; i < B * n_ct; ++i)
+        if ((rc = check_ct(ctx, &in[i], L, HE_NTT, "he_fc_layer input"))) return rc;
+    for (int b = 0; b < B; ++b)
         if ((rc = check_ct(ctx, &out[b], L, -1, "he_fc_layer output"))) return rc;
-    }
     // keys: taps 1 .. M-1, then the sum steps
     const std::vector<int32_t> steps = fc_steps(n_out, period);
     std::vector<const uint64_t*> keys(steps.size());
@@ -151,59 +157,63 @@ extern "C" int he_fc_layer_batch(he_ctx* ctx, const he_ct* in, int B, const int3
         if ((rc = he_get_key(ctx, gs[s], &keys[s]))) return rc;
     }
     const size_t N = ctx->N, ct = 2 * (size_t)L * N, ext_ct = 2 * (size_t)LK * N;
-    const int n_chunks = (M + HE_MAX_TAPS - 1) / HE_MAX_TAPS;
-    const size_t wn = (size_t)n_out * n_in;
-    const size_t need = (size_t)B * ct * 4                       // X, P x, A, A2
-                        + (size_t)M * (2 * N + (size_t)LK * N)     // slots, tmp, plaintexts
+    const int T = n_ct * M;                                  // taps: (input ciphertext, diagonal)
+    const int n_chunks = (T + HE_MAX_TAPS - 1) / HE_MAX_TAPS;
+    const size_t wn = (size_t)n_out * n_feat;
+    const size_t items = (size_t)B * n_ct;
+    const size_t need = items * ct * 2 + (size_t)B * ct * 2       // X, P x; A, A2
+                        + (size_t)T * (2 * N + (size_t)LK * N)     // slots, tmp, plaintexts
                         + (size_t)B * ext_ct * (n_chunks > 1 ? 2 : 1)
-                        + (size_t)B * rot_scratch_per_item(ctx) + (wn + period) / 2 + 1 + 32 * 16;
+                        + items * rot_scratch_per_item(ctx) + (wn + inv.size()) / 2 + 1 + 32 * 16;
     if ((rc = arena_reserve(ctx, need))) return rc;
     arena_reset(ctx);
-    uint64_t* X = arena_take(ctx, (size_t)B * ct);
-    uint64_t* XP = arena_take(ctx, (size_t)B * ct);
+    uint64_t* X = arena_take(ctx, items * ct);
+    uint64_t* XP = arena_take(ctx, items * ct);
     uint64_t* A = arena_take(ctx, (size_t)B * ct);
     uint64_t* A2 = arena_take(ctx, (size_t)B * ct);
-    int64_t* slots = (int64_t*)arena_take(ctx, (size_t)M * N);
-    uint64_t* tmp = arena_take(ctx, (size_t)M * N);
-    uint64_t* pts = arena_take(ctx, (size_t)M * LK * N);
+    int64_t* slots = (int64_t*)arena_take(ctx, (size_t)T * N);
+    uint64_t* tmp = arena_take(ctx, (size_t)T * N);
+    uint64_t* pts = arena_take(ctx, (size_t)T * LK * N);
     uint64_t* AX = arena_take(ctx, (size_t)B * ext_ct);
     uint64_t* AX2 = n_chunks > 1 ? arena_take(ctx, (size_t)B * ext_ct) : nullptr;
     int32_t* d_w = (int32_t*)arena_take(ctx, (wn + 1) / 2);
-    int32_t* d_inv = (int32_t*)arena_take(ctx, ((size_t)period + 1) / 2);
-    RotBufs rb = rot_bufs_take(ctx, B);
+    int32_t* d_inv = (int32_t*)arena_take(ctx, (inv.size() + 1) / 2);
+    RotBufs rb = rot_bufs_take(ctx, (int)items);
     if (!rb.v) return he_fail(ctx, HE_ENOMEM, "he_fc_layer: scratch");
 
     // diagonal plaintexts, lifted to Q u P in Montgomery form
     phase_begin(ctx, HE_PHASE_ENCODE);
     HE_CHECK_CUDA(ctx, cudaMemcpyAsync(d_w, weights, wn * 4, cudaMemcpyHostToDevice, ctx->stream));
-    HE_CHECK_CUDA(ctx, cudaMemcpyAsync(d_inv, inv.data(), (size_t)period * 4, cudaMemcpyHostToDevice,
+    HE_CHECK_CUDA(ctx, cudaMemcpyAsync(d_inv, inv.data(), inv.size() * 4, cudaMemcpyHostToDevice,
                                        ctx->stream));
     ++ctx->launches;
-    k_fc_diag_slots<<<dim3((unsigned)((N + 255) / 256), M), 256, 0, ctx->stream>>>(
-        d_w, d_inv, n_out, n_in, M, period, ctx->logN, slots);
-    encode_device(ctx, slots, M, tmp, pts, 1, LK);
+    k_fc_diag_slots<<<dim3((unsigned)((N + 255) / 256), T), 256, 0, ctx->stream>>>(
+        d_w, d_inv, n_out, n_feat, M, period, ctx->logN, slots);
+    encode_device(ctx, slots, T, tmp, pts, 1, LK);
     phase_end(ctx);
 
-    for (int b = 0; b < B; ++b)
-        HE_CHECK_CUDA(ctx, cudaMemcpyAsync(X + (size_t)b * ct, in[b].data, ct * 8,
-                                           cudaMemcpyDeviceToDevice, ctx->stream));
+    for (size_t i = 0; i < items; ++i)
+        HE_CHECK_CUDA(ctx, cudaMemcpyAsync(X + i * ct, in[i].data, ct * 8, cudaMemcpyDeviceToDevice,
+                                           ctx->stream));
     phase_begin(ctx, HE_PHASE_MODUP);
-    modup_items(ctx, X, B, 1u, rb);
-    launch_scale_p(ctx, X, XP, B);
+    modup_items(ctx, X, (int)items, 1u, rb);
+    launch_scale_p(ctx, X, XP, (int)items);
     phase_end(ctx);
-    // sum_k rot(x, k) diag_k in Q u P, at most HE_MAX_TAPS taps per launch
+    // sum over (G, k) of rot(x_G, k) diag_{G,k} in Q u P, at most HE_MAX_TAPS taps per launch
     phase_begin(ctx, HE_PHASE_TAPS);
     for (int c = 0; c < n_chunks; ++c) {
-        const int k0 = c * HE_MAX_TAPS, nk = std::min(HE_MAX_TAPS, M - k0);
+        const int t0 = c * HE_MAX_TAPS, nt = std::min(HE_MAX_TAPS, T - t0);
         TapTable tt{};
-        tt.n = nk;
+        tt.n = nt;
         tt.r = 1;
-        for (int t = 0; t < nk; ++t) {
-            const int k = k0 + t;
-            tt.key[t] = k ? keys[k - 1] : nullptr;
-            tt.g[t] = k ? gs[k - 1] : 1u;
+        tt.n_sub = n_ct;
+        for (int u = 0; u < nt; ++u) {
+            const int G = (t0 + u) / M, k = (t0 + u) - G * M;
+            tt.key[u] = k ? keys[k - 1] : nullptr;
+            tt.g[u] = k ? gs[k - 1] : 1u;
+            tt.sub[u] = (uint8_t)G;
         }
-        launch_ks_mac_ext(ctx, rb.D, XP, pts + (size_t)k0 * LK * N, tt, c ? AX2 : AX, B);
+        launch_ks_mac_ext(ctx, rb.D, XP, pts + (size_t)t0 * LK * N, tt, c ? AX2 : AX, B);
         if (c) {
             std::vector<const uint64_t*> xa(B), xb(B);
             std::vector<uint64_t*> xo(B);
@@ -233,10 +243,10 @@ extern "C" int he_fc_layer_batch(he_ctx* ctx, const he_ct* in, int B, const int3
         launch_ks_combine(ctx, AX, ext_ct, rb.v, ct, nullptr, nullptr, op, B, 1u);
     }
     phase_end(ctx);
-    ctx->ops[0] += (uint64_t)B * M;
-    ctx->ops[1] += (uint64_t)B * (M - 1);
-    ctx->ops[2] += (uint64_t)B * (M - 1);
-    ctx->ops[3] += (uint64_t)B * (M - 1);
+    ctx->ops[0] += (uint64_t)B * T;
+    ctx->ops[1] += (uint64_t)B * (T - 1);
+    ctx->ops[2] += (uint64_t)B * n_ct * (M - 1);
+    ctx->ops[3] += (uint64_t)B * n_ct * (M - 1);
     // rotate-and-sum over the windows of one period; the last step writes the outputs
     phase_begin(ctx, HE_PHASE_ROTATE);
     const int n_sum = (int)steps.size() - (M - 1);
@@ -254,6 +264,19 @@ extern "C" int he_fc_layer_batch(he_ctx* ctx, const he_ct* in, int B, const int3
     phase_end(ctx);
     for (int b = 0; b < B; ++b) out[b].domain = HE_NTT;
     return he_launch_check(ctx, "he_fc_layer");
+}
+
+extern "C" int he_fc_layer_batch(he_ctx* ctx, const he_ct* in, int B, const int32_t* weights,
+                                 const int32_t* pos, int n_in, int n_out, int period,
+                                 he_ct* out) {
+    return fc_core(ctx, in, B, 1, weights, nullptr, pos, n_in, n_out, period, out);
+}
+
+extern "C" int he_fc_mc_batch(he_ctx* ctx, const he_ct* in, int B, int n_ct,
+                              const int32_t* weights, const int32_t* ct_of, const int32_t* pos,
+                              int n_feat, int n_out, int period, he_ct* out) {
+    if (ctx && !ct_of) return he_fail(ctx, HE_EINVAL, "he_fc_mc: null ciphertext indices");
+    return fc_core(ctx, in, B, n_ct, weights, ct_of, pos, n_feat, n_out, period, out);
 }
 
 extern "C" int he_combine_batch(he_ctx* ctx, const he_ct* in, int B, int n_ch, int block,

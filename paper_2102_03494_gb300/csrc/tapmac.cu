@@ -132,13 +132,15 @@ __device__ __forceinline__ void issue_tap(uint64_t* st, uint64_t* bar, int t, co
             src = pts + ((size_t)(c_lo + c) * tt.n + t) * LN + (size_t)l * N + n0;
         } else if (i < nkeys + npts + ndig) {
             const int q = i - nkeys - npts, ib = q / DNUM, j = q - ib * DNUM;
+            const size_t it = (size_t)(b0 + ib) * tt.n_sub + tt.sub[t];
             dst = st + S::DIG + (ib * DNUM + j) * kTile;
-            src = D + ((size_t)(b0 + ib) * DNUM + j) * LN + (size_t)l * N + src0;
+            src = D + (it * DNUM + j) * LN + (size_t)l * N + src0;
         } else {
             const int q = i - nkeys - npts - ndig;
             const int ib = key ? q : q >> 1, k = key ? 0 : (q & 1);
+            const size_t it = (size_t)(b0 + ib) * tt.n_sub + tt.sub[t];
             dst = st + S::XP + (ib * 2 + k) * kTile;
-            src = XPg + ((size_t)(b0 + ib) * 2 + k) * L * N + (size_t)l * N + src0;
+            src = XPg + (it * 2 + k) * L * N + (size_t)l * N + src0;
         }
         bulk_copy(dst, src, row, bar);
     }

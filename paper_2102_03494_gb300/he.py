@@ -40,6 +40,10 @@ class HeNet(ctypes.Structure):
     _fields_ = [("conv", HeLayout), ("m1", ctypes.c_int32), ("m2", ctypes.c_int32)]
 
 
+class HeMcConv(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in ("C_in", "H", "W", "d", "pad", "r", "O_c")]
+
+
 class HeError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{msg} (code {code})")
@@ -85,6 +89,16 @@ _SIGS = {
                            ctypes.c_int, _CTP], ctypes.c_int),
     "he_combine_batch": ([_P, _CTP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _CTP], ctypes.c_int),
     "he_net_required_steps": ([_P, ctypes.POINTER(HeNet), _I32P, ctypes.c_int], ctypes.c_int),
+    "he_mc_conv_batch": ([_P, _CTP, ctypes.c_int, _I32P, _I32P, ctypes.POINTER(HeMcConv), _CTP],
+                         ctypes.c_int),
+    "he_rotate_sum_batch": ([_P, _CTP, ctypes.c_int, _I32P, ctypes.c_int], ctypes.c_int),
+    "he_fc_mc_batch": ([_P, _CTP, ctypes.c_int, ctypes.c_int, _I32P, _I32P, _I32P, ctypes.c_int,
+                        ctypes.c_int, ctypes.c_int, _CTP], ctypes.c_int),
+    "he_deep_required_steps": ([_P, ctypes.POINTER(HeMcConv), ctypes.c_int, ctypes.c_int, _I32P,
+                                ctypes.c_int], ctypes.c_int),
+    "he_deep_batch": ([_P, _CTP, ctypes.c_int, ctypes.POINTER(HeMcConv), ctypes.c_int,
+                       ctypes.POINTER(_I32P), ctypes.POINTER(_I32P), _I32P, ctypes.c_int, _CTP],
+                      ctypes.c_int),
     "he_net_batch": ([_P, _CTP, ctypes.c_int, _I32P, _I32P, _I32P, _I32P, ctypes.POINTER(HeNet),
                       _CTP], ctypes.c_int),
     "he_ffconv_layer": ([_P, _CTP, _I32P, _I32P, ctypes.POINTER(HeLayout), _CTP], ctypes.c_int),
@@ -379,6 +393,73 @@ class Context:
         f2, pf2 = _i32(F2)
         self._ck(lib().he_net_batch(self.h, ia, B, pw1, pw2, pf1, pf2, ctypes.byref(net), oa),
                  "he_net_batch")
+        return outs
+
+    # ---- deeper networks (several ciphertexts per tensor)
+    @staticmethod
+    def mc_conv(C_in, H, W, d, r, O_c):
+        """Stride-1 same convolution; r = 0 (or None) for the unfactorized layer."""
+        return HeMcConv(C_in, H, W, d, (d - 1) // 2, int(r or 0), O_c)
+
+    def mc_cts(self, channels, H, W):
+        """Ciphertexts holding `channels` maps of H x W in the block layout."""
+        bk = 1 << max(0, (H * W - 1).bit_length())
+        g = (self.N // 2) // bk
+        return -(-channels // g)
+
+    def he_mc_conv_batch(self, cts, W1, W2, conv, outs=None):
+        n_in = self.mc_cts(conv.C_in, conv.H, conv.W)
+        B = len(cts) // n_in
+        n_out = self.mc_cts(conv.O_c, conv.H, conv.W)
+        outs = [self.new_ct() for _ in range(B * n_out)] if outs is None else outs
+        ia, oa = self.ct_array(cts), self.ct_array(outs)
+        w1, pw1 = _i32(W1)
+        if W2 is None:
+            pw2 = None
+        else:
+            w2, pw2 = _i32(W2)
+        self._ck(lib().he_mc_conv_batch(self.h, ia, B, pw1, pw2, ctypes.byref(conv), oa),
+                 "he_mc_conv_batch")
+        return outs
+
+    def he_rotate_sum_batch(self, cts, steps):
+        st, pst = _i32(steps)
+        arr = self.ct_array(cts)
+        self._ck(lib().he_rotate_sum_batch(self.h, arr, len(cts), pst, len(st)), "he_rotate_sum_batch")
+        return cts
+
+    def he_fc_mc_batch(self, cts, n_ct, F, ct_of, pos, period, outs=None):
+        B = len(cts) // n_ct
+        outs = [self.new_ct() for _ in range(B)] if outs is None else outs
+        f, pf = _i32(F)
+        co, pco = _i32(ct_of)
+        ps, pps = _i32(pos)
+        ia, oa = self.ct_array(cts), self.ct_array(outs)
+        self._ck(lib().he_fc_mc_batch(self.h, ia, B, n_ct, pf, pco, pps, len(ps), f.shape[0], period,
+                                      oa), "he_fc_mc_batch")
+        return outs
+
+    def he_deep_required_steps(self, convs, n_cls):
+        arr = (HeMcConv * len(convs))(*convs)
+        out = np.zeros(8192, dtype=np.int32)
+        n = lib().he_deep_required_steps(self.h, arr, len(convs), n_cls, out.ctypes.data_as(_I32P), 8192)
+        if n < 0:
+            raise HeError(n, "he_deep_required_steps: shape does not fit the ring")
+        return [int(x) for x in out[:n]]
+
+    def he_deep_batch(self, cts, convs, W1s, W2s, F, outs=None):
+        n_in = self.mc_cts(convs[0].C_in, convs[0].H, convs[0].W)
+        B = len(cts) // n_in
+        outs = [self.new_ct() for _ in range(B)] if outs is None else outs
+        keep = [_i32(w) for w in W1s]
+        keep2 = [None if w is None else _i32(w) for w in W2s]
+        p1 = (_I32P * len(convs))(*[k[1] for k in keep])
+        p2 = (_I32P * len(convs))(*[(k[1] if k is not None else _I32P()) for k in keep2])
+        f, pf = _i32(F)
+        arr = (HeMcConv * len(convs))(*convs)
+        ia, oa = self.ct_array(cts), self.ct_array(outs)
+        self._ck(lib().he_deep_batch(self.h, ia, B, arr, len(convs), p1, p2, pf, f.shape[0], oa),
+                 "he_deep_batch")
         return outs
 
     def he_rescale(self, ct, out=None):
