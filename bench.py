@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--net", action="store_true",
                     help="time the three-layer network (batch --net-batch, N=2^14) instead")
     ap.add_argument("--net-batch", type=int, default=64)
+    ap.add_argument("--deep", action="store_true",
+                    help="time the deeper 3x32x32 network (factorized ranks vs unfactorized)")
+    ap.add_argument("--deep-batch", type=int, default=16)
     return ap.parse_args()
 
 
@@ -539,6 +542,98 @@ def run_net(args):
     print(json.dumps(line))
 
 
+def run_deep(args):
+    """The deeper network on a batch of encrypted 3 x 32 x 32 images at N = 2^15 (12 + 3
+    primes): three 3 x 3 convolutions 3 -> 64 -> 64 -> 128 channels, each factorized at rank
+    r in {8, 16, 32} or unfactorized, x^2 after each, global sum pooling, 10 classes.  One step
+    = one batch through the whole network; every variant is timed."""
+    import numpy as np
+    import torch
+
+    from paper_2102_03494_gb300 import he
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    B = args.deep_batch
+    stream = torch.cuda.Stream()
+    ctx = he.Context(log_n=LOG_N, n_q=N_Q, n_p=N_P, alpha=ALPHA, stream=stream)
+    chans, H, W, n_cls = (64, 64, 128), 32, 32, 10
+    N = 1 << LOG_N
+
+    def convs_for(r):
+        out, C = [], 3
+        for O in chans:
+            out.append(ctx.mc_conv(C, H, W, 3, r, O))
+            C = O
+        return out
+
+    steps = ctx.he_deep_required_steps(convs_for(8), n_cls)
+    sk = ctx.he_keygen_secret(1000 + rank)
+    ctx.he_keygen_galois(sk, 2000 + rank, steps)
+    rng = np.random.default_rng(11)
+    xs = rng.integers(0, 256, (B, 3, H, W))
+    cts = []
+    for b in range(B):
+        v = np.zeros(N, dtype=np.int64)
+        for c in range(3):
+            v[c * 1024: c * 1024 + H * W] = xs[b, c].reshape(-1)
+        cts.append(ctx.he_encrypt(sk, v, 3000 + b))
+    outs = [ctx.new_ct() for _ in range(B)]
+    variants = []
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    for r in (8, 16, 32, 0):
+        convs = convs_for(r)
+        W1s, W2s, C = [], [], 3
+        for O in chans:
+            rr = r or O
+            W1s.append(rng.integers(-8, 9, (rr, C, 3, 3)).astype(np.int32))
+            W2s.append(rng.integers(-8, 9, (O, r)).astype(np.int32) if r else None)
+            C = O
+        F = rng.integers(-8, 9, (n_cls, C)).astype(np.int32)
+
+        def step():
+            ctx.he_deep_batch(cts, convs, W1s, W2s, F, outs)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        ctx.he_reset_op_counts()
+        ctx.he_phase_times()
+        ctx.he_set_phase_timing(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        phases = ctx.he_phase_times()
+        ctx.he_set_phase_timing(False)
+        ms = e0.elapsed_time(e1) / args.steps
+        ops = {k: v // (B * args.steps) for k, v in ctx.he_op_counts().items()}
+        variants.append({"rank": r or "unfactorized", "images_per_s": B / (ms / 1000.0),
+                         "ms_per_batch": ms, "ops_per_image": ops,
+                         "phases_ms_per_batch": {k: v[0] / args.steps for k, v in phases.items() if v[1]}})
+    clk = clocks.stop()
+    if rank != 0:
+        return
+    unf = variants[-1]["ms_per_batch"]
+    for v in variants[:-1]:
+        v["speedup_vs_unfactorized"] = unf / v["ms_per_batch"]
+    best = variants[0]
+    line = {"metric": "encrypted 3x32x32 network throughput (images/s) at N=2^15",
+            "value": best["images_per_s"], "unit": "images/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": best["ms_per_batch"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "3x32x32 -> 3x3 conv 64 -> x^2 -> 3x3 conv 64 -> x^2 -> 3x3 conv "
+                                   "128 -> x^2 -> sum pool -> FC 128->10, N=2^15, 12x50-bit q, "
+                                   "3x60-bit p, alpha=3; value = rank 8",
+                       "batch_per_gpu": B, "galois_keys": len(steps) - 1},
+            "clocks": clk, "variants": variants}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -549,6 +644,9 @@ def main():
         return
     if args.net:
         run_net(args)
+        return
+    if args.deep:
+        run_deep(args)
         return
     run(args)
 

@@ -310,14 +310,15 @@ int he_rotate_sum_batch(he_ctx* ctx, he_ct* cts, int n, const int32_t* steps, in
 int he_fc_mc_batch(he_ctx* ctx, const he_ct* in, int B, int n_ct, const int32_t* weights,
                    const int32_t* ct_of, const int32_t* pos, int n_feat, int n_out, int period,
                    he_ct* out);
-/* Steps whose keys he_deep_batch needs (layer taps and folds, pooling, classifier), then
- * HE_RELIN_KEY; count returned, at most cap written. */
+/* Steps whose keys he_deep_batch needs (layer taps and folds, classifier), then HE_RELIN_KEY;
+ * count returned, at most cap written. */
 int he_deep_required_steps(const he_ctx* ctx, const he_mc_conv* convs, int n_layers, int n_cls,
                            int32_t* steps_out, int cap);
 /* The deeper network on B images: for each layer he_mc_conv_batch then the square
- * (he_multiply_batch) of every output ciphertext; global sum pooling inside the blocks
- * (he_rotate_sum_batch); a fully connected layer to n_cls classes over the pooled channel sums
- * (he_fc_mc_batch, period N/2).  lowrank_w[l] / restore_w[l] as for he_mc_conv_batch
+ * (he_multiply_batch) of every output ciphertext; then global sum pooling and a fully
+ * connected layer to n_cls classes, evaluated together as one fully connected layer over every
+ * activation (feature (c, pixel) weighted fc_w[j][c]; he_fc_mc_batch, period N/2) -- the
+ * pooling costs no rotation.  lowrank_w[l] / restore_w[l] as for he_mc_conv_batch
  * (restore_w[l] NULL for unfactorized layers); fc_w host int32 [n_cls][O_c of the last layer].
  * in: [B][ceil(C0 / g)] packed as above; out[B]: class j at slots p of row 0 with
  * p mod next_pow2(n_cls) = j.  Intermediate ciphertexts live in a context-owned buffer. */

@@ -15,19 +15,22 @@ Packing (the readings, each also listed among the design readings):
   * layer, W1 under DensePack: for every input ciphertext the d^2 filter taps are rotations by
     delta = (i - pad) W + (j - pad) (hoisted, left in Q u P as in ffconv.py's dp_shift_ext);
     for every low-rank channel c' the tap products of all input ciphertexts are summed in Q u P
-    and divided by P once; a full rotate-and-sum over the g blocks (acc <- acc + rot(acc,
-    Bk 2^e), e < log2 g) then leaves y1[c'] replicated in every block;
+    and divided by P once; the sum over the g blocks, y1[c'] = sum_{u<g} rot(acc, u Bk), then
+    leaves the channel's output replicated in every block -- its g - 1 rotations are hoisted
+    from one ModUp and summed in Q u P with one ModDown (cheaper than log2 g sequential
+    rotate-and-sum steps, each with its own ModUp and ModDown);
   * W2 (and the unfactorized packing) without rotations: output ciphertext G is
     sum_c' y1[c'] * P[G][c'] with P[G][c'] holding W2[G g + j][c'] on the pixels of block j
     (a block-wise ConvPack product; the unfactorized layer uses W2 = identity, O_c = r);
-  * pooling: rotate-and-sum inside the blocks (steps 1, 2, ..., Bk/2): block j's first slot
-    then holds the sum over its H x W pixels (other slots hold partial sums, never read);
-  * fully connected over the pooled ciphertexts: the diagonal schedule of network.py with the
-    taps of every input ciphertext summed in Q u P before one ModDown, positions
-    (c mod g) Bk in ciphertext c // g, period N/2; output j at slots p = j mod M.
+  * pooling and classifier in one linear map: logit_j = sum_c F[j][c] sum_pixels a[c, pixel],
+    i.e. a fully connected layer whose features are all C H W activations (feature (c, pixel)
+    at slot (c mod g) Bk + pixel of ciphertext c // g, weight F[j][c]); evaluated with the
+    diagonal schedule of network.py, the taps of every input ciphertext summed in Q u P before
+    one ModDown, period N/2; output j at slots p = j mod M.  (The in-block rotate-and-sum
+    he_pool is kept as a step of its own.)
 """
 from dataclasses import dataclass, field
-from typing import List, Optional, Tuple
+from typing import List, Optional
 
 import numpy as np
 
@@ -154,8 +157,9 @@ def restore_slots(W2, shape: DeepShape, n: int, G: int, c: int, O_c: int):
 
 
 def fold_steps(shape: DeepShape, n: int):
+    """Rotations of the block sum: u Bk for u = 1 .. g - 1."""
     g = per_ct(shape, n)
-    return [shape.Bk << e for e in range(g.bit_length() - 1)]
+    return [u * shape.Bk for u in range(1, g)]
 
 
 def he_conv(prm, cts_in, W1, W2, spec: ConvSpec, C_in: int, shape: DeepShape, keys,
@@ -189,10 +193,15 @@ def he_conv(prm, cts_in, W1, W2, spec: ConvSpec, C_in: int, shape: DeepShape, ke
                     acc = [bfv.rns_add(acc[h], term[h], prm.qp) for h in range(2)]
                     ops.addcc += 1
         ct = bfv.Ct(bfv.moddown(prm, acc[0]), bfv.moddown(prm, acc[1]))
-        for st in fold_steps(shape, n):
-            ct = bfv.add(prm, ct, bfv.rotate(prm, ct, st, keys))
-            ops.rot += 1
-            ops.addcc += 1
+        fs = fold_steps(shape, n)
+        if fs:
+            pairs = [bfv.scale_by_p_ext(prm, ct)] + bfv.rotate_hoisted_ext(prm, ct, fs, keys)
+            tot = pairs[0]
+            for pr in pairs[1:]:
+                tot = [bfv.rns_add(tot[h], pr[h], prm.qp) for h in range(2)]
+                ops.addcc += 1
+            ops.rot += len(fs)
+            ct = bfv.Ct(bfv.moddown(prm, tot[0]), bfv.moddown(prm, tot[1]))
         y1.append(ct)
     O_c = spec.O_c
     W2m = np.eye(O_c, dtype=np.int64) if W2 is None else np.asarray(W2)
@@ -228,32 +237,46 @@ def he_pool(prm, ct, shape: DeepShape, keys, ops: OpCount = None):
 
 
 def fc_inputs(C: int, shape: DeepShape, n: int):
-    """(ciphertext, position) of every pooled feature c."""
+    """(ciphertext, position) of every pooled feature c (block start)."""
     g = per_ct(shape, n)
     return [(c // g, (c % g) * shape.Bk) for c in range(C)]
 
 
-def fc_diagonals_multi(F, C: int, shape: DeepShape, n: int):
-    """diag[G][k] of the multi-ciphertext fully connected layer (period N/2)."""
+def pooled_fc_features(F, C: int, shape: DeepShape, n: int):
+    """The classifier with the sum pooling folded in: features (c, pixel) at (ciphertext c // g,
+    slot (c mod g) Bk + pixel) with weight F[j][c]; returns (weights [m][C H W], ct_of, pos)."""
+    g = per_ct(shape, n)
+    hw = shape.H * shape.W
+    F = np.asarray(F, dtype=np.int64)
+    ct_of, pos = [], []
+    for c in range(C):
+        for p in range(hw):
+            ct_of.append(c // g)
+            pos.append((c % g) * shape.Bk + p)
+    return np.repeat(F, hw, axis=1), ct_of, pos
+
+
+def fc_diagonals_multi(F, ct_of, pos, n: int, per: int):
+    """diag[G][k] of the fully connected layer over several ciphertexts: feature i at slot
+    pos[i] (inside one period) of ciphertext ct_of[i]."""
     F = np.asarray(F, dtype=np.int64)
     m = F.shape[0]
     M = next_pow2(m)
     half = n // 2
-    feats = fc_inputs(C, shape, n)
-    nG = max(G for G, _ in feats) + 1
-    inv = [dict() for _ in range(nG)]
-    for i, (G, p) in enumerate(feats):
-        inv[G][p] = i
+    nG = max(ct_of) + 1
+    inv = -np.ones((nG, per), dtype=np.int64)
+    for i, (G, p) in enumerate(zip(ct_of, pos)):
+        if not 0 <= p < per or inv[G, p] >= 0:
+            raise ValueError("feature positions must be distinct and inside one period")
+        inv[G, p] = i
     diags = [[np.zeros(n, dtype=np.int64) for _ in range(M)] for _ in range(nG)]
+    p_all = np.arange(half)
+    j_all = p_all % M
     for G in range(nG):
         for k in range(M):
-            for p in range(half):
-                j = p % M
-                if j >= m:
-                    continue
-                i = inv[G].get((p + k) % half)
-                if i is not None:
-                    diags[G][k][p] = F[j, i]
+            i_all = inv[G, (p_all + k) % per]
+            ok = (j_all < m) & (i_all >= 0)
+            diags[G][k][p_all[ok]] = F[j_all[ok], i_all[ok]]
     return diags
 
 
@@ -262,9 +285,10 @@ def fc_sum_steps(m: int, n: int):
     return [M << e for e in range((n // 2 // M).bit_length() - 1)]
 
 
-def he_fc_multi(prm, cts, F, C: int, shape: DeepShape, keys, ops: OpCount = None):
+def he_fc_multi(prm, cts, F, ct_of, pos, keys, ops: OpCount = None):
+    """Fully connected layer over the ciphertexts cts (period N/2)."""
     ops = ops if ops is not None else OpCount()
-    diags = fc_diagonals_multi(F, C, shape, prm.n)
+    diags = fc_diagonals_multi(F, ct_of, pos, prm.n, prm.n // 2)
     M = len(diags[0])
     acc = None
     for G, ct in enumerate(cts):
@@ -294,7 +318,7 @@ def deep_steps(shape: DeepShape, n: int):
     st = []
     for spec in shape.convs:
         st += [dl for (_, _, dl) in tap_offsets(spec, shape) if dl != 0]
-    st += fold_steps(shape, n) + pool_steps(shape)
+    st += fold_steps(shape, n)
     st += list(range(1, next_pow2(shape.n_cls))) + fc_sum_steps(shape.n_cls, n)
     out = []
     for s in st:
@@ -316,8 +340,8 @@ def he_deep(prm, cts_in, weights, shape: DeepShape, keys, rlk, ops: OpCount = No
         C = spec.O_c
         if trace is not None:
             trace.append(cts)
-    pooled = [he_pool(prm, c, shape, keys, ops) for c in cts]
-    return he_fc_multi(prm, pooled, weights["fc"], C, shape, keys, ops)
+    Fx, ct_of, pos = pooled_fc_features(weights["fc"], C, shape, prm.n)
+    return he_fc_multi(prm, cts, Fx, ct_of, pos, keys, ops)
 
 
 def rand_weights(shape: DeepShape, seed: int, lo=-8, hi=8):
@@ -344,6 +368,5 @@ def expected_rotations(shape: DeepShape, n: int):
         rot += n_cts(C, g) * taps + r * len(fold_steps(shape, n))
         C = spec.O_c
     nC = n_cts(C, g)
-    rot += nC * len(pool_steps(shape))
     rot += nC * (next_pow2(shape.n_cls) - 1) + len(fc_sum_steps(shape.n_cls, n))
     return rot

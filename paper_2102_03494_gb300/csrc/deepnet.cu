@@ -1,6 +1,6 @@
 // deepnet.cu -- convolution layers over several ciphertexts per tensor, and the deeper network
-// built from them (stride-1 "same" convolutions, factorized or not, x^2, global sum pooling,
-// a fully connected classifier).
+// built from them (stride-1 "same" convolutions, factorized or not, x^2, global sum pooling
+// and a fully connected classifier, the last two evaluated as one linear map).
 //
 // Tensor layout: channel c of an H x W map occupies block c mod g of ciphertext c / g (row 0),
 // block size Bk = next_pow2(H W), g = (N/2) / Bk, pixel (h, w) at offset h W + w.
@@ -8,8 +8,10 @@
 // Layer: for every input ciphertext the d^2 taps are rotations by delta = (i - pad) W +
 // (j - pad), hoisted and left in Q u P; the fused tap kernel sums, for each low-rank channel c',
 // the tap products of all input ciphertexts of an image (per-tap input selection) and one
-// ModDown follows.  A full rotate-and-sum over the g blocks (acc <- acc + rot(acc, Bk 2^e))
-// leaves y1[c'] replicated in every block, so the restore needs no rotation: output ciphertext
+// ModDown follows.  The block sum y1[c'] = sum_{u<g} rot(acc, u Bk) -- its g - 1 rotations
+// hoisted from one ModUp and summed in Q u P by the same tap kernel against the plaintext 1,
+// one ModDown -- leaves the channel replicated in every block, so the restore needs no
+// rotation: output ciphertext
 // G is sum_c' y1[c'] * P[G][c'], P[G][c'] holding W2[G g + j][c'] on the pixels of block j
 // (for the unfactorized layer W2 is the identity and r = O_c).
 #include <algorithm>
@@ -77,6 +79,17 @@ __global__ void k_mc_restore_slots(const int32_t* __restrict__ W2, int r, int O_
     slots[(size_t)blockIdx.y * N + p] = v;
 }
 
+// copies[t][l][n] = 2^64 mod q_l (the plaintext 1 in Montgomery form), t < copies, l < rows.
+__global__ void k_mont_ones(uint64_t* __restrict__ out, int rows, int copies, int logN,
+                            const ModConst* __restrict__ mods) {
+    const int N = 1 << logN;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int l = blockIdx.y;
+    const uint64_t one = to_mont(1, mods[l]);
+    for (int t = 0; t < copies; ++t) out[((size_t)t * rows + l) * N + n] = one;
+}
+
 struct McGeom {
     int Bk, lbk, g, n_in, n_out, r, taps, T;
 };
@@ -105,7 +118,7 @@ std::vector<int32_t> mc_conv_steps(const he_mc_conv& cv, const McGeom& m) {
             const int dl = (i - cv.pad) * cv.W + (j - cv.pad);
             if (dl) st.push_back(dl);
         }
-    for (int b = m.Bk; b < m.Bk * m.g; b <<= 1) st.push_back(b);
+    for (int u = 1; u < m.g; ++u) st.push_back(u * m.Bk);
     return st;
 }
 
@@ -136,22 +149,27 @@ extern "C" int he_mc_conv_batch(he_ctx* ctx, const he_ct* in, int B, const int32
             tap_g[i * conv->d + j] = galois_elt(ctx, dl);
             if ((rc = he_get_key(ctx, tap_g[i * conv->d + j], &tap_key[i * conv->d + j]))) return rc;
         }
+    // block sum: rotations by u Bk, u = 1 .. g - 1 (tap u of the block-sum tap table)
     std::vector<uint32_t> fold_g;
-    for (int b = m.Bk; b < m.Bk * m.g; b <<= 1) {
-        fold_g.push_back(galois_elt(ctx, b));
-        const uint64_t* k = nullptr;
-        if ((rc = he_get_key(ctx, fold_g.back(), &k))) return rc;
+    std::vector<const uint64_t*> fold_key;
+    for (int u = 1; u < m.g; ++u) {
+        fold_g.push_back(galois_elt(ctx, u * m.Bk));
+        fold_key.push_back(nullptr);
+        if ((rc = he_get_key(ctx, fold_g.back(), &fold_key.back()))) return rc;
     }
+    if (m.g > HE_MAX_TAPS) return he_fail(ctx, HE_EINVAL, "he_mc_conv: too many blocks per row");
     const size_t N = ctx->N, ct = 2 * (size_t)L * N, ext_ct = 2 * (size_t)LK * N;
     const size_t items = (size_t)B * m.n_in;
     const int CH = std::min(m.r, 8);                         // low-rank channels per pass
     const int tmax = std::min(m.T, HE_MAX_TAPS);             // taps per tap launch
     const int n_tc = (m.T + tmax - 1) / tmax;
-    const int fold_chunk = std::min(B * CH, 16);
+    const int fold_items = B * CH;                           // ciphertexts block-summed at once
     const size_t w1n = (size_t)m.r * conv->C_in * m.taps, w2n = restore_w ? (size_t)conv->O_c * m.r : 0;
     const size_t need = items * ct * 2                            // X, P x
                         + items * rot_scratch_per_item(ctx)       // input ModUp digits
-                        + (size_t)fold_chunk * rot_scratch_per_item(ctx)
+                        + (size_t)fold_items * rot_scratch_per_item(ctx)
+                        + (size_t)fold_items * (ct + ext_ct)      // P y1, block sums
+                        + (size_t)m.g * LK * N                    // the plaintext 1
                         + (size_t)CH * tmax * (2 * N + (size_t)LK * N)   // tap slots, tmp, plaintexts
                         + (size_t)B * CH * ext_ct * (n_tc > 1 ? 2 : 1)
                         + (size_t)B * CH * ct * 3                 // y1, its fold partner, ModDown
@@ -162,7 +180,10 @@ extern "C" int he_mc_conv_batch(he_ctx* ctx, const he_ct* in, int B, const int32
     uint64_t* X = arena_take(ctx, items * ct);
     uint64_t* XP = arena_take(ctx, items * ct);
     RotBufs rb = rot_bufs_take(ctx, (int)items);
-    RotBufs rbf = rot_bufs_take(ctx, fold_chunk);
+    RotBufs rbf = rot_bufs_take(ctx, fold_items);
+    uint64_t* YP = arena_take(ctx, (size_t)fold_items * ct);
+    uint64_t* AF = arena_take(ctx, (size_t)fold_items * ext_ct);
+    uint64_t* ones = arena_take(ctx, (size_t)m.g * LK * N);
     int64_t* slots = (int64_t*)arena_take(ctx, (size_t)CH * tmax * N);
     uint64_t* tmp = arena_take(ctx, (size_t)CH * tmax * N);
     uint64_t* pts = arena_take(ctx, (size_t)CH * tmax * LK * N);
@@ -176,7 +197,10 @@ extern "C" int he_mc_conv_batch(he_ctx* ctx, const he_ct* in, int B, const int32
     uint64_t* rpts = arena_take(ctx, (size_t)m.n_out * CH * L * N);
     int32_t* d_w1 = (int32_t*)arena_take(ctx, (w1n + 1) / 2);
     int32_t* d_w2 = w2n ? (int32_t*)arena_take(ctx, (w2n + 1) / 2) : nullptr;
-    if (!d_w1 || !rb.v || !rbf.v) return he_fail(ctx, HE_ENOMEM, "he_mc_conv: scratch");
+    if (!d_w1 || !rb.v || !rbf.v || !ones) return he_fail(ctx, HE_ENOMEM, "he_mc_conv: scratch");
+    ++ctx->launches;
+    k_mont_ones<<<dim3((unsigned)((N + 255) / 256), LK), 256, 0, ctx->stream>>>(ones, LK, m.g,
+                                                                            ctx->logN, ctx->d_mod);
 
     HE_CHECK_CUDA(ctx, cudaMemcpyAsync(d_w1, lowrank_w, w1n * 4, cudaMemcpyHostToDevice, ctx->stream));
     if (w2n)
@@ -244,17 +268,32 @@ extern "C" int he_mc_conv_batch(he_ctx* ctx, const he_ct* in, int B, const int32
             launch_ks_combine(ctx, AX, ext_ct, V, ct, nullptr, nullptr, op, it, 1u);
         }
         phase_end(ctx);
-        // fold over the g blocks: y1 replicated in every block
-        phase_begin(ctx, HE_PHASE_ROTATE);
+        // block sum: y1 = sum_{u<g} rot(Y, u Bk) (hoisted, summed in Q u P, one ModDown)
         uint64_t* Ya = Y;
-        uint64_t* Yb = Y2;
-        for (uint32_t gf : fold_g) {
-            std::vector<uint64_t*> o(it);
-            for (int q = 0; q < it; ++q) o[q] = Yb + (size_t)q * ct;
-            if ((rc = rotate_contig(ctx, Ya, it, gf, Ya, o, rbf, fold_chunk))) return rc;
-            std::swap(Ya, Yb);
+        if (m.g > 1) {
+            phase_begin(ctx, HE_PHASE_ROTATE);
+            modup_items(ctx, Y, it, 1u, rbf);
+            launch_scale_p(ctx, Y, YP, it);
+            TapTable ft{};
+            ft.n = m.g;
+            ft.r = 1;
+            ft.n_sub = 1;
+            for (int u = 0; u < m.g; ++u) {
+                ft.key[u] = u ? fold_key[u - 1] : nullptr;
+                ft.g[u] = u ? fold_g[u - 1] : 1u;
+            }
+            launch_ks_mac_ext(ctx, rbf.D, YP, ones, ft, AF, it);
+            ntt_inverse(ctx, AF + (size_t)L * N, it * 2, (size_t)LK * N, ctx->K, L);
+            launch_moddown_conv(ctx, AF, ext_ct, V, ct, it);
+            ntt_forward(ctx, V, it * 2, (size_t)L * N, L, 0);
+            std::vector<uint64_t*> yo(it);
+            for (int q = 0; q < it; ++q) yo[q] = Y2 + (size_t)q * ct;
+            auto op = upload_out_ptrs(ctx, yo);
+            if (!op) return he_fail(ctx, HE_ECUDA, "pointer table upload failed");
+            launch_ks_combine(ctx, AF, ext_ct, V, ct, nullptr, nullptr, op, it, 1u);
+            Ya = Y2;
+            phase_end(ctx);
         }
-        phase_end(ctx);
         // restore: out[b][G] (+)= sum_c y1[b][c] * P[G][c]
         phase_begin(ctx, HE_PHASE_RESTORE);
         ++ctx->launches;
@@ -286,14 +325,14 @@ extern "C" int he_mc_conv_batch(he_ctx* ctx, const he_ct* in, int B, const int32
         launch_mac(ctx, a1, a2, cn, a3, a4, B * m.n_out, L);
         phase_end(ctx);
     }
-    // MulPC: tap products and nonzero restore products; AddCC: their sums (the folds' additions
-    // and rotations are counted by rotate_contig); rotations: the hoisted taps
-    const uint64_t taps_rot = (uint64_t)m.n_in * (m.taps - 1);
+    // MulPC: tap products and nonzero restore products; AddCC: their sums and the block sums;
+    // rotations (all hoisted): the taps and the block sums
+    const uint64_t rot = (uint64_t)m.n_in * (m.taps - 1) + (uint64_t)m.r * (m.g - 1);
     ctx->ops[0] += (uint64_t)B * ((uint64_t)m.r * m.T + nz_restore);
-    ctx->ops[1] += (uint64_t)B * ((uint64_t)m.r * (m.T - 1) +
+    ctx->ops[1] += (uint64_t)B * ((uint64_t)m.r * (m.T - 1 + m.g - 1) +
                                   (nz_restore > (uint64_t)m.n_out ? nz_restore - m.n_out : 0));
-    ctx->ops[2] += (uint64_t)B * taps_rot;
-    ctx->ops[3] += (uint64_t)B * taps_rot;
+    ctx->ops[2] += (uint64_t)B * rot;
+    ctx->ops[3] += (uint64_t)B * rot;
     for (int i = 0; i < B * m.n_out; ++i) out[i].domain = HE_NTT;
     return he_launch_check(ctx, "he_mc_conv");
 }
@@ -348,7 +387,6 @@ extern "C" int he_deep_required_steps(const he_ctx* ctx, const he_mc_conv* convs
         if (mc_geom(c, &convs[l], &m)) return HE_EINVAL;
         for (int32_t s : mc_conv_steps(convs[l], m)) st.push_back(s);
     }
-    for (int s = 1; s < m.Bk; s <<= 1) st.push_back(s);                 // pooling
     const int M = next_pow2_i(n_cls);
     for (int k = 1; k < M; ++k) st.push_back(k);                          // classifier
     for (int s = M; s < half; s <<= 1) st.push_back(s);
@@ -414,18 +452,18 @@ extern "C" int he_deep_batch(he_ctx* ctx, const he_ct* in, int B, const he_mc_co
         if ((rc = he_multiply_batch(ctx, y.data(), y.data(), (int)y.size(), a.data()))) return rc;
         cur = a;
     }
-    // global sum pooling inside the blocks, then the classifier over the pooled ciphertexts
+    // global sum pooling and the classifier as one linear map: logit_j = sum over (c, pixel) of
+    // F[j][c] a[c, pixel], a fully connected layer over every activation of the last layer
     const McGeom& m = gm.back();
-    std::vector<int32_t> pool;
-    for (int s = 1; s < m.Bk; s <<= 1) pool.push_back(s);
-    if ((rc = he_rotate_sum_batch(ctx, cur.data(), (int)cur.size(), pool.data(), (int)pool.size())))
-        return rc;
-    const int C = convs[n_layers - 1].O_c;
-    std::vector<int32_t> ct_of(C), pos(C);
-    for (int c = 0; c < C; ++c) {
-        ct_of[c] = c / m.g;
-        pos[c] = (c % m.g) * m.Bk;
-    }
-    return he_fc_mc_batch(ctx, cur.data(), B, m.n_out, fc_w, ct_of.data(), pos.data(), C, n_cls,
-                          (int)(ctx->N / 2), out);
+    const int C = convs[n_layers - 1].O_c, hw = convs[0].H * convs[0].W;
+    std::vector<int32_t> ct_of((size_t)C * hw), pos((size_t)C * hw), Fx((size_t)n_cls * C * hw);
+    for (int c = 0; c < C; ++c)
+        for (int p = 0; p < hw; ++p) {
+            const size_t i = (size_t)c * hw + p;
+            ct_of[i] = c / m.g;
+            pos[i] = (c % m.g) * m.Bk + p;
+            for (int j = 0; j < n_cls; ++j) Fx[(size_t)j * C * hw + i] = fc_w[(size_t)j * C + c];
+        }
+    return he_fc_mc_batch(ctx, cur.data(), B, m.n_out, Fx.data(), ct_of.data(), pos.data(),
+                          C * hw, n_cls, (int)(ctx->N / 2), out);
 }

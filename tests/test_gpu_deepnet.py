@@ -33,6 +33,7 @@ def small():
     ctx = make_ctx(prm)
     s = bfv.keygen_secret(prm, 1)
     steps = deepnet.deep_steps(SHAPE, prm.n)
+    steps += [st for st in deepnet.pool_steps(SHAPE) if st not in steps]
     keys, blob = {}, []
     for st in steps:
         g = bfv.galois_of(st, prm.n)
@@ -93,10 +94,11 @@ def test_pool_and_classifier_are_bit_exact(small):
     feats = deepnet.fc_inputs(C, SHAPE, prm.n)
     imgs = [[deepnet.he_pool(prm, encrypt_slots(prm, s, rng.integers(0, prm.t, prm.n), 300 + 10 * b + g),
                              SHAPE, keys) for g in range(2)] for b in range(2)]
-    got = ctx.he_fc_mc_batch([upload_ntt(ctx, c) for img in imgs for c in img], 2, F,
-                             [G for G, _ in feats], [p for _, p in feats], prm.n // 2)
+    ct_of, pos = [G for G, _ in feats], [p for _, p in feats]
+    got = ctx.he_fc_mc_batch([upload_ntt(ctx, c) for img in imgs for c in img], 2, F, ct_of, pos,
+                             prm.n // 2)
     for b in range(2):
-        want = deepnet.he_fc_multi(prm, imgs[b], F, C, SHAPE, keys)
+        want = deepnet.he_fc_multi(prm, imgs[b], F, ct_of, pos, keys)
         assert (download_coeff(ctx, got[b]) == want.stack()).all(), b
 
 
@@ -108,6 +110,7 @@ def test_network_is_bit_exact(small):
     steps = ctx.he_deep_required_steps(convs, SHAPE.n_cls)
     assert steps[-1] == he.HE_RELIN_KEY
     assert sorted(steps[:-1]) == sorted(deepnet.deep_steps(SHAPE, prm.n))
+    # pooling is folded into the classifier: no in-block steps beyond the classifier's
     rng = np.random.default_rng(7)
     xs = [rng.integers(0, 256, (3, 8, 8)) for _ in range(2)]
     cts = [encrypt_tensor(prm, s, x, SHAPE, 400 + 10 * b) for b, x in enumerate(xs)]

@@ -63,7 +63,7 @@ def test_pack_tensor_layout():
 def ring():
     prm = params.Params(log_n=11, n_q=5, n_p=2, alpha=2)
     s = bfv.keygen_secret(prm, 1)
-    keys, _ = oracle_keys(prm, s, deepnet.deep_steps(SHAPE, prm.n))
+    keys, _ = oracle_keys(prm, s, deepnet.deep_steps(SHAPE, prm.n) + deepnet.pool_steps(SHAPE))
     rlk = bfv.relin_key(prm, s, 2)
     return prm, s, keys, rlk
 
@@ -110,6 +110,27 @@ def test_encrypted_layers_decrypt_to_plain(ring):
         C = spec.O_c
 
 
+def test_pooling_folded_into_the_classifier(ring):
+    """The classifier over all activations with repeated weights equals sum pooling followed
+    by the classifier over the pooled sums (both decrypted)."""
+    prm, s, keys, rlk = ring
+    rng = np.random.default_rng(13)
+    C = 20
+    a = rng.integers(0, prm.t, (C, 8, 8))
+    cts = [bfv.encrypt(prm, s, encoder.encode(v, prm), 40 + i)
+           for i, v in enumerate(deepnet.pack_tensor(a, SHAPE, prm.n))]
+    F = rng.integers(-8, 9, (SHAPE.n_cls, C))
+    Fx, ct_of, pos = deepnet.pooled_fc_features(F, C, SHAPE, prm.n)
+    merged = dec(prm, s, deepnet.he_fc_multi(prm, cts, Fx, ct_of, pos, keys))
+    pooled = [deepnet.he_pool(prm, c, SHAPE, keys) for c in cts]
+    feats = deepnet.fc_inputs(C, SHAPE, prm.n)
+    two = dec(prm, s, deepnet.he_fc_multi(prm, pooled, F, [G for G, _ in feats],
+                                          [p for _, p in feats], keys))
+    want = (F.astype(object) @ a.reshape(C, -1).sum(axis=1).astype(object)) % prm.t
+    M = deepnet.next_pow2(SHAPE.n_cls)
+    assert (merged[:M][:SHAPE.n_cls] == want).all() and (two[:M][:SHAPE.n_cls] == want).all()
+
+
 def test_network_decrypts_to_plain_and_counts(ring):
     prm, s, keys, rlk = ring
     w = deepnet.rand_weights(SHAPE, 9)
@@ -135,9 +156,10 @@ def test_factorized_needs_fewer_rotations():
     unf = deepnet.DeepShape(3, 32, 32, [deepnet.ConvSpec(64, None), deepnet.ConvSpec(64, None),
                                         deepnet.ConvSpec(128, None)])
     rf, ru = deepnet.expected_rotations(fac, n), deepnet.expected_rotations(unf, n)
-    # taps: 8 (1 ct) + 32 + 32 (4 cts); folds 4 per channel; pooling 10 x 8; classifier 8 x 15 + 10
-    assert rf == 8 + 32 + 32 + 4 * (8 + 8 + 8) + 80 + 130
-    assert ru == 8 + 32 + 32 + 4 * (64 + 64 + 128) + 80 + 130
+    # taps: 8 (1 ct) + 32 + 32 (4 cts); block sums 15 hoisted per channel; pooling folded
+    # into the classifier: 8 x 15 + 10
+    assert rf == 8 + 32 + 32 + 15 * (8 + 8 + 8) + 130
+    assert ru == 8 + 32 + 32 + 15 * (64 + 64 + 128) + 130
 
 
 def test_planted_restore_block_slip_is_caught(ring, monkeypatch):
