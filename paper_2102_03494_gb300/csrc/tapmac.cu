@@ -3,21 +3,25 @@
 // Same arithmetic as k_ks_mac_ext (kernels.cu): for coefficient n of limb l of image b,
 //   acc_k[c'] = sum_tap pt[c'][tap] * x_k(tap)   over Q u P,
 //   x_0(tap) = sum_j D_j[perm_g(n)] key_j,0 + (P c0)[perm_g(n)],  x_1(tap) = sum_j D_j[perm_g(n)] key_j,1.
-// A CTA owns an aligned tile of 256 coefficients of one limb for two images.  For every tap the
-// operands the tile needs are contiguous 2 KiB rows: the 2 dnum key rows and the channel
-// plaintext rows at the tile, and -- because the NTT-domain automorphism maps every aligned
-// block of 2^k positions onto an aligned block of 2^k positions (the bits of p above bit k only
-// feed the bits of perm(p) above bit k) -- the ModUp digit rows and the P c0 row of the one
-// aligned 256-block that holds perm_g of the tile.  Warp 0 copies them with cp.async.bulk into
-// one of two shared-memory stages, completed on an mbarrier, while all warps compute on the
-// other stage.  Every wait is bounded: on expiry the kernel sets a bit in the context's device
-// error word, waits (again bounded) for its own copies and returns.
+// A CTA owns an aligned tile of 128 or 256 coefficients of one limb for two images.  For every
+// tap the operands the tile needs are contiguous rows of the tile's size: the 2 dnum key rows
+// and the channel plaintext rows at the tile, and -- because the NTT-domain automorphism maps
+// every aligned block of 2^k positions onto an aligned block of 2^k positions (the bits of p
+// above bit k only feed the bits of perm(p) above bit k) -- the ModUp digit rows and the P c0
+// row of the one aligned block that holds perm_g of the tile.  Warp 0 copies them with
+// cp.async.bulk into one of two shared-memory stages, completed on an mbarrier, while all warps
+// compute on the other stage.  Every wait is bounded: on expiry the kernel sets a bit in the
+// context's device error word, waits (again bounded) for its own copies and returns.
 #include "he_internal.cuh"
 #include "kernels.cuh"
 
 namespace {
 
-constexpr int kTile = 256;
+// Coefficients per CTA (one per thread): 128 when the key has four or more digits (the
+// stages are large and four CTAs share an SM), else 256.
+template <int DNUM>
+constexpr int tile_of() { return DNUM >= 4 ? 128 : 256; }
+constexpr int kMaxTile = 256;
 constexpr uint32_t kWaitSpins = 1u << 20;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -91,11 +95,12 @@ __device__ __forceinline__ uint64_t reduce_sum(U128 x, uint64_t q, uint64_t qinv
 // | P x [2 img][2 poly][T].
 template <int DNUM>
 struct Stage {
+    static constexpr int T = tile_of<DNUM>();
     static constexpr int KEYS = 0;
-    static constexpr int PTS = DNUM * 2 * kTile;
-    static constexpr int DIG = PTS + 2 * kTile;
-    static constexpr int XP = DIG + 2 * DNUM * kTile;
-    static constexpr int WORDS = XP + 4 * kTile;
+    static constexpr int PTS = DNUM * 2 * T;
+    static constexpr int DIG = PTS + 2 * T;
+    static constexpr int XP = DIG + 2 * DNUM * T;
+    static constexpr int WORDS = XP + 4 * T;
 };
 
 // Warp 0 stages tap t into stage buffer `st`, completing on `bar`.
@@ -107,6 +112,7 @@ __device__ __forceinline__ void issue_tap(uint64_t* st, uint64_t* bar, int t, co
                                          int b0, int nb, int l, int L, int n0, size_t LN, int N,
                                          int logN) {
     using S = Stage<DNUM>;
+    constexpr int kTile = S::T;
     const int lane = threadIdx.x & 31;
     const uint64_t* key = tt.key[t];
     const bool qlimb = l < L;
@@ -153,6 +159,7 @@ k_ks_mac_ext_bulk(const uint64_t* __restrict__ D, const uint64_t* __restrict__ X
                   uint64_t* __restrict__ A, int L, int K, int logN,
                   const ModConst* __restrict__ mods, int* __restrict__ err) {
     using S = Stage<DNUM>;
+    constexpr int kTile = S::T;
     extern __shared__ __align__(128) uint64_t smem[];
     __shared__ __align__(8) uint64_t bars[2];    // stage filled (1 arrival + copied bytes)
     const int N = 1 << logN;
@@ -277,6 +284,7 @@ void launch_bulk(he_ctx* c, const uint64_t* D, const uint64_t* XP, const uint64_
                              (int)smem);
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
+    constexpr int kTile = Stage<DNUM>::T;
     const dim3 grid((B + 1) / 2, c->N / kTile, c->L + c->K);
     k_ks_mac_ext_bulk<DNUM><<<grid, kTile, smem, c->stream>>>(D, XP, pts, tt, c_lo, cnt, B, A, c->L,
                                                             c->K, c->logN, c->d_mod, c->d_err);
@@ -284,7 +292,7 @@ void launch_bulk(he_ctx* c, const uint64_t* D, const uint64_t* XP, const uint64_
 
 }  // namespace
 
-bool tapmac_bulk_supported(const he_ctx* c) { return c->N >= kTile && c->dnum <= 8; }
+bool tapmac_bulk_supported(const he_ctx* c) { return c->N >= kMaxTile && c->dnum <= 8; }
 
 void launch_ks_mac_ext_bulk(he_ctx* c, const uint64_t* D, const uint64_t* XP, const uint64_t* pts,
                             const TapTable& tt, uint64_t* A, int B) {
