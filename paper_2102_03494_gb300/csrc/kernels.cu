@@ -359,23 +359,27 @@ __global__ void k_mac(const uint64_t* const* __restrict__ X, const uint64_t* con
 __global__ void k_convpack(const uint64_t* __restrict__ x, int r, int O_c,
                            const uint64_t* __restrict__ wm, uint64_t* const* outp, int L,
                            int logN, const ModConst* __restrict__ mods) {
+    // one thread per (image, limb, coefficient) computes every output channel: the r input
+    // residues are read from HBM once (then from L1), each output written once
     const int N = 1 << logN;
     const int n = blockIdx.y * blockDim.x + threadIdx.x;
     if (n >= N) return;
     const int i = blockIdx.z;
-    const int b = blockIdx.x / O_c, c = blockIdx.x - b * O_c;
+    const int b = blockIdx.x;
     const ModConst M = mods[i];
     const size_t ct = (size_t)2 * L * N;
     const uint64_t* xb = x + (size_t)b * r * ct + (size_t)i * N + n;
-    U128 a0{0, 0}, a1{0, 0};
-    for (int cp = 0; cp < r; ++cp) {
-        uint64_t w = wm[((size_t)c * r + cp) * L + i];
-        mac128(a0, xb[cp * ct], w);
-        mac128(a1, xb[cp * ct + (size_t)L * N], w);
+    for (int c = 0; c < O_c; ++c) {
+        U128 a0{0, 0}, a1{0, 0};
+        for (int cp = 0; cp < r; ++cp) {
+            const uint64_t w = wm[((size_t)c * r + cp) * L + i];
+            mac128(a0, xb[cp * ct], w);
+            mac128(a1, xb[cp * ct + (size_t)L * N], w);
+        }
+        uint64_t* ob = outp[(size_t)b * O_c + c] + (size_t)i * N + n;
+        ob[0] = redc(a0, M.q, M.qinv_neg);
+        ob[(size_t)L * N] = redc(a1, M.q, M.qinv_neg);
     }
-    uint64_t* ob = outp[blockIdx.x] + (size_t)i * N + n;
-    ob[0] = redc(a0, M.q, M.qinv_neg);
-    ob[(size_t)L * N] = redc(a1, M.q, M.qinv_neg);
 }
 
 // out = a + b for `rows` limbs (pointer tables, each entry rows*N contiguous)
@@ -791,8 +795,8 @@ void launch_mac(he_ctx* c, const uint64_t* const* X, const uint64_t* const* P, i
 void launch_convpack(he_ctx* c, const uint64_t* x, int B, int r, int O_c, const uint64_t* wm,
                      uint64_t* const* outp, int L) {
     ++c->launches;
-    k_convpack<<<grid_nx(B * O_c, c->N, L), 256, 0, c->stream>>>(x, r, O_c, wm, outp, L,
-                                                                 c->logN, c->d_mod);
+    k_convpack<<<grid_nx(B, c->N, L), 256, 0, c->stream>>>(x, r, O_c, wm, outp, L, c->logN,
+                                                           c->d_mod);
 }
 
 void launch_add(he_ctx* c, const uint64_t* const* a, const uint64_t* const* b,
