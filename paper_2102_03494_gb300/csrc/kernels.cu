@@ -70,10 +70,15 @@ __global__ void k_modup(const uint64_t* __restrict__ x_coeff, size_t xc_stride,
     const uint64_t* xc = x_coeff + blockIdx.x * xc_stride;
     const uint64_t* xn = x_ntt + blockIdx.x * xn_stride;
     uint64_t* o = out + blockIdx.x * out_stride + (size_t)j * LK * N;
-    uint64_t y[8];
-    for (int i = i0; i < i1; ++i) {
-        ShoupPair w = inv[i];
-        y[i - i0] = mul_shoup(xc[(size_t)i * N + n], w.w, w.ws, mods[i].q);
+    const int na = i1 - i0;                  // primes in this digit (<= 8)
+    uint64_t y[8];                           // unrolled with constant indices: registers
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        y[k] = 0;
+        if (k < na) {
+            const ShoupPair w = inv[i0 + k];
+            y[k] = mul_shoup(xc[(size_t)(i0 + k) * N + n], w.w, w.ws, mods[i0 + k].q);
+        }
     }
     const uint32_t src = perm_src(n, g_own, logN);
     for (int l = 0; l < LK; ++l) {
@@ -82,10 +87,14 @@ __global__ void k_modup(const uint64_t* __restrict__ x_coeff, size_t xc_stride,
             continue;
         }
         const uint64_t ql = mods[l].q;
+        const ShoupPair* cl = cst + (size_t)j * alpha * LK + l;
         uint64_t acc = 0;
-        for (int i = i0; i < i1; ++i) {
-            ShoupPair c = cst[((size_t)j * alpha + (i - i0)) * LK + l];
-            acc = add_mod(acc, mul_shoup(y[i - i0], c.w, c.ws, ql), ql);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (k < na) {
+                const ShoupPair c = cl[(size_t)k * LK];
+                acc = add_mod(acc, mul_shoup(y[k], c.w, c.ws, ql), ql);
+            }
         }
         o[(size_t)l * N + n] = acc;
     }
@@ -129,18 +138,25 @@ __global__ void k_moddown_conv(const uint64_t* __restrict__ u, size_t u_stride,
     const int k = blockIdx.z;  // polynomial 0 or 1
     const int LK = L + K;
     const uint64_t* ub = u + blockIdx.x * u_stride + (size_t)k * LK * N + (size_t)L * N;
-    uint64_t y[8];
-    for (int kk = 0; kk < K; ++kk) {
-        ShoupPair w = inv[kk];
-        y[kk] = mul_shoup(ub[(size_t)kk * N + n], w.w, w.ws, mods[L + kk].q);
+    uint64_t y[8];                           // K <= 8; constant indices keep y in registers
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+        y[kk] = 0;
+        if (kk < K) {
+            const ShoupPair w = inv[kk];
+            y[kk] = mul_shoup(ub[(size_t)kk * N + n], w.w, w.ws, mods[L + kk].q);
+        }
     }
     uint64_t* vb = v + blockIdx.x * v_stride + (size_t)k * L * N;
     for (int i = 0; i < L; ++i) {
         const uint64_t qi = mods[i].q;
         uint64_t acc = 0;
-        for (int kk = 0; kk < K; ++kk) {
-            ShoupPair c = cst[(size_t)kk * L + i];
-            acc = add_mod(acc, mul_shoup(y[kk], c.w, c.ws, qi), qi);
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+            if (kk < K) {
+                const ShoupPair c = cst[(size_t)kk * L + i];
+                acc = add_mod(acc, mul_shoup(y[kk], c.w, c.ws, qi), qi);
+            }
         }
         vb[(size_t)i * N + n] = acc;
     }
