@@ -36,6 +36,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--pack", default="dp_shift_ext", choices=["dp_shift", "dp_shift_ext", "dp_dot"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the short network runs reported under 'also'")
     ap.add_argument("--serving", action="store_true",
                     help="run the serving loop (mixed rings, Poisson arrivals) instead")
     ap.add_argument("--net", action="store_true",
@@ -44,6 +46,8 @@ def parse():
     ap.add_argument("--deep", action="store_true",
                     help="time the deeper 3x32x32 network (factorized ranks vs unfactorized)")
     ap.add_argument("--deep-batch", type=int, default=16)
+    ap.add_argument("--deep-ranks", default="8,16,32,0",
+                    help="comma-separated ranks to time (0 = unfactorized)")
     return ap.parse_args()
 
 
@@ -295,7 +299,33 @@ def run(args):
         dt, n, desc = oracle_sample(n_steps=2)
         line["cpu_baseline"] = {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": desc}
+    if world == 1 and not args.no_extra:
+        line["also"] = extra_workloads()
     print(json.dumps(line))
+
+
+def extra_workloads():
+    """Short runs of the two network workloads (their own modes, in child processes on the same
+    GPU), summarised beside the layer line; failures are reported, not raised."""
+    out = {}
+    for key, flags in (("network_n14_b64", ["--net", "--steps", "3", "--warmup", "2"]),
+                       ("deep_3x32x32_n15_b16", ["--deep", "--deep-ranks", "8", "--steps", "2",
+                                                 "--warmup", "1"])):
+        try:
+            res = subprocess.run([sys.executable, os.path.abspath(__file__)] + flags,
+                                 capture_output=True, text=True, timeout=600)
+            rec = json.loads(res.stdout.strip().splitlines()[-1])
+            keep = {k: rec[k] for k in ("metric", "value", "unit", "ms_per_step") if k in rec}
+            keep["batch"] = rec.get("config", {}).get("batch_per_gpu")
+            if "ops_per_image" in rec:
+                keep["ops_per_image"] = rec["ops_per_image"]
+            if "variants" in rec:
+                keep["ops_per_image"] = rec["variants"][0]["ops_per_image"]
+            keep["clocks"] = rec.get("clocks")
+            out[key] = keep
+        except Exception as e:             # noqa: BLE001 -- reported in the line
+            out[key] = {"error": f"{type(e).__name__}: {e}"[:300]}
+    return out
 
 
 def measured_peaks():
@@ -583,7 +613,7 @@ def run_deep(args):
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    for r in (8, 16, 32, 0):
+    for r in [int(v) for v in args.deep_ranks.split(",")]:
         convs = convs_for(r)
         W1s, W2s, C = [], [], 3
         for O in chans:
@@ -618,9 +648,10 @@ def run_deep(args):
     clk = clocks.stop()
     if rank != 0:
         return
-    unf = variants[-1]["ms_per_batch"]
-    for v in variants[:-1]:
-        v["speedup_vs_unfactorized"] = unf / v["ms_per_batch"]
+    unf = [v["ms_per_batch"] for v in variants if v["rank"] == "unfactorized"]
+    for v in variants:
+        if unf and v["rank"] != "unfactorized":
+            v["speedup_vs_unfactorized"] = unf[0] / v["ms_per_batch"]
     best = variants[0]
     line = {"metric": "encrypted 3x32x32 network throughput (images/s) at N=2^15",
             "value": best["images_per_s"], "unit": "images/s", "n_gpus": world, "steps": args.steps,
