@@ -2,8 +2,9 @@
 
 Bit-exact on every output ciphertext coefficient where the oracle finishes in seconds (small
 rings, and the 1 x 28 x 28 layer at N = 8192 under DP_SHIFT); at the benchmark's N = 2^15
-configuration and for DP_DOT at N = 8192, the decrypted outputs are compared with the plain
-integer convolution mod t (exact), and operation counts with the schedule's formulas."""
+configuration one sampled image of the timed batch of 16 is compared bit for bit, and every
+image's decrypted outputs (as for DP_DOT at N = 8192) with the plain integer convolution mod t
+(exact), and operation counts with the schedule's formulas."""
 import numpy as np
 import pytest
 
@@ -138,6 +139,25 @@ def test_bench_layer_n15_decrypts_to_the_convolution(pack, B):
     outs = ctx.he_ffconv_layer_batch(cts, W1, W2, lay)
     for b in range(B):
         check_decrypted(ctx, prm, sk, lay_o, outs[b * 5:(b + 1) * 5], xs[b], W1, W2)
+
+
+def test_bench_layer_n15_sampled_image_is_bit_exact():
+    """The benchmark's own launch: N = 2^15 (12 + 3 primes, digits of 3), dp_shift_ext, a batch
+    of 16 images in one call; one sampled image's five output ciphertexts are compared bit for
+    bit with the oracle (oracle keys and encryptions; about two CPU-minutes of oracle work)."""
+    prm = params.cfg_n15()
+    shape = workloads.MNIST_LAYER
+    lay_o, s, steps, keys, blob, xs, W1, W2, cts = setup_layer(prm, shape, "dp_shift_ext",
+                                                               seed=5, B=16)
+    ctx = make_ctx(prm)
+    lay = ctx.layout(*shape.astuple(), pack="dp_shift_ext")
+    ctx.he_load_keys(blob, gpu_steps(steps))
+    outs = ctx.he_ffconv_layer_batch([upload_ntt(ctx, c) for c in cts], W1, W2, lay)
+    b = 11                                      # the sampled image
+    want = ffconv.he_layer(prm, cts[b], W1, W2, lay_o, keys)
+    for c in range(shape.O_c):
+        assert (download_coeff(ctx, outs[b * shape.O_c + c]) == want[c].stack()).all(), c
+    check_decrypted(ctx, prm, s, lay_o, outs[b * shape.O_c:(b + 1) * shape.O_c], xs[b], W1, W2)
 
 
 @pytest.mark.parametrize("B", [1, 2])
