@@ -197,6 +197,7 @@ def run(args):
         slots[: x.size] = x.reshape(-1)
         cts.append(ctx.he_encrypt(sk, slots, 3000 + b))
     outs = [ctx.new_ct() for _ in range(B * shape.O_c)]
+    tile_ms = ctx.he_autotune(B)          # untimed: picks the tap-kernel tile for this batch
     torch.cuda.synchronize()
 
     def layer():
@@ -306,7 +307,9 @@ def run(args):
                        "batch_per_gpu": B, "layer_ms_per_batch": ms / args.steps,
                        "layer_ms_per_image": ms / args.steps / B, "hoisted_rotations_per_image": n_rot,
                        "parallelism": f"replicas x{world}",
-                       "l2": "inputs larger than L2 (keys 377 MB + ModUp digits per step)"},
+                       "l2": "inputs larger than L2 (keys 377 MB + ModUp digits per step)",
+                       "autotune": {"tap_tile_ms": {"128": tile_ms[0], "256": tile_ms[1]},
+                                    "tap_tile": 128 if tile_ms[0] <= tile_ms[1] else 256}},
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": B * ct_bytes,
                     "d2h_bytes_per_step": B * shape.O_c * ct_bytes, "ms_per_step": ms_e2e / args.steps,
                     "note": "pinned host buffers; copies of neighbouring steps overlap the layer "

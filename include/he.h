@@ -326,6 +326,17 @@ int he_deep_batch(he_ctx* ctx, const he_ct* in, int B, const he_mc_conv* convs, 
                   const int32_t* const* lowrank_w, const int32_t* const* restore_w,
                   const int32_t* fc_w, int n_cls, he_ct* out);
 
+/* ---- tuning ------------------------------------------------------------------------ */
+
+/* Autotuner of an implementation parameter (no counterpart in the paper; results never depend
+ * on it): times the fused tap kernel (key switch + plaintext MAC in Q u P) with 128- and
+ * 256-coefficient tiles on synthetic operands of `batch` images (25 taps, 2 channels, this
+ * context's key shape) and keeps the faster tile for every later call on the context.
+ * force_tile = 128 or 256 sets the tile without timing; 0 times.  ms_out (2 doubles, may be
+ * NULL) receives the time per launch of each tile.  Without a call the tile is 128 for keys
+ * of four or more digits, else 256.  Uses the context scratch; synchronises the stream. */
+int he_autotune(he_ctx* ctx, int batch, int force_tile, double* ms_out);
+
 /* ---- primitives for measurement --------------------------------------------------- */
 
 /* Negacyclic NTT (inverse = 0) or inverse NTT (inverse = 1) in place on `n_items` blocks of

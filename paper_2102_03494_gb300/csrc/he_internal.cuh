@@ -176,6 +176,7 @@ struct he_ctx {
     std::map<uint32_t, GaloisKey> keys; // by Galois element
     Arena arena;
     Arena net;                          // ciphertexts between the layers of he_net_batch
+    int tap_tile = 0;                   // tap kernel tile chosen by he_autotune (0: default)
     Staging staging;
     uint64_t ops[4] = {0, 0, 0, 0};     // MulPC, AddCC, Rot, KeySwitch
     uint64_t launches = 0;              // kernels launched by this context

@@ -17,11 +17,10 @@
 
 namespace {
 
-// Coefficients per CTA (one per thread): 128 when the key has four or more digits (the
-// stages are large and four CTAs share an SM), else 256.
-template <int DNUM>
-constexpr int tile_of() { return DNUM >= 4 ? 128 : 256; }
+// Coefficients per CTA (one per thread): 128 or 256.  Without autotuning (he_autotune) the
+// tile is 128 when the key has four or more digits (large stages, four CTAs per SM), else 256.
 constexpr int kMaxTile = 256;
+int default_tile(int dnum) { return dnum >= 4 ? 128 : 256; }
 constexpr uint32_t kWaitSpins = 1u << 20;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -93,9 +92,9 @@ __device__ __forceinline__ uint64_t reduce_sum(U128 x, uint64_t q, uint64_t qinv
 
 // Shared-memory stage (uint64 words): keys [DNUM][2][T] | pts [2][T] | digits [2 img][DNUM][T]
 // | P x [2 img][2 poly][T].
-template <int DNUM>
+template <int DNUM, int TILE>
 struct Stage {
-    static constexpr int T = tile_of<DNUM>();
+    static constexpr int T = TILE;
     static constexpr int KEYS = 0;
     static constexpr int PTS = DNUM * 2 * T;
     static constexpr int DIG = PTS + 2 * T;
@@ -104,14 +103,14 @@ struct Stage {
 };
 
 // Warp 0 stages tap t into stage buffer `st`, completing on `bar`.
-template <int DNUM>
+template <int DNUM, int TILE>
 __device__ __forceinline__ void issue_tap(uint64_t* st, uint64_t* bar, int t, const TapTable& tt,
                                          const uint64_t* __restrict__ D,
                                          const uint64_t* __restrict__ XPg,
                                          const uint64_t* __restrict__ pts, int c_lo, int c_cnt,
                                          int b0, int nb, int l, int L, int n0, size_t LN, int N,
                                          int logN) {
-    using S = Stage<DNUM>;
+    using S = Stage<DNUM, TILE>;
     constexpr int kTile = S::T;
     const int lane = threadIdx.x & 31;
     const uint64_t* key = tt.key[t];
@@ -152,13 +151,13 @@ __device__ __forceinline__ void issue_tap(uint64_t* st, uint64_t* bar, int t, co
     }
 }
 
-template <int DNUM>
+template <int DNUM, int TILE>
 __global__ void __launch_bounds__(256)
 k_ks_mac_ext_bulk(const uint64_t* __restrict__ D, const uint64_t* __restrict__ XPg,
                   const uint64_t* __restrict__ pts, TapTable tt, int c_lo, int c_cnt, int B,
                   uint64_t* __restrict__ A, int L, int K, int logN,
                   const ModConst* __restrict__ mods, int* __restrict__ err) {
-    using S = Stage<DNUM>;
+    using S = Stage<DNUM, TILE>;
     constexpr int kTile = S::T;
     extern __shared__ __align__(128) uint64_t smem[];
     __shared__ __align__(8) uint64_t bars[2];    // stage filled (1 arrival + copied bytes)
@@ -181,9 +180,9 @@ k_ks_mac_ext_bulk(const uint64_t* __restrict__ D, const uint64_t* __restrict__ X
     }
     __syncthreads();
     if (tid < 32) {
-        issue_tap<DNUM>(smem, &bars[0], 0, tt, D, XPg, pts, c_lo, c_cnt, b0, nb, l, L, n0, LN, N, logN);
+        issue_tap<DNUM, TILE>(smem, &bars[0], 0, tt, D, XPg, pts, c_lo, c_cnt, b0, nb, l, L, n0, LN, N, logN);
         if (tt.n > 1)
-            issue_tap<DNUM>(smem + S::WORDS, &bars[1], 1, tt, D, XPg, pts, c_lo, c_cnt, b0, nb, l, L,
+            issue_tap<DNUM, TILE>(smem + S::WORDS, &bars[1], 1, tt, D, XPg, pts, c_lo, c_cnt, b0, nb, l, L,
                             n0, LN, N, logN);
     }
     // unreduced sums of at most HE_MAX_TAPS products below q^2 each: < 64 q^2 < 2^126
@@ -249,7 +248,7 @@ k_ks_mac_ext_bulk(const uint64_t* __restrict__ D, const uint64_t* __restrict__ X
         __syncthreads();   // every warp is done with stage s before it is refilled
         if (tid < 32 && t + 2 < tt.n) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue_tap<DNUM>(st, &bars[s], t + 2, tt, D, XPg, pts, c_lo, c_cnt, b0, nb, l, L, n0, LN,
+            issue_tap<DNUM, TILE>(st, &bars[s], t + 2, tt, D, XPg, pts, c_lo, c_cnt, b0, nb, l, L, n0, LN,
                             N, logN);
         }
     }
@@ -272,22 +271,36 @@ k_ks_mac_ext_bulk(const uint64_t* __restrict__ D, const uint64_t* __restrict__ X
     }
 }
 
-template <int DNUM>
+template <int DNUM, int TILE>
 void launch_bulk(he_ctx* c, const uint64_t* D, const uint64_t* XP, const uint64_t* pts,
                  const TapTable& tt, uint64_t* A, int B, int c_lo, int cnt) {
-    const size_t smem = 2 * (size_t)Stage<DNUM>::WORDS * 8;
+    const size_t smem = 2 * (size_t)Stage<DNUM, TILE>::WORDS * 8;
     static bool attr_set[64] = {};   // per template instance and device
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-        cudaFuncSetAttribute(k_ks_mac_ext_bulk<DNUM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+        cudaFuncSetAttribute(k_ks_mac_ext_bulk<DNUM, TILE>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
-    constexpr int kTile = Stage<DNUM>::T;
-    const dim3 grid((B + 1) / 2, c->N / kTile, c->L + c->K);
-    k_ks_mac_ext_bulk<DNUM><<<grid, kTile, smem, c->stream>>>(D, XP, pts, tt, c_lo, cnt, B, A, c->L,
-                                                            c->K, c->logN, c->d_mod, c->d_err);
+    const dim3 grid((B + 1) / 2, c->N / TILE, c->L + c->K);
+    k_ks_mac_ext_bulk<DNUM, TILE><<<grid, TILE, smem, c->stream>>>(
+        D, XP, pts, tt, c_lo, cnt, B, A, c->L, c->K, c->logN, c->d_mod, c->d_err);
+}
+
+template <int TILE>
+void launch_bulk_tile(he_ctx* c, const uint64_t* D, const uint64_t* XP, const uint64_t* pts,
+                      const TapTable& tt, uint64_t* A, int B, int c_lo, int cnt) {
+    switch (c->dnum) {
+        case 1: launch_bulk<1, TILE>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
+        case 2: launch_bulk<2, TILE>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
+        case 3: launch_bulk<3, TILE>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
+        case 4: launch_bulk<4, TILE>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
+        case 5: launch_bulk<5, TILE>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
+        case 6: launch_bulk<6, TILE>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
+        case 7: launch_bulk<7, TILE>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
+        default: launch_bulk<8, TILE>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
+    }
 }
 
 }  // namespace
@@ -296,18 +309,80 @@ bool tapmac_bulk_supported(const he_ctx* c) { return c->N >= kMaxTile && c->dnum
 
 void launch_ks_mac_ext_bulk(he_ctx* c, const uint64_t* D, const uint64_t* XP, const uint64_t* pts,
                             const TapTable& tt, uint64_t* A, int B) {
+    const int tile = c->tap_tile ? c->tap_tile : default_tile(c->dnum);
     for (int c_lo = 0; c_lo < tt.r; c_lo += 2) {
         ++c->launches;
         const int cnt = tt.r - c_lo < 2 ? tt.r - c_lo : 2;
-        switch (c->dnum) {
-            case 1: launch_bulk<1>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
-            case 2: launch_bulk<2>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
-            case 3: launch_bulk<3>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
-            case 4: launch_bulk<4>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
-            case 5: launch_bulk<5>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
-            case 6: launch_bulk<6>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
-            case 7: launch_bulk<7>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
-            default: launch_bulk<8>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
-        }
+        if (tile == 128) launch_bulk_tile<128>(c, D, XP, pts, tt, A, B, c_lo, cnt);
+        else launch_bulk_tile<256>(c, D, XP, pts, tt, A, B, c_lo, cnt);
     }
+}
+
+// Autotuner of the tap kernel: times both tiles on synthetic operands of `batch` images (25
+// taps, 2 channels, the context's key shape) and keeps the faster for this context.
+extern "C" int he_autotune(he_ctx* ctx, int batch, int force_tile, double* ms_out) {
+    if (!ctx) return HE_EINVAL;
+    if (force_tile) {
+        if (force_tile != 128 && force_tile != 256)
+            return he_fail(ctx, HE_EINVAL, "he_autotune: tile must be 128 or 256");
+        ctx->tap_tile = force_tile;
+        return HE_OK;
+    }
+    if (batch < 1 || batch > 1024) return he_fail(ctx, HE_EINVAL, "he_autotune: batch out of range");
+    if (!tapmac_bulk_supported(ctx)) return HE_OK;        // nothing to choose
+    const int L = ctx->L, LK = L + ctx->K, dn = ctx->dnum, taps = 25, r = 2;
+    const size_t N = ctx->N, LN = (size_t)LK * N;
+    const size_t nD = (size_t)batch * dn * LN, nXP = (size_t)batch * 2 * L * N,
+                 nP = (size_t)r * taps * LN, nK = (size_t)dn * 2 * LN,
+                 nA = (size_t)batch * r * 2 * LN;
+    int rc = arena_reserve(ctx, nD + nXP + nP + nK + nA + 32 * 8);
+    if (rc) return rc;
+    arena_reset(ctx);
+    uint64_t* D = arena_take(ctx, nD);
+    uint64_t* XP = arena_take(ctx, nXP);
+    uint64_t* P = arena_take(ctx, nP);
+    uint64_t* Kb = arena_take(ctx, nK);
+    uint64_t* A = arena_take(ctx, nA);
+    // uniform residues, one counter stream per row block
+    uint64_t blk = 0;
+    auto fill = [&](uint64_t* p, size_t rows_total, int rows_per_block) {
+        for (size_t r0 = 0; r0 < rows_total; r0 += rows_per_block)
+            launch_uniform(ctx, he_stream_state(0x61757475ull, blk++), p + r0 * N, rows_per_block, 0, 0);
+    };
+    fill(D, (size_t)batch * dn * LK, LK);
+    fill(XP, (size_t)batch * 2 * L, L);
+    fill(P, (size_t)r * taps * LK, LK);
+    fill(Kb, (size_t)dn * 2 * LK, LK);
+    TapTable tt{};
+    tt.n = taps;
+    tt.r = r;
+    tt.n_sub = 1;
+    for (int t = 0; t < taps; ++t) {
+        tt.key[t] = t ? Kb : nullptr;
+        tt.g[t] = t ? galois_elt(ctx, t) : 1u;
+    }
+    const int tiles[2] = {128, 256};
+    double ms[2] = {0, 0};
+    cudaEvent_t e0, e1;
+    HE_CHECK_CUDA(ctx, cudaEventCreate(&e0));
+    HE_CHECK_CUDA(ctx, cudaEventCreate(&e1));
+    for (int v = 0; v < 2; ++v) {
+        ctx->tap_tile = tiles[v];
+        launch_ks_mac_ext_bulk(ctx, D, XP, P, tt, A, batch);          // warm-up
+        cudaEventRecord(e0, ctx->stream);
+        for (int rep = 0; rep < 3; ++rep) launch_ks_mac_ext_bulk(ctx, D, XP, P, tt, A, batch);
+        cudaEventRecord(e1, ctx->stream);
+        cudaEventSynchronize(e1);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        ms[v] = t / 3.0;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->tap_tile = ms[0] <= ms[1] ? tiles[0] : tiles[1];
+    if (ms_out) {
+        ms_out[0] = ms[0];
+        ms_out[1] = ms[1];
+    }
+    return he_launch_check(ctx, "he_autotune");
 }

@@ -89,6 +89,7 @@ _SIGS = {
                            ctypes.c_int, _CTP], ctypes.c_int),
     "he_combine_batch": ([_P, _CTP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _CTP], ctypes.c_int),
     "he_net_required_steps": ([_P, ctypes.POINTER(HeNet), _I32P, ctypes.c_int], ctypes.c_int),
+    "he_autotune": ([_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "he_mc_conv_batch": ([_P, _CTP, ctypes.c_int, _I32P, _I32P, ctypes.POINTER(HeMcConv), _CTP],
                          ctypes.c_int),
     "he_rotate_sum_batch": ([_P, _CTP, ctypes.c_int, _I32P, ctypes.c_int], ctypes.c_int),
@@ -394,6 +395,13 @@ class Context:
         self._ck(lib().he_net_batch(self.h, ia, B, pw1, pw2, pf1, pf2, ctypes.byref(net), oa),
                  "he_net_batch")
         return outs
+
+    def he_autotune(self, batch, force_tile=0):
+        """Pick the tap-kernel tile by timing (force_tile 128 / 256 sets it); returns the
+        per-launch times of the 128 and 256 tiles (zeros when forced)."""
+        ms = (ctypes.c_double * 2)()
+        self._ck(lib().he_autotune(self.h, batch, force_tile, ms), "he_autotune")
+        return float(ms[0]), float(ms[1])
 
     # ---- deeper networks (several ciphertexts per tensor)
     @staticmethod

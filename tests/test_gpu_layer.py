@@ -160,6 +160,29 @@ def test_bench_layer_n15_sampled_image_is_bit_exact():
     check_decrypted(ctx, prm, s, lay_o, outs[b * shape.O_c:(b + 1) * shape.O_c], xs[b], W1, W2)
 
 
+def test_autotuned_tap_tile_keeps_the_bits():
+    """he_autotune times the two tap-kernel tiles and keeps one; either forced tile gives the
+    oracle's bits."""
+    prm = params.Params(log_n=10, n_q=4, n_p=2, alpha=2)
+    shape = workloads.LayerShape(2, 6, 6, 3, 1, 1, 3, 2)
+    lay_o, s, steps, keys, blob, xs, W1, W2, cts = setup_layer(prm, shape, "dp_shift_ext", seed=9, B=3)
+    ctx = make_ctx(prm)
+    lay = ctx.layout(*shape.astuple(), pack="dp_shift_ext")
+    ctx.he_load_keys(blob, gpu_steps(steps))
+    t128, t256 = ctx.he_autotune(3)
+    assert t128 > 0 and t256 > 0
+    want = [ffconv.he_layer(prm, c, W1, W2, lay_o, keys) for c in cts]
+    for tile in (128, 256):
+        ctx.he_autotune(3, force_tile=tile)
+        outs = ctx.he_ffconv_layer_batch([upload_ntt(ctx, c) for c in cts], W1, W2, lay)
+        for b in range(3):
+            for c in range(shape.O_c):
+                assert (download_coeff(ctx, outs[b * shape.O_c + c]) == want[b][c].stack()).all()
+    from paper_2102_03494_gb300 import he
+    with pytest.raises(he.HeError):
+        ctx.he_autotune(3, force_tile=64)
+
+
 @pytest.mark.parametrize("B", [1, 2])
 def test_cp_cp_layers_are_bit_exact(B):
     """CP-HI2C-CP (Table VI's TinyNet packing) on small rings and at the TinyNet-shaped layer
