@@ -374,9 +374,11 @@ KS_MAC_EXT_TRAFFIC = {16: 1313583104 + 241992192}
 
 
 # 64 x 64 -> 128-bit products per second of the GPU's integer multiplier: 152 SMs x 64 32-bit
-# multiply-adds per clock x clock / 4 (a 64 x 64-bit product takes four 32 x 32-bit ones).
+# multiply-adds per clock x clock / 8.  A 64 x 64 -> 128-bit product is four 32 x 32 -> 64-bit
+# partial products, and each of those is two multiply-add instructions (its low and its high
+# word), so it takes at least 8 of the SM's 64 multiply-add issue slots per clock.
 def mul64_peak_per_s(sm_mhz):
-    return 152 * 64 / 4 * sm_mhz * 1e6
+    return 152 * 64 / 8 * sm_mhz * 1e6
 
 
 def taps_roofline(phases, args, B, n_rot):
@@ -397,7 +399,8 @@ def taps_roofline(phases, args, B, n_rot):
             "unit": "T mul64/s", "frac": achieved / peak,
             "traffic": KS_MAC_EXT_TRAFFIC.get(B) if args.pack == "dp_shift_ext" else None,
             "launch_us": sec * 1e6, "products_per_launch": products,
-            "peak_note": "152 SMs x 64 IMAD/clk / 4 per 64x64-bit product x max SM clock of "
+            "peak_note": "152 SMs x 64 IMAD/clk / 8 per 64x64->128-bit product (4 partial "
+                         "products, low and high word each) x max SM clock of "
                          f"MEASURED_PEAKS ({pk['src']})"}
 
 
