@@ -47,6 +47,7 @@ __device__ __forceinline__ uint64_t neg_mod(uint64_t a, uint64_t q) { return a ?
 
 // High 64 bits of a 64 x 64-bit product from 32-bit partial products in one carry chain (the
 // low word of a0 b0 cannot carry: it is never added to).
+#pragma nv_diag_suppress 550   // c1 below is written by the chain and read only through carries
 __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) {
     const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32);
     const uint32_t b0 = (uint32_t)b, b1 = (uint32_t)(b >> 32);
@@ -62,8 +63,9 @@ __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) {
         "addc.u32 %2, %2, 0;"
         : "=&r"(c1), "=&r"(c2), "=&r"(c3)
         : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
-    return ((uint64_t)c3 << 32) | c2;
+    return ((uint64_t)c3 << 32) | c2;   // c1 (bits 32..63) only feeds the carries
 }
+#pragma nv_diag_default 550
 
 // x * w mod q, x any 64-bit value, w < q, ws = floor(w 2^64 / q).
 __device__ __forceinline__ uint64_t mul_shoup(uint64_t x, uint64_t w, uint64_t ws, uint64_t q) {
