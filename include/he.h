@@ -233,6 +233,16 @@ int he_ffconv_layer(he_ctx* ctx, const he_ct* ct_in, const int32_t* lowrank_w,
  * Galois element share each key read. */
 int he_ffconv_layer_batch(he_ctx* ctx, const he_ct* ct_in, int B, const int32_t* lowrank_w,
                           const int32_t* restore_w, const he_layout* layout, he_ct* ct_out);
+/* Layer plans: the weights of a layer kept on the device with its W1 plaintexts already
+ * encoded (like the Galois keys, model state that a server holds across requests).
+ * he_ffconv_plan copies the weights, encodes the plaintexts once (Montgomery form, Q u P for
+ * HE_DP_SHIFT_EXT) and returns a plan id; he_ffconv_layer_planned then runs
+ * he_ffconv_layer_batch without the encode step (same results); he_ffconv_plan_free releases it.
+ * HE_EINVAL for an unknown plan. */
+int he_ffconv_plan(he_ctx* ctx, const int32_t* lowrank_w, const int32_t* restore_w,
+                   const he_layout* layout, int32_t* plan_out);
+int he_ffconv_layer_planned(he_ctx* ctx, int32_t plan, const he_ct* ct_in, int B, he_ct* ct_out);
+int he_ffconv_plan_free(he_ctx* ctx, int32_t plan);
 /* Rotation steps the layer needs keys for; writes at most `cap` steps into steps_out and
  * returns the count (or HE_EINVAL for a layout that does not fit the ring). */
 int he_ffconv_required_steps(const he_ctx* ctx, const he_layout* layout, int32_t* steps_out,

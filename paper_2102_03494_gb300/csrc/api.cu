@@ -320,6 +320,8 @@ static void free_ctx(he_ctx* c) {
         if (p) cudaFree(p);
     for (auto& kv : c->keys)
         if (kv.second.dev) cudaFree(kv.second.dev);
+    for (auto& kv : c->plans)
+        if (kv.second.pts) cudaFree(kv.second.pts);
     if (c->staging.host) cudaFreeHost(c->staging.host);
     for (auto e : c->staging.ev)
         if (e) cudaEventDestroy(e);

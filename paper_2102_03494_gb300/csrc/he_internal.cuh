@@ -179,6 +179,13 @@ struct he_ctx {
     Arena arena;
     Arena net;                          // ciphertexts between the layers of he_net_batch
     int tap_tile = 0;                   // tap kernel tile chosen by he_autotune (0: default)
+    struct LayerPlan {                  // he_ffconv_plan: weights and encoded W1 plaintexts
+        he_layout layout;
+        std::vector<int32_t> w1, w2;
+        uint64_t* pts = nullptr;        // device, NULL for HE_CP_CP
+    };
+    std::map<int32_t, LayerPlan> plans;
+    int32_t next_plan = 1;
     Staging staging;
     uint64_t ops[4] = {0, 0, 0, 0};     // MulPC, AddCC, Rot, KeySwitch
     uint64_t launches = 0;              // kernels launched by this context

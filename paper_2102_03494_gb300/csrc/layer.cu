@@ -294,9 +294,36 @@ static int cp_cp_layer(he_ctx* ctx, const he_ct* ct_in, int B, const int32_t* lo
     return restore_layer(ctx, A, B, y, restore_w, ct_out, Y, last, sprd);
 }
 
-extern "C" int he_ffconv_layer_batch(he_ctx* ctx, const he_ct* ct_in, int B,
-                                     const int32_t* lowrank_w, const int32_t* restore_w,
-                                     const he_layout* layout, he_ct* ct_out) {
+// W1 plaintexts of a layout (n_pt of them, pt_rows limbs each) from the integer weights:
+// slot vectors on the device, then encoded in Montgomery form (slots, tmp: n_pt N words).
+static int encode_w1(he_ctx* ctx, const he_layout& y, const LayoutInfo& li,
+                     const int32_t* lowrank_w, int64_t* slots, uint64_t* tmp, uint64_t* pts) {
+    const size_t N = ctx->N;
+    const bool dot = y.pack == HE_DP_DOT;
+    const int r = y.r, LK = ctx->L + ctx->K;
+    const int pt_rows = y.pack == HE_DP_SHIFT_EXT ? LK : ctx->L;
+    const int n_pt = dot ? r * li.S + li.S : r * li.taps;
+    const size_t w1n = (size_t)r * y.I_c * y.d * y.d;
+    const int32_t* d_w1 = (const int32_t*)upload_small(ctx, lowrank_w, w1n * 4);
+    if (!d_w1) return he_fail(ctx, HE_EINVAL, "he_ffconv_layer: W1 too large for staging");
+    HE_CHECK_CUDA(ctx, cudaMemsetAsync(slots, 0, (size_t)n_pt * N * 8, ctx->stream));
+    ++ctx->launches;
+    if (dot)
+        k_dp_dot_slots<<<dim3(n_pt, 1), 256, 0, ctx->stream>>>(d_w1, y.I_c, y.I_h, y.I_w, y.d, y.stride,
+                                                               y.pad, r, li.O_w, li.S, ctx->logN, slots);
+    else
+        k_dp_shift_slots<<<dim3(n_pt, 4), 256, 0, ctx->stream>>>(d_w1, y.I_c, y.I_h, y.I_w, y.d,
+                                                                 y.stride, y.pad, r, li.O_h, li.O_w,
+                                                                 li.B_c, ctx->logN, slots);
+    encode_device(ctx, slots, n_pt, tmp, pts, 1, pt_rows);
+    return HE_OK;
+}
+
+// The layer on B images; pre_pts, when given, holds the W1 plaintexts already encoded (a
+// plan's), and the encode step is skipped.
+static int layer_impl(he_ctx* ctx, const he_ct* ct_in, int B, const int32_t* lowrank_w,
+                      const int32_t* restore_w, const he_layout* layout, he_ct* ct_out,
+                      const uint64_t* pre_pts) {
     if (!ctx) return HE_EINVAL;
     if (!ct_in || !lowrank_w || !restore_w || !layout || !ct_out || B < 1)
         return he_fail(ctx, HE_EINVAL, "he_ffconv_layer: null argument");
@@ -366,21 +393,13 @@ extern "C" int he_ffconv_layer_batch(he_ctx* ctx, const he_ct* ct_in, int B,
         HE_CHECK_CUDA(ctx, cudaMemcpyAsync(X + b * ct, ct_in[b].data, ct * 8, cudaMemcpyDeviceToDevice,
                                            ctx->stream));
     // (a1) plaintexts: slot vectors from the integer weights, encoded in Montgomery form
-    phase_begin(ctx, HE_PHASE_ENCODE);
-    const size_t w1n = (size_t)r * y.I_c * y.d * y.d;
-    const int32_t* d_w1 = (const int32_t*)upload_small(ctx, lowrank_w, w1n * 4);
-    if (!d_w1) return he_fail(ctx, HE_EINVAL, "he_ffconv_layer: W1 too large for staging");
-    HE_CHECK_CUDA(ctx, cudaMemsetAsync(slots, 0, (size_t)n_pt * N * 8, ctx->stream));
-    ++ctx->launches;
-    if (dot)
-        k_dp_dot_slots<<<dim3(n_pt, 1), 256, 0, ctx->stream>>>(d_w1, y.I_c, y.I_h, y.I_w, y.d, y.stride,
-                                                               y.pad, r, li.O_w, li.S, ctx->logN, slots);
-    else
-        k_dp_shift_slots<<<dim3(n_pt, 4), 256, 0, ctx->stream>>>(d_w1, y.I_c, y.I_h, y.I_w, y.d,
-                                                                 y.stride, y.pad, r, li.O_h, li.O_w,
-                                                                 li.B_c, ctx->logN, slots);
-    encode_device(ctx, slots, n_pt, tmp, pts, 1, pt_rows);
-    phase_end(ctx);
+    if (pre_pts) {
+        pts = const_cast<uint64_t*>(pre_pts);
+    } else {
+        phase_begin(ctx, HE_PHASE_ENCODE);
+        if ((rc = encode_w1(ctx, y, li, lowrank_w, slots, tmp, pts))) return rc;
+        phase_end(ctx);
+    }
 
     if (dot) {
         // prod[b][c'][o] = X[b] * filter(c', o)
@@ -536,4 +555,73 @@ extern "C" int he_ffconv_layer_batch(he_ctx* ctx, const he_ct* ct_in, int B,
 extern "C" int he_ffconv_layer(he_ctx* ctx, const he_ct* ct_in, const int32_t* lowrank_w,
                                const int32_t* restore_w, const he_layout* layout, he_ct* ct_out) {
     return he_ffconv_layer_batch(ctx, ct_in, 1, lowrank_w, restore_w, layout, ct_out);
+}
+
+extern "C" int he_ffconv_layer_batch(he_ctx* ctx, const he_ct* ct_in, int B,
+                                     const int32_t* lowrank_w, const int32_t* restore_w,
+                                     const he_layout* layout, he_ct* ct_out) {
+    return layer_impl(ctx, ct_in, B, lowrank_w, restore_w, layout, ct_out, nullptr);
+}
+
+// ------------------------------------------------------------------ layer plans
+
+extern "C" int he_ffconv_plan(he_ctx* ctx, const int32_t* lowrank_w, const int32_t* restore_w,
+                              const he_layout* layout, int32_t* plan_out) {
+    if (!ctx) return HE_EINVAL;
+    if (!lowrank_w || !restore_w || !layout || !plan_out)
+        return he_fail(ctx, HE_EINVAL, "he_ffconv_plan: null argument");
+    LayoutInfo li;
+    std::string why;
+    int rc = layout_info(ctx, layout, &li, &why);
+    if (rc) return he_fail(ctx, rc, "he_ffconv_plan: " + why);
+    const he_layout& y = *layout;
+    he_ctx::LayerPlan pl;
+    pl.layout = y;
+    pl.w1.assign(lowrank_w, lowrank_w + (size_t)y.r * y.I_c * y.d * y.d);
+    pl.w2.assign(restore_w, restore_w + (size_t)y.O_c * y.r);
+    if (y.pack != HE_CP_CP) {
+        const size_t N = ctx->N;
+        const int pt_rows = y.pack == HE_DP_SHIFT_EXT ? ctx->L + ctx->K : ctx->L;
+        const int n_pt = y.pack == HE_DP_DOT ? y.r * li.S + li.S : y.r * li.taps;
+        if (cudaMalloc((void**)&pl.pts, (size_t)n_pt * pt_rows * N * 8) != cudaSuccess) {
+            cudaGetLastError();
+            return he_fail(ctx, HE_ENOMEM, "he_ffconv_plan: plaintext allocation failed");
+        }
+        if ((rc = arena_reserve(ctx, 2 * (size_t)n_pt * N + 64))) {
+            cudaFree(pl.pts);
+            return rc;
+        }
+        arena_reset(ctx);
+        int64_t* slots = (int64_t*)arena_take(ctx, (size_t)n_pt * N);
+        uint64_t* tmp = arena_take(ctx, (size_t)n_pt * N);
+        if ((rc = encode_w1(ctx, y, li, pl.w1.data(), slots, tmp, pl.pts)) ||
+            (rc = he_launch_check(ctx, "he_ffconv_plan"))) {
+            cudaStreamSynchronize(ctx->stream);
+            cudaFree(pl.pts);
+            return rc;
+        }
+    }
+    const int32_t id = ctx->next_plan++;
+    ctx->plans[id] = std::move(pl);
+    *plan_out = id;
+    return HE_OK;
+}
+
+extern "C" int he_ffconv_layer_planned(he_ctx* ctx, int32_t plan, const he_ct* ct_in, int B,
+                                       he_ct* ct_out) {
+    if (!ctx) return HE_EINVAL;
+    auto it = ctx->plans.find(plan);
+    if (it == ctx->plans.end()) return he_fail(ctx, HE_EINVAL, "he_ffconv_layer_planned: no such plan");
+    const he_ctx::LayerPlan& pl = it->second;
+    return layer_impl(ctx, ct_in, B, pl.w1.data(), pl.w2.data(), &pl.layout, ct_out, pl.pts);
+}
+
+extern "C" int he_ffconv_plan_free(he_ctx* ctx, int32_t plan) {
+    if (!ctx) return HE_EINVAL;
+    auto it = ctx->plans.find(plan);
+    if (it == ctx->plans.end()) return he_fail(ctx, HE_EINVAL, "he_ffconv_plan_free: no such plan");
+    cudaStreamSynchronize(ctx->stream);
+    if (it->second.pts) cudaFree(it->second.pts);
+    ctx->plans.erase(it);
+    return HE_OK;
 }

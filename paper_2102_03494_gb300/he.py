@@ -106,6 +106,9 @@ _SIGS = {
     "he_ffconv_layer_batch": ([_P, _CTP, ctypes.c_int, _I32P, _I32P, ctypes.POINTER(HeLayout), _CTP],
                               ctypes.c_int),
     "he_ffconv_required_steps": ([_P, ctypes.POINTER(HeLayout), _I32P, ctypes.c_int], ctypes.c_int),
+    "he_ffconv_plan": ([_P, _I32P, _I32P, ctypes.POINTER(HeLayout), _I32P], ctypes.c_int),
+    "he_ffconv_layer_planned": ([_P, ctypes.c_int32, _CTP, ctypes.c_int, _CTP], ctypes.c_int),
+    "he_ffconv_plan_free": ([_P, ctypes.c_int32], ctypes.c_int),
     "he_ntt": ([_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
 }
 _lib = None
@@ -502,6 +505,27 @@ class Context:
         self._ck(lib().he_ffconv_layer_batch(self.h, ia, B, pw1, pw2, ctypes.byref(lay), oa),
                  "he_ffconv_layer_batch")
         return outs
+
+    def he_ffconv_plan(self, W1, W2, lay):
+        w1, pw1 = _i32(W1)
+        w2, pw2 = _i32(W2)
+        pid = (ctypes.c_int32 * 1)()
+        self._ck(lib().he_ffconv_plan(self.h, pw1, pw2, ctypes.byref(lay), pid), "he_ffconv_plan")
+        return int(pid[0])
+
+    def he_ffconv_layer_planned(self, plan, cts_in, lay, outs=None):
+        """lay: the plan's layout (for the output count); cts_in as for he_ffconv_layer_batch."""
+        B = len(cts_in)
+        if lay.pack == HE_CP_CP:
+            B //= lay.d * lay.d * lay.I_c
+        lv = self.L - 1 if lay.modswitch else self.L
+        outs = [self.new_ct(level=lv) for _ in range(B * lay.O_c)] if outs is None else outs
+        ia, oa = self.ct_array(cts_in), self.ct_array(outs)
+        self._ck(lib().he_ffconv_layer_planned(self.h, plan, ia, B, oa), "he_ffconv_layer_planned")
+        return outs
+
+    def he_ffconv_plan_free(self, plan):
+        self._ck(lib().he_ffconv_plan_free(self.h, plan), "he_ffconv_plan_free")
 
     def he_ffconv_layer(self, ct_in, W1, W2, lay, outs=None):
         lv = self.L - 1 if lay.modswitch else self.L

@@ -181,6 +181,8 @@ class GpuRing:
         steps = self.ctx[0].he_ffconv_required_steps(self.lay)
         for c in self.ctx:
             c.he_keygen_galois(self.sk, key_seed, steps)
+        # model state resident per worker, like the keys: the weights with their plaintexts
+        self.plans = [c.he_ffconv_plan(W1, W2, self.lay) for c in self.ctx]
         self.N = 1 << spec.log_n
         self.ct_bytes = 2 * spec.n_q * self.N * 8
         self.O_c = spec.shape[7]
@@ -201,7 +203,8 @@ class GpuRing:
         with torch.cuda.stream(self.streams[worker]):
             # allocated (and zero-filled) on the worker's stream, ordered before the layer
             outs = [ctx.new_ct() for _ in range(len(requests) * self.O_c)]
-            ctx.he_ffconv_layer_batch([r.payload for r in requests], self.W1, self.W2, self.lay, outs)
+            ctx.he_ffconv_layer_planned(self.plans[worker], [r.payload for r in requests], self.lay,
+                                        outs)
             ev = torch.cuda.Event()
             ev.record(self.streams[worker])
         return (ev, outs)
@@ -220,6 +223,6 @@ class GpuRing:
         ctx = self.ctx[0]
         with torch.cuda.stream(self.streams[0]):
             outs = [ctx.new_ct() for _ in range(self.O_c)]
-            ctx.he_ffconv_layer_batch([payload], self.W1, self.W2, self.lay, outs)
+            ctx.he_ffconv_layer_planned(self.plans[0], [payload], self.lay, outs)
         self.streams[0].synchronize()
         return outs

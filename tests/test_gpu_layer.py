@@ -160,6 +160,31 @@ def test_bench_layer_n15_sampled_image_is_bit_exact():
     check_decrypted(ctx, prm, s, lay_o, outs[b * shape.O_c:(b + 1) * shape.O_c], xs[b], W1, W2)
 
 
+@pytest.mark.parametrize("pack", ["dp_dot", "dp_shift", "dp_shift_ext", "cp_cp"])
+def test_planned_layer_matches_the_plain_call(pack):
+    """A layer plan (weights resident, W1 plaintexts encoded once) gives the oracle's bits,
+    call after call; freeing it makes the id unknown."""
+    prm = params.Params(log_n=9, n_q=3, n_p=1, alpha=1)
+    shape = workloads.LayerShape(2, 6, 6, 3, 1, 1, 2, 2)
+    lay_o, s, steps, keys, blob, xs, W1, W2, cts = setup_layer(prm, shape, pack, seed=4, B=2)
+    ctx = make_ctx(prm)
+    lay = ctx.layout(*shape.astuple(), pack=pack)
+    ctx.he_load_keys(blob, gpu_steps(steps))
+    plan = ctx.he_ffconv_plan(W1, W2, lay)
+    K = shape.d * shape.d * shape.I_c if pack == "cp_cp" else 1
+    want = [ffconv.he_layer(prm, cts[b * K:(b + 1) * K] if pack == "cp_cp" else cts[b], W1, W2,
+                            lay_o, keys) for b in range(2)]
+    for _ in range(2):
+        outs = ctx.he_ffconv_layer_planned(plan, [upload_ntt(ctx, c) for c in cts], lay)
+        for b in range(2):
+            for c in range(shape.O_c):
+                assert (download_coeff(ctx, outs[b * shape.O_c + c]) == want[b][c].stack()).all()
+    ctx.he_ffconv_plan_free(plan)
+    from paper_2102_03494_gb300 import he
+    with pytest.raises(he.HeError):
+        ctx.he_ffconv_layer_planned(plan, [upload_ntt(ctx, c) for c in cts], lay)
+
+
 def test_autotuned_tap_tile_keeps_the_bits():
     """he_autotune times the two tap-kernel tiles and keeps one; either forced tile gives the
     oracle's bits."""
