@@ -303,6 +303,10 @@ def run(args):
     ctx.he_ffconv_plan_free(plan)
 
     roof = taps_roofline(phases, args, B, n_rot)
+    if roof is not None:          # the measured multiply-accumulate rate, for context
+        chain, cols = ctx.he_probe_int_mac()
+        roof["probe_mul64_per_s"] = {"carry_chain_T": chain / 1e12, "column_sums_T": cols / 1e12,
+                                     "frac_of_carry_chain": roof["achieved"] / (chain / 1e12)}
     layer_bytes = layer_algorithmic_bytes(B, shape.O_c, n_rot)
     peaks = measured_peaks()
 

@@ -143,7 +143,9 @@ int he_keygen_galois(he_ctx* ctx, const int64_t* sk, uint64_t seed, const int32_
  * HE_ENOKEY if absent. */
 int he_export_galois(he_ctx* ctx, int32_t step, uint64_t* blob_out);
 /* Load n_steps keys from the host blob (n_steps consecutive keys in the layout of
- * he_export_galois) and keep them resident; replaces a key with the same Galois element. */
+ * he_export_galois) and keep them resident; replaces a key with the same Galois element.
+ * Every residue must lie below its modulus: otherwise (corrupted material) none of the keys
+ * of this call is kept and HE_EINVAL is returned. */
 int he_load_keys(he_ctx* ctx, const uint64_t* galois_blob, const int32_t* steps, int n_steps);
 /* Encrypt the slot vector `slots` (host int64[N], taken mod t) under the host secret sk
  * with randomness from `seed` (streams 2 and 3).  out->data must hold [2][n_q][N]; the
@@ -348,6 +350,12 @@ int he_deep_batch(he_ctx* ctx, const he_ct* in, int B, const he_mc_conv* convs, 
 int he_autotune(he_ctx* ctx, int batch, int force_tile, double* ms_out);
 
 /* ---- primitives for measurement --------------------------------------------------- */
+
+/* Microbenchmark of the 64 x 64 -> 128-bit multiply-accumulate rate (registers only, eight
+ * independent accumulators per thread, 8 CTAs of 256 threads per SM): out[0] = products/s of
+ * the 32-bit multiply-add carry chain the kernels use, out[1] = products/s with 30-bit limbs
+ * summed into 64-bit column accumulators.  Uses the context stream and scratch; synchronous. */
+int he_probe_int_mac(he_ctx* ctx, double* out);
 
 /* Negacyclic NTT (inverse = 0) or inverse NTT (inverse = 1) in place on `n_items` blocks of
  * n_limbs limbs each (device [n_items][n_limbs][N]); limb i uses the i-th ciphertext prime

@@ -62,17 +62,37 @@ extern "C" int he_export_galois(he_ctx* ctx, int32_t step, uint64_t* blob_out) {
 extern "C" int he_load_keys(he_ctx* ctx, const uint64_t* blob, const int32_t* steps, int n_steps) {
     if (!ctx || n_steps < 0 || (n_steps > 0 && (!blob || !steps))) return HE_EINVAL;
     const size_t LK = ctx->L + ctx->K, per = (size_t)ctx->dnum * 2 * LK * ctx->N;
+    int rc = arena_reserve(ctx, 64);
+    if (rc) return rc;
+    arena_reset(ctx);
+    int* bad = (int*)arena_take(ctx, 1);          // set when a residue is not below its modulus
+    HE_CHECK_CUDA(ctx, cudaMemsetAsync(bad, 0, sizeof(int), ctx->stream));
+    std::vector<uint32_t> loaded;
     for (int s = 0; s < n_steps; ++s) {
         uint64_t* key = nullptr;
-        int rc = key_alloc(ctx, galois_elt(ctx, steps[s]), &key);
-        if (rc) return rc;
+        const uint32_t g = galois_elt(ctx, steps[s]);
+        if ((rc = key_alloc(ctx, g, &key))) return rc;
+        loaded.push_back(g);
         HE_CHECK_CUDA(ctx, cudaMemcpyAsync(key, blob + (size_t)s * per, per * 8,
                                            cudaMemcpyHostToDevice, ctx->stream));
+        launch_check_range(ctx, key, (int)(2 * ctx->dnum * LK), (int)LK, bad);
         ntt_forward(ctx, key, 2 * ctx->dnum, LK * ctx->N, (int)LK, 0);
         launch_to_mont(ctx, key, 1, (int)(2 * ctx->dnum * LK), (int)LK, 0);
     }
-    int rc = he_launch_check(ctx, "he_load_keys");
+    rc = he_launch_check(ctx, "he_load_keys");
+    int h_bad = 0;
+    HE_CHECK_CUDA(ctx, cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     HE_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (!rc && h_bad) {                           // corrupted material: none of these keys stay
+        for (uint32_t g : loaded) {
+            auto it = ctx->keys.find(g);
+            if (it != ctx->keys.end()) {
+                if (it->second.dev) cudaFree(it->second.dev);
+                ctx->keys.erase(it);
+            }
+        }
+        return he_fail(ctx, HE_EINVAL, "he_load_keys: key residue not below its modulus");
+    }
     return rc;
 }
 

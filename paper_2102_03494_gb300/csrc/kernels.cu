@@ -411,6 +411,16 @@ __global__ void k_add(const uint64_t* const* ap, const uint64_t* const* bp, uint
     (void)polys;
 }
 
+// bad |= 1 when some residue of `rows` rows (row r modulo mods[r % period]) is not below it.
+__global__ void k_check_range(const uint64_t* __restrict__ x, int period, int logN,
+                              const ModConst* __restrict__ mods, int* bad) {
+    const int N = 1 << logN;
+    const int n = blockIdx.y * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int r = blockIdx.z;
+    if (x[(size_t)r * N + n] >= mods[r % period].q) atomicOr(bad, 1);
+}
+
 // Convert rows to Montgomery form in place (x -> x 2^64 mod q); row r uses mods[mod_off + r % period].
 __global__ void k_to_mont(uint64_t* data, int rows, int period, int mod_off, int logN,
                           const ModConst* __restrict__ mods) {
@@ -826,6 +836,12 @@ void launch_add_rows(he_ctx* c, const uint64_t* const* a, const uint64_t* const*
     ++c->launches;
     k_add<<<grid_nx(items, c->N, 2 * rows_per_poly), 256, 0, c->stream>>>(a, b, o, rows_per_poly, 2,
                                                                           c->logN, c->d_mod);
+}
+
+void launch_check_range(he_ctx* c, const uint64_t* data, int rows, int period, int* bad) {
+    ++c->launches;
+    k_check_range<<<grid_nx(1, c->N, rows), 256, 0, c->stream>>>(data, period, c->logN, c->d_mod,
+                                                                 bad);
 }
 
 void launch_to_mont(he_ctx* c, uint64_t* data, int items, int rows, int period, int mod_off) {

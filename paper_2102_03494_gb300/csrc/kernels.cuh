@@ -46,6 +46,8 @@ void launch_convpack(he_ctx* c, const uint64_t* x, int B, int r, int O_c, const 
                      uint64_t* const* outp, int L);
 void launch_add(he_ctx* c, const uint64_t* const* a, const uint64_t* const* b,
                 uint64_t* const* o, int items, int L);
+// *bad |= 1 when a residue of `rows` rows (row r modulo mods[r % period]) is not below it.
+void launch_check_range(he_ctx* c, const uint64_t* data, int rows, int period, int* bad);
 // Pairs of polynomials over the first rows_per_poly moduli (e.g. Q u P): o = a + b.
 void launch_add_rows(he_ctx* c, const uint64_t* const* a, const uint64_t* const* b,
                      uint64_t* const* o, int items, int rows_per_poly);

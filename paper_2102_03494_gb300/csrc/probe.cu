@@ -1,0 +1,110 @@
+// probe.cu -- microbenchmark of the GPU's 64 x 64 -> 128-bit multiply-accumulate rate, the
+// operation the key-switch, plaintext-product and base-conversion kernels are built from.
+//
+// Two forms, registers only, eight independent accumulators per thread:
+//   chain: mac128 (he_internal.cuh), the 32-bit multiply-add carry chain the kernels use;
+//   cols:  the same product as four 32 x 32 -> 64-bit partial products summed into three
+//          64-bit column accumulators (operands below 2^60 split at bit 30), no carry chain.
+// Each iteration also advances one operand (so nothing is loop-invariant); every thread
+// writes one word so that no work is dead.
+#include "he_internal.cuh"
+
+namespace {
+
+constexpr int kAcc = 8;
+
+__global__ void __launch_bounds__(256) k_probe_chain(const uint64_t* __restrict__ in,
+                                                     uint64_t* __restrict__ out, int iters) {
+    uint64_t x[kAcc], y[kAcc];
+    U128 acc[kAcc];
+#pragma unroll
+    for (int a = 0; a < kAcc; ++a) {
+        x[a] = in[a] + threadIdx.x;
+        y[a] = in[kAcc + a];
+        acc[a] = U128{0, 0};
+    }
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int a = 0; a < kAcc; ++a) {
+            mac128(acc[a], x[a], y[a]);
+            x[a] += y[a];
+        }
+    }
+    uint64_t r = 0;
+#pragma unroll
+    for (int a = 0; a < kAcc; ++a) r ^= acc[a].lo ^ acc[a].hi;
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = r;
+}
+
+__global__ void __launch_bounds__(256) k_probe_cols(const uint64_t* __restrict__ in,
+                                                    uint64_t* __restrict__ out, int iters) {
+    uint32_t x0[kAcc], x1[kAcc], y0[kAcc], y1[kAcc];
+    uint64_t c0[kAcc], c1[kAcc], c2[kAcc];
+    const uint64_t m60 = (1ull << 60) - 1;
+#pragma unroll
+    for (int a = 0; a < kAcc; ++a) {
+        const uint64_t xv = (in[a] + threadIdx.x) & m60, yv = in[kAcc + a] & m60;
+        x0[a] = (uint32_t)(xv & 0x3fffffff);
+        x1[a] = (uint32_t)(xv >> 30);
+        y0[a] = (uint32_t)(yv & 0x3fffffff);
+        y1[a] = (uint32_t)(yv >> 30);
+        c0[a] = c1[a] = c2[a] = 0;
+    }
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int a = 0; a < kAcc; ++a) {
+            c0[a] += (uint64_t)x0[a] * y0[a];
+            c1[a] += (uint64_t)x0[a] * y1[a];
+            c1[a] += (uint64_t)x1[a] * y0[a];
+            c2[a] += (uint64_t)x1[a] * y1[a];
+            x0[a] = (x0[a] + y0[a]) & 0x3fffffff;
+        }
+    }
+    uint64_t r = 0;
+#pragma unroll
+    for (int a = 0; a < kAcc; ++a) r ^= c0[a] ^ c1[a] ^ c2[a];
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = r;
+}
+
+}  // namespace
+
+extern "C" int he_probe_int_mac(he_ctx* ctx, double* out) {
+    if (!ctx || !out) return HE_EINVAL;
+    int sms = 0, dev = 0;
+    HE_CHECK_CUDA(ctx, cudaGetDevice(&dev));
+    HE_CHECK_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = sms * 8, threads = 256, iters = 4096;
+    int rc = arena_reserve(ctx, 2 * kAcc + (size_t)blocks * threads + 64);
+    if (rc) return rc;
+    arena_reset(ctx);
+    uint64_t* in = arena_take(ctx, 2 * kAcc);
+    uint64_t* o = arena_take(ctx, (size_t)blocks * threads);
+    uint64_t h[2 * kAcc];
+    for (int i = 0; i < 2 * kAcc; ++i) h[i] = (0x0123456789abcdefull * (i + 1)) & ((1ull << 59) - 1);
+    HE_CHECK_CUDA(ctx, cudaMemcpyAsync(in, h, sizeof(h), cudaMemcpyHostToDevice, ctx->stream));
+    cudaEvent_t e0, e1;
+    HE_CHECK_CUDA(ctx, cudaEventCreate(&e0));
+    HE_CHECK_CUDA(ctx, cudaEventCreate(&e1));
+    const double prods = (double)blocks * threads * iters * kAcc;
+    for (int v = 0; v < 2; ++v) {
+        for (int rep = 0; rep < 2; ++rep) {                       // warm-up
+            ++ctx->launches;
+            if (v == 0) k_probe_chain<<<blocks, threads, 0, ctx->stream>>>(in, o, iters);
+            else k_probe_cols<<<blocks, threads, 0, ctx->stream>>>(in, o, iters);
+        }
+        cudaEventRecord(e0, ctx->stream);
+        for (int rep = 0; rep < 5; ++rep) {
+            ++ctx->launches;
+            if (v == 0) k_probe_chain<<<blocks, threads, 0, ctx->stream>>>(in, o, iters);
+            else k_probe_cols<<<blocks, threads, 0, ctx->stream>>>(in, o, iters);
+        }
+        cudaEventRecord(e1, ctx->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        out[v] = prods * 5 / (ms / 1e3);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return he_launch_check(ctx, "he_probe_int_mac");
+}

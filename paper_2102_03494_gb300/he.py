@@ -90,6 +90,7 @@ _SIGS = {
     "he_combine_batch": ([_P, _CTP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _CTP], ctypes.c_int),
     "he_net_required_steps": ([_P, ctypes.POINTER(HeNet), _I32P, ctypes.c_int], ctypes.c_int),
     "he_autotune": ([_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "he_probe_int_mac": ([_P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "he_mc_conv_batch": ([_P, _CTP, ctypes.c_int, _I32P, _I32P, ctypes.POINTER(HeMcConv), _CTP],
                          ctypes.c_int),
     "he_rotate_sum_batch": ([_P, _CTP, ctypes.c_int, _I32P, ctypes.c_int], ctypes.c_int),
@@ -405,6 +406,12 @@ class Context:
         ms = (ctypes.c_double * 2)()
         self._ck(lib().he_autotune(self.h, batch, force_tile, ms), "he_autotune")
         return float(ms[0]), float(ms[1])
+
+    def he_probe_int_mac(self):
+        """Measured 64 x 64 -> 128-bit products/s: (carry chain, 32-bit column sums)."""
+        out = (ctypes.c_double * 2)()
+        self._ck(lib().he_probe_int_mac(self.h, out), "he_probe_int_mac")
+        return float(out[0]), float(out[1])
 
     # ---- deeper networks (several ciphertexts per tensor)
     @staticmethod

@@ -188,6 +188,29 @@ def test_error_paths():
     bad = ctx.layout(1, 40, 40, 5, 2, 1, 2, 5)          # 1600 slots > N/2 = 256
     with pytest.raises(he.HeError):
         ctx.he_ffconv_required_steps(bad)
+    # corrupted key material (a residue equal to its modulus) is refused and not kept
+    key = bfv.galois_key(prm, s, bfv.galois_of(3, prm.n), 7)
+    blob = key.reshape(-1).copy()
+    blob[5 * prm.n + 17] = prm.qp[5 % len(prm.qp)]     # row 5 of the first (b) polynomial
+    with pytest.raises(he.HeError) as e:
+        ctx.he_load_keys(blob, [3])
+    assert e.value.code == he.HE_EINVAL
+    with pytest.raises(he.HeError) as e:
+        ctx.he_rotate(d, 3)
+    assert e.value.code == he.HE_ENOKEY
+    ctx.he_load_keys(key.reshape(-1), [3])                 # intact material loads
+    ctx.he_rotate(d, 3)
     with pytest.raises(he.HeError) as e:
         ctx.he_ffconv_layer(d, np.ones((2, 1, 5, 5)), np.ones((5, 2)), bad)
     assert e.value.code == he.HE_EINVAL
+
+
+def test_integer_rate_probe_is_sane():
+    """The multiply-accumulate probe returns rates below the derived issue-slot bound
+    (152 SMs x 64 multiply-adds per clock / 8 per product at 2070 MHz, with margin)."""
+    prm = params.Params(log_n=9, n_q=3, n_p=1, alpha=1)
+    ctx = make_ctx(prm)
+    chain, cols = ctx.he_probe_int_mac()
+    bound = 152 * 64 / 8 * 2070e6
+    assert 0.05 * bound < chain < 1.2 * bound
+    assert 0.05 * bound < cols < 1.5 * bound
