@@ -241,10 +241,13 @@ k_ks_mac_ext_bulk(const uint64_t* __restrict__ D, const uint64_t* __restrict__ X
 #pragma unroll
         for (int ib = 0; ib < 2; ++ib)
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                mac128(a128[ib][0][k], x[ib][k], p0);
-                mac128(a128[ib][1][k], x[ib][k], p1);
-            }
+            for (int k = 0; k < 2; ++k) mac128(a128[ib][0][k], x[ib][k], p0);
+        if (c_cnt > 1) {                 // uniform over the launch: one channel skips this
+#pragma unroll
+            for (int ib = 0; ib < 2; ++ib)
+#pragma unroll
+                for (int k = 0; k < 2; ++k) mac128(a128[ib][1][k], x[ib][k], p1);
+        }
         __syncthreads();   // every warp is done with stage s before it is refilled
         if (tid < 32 && t + 2 < tt.n) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
