@@ -117,15 +117,17 @@ class Params:
         return list(range(j * self.alpha, min((j + 1) * self.alpha, self.n_q)))
 
 
-# Parameter sets used across the tests and the benchmark (see the design doc for the mapping).
+# Parameter sets used across the tests and the benchmark.
 def cfg_small_layer():
     """5x5 stride-2 layer ring: N = 8192, three 50-bit q's, one 60-bit special prime."""
     return Params(log_n=13, n_q=3, n_p=1, alpha=1)
 
 
 def cfg_n14():
+    """The three-layer network's ring: N = 2^14, six 50-bit q's, two 60-bit p's, digits of 2."""
     return Params(log_n=14, n_q=6, n_p=2, alpha=2)
 
 
 def cfg_n15():
+    """The benchmark layer's ring: N = 2^15, twelve 50-bit q's, three 60-bit p's, digits of 3."""
     return Params(log_n=15, n_q=12, n_p=3, alpha=3)
