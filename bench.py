@@ -326,7 +326,8 @@ def run(args):
                        "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (keys 377 MB + ModUp digits per step)",
                        "autotune": {"tap_tile_ms": {"128": tile_ms[0], "256": tile_ms[1]},
-                                    "tap_tile": 128 if tile_ms[0] <= tile_ms[1] else 256}},
+                                    "tap_tile": 128 if tile_ms[0] <= tile_ms[1] else 256,
+                                    "ntt_log2_n1": tile_ms[3], "ntt_ms": tile_ms[2]}},
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": B * ct_bytes,
                     "d2h_bytes_per_step": B * shape.O_c * ct_bytes, "ms_per_step": ms_e2e / args.steps,
                     "note": "pinned host buffers; copies of neighbouring steps overlap the layer "
@@ -551,6 +552,7 @@ def run_net(args):
         slots[: x.size] = x.reshape(-1)
         cts.append(ctx.he_encrypt(sk, slots, 3000 + b))
     outs = [ctx.new_ct() for _ in range(B)]
+    tuned = ctx.he_autotune(B)            # untimed
     torch.cuda.synchronize()
 
     def step():
@@ -620,6 +622,7 @@ def run_net(args):
                     "h2d_bytes_per_step": B * ct_bytes, "d2h_bytes_per_step": B * ct_bytes,
                     "ms_per_step": ms_e2e / args.steps},
             "gpu_launches": launches, "clocks": clk,
+            "autotune": {"tap_tile_ms": tuned[:2], "ntt_log2_n1": tuned[3]},
             "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items() if v[1]}}
     print(json.dumps(line))
 
@@ -661,6 +664,7 @@ def run_deep(args):
             v[c * 1024: c * 1024 + H * W] = xs[b, c].reshape(-1)
         cts.append(ctx.he_encrypt(sk, v, 3000 + b))
     outs = [ctx.new_ct() for _ in range(B)]
+    tuned = ctx.he_autotune(B)            # untimed
     variants = []
     clocks = ClockSampler(local)
     clocks.start()
@@ -713,6 +717,7 @@ def run_deep(args):
                                    "128 -> x^2 -> sum pool -> FC 128->10, N=2^15, 12x50-bit q, "
                                    "3x60-bit p, alpha=3; value = rank 8",
                        "batch_per_gpu": B, "galois_keys": len(steps) - 1},
+            "autotune": {"tap_tile_ms": tuned[:2], "ntt_log2_n1": tuned[3]},
             "clocks": clk, "variants": variants}
     print(json.dumps(line))
 

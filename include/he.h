@@ -340,13 +340,16 @@ int he_deep_batch(he_ctx* ctx, const he_ct* in, int B, const he_mc_conv* convs, 
 
 /* ---- tuning ------------------------------------------------------------------------ */
 
-/* Autotuner of an implementation parameter (no counterpart in the paper; results never depend
- * on it): times the fused tap kernel (key switch + plaintext MAC in Q u P) with 128- and
- * 256-coefficient tiles on synthetic operands of `batch` images (25 taps, 2 channels, this
- * context's key shape) and keeps the faster tile for every later call on the context.
- * force_tile = 128 or 256 sets the tile without timing; 0 times.  ms_out (2 doubles, may be
- * NULL) receives the time per launch of each tile.  Without a call the tile is 128 for keys
- * of four or more digits, else 256.  Uses the context scratch; synchronises the stream. */
+/* Autotuner of implementation parameters (no counterpart in the paper; results never depend
+ * on them): (1) the split N = N1 N2 of the two-pass NTT, timing forward + inverse transforms
+ * of `batch` ciphertexts for each candidate split; (2) the fused tap kernel's tile (128 or 256
+ * coefficients per CTA), timing it on synthetic operands of `batch` images (25 taps, 2
+ * channels, this context's key shape).  The fastest of each is kept for every later call on
+ * the context.  force_tile = 128 or 256 only sets the tile, without timing.  ms_out (4
+ * doubles, may be NULL): tap-kernel time per launch with tile 128 and with 256, the NTT time
+ * of the chosen split, and that split's log2 N1.  Without a call: tile 128 for keys of four or
+ * more digits (else 256), split log2 N1 = floor(log2 N / 2).  Uses the context scratch;
+ * synchronises the stream. */
 int he_autotune(he_ctx* ctx, int batch, int force_tile, double* ms_out);
 
 /* ---- primitives for measurement --------------------------------------------------- */

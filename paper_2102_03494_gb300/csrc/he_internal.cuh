@@ -179,6 +179,7 @@ struct he_ctx {
     Arena arena;
     Arena net;                          // ciphertexts between the layers of he_net_batch
     int tap_tile = 0;                   // tap kernel tile chosen by he_autotune (0: default)
+    int ntt_s1 = 0;                     // NTT split log2 N1 chosen by he_autotune (0: default)
     struct LayerPlan {                  // he_ffconv_plan: weights and encoded W1 plaintexts
         he_layout layout;
         std::vector<int32_t> w1, w2;
@@ -245,5 +246,7 @@ void he_cdt_compute(uint64_t out[20]);
 // `rows` consecutive limbs; limb r of a block uses modulus index mod_off + r.
 void ntt_forward(he_ctx* ctx, uint64_t* data, int items, size_t item_stride, int rows,
                  int mod_off);
+// Splits log2 N1 of the two-pass NTT worth timing for this ring (the default first).
+int ntt_split_candidates(int logN, int* out, int cap);
 void ntt_inverse(he_ctx* ctx, uint64_t* data, int items, size_t item_stride, int rows,
                  int mod_off);

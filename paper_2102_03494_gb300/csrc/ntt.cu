@@ -5,7 +5,7 @@
 // order, position p holding a(psi^(2 brv(p) + 1)).  Inverse: Gentleman-Sande with
 // psi^-brv(m + i), stages in reverse, then the factor N^-1.
 //
-// The N = N1 N2 points (N1 = 2^s1, s1 = floor(log N / 2)) are split in two passes:
+// The N = N1 N2 points (N1 = 2^s1, s1 chosen for the fewest rounds) are split in two passes:
 //   column pass: stages s < s1 act on elements with the same j mod N2 (strided columns);
 //                one CTA holds `cols` adjacent columns x N1 rows;
 //   row pass:    stages s >= s1 act inside contiguous blocks of N2 elements; one CTA holds
@@ -239,9 +239,32 @@ struct Split {
     int s1, cols, lc, col_ctas, col_threads, blocks, row_ctas, row_threads;
 };
 
-Split split_of(int logN) {
+// The split N = N1 N2 with the fewest radix-8 rounds (ceil(s1/3) + ceil(s2/3), both passes at
+// most kTile points); among those the most balanced, then the smaller N1 (more adjacent columns
+// per CTA in the column pass).  A candidate for the autotuner; the default split is
+// s1 = floor(log N / 2) (measured faster at N = 2^15 although it takes one more round).
+int best_s1(int logN) {
+    int best = logN / 2, best_cost = 1 << 30, best_tilt = 1 << 30;
+    for (int s = 1; s < logN; ++s) {
+        if ((1 << s) > kTile || (1 << (logN - s)) > kTile) continue;
+        const int cost = (s + 2) / 3 + (logN - s + 2) / 3;
+        const int tilt = 2 * s > logN ? 2 * s - logN : logN - 2 * s;
+        if (cost < best_cost || (cost == best_cost && tilt < best_tilt)) {
+            best = s;
+            best_cost = cost;
+            best_tilt = tilt;
+        }
+    }
+    return best;
+}
+
+bool split_ok(int logN, int s1) {
+    return s1 >= 1 && s1 < logN && (1 << s1) <= kTile && (1 << (logN - s1)) <= kTile;
+}
+
+Split split_of(int logN, int s1) {
     Split sp;
-    sp.s1 = logN / 2;
+    sp.s1 = split_ok(logN, s1) ? s1 : logN / 2;
     const int N1 = 1 << sp.s1, N2 = 1 << (logN - sp.s1);
     sp.cols = kTile / N1;
     if (sp.cols > N2) sp.cols = N2;
@@ -260,11 +283,23 @@ Split split_of(int logN) {
 
 }  // namespace
 
+int ntt_split_candidates(int logN, int* out, int cap) {
+    int n = 0;
+    const int cand[4] = {logN / 2, best_s1(logN), logN / 2 - 1, logN / 2 + 1};
+    for (int c : cand) {
+        if (!split_ok(logN, c)) continue;
+        bool dup = false;
+        for (int i = 0; i < n; ++i) dup |= out[i] == c;
+        if (!dup && n < cap) out[n++] = c;
+    }
+    return n;
+}
+
 void ntt_forward(he_ctx* ctx, uint64_t* data, int items, size_t item_stride, int rows,
                  int mod_off) {
     if (items <= 0 || rows <= 0) return;
     ctx->launches += 2;
-    const Split sp = split_of(ctx->logN);
+    const Split sp = split_of(ctx->logN, ctx->ntt_s1);
     dim3 gc(sp.col_ctas, rows, items), gr(sp.row_ctas, rows, items);
     k_ntt_cols<false><<<gc, sp.col_threads, 0, ctx->stream>>>(
         data, item_stride, mod_off, ctx->logN, sp.s1, sp.lc, ctx->d_mod, ctx->d_tw_fwd);
@@ -276,7 +311,7 @@ void ntt_inverse(he_ctx* ctx, uint64_t* data, int items, size_t item_stride, int
                  int mod_off) {
     if (items <= 0 || rows <= 0) return;
     ctx->launches += 2;
-    const Split sp = split_of(ctx->logN);
+    const Split sp = split_of(ctx->logN, ctx->ntt_s1);
     dim3 gc(sp.col_ctas, rows, items), gr(sp.row_ctas, rows, items);
     k_ntt_rows<true><<<gr, sp.row_threads, 0, ctx->stream>>>(
         data, item_stride, mod_off, ctx->logN, sp.s1, sp.blocks, ctx->d_mod, ctx->d_tw_inv);

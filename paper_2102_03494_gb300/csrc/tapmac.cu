@@ -321,8 +321,49 @@ void launch_ks_mac_ext_bulk(he_ctx* c, const uint64_t* D, const uint64_t* XP, co
     }
 }
 
-// Autotuner of the tap kernel: times both tiles on synthetic operands of `batch` images (25
-// taps, 2 channels, the context's key shape) and keeps the faster for this context.
+// Autotuner: times the NTT splits worth trying on a batch's ciphertexts (forward and inverse)
+// and both tap-kernel tiles on synthetic operands of `batch` images (25 taps, 2 channels, the
+// context's key shape), and keeps the fastest of each for this context.
+static int tune_ntt(he_ctx* ctx, int batch, double* best_ms) {
+    int cand[4];
+    const int nc = ntt_split_candidates(ctx->logN, cand, 4);
+    const size_t items = (size_t)2 * batch, n = items * ctx->L * ctx->N;
+    int rc = arena_reserve(ctx, n + 32);
+    if (rc) return rc;
+    arena_reset(ctx);
+    uint64_t* X = arena_take(ctx, n);
+    for (size_t it = 0; it < items; ++it)
+        launch_uniform(ctx, he_stream_state(0x6e7474ull, it), X + it * ctx->L * ctx->N, ctx->L, 0, 0);
+    cudaEvent_t e0, e1;
+    HE_CHECK_CUDA(ctx, cudaEventCreate(&e0));
+    HE_CHECK_CUDA(ctx, cudaEventCreate(&e1));
+    double best = 1e30;
+    int best_s1 = cand[0];
+    for (int c = 0; c < nc; ++c) {
+        ctx->ntt_s1 = cand[c];
+        ntt_forward(ctx, X, (int)items, (size_t)ctx->L * ctx->N, ctx->L, 0);     // warm-up
+        ntt_inverse(ctx, X, (int)items, (size_t)ctx->L * ctx->N, ctx->L, 0);
+        cudaEventRecord(e0, ctx->stream);
+        for (int rep = 0; rep < 3; ++rep) {
+            ntt_forward(ctx, X, (int)items, (size_t)ctx->L * ctx->N, ctx->L, 0);
+            ntt_inverse(ctx, X, (int)items, (size_t)ctx->L * ctx->N, ctx->L, 0);
+        }
+        cudaEventRecord(e1, ctx->stream);
+        cudaEventSynchronize(e1);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (t / 3.0 < best) {
+            best = t / 3.0;
+            best_s1 = cand[c];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->ntt_s1 = best_s1;
+    *best_ms = best;
+    return he_launch_check(ctx, "he_autotune");
+}
+
 extern "C" int he_autotune(he_ctx* ctx, int batch, int force_tile, double* ms_out) {
     if (!ctx) return HE_EINVAL;
     if (force_tile) {
@@ -332,14 +373,20 @@ extern "C" int he_autotune(he_ctx* ctx, int batch, int force_tile, double* ms_ou
         return HE_OK;
     }
     if (batch < 1 || batch > 1024) return he_fail(ctx, HE_EINVAL, "he_autotune: batch out of range");
-    if (!tapmac_bulk_supported(ctx)) return HE_OK;        // nothing to choose
+    double ntt_ms = 0;
+    int rc = tune_ntt(ctx, batch, &ntt_ms);
+    if (rc) return rc;
+    if (ms_out) {
+        ms_out[2] = ntt_ms;
+        ms_out[3] = ctx->ntt_s1;
+    }
+    if (!tapmac_bulk_supported(ctx)) return HE_OK;        // no tile to choose
     const int L = ctx->L, LK = L + ctx->K, dn = ctx->dnum, taps = 25, r = 2;
     const size_t N = ctx->N, LN = (size_t)LK * N;
     const size_t nD = (size_t)batch * dn * LN, nXP = (size_t)batch * 2 * L * N,
                  nP = (size_t)r * taps * LN, nK = (size_t)dn * 2 * LN,
                  nA = (size_t)batch * r * 2 * LN;
-    int rc = arena_reserve(ctx, nD + nXP + nP + nK + nA + 32 * 8);
-    if (rc) return rc;
+    if ((rc = arena_reserve(ctx, nD + nXP + nP + nK + nA + 32 * 8))) return rc;
     arena_reset(ctx);
     uint64_t* D = arena_take(ctx, nD);
     uint64_t* XP = arena_take(ctx, nXP);

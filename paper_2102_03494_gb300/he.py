@@ -401,11 +401,11 @@ class Context:
         return outs
 
     def he_autotune(self, batch, force_tile=0):
-        """Pick the tap-kernel tile by timing (force_tile 128 / 256 sets it); returns the
-        per-launch times of the 128 and 256 tiles (zeros when forced)."""
-        ms = (ctypes.c_double * 2)()
+        """Tune the NTT split and the tap-kernel tile by timing (force_tile 128 / 256 only
+        sets the tile); returns (tap ms with tile 128, with 256, NTT ms, chosen log2 N1)."""
+        ms = (ctypes.c_double * 4)()
         self._ck(lib().he_autotune(self.h, batch, force_tile, ms), "he_autotune")
-        return float(ms[0]), float(ms[1])
+        return float(ms[0]), float(ms[1]), float(ms[2]), int(ms[3])
 
     def he_probe_int_mac(self):
         """Measured 64 x 64 -> 128-bit products/s: (carry chain, 32-bit column sums)."""

@@ -194,8 +194,8 @@ def test_autotuned_tap_tile_keeps_the_bits():
     ctx = make_ctx(prm)
     lay = ctx.layout(*shape.astuple(), pack="dp_shift_ext")
     ctx.he_load_keys(blob, gpu_steps(steps))
-    t128, t256 = ctx.he_autotune(3)
-    assert t128 > 0 and t256 > 0
+    t128, t256, t_ntt, s1 = ctx.he_autotune(3)
+    assert t128 > 0 and t256 > 0 and t_ntt > 0 and 1 <= s1 < prm.log_n
     want = [ffconv.he_layer(prm, c, W1, W2, lay_o, keys) for c in cts]
     for tile in (128, 256):
         ctx.he_autotune(3, force_tile=tile)
