@@ -35,7 +35,7 @@ enum {
     HE_ENOMEM = -2,   /* device allocation failed */
     HE_ENOKEY = -3,   /* a rotation needs a Galois key that is not loaded */
     HE_ECUDA = -4,    /* a CUDA call or kernel launch failed */
-    HE_ETIMEOUT = -5  /* reserved for bounded device waits */
+    HE_ETIMEOUT = -5  /* a bounded device-side wait ran out (reported by the next call) */
 };
 
 enum { HE_COEFF = 0, HE_NTT = 1 };            /* representation of a ciphertext's limbs */
@@ -77,10 +77,8 @@ typedef struct {
 
 /* Shape of one FFConv layer (Sec. 3.1 notation): input I_c x I_h x I_w, low-rank filters
  * W1 of d x d x I_c x r (r = O'_c of Eq. 2), restoring filters W2 of 1 x 1 x r x O_c,
- * stride and zero padding of W1, pack = HE_DP_DOT, HE_DP_SHIFT, HE_DP_SHIFT_EXT or HE_CP_CP,
- * modswitch
- * != 0 drops the
- * last ciphertext prime at the end of the layer. */
+ * stride and zero padding of W1, pack = HE_DP_DOT, HE_DP_SHIFT, HE_DP_SHIFT_EXT or HE_CP_CP;
+ * modswitch != 0 drops the last ciphertext prime at the end of the layer. */
 typedef struct {
     int32_t I_c, I_h, I_w, d, stride, pad, r, O_c;
     int32_t pack;
@@ -192,9 +190,10 @@ int he_add(he_ctx* ctx, const he_ct* a, const he_ct* b, he_ct* out);
 /* Ciphertext product with relinearisation (Sec. 2.1's homomorphic multiplication; with a = b
  * the square x^2 the paper uses as activation, Sec. 3): out decrypts to the slot-wise product.
  * Exactly round(t/Q (a0 + a1 s)(b0 + b1 s)) coefficient-wise -- the centred lifts are
- * multiplied over an auxiliary basis B (prod B > N Q, chosen by the context) and the scaling
- * is decided on multi-word integers -- then the s^2 component is key-switched with the key of
- * step HE_RELIN_KEY.  a, b, out: NTT domain, full level (out may alias an input).
+ * multiplied over an auxiliary basis B (prod B > 16 N Q, chosen by the context), and every
+ * rounding is decided exactly (128-bit fixed-point fractions, multi-word integers where those
+ * cannot decide) -- then the s^2 component is key-switched with the key of step HE_RELIN_KEY.
+ * a, b, out: NTT domain, full level (out may alias an input); at most 32 ciphertext primes.
  * HE_ENOKEY without the relinearisation key. */
 int he_multiply(he_ctx* ctx, const he_ct* a, const he_ct* b, he_ct* out);
 /* The same for n pairs: out[i] = a[i] b[i] (out[i] may alias a[i] or b[i]); pairs with
@@ -305,16 +304,17 @@ typedef struct {
  * h W + w; other slots zero.  Packing (DensePack over several ciphertexts, Sec. 3.2 with the
  * FFConv factorization of Sec. 4): every input ciphertext is rotated by the d^2 - 1 nonzero tap
  * offsets (hoisted, summed in Q u P per low-rank channel over all input ciphertexts, one
- * ModDown each); a rotate-and-sum over the g blocks (steps Bk 2^e) replicates each low-rank
- * output in every block; output ciphertext G = sum_c' y1[c'] * P[G][c'] with P[G][c'] holding
+ * ModDown each); the block sum y1 = sum_{u<g} rot(acc, u Bk) (g - 1 rotations hoisted from one
+ * ModUp, summed in Q u P, one ModDown) replicates each low-rank output in every block; output
+ * ciphertext G = sum_c' y1[c'] * P[G][c'] with P[G][c'] holding
  * restore_w[G g + j][c'] on block j (identity when unfactorized) -- no rotation.  in:
  * [B][ceil(C_in / g)], out: [B][ceil(O_c / g)], full level, NTT domain.  lowrank_w: host int32
  * [r or O_c][C_in][d][d]; restore_w: host int32 [O_c][r], NULL when r = 0.  Keys: the nonzero
- * tap offsets (i - pad) W + (j - pad) and the fold steps Bk 2^e < N/2. */
+ * tap offsets (i - pad) W + (j - pad) and the block steps u Bk, u = 1 .. g - 1. */
 int he_mc_conv_batch(he_ctx* ctx, const he_ct* in, int B, const int32_t* lowrank_w,
                      const int32_t* restore_w, const he_mc_conv* conv, he_ct* out);
 /* In place, for each step in order: x <- x + rot(x, step), on n ciphertexts (full level, NTT
- * domain); e.g. the global sum pooling inside blocks (steps 1, 2, ..., Bk/2). */
+ * domain); e.g. a sum pooling inside blocks of Bk slots (steps 1, 2, ..., Bk/2). */
 int he_rotate_sum_batch(he_ctx* ctx, he_ct* cts, int n, const int32_t* steps, int n_steps);
 /* he_fc_layer_batch over n_ct input ciphertexts per image (in: [B][n_ct]): feature i at slot
  * pos[i] of ciphertext ct_of[i]; the taps of all input ciphertexts are summed in Q u P before the
