@@ -300,6 +300,18 @@ def run(args):
     s1.record(stream)
     torch.cuda.synchronize()
     ms_single_planned = s0.elapsed_time(s1) / n_single
+    # ... and captured into a CUDA graph: one submission per image, reading the bound input
+    gid, _ = ctx.he_ffconv_graph_create(plan, one, lay, one_out)
+    for _ in range(3):
+        ctx.he_graph_launch(gid)
+    torch.cuda.synchronize()
+    s0.record(stream)
+    for _ in range(n_single):
+        ctx.he_graph_launch(gid)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    ms_single_graph = s0.elapsed_time(s1) / n_single
+    ctx.he_graph_free(gid)
     ctx.he_ffconv_plan_free(plan)
 
     roof = taps_roofline(phases, args, B, n_rot)
@@ -336,6 +348,7 @@ def run(args):
             "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items() if v[1]},
             "batching": {"one_at_a_time_ms_per_image": ms_single,
                          "one_at_a_time_weights_resident_ms_per_image": ms_single_planned,
+                         "one_at_a_time_captured_graph_ms_per_image": ms_single_graph,
                          "batched_ms_per_image": ms / args.steps / B,
                          "factor": ms_single / (ms / args.steps / B),
                          "note": "same layer, same outputs; one image per call vs the batch"},
@@ -389,7 +402,7 @@ def measured_peaks():
 # DRAM bytes (read + write) of one k_ks_mac_ext launch, from one ncu capture of the current
 # kernel version at the bench shape (profiles/k_ks_mac_ext_n15.md); cleared when the kernel
 # changes and until it is captured again.
-KS_MAC_EXT_TRAFFIC = {16: 1313583104 + 241992192}
+KS_MAC_EXT_TRAFFIC = {}
 
 
 # 64 x 64 -> 128-bit products per second of the GPU's integer multiplier: 152 SMs x 64 32-bit
@@ -450,7 +463,7 @@ def run_serving(args):
         shape = workloads.LayerShape(*sp.shape)
         W1, W2 = workloads.weights(i, shape, lo=-8, hi=8)
         rings[name] = serving.GpuRing(sp, workers=2, W1=W1, W2=W2, sk_seed=1 + i, key_seed=11 + i,
-                                      keep_results=False)
+                                      keep_results=False, graphs=8)
 
     def make_requests(rate, count, seed):
         reqs = serving.poisson_arrivals(seed=seed, rate=rate, count=count, mix=mix)
@@ -472,24 +485,36 @@ def run_serving(args):
         for r in reqs:
             r.payload = r.result = None
 
-    # warm-up of every worker of every ring at the largest batch (scratch sizing, first launches)
+    # warm-up of every worker of every ring at the largest batch (first launches), both forms
     warm = make_requests(1e9, 64, seed=99)
     for name, ring in rings.items():
         mine = [r for r in warm if r.ring == name][:8]
-        for w in range(ring.workers):
-            ring.launch(w, mine)
+        for use in (False, True):
+            ring.use_graphs = use
+            for w in range(ring.workers):
+                ring.launch(w, mine)
     torch.cuda.synchronize()
     out = {"metric": "serving: mixed-ring encrypted FFConv-layer requests, continuous batching",
            "unit": "requests/s and ms", "mix": mix, "workers_per_ring": 2, "max_batch": 8,
+           "served": "batches run as captured CUDA graphs (one per worker and batch size)",
+           "served_calls": "the same scheduler, batches run as library calls",
            "rates": []}
-    for rate in (100.0, 400.0, 800.0, 1600.0):
-        count = int(min(rate * 1.5, 1200))
+
+    def serve(rate, count, graphs):
+        for ring in rings.values():
+            ring.use_graphs = graphs
         reqs = make_requests(rate, count, seed=int(rate))
         sched = serving.Scheduler(rings, max_batch=8, memory_budget=64 << 30,
                                   clock=time.perf_counter)
         done = sched.serve(reqs)
         torch.cuda.synchronize()
-        served = serving.latency_stats(done)
+        release(reqs)
+        return serving.latency_stats(done)
+
+    for rate in (100.0, 400.0, 800.0, 1600.0):
+        count = int(min(rate * 1.5, 1200))
+        served_calls = serve(rate, count, False)
+        served = serve(rate, count, True)
         # the plain form: one request per call in arrival order on one stream
         plain_reqs = make_requests(rate, count, seed=int(rate))
         t_free, lat, t_first = 0.0, [], None
@@ -501,12 +526,11 @@ def run_serving(args):
             t_free = start + dt
             lat.append((t_free - r.t_arrive) * 1000.0)
         span = t_free - plain_reqs[0].t_arrive
-        release(reqs)
         release(plain_reqs)
         plain = {"requests": count, "p50_ms": float(np.percentile(lat, 50)),
                  "p99_ms": float(np.percentile(lat, 99)), "requests_per_s": count / span}
-        out["rates"].append({"offered_per_s": rate, "served": served, "plain": plain,
-                             "p99_factor": plain["p99_ms"] / served["p99_ms"]})
+        out["rates"].append({"offered_per_s": rate, "served": served, "served_calls": served_calls,
+                             "plain": plain, "p99_factor": plain["p99_ms"] / served["p99_ms"]})
     print(json.dumps(out))
 
 

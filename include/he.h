@@ -244,6 +244,24 @@ int he_ffconv_plan(he_ctx* ctx, const int32_t* lowrank_w, const int32_t* restore
                    const he_layout* layout, int32_t* plan_out);
 int he_ffconv_layer_planned(he_ctx* ctx, int32_t plan, const he_ct* ct_in, int B, he_ct* ct_out);
 int he_ffconv_plan_free(he_ctx* ctx, int32_t plan);
+/* Captured layers.  he_ffconv_graph_create runs he_ffconv_layer_planned(plan, ct_in, B,
+ * ct_out) once on the context stream (so ct_out holds its result on return), then records
+ * the same call, on these exact buffers, into a CUDA graph and returns a graph id.
+ * he_graph_launch replays it on the context stream: one submission for the layer's kernels
+ * and copies; it reads whatever ct_in holds at that point and overwrites ct_out.  The caller
+ * keeps ct_in and ct_out allocated while the graph lives.  Scratch: share_scratch = 0 gives
+ * the graph a scratch area of its own; 1 records it on the context's scratch (no extra
+ * memory; safe because all of a context's work runs in order on its stream), valid until a
+ * later call needs more scratch than the context holds and reallocates it -- capture the
+ * largest batch first.  The resident keys and the plan are used by reference: new key
+ * material loaded for the same steps is picked up, while a launch after the plan was freed,
+ * a key was dropped or the shared scratch was reallocated fails with HE_EINVAL (recreate the
+ * graph).  he_graph_free releases it (after the stream drains).  HE_EINVAL for unknown ids;
+ * capture errors as HE_ECUDA. */
+int he_ffconv_graph_create(he_ctx* ctx, int32_t plan, const he_ct* ct_in, int B, he_ct* ct_out,
+                           int share_scratch, int32_t* graph_out);
+int he_graph_launch(he_ctx* ctx, int32_t graph);
+int he_graph_free(he_ctx* ctx, int32_t graph);
 /* Rotation steps the layer needs keys for; writes at most `cap` steps into steps_out and
  * returns the count (or HE_EINVAL for a layout that does not fit the ring). */
 int he_ffconv_required_steps(const he_ctx* ctx, const he_layout* layout, int32_t* steps_out,

@@ -14,8 +14,8 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libhe.so")
-UNITS = ["api.cu", "deepnet.cu", "eval.cu", "kernels.cu", "layer.cu", "mult.cu", "network.cu",
-         "noalloc.cu", "ntt.cu", "probe.cu", "tapmac.cu"]
+UNITS = ["api.cu", "deepnet.cu", "eval.cu", "graph.cu", "kernels.cu", "layer.cu", "mult.cu",
+         "network.cu", "noalloc.cu", "ntt.cu", "probe.cu", "tapmac.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -255,6 +255,7 @@ int arena_reserve(he_ctx* ctx, size_t n_u64) {
         return he_fail(ctx, HE_ENOMEM, "scratch allocation of " + std::to_string(want) + " bytes failed");
     }
     ctx->arena.cap = want;
+    ++ctx->arena_epoch;
     return HE_OK;
 }
 
@@ -271,6 +272,16 @@ uint64_t* arena_take(he_ctx* ctx, size_t n_u64) {
 // Small host->device uploads go through a ring of pinned staging slots so that they stay
 // asynchronous; a slot is reused only after the copy that last read it has executed.
 const void* upload_small(he_ctx* ctx, const void* src, size_t bytes) {
+    if (ctx->capture_allocs) {                   // graph capture: a buffer the graph owns
+        void* d = nullptr;
+        if (cudaMalloc(&d, bytes ? bytes : 8) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        ctx->capture_allocs->push_back(d);
+        if (bytes && cudaMemcpy(d, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return nullptr;
+        return d;
+    }
     Staging& st = ctx->staging;
     if (bytes > st.slot_bytes) return nullptr;
     int slot = st.next;
@@ -322,6 +333,7 @@ static void free_ctx(he_ctx* c) {
         if (kv.second.dev) cudaFree(kv.second.dev);
     for (auto& kv : c->plans)
         if (kv.second.pts) cudaFree(kv.second.pts);
+    for (auto& kv : c->graphs) graph_release(kv.second);
     if (c->staging.host) cudaFreeHost(c->staging.host);
     for (auto e : c->staging.ev)
         if (e) cudaEventDestroy(e);

@@ -89,6 +89,7 @@ extern "C" int he_load_keys(he_ctx* ctx, const uint64_t* blob, const int32_t* st
             if (it != ctx->keys.end()) {
                 if (it->second.dev) cudaFree(it->second.dev);
                 ctx->keys.erase(it);
+                ++ctx->keys_epoch;
             }
         }
         return he_fail(ctx, HE_EINVAL, "he_load_keys: key residue not below its modulus");

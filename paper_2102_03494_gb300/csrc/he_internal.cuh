@@ -187,6 +187,24 @@ struct he_ctx {
     };
     std::map<int32_t, LayerPlan> plans;
     int32_t next_plan = 1;
+    uint64_t keys_epoch = 0;            // bumped whenever a resident key is dropped
+    uint64_t arena_epoch = 0;           // bumped whenever the scratch arena is reallocated
+    struct LayerGraph {                 // he_ffconv_graph_create: a captured planned layer
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        Arena arena;                    // the graph's own scratch (empty when shared)
+        bool shared = false;            // recorded on the context's scratch
+        uint64_t arena_epoch = 0;       // ... at this generation of it
+        std::vector<void*> allocs;      // small tables uploaded while capturing
+        int32_t plan = 0;
+        uint64_t keys_epoch = 0;
+        uint64_t launches = 0, ops[4] = {0, 0, 0, 0};   // per replay
+    };
+    std::map<int32_t, LayerGraph> graphs;
+    int32_t next_graph = 1;
+    // While a graph is captured, small uploads go to device buffers listed here (owned by
+    // the graph) instead of the staging ring, whose slots are reused.
+    std::vector<void*>* capture_allocs = nullptr;
     Staging staging;
     uint64_t ops[4] = {0, 0, 0, 0};     // MulPC, AddCC, Rot, KeySwitch
     uint64_t launches = 0;              // kernels launched by this context
@@ -232,6 +250,8 @@ int check_ct(he_ctx* ctx, const he_ct* ct, int need_limbs, int need_domain, cons
 void encode_device(he_ctx* ctx, const int64_t* d_slots, int items, uint64_t* tmp, uint64_t* out,
                    int mont, int rows);
 int he_get_key(he_ctx* ctx, uint32_t g, const uint64_t** key);
+// Frees a captured layer's graph, scratch and tables (graph.cu); the stream must be idle.
+void graph_release(he_ctx::LayerGraph& g);
 
 // host arithmetic (api.cu)
 uint64_t h_mulmod(uint64_t a, uint64_t b, uint64_t q);

@@ -364,8 +364,10 @@ static int layer_impl(he_ctx* ctx, const he_ct* ct_in, int B, const int32_t* low
                           : std::min(dot ? n_prod : (li.fold ? B * r : B), rotation_chunk(ctx));
     const int rot_items = chunk;
     const size_t ext_acc = ext ? (size_t)B * r * 2 * LK * N + (size_t)B * ct : 0;  // sums, P x
+    // slots, tmp and plaintexts of the encode step (none when a plan holds the plaintexts)
+    const size_t enc_words = pre_pts ? 0 : (size_t)n_pt * (2 * N + (size_t)pt_rows * N);
     size_t need = (size_t)B * ct                              // X
-                  + (size_t)n_pt * (2 * N + (size_t)pt_rows * N)  // slots, tmp, plaintexts
+                  + enc_words
                   + (size_t)n_prod * ct * (dot ? 2 : 1)        // products (double buffer for DP_DOT)
                   + (size_t)2 * B * r * ct + ext_acc           // accumulators (double buffer)
                   + (size_t)rot_items * rot_scratch_per_item(ctx)
@@ -373,9 +375,9 @@ static int layer_impl(he_ctx* ctx, const he_ct* ct_in, int B, const int32_t* low
     if ((rc = arena_reserve(ctx, need))) return rc;
     arena_reset(ctx);
     uint64_t* X = arena_take(ctx, (size_t)B * ct);
-    int64_t* slots = (int64_t*)arena_take(ctx, (size_t)n_pt * N);
-    uint64_t* tmp = arena_take(ctx, (size_t)n_pt * N);
-    uint64_t* pts = arena_take(ctx, (size_t)n_pt * pt_rows * N);
+    int64_t* slots = pre_pts ? nullptr : (int64_t*)arena_take(ctx, (size_t)n_pt * N);
+    uint64_t* tmp = pre_pts ? nullptr : arena_take(ctx, (size_t)n_pt * N);
+    uint64_t* pts = pre_pts ? const_cast<uint64_t*>(pre_pts) : arena_take(ctx, (size_t)n_pt * pt_rows * N);
     uint64_t* PR = n_prod ? arena_take(ctx, (size_t)n_prod * ct) : nullptr;
     uint64_t* AX = ext ? arena_take(ctx, (size_t)B * r * 2 * LK * N) : nullptr;
     uint64_t* XP = ext ? arena_take(ctx, (size_t)B * ct) : nullptr;
@@ -393,9 +395,7 @@ static int layer_impl(he_ctx* ctx, const he_ct* ct_in, int B, const int32_t* low
         HE_CHECK_CUDA(ctx, cudaMemcpyAsync(X + b * ct, ct_in[b].data, ct * 8, cudaMemcpyDeviceToDevice,
                                            ctx->stream));
     // (a1) plaintexts: slot vectors from the integer weights, encoded in Montgomery form
-    if (pre_pts) {
-        pts = const_cast<uint64_t*>(pre_pts);
-    } else {
+    if (!pre_pts) {
         phase_begin(ctx, HE_PHASE_ENCODE);
         if ((rc = encode_w1(ctx, y, li, lowrank_w, slots, tmp, pts))) return rc;
         phase_end(ctx);

@@ -110,6 +110,10 @@ _SIGS = {
     "he_ffconv_plan": ([_P, _I32P, _I32P, ctypes.POINTER(HeLayout), _I32P], ctypes.c_int),
     "he_ffconv_layer_planned": ([_P, ctypes.c_int32, _CTP, ctypes.c_int, _CTP], ctypes.c_int),
     "he_ffconv_plan_free": ([_P, ctypes.c_int32], ctypes.c_int),
+    "he_ffconv_graph_create": ([_P, ctypes.c_int32, _CTP, ctypes.c_int, _CTP, ctypes.c_int, _I32P],
+                               ctypes.c_int),
+    "he_graph_launch": ([_P, ctypes.c_int32], ctypes.c_int),
+    "he_graph_free": ([_P, ctypes.c_int32], ctypes.c_int),
     "he_ntt": ([_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
 }
 _lib = None
@@ -165,6 +169,7 @@ class Context:
         self.N = 1 << log_n
         self.L, self.K, self.alpha = n_q, n_p, alpha
         self.dnum = -(-n_q // alpha)
+        self._graph_refs = {}                     # graph id -> the tensors it reads / writes
         prm = HeParams(log_n, n_q, q_bits, n_p, p_bits, alpha, t)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = _P()
@@ -533,6 +538,29 @@ class Context:
 
     def he_ffconv_plan_free(self, plan):
         self._ck(lib().he_ffconv_plan_free(self.h, plan), "he_ffconv_plan_free")
+
+    def he_ffconv_graph_create(self, plan, cts_in, lay, outs=None, share_scratch=False):
+        """Captures the planned layer on these buffers; returns (graph id, outs).  The
+        tensors stay referenced here until he_graph_free, since the graph reads and writes
+        them in place at every he_graph_launch."""
+        B = len(cts_in)
+        if lay.pack == HE_CP_CP:
+            B //= lay.d * lay.d * lay.I_c
+        lv = self.L - 1 if lay.modswitch else self.L
+        outs = [self.new_ct(level=lv) for _ in range(B * lay.O_c)] if outs is None else outs
+        ia, oa = self.ct_array(cts_in), self.ct_array(outs)
+        gid = (ctypes.c_int32 * 1)()
+        self._ck(lib().he_ffconv_graph_create(self.h, plan, ia, B, oa, int(bool(share_scratch)), gid),
+                 "he_ffconv_graph_create")
+        self._graph_refs[int(gid[0])] = (list(cts_in), list(outs))
+        return int(gid[0]), outs
+
+    def he_graph_launch(self, graph):
+        self._ck(lib().he_graph_launch(self.h, graph), "he_graph_launch")
+
+    def he_graph_free(self, graph):
+        self._ck(lib().he_graph_free(self.h, graph), "he_graph_free")
+        self._graph_refs.pop(graph, None)
 
     def he_ffconv_layer(self, ct_in, W1, W2, lay, outs=None):
         lv = self.L - 1 if lay.modswitch else self.L

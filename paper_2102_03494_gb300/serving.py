@@ -167,7 +167,10 @@ class GpuRing:
     context, weights fixed per ring."""
 
     def __init__(self, spec: RingSpec, workers: int, W1, W2, sk_seed: int, key_seed: int,
-                 keep_results: bool = True):
+                 keep_results: bool = True, graphs: int = 0):
+        """graphs = G > 0: every worker also captures its layer into CUDA graphs for batches of
+        1 .. G images, on input / output buffers of its own (the largest batch first, all on
+        the worker context's scratch); a batch then costs two copies and one submission."""
         import torch
         from . import he
         self.spec, self.workers = spec, workers
@@ -186,6 +189,19 @@ class GpuRing:
         self.N = 1 << spec.log_n
         self.ct_bytes = 2 * spec.n_q * self.N * 8
         self.O_c = spec.shape[7]
+        self.graphs = []                          # per worker: batch size -> (ins, outs, id)
+        self.use_graphs = graphs > 0              # launch through them (a switch for comparisons)
+        for w, c in enumerate(self.ctx):
+            g = {}
+            if graphs > 0:
+                with torch.cuda.stream(self.streams[w]):
+                    ins = [c.new_ct() for _ in range(graphs)]
+                    outs = [c.new_ct() for _ in range(graphs * self.O_c)]
+                for b in range(graphs, 0, -1):
+                    gid, _ = c.he_ffconv_graph_create(self.plans[w], ins[:b], self.lay,
+                                                      outs[:b * self.O_c], share_scratch=True)
+                    g[b] = (ins[:b], outs[:b * self.O_c], gid)
+            self.graphs.append(g)
 
     def encrypt(self, slots, seed):
         return self.ctx[0].he_encrypt(self.sk, slots, seed)
@@ -200,6 +216,18 @@ class GpuRing:
     def launch(self, worker, requests):
         import torch
         ctx = self.ctx[worker]
+        captured = self.graphs[worker].get(len(requests)) if self.use_graphs else None
+        if captured is not None:
+            ins, outs, gid = captured
+            with torch.cuda.stream(self.streams[worker]):
+                for buf, r in zip(ins, requests):
+                    buf.copy_(r.payload)
+                ctx.he_graph_launch(gid)
+                # the bound outputs are rewritten by the worker's next batch: keep copies
+                res = [o.clone() for o in outs] if self.keep_results else None
+                ev = torch.cuda.Event()
+                ev.record(self.streams[worker])
+            return (ev, res)
         with torch.cuda.stream(self.streams[worker]):
             # allocated (and zero-filled) on the worker's stream, ordered before the layer
             outs = [ctx.new_ct() for _ in range(len(requests) * self.O_c)]
@@ -216,6 +244,13 @@ class GpuRing:
         outs = handle[1]
         for i, r in enumerate(requests):
             r.result = outs[i * self.O_c:(i + 1) * self.O_c] if self.keep_results else None
+
+    def close(self):
+        """Frees the captured graphs (the contexts go with the ring)."""
+        for c, g in zip(self.ctx, self.graphs):
+            for _, _, gid in g.values():
+                c.he_graph_free(gid)
+        self.graphs = [{} for _ in self.ctx]
 
     def run_alone(self, payload):
         """The plain form: one request, one call, waited for."""

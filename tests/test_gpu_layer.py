@@ -185,6 +185,75 @@ def test_planned_layer_matches_the_plain_call(pack):
         ctx.he_ffconv_layer_planned(plan, [upload_ntt(ctx, c) for c in cts], lay)
 
 
+@pytest.mark.parametrize("pack", ["dp_dot", "dp_shift", "dp_shift_ext", "cp_cp"])
+def test_captured_layer_replays_bit_exact(pack):
+    """A planned layer captured into a CUDA graph: the capture call, every replay and a replay
+    on new inputs written into the bound buffers give the oracle's bits, also after another
+    call grew the context's own scratch; a graph recorded on the context's scratch works
+    until a call regrows it; freeing the graph or its plan ends its replays."""
+    from paper_2102_03494_gb300 import he
+    prm = params.Params(log_n=9, n_q=3, n_p=1, alpha=1)
+    shape = workloads.LayerShape(2, 6, 6, 3, 1, 1, 2, 2)
+    lay_o, s, steps, keys, blob, xs, W1, W2, cts = setup_layer(prm, shape, pack, seed=5, B=2)
+    ctx = make_ctx(prm)
+    lay = ctx.layout(*shape.astuple(), pack=pack)
+    ctx.he_load_keys(blob, gpu_steps(steps))
+    plan = ctx.he_ffconv_plan(W1, W2, lay)
+    K = shape.d * shape.d * shape.I_c if pack == "cp_cp" else 1
+    img = [cts[b * K:(b + 1) * K] if pack == "cp_cp" else [cts[b]] for b in range(2)]
+    want = [ffconv.he_layer(prm, img[b] if pack == "cp_cp" else img[b][0], W1, W2, lay_o, keys)
+            for b in range(2)]
+
+    def check(outs, order):
+        for b in range(2):
+            for c in range(shape.O_c):
+                got = download_coeff(ctx, outs[b * shape.O_c + c])
+                assert (got == want[order[b]][c].stack()).all(), (b, c)
+
+    ins = [upload_ntt(ctx, c) for c in cts]
+    n0 = ctx.he_launch_count()
+    gid, outs = ctx.he_ffconv_graph_create(plan, ins, lay)
+    per_call = ctx.he_launch_count() - n0
+    check(outs, [0, 1])
+    for o in outs:
+        o.zero_()
+    n1 = ctx.he_launch_count()
+    ctx.he_graph_launch(gid)
+    assert ctx.he_launch_count() - n1 == per_call     # the replay counts the captured kernels
+    check(outs, [0, 1])
+    # new inputs in the bound buffers: the two images swapped
+    for b in range(2):
+        for k in range(K):
+            ins[b * K + k].copy_(upload_ntt(ctx, img[1 - b][k]))
+    ctx.he_graph_launch(gid)
+    check(outs, [1, 0])
+    # a larger uncaptured call regrows the context scratch; the graph keeps its own
+    ctx.he_ffconv_layer_batch([upload_ntt(ctx, c) for c in cts * 3], W1, W2, lay)
+    for b in range(2):
+        for k in range(K):
+            ins[b * K + k].copy_(upload_ntt(ctx, img[b][k]))
+    ctx.he_graph_launch(gid)
+    check(outs, [0, 1])
+    ctx.he_graph_free(gid)
+    with pytest.raises(he.HeError):
+        ctx.he_graph_launch(gid)
+    # recorded on the context's scratch: valid until a call regrows it
+    gid2, _ = ctx.he_ffconv_graph_create(plan, ins, lay, outs=outs, share_scratch=True)
+    for o in outs:
+        o.zero_()
+    ctx.he_graph_launch(gid2)
+    check(outs, [0, 1])
+    ctx.he_ffconv_layer_batch([upload_ntt(ctx, c) for c in cts * 10], W1, W2, lay)
+    with pytest.raises(he.HeError):
+        ctx.he_graph_launch(gid2)
+    ctx.he_graph_free(gid2)
+    gid3, _ = ctx.he_ffconv_graph_create(plan, ins, lay, outs=outs)
+    ctx.he_ffconv_plan_free(plan)
+    with pytest.raises(he.HeError):
+        ctx.he_graph_launch(gid3)
+    ctx.he_graph_free(gid3)
+
+
 def test_autotuned_tap_tile_keeps_the_bits():
     """he_autotune times the two tap-kernel tiles and keeps one; either forced tile gives the
     oracle's bits."""

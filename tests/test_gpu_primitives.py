@@ -214,3 +214,29 @@ def test_integer_rate_probe_is_sane():
     bound = 152 * 64 / 8 * 2070e6
     assert 0.05 * bound < chain < 1.2 * bound
     assert 0.05 * bound < cols < 1.5 * bound
+
+
+@pytest.mark.parametrize("cfg", [(13, 3, 1, 1), (14, 8, 2, 2), (15, 16, 4, 4), (16, 24, 6, 6)])
+def test_sweep_rotations_are_bit_exact(cfg):
+    """Corners of the primitive sweep: N = 2^13 .. 2^16 with 3, 8, 16, 24 primes of 50 bits and
+    1, 2, 4, 6 special primes (alpha = K); uniform random residues as ciphertexts, two steps
+    uniform in [1, N/2); plain, batched and hoisted rotations against the oracle."""
+    prm = params.Params(log_n=cfg[0], n_q=cfg[1], n_p=cfg[2], alpha=cfg[3])
+    ctx = make_ctx(prm)
+    s = bfv.keygen_secret(prm, 21)
+    rng = np.random.default_rng(cfg[0])
+    steps = [int(x) for x in rng.integers(1, prm.n // 2, 2)]
+    keys, blob = oracle_keys(prm, s, steps)
+    ctx.he_load_keys(blob, steps)
+    cts = [bfv.Ct(*[np.stack([rng.integers(0, q, prm.n, dtype=np.uint64) for q in prm.q])
+                    for _ in range(2)]) for _ in range(2)]
+    ds = [upload_ntt(ctx, c) for c in cts]
+    want = bfv.rotate(prm, cts[0], steps[0], keys)
+    assert (download_coeff(ctx, ctx.he_rotate(ds[0], steps[0])) == want.stack()).all()
+    outs = ctx.he_rotate_batch(ds, steps[0])
+    assert (download_coeff(ctx, outs[0]) == want.stack()).all()
+    if prm.log_n < 16:
+        assert (download_coeff(ctx, outs[1]) == bfv.rotate(prm, cts[1], steps[0], keys).stack()).all()
+    hs = ctx.he_rotate_hoisted(ds[1], steps)
+    for o, w in zip(hs, bfv.rotate_hoisted(prm, cts[1], steps, keys)):
+        assert (download_coeff(ctx, o) == w.stack()).all()

@@ -1,6 +1,7 @@
 """Serving loop on the GPU: requests for two rings arrive over time and are batched
-continuously across worker streams; every result is bit-identical to the same request run
-alone (one image per call) and decrypts to the plain layer."""
+continuously across worker streams (plain calls or captured CUDA graphs); every result is
+bit-identical to the same request run alone (one image per call) and decrypts to the plain
+layer."""
 import numpy as np
 import pytest
 import torch
@@ -11,7 +12,9 @@ from paper_2102_03494_gb300 import serving, workloads
 pytestmark = pytest.mark.gpu
 
 
-def test_results_are_identical_alone_and_in_the_mix():
+@pytest.mark.parametrize("graphs", [0, 4])
+def test_results_are_identical_alone_and_in_the_mix(graphs):
+    """graphs = 4: every batch runs as a captured CUDA graph of its size."""
     specs = {"a": serving.RingSpec(10, 3, 1, 1, (1, 8, 8, 3, 2, 1, 2, 3)),
              "b": serving.RingSpec(11, 4, 2, 2, (2, 6, 6, 3, 1, 1, 2, 2))}
     rings, weights = {}, {}
@@ -19,7 +22,8 @@ def test_results_are_identical_alone_and_in_the_mix():
         shape = workloads.LayerShape(*sp.shape)
         W1, W2 = workloads.weights(i, shape)
         weights[name] = (shape, W1, W2)
-        rings[name] = serving.GpuRing(sp, workers=2, W1=W1, W2=W2, sk_seed=10 + i, key_seed=20 + i)
+        rings[name] = serving.GpuRing(sp, workers=2, W1=W1, W2=W2, sk_seed=10 + i, key_seed=20 + i,
+                                      graphs=graphs)
     reqs = serving.poisson_arrivals(seed=3, rate=2000.0, count=24, mix={"a": 0.5, "b": 0.5})
     images = {}
     for r in reqs:
@@ -47,6 +51,8 @@ def test_results_are_identical_alone_and_in_the_mix():
                 assert v[ffconv.output_slot(lay, oh, ow)] == y2[0, oh, ow] % 65537
     stats = serving.latency_stats(done)
     assert stats["p99_ms"] >= stats["p50_ms"] > 0
+    for ring in rings.values():
+        ring.close()
 
 
 def serving_clock():
