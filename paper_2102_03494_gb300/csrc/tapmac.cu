@@ -7,11 +7,17 @@
 // tap the operands the tile needs are contiguous rows of the tile's size: the 2 dnum key rows
 // and the channel plaintext rows at the tile, and -- because the NTT-domain automorphism maps
 // every aligned block of 2^k positions onto an aligned block of 2^k positions (the bits of p
-// above bit k only feed the bits of perm(p) above bit k) -- the ModUp digit rows and the P c0
-// row of the one aligned block that holds perm_g of the tile.  Warp 0 copies them with
-// cp.async.bulk into one of two shared-memory stages, completed on an mbarrier, while all warps
-// compute on the other stage.  Every wait is bounded: on expiry the kernel sets a bit in the
-// context's device error word, waits (again bounded) for its own copies and returns.
+// above bit k only feed the bits of perm(p) above bit k) -- the ModUp digit rows of the one
+// aligned block that holds perm_g of the tile.  (P c0)[perm_g(n)] is one word per image and
+// tap, read straight from global memory.
+//
+// Warp-specialised pipeline: the CTA's last warp only stages taps, with cp.async.bulk, into
+// three shared-memory stages; stage s is "full" when its copied bytes have landed (an
+// mbarrier with a transaction count) and "empty" when every compute warp has arrived on a
+// second mbarrier after its last read of it.  The compute warps (one coefficient per thread)
+// never meet at a block barrier inside the tap loop, so no warp waits for the copy issue.
+// Every wait is bounded: on expiry the kernel sets a bit in the context's device error word,
+// waits (again bounded) for its own copies and returns.
 #include "he_internal.cuh"
 #include "kernels.cuh"
 
@@ -90,19 +96,26 @@ __device__ __forceinline__ uint64_t reduce_sum(U128 x, uint64_t q, uint64_t qinv
     return redc(x, q, qinv_neg);
 }
 
-// Shared-memory stage (uint64 words): keys [DNUM][2][T] | pts [2][T] | digits [2 img][DNUM][T]
-// | P x [2 img][2 poly][T].
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+constexpr int kStages = 3;
+
+// Shared-memory stage (uint64 words): keys [DNUM][2][T] | pts [2][T] | digits [2 img][DNUM][T].
+// A key-less tap (the centre, no rotation) stages the rows P x [2 img][2 poly] in the digit
+// area instead.
 template <int DNUM, int TILE>
 struct Stage {
     static constexpr int T = TILE;
     static constexpr int KEYS = 0;
     static constexpr int PTS = DNUM * 2 * T;
     static constexpr int DIG = PTS + 2 * T;
-    static constexpr int XP = DIG + 2 * DNUM * T;
-    static constexpr int WORDS = XP + 4 * T;
+    static constexpr int XP = DIG;
+    static constexpr int WORDS = DIG + (2 * DNUM > 4 ? 2 * DNUM : 4) * T;
 };
 
-// Warp 0 stages tap t into stage buffer `st`, completing on `bar`.
+// The producer warp stages tap t into stage buffer `st`, completing on `bar`.
 template <int DNUM, int TILE>
 __device__ __forceinline__ void issue_tap(uint64_t* st, uint64_t* bar, int t, const TapTable& tt,
                                          const uint64_t* __restrict__ D,
@@ -121,7 +134,7 @@ __device__ __forceinline__ void issue_tap(uint64_t* st, uint64_t* bar, int t, co
     const int nkeys = key ? 2 * DNUM : 0;
     const int npts = c_cnt;
     const int ndig = key ? nb * DNUM : 0;
-    const int nxp = qlimb ? (key ? nb : 2 * nb) : 0;
+    const int nxp = (qlimb && !key) ? 2 * nb : 0;
     const int total = nkeys + npts + ndig + nxp;
     if (lane == 0) mbar_expect_tx(bar, (uint32_t)total * row);
     __syncwarp();
@@ -141,140 +154,156 @@ __device__ __forceinline__ void issue_tap(uint64_t* st, uint64_t* bar, int t, co
             dst = st + S::DIG + (ib * DNUM + j) * kTile;
             src = D + (it * DNUM + j) * LN + (size_t)l * N + src0;
         } else {
-            const int q = i - nkeys - npts - ndig;
-            const int ib = key ? q : q >> 1, k = key ? 0 : (q & 1);
+            const int q = i - nkeys - npts - ndig, ib = q >> 1, k = q & 1;
             const size_t it = (size_t)(b0 + ib) * tt.n_sub + tt.sub[t];
             dst = st + S::XP + (ib * 2 + k) * kTile;
-            src = XPg + (it * 2 + k) * L * N + (size_t)l * N + src0;
+            src = XPg + (it * 2 + k) * L * N + (size_t)l * N + n0;
         }
         bulk_copy(dst, src, row, bar);
     }
 }
 
 // CTAs per SM the register budget is sized for: at 128-coefficient tiles with up to four key
-// digits the two stages take 45 KB, so five CTAs fit in shared memory; capping registers at
-// 96 lets all five run (20 warps per SM instead of 16; 7-8 % faster at N = 2^15, B = 16-64).
-constexpr int min_ctas(int dnum, int tile) { return tile == 128 && dnum <= 4 ? 5 : 1; }
+// digits the three stages take 54 KB, so four CTAs (4 x 5 warps) fit; 94 registers a thread.
+constexpr int min_ctas(int dnum, int tile) { return tile == 128 && dnum <= 4 ? 4 : 1; }
 
 template <int DNUM, int TILE>
-__global__ void __launch_bounds__(TILE, min_ctas(DNUM, TILE))
+__global__ void __launch_bounds__(TILE + 32, min_ctas(DNUM, TILE))
 k_ks_mac_ext_bulk(const uint64_t* __restrict__ D, const uint64_t* __restrict__ XPg,
                   const uint64_t* __restrict__ pts, TapTable tt, int c_lo, int c_cnt, int B,
                   uint64_t* __restrict__ A, int L, int K, int logN,
                   const ModConst* __restrict__ mods, int* __restrict__ err) {
     using S = Stage<DNUM, TILE>;
     constexpr int kTile = S::T;
+    constexpr int kComputeWarps = kTile / 32;
     extern __shared__ __align__(128) uint64_t smem[];
-    __shared__ __align__(8) uint64_t bars[2];    // stage filled (1 arrival + copied bytes)
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
     const int N = 1 << logN;
     const int tid = threadIdx.x;
     const int n0 = blockIdx.y * kTile;
-    const int n = n0 + tid;
     const int l = blockIdx.z;
     const int b0 = blockIdx.x * 2;
     const int nb = B - b0 < 2 ? B - b0 : 2;
     const int LK = L + K;
-    const ModConst M = mods[l];
-    const uint64_t q = M.q, qi = M.qinv_neg;
     const bool qlimb = l < L;
     const size_t LN = (size_t)LK * N;
+    const size_t LNq = (size_t)L * N;
     if (tid == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);                 // the producer's expect_tx arrival + bytes
+            mbar_init(&empty[s], kComputeWarps);    // one arrival per compute warp
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    if (tid < 32) {
-        issue_tap<DNUM, TILE>(smem, &bars[0], 0, tt, D, XPg, pts, c_lo, c_cnt, b0, nb, l, L, n0, LN, N, logN);
-        if (tt.n > 1)
-            issue_tap<DNUM, TILE>(smem + S::WORDS, &bars[1], 1, tt, D, XPg, pts, c_lo, c_cnt, b0, nb, l, L,
-                            n0, LN, N, logN);
-    }
-    // unreduced sums of at most HE_MAX_TAPS products below q^2 each: < 64 q^2 < 2^126
-    U128 a128[2][2][2];
-#pragma unroll
-    for (int ib = 0; ib < 2; ++ib)
-#pragma unroll
-        for (int c = 0; c < 2; ++c)
-#pragma unroll
-            for (int k = 0; k < 2; ++k) a128[ib][c][k] = U128{0, 0};
-    uint32_t parity = 0u;      // bit s: phase of stage s's barrier (a register, not an array)
+    // a wait that runs out does not leave its loop (the other side would then wait too): the
+    // thread goes on and the error bit makes the result unusable
     bool ok = true;
-    for (int t = 0; t < tt.n; ++t) {
-        const int s = t & 1;
-        uint64_t* st = smem + s * S::WORDS;
-        // a wait that runs out does not leave the loop (the other warps would then wait at
-        // the barrier below): the thread goes on with whatever the stage holds and the
-        // error bit makes the result unusable
-        ok &= mbar_wait(&bars[s], (parity >> s) & 1u);
-        parity ^= 1u << s;
-        const uint64_t p0 = st[S::PTS + tid];
-        const uint64_t p1 = c_cnt > 1 ? st[S::PTS + kTile + tid] : 0;
-        uint64_t x[2][2];
-        if (!tt.key[t]) {
-#pragma unroll
-            for (int ib = 0; ib < 2; ++ib) {
-                x[ib][0] = (qlimb && ib < nb) ? st[S::XP + (ib * 2) * kTile + tid] : 0;
-                x[ib][1] = (qlimb && ib < nb) ? st[S::XP + (ib * 2 + 1) * kTile + tid] : 0;
+    if (tid >= kTile) {                               // the producer warp
+        for (int t = 0; t < tt.n; ++t) {
+            const int s = t % kStages;
+            if (t >= kStages) {                       // every compute warp is done with tap t - 3
+                ok &= mbar_wait(&empty[s], (uint32_t)((t / kStages) - 1) & 1u);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             }
-        } else {
-            const int loc = (int)(perm_of((uint32_t)n, tt.g[t], logN) & (kTile - 1));
-            uint64_t kv[DNUM][2];
-#pragma unroll
-            for (int j = 0; j < DNUM; ++j) {
-                kv[j][0] = st[S::KEYS + (2 * j) * kTile + tid];
-                kv[j][1] = st[S::KEYS + (2 * j + 1) * kTile + tid];
-            }
-#pragma unroll
-            for (int ib = 0; ib < 2; ++ib) {
-                if (ib >= nb) {
-                    x[ib][0] = x[ib][1] = 0;
-                    continue;
-                }
-                U128 s0{0, 0}, s1{0, 0};
-#pragma unroll
-                for (int j = 0; j < DNUM; ++j) {
-                    const uint64_t d = st[S::DIG + (ib * DNUM + j) * kTile + loc];
-                    mac128(s0, d, kv[j][0]);
-                    mac128(s1, d, kv[j][1]);
-                }
-                if (qlimb) s0.hi += st[S::XP + (ib * 2) * kTile + loc];   // + (P c0) 2^64
-                x[ib][0] = redc_w(s0, q, qi);
-                x[ib][1] = redc(s1, q, qi);
-            }
+            issue_tap<DNUM, TILE>(smem + s * S::WORDS, &full[s], t, tt, D, XPg, pts, c_lo, c_cnt,
+                                  b0, nb, l, L, n0, LN, N, logN);
         }
+    } else {
+        const ModConst M = mods[l];
+        const uint64_t q = M.q, qi = M.qinv_neg;
+        const int n = n0 + tid;
+        // unreduced sums of at most HE_MAX_TAPS products below q^2 each: < 64 q^2 < 2^126
+        U128 a128[2][2][2];
 #pragma unroll
         for (int ib = 0; ib < 2; ++ib)
 #pragma unroll
-            for (int k = 0; k < 2; ++k) mac128(a128[ib][0][k], x[ib][k], p0);
-        if (c_cnt > 1) {                 // uniform over the launch: one channel skips this
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int k = 0; k < 2; ++k) a128[ib][c][k] = U128{0, 0};
+        for (int t = 0; t < tt.n; ++t) {
+            const int s = t % kStages;
+            const uint64_t* st = smem + s * S::WORDS;
+            ok &= mbar_wait(&full[s], (uint32_t)(t / kStages) & 1u);
+            uint64_t x[2][2];
+            if (!tt.key[t]) {
+#pragma unroll
+                for (int ib = 0; ib < 2; ++ib) {
+                    x[ib][0] = (qlimb && ib < nb) ? st[S::XP + (ib * 2) * kTile + tid] : 0;
+                    x[ib][1] = (qlimb && ib < nb) ? st[S::XP + (ib * 2 + 1) * kTile + tid] : 0;
+                }
+            } else {
+                const uint32_t pn = perm_of((uint32_t)n, tt.g[t], logN);
+                const int loc = (int)(pn & (kTile - 1));
+                uint64_t xp[2] = {0, 0};                  // (P c0)[perm_g(n)] of each image
+                if (qlimb) {
+#pragma unroll
+                    for (int ib = 0; ib < 2; ++ib)
+                        if (ib < nb)
+                            xp[ib] = __ldg(XPg + ((size_t)(b0 + ib) * tt.n_sub + tt.sub[t]) * 2 * LNq +
+                                           (size_t)l * N + pn);
+                }
+                uint64_t kv[DNUM][2];
+#pragma unroll
+                for (int j = 0; j < DNUM; ++j) {
+                    kv[j][0] = st[S::KEYS + (2 * j) * kTile + tid];
+                    kv[j][1] = st[S::KEYS + (2 * j + 1) * kTile + tid];
+                }
+#pragma unroll
+                for (int ib = 0; ib < 2; ++ib) {
+                    if (ib >= nb) {
+                        x[ib][0] = x[ib][1] = 0;
+                        continue;
+                    }
+                    U128 s0{0, 0}, s1{0, 0};
+#pragma unroll
+                    for (int j = 0; j < DNUM; ++j) {
+                        const uint64_t d = st[S::DIG + (ib * DNUM + j) * kTile + loc];
+                        mac128(s0, d, kv[j][0]);
+                        mac128(s1, d, kv[j][1]);
+                    }
+                    s0.hi += xp[ib];                      // + (P c0) 2^64 (zero on P limbs)
+                    x[ib][0] = redc_w(s0, q, qi);
+                    x[ib][1] = redc(s1, q, qi);
+                }
+            }
+            const uint64_t p0 = st[S::PTS + tid];
+            const uint64_t p1 = c_cnt > 1 ? st[S::PTS + kTile + tid] : 0;
+            __syncwarp();
+            if ((tid & 31) == 0) mbar_arrive(&empty[s]);   // this warp's last read of stage s
 #pragma unroll
             for (int ib = 0; ib < 2; ++ib)
 #pragma unroll
-                for (int k = 0; k < 2; ++k) mac128(a128[ib][1][k], x[ib][k], p1);
+                for (int k = 0; k < 2; ++k) mac128(a128[ib][0][k], x[ib][k], p0);
+            if (c_cnt > 1) {                 // uniform over the launch: one channel skips this
+#pragma unroll
+                for (int ib = 0; ib < 2; ++ib)
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) mac128(a128[ib][1][k], x[ib][k], p1);
+            }
         }
-        __syncthreads();   // every warp is done with stage s before it is refilled
-        if (tid < 32 && t + 2 < tt.n) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue_tap<DNUM, TILE>(st, &bars[s], t + 2, tt, D, XPg, pts, c_lo, c_cnt, b0, nb, l, L, n0, LN,
-                            N, logN);
+        if (ok) {
+#pragma unroll
+            for (int ib = 0; ib < 2; ++ib) {
+                if (ib >= nb) break;
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    if (c >= c_cnt) break;
+                    uint64_t* ab = A + (((size_t)(b0 + ib) * tt.r + c_lo + c) * 2) * LN + (size_t)l * N + n;
+                    ab[0] = reduce_sum(a128[ib][c][0], q, qi);
+                    ab[LN] = reduce_sum(a128[ib][c][1], q, qi);
+                }
+            }
         }
     }
+    if (!ok) atomicOr(err, 1);
+    __syncthreads();
     if (!ok) {
-        atomicOr(err, 1);
-        // let this CTA's copies land before its shared memory is released (bounded)
-        for (int s = 0; s < 2; ++s) mbar_wait(&bars[s], (parity >> s) & 1u);
-        return;
-    }
-#pragma unroll
-    for (int ib = 0; ib < 2; ++ib) {
-        if (ib >= nb) break;
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            if (c >= c_cnt) break;
-            uint64_t* ab = A + (((size_t)(b0 + ib) * tt.r + c_lo + c) * 2) * LN + (size_t)l * N + n;
-            ab[0] = reduce_sum(a128[ib][c][0], q, qi);
-            ab[LN] = reduce_sum(a128[ib][c][1], q, qi);
+        // let this CTA's copies land before its shared memory is released (bounded): the last
+        // tap staged in each stage
+        for (int s = 0; s < kStages && s < tt.n; ++s) {
+            const int last = s + kStages * ((tt.n - 1 - s) / kStages);
+            mbar_wait(&full[s], (uint32_t)(last / kStages) & 1u);
         }
     }
 }
@@ -282,7 +311,7 @@ k_ks_mac_ext_bulk(const uint64_t* __restrict__ D, const uint64_t* __restrict__ X
 template <int DNUM, int TILE>
 void launch_bulk(he_ctx* c, const uint64_t* D, const uint64_t* XP, const uint64_t* pts,
                  const TapTable& tt, uint64_t* A, int B, int c_lo, int cnt) {
-    const size_t smem = 2 * (size_t)Stage<DNUM, TILE>::WORDS * 8;
+    const size_t smem = (size_t)kStages * Stage<DNUM, TILE>::WORDS * 8;
     static bool attr_set[64] = {};   // per template instance and device
     int dev = 0;
     cudaGetDevice(&dev);
@@ -292,7 +321,7 @@ void launch_bulk(he_ctx* c, const uint64_t* D, const uint64_t* XP, const uint64_
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
     const dim3 grid((B + 1) / 2, c->N / TILE, c->L + c->K);
-    k_ks_mac_ext_bulk<DNUM, TILE><<<grid, TILE, smem, c->stream>>>(
+    k_ks_mac_ext_bulk<DNUM, TILE><<<grid, TILE + 32, smem, c->stream>>>(
         D, XP, pts, tt, c_lo, cnt, B, A, c->L, c->K, c->logN, c->d_mod, c->d_err);
 }
 
