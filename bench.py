@@ -1,7 +1,9 @@
 """Benchmark: the encrypted FFConv layer at N = 2^15 on one GB300 (or N replicas).
 
-One step = one encrypted FFConv layer (DP_SHIFT schedule: 24 hoisted rotations of each input,
-tap MACs, ConvPack restore) over a batch of B encrypted 1 x 28 x 28 images, RNS-BFV with
+One step = one encrypted FFConv layer (DP_SHIFT_EXT schedule: 24 hoisted rotations of each
+input key-switched and multiplied by the tap plaintexts in the extended basis, one ModDown per
+channel, ConvPack restore) over a batch of B encrypted 1 x 28 x 28 images (B = 64 by default,
+the batched size of the layer workload; B = 1 latencies are reported beside it), RNS-BFV with
 N = 2^15, 12 x 50-bit ciphertext primes, 3 x 60-bit special primes, key-switching digits of
 3 primes.  Inputs are seeded synthetic images (pixels uniform in [0, 255]) and weights
 (uniform in [-8, 8]) standing in for MNIST and trained weights.
@@ -32,7 +34,7 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--pack", default="dp_shift_ext", choices=["dp_shift", "dp_shift_ext", "dp_dot"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -90,6 +92,31 @@ def oracle_sample(n_steps=2, seed=0):
     return dt, len(steps), f"oracle hoisted rotation of 1 ciphertext by {len(steps)} steps at N=2^15, L=12, K=3"
 
 
+def copy_bandwidth(stream, nbytes=1 << 29):
+    """Host <-> device copy rate (GB/s) of one large pinned copy each way, on `stream`."""
+    import torch
+    dev = torch.empty(nbytes // 8, dtype=torch.int64, device="cuda")
+    host = torch.empty(nbytes // 8, dtype=torch.int64).pin_memory()
+    out = []
+    for h2d in (True, False):
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                (dev.copy_(host, non_blocking=True) if h2d else host.copy_(dev, non_blocking=True))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(3):
+                (dev.copy_(host, non_blocking=True) if h2d else host.copy_(dev, non_blocking=True))
+            b.record(stream)
+        torch.cuda.synchronize()
+        out.append(3 * nbytes / (a.elapsed_time(b) / 1e3) / 1e9)
+    return out[0], out[1]
+
+
+def workload_name(args):
+    return (f"FFConv layer 1x28x28 -> 5x5 s2 p1 (r=2) -> 1x1 (5 ch), {args.pack}, "
+            "N=2^15, 12x50-bit q, 3x60-bit p, alpha=3")
+
+
 def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
@@ -106,8 +133,10 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
-            "config": {"workload": "hoisted rotations of the FFConv layer input, N=2^15, L=12, K=3, alpha=3",
-                       "ring": "N=32768, 12x50-bit q, 3x60-bit p", "l2": "inputs larger than L2"},
+            "config": {"workload": workload_name(args), "batch_per_gpu": args.batch,
+                       "parallelism": f"replicas x{world} (rank 0 times the oracle)",
+                       "sample": "each step: the oracle's hoisted rotation of one layer input "
+                                 "(one ModUp, one key switch), the unit the metric counts"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": desc.replace("by 2 steps", "by 1 step") + f", {args.steps} samples"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -272,6 +301,7 @@ def run(args):
     e1.record(stream)
     torch.cuda.synchronize()
     ms_e2e = e0.elapsed_time(e1)
+    h2d_gbs, d2h_gbs = copy_bandwidth(stream)
 
     # the plain one-request-at-a-time form: the same layer on one image per call (outputs are
     # bit-identical to the batched call's; tests/test_gpu_layer.py checks it)
@@ -331,19 +361,22 @@ def run(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": f"FFConv layer 1x28x28 -> 5x5 s2 p1 (r=2) -> 1x1 (5 ch), {args.pack}, "
-                                   "N=2^15, 12x50-bit q, 3x60-bit p, alpha=3",
+            "config": {"workload": workload_name(args),
                        "batch_per_gpu": B, "layer_ms_per_batch": ms / args.steps,
                        "layer_ms_per_image": ms / args.steps / B, "hoisted_rotations_per_image": n_rot,
                        "parallelism": f"replicas x{world}",
-                       "l2": "inputs larger than L2 (keys 377 MB + ModUp digits per step)",
+                       "l2": "inputs larger than L2 (keys 755 MB + ModUp digits per step)",
                        "autotune": {"tap_tile_ms": {"128": tile_ms[0], "256": tile_ms[1]},
                                     "tap_tile": 128 if tile_ms[0] <= tile_ms[1] else 256,
                                     "ntt_log2_n1": tile_ms[3], "ntt_ms": tile_ms[2]}},
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": B * ct_bytes,
                     "d2h_bytes_per_step": B * shape.O_c * ct_bytes, "ms_per_step": ms_e2e / args.steps,
                     "note": "pinned host buffers; copies of neighbouring steps overlap the layer "
-                            "(two buffer sets, two copy streams)"},
+                            "(two buffer sets, two copy streams)",
+                    "copy_gbs": {"h2d": h2d_gbs, "d2h": d2h_gbs,
+                                 "d2h_ms_per_step": B * shape.O_c * ct_bytes / d2h_gbs / 1e6,
+                                 "note": "one 512 MiB pinned copy each way, untimed: the end-to-end "
+                                         "step is bound by max(layer, output copy)"}},
             "gpu_launches": launches, "clocks": clk, "roofline": roof,
             "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items() if v[1]},
             "batching": {"one_at_a_time_ms_per_image": ms_single,
@@ -402,7 +435,7 @@ def measured_peaks():
 # DRAM bytes (read + write) of one k_ks_mac_ext launch, from one ncu capture of the current
 # kernel version at the bench shape (profiles/k_ks_mac_ext_n15.md); cleared when the kernel
 # changes and until it is captured again.
-KS_MAC_EXT_TRAFFIC = {}
+KS_MAC_EXT_TRAFFIC = {64: 3415376896 + 990737152}
 
 
 # 64 x 64 -> 128-bit products per second of the GPU's integer multiplier: 152 SMs x 64 32-bit
