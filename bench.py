@@ -40,6 +40,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the short network runs reported under 'also'")
+    ap.add_argument("--serving-layers", action="store_true",
+                    help="serving loop over single FFConv layers (28 x 28 at N = 2^14, 3 x 32 x 32 "
+                         "at N = 2^15) instead of whole networks")
     ap.add_argument("--serving", action="store_true",
                     help="run the serving loop (mixed rings, Poisson arrivals) instead")
     ap.add_argument("--net", action="store_true",
@@ -479,7 +482,110 @@ def layer_algorithmic_bytes(B, O_c, n_rot):
 
 
 def run_serving(args):
-    """Serving loop: Poisson arrivals of mixed requests -- 60 % the 28 x 28 layer at N = 2^14
+    """Serving loop over whole networks: Poisson arrivals of mixed requests -- 60 % the 28 x 28
+    three-layer network at N = 2^14 (6 + 2 primes; FFConv layer, combine, x^2, FC 845 -> 100,
+    x^2, FC 100 -> 10), 40 % the 3 x 32 x 32 network at N = 2^15 (12 + 3 primes; 3 x 3
+    convolutions 3 -> 64 -> 64 -> 128 at rank 8, x^2 after each, pooled classifier to 10) --
+    with keys resident, footprint admission and continuous batching over two worker streams per
+    ring, against the plain form (one request per call, in arrival order, one stream)."""
+    import numpy as np
+    import torch
+
+    from paper_2102_03494_gb300 import serving, workloads
+
+    shape = workloads.MNIST_LAYER
+    n1 = shape.O_c * ((shape.I_h + 2 * shape.pad - shape.d) // shape.stride + 1) ** 2
+    rng = np.random.default_rng(21)
+    W1, W2 = workloads.weights(0, shape)
+    F1 = rng.integers(-8, 9, (NET_M1, n1))
+    F2 = rng.integers(-8, 9, (NET_M2, NET_M1))
+    net = serving.NetRing(serving.NetSpec(NET_LOG_N, NET_N_Q, NET_N_P, NET_ALPHA, shape.astuple(),
+                                          NET_M1, NET_M2),
+                          workers=2, W1=W1, W2=W2, F1=F1, F2=F2, sk_seed=1, key_seed=11,
+                          keep_results=False)
+    chans, rank = (64, 64, 128), 8
+    W1s, W2s, C = [], [], 3
+    for O in chans:
+        W1s.append(rng.integers(-8, 9, (rank, C, 3, 3)).astype(np.int32))
+        W2s.append(rng.integers(-8, 9, (O, rank)).astype(np.int32))
+        C = O
+    F = rng.integers(-8, 9, (10, C)).astype(np.int32)
+    deep = serving.DeepRing(serving.DeepSpec(LOG_N, N_Q, N_P, ALPHA, 3, 32, 32, chans, rank, 10),
+                            workers=2, W1s=W1s, W2s=W2s, F=F, sk_seed=2, key_seed=12,
+                            keep_results=False)
+    rings = {"n14_net3": net, "n15_deep": deep}
+    mix = {"n14_net3": 0.6, "n15_deep": 0.4}
+    max_batch = 8
+
+    def make_requests(rate, count, seed):
+        reqs = serving.poisson_arrivals(seed=seed, rate=rate, count=count, mix=mix)
+        for r in reqs:
+            g = np.random.default_rng(r.rid + 1000 * seed)
+            if r.ring == "n14_net3":
+                x = g.integers(0, 256, (shape.I_h, shape.I_w))
+                slots = np.zeros(1 << NET_LOG_N, dtype=np.int64)
+                slots[: x.size] = x.reshape(-1)
+                r.payload = net.encrypt(slots, 7000 + r.rid)
+            else:
+                x = g.integers(0, 256, (3, 32, 32))
+                slots = np.zeros(1 << LOG_N, dtype=np.int64)
+                for c in range(3):
+                    slots[c * 1024: c * 1024 + 1024] = x[c].reshape(-1)
+                r.payload = [deep.encrypt(slots, 7000 + r.rid)]
+        torch.cuda.synchronize()
+        return reqs
+
+    def release(reqs):
+        for r in reqs:
+            r.payload = r.result = None
+
+    # warm-up of every worker of every ring at the largest batch (scratch sizing, first launches)
+    warm = make_requests(1e9, 32, seed=99)
+    for name, ring in rings.items():
+        mine = [r for r in warm if r.ring == name][:max_batch]
+        for w in range(ring.workers):
+            ring.launch(w, mine)
+        ring.run_alone(mine[0].payload)
+    torch.cuda.synchronize()
+    release(warm)
+    out = {"metric": "serving: mixed-ring encrypted network requests, continuous batching",
+           "unit": "requests/s and ms", "mix": mix, "workers_per_ring": 2, "max_batch": max_batch,
+           "workload": {"n14_net3": "1x28x28 -> FFConv 5x5 s2 (r=2) -> 5 ch -> combine -> x^2 -> "
+                                    "FC 845->100 -> x^2 -> FC 100->10, N=2^14, 6+2 primes",
+                        "n15_deep": "3x32x32 -> 3x3 conv 64 -> x^2 -> 64 -> x^2 -> 128 -> x^2 -> "
+                                    "pooled FC 128->10, rank 8, N=2^15, 12+3 primes"},
+           "rates": []}
+    for rate in (20.0, 60.0, 120.0, 240.0):
+        count = int(max(60, min(rate * 3, 480)))
+        reqs = make_requests(rate, count, seed=int(rate))
+        sched = serving.Scheduler(rings, max_batch=max_batch, memory_budget=64 << 30,
+                                  clock=time.perf_counter)
+        done = sched.serve(reqs)
+        torch.cuda.synchronize()
+        release(reqs)
+        served = serving.latency_stats(done)
+        by_ring = {name: serving.latency_stats([r for r in done if r.ring == name]) for name in rings}
+        # the plain form: one request per call in arrival order on one stream
+        plain_reqs = make_requests(rate, count, seed=int(rate))
+        t_free, lat = 0.0, []
+        for r in plain_reqs:
+            t0 = time.perf_counter()
+            rings[r.ring].run_alone(r.payload)
+            dt = time.perf_counter() - t0
+            start = max(r.t_arrive, t_free)
+            t_free = start + dt
+            lat.append((t_free - r.t_arrive) * 1000.0)
+        span = t_free - plain_reqs[0].t_arrive
+        release(plain_reqs)
+        plain = {"requests": count, "p50_ms": float(np.percentile(lat, 50)),
+                 "p99_ms": float(np.percentile(lat, 99)), "requests_per_s": count / span}
+        out["rates"].append({"offered_per_s": rate, "served": served, "served_by_ring": by_ring,
+                             "plain": plain, "p99_factor": plain["p99_ms"] / served["p99_ms"]})
+    print(json.dumps(out))
+
+
+def run_serving_layers(args):
+    """Serving loop over single layers: Poisson arrivals of mixed requests -- 60 % the 28 x 28 layer at N = 2^14
     (6 + 2 primes), 40 % a 3 x 32 x 32 layer (3 x 3 stride 1, r = 8 -> 64 channels) at
     N = 2^15 (12 + 3 primes) -- continuously batched over two worker streams per ring,
     against the plain form (one request per call, in arrival order, one stream)."""
@@ -783,6 +889,9 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.serving_layers:
+        run_serving_layers(args)
         return
     if args.serving:
         run_serving(args)

@@ -1,7 +1,8 @@
-"""Serving loop: continuous batching of encrypted FFConv-layer requests on one GPU.
+"""Serving loop: continuous batching of encrypted inference requests on one GPU.
 
-Requests for layers on different rings (e.g. the 28 x 28 layer at N = 2^14 and a 3 x 32 x 32
-layer at N = 2^15) arrive over time.  The scheduler
+Requests for networks (or single FFConv layers) on different rings -- e.g. the 28 x 28
+three-layer network at N = 2^14 and the 3 x 32 x 32 network at N = 2^15 -- arrive over time.
+The scheduler
   * admits a waiting request when its device-memory footprint fits the budget (inputs,
     outputs and its share of scratch), freeing the footprint when its batch completes;
   * groups admitted requests of the same ring, oldest first, into batches of up to
@@ -12,7 +13,9 @@ layer at N = 2^15) arrive over time.  The scheduler
 Completion is detected with CUDA events; latency = completion - arrival.
 
 The scheduling logic (`Scheduler`) is plain host code that drives an executor interface, so
-it is tested with a fake executor on the CPU; `GpuRing` is the executor over libhe.
+it is tested with a fake executor on the CPU; the executors over libhe are `GpuRing` (one
+FFConv layer, optionally replayed as captured CUDA graphs), `NetRing` (the three-layer
+network) and `DeepRing` (the multi-ciphertext network).
 """
 from dataclasses import dataclass, field
 from typing import Callable, Dict, List, Optional
@@ -261,3 +264,132 @@ class GpuRing:
             ctx.he_ffconv_layer_planned(self.plans[0], [payload], self.lay, outs)
         self.streams[0].synchronize()
         return outs
+
+
+# ---------------------------------------------------------------- whole-network executors
+
+@dataclass
+class NetSpec:
+    """The three-layer network on one ring: FFConv layer (DP_SHIFT_EXT), channel combine, x^2,
+    fully connected to m1, x^2, fully connected to m2."""
+    log_n: int
+    n_q: int
+    n_p: int
+    alpha: int
+    shape: tuple                      # the layer's (I_c, I_h, I_w, d, stride, pad, r, O_c)
+    m1: int
+    m2: int
+
+
+@dataclass
+class DeepSpec:
+    """The multi-ciphertext network on one ring: 3 x 3 stride-1 convolutions C0 -> channels[0]
+    -> ... (each factorized at `rank`, 0 = unfactorized), x^2 after each, sum pooling folded
+    into the classifier to n_cls outputs."""
+    log_n: int
+    n_q: int
+    n_p: int
+    alpha: int
+    C0: int
+    H: int
+    W: int
+    channels: tuple
+    rank: int
+    n_cls: int
+
+
+class _NetWorkers:
+    """Workers of one ring serving whole networks: a library context and a CUDA stream each,
+    the Galois and relinearisation keys resident in every context, the weights fixed.  One
+    output ciphertext per request (the logits)."""
+
+    def __init__(self, log_n, n_q, n_p, alpha, workers, keep_results):
+        import torch
+        from . import he
+        self.workers = workers
+        self.keep_results = keep_results
+        self.streams = [torch.cuda.Stream() for _ in range(workers)]
+        self.ctx = [he.Context(log_n, n_q, n_p, alpha, stream=s) for s in self.streams]
+        self.N = 1 << log_n
+        self.ct_bytes = 2 * n_q * self.N * 8
+        self.ext_bytes = 2 * (n_q + n_p) * self.N * 8
+
+    def _keys(self, sk_seed, key_seed, steps):
+        self.sk = self.ctx[0].he_keygen_secret(sk_seed)
+        for c in self.ctx:
+            c.he_keygen_galois(self.sk, key_seed, steps)
+
+    def encrypt(self, slots, seed):
+        return self.ctx[0].he_encrypt(self.sk, slots, seed)
+
+    def _inputs(self, payload):
+        return payload if isinstance(payload, (list, tuple)) else [payload]
+
+    def launch(self, worker, requests):
+        import torch
+        ctx = self.ctx[worker]
+        with torch.cuda.stream(self.streams[worker]):
+            outs = [ctx.new_ct() for _ in requests]
+            self._call(ctx, [c for r in requests for c in self._inputs(r.payload)], outs)
+            ev = torch.cuda.Event()
+            ev.record(self.streams[worker])
+        return (ev, outs)
+
+    def done(self, handle):
+        return handle[0].query()
+
+    def results(self, handle, requests):
+        for i, r in enumerate(requests):
+            r.result = [handle[1][i]] if self.keep_results else None
+
+    def run_alone(self, payload):
+        """The plain form: one request, one call, waited for."""
+        import torch
+        ctx = self.ctx[0]
+        with torch.cuda.stream(self.streams[0]):
+            outs = [ctx.new_ct()]
+            self._call(ctx, self._inputs(payload), outs)
+        self.streams[0].synchronize()
+        return outs
+
+
+class NetRing(_NetWorkers):
+    def __init__(self, spec: NetSpec, workers: int, W1, W2, F1, F2, sk_seed: int, key_seed: int,
+                 keep_results: bool = True):
+        super().__init__(spec.log_n, spec.n_q, spec.n_p, spec.alpha, workers, keep_results)
+        self.spec = spec
+        self.W1, self.W2, self.F1, self.F2 = W1, W2, F1, F2
+        self.lay = self.ctx[0].layout(*spec.shape, pack="dp_shift_ext")
+        self.net = self.ctx[0].net(self.lay, spec.m1, spec.m2)
+        self._keys(sk_seed, key_seed, self.ctx[0].he_net_required_steps(self.net))
+
+    def footprint(self, req):
+        # input, output, the five channel outputs and the combined vector, plus the layer's
+        # extended-basis scratch share
+        return self.ct_bytes * (2 + self.spec.shape[7] + 2) + 8 * self.ext_bytes
+
+    def _call(self, ctx, cts, outs):
+        ctx.he_net_batch(cts, self.W1, self.W2, self.F1, self.F2, self.net, outs)
+
+
+class DeepRing(_NetWorkers):
+    def __init__(self, spec: DeepSpec, workers: int, W1s, W2s, F, sk_seed: int, key_seed: int,
+                 keep_results: bool = True):
+        super().__init__(spec.log_n, spec.n_q, spec.n_p, spec.alpha, workers, keep_results)
+        self.spec = spec
+        self.W1s, self.W2s, self.F = W1s, W2s, F
+        self.convs, C = [], spec.C0
+        for O in spec.channels:
+            self.convs.append(self.ctx[0].mc_conv(C, spec.H, spec.W, 3, spec.rank, O))
+            C = O
+        self.n_in = self.ctx[0].mc_cts(spec.C0, spec.H, spec.W)
+        self._keys(sk_seed, key_seed, self.ctx[0].he_deep_required_steps(self.convs, spec.n_cls))
+
+    def footprint(self, req):
+        # inputs, output, the widest tensor twice (in and out of a layer) and the layers'
+        # extended-basis scratch share
+        widest = max(self.ctx[0].mc_cts(c, self.spec.H, self.spec.W) for c in self.spec.channels)
+        return self.ct_bytes * (self.n_in + 1 + 2 * widest) + 16 * self.ext_bytes
+
+    def _call(self, ctx, cts, outs):
+        ctx.he_deep_batch(cts, self.convs, self.W1s, self.W2s, self.F, outs)
