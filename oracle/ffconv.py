@@ -31,6 +31,13 @@ ConvPack (Sec. 3.2, Fig. 2a).  Schedules of W1:
   cp_cp    (CP-HI2C-CP, Sec. 4.2 'ConvPack for W1', Fig. 5): the client packs the Im2Col
            columns of the input (one ciphertext per column, I[o, k] at slot o); W1 and W2 are
            both ConvPack scalar products and the layer needs no rotation.
+  dp_dp    (DP-DP, Table IX's DensePack-DensePack baseline): W1 exactly as dp_dot, then the
+           r channel ciphertexts are combined into one dense vector Y (channel c' rotated by
+           -c' S, so y1[c', o] sits at slot c' S + o) and W2 is a DensePack layer too: for every
+           output (c, o), Y times the plaintext holding W2[c, c'] at slot c' S + o, rotate-and-
+           sum with steps 1, 2, .., 2^(k2-1) where 2^k2 > (r - 1) S (slot o then holds the dot
+           product), and the one-hot mask of slot o gathers the O_c S products into the O_c
+           output ciphertexts (y2[c, oh, ow] at slot oh O_w + ow).
   dp_shift_ext (the same slots and plaintexts as dp_shift): the hoisted rotations stay in the
            extended basis Q u P, each as (u0 + P phi(c0), u1); the tap products are summed
            there (plaintexts lifted to Q u P) and divided by P once per channel (one ModDown
@@ -58,7 +65,7 @@ class Layout:
     pad: int
     r: int
     O_c: int
-    pack: str = "dp_shift"      # "dp_dot" | "dp_shift" | "dp_shift_ext" | "cp_cp"
+    pack: str = "dp_shift"      # "dp_dot" | "dp_shift" | "dp_shift_ext" | "cp_cp" | "dp_dp"
     modswitch: bool = False
 
     @property
@@ -125,14 +132,14 @@ def input_slots(x, lay: Layout, n: int):
     """Slot vector of the packed input image (row 0)."""
     v = np.zeros(n, dtype=np.int64)
     hw = lay.I_h * lay.I_w
-    block = hw if lay.pack == "dp_dot" else lay.B_c
+    block = hw if lay.pack in ("dp_dot", "dp_dp") else lay.B_c
     for ci in range(lay.I_c):
         v[ci * block: ci * block + hw] = np.asarray(x[ci]).reshape(-1)
     return v
 
 
 def output_slot(lay: Layout, oh: int, ow: int) -> int:
-    if lay.pack in ("dp_dot", "cp_cp"):
+    if lay.pack in ("dp_dot", "cp_cp", "dp_dp"):
         return oh * lay.O_w + ow
     return (lay.stride * oh) * lay.I_w + lay.stride * ow
 
@@ -143,9 +150,11 @@ def check_fits(lay: Layout, n: int):
         if lay.S > n:
             raise ValueError("cp_cp output positions must fit in N slots")
         return
-    if lay.pack == "dp_dot":
+    if lay.pack in ("dp_dot", "dp_dp"):
         if lay.I_c * lay.I_h * lay.I_w > n or lay.S > half:
             raise ValueError("dp_dot input must fit in N slots and its output in N/2")
+        if lay.pack == "dp_dp" and (lay.r * lay.S > half or lay.modswitch):
+            raise ValueError("dp_dp needs r S <= N/2 (one dense vector) and no modulus switch")
     else:
         span = lay.B_c * (1 << (lay.I_c - 1).bit_length())
         if span > half:
@@ -153,7 +162,7 @@ def check_fits(lay: Layout, n: int):
 
 
 def spans_both_rows(lay: Layout, n: int) -> bool:
-    return lay.pack == "dp_dot" and lay.I_c * lay.I_h * lay.I_w > n // 2
+    return lay.pack in ("dp_dot", "dp_dp") and lay.I_c * lay.I_h * lay.I_w > n // 2
 
 
 def _window_covers(lay: Layout, k: int) -> bool:
@@ -196,12 +205,29 @@ def dp_dot_steps(lay: Layout, n: int):
     return steps + ([bfv.ROW_SWAP] if spans_both_rows(lay, n) else [])
 
 
+def dp_dp_combine_steps(lay: Layout):
+    """Rotations moving channel c' of W1's output to slots c' S + o (c' = 1 .. r-1)."""
+    return [-c * lay.S for c in range(1, lay.r)]
+
+
+def dp_dp_sum_steps(lay: Layout):
+    """W2's rotate-and-sum: 1, 2, .., 2^(k2-1) with 2^k2 > (r - 1) S."""
+    k2 = ((lay.r - 1) * lay.S).bit_length()
+    return [1 << e for e in range(k2)]
+
+
 def required_steps(lay: Layout, n: int):
     """Rotation steps (slots) whose Galois keys the layer needs."""
     if lay.pack == "cp_cp":
         return []
     if lay.pack == "dp_dot":
         return dp_dot_steps(lay, n)
+    if lay.pack == "dp_dp":
+        out = []
+        for st in dp_dot_steps(lay, n) + dp_dp_combine_steps(lay) + dp_dp_sum_steps(lay):
+            if st not in out:
+                out.append(st)
+        return out
     steps = [dl for (_, _, dl) in lay.taps() if dl != 0]
     return steps + lay.channel_fold_steps()
 
@@ -232,6 +258,14 @@ def dp_shift_tap_slots(W1, lay: Layout, n: int, c: int, i: int, j: int):
                 w = lay.stride * ow + j - lay.pad
                 if 0 <= h < lay.I_h and 0 <= w < lay.I_w:
                     v[ci * lay.B_c + output_slot(lay, oh, ow)] = W1[c][ci][i][j]
+    return v
+
+
+def dp_dp_row_slots(W2, lay: Layout, n: int, c: int, o: int):
+    """Row (c, o) of W2 under DensePack: W2[c, c'] at slot c' S + o of the dense vector."""
+    v = np.zeros(n, dtype=np.int64)
+    for cp in range(lay.r):
+        v[cp * lay.S + o] = W2[c][cp]
     return v
 
 
@@ -318,7 +352,7 @@ def he_layer(prm, ct_in, W1, W2, lay: Layout, keys, ops: OpCount = None,
     n = prm.n
     half = n // 2
     cts_w1 = []
-    if lay.pack == "dp_dot":
+    if lay.pack in ("dp_dot", "dp_dp"):
         sum_steps = dp_dot_steps(lay, n)
         for c in range(lay.r):
             acc = None
@@ -381,17 +415,54 @@ def he_layer(prm, ct_in, W1, W2, lay: Layout, keys, ops: OpCount = None,
                 ops.rot += 1
                 ops.addcc += 1
             cts_w1.append(acc)
+    if lay.pack == "dp_dp":
+        return _w2_dense(prm, cts_w1, W2, lay, keys, ops)
     return _restore(prm, cts_w1, W2, lay, ops)
+
+
+def _w2_dense(prm, cts_w1, W2, lay: Layout, keys, ops: OpCount):
+    """W2 under DensePack (dp_dp): combine the channel ciphertexts into one dense vector, then
+    one dense vector-row product per output (c, o), gathered by one-hot masks."""
+    n = prm.n
+    Y = cts_w1[0]
+    for cp, st in zip(range(1, lay.r), dp_dp_combine_steps(lay)):
+        Y = bfv.add(prm, Y, bfv.rotate(prm, cts_w1[cp], st, keys))
+        ops.rot += 1
+        ops.addcc += 1
+    outs = []
+    for c in range(lay.O_c):
+        acc = None
+        for o in range(lay.S):
+            z = bfv.mul_plain(prm, Y, bfv.pt_rns(encode(dp_dp_row_slots(W2, lay, n, c, o), prm), prm))
+            ops.mulpc += 1
+            for st in dp_dp_sum_steps(lay):
+                z = bfv.add(prm, z, bfv.rotate(prm, z, st, keys))
+                ops.rot += 1
+                ops.addcc += 1
+            term = bfv.mul_plain(prm, z, bfv.pt_rns(encode(mask_slots(n, o), prm), prm))
+            ops.mulpc += 1
+            if acc is None:
+                acc = term
+            else:
+                acc = bfv.add(prm, acc, term)
+                ops.addcc += 1
+        outs.append(acc)
+    return outs
 
 
 def expected_ops(lay: Layout, n: int):
     """Operation counts of the schedules (Tables I-III for the paper's dp_dot form)."""
-    n_sum = len(dp_dot_steps(lay, n)) if lay.pack == "dp_dot" else 0
+    n_sum = len(dp_dot_steps(lay, n)) if lay.pack in ("dp_dot", "dp_dp") else 0
     r, S, O_c = lay.r, lay.S, lay.O_c
     restore_mul, restore_add = O_c * r, O_c * (r - 1)
     if lay.pack == "cp_cp":
         K = lay.d * lay.d * lay.I_c     # Table II, FFConv row: MulPC O'_c (K + O_c)
         return {"mulpc": r * (K + O_c), "addcc": r * (K - 1) + restore_add, "rot": 0}
+    if lay.pack == "dp_dp":
+        k2 = len(dp_dp_sum_steps(lay))
+        return {"mulpc": 2 * r * S + 2 * O_c * S,
+                "addcc": r * S * n_sum + r * (S - 1) + (r - 1) + O_c * S * k2 + O_c * (S - 1),
+                "rot": r * S * n_sum + (r - 1) + O_c * S * k2}
     if lay.pack == "dp_dot":
         return {"mulpc": 2 * r * S + restore_mul,
                 "addcc": r * S * n_sum + r * (S - 1) + restore_add,

@@ -74,7 +74,7 @@ def check_outputs(prm, s, lay, outs, y2):
         for oh in range(lay.O_h):
             for ow in range(lay.O_w):
                 want[ffconv.output_slot(lay, oh, ow)] = y2[c, oh, ow] % prm.t
-        if lay.I_c == 1 or lay.pack in ("dp_dot", "cp_cp"):
+        if lay.I_c == 1 or lay.pack in ("dp_dot", "cp_cp", "dp_dp"):
             assert (v == want).all()
         else:   # folded channels leave partial sums in the other channel blocks
             pos = [ffconv.output_slot(lay, oh, ow) for oh in range(lay.O_h) for ow in range(lay.O_w)]
@@ -82,7 +82,7 @@ def check_outputs(prm, s, lay, outs, y2):
         assert bfv.noise_bits(prm, s, ct)[1] > 10
 
 
-@pytest.mark.parametrize("pack", ["dp_dot", "dp_shift", "dp_shift_ext", "cp_cp"])
+@pytest.mark.parametrize("pack", ["dp_dot", "dp_shift", "dp_shift_ext", "cp_cp", "dp_dp"])
 @pytest.mark.parametrize("shape", [(1, 6, 6, 3, 2, 1, 2, 3), (2, 5, 5, 3, 1, 1, 2, 2), (3, 4, 4, 3, 2, 1, 2, 3)])
 def test_encrypted_layer_decrypts_to_plain_layer(pack, shape):
     prm = params.Params(log_n=7, n_q=3, n_p=1, alpha=1)
