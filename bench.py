@@ -263,12 +263,14 @@ def run(args):
     # inputs host -> device from pinned memory, runs the layer and copies every output
     # ciphertext device -> host.  Two buffer sets pipeline the steps: the H2D copy of step i + 1
     # and the D2H copy of step i - 1 run on copy streams while step i's layer runs.
-    h_in = [torch.empty((2, N_Q, N), dtype=torch.int64).pin_memory() for _ in range(B)]
+    # one pinned host block per direction and one device block per buffer set, so that each
+    # step's inputs and outputs move as one copy each
+    h_in = torch.empty((B, 2, N_Q, N), dtype=torch.int64).pin_memory()
     for h, c in zip(h_in, cts):
         h.copy_(c)
-    h_out = [torch.empty((2, N_Q, N), dtype=torch.int64).pin_memory() for _ in range(B * shape.O_c)]
-    sets = [(cts, outs), ([ctx.new_ct() for _ in range(B)],
-                          [ctx.new_ct() for _ in range(B * shape.O_c)])]
+    h_out = torch.empty((B * shape.O_c, 2, N_Q, N), dtype=torch.int64).pin_memory()
+    blocks = [(ctx.new_ct(count=B), ctx.new_ct(count=B * shape.O_c)) for _ in range(2)]
+    sets = [(list(bi), list(bo)) for bi, bo in blocks]
     up, down = torch.cuda.Stream(), torch.cuda.Stream()
     ev_in = [torch.cuda.Event(), torch.cuda.Event()]      # inputs of set k on the device
     ev_used = [torch.cuda.Event(), torch.cuda.Event()]    # layer on set k finished
@@ -281,8 +283,7 @@ def run(args):
         with torch.cuda.stream(up):
             up.wait_event(e0)
             up.wait_event(ev_used[k])                      # the layer two steps back is done
-            for h, c in zip(h_in, sets[k][0]):
-                c.copy_(h, non_blocking=True)
+            blocks[k][0].copy_(h_in, non_blocking=True)
             ev_in[k].record(up)
 
     load(0)
@@ -296,8 +297,7 @@ def run(args):
         ev_used[k].record(stream)
         with torch.cuda.stream(down):
             down.wait_event(ev_used[k])
-            for h, o in zip(h_out, sets[k][1]):
-                h.copy_(o, non_blocking=True)
+            h_out.copy_(blocks[k][1], non_blocking=True)
             ev_out[k].record(down)
     stream.wait_event(ev_out[0])
     stream.wait_event(ev_out[1])
@@ -374,8 +374,8 @@ def run(args):
                                     "ntt_log2_n1": tile_ms[3], "ntt_ms": tile_ms[2]}},
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": B * ct_bytes,
                     "d2h_bytes_per_step": B * shape.O_c * ct_bytes, "ms_per_step": ms_e2e / args.steps,
-                    "note": "pinned host buffers; copies of neighbouring steps overlap the layer "
-                            "(two buffer sets, two copy streams)",
+                    "note": "pinned host buffers, one copy per direction and step; copies of "
+                            "neighbouring steps overlap the layer (two buffer sets, two copy streams)",
                     "copy_gbs": {"h2d": h2d_gbs, "d2h": d2h_gbs,
                                  "d2h_ms_per_step": B * shape.O_c * ct_bytes / d2h_gbs / 1e6,
                                  "note": "one 512 MiB pinned copy each way, untimed: the end-to-end "
@@ -502,7 +502,7 @@ def run_serving(args):
     net = serving.NetRing(serving.NetSpec(NET_LOG_N, NET_N_Q, NET_N_P, NET_ALPHA, shape.astuple(),
                                           NET_M1, NET_M2),
                           workers=2, W1=W1, W2=W2, F1=F1, F2=F2, sk_seed=1, key_seed=11,
-                          keep_results=False)
+                          keep_results=False, graphs=8)
     chans, rank = (64, 64, 128), 8
     W1s, W2s, C = [], [], 3
     for O in chans:
@@ -512,7 +512,7 @@ def run_serving(args):
     F = rng.integers(-8, 9, (10, C)).astype(np.int32)
     deep = serving.DeepRing(serving.DeepSpec(LOG_N, N_Q, N_P, ALPHA, 3, 32, 32, chans, rank, 10),
                             workers=2, W1s=W1s, W2s=W2s, F=F, sk_seed=2, key_seed=12,
-                            keep_results=False)
+                            keep_results=False, graphs=8)
     rings = {"n14_net3": net, "n15_deep": deep}
     mix = {"n14_net3": 0.6, "n15_deep": 0.4}
     max_batch = 8
@@ -539,32 +539,44 @@ def run_serving(args):
         for r in reqs:
             r.payload = r.result = None
 
-    # warm-up of every worker of every ring at the largest batch (scratch sizing, first launches)
+    # warm-up of every worker of every ring at the largest batch, both forms (the graphs were
+    # recorded when the rings were built)
     warm = make_requests(1e9, 32, seed=99)
     for name, ring in rings.items():
         mine = [r for r in warm if r.ring == name][:max_batch]
-        for w in range(ring.workers):
-            ring.launch(w, mine)
+        for use in (False, True):
+            ring.use_graphs = use
+            for w in range(ring.workers):
+                ring.launch(w, mine)
         ring.run_alone(mine[0].payload)
     torch.cuda.synchronize()
     release(warm)
-    out = {"metric": "serving: mixed-ring encrypted network requests, continuous batching",
-           "unit": "requests/s and ms", "mix": mix, "workers_per_ring": 2, "max_batch": max_batch,
-           "workload": {"n14_net3": "1x28x28 -> FFConv 5x5 s2 (r=2) -> 5 ch -> combine -> x^2 -> "
-                                    "FC 845->100 -> x^2 -> FC 100->10, N=2^14, 6+2 primes",
-                        "n15_deep": "3x32x32 -> 3x3 conv 64 -> x^2 -> 64 -> x^2 -> 128 -> x^2 -> "
-                                    "pooled FC 128->10, rank 8, N=2^15, 12+3 primes"},
-           "rates": []}
-    for rate in (20.0, 60.0, 120.0, 240.0):
-        count = int(max(60, min(rate * 3, 480)))
+
+    def serve(rate, count, graphs):
+        for ring in rings.values():
+            ring.use_graphs = graphs
         reqs = make_requests(rate, count, seed=int(rate))
         sched = serving.Scheduler(rings, max_batch=max_batch, memory_budget=64 << 30,
                                   clock=time.perf_counter)
         done = sched.serve(reqs)
         torch.cuda.synchronize()
         release(reqs)
-        served = serving.latency_stats(done)
-        by_ring = {name: serving.latency_stats([r for r in done if r.ring == name]) for name in rings}
+        return (serving.latency_stats(done),
+                {name: serving.latency_stats([r for r in done if r.ring == name]) for name in rings})
+
+    out = {"metric": "serving: mixed-ring encrypted network requests, continuous batching",
+           "unit": "requests/s and ms", "mix": mix, "workers_per_ring": 2, "max_batch": max_batch,
+           "workload": {"n14_net3": "1x28x28 -> FFConv 5x5 s2 (r=2) -> 5 ch -> combine -> x^2 -> "
+                                    "FC 845->100 -> x^2 -> FC 100->10, N=2^14, 6+2 primes",
+                        "n15_deep": "3x32x32 -> 3x3 conv 64 -> x^2 -> 64 -> x^2 -> 128 -> x^2 -> "
+                                    "pooled FC 128->10, rank 8, N=2^15, 12+3 primes"},
+           "served": "batches replayed as recorded CUDA graphs (one per worker and batch size)",
+           "served_calls": "the same scheduler, batches run as library calls",
+           "rates": []}
+    for rate in (20.0, 60.0, 120.0, 240.0):
+        count = int(max(60, min(rate * 3, 480)))
+        served_calls, _ = serve(rate, count, False)
+        served, by_ring = serve(rate, count, True)
         # the plain form: one request per call in arrival order on one stream
         plain_reqs = make_requests(rate, count, seed=int(rate))
         t_free, lat = 0.0, []
@@ -580,7 +592,8 @@ def run_serving(args):
         plain = {"requests": count, "p50_ms": float(np.percentile(lat, 50)),
                  "p99_ms": float(np.percentile(lat, 99)), "requests_per_s": count / span}
         out["rates"].append({"offered_per_s": rate, "served": served, "served_by_ring": by_ring,
-                             "plain": plain, "p99_factor": plain["p99_ms"] / served["p99_ms"]})
+                             "served_calls": served_calls, "plain": plain,
+                             "p99_factor": plain["p99_ms"] / served["p99_ms"]})
     print(json.dumps(out))
 
 

@@ -244,20 +244,33 @@ int he_ffconv_plan(he_ctx* ctx, const int32_t* lowrank_w, const int32_t* restore
                    const he_layout* layout, int32_t* plan_out);
 int he_ffconv_layer_planned(he_ctx* ctx, int32_t plan, const he_ct* ct_in, int B, he_ct* ct_out);
 int he_ffconv_plan_free(he_ctx* ctx, int32_t plan);
-/* Captured layers.  he_ffconv_graph_create runs he_ffconv_layer_planned(plan, ct_in, B,
- * ct_out) once on the context stream (so ct_out holds its result on return), then records
- * the same call, on these exact buffers, into a CUDA graph and returns a graph id.
- * he_graph_launch replays it on the context stream: one submission for the layer's kernels
- * and copies; it reads whatever ct_in holds at that point and overwrites ct_out.  The caller
- * keeps ct_in and ct_out allocated while the graph lives.  Scratch: share_scratch = 0 gives
- * the graph a scratch area of its own; 1 records it on the context's scratch (no extra
- * memory; safe because all of a context's work runs in order on its stream), valid until a
- * later call needs more scratch than the context holds and reallocates it -- capture the
- * largest batch first.  The resident keys and the plan are used by reference: new key
- * material loaded for the same steps is picked up, while a launch after the plan was freed,
- * a key was dropped or the shared scratch was reallocated fails with HE_EINVAL (recreate the
- * graph).  he_graph_free releases it (after the stream drains).  HE_EINVAL for unknown ids;
- * capture errors as HE_ECUDA. */
+/* Recorded call sequences (CUDA graphs).  he_graph_begin starts recording on this context:
+ * the library calls that follow and only enqueue device work (rotations, products, layers,
+ * networks: everything except the entry points below) run their host code but their kernels
+ * and copies are recorded instead of executed, until he_graph_end returns the recording as a
+ * graph id.  he_graph_launch replays a graph on the context stream with one submission; each
+ * replay reads the device buffers the recorded calls read (whatever they hold then) and
+ * writes the ones they wrote.  The caller keeps those buffers allocated while the graph lives.
+ * Rules: the recorded calls must not need more scratch than the context holds, so run the
+ * same calls once before recording (a call that would grow the scratch or the network buffer
+ * fails with HE_EINVAL while recording); he_keygen_*, he_load_keys, he_export_galois,
+ * he_encrypt, he_decrypt, he_encode, he_autotune, he_probe_int_mac, he_ffconv_plan(_free),
+ * he_phase_times, he_set_stream, he_ffconv_graph_create, he_graph_launch and he_graph_free
+ * refuse to run while recording (HE_EINVAL).
+ * Scratch: share_scratch = 1 records on the context's scratch (no extra memory; safe because
+ * all of a context's work runs in order on its stream), valid until a later call reallocates
+ * it; 0 gives the graph a scratch area of its own (of the context's current size).  The
+ * resident keys, layer plans and network buffer are used by reference: new key material for
+ * the same steps is picked up, while a launch after a used plan was freed, a key was dropped,
+ * or the shared scratch or network buffer was reallocated fails with HE_EINVAL (record
+ * again).  If any call fails while recording (refused ones included), he_graph_end discards
+ * the recording and returns that call's error code.  he_graph_free releases a graph (after
+ * the stream drains). */
+int he_graph_begin(he_ctx* ctx, int share_scratch);
+int he_graph_end(he_ctx* ctx, int32_t* graph_out);
+/* A planned layer recorded in one call: he_ffconv_layer_planned(plan, ct_in, B, ct_out) runs
+ * once (ct_out holds its result on return; for share_scratch = 0 it sizes a scratch area the
+ * graph keeps), then is recorded on these exact buffers. */
 int he_ffconv_graph_create(he_ctx* ctx, int32_t plan, const he_ct* ct_in, int B, he_ct* ct_out,
                            int share_scratch, int32_t* graph_out);
 int he_graph_launch(he_ctx* ctx, int32_t graph);

@@ -217,7 +217,12 @@ uint64_t he_stream_state(uint64_t seed, uint64_t stream) { return h_mix64(seed ^
 // ------------------------------------------------------------------ context plumbing
 
 int he_fail(he_ctx* ctx, int code, const std::string& msg) {
-    if (ctx) ctx->err = msg;
+    if (ctx) {
+        ctx->err = msg;
+        // any failure while recording spoils the recording (a call may have recorded part of
+        // its work before failing): he_graph_end then discards it
+        if (ctx->rec && !ctx->rec->failed) ctx->rec->failed = code;
+    }
     return code;
 }
 
@@ -240,9 +245,15 @@ int he_launch_check(he_ctx* ctx, const char* what) {
     return HE_OK;
 }
 
+static int refuse_growth(he_ctx* ctx) {
+    return he_fail(ctx, HE_EINVAL, "a recorded call needs more scratch than the context holds: "
+                                   "run the same calls once before he_graph_begin");
+}
+
 int arena_reserve(he_ctx* ctx, size_t n_u64) {
     size_t bytes = n_u64 * 8 + 4096;
     if (bytes <= ctx->arena.cap) return HE_OK;
+    if (ctx->rec) return refuse_growth(ctx);
     if (ctx->arena.base) {
         cudaStreamSynchronize(ctx->stream);
         cudaFree(ctx->arena.base);
@@ -259,6 +270,25 @@ int arena_reserve(he_ctx* ctx, size_t n_u64) {
     return HE_OK;
 }
 
+int net_reserve(he_ctx* ctx, size_t n_u64) {
+    const size_t bytes = n_u64 * 8 + 4096;
+    if (bytes <= ctx->net.cap) return HE_OK;
+    if (ctx->rec) return refuse_growth(ctx);
+    if (ctx->net.base) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->net.base);
+        ctx->net.base = nullptr;
+        ctx->net.cap = 0;
+    }
+    if (cudaMalloc(&ctx->net.base, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return he_fail(ctx, HE_ENOMEM, "network buffer allocation failed");
+    }
+    ctx->net.cap = bytes;
+    ++ctx->net_epoch;
+    return HE_OK;
+}
+
 void arena_reset(he_ctx* ctx) { ctx->arena.used = 0; }
 
 uint64_t* arena_take(he_ctx* ctx, size_t n_u64) {
@@ -272,13 +302,13 @@ uint64_t* arena_take(he_ctx* ctx, size_t n_u64) {
 // Small host->device uploads go through a ring of pinned staging slots so that they stay
 // asynchronous; a slot is reused only after the copy that last read it has executed.
 const void* upload_small(he_ctx* ctx, const void* src, size_t bytes) {
-    if (ctx->capture_allocs) {                   // graph capture: a buffer the graph owns
+    if (ctx->rec) {                              // recording a graph: a buffer the graph owns
         void* d = nullptr;
         if (cudaMalloc(&d, bytes ? bytes : 8) != cudaSuccess) {
             cudaGetLastError();
             return nullptr;
         }
-        ctx->capture_allocs->push_back(d);
+        ctx->rec->g.allocs.push_back(d);
         if (bytes && cudaMemcpy(d, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return nullptr;
         return d;
     }
@@ -294,6 +324,27 @@ const void* upload_small(he_ctx* ctx, const void* src, size_t bytes) {
         return nullptr;
     cudaEventRecord(st.ev[slot], ctx->stream);
     return d;
+}
+
+// Host -> device copy of call arguments into device memory the call owns (scratch): an
+// ordinary asynchronous copy, or, while a graph is recorded, a copy into a device buffer the
+// graph owns plus a recorded device-to-device copy (a replay must not read host memory that
+// belonged to the recorded call).
+int upload_host(he_ctx* ctx, void* dst, const void* src, size_t bytes) {
+    if (!bytes) return HE_OK;
+    if (ctx->rec) {
+        void* d = nullptr;
+        if (cudaMalloc(&d, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return he_fail(ctx, HE_ENOMEM, "table allocation while recording failed");
+        }
+        ctx->rec->g.allocs.push_back(d);
+        HE_CHECK_CUDA(ctx, cudaMemcpy(d, src, bytes, cudaMemcpyHostToDevice));
+        HE_CHECK_CUDA(ctx, cudaMemcpyAsync(dst, d, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+        return HE_OK;
+    }
+    HE_CHECK_CUDA(ctx, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    return HE_OK;
 }
 
 uint32_t galois_elt(const he_ctx* ctx, int32_t step) {
@@ -322,6 +373,7 @@ static int upload_vec(he_ctx* ctx, T** dptr, const std::vector<T>& v) {
 
 static void free_ctx(he_ctx* c) {
     if (!c) return;
+    recording_abort(c);
     if (c->stream || true) cudaStreamSynchronize(c->stream);
     void* ptrs[] = {c->d_mod, c->d_tw_fwd, c->d_tw_inv, c->d_slot_pos, c->d_cdt,
                     c->d_modup_inv, c->d_modup_c, c->d_md_inv, c->d_md_c, c->d_md_pinv,
@@ -502,6 +554,7 @@ extern "C" const char* he_last_error(const he_ctx* ctx) { return ctx ? ctx->err.
 
 extern "C" int he_set_stream(he_ctx* ctx, void* stream) {
     if (!ctx) return HE_EINVAL;
+    HE_NOT_RECORDING(ctx, "he_set_stream");
     ctx->stream = (cudaStream_t)stream;
     return HE_OK;
 }
@@ -555,6 +608,7 @@ extern "C" int he_set_phase_timing(he_ctx* ctx, int enable) {
 
 extern "C" int he_phase_times(he_ctx* ctx, double* ms_out, uint64_t* calls_out) {
     if (!ctx) return HE_EINVAL;
+    HE_NOT_RECORDING(ctx, "he_phase_times");
     int rc = check_device_error(ctx);
     if (rc) return rc;
     for (auto& sp : ctx->spans) {
@@ -632,6 +686,7 @@ void encode_device(he_ctx* ctx, const int64_t* d_slots, int items, uint64_t* tmp
 
 extern "C" int he_encode(he_ctx* ctx, const int64_t* slots, uint64_t* pt_out) {
     if (!ctx || !slots || !pt_out) return HE_EINVAL;
+    HE_NOT_RECORDING(ctx, "he_encode");
     if (!ctx->batching) return he_fail(ctx, HE_EINVAL, "he_encode: t is not 1 mod 2N");
     const size_t N = ctx->N;
     int rc = arena_reserve(ctx, 2 * N);
@@ -662,6 +717,7 @@ static void secret_to_device(he_ctx* ctx, const int64_t* d_sk, int rows, uint64_
 
 extern "C" int he_keygen_secret(he_ctx* ctx, uint64_t seed, int64_t* sk_out) {
     if (!ctx || !sk_out) return HE_EINVAL;
+    HE_NOT_RECORDING(ctx, "he_keygen_secret");
     int rc = arena_reserve(ctx, ctx->N);
     if (rc) return rc;
     arena_reset(ctx);
@@ -676,6 +732,7 @@ extern "C" int he_keygen_secret(he_ctx* ctx, uint64_t seed, int64_t* sk_out) {
 extern "C" int he_encrypt(he_ctx* ctx, const int64_t* sk, const int64_t* slots, uint64_t seed,
                           he_ct* out) {
     if (!ctx || !sk || !slots) return HE_EINVAL;
+    HE_NOT_RECORDING(ctx, "he_encrypt");
     int rc = check_ct(ctx, out, ctx->L, -1, "he_encrypt");
     if (rc) return rc;
     if (!ctx->batching) return he_fail(ctx, HE_EINVAL, "he_encrypt: t is not 1 mod 2N");
@@ -723,6 +780,7 @@ extern "C" int he_encrypt(he_ctx* ctx, const int64_t* sk, const int64_t* slots, 
 
 extern "C" int he_decrypt(he_ctx* ctx, const int64_t* sk, const he_ct* ct, int64_t* slots_out) {
     if (!ctx || !sk || !slots_out) return HE_EINVAL;
+    HE_NOT_RECORDING(ctx, "he_decrypt");
     int rc = check_ct(ctx, ct, 0, -1, "he_decrypt");
     if (rc) return rc;
     if (!ctx->batching) return he_fail(ctx, HE_EINVAL, "he_decrypt: t is not 1 mod 2N");
@@ -778,6 +836,7 @@ extern "C" int he_decrypt(he_ctx* ctx, const int64_t* sk, const he_ct* ct, int64
 extern "C" int he_keygen_galois(he_ctx* ctx, const int64_t* sk, uint64_t seed,
                                 const int32_t* steps, int n_steps) {
     if (!ctx || !sk || (n_steps > 0 && !steps) || n_steps < 0) return HE_EINVAL;
+    HE_NOT_RECORDING(ctx, "he_keygen_galois");
     const size_t N = ctx->N, LK = ctx->L + ctx->K;
     int rc = arena_reserve(ctx, 2 * N + 4 * LK * N);
     if (rc) return rc;

@@ -202,9 +202,8 @@ extern "C" int he_mc_conv_batch(he_ctx* ctx, const he_ct* in, int B, const int32
     k_mont_ones<<<dim3((unsigned)((N + 255) / 256), LK), 256, 0, ctx->stream>>>(ones, LK, m.g,
                                                                             ctx->logN, ctx->d_mod);
 
-    HE_CHECK_CUDA(ctx, cudaMemcpyAsync(d_w1, lowrank_w, w1n * 4, cudaMemcpyHostToDevice, ctx->stream));
-    if (w2n)
-        HE_CHECK_CUDA(ctx, cudaMemcpyAsync(d_w2, restore_w, w2n * 4, cudaMemcpyHostToDevice, ctx->stream));
+    if ((rc = upload_host(ctx, d_w1, lowrank_w, w1n * 4))) return rc;
+    if (w2n && (rc = upload_host(ctx, d_w2, restore_w, w2n * 4))) return rc;
     for (size_t i = 0; i < items; ++i)
         HE_CHECK_CUDA(ctx, cudaMemcpyAsync(X + i * ct, in[i].data, ct * 8, cudaMemcpyDeviceToDevice,
                                            ctx->stream));
@@ -424,19 +423,7 @@ extern "C" int he_deep_batch(he_ctx* ctx, const he_ct* in, int B, const he_mc_co
     for (auto& m : gm) widest = std::max(widest, m.n_out);
     // two ping-pong sets of activations in the context's network buffer
     const size_t set = (size_t)B * widest * ct;
-    if (ctx->net.cap < (2 * set) * 8 + 4096) {
-        if (ctx->net.base) {
-            cudaStreamSynchronize(ctx->stream);
-            cudaFree(ctx->net.base);
-            ctx->net.base = nullptr;
-            ctx->net.cap = 0;
-        }
-        if (cudaMalloc(&ctx->net.base, 2 * set * 8 + 4096) != cudaSuccess) {
-            cudaGetLastError();
-            return he_fail(ctx, HE_ENOMEM, "he_deep: activation buffer");
-        }
-        ctx->net.cap = 2 * set * 8 + 4096;
-    }
+    if ((rc = net_reserve(ctx, 2 * set))) return rc;
     uint64_t* bufs[2] = {(uint64_t*)ctx->net.base, (uint64_t*)ctx->net.base + set};
     auto cts_at = [&](uint64_t* p, int n) {
         std::vector<he_ct> v(n);

@@ -43,6 +43,7 @@ int he_key_for_generation(he_ctx* ctx, uint32_t g, uint64_t** dev) { return key_
 
 extern "C" int he_export_galois(he_ctx* ctx, int32_t step, uint64_t* blob_out) {
     if (!ctx || !blob_out) return HE_EINVAL;
+    HE_NOT_RECORDING(ctx, "he_export_galois");
     const uint64_t* key = nullptr;
     int rc = he_get_key(ctx, galois_elt(ctx, step), &key);
     if (rc) return rc;
@@ -61,6 +62,7 @@ extern "C" int he_export_galois(he_ctx* ctx, int32_t step, uint64_t* blob_out) {
 
 extern "C" int he_load_keys(he_ctx* ctx, const uint64_t* blob, const int32_t* steps, int n_steps) {
     if (!ctx || n_steps < 0 || (n_steps > 0 && (!blob || !steps))) return HE_EINVAL;
+    HE_NOT_RECORDING(ctx, "he_load_keys");
     const size_t LK = ctx->L + ctx->K, per = (size_t)ctx->dnum * 2 * LK * ctx->N;
     int rc = arena_reserve(ctx, 64);
     if (rc) return rc;

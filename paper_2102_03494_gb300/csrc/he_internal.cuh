@@ -189,22 +189,34 @@ struct he_ctx {
     int32_t next_plan = 1;
     uint64_t keys_epoch = 0;            // bumped whenever a resident key is dropped
     uint64_t arena_epoch = 0;           // bumped whenever the scratch arena is reallocated
-    struct LayerGraph {                 // he_ffconv_graph_create: a captured planned layer
+    uint64_t net_epoch = 0;             // bumped whenever the network buffer is reallocated
+    struct LayerGraph {                 // a recorded sequence of library calls (graph.cu)
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
         Arena arena;                    // the graph's own scratch (empty when shared)
         bool shared = false;            // recorded on the context's scratch
         uint64_t arena_epoch = 0;       // ... at this generation of it
-        std::vector<void*> allocs;      // small tables uploaded while capturing
-        int32_t plan = 0;
+        uint64_t net_epoch = 0;         // network buffer generation at recording
         uint64_t keys_epoch = 0;
+        std::vector<void*> allocs;      // small tables uploaded while recording
+        std::vector<int32_t> plans;     // layer plans the recorded calls use
         uint64_t launches = 0, ops[4] = {0, 0, 0, 0};   // per replay
     };
     std::map<int32_t, LayerGraph> graphs;
     int32_t next_graph = 1;
-    // While a graph is captured, small uploads go to device buffers listed here (owned by
-    // the graph) instead of the staging ring, whose slots are reused.
-    std::vector<void*>* capture_allocs = nullptr;
+    // While recording (he_graph_begin .. he_graph_end): the graph being built, the user's
+    // stream and scratch to restore, and the counters to roll back.  Small uploads then go to
+    // device buffers the graph owns instead of the reused staging ring, and the scratch and
+    // network buffers refuse to grow.
+    struct Recording {
+        LayerGraph g;
+        cudaStream_t user_stream = nullptr, cs = nullptr;
+        Arena saved;
+        bool timing = false;
+        int failed = 0;                 // first error code of a call made while recording
+        uint64_t launches0 = 0, ops0[4] = {0, 0, 0, 0};
+    };
+    Recording* rec = nullptr;
     Staging staging;
     uint64_t ops[4] = {0, 0, 0, 0};     // MulPC, AddCC, Rot, KeySwitch
     uint64_t launches = 0;              // kernels launched by this context
@@ -230,6 +242,14 @@ struct he_ctx {
     } while (0)
 
 int he_fail(he_ctx* ctx, int code, const std::string& msg);
+// Entry points that synchronise, return host data or change resident state refuse to run
+// while a graph is being recorded.
+#define HE_NOT_RECORDING(ctx, name)                                                    \
+    do {                                                                               \
+        if ((ctx)->rec) return he_fail((ctx), HE_EINVAL, name ": not while recording a graph"); \
+    } while (0)
+// Ends and discards a recording in progress (context teardown).
+void recording_abort(he_ctx* ctx);
 // Synchronise the stream and report HE_ETIMEOUT if a kernel's bounded wait ran out.
 int check_device_error(he_ctx* ctx);
 int he_launch_check(he_ctx* ctx, const char* what);
@@ -237,6 +257,8 @@ int he_launch_check(he_ctx* ctx, const char* what);
 uint64_t* arena_take(he_ctx* ctx, size_t n_u64);
 void arena_reset(he_ctx* ctx);
 int arena_reserve(he_ctx* ctx, size_t n_u64);
+// The context's buffer for a network's activations (grow-only, like the arena).
+int net_reserve(he_ctx* ctx, size_t n_u64);
 
 uint32_t galois_elt(const he_ctx* ctx, int32_t step);
 // Phase timing: phase_begin/phase_end bracket work of one phase (HE_PHASE_*) with events on
@@ -244,6 +266,7 @@ uint32_t galois_elt(const he_ctx* ctx, int32_t step);
 void phase_begin(he_ctx* ctx, int phase);
 void phase_end(he_ctx* ctx);
 const void* upload_small(he_ctx* ctx, const void* src, size_t bytes);
+int upload_host(he_ctx* ctx, void* dst, const void* src, size_t bytes);
 int check_ct(he_ctx* ctx, const he_ct* ct, int need_limbs, int need_domain, const char* what);
 // Slot values (items x N int64, device) -> plaintexts [items][rows][N]: centred lift modulo
 // the first `rows` moduli (L for Q, L + K for Q u P), NTT domain, Montgomery form if mont.

@@ -568,6 +568,7 @@ extern "C" int he_ffconv_layer_batch(he_ctx* ctx, const he_ct* ct_in, int B,
 extern "C" int he_ffconv_plan(he_ctx* ctx, const int32_t* lowrank_w, const int32_t* restore_w,
                               const he_layout* layout, int32_t* plan_out) {
     if (!ctx) return HE_EINVAL;
+    HE_NOT_RECORDING(ctx, "he_ffconv_plan");
     if (!lowrank_w || !restore_w || !layout || !plan_out)
         return he_fail(ctx, HE_EINVAL, "he_ffconv_plan: null argument");
     LayoutInfo li;
@@ -613,11 +614,13 @@ extern "C" int he_ffconv_layer_planned(he_ctx* ctx, int32_t plan, const he_ct* c
     auto it = ctx->plans.find(plan);
     if (it == ctx->plans.end()) return he_fail(ctx, HE_EINVAL, "he_ffconv_layer_planned: no such plan");
     const he_ctx::LayerPlan& pl = it->second;
+    if (ctx->rec) ctx->rec->g.plans.push_back(plan);     // a replay needs the plan alive
     return layer_impl(ctx, ct_in, B, pl.w1.data(), pl.w2.data(), &pl.layout, ct_out, pl.pts);
 }
 
 extern "C" int he_ffconv_plan_free(he_ctx* ctx, int32_t plan) {
     if (!ctx) return HE_EINVAL;
+    HE_NOT_RECORDING(ctx, "he_ffconv_plan_free");
     auto it = ctx->plans.find(plan);
     if (it == ctx->plans.end()) return he_fail(ctx, HE_EINVAL, "he_ffconv_plan_free: no such plan");
     cudaStreamSynchronize(ctx->stream);

@@ -53,23 +53,6 @@ int next_pow2(int x) {
     return p;
 }
 
-int net_reserve(he_ctx* ctx, size_t n_u64) {
-    const size_t bytes = n_u64 * 8 + 4096;
-    if (bytes <= ctx->net.cap) return HE_OK;
-    if (ctx->net.base) {
-        cudaStreamSynchronize(ctx->stream);
-        cudaFree(ctx->net.base);
-        ctx->net.base = nullptr;
-        ctx->net.cap = 0;
-    }
-    if (cudaMalloc(&ctx->net.base, bytes) != cudaSuccess) {
-        cudaGetLastError();
-        return he_fail(ctx, HE_ENOMEM, "network buffer allocation failed");
-    }
-    ctx->net.cap = bytes;
-    return HE_OK;
-}
-
 struct ConvGeom {
     int O_h, O_w, S, blk;
     std::vector<int32_t> slot;   // output slot of (oh, ow) in the layer's own layout
@@ -183,9 +166,8 @@ static int fc_core(he_ctx* ctx, const he_ct* in, int B, int n_ct, const int32_t*
 
     // diagonal plaintexts, lifted to Q u P in Montgomery form
     phase_begin(ctx, HE_PHASE_ENCODE);
-    HE_CHECK_CUDA(ctx, cudaMemcpyAsync(d_w, weights, wn * 4, cudaMemcpyHostToDevice, ctx->stream));
-    HE_CHECK_CUDA(ctx, cudaMemcpyAsync(d_inv, inv.data(), inv.size() * 4, cudaMemcpyHostToDevice,
-                                       ctx->stream));
+    if ((rc = upload_host(ctx, d_w, weights, wn * 4))) return rc;
+    if ((rc = upload_host(ctx, d_inv, inv.data(), inv.size() * 4))) return rc;
     ++ctx->launches;
     k_fc_diag_slots<<<dim3((unsigned)((N + 255) / 256), T), 256, 0, ctx->stream>>>(
         d_w, d_inv, n_out, n_feat, M, period, ctx->logN, slots);

@@ -70,6 +70,7 @@ __global__ void __launch_bounds__(256) k_probe_cols(const uint64_t* __restrict__
 
 extern "C" int he_probe_int_mac(he_ctx* ctx, double* out) {
     if (!ctx || !out) return HE_EINVAL;
+    HE_NOT_RECORDING(ctx, "he_probe_int_mac");
     int sms = 0, dev = 0;
     HE_CHECK_CUDA(ctx, cudaGetDevice(&dev));
     HE_CHECK_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

@@ -400,6 +400,7 @@ static int tune_ntt(he_ctx* ctx, int batch, double* best_ms) {
 
 extern "C" int he_autotune(he_ctx* ctx, int batch, int force_tile, double* ms_out) {
     if (!ctx) return HE_EINVAL;
+    HE_NOT_RECORDING(ctx, "he_autotune");
     if (force_tile) {
         if (force_tile != 128 && force_tile != 256)
             return he_fail(ctx, HE_EINVAL, "he_autotune: tile must be 128 or 256");

@@ -113,6 +113,8 @@ _SIGS = {
     "he_ffconv_graph_create": ([_P, ctypes.c_int32, _CTP, ctypes.c_int, _CTP, ctypes.c_int, _I32P],
                                ctypes.c_int),
     "he_graph_launch": ([_P, ctypes.c_int32], ctypes.c_int),
+    "he_graph_begin": ([_P, ctypes.c_int], ctypes.c_int),
+    "he_graph_end": ([_P, _I32P], ctypes.c_int),
     "he_graph_free": ([_P, ctypes.c_int32], ctypes.c_int),
     "he_ntt": ([_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
 }
@@ -554,6 +556,18 @@ class Context:
                  "he_ffconv_graph_create")
         self._graph_refs[int(gid[0])] = (list(cts_in), list(outs))
         return int(gid[0]), outs
+
+    def he_graph_begin(self, share_scratch=False):
+        """Start recording the calls that follow on this context (see he_graph_end)."""
+        self._ck(lib().he_graph_begin(self.h, int(bool(share_scratch))), "he_graph_begin")
+
+    def he_graph_end(self, keep=()):
+        """Finish the recording; returns the graph id.  `keep`: tensors the recorded calls
+        read or write, held here until he_graph_free."""
+        gid = (ctypes.c_int32 * 1)()
+        self._ck(lib().he_graph_end(self.h, gid), "he_graph_end")
+        self._graph_refs[int(gid[0])] = list(keep)
+        return int(gid[0])
 
     def he_graph_launch(self, graph):
         self._ck(lib().he_graph_launch(self.h, graph), "he_graph_launch")

@@ -300,8 +300,9 @@ class DeepSpec:
 
 class _NetWorkers:
     """Workers of one ring serving whole networks: a library context and a CUDA stream each,
-    the Galois and relinearisation keys resident in every context, the weights fixed.  One
-    output ciphertext per request (the logits)."""
+    the Galois and relinearisation keys resident in every context, the weights fixed, batches
+    run as library calls or replayed as recorded CUDA graphs.  One output ciphertext per
+    request (the logits)."""
 
     def __init__(self, log_n, n_q, n_p, alpha, workers, keep_results):
         import torch
@@ -319,6 +320,38 @@ class _NetWorkers:
         for c in self.ctx:
             c.he_keygen_galois(self.sk, key_seed, steps)
 
+    def _record(self, graphs, n_in):
+        """graphs = G > 0: every worker records its network call into CUDA graphs for
+        batches of 1 .. G requests on input / output buffers of its own (each batch size run
+        once first, the largest first, so that the context's scratch and network buffer are
+        sized before any recording; all graphs of a worker share them)."""
+        import torch
+        self.graphs = []
+        self.use_graphs = graphs > 0
+        for w, c in enumerate(self.ctx):
+            g = {}
+            if graphs > 0:
+                with torch.cuda.stream(self.streams[w]):
+                    ins = [c.new_ct() for _ in range(graphs * n_in)]
+                    outs = [c.new_ct() for _ in range(graphs)]
+                for b in range(graphs, 0, -1):
+                    with torch.cuda.stream(self.streams[w]):
+                        self._call(c, ins[:b * n_in], outs[:b])
+                    c.he_graph_begin(share_scratch=True)
+                    try:
+                        self._call(c, ins[:b * n_in], outs[:b])
+                    finally:
+                        gid = c.he_graph_end(keep=ins + outs)
+                    g[b] = (ins[:b * n_in], outs[:b], gid)
+            self.graphs.append(g)
+
+    def close(self):
+        """Frees the recorded graphs (the contexts go with the ring)."""
+        for c, g in zip(self.ctx, getattr(self, "graphs", [])):
+            for _, _, gid in g.values():
+                c.he_graph_free(gid)
+        self.graphs = [{} for _ in self.ctx]
+
     def encrypt(self, slots, seed):
         return self.ctx[0].he_encrypt(self.sk, slots, seed)
 
@@ -328,9 +361,20 @@ class _NetWorkers:
     def launch(self, worker, requests):
         import torch
         ctx = self.ctx[worker]
+        cts = [c for r in requests for c in self._inputs(r.payload)]
+        graphs = getattr(self, "graphs", None)
+        captured = graphs[worker].get(len(requests)) if graphs and self.use_graphs else None
         with torch.cuda.stream(self.streams[worker]):
-            outs = [ctx.new_ct() for _ in requests]
-            self._call(ctx, [c for r in requests for c in self._inputs(r.payload)], outs)
+            if captured is not None:
+                ins, bound, gid = captured
+                for buf, c in zip(ins, cts):
+                    buf.copy_(c)
+                ctx.he_graph_launch(gid)
+                # the bound outputs are rewritten by the worker's next batch: keep copies
+                outs = [o.clone() for o in bound] if self.keep_results else None
+            else:
+                outs = [ctx.new_ct() for _ in requests]
+                self._call(ctx, cts, outs)
             ev = torch.cuda.Event()
             ev.record(self.streams[worker])
         return (ev, outs)
@@ -355,13 +399,14 @@ class _NetWorkers:
 
 class NetRing(_NetWorkers):
     def __init__(self, spec: NetSpec, workers: int, W1, W2, F1, F2, sk_seed: int, key_seed: int,
-                 keep_results: bool = True):
+                 keep_results: bool = True, graphs: int = 0):
         super().__init__(spec.log_n, spec.n_q, spec.n_p, spec.alpha, workers, keep_results)
         self.spec = spec
         self.W1, self.W2, self.F1, self.F2 = W1, W2, F1, F2
         self.lay = self.ctx[0].layout(*spec.shape, pack="dp_shift_ext")
         self.net = self.ctx[0].net(self.lay, spec.m1, spec.m2)
         self._keys(sk_seed, key_seed, self.ctx[0].he_net_required_steps(self.net))
+        self._record(graphs, 1)
 
     def footprint(self, req):
         # input, output, the five channel outputs and the combined vector, plus the layer's
@@ -374,7 +419,7 @@ class NetRing(_NetWorkers):
 
 class DeepRing(_NetWorkers):
     def __init__(self, spec: DeepSpec, workers: int, W1s, W2s, F, sk_seed: int, key_seed: int,
-                 keep_results: bool = True):
+                 keep_results: bool = True, graphs: int = 0):
         super().__init__(spec.log_n, spec.n_q, spec.n_p, spec.alpha, workers, keep_results)
         self.spec = spec
         self.W1s, self.W2s, self.F = W1s, W2s, F
@@ -384,6 +429,7 @@ class DeepRing(_NetWorkers):
             C = O
         self.n_in = self.ctx[0].mc_cts(spec.C0, spec.H, spec.W)
         self._keys(sk_seed, key_seed, self.ctx[0].he_deep_required_steps(self.convs, spec.n_cls))
+        self._record(graphs, self.n_in)
 
     def footprint(self, req):
         # inputs, output, the widest tensor twice (in and out of a layer) and the layers'

@@ -175,3 +175,47 @@ def test_mnist_network_n14_decrypts_to_plain():
         assert (dec[:16][:m2] == z2).all(), b
         assert not dec[m2:16].any()
         assert (dec[: prm.n // 2].reshape(-1, 16)[:, :m2] == z2).all()
+
+
+def test_recorded_network_replays_bit_exact(small):
+    """The whole network recorded as a CUDA graph (he_graph_begin .. he_graph_end) gives, at
+    every replay, the bits of the plain call on whatever the bound inputs hold; a refused call
+    spoils a recording; a graph stops replaying once the network buffer is reallocated."""
+    from paper_2102_03494_gb300 import he
+    prm, ctx, s, keys, rlk = small
+    _, W1, W2, F1, F2 = rand_net(SMALL, M1, M2, seed=7)
+    net = ctx.net(gpu_layout(ctx, SMALL), M1, M2)
+    cts = [encrypt_slots(prm, s, input_slots(np.random.default_rng(200 + b).integers(0, 256, (1, 12, 12)),
+                                             SMALL, prm.n), 70 + b) for b in range(2)]
+    ins = [upload_ntt(ctx, c) for c in cts]
+    outs = [ctx.new_ct() for _ in range(2)]
+    ctx.he_net_batch(ins, W1, W2, F1, F2, net, outs)          # sizes scratch and network buffer
+    want = [download_coeff(ctx, o) for o in outs]
+    assert (want[0] == network.he_net(prm, cts[0], W1, W2, SMALL, F1, F2, keys, rlk).stack()).all()
+    ctx.he_graph_begin(share_scratch=True)
+    ctx.he_net_batch(ins, W1, W2, F1, F2, net, outs)
+    with pytest.raises(he.HeError):
+        ctx.he_decrypt(s, outs[0])                            # refused while recording
+    with pytest.raises(he.HeError):
+        ctx.he_graph_end()                                    # ... which spoiled the recording
+    graphs = []
+    for share in (True, False):
+        ctx.he_graph_begin(share_scratch=share)
+        ctx.he_net_batch(ins, W1, W2, F1, F2, net, outs)
+        graphs.append(ctx.he_graph_end(keep=ins + outs))
+    for gid in graphs:
+        for o in outs:
+            o.zero_()
+        ctx.he_graph_launch(gid)
+        for b in range(2):
+            assert (download_coeff(ctx, outs[b]) == want[b]).all(), (gid, b)
+    a, b = ins[0].clone(), ins[1].clone()
+    ins[0].copy_(b)
+    ins[1].copy_(a)
+    ctx.he_graph_launch(graphs[1])
+    assert (download_coeff(ctx, outs[0]) == want[1]).all() and (download_coeff(ctx, outs[1]) == want[0]).all()
+    ctx.he_net_batch(ins * 4, W1, W2, F1, F2, net)            # a larger batch regrows the buffers
+    for gid in graphs:
+        with pytest.raises(he.HeError):
+            ctx.he_graph_launch(gid)
+        ctx.he_graph_free(gid)

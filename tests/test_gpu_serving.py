@@ -60,11 +60,13 @@ def serving_clock():
     return time.perf_counter
 
 
-def test_networks_are_identical_alone_and_in_the_mix():
+@pytest.mark.parametrize("graphs", [0, 4])
+def test_networks_are_identical_alone_and_in_the_mix(graphs):
     """Whole networks served: the three-layer network (N = 2048, 1 x 12 x 12 -> 3 channels ->
     20 -> 4) and a multi-ciphertext network (N = 2048, 3 x 8 x 8 -> 20 -> 24 channels at rank
-    4, 4 classes) on two rings; every result is bit-identical to the same request run alone and
-    decrypts to the plain network mod t."""
+    4, 4 classes) on two rings, batches run as calls or replayed as recorded graphs; every
+    result is bit-identical to the same request run alone and decrypts to the plain network
+    mod t."""
     from oracle import deepnet, network
     from oracle.ffconv import Layout, input_slots
     rng = np.random.default_rng(17)
@@ -75,13 +77,15 @@ def test_networks_are_identical_alone_and_in_the_mix():
     F1 = rng.integers(-8, 9, (m1, lay.O_c * lay.S))
     F2 = rng.integers(-8, 9, (m2, m1))
     net_ring = serving.NetRing(serving.NetSpec(11, 4, 2, 2, (1, 12, 12, 3, 2, 1, 2, 3), m1, m2),
-                               workers=2, W1=W1, W2=W2, F1=F1, F2=F2, sk_seed=31, key_seed=32)
+                               workers=2, W1=W1, W2=W2, F1=F1, F2=F2, sk_seed=31, key_seed=32,
+                               graphs=graphs)
     shape = deepnet.DeepShape(3, 8, 8, [deepnet.ConvSpec(20, 4), deepnet.ConvSpec(24, 4)], n_cls=4)
     w = deepnet.rand_weights(shape, 5)
     deep_ring = serving.DeepRing(serving.DeepSpec(11, 5, 2, 2, 3, 8, 8, (20, 24), 4, 4), workers=2,
                                  W1s=[np.asarray(a, np.int32) for a, _ in w["convs"]],
                                  W2s=[np.asarray(b, np.int32) for _, b in w["convs"]],
-                                 F=np.asarray(w["fc"], np.int32), sk_seed=41, key_seed=42)
+                                 F=np.asarray(w["fc"], np.int32), sk_seed=41, key_seed=42,
+                                 graphs=graphs)
     rings = {"net": net_ring, "deep": deep_ring}
     reqs = serving.poisson_arrivals(seed=5, rate=1000.0, count=20, mix={"net": 0.6, "deep": 0.4})
     images = {}
@@ -110,3 +114,5 @@ def test_networks_are_identical_alone_and_in_the_mix():
         else:
             _, logits = deepnet.plain_deep(images[r.rid], w, shape, 65537)
             assert (dec[:deepnet.next_pow2(shape.n_cls)][:shape.n_cls] == logits).all()
+    for ring in rings.values():
+        ring.close()
