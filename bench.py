@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--serving-layers", action="store_true",
                     help="serving loop over single FFConv layers (28 x 28 at N = 2^14, 3 x 32 x 32 "
                          "at N = 2^15) instead of whole networks")
+    ap.add_argument("--packing", action="store_true",
+                    help="Table IX: the packing variants on WideNet's factorized second layer")
     ap.add_argument("--serving", action="store_true",
                     help="run the serving loop (mixed rings, Poisson arrivals) instead")
     ap.add_argument("--net", action="store_true",
@@ -689,6 +691,76 @@ def run_serving_layers(args):
 NET_LOG_N, NET_N_Q, NET_N_P, NET_ALPHA, NET_M1, NET_M2 = 14, 6, 2, 2, 100, 10
 
 
+def run_packing(args):
+    """The packing variants of Table IX on its layer: WideNet's second convolution, factorized
+    (83 x 13 x 13 input, 6 x 6 stride 2 pad 1 -> r = 20, then 1 x 1 -> 163 channels), one
+    encrypted image at N = 2^14 (6 + 2 primes): DP-HI2C-CP (dp_dot, the paper's FFConv form),
+    DP-DP (dp_dp, LoLa's form) and CP-HI2C-CP (cp_cp; the Im2Col columns come from the client
+    here, so the homomorphic Im2Col that Table IX charges to it is not in the time)."""
+    import numpy as np
+    import torch
+
+    from paper_2102_03494_gb300 import he
+
+    torch.cuda.set_device(0)
+    shape = (83, 13, 13, 6, 2, 1, 20, 163)
+    I_c, I_h, I_w, d, st, pad, r, O_c = shape
+    O = (I_h + 2 * pad - d) // st + 1
+    stream = torch.cuda.Stream()
+    ctx = he.Context(log_n=NET_LOG_N, n_q=NET_N_Q, n_p=NET_N_P, alpha=NET_ALPHA, stream=stream)
+    N = 1 << NET_LOG_N
+    rng = np.random.default_rng(31)
+    x = rng.integers(0, 256, (I_c, I_h, I_w))
+    W1 = rng.integers(-8, 9, (r, I_c, d, d)).astype(np.int32)
+    W2 = rng.integers(-8, 9, (O_c, r)).astype(np.int32)
+    sk = ctx.he_keygen_secret(41)
+    lay_dp = ctx.layout(*shape, pack="dp_dp")
+    ctx.he_keygen_galois(sk, 42, ctx.he_ffconv_required_steps(lay_dp))   # covers dp_dot's too
+    dense = np.zeros(N, dtype=np.int64)
+    dense[: x.size] = x.reshape(-1)
+    ct_dense = ctx.he_encrypt(sk, dense, 43)
+    cols = []
+    for ci in range(I_c):
+        for i in range(d):
+            for j in range(d):
+                v = np.zeros(N, dtype=np.int64)
+                for oh in range(O):
+                    for ow in range(O):
+                        h, w = st * oh + i - pad, st * ow + j - pad
+                        if 0 <= h < I_h and 0 <= w < I_w:
+                            v[oh * O + ow] = x[ci, h, w]
+                cols.append(ctx.he_encrypt(sk, v, 1000 + len(cols)))
+    torch.cuda.synchronize()
+    paper_s = {"dp_dot": 75.27, "dp_dp": 784.45, "cp_cp": 2560.49}
+    rows = []
+    for pack in ("dp_dot", "dp_dp", "cp_cp"):
+        lay = ctx.layout(*shape, pack=pack)
+        cts = cols if pack == "cp_cp" else [ct_dense]
+        outs = [ctx.new_ct() for _ in range(O_c)]
+        for _ in range(max(1, args.warmup)):
+            ctx.he_ffconv_layer_batch(cts, W1, W2, lay, outs)
+        torch.cuda.synchronize()
+        ctx.he_reset_op_counts()
+        reps = 2
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            ctx.he_ffconv_layer_batch(cts, W1, W2, lay, outs)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ops = {k: v // reps for k, v in ctx.he_op_counts().items()}
+        rows.append({"packing": {"dp_dot": "DP-HI2C-CP", "dp_dp": "DP-DP", "cp_cp": "CP-HI2C-CP"}[pack],
+                     "pack": pack, "ms_per_image": e0.elapsed_time(e1) / reps, "ops_per_image": ops,
+                     "paper_cpu_s": paper_s[pack]})
+    print(json.dumps({"metric": "FFConv packing variants on WideNet's factorized second layer (Table IX)",
+                      "unit": "ms per image", "config": {
+                          "layer": "83x13x13 -> 6x6 s2 p1 (r=20) -> 1x1 (163 ch)",
+                          "ring": "N=2^14, 6x50-bit q, 2x60-bit p, alpha=2, t=65537",
+                          "note": "cp_cp takes client-side Im2Col columns (2988 ciphertexts); the "
+                                  "paper's CP-HI2C-CP time includes 2530 s of homomorphic Im2Col"},
+                      "variants": rows}))
+
+
 def run_net(args):
     """The three-layer network on a batch of encrypted 1 x 28 x 28 images: FFConv layer
     (5 x 5 stride 2, r = 2 -> 5 channels, extended-basis schedule), channel combine, x^2,
@@ -902,6 +974,9 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.packing:
+        run_packing(args)
         return
     if args.serving_layers:
         run_serving_layers(args)

@@ -39,7 +39,7 @@ enum {
 };
 
 enum { HE_COEFF = 0, HE_NTT = 1 };            /* representation of a ciphertext's limbs */
-enum { HE_DP_DOT = 0, HE_DP_SHIFT = 1, HE_DP_SHIFT_EXT = 2, HE_CP_CP = 3 };  /* W1 schedule */
+enum { HE_DP_DOT = 0, HE_DP_SHIFT = 1, HE_DP_SHIFT_EXT = 2, HE_CP_CP = 3, HE_DP_DP = 4 };  /* schedule */
 
 /* Rotation step that swaps the two rows of slots (Galois element 2N - 1). */
 #define HE_ROW_SWAP ((int32_t)0x7fffffff)
@@ -77,8 +77,9 @@ typedef struct {
 
 /* Shape of one FFConv layer (Sec. 3.1 notation): input I_c x I_h x I_w, low-rank filters
  * W1 of d x d x I_c x r (r = O'_c of Eq. 2), restoring filters W2 of 1 x 1 x r x O_c,
- * stride and zero padding of W1, pack = HE_DP_DOT, HE_DP_SHIFT, HE_DP_SHIFT_EXT or HE_CP_CP;
- * modswitch != 0 drops the last ciphertext prime at the end of the layer. */
+ * stride and zero padding of W1, pack = HE_DP_DOT, HE_DP_SHIFT, HE_DP_SHIFT_EXT, HE_CP_CP or
+ * HE_DP_DP (the DensePack-DensePack baseline of Table IX: W2 also under DensePack);
+ * modswitch != 0 drops the last ciphertext prime at the end of the layer (not with HE_DP_DP). */
 typedef struct {
     int32_t I_c, I_h, I_w, d, stride, pad, r, O_c;
     int32_t pack;
@@ -204,7 +205,7 @@ int he_rescale(he_ctx* ctx, const he_ct* in, he_ct* out);
 
 /* Encrypted FFConv layer, FFConv packing DP-HI2C-CP (Sec. 4.2, Fig. 4; Tables I-III).
  *   ct_in      one ciphertext (NTT domain, level n_q) holding the input image packed as the
- *              layout requires: HE_DP_DOT slot ci*I_h*I_w + h*I_w + w;
+ *              layout requires: HE_DP_DOT and HE_DP_DP slot ci*I_h*I_w + h*I_w + w;
  *              HE_DP_SHIFT(_EXT) slot ci*B_c + h*I_w + w with B_c = I_h*I_w for I_c = 1,
  *              else the next power of two.
  *   lowrank_w  host int32 [r][I_c][d][d] (W1), restore_w host int32 [O_c][r] (W2); weights
@@ -226,7 +227,14 @@ int he_rescale(he_ctx* ctx, const he_ct* in, he_ct* out);
  * ciphertexts per image (image b's column k = (ci, i, j) at index b*K + k, holding the input
  * pixel under tap (i, j) of output o at slot o = oh*O_w + ow); W1 and W2 are both ConvPack
  * scalar products (MulPC r (K + O_c), Table II), no Galois key is needed, and output channel
- * c holds y2[c, oh, ow] at slot oh*O_w + ow. */
+ * c holds y2[c, oh, ow] at slot oh*O_w + ow.
+ * HE_DP_DP is the DensePack-DensePack baseline of Table IX (LoLa's packing): W1 as HE_DP_DOT,
+ * the r channel ciphertexts combined into one dense vector (channel c' rotated by -c'*S so
+ * y1[c', o] sits at slot c'*S + o), then W2 under DensePack too: per output (c, o) the vector
+ * times the plaintext holding W2[c][c'] at slot c'*S + o, rotate-and-sum with steps 1, 2, ..,
+ * 2^(k2-1) where 2^k2 > (r-1)*S, and one-hot masks gather the O_c*S dot products (output slot
+ * oh*O_w + ow, zero elsewhere).  Needs r*S <= N/2 and no modswitch; r - 1 + O_c*S*k2
+ * rotations beyond HE_DP_DOT's. */
 int he_ffconv_layer(he_ctx* ctx, const he_ct* ct_in, const int32_t* lowrank_w,
                     const int32_t* restore_w, const he_layout* layout, he_ct* ct_out);
 /* The same layer on B independent ciphertexts with shared weights: ct_in[B],

@@ -347,6 +347,15 @@ int upload_host(he_ctx* ctx, void* dst, const void* src, size_t bytes) {
     return HE_OK;
 }
 
+// Call arguments to the device: through a pinned staging slot when they fit (asynchronous),
+// else into `scratch` (device memory of the caller's) with upload_host, whose copy from
+// pageable memory waits for the stream first.  Returns the device copy or NULL.
+const void* upload_args(he_ctx* ctx, const void* src, size_t bytes, void* scratch) {
+    if (bytes <= ctx->staging.slot_bytes) return upload_small(ctx, src, bytes);
+    if (!scratch || upload_host(ctx, scratch, src, bytes)) return nullptr;
+    return scratch;
+}
+
 uint32_t galois_elt(const he_ctx* ctx, int32_t step) {
     const uint64_t two_n = 2ull * ctx->N;
     if (step == HE_ROW_SWAP) return (uint32_t)(two_n - 1);

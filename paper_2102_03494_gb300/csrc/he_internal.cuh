@@ -267,6 +267,7 @@ void phase_begin(he_ctx* ctx, int phase);
 void phase_end(he_ctx* ctx);
 const void* upload_small(he_ctx* ctx, const void* src, size_t bytes);
 int upload_host(he_ctx* ctx, void* dst, const void* src, size_t bytes);
+const void* upload_args(he_ctx* ctx, const void* src, size_t bytes, void* scratch);
 int check_ct(he_ctx* ctx, const he_ct* ct, int need_limbs, int need_domain, const char* what);
 // Slot values (items x N int64, device) -> plaintexts [items][rows][N]: centred lift modulo
 // the first `rows` moduli (L for Q, L + K for Q u P), NTT domain, Montgomery form if mont.

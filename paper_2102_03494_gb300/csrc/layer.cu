@@ -10,6 +10,10 @@
 // rows; Table VIII's 7000 = 500 x 14 and 120 = 10 x 12).  One-hot masks then gather the r*S
 // dot products into r ciphertexts (no rotation: Table III, DP-HI2C-CP, d = 1).
 //
+// HE_DP_DP (Table IX's DensePack-DensePack baseline): W1 as HE_DP_DOT, then W2 under DensePack
+// as well (dp_dp_tail): the channels combined into one dense vector, one dense vector-row
+// product and rotate-and-sum per output (c, o), one-hot masks gathering the results.
+//
 // HE_DP_SHIFT (hoisted taps): one hoisted rotation of the input per filter tap
 // delta = (i - pad) I_w + (j - pad) and a plaintext per (c', tap) holding W1[c', ci, i, j] at
 // the output base slots; channels folded with rotations by B_c 2^e.
@@ -65,7 +69,7 @@ int layout_info(const he_ctx* c, const he_layout* y, LayoutInfo* li, std::string
     if (y->I_c < 1 || y->I_h < 1 || y->I_w < 1 || y->d < 1 || y->stride < 1 || y->pad < 0 ||
         y->r < 1 || y->O_c < 1 ||
         (y->pack != HE_DP_DOT && y->pack != HE_DP_SHIFT && y->pack != HE_DP_SHIFT_EXT &&
-         y->pack != HE_CP_CP)) {
+         y->pack != HE_CP_CP && y->pack != HE_DP_DP)) {
         *why = "layout fields out of range";
         return HE_EINVAL;
     }
@@ -88,10 +92,14 @@ int layout_info(const he_ctx* c, const he_layout* y, LayoutInfo* li, std::string
             *why = "CP_CP output positions must fit in N slots";
             return HE_EINVAL;
         }
-    } else if (y->pack == HE_DP_DOT) {
+    } else if (y->pack == HE_DP_DOT || y->pack == HE_DP_DP) {
         long long span = (long long)y->I_c * li->hw;
         if (span > c->N || li->S > half) {
             *why = "DP_DOT input must fit in N slots and its output in N/2";
+            return HE_EINVAL;
+        }
+        if (y->pack == HE_DP_DP && ((long long)y->r * li->S > half || y->modswitch)) {
+            *why = "DP_DP needs r S <= N/2 (one dense vector) and no modulus switch";
             return HE_EINVAL;
         }
         const int full = ceil_log2(half);
@@ -111,12 +119,26 @@ int layout_info(const he_ctx* c, const he_layout* y, LayoutInfo* li, std::string
     return HE_OK;
 }
 
+// DP_DP: W2's rotate-and-sum depth, the smallest k2 with 2^k2 > (r - 1) S.
+int dp_dp_k2(const he_layout& y, const LayoutInfo& li) {
+    int k = 0;
+    while ((1ll << k) <= (long long)(y.r - 1) * li.S) ++k;
+    return k;
+}
+
 std::vector<int32_t> layer_steps(const he_layout& y, const LayoutInfo& li) {
     std::vector<int32_t> st;
     if (y.pack == HE_CP_CP) return st;   // ConvPack throughout: no rotation
-    if (y.pack == HE_DP_DOT) {
+    if (y.pack == HE_DP_DOT || y.pack == HE_DP_DP) {
         for (int e = 0; e < li.sum_depth; ++e) st.push_back(1 << e);
         if (li.both_rows) st.push_back(HE_ROW_SWAP);
+        if (y.pack == HE_DP_DP) {             // combine, then W2's rotate-and-sum
+            auto add = [&](int32_t v) {
+                if (std::find(st.begin(), st.end(), v) == st.end()) st.push_back(v);
+            };
+            for (int c = 1; c < y.r; ++c) add(-c * li.S);
+            for (int e = 0; e < dp_dp_k2(y, li); ++e) add(1 << e);
+        }
     } else {
         for (int i = 0; i < y.d; ++i)
             for (int j = 0; j < y.d; ++j) {
@@ -172,6 +194,16 @@ __global__ void k_dp_dot_slots(const int32_t* __restrict__ w1, int I_c, int I_h,
     }
 }
 
+// DP_DP: plaintext c S + o (row (c, o) of W2 under DensePack) holds W2[c][c'] at slot
+// c' S + o of the dense vector, c' < r (slots zeroed beforehand).
+__global__ void k_dp_dp_rows(const int32_t* __restrict__ w2, int r, int S, int logN,
+                             int64_t* __restrict__ out) {
+    const int N = 1 << logN;
+    const int row = blockIdx.x, c = row / S, o = row - c * S;
+    for (int cp = threadIdx.x; cp < r; cp += blockDim.x)
+        out[(size_t)row * N + (size_t)cp * S + o] = w2[c * r + cp];
+}
+
 // Channel fold (input channels in blocks of B_c slots): acc <- acc + rot(acc, B_c 2^e); the
 // result ends in A (A and A2 are swapped as needed).
 int fold_channels(he_ctx* ctx, uint64_t*& A, uint64_t*& A2, int items, const LayoutInfo& li,
@@ -217,14 +249,16 @@ static std::vector<uint64_t> weights_mont(const he_ctx* ctx, const int32_t* w, i
 
 // W2 under ConvPack (Table II): ct_out[b][c] = sum_c' W2[c][c'] ct_w1[b][c'] with scalar
 // plaintexts, from the channel results A [B][r][2][L][N]; then the optional modulus switch.
+// d_wm: O_c r L words of the caller's scratch for the weights.
 static int restore_layer(he_ctx* ctx, const uint64_t* A, int B, const he_layout& y,
                          const int32_t* restore_w, he_ct* ct_out, uint64_t* Y, uint64_t* last,
-                         uint64_t* sprd) {
+                         uint64_t* sprd, uint64_t* d_wm) {
     const int L = ctx->L, r = y.r, O_c = y.O_c;
     const size_t ct = 2 * (size_t)L * ctx->N;
     const std::vector<uint64_t> wm = weights_mont(ctx, restore_w, O_c, r);
-    const uint64_t* d_wm = (const uint64_t*)upload_small(ctx, wm.data(), wm.size() * 8);
-    if (!d_wm) return he_fail(ctx, HE_EINVAL, "he_ffconv_layer: W2 too large for staging");
+    d_wm = (uint64_t*)upload_args(ctx, wm.data(), wm.size() * 8, d_wm);
+    if (!d_wm) return he_fail(ctx, HE_ECUDA, "he_ffconv_layer: W2 upload failed");
+    int rc;
     std::vector<uint64_t*> dst(B * O_c);
     for (int o = 0; o < B * O_c; ++o) {
         dst[o] = y.modswitch ? Y + (size_t)o * ct : ct_out[o].data;
@@ -236,7 +270,7 @@ static int restore_layer(he_ctx* ctx, const uint64_t* A, int B, const he_layout&
     launch_convpack(ctx, A, B, r, O_c, d_wm, dp, L);
     ctx->ops[0] += (uint64_t)B * O_c * r;
     ctx->ops[1] += (uint64_t)B * O_c * (r - 1);
-    int rc = he_launch_check(ctx, "he_ffconv_layer");
+    rc = he_launch_check(ctx, "he_ffconv_layer");
     if (rc) return rc;
     if (y.modswitch) {
         std::vector<const uint64_t*> xs(B * O_c);
@@ -249,6 +283,115 @@ static int restore_layer(he_ctx* ctx, const uint64_t* A, int B, const he_layout&
     }
     phase_end(ctx);
     return HE_OK;
+}
+
+// Scratch (u64 words) of the DP_DP tail for B images.
+static size_t dp_dp_scratch(const he_ctx* ctx, const he_layout& y, const LayoutInfo& li, int B) {
+    const size_t N = ctx->N, ct = 2 * (size_t)ctx->L * N, rows = (size_t)y.O_c * li.S;
+    return 2 * (size_t)B * ct + 2 * (size_t)B * rows * ct + rows * (2 * N + (size_t)ctx->L * N) + 256;
+}
+
+// DP-DP tail (Table IX's DensePack-DensePack baseline) after the DP_DOT W1: the r channel
+// ciphertexts A[b][c'] (y1[c', o] at slot o) are combined into one dense vector
+// Y[b] = sum_c' rot(A[b][c'], -c' S); W2 under DensePack: z[b][c][o] = Y[b] * row(c, o),
+// rotate-and-sum over 2^k2 > (r - 1) S slots (slot o then holds y2[c, o]), and the one-hot
+// masks of the DP_DOT plaintexts gather the O_c S dot products into ct_out.  Buffers come from
+// the arena the caller reserved (dp_dp_scratch words).
+static int dp_dp_tail(he_ctx* ctx, const uint64_t* A, int B, const he_layout& y,
+                      const LayoutInfo& li, const int32_t* restore_w, he_ct* ct_out,
+                      const uint64_t* mask_pts, const RotBufs& rb, int chunk) {
+    const int L = ctx->L, r = y.r, O_c = y.O_c, S = li.S, k2 = dp_dp_k2(y, li);
+    const size_t N = ctx->N, ct = 2 * (size_t)L * N;
+    const int n_rows = O_c * S, n2 = B * n_rows;
+    uint64_t* Xc = arena_take(ctx, (size_t)B * ct);
+    uint64_t* Y = arena_take(ctx, (size_t)B * ct);
+    uint64_t* Z = arena_take(ctx, (size_t)n2 * ct);
+    uint64_t* Z2 = arena_take(ctx, (size_t)n2 * ct);
+    int64_t* slots = (int64_t*)arena_take(ctx, (size_t)n_rows * N);
+    uint64_t* tmp = arena_take(ctx, (size_t)n_rows * N);
+    uint64_t* rows = arena_take(ctx, (size_t)n_rows * L * N);
+    if (!rows) return he_fail(ctx, HE_ENOMEM, "he_ffconv_layer: DP_DP scratch");
+    int rc;
+    // combine the channels into one dense vector per image
+    phase_begin(ctx, HE_PHASE_ROTATE);
+    for (int b = 0; b < B; ++b)
+        HE_CHECK_CUDA(ctx, cudaMemcpyAsync(Y + (size_t)b * ct, A + (size_t)b * r * ct, ct * 8,
+                                           cudaMemcpyDeviceToDevice, ctx->stream));
+    for (int c = 1; c < r; ++c) {
+        std::vector<uint64_t*> o(B);
+        for (int b = 0; b < B; ++b) {
+            HE_CHECK_CUDA(ctx, cudaMemcpyAsync(Xc + (size_t)b * ct, A + ((size_t)b * r + c) * ct, ct * 8,
+                                               cudaMemcpyDeviceToDevice, ctx->stream));
+            o[b] = Y + (size_t)b * ct;
+        }
+        if ((rc = rotate_contig(ctx, Xc, B, galois_elt(ctx, -c * S), Y, o, rb, chunk))) return rc;
+    }
+    phase_end(ctx);
+    // W2 rows under DensePack
+    phase_begin(ctx, HE_PHASE_ENCODE);
+    const int32_t* d_w2 = (const int32_t*)upload_small(ctx, restore_w, (size_t)O_c * r * 4);
+    if (!d_w2) return he_fail(ctx, HE_EINVAL, "he_ffconv_layer: W2 too large for staging");
+    HE_CHECK_CUDA(ctx, cudaMemsetAsync(slots, 0, (size_t)n_rows * N * 8, ctx->stream));
+    ++ctx->launches;
+    k_dp_dp_rows<<<n_rows, 32, 0, ctx->stream>>>(d_w2, r, S, ctx->logN, slots);
+    encode_device(ctx, slots, n_rows, tmp, rows, 1, L);
+    phase_end(ctx);
+    // z[b][c][o] = Y[b] * row(c, o), in launches of at most 8192 products (pointer tables)
+    phase_begin(ctx, HE_PHASE_RESTORE);
+    for (int s0 = 0; s0 < n2; s0 += 8192) {
+        const int n = std::min(8192, n2 - s0);
+        std::vector<const uint64_t*> xs(n), ps(n);
+        std::vector<uint64_t*> os(n);
+        for (int i = 0; i < n; ++i) {
+            const int q = s0 + i, b = q / n_rows, row = q - b * n_rows;
+            xs[i] = Y + (size_t)b * ct;
+            ps[i] = rows + (size_t)row * L * N;
+            os[i] = Z + (size_t)q * ct;
+        }
+        auto xp = upload_ptrs(ctx, xs);
+        auto pp = upload_ptrs(ctx, ps);
+        auto op = upload_out_ptrs(ctx, os);
+        if (!xp || !pp || !op) return he_fail(ctx, HE_ECUDA, "pointer table upload failed");
+        launch_mac(ctx, xp, pp, 1, nullptr, op, n, L);
+    }
+    phase_end(ctx);
+    // rotate-and-sum: z <- z + rot(z, 2^e)
+    phase_begin(ctx, HE_PHASE_ROTATE);
+    for (int e = 0; e < k2; ++e) {
+        std::vector<uint64_t*> o(n2);
+        for (int q = 0; q < n2; ++q) o[q] = Z2 + (size_t)q * ct;
+        if ((rc = rotate_contig(ctx, Z, n2, galois_elt(ctx, 1 << e), Z, o, rb, chunk))) return rc;
+        std::swap(Z, Z2);
+    }
+    phase_end(ctx);
+    // gather: ct_out[b][c] = sum_o z[b][c][o] * mask_o
+    phase_begin(ctx, HE_PHASE_RESTORE);
+    const int tmax = max_mac_terms(ctx);
+    for (int o0 = 0; o0 < S; o0 += tmax) {
+        const int T = std::min(tmax, S - o0);
+        std::vector<const uint64_t*> mx((size_t)B * O_c * T), mp((size_t)B * O_c * T), ai;
+        std::vector<uint64_t*> ao((size_t)B * O_c);
+        for (int q = 0; q < B * O_c; ++q) {
+            for (int t = 0; t < T; ++t) {
+                mx[(size_t)q * T + t] = Z + ((size_t)q * S + o0 + t) * ct;
+                mp[(size_t)q * T + t] = mask_pts + (size_t)(o0 + t) * L * N;
+            }
+            ao[q] = ct_out[q].data;
+            ai.push_back(o0 ? ct_out[q].data : nullptr);
+        }
+        auto a1 = upload_ptrs(ctx, mx);
+        auto a2 = upload_ptrs(ctx, mp);
+        auto a3 = o0 ? upload_ptrs(ctx, ai) : nullptr;
+        auto a4 = upload_out_ptrs(ctx, ao);
+        if (!a1 || !a2 || !a4 || (o0 && !a3)) return he_fail(ctx, HE_ECUDA, "pointer table upload failed");
+        launch_mac(ctx, a1, a2, T, a3, a4, B * O_c, L);
+    }
+    for (int q = 0; q < B * O_c; ++q) ct_out[q].domain = HE_NTT;
+    phase_end(ctx);
+    // (rotate_contig counted the rotations, key switches and the additions that follow them)
+    ctx->ops[0] += (uint64_t)B * 2 * n_rows;
+    ctx->ops[1] += (uint64_t)B * O_c * (S - 1);
+    return he_launch_check(ctx, "he_ffconv_layer");
 }
 
 // CP-HI2C-CP (Sec. 4.2 'ConvPack for W1', Fig. 5): ct_in holds K = d^2 I_c Im2Col column
@@ -268,7 +411,8 @@ static int cp_cp_layer(he_ctx* ctx, const he_ct* ct_in, int B, const int32_t* lo
     if (K > max_mac_terms(ctx)) return he_fail(ctx, HE_EINVAL, "he_ffconv_layer: too many columns");
     const size_t N = ctx->N, ct = 2 * (size_t)L * N;
     size_t need = (size_t)B * K * ct + (size_t)B * r * ct +
-                  (y.modswitch ? (size_t)B * O_c * (ct + 2 * N + 2 * (L - 1) * N) : 0) + 1024;
+                  (y.modswitch ? (size_t)B * O_c * (ct + 2 * N + 2 * (L - 1) * N) : 0) +
+                  (size_t)(r * K + O_c * r) * L + 1024;                        // weights
     if ((rc = arena_reserve(ctx, need))) return rc;
     arena_reset(ctx);
     uint64_t* X = arena_take(ctx, (size_t)B * K * ct);
@@ -279,9 +423,12 @@ static int cp_cp_layer(he_ctx* ctx, const he_ct* ct_in, int B, const int32_t* lo
     for (int i = 0; i < B * K; ++i)
         HE_CHECK_CUDA(ctx, cudaMemcpyAsync(X + (size_t)i * ct, ct_in[i].data, ct * 8,
                                            cudaMemcpyDeviceToDevice, ctx->stream));
+    uint64_t* d_wm = arena_take(ctx, (size_t)r * K * L);
+    uint64_t* d_wm2 = arena_take(ctx, (size_t)O_c * r * L);
     const std::vector<uint64_t> wm = weights_mont(ctx, lowrank_w, r, K);
-    const uint64_t* d_wm = (const uint64_t*)upload_small(ctx, wm.data(), wm.size() * 8);
-    if (!d_wm) return he_fail(ctx, HE_EINVAL, "he_ffconv_layer: W1 too large for staging");
+    if (!d_wm || !d_wm2) return he_fail(ctx, HE_ENOMEM, "he_ffconv_layer: scratch");
+    d_wm = (uint64_t*)upload_args(ctx, wm.data(), wm.size() * 8, d_wm);
+    if (!d_wm) return he_fail(ctx, HE_ECUDA, "he_ffconv_layer: W1 upload failed");
     std::vector<uint64_t*> ao(B * r);
     for (int q = 0; q < B * r; ++q) ao[q] = A + (size_t)q * ct;
     auto op = upload_out_ptrs(ctx, ao);
@@ -291,7 +438,7 @@ static int cp_cp_layer(he_ctx* ctx, const he_ct* ct_in, int B, const int32_t* lo
     phase_end(ctx);
     ctx->ops[0] += (uint64_t)B * r * K;
     ctx->ops[1] += (uint64_t)B * r * (K - 1);
-    return restore_layer(ctx, A, B, y, restore_w, ct_out, Y, last, sprd);
+    return restore_layer(ctx, A, B, y, restore_w, ct_out, Y, last, sprd, d_wm2);
 }
 
 // W1 plaintexts of a layout (n_pt of them, pt_rows limbs each) from the integer weights:
@@ -299,7 +446,7 @@ static int cp_cp_layer(he_ctx* ctx, const he_ct* ct_in, int B, const int32_t* lo
 static int encode_w1(he_ctx* ctx, const he_layout& y, const LayoutInfo& li,
                      const int32_t* lowrank_w, int64_t* slots, uint64_t* tmp, uint64_t* pts) {
     const size_t N = ctx->N;
-    const bool dot = y.pack == HE_DP_DOT;
+    const bool dot = y.pack == HE_DP_DOT || y.pack == HE_DP_DP;
     const int r = y.r, LK = ctx->L + ctx->K;
     const int pt_rows = y.pack == HE_DP_SHIFT_EXT ? LK : ctx->L;
     const int n_pt = dot ? r * li.S + li.S : r * li.taps;
@@ -351,7 +498,7 @@ static int layer_impl(he_ctx* ctx, const he_ct* ct_in, int B, const int32_t* low
 
     const size_t N = ctx->N, ct = 2 * (size_t)L * N;
     const int r = y.r, O_c = y.O_c;
-    const bool dot = y.pack == HE_DP_DOT;
+    const bool dot = y.pack == HE_DP_DOT || y.pack == HE_DP_DP;   // DP_DP: W1 as DP_DOT
     const bool ext = y.pack == HE_DP_SHIFT_EXT;
     if (ext && li.taps > HE_MAX_TAPS) return he_fail(ctx, HE_EINVAL, "he_ffconv_layer: too many filter taps");
     const int LK = L + ctx->K;
@@ -371,7 +518,9 @@ static int layer_impl(he_ctx* ctx, const he_ct* ct_in, int B, const int32_t* low
                   + (size_t)n_prod * ct * (dot ? 2 : 1)        // products (double buffer for DP_DOT)
                   + (size_t)2 * B * r * ct + ext_acc           // accumulators (double buffer)
                   + (size_t)rot_items * rot_scratch_per_item(ctx)
-                  + (y.modswitch ? (size_t)B * O_c * (ct + 2 * N + 2 * (L - 1) * N) : 0) + 1024;
+                  + (y.modswitch ? (size_t)B * O_c * (ct + 2 * N + 2 * (L - 1) * N) : 0)
+                  + (y.pack == HE_DP_DP ? dp_dp_scratch(ctx, y, li, B) : 0)
+                  + (size_t)O_c * r * L + 1024;                                 // W2 weights
     if ((rc = arena_reserve(ctx, need))) return rc;
     arena_reset(ctx);
     uint64_t* X = arena_take(ctx, (size_t)B * ct);
@@ -388,7 +537,9 @@ static int layer_impl(he_ctx* ctx, const he_ct* ct_in, int B, const int32_t* low
     uint64_t* Y = y.modswitch ? arena_take(ctx, (size_t)B * O_c * ct) : nullptr;
     uint64_t* last = y.modswitch ? arena_take(ctx, (size_t)B * O_c * 2 * N) : nullptr;
     uint64_t* sprd = y.modswitch ? arena_take(ctx, (size_t)B * O_c * 2 * (L - 1) * N) : nullptr;
-    if (!rb.v || (y.modswitch && !sprd)) return he_fail(ctx, HE_ENOMEM, "he_ffconv_layer: scratch");
+    uint64_t* d_wm2 = arena_take(ctx, (size_t)O_c * r * L);
+    if (!rb.v || !d_wm2 || (y.modswitch && !sprd))
+        return he_fail(ctx, HE_ENOMEM, "he_ffconv_layer: scratch");
 
     // inputs -> contiguous X
     for (int b = 0; b < B; ++b)
@@ -420,9 +571,11 @@ static int layer_impl(he_ctx* ctx, const he_ct* ct_in, int B, const int32_t* low
         launch_mac(ctx, xp, pp, 1, nullptr, op, n_prod, L);
         phase_end(ctx);
         ctx->ops[0] += n_prod;
-        // rotate-and-sum: PR2 = PR + rot(PR, step), then swap
+        // rotate-and-sum: PR2 = PR + rot(PR, step), then swap (the first sum_depth (+ row
+        // swap) steps; DP_DP's list continues with its combine and W2 steps)
         phase_begin(ctx, HE_PHASE_ROTATE);
-        for (size_t si = 0; si < steps.size(); ++si) {
+        const size_t n_w1_steps = (size_t)li.sum_depth + (li.both_rows ? 1 : 0);
+        for (size_t si = 0; si < n_w1_steps; ++si) {
             std::vector<uint64_t*> outs(n_prod);
             for (int it = 0; it < n_prod; ++it) outs[it] = PR2 + (size_t)it * ct;
             if ((rc = rotate_contig(ctx, PR, n_prod, gs[si], PR, outs, rb, chunk))) return rc;
@@ -549,7 +702,10 @@ static int layer_impl(he_ctx* ctx, const he_ct* ct_in, int B, const int32_t* low
         phase_end(ctx);
     }
 
-    return restore_layer(ctx, A, B, y, restore_w, ct_out, Y, last, sprd);
+    if (y.pack == HE_DP_DP)
+        return dp_dp_tail(ctx, A, B, y, li, restore_w, ct_out, pts + (size_t)r * li.S * L * N, rb,
+                          rot_items);
+    return restore_layer(ctx, A, B, y, restore_w, ct_out, Y, last, sprd, d_wm2);
 }
 
 extern "C" int he_ffconv_layer(he_ctx* ctx, const he_ct* ct_in, const int32_t* lowrank_w,
@@ -583,7 +739,7 @@ extern "C" int he_ffconv_plan(he_ctx* ctx, const int32_t* lowrank_w, const int32
     if (y.pack != HE_CP_CP) {
         const size_t N = ctx->N;
         const int pt_rows = y.pack == HE_DP_SHIFT_EXT ? ctx->L + ctx->K : ctx->L;
-        const int n_pt = y.pack == HE_DP_DOT ? y.r * li.S + li.S : y.r * li.taps;
+        const int n_pt = (y.pack == HE_DP_DOT || y.pack == HE_DP_DP) ? y.r * li.S + li.S : y.r * li.taps;
         if (cudaMalloc((void**)&pl.pts, (size_t)n_pt * pt_rows * N * 8) != cudaSuccess) {
             cudaGetLastError();
             return he_fail(ctx, HE_ENOMEM, "he_ffconv_plan: plaintext allocation failed");

@@ -68,7 +68,7 @@ ConvGeom conv_geom(const he_layout& y) {
     int top = 0;
     for (int oh = 0; oh < g.O_h; ++oh)
         for (int ow = 0; ow < g.O_w; ++ow) {
-            const bool dense = y.pack == HE_DP_DOT || y.pack == HE_CP_CP;
+            const bool dense = y.pack == HE_DP_DOT || y.pack == HE_CP_CP || y.pack == HE_DP_DP;
             const int s = dense ? oh * g.O_w + ow : (y.stride * oh) * y.I_w + y.stride * ow;
             g.slot.push_back(s);
             top = std::max(top, s);

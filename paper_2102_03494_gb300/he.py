@@ -12,7 +12,7 @@ import numpy as np
 
 HE_OK, HE_EINVAL, HE_ENOMEM, HE_ENOKEY, HE_ECUDA, HE_ETIMEOUT = 0, -1, -2, -3, -4, -5
 HE_COEFF, HE_NTT = 0, 1
-HE_DP_DOT, HE_DP_SHIFT, HE_DP_SHIFT_EXT, HE_CP_CP = 0, 1, 2, 3
+HE_DP_DOT, HE_DP_SHIFT, HE_DP_SHIFT_EXT, HE_CP_CP, HE_DP_DP = 0, 1, 2, 3, 4
 HE_ROW_SWAP = 0x7FFFFFFF
 HE_RELIN_KEY = -0x80000000
 
@@ -496,7 +496,7 @@ class Context:
     @staticmethod
     def layout(I_c, I_h, I_w, d, stride, pad, r, O_c, pack="dp_shift", modswitch=False):
         packs = {"dp_dot": HE_DP_DOT, "dp_shift": HE_DP_SHIFT, "dp_shift_ext": HE_DP_SHIFT_EXT,
-                 "cp_cp": HE_CP_CP}
+                 "cp_cp": HE_CP_CP, "dp_dp": HE_DP_DP}
         return HeLayout(I_c, I_h, I_w, d, stride, pad, r, O_c, packs[pack], int(bool(modswitch)))
 
     def he_ffconv_required_steps(self, lay):

@@ -44,7 +44,7 @@ SMALL = [workloads.LayerShape(1, 8, 8, 3, 2, 1, 2, 3), workloads.LayerShape(2, 6
          workloads.LayerShape(3, 5, 7, 3, 2, 1, 3, 4), workloads.LayerShape(1, 9, 9, 5, 2, 2, 1, 2)]
 
 
-@pytest.mark.parametrize("pack", ["dp_shift", "dp_shift_ext", "dp_dot"])
+@pytest.mark.parametrize("pack", ["dp_shift", "dp_shift_ext", "dp_dot", "dp_dp"])
 @pytest.mark.parametrize("si", range(len(SMALL)))
 def test_small_layers_are_bit_exact(pack, si):
     prm = params.Params(log_n=9, n_q=3, n_p=1, alpha=1)
