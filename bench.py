@@ -307,6 +307,18 @@ def run(args):
     torch.cuda.synchronize()
     ms_e2e = e0.elapsed_time(e1)
     h2d_gbs, d2h_gbs = copy_bandwidth(stream)
+    # per-step latency distribution of the same layer (untimed for `value`): 50 steps, an
+    # event pair each
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(50)]
+    torch.cuda.synchronize()
+    for a, b in evs:
+        a.record(stream)
+        layer()
+        b.record(stream)
+    torch.cuda.synchronize()
+    lat = sorted(a.elapsed_time(b) for a, b in evs)
+    lat_p50, lat_p99 = lat[len(lat) // 2], lat[min(len(lat) - 1, int(0.99 * len(lat)))]
 
     # the plain one-request-at-a-time form: the same layer on one image per call (outputs are
     # bit-identical to the batched call's; tests/test_gpu_layer.py checks it)
@@ -368,6 +380,7 @@ def run(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": workload_name(args),
                        "batch_per_gpu": B, "layer_ms_per_batch": ms / args.steps,
+                       "layer_ms_per_batch_p50_p99": [lat_p50, lat_p99],
                        "layer_ms_per_image": ms / args.steps / B, "hoisted_rotations_per_image": n_rot,
                        "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (keys 755 MB + ModUp digits per step)",

@@ -398,6 +398,40 @@ __global__ void k_convpack(const uint64_t* __restrict__ x, int r, int O_c,
     }
 }
 
+// The same with R <= 8 inputs held in registers: each input residue is loaded once, then every
+// output channel is formed from the registers.
+template <int R>
+__global__ void k_convpack_reg(const uint64_t* __restrict__ x, int O_c,
+                               const uint64_t* __restrict__ wm, uint64_t* const* outp, int L,
+                               int logN, const ModConst* __restrict__ mods) {
+    const int N = 1 << logN;
+    const int n = blockIdx.y * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int i = blockIdx.z;
+    const int b = blockIdx.x;
+    const ModConst M = mods[i];
+    const size_t ct = (size_t)2 * L * N;
+    const uint64_t* xb = x + (size_t)b * R * ct + (size_t)i * N + n;
+    uint64_t x0[R], x1[R];
+#pragma unroll
+    for (int cp = 0; cp < R; ++cp) {
+        x0[cp] = xb[cp * ct];
+        x1[cp] = xb[cp * ct + (size_t)L * N];
+    }
+    for (int c = 0; c < O_c; ++c) {
+        U128 a0{0, 0}, a1{0, 0};
+#pragma unroll
+        for (int cp = 0; cp < R; ++cp) {
+            const uint64_t w = wm[((size_t)c * R + cp) * L + i];
+            mac128(a0, x0[cp], w);
+            mac128(a1, x1[cp], w);
+        }
+        uint64_t* ob = outp[(size_t)b * O_c + c] + (size_t)i * N + n;
+        ob[0] = redc(a0, M.q, M.qinv_neg);
+        ob[(size_t)L * N] = redc(a1, M.q, M.qinv_neg);
+    }
+}
+
 // out = a + b for `rows` limbs (pointer tables, each entry rows*N contiguous)
 __global__ void k_add(const uint64_t* const* ap, const uint64_t* const* bp, uint64_t* const* op,
                       int rows_per_poly, int polys, int logN, const ModConst* __restrict__ mods) {
@@ -821,8 +855,22 @@ void launch_mac(he_ctx* c, const uint64_t* const* X, const uint64_t* const* P, i
 void launch_convpack(he_ctx* c, const uint64_t* x, int B, int r, int O_c, const uint64_t* wm,
                      uint64_t* const* outp, int L) {
     ++c->launches;
-    k_convpack<<<grid_nx(B, c->N, L), 256, 0, c->stream>>>(x, r, O_c, wm, outp, L, c->logN,
-                                                           c->d_mod);
+    const dim3 grid = grid_nx(B, c->N, L);
+#define HE_CONVPACK_REG(R)                                                                  \
+    k_convpack_reg<R><<<grid, 256, 0, c->stream>>>(x, O_c, wm, outp, L, c->logN, c->d_mod)
+    switch (r) {
+        case 1: HE_CONVPACK_REG(1); break;
+        case 2: HE_CONVPACK_REG(2); break;
+        case 3: HE_CONVPACK_REG(3); break;
+        case 4: HE_CONVPACK_REG(4); break;
+        case 5: HE_CONVPACK_REG(5); break;
+        case 6: HE_CONVPACK_REG(6); break;
+        case 7: HE_CONVPACK_REG(7); break;
+        case 8: HE_CONVPACK_REG(8); break;
+        default:
+            k_convpack<<<grid, 256, 0, c->stream>>>(x, r, O_c, wm, outp, L, c->logN, c->d_mod);
+    }
+#undef HE_CONVPACK_REG
 }
 
 void launch_add(he_ctx* c, const uint64_t* const* a, const uint64_t* const* b,
