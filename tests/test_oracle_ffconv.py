@@ -151,3 +151,19 @@ def test_conv_pack_counts_follow_table_ii():
     assert (lay.S, lay.d * lay.d * lay.I_c) == (144, 64)
     ops = ffconv.expected_ops(lay, 8192)
     assert ops["mulpc"] == 13 * (64 + 56) and ops["rot"] == 0
+
+
+@pytest.mark.parametrize("slip", ["combine_sign", "short_sum"])
+def test_planted_dp_dp_slips_are_caught(monkeypatch, slip):
+    """DP-DP: combining the channels with the wrong rotation direction, or stopping W2's
+    rotate-and-sum one step short of (r - 1) S, breaks the decryption pin."""
+    prm = params.Params(log_n=7, n_q=3, n_p=1, alpha=1)
+    lay = ffconv.Layout(2, 5, 5, 3, 1, 1, 2, 2, pack="dp_dp")
+    if slip == "combine_sign":
+        monkeypatch.setattr(ffconv, "dp_dp_combine_steps", lambda l: [c * l.S for c in range(1, l.r)])
+    else:
+        real = ffconv.dp_dp_sum_steps
+        monkeypatch.setattr(ffconv, "dp_dp_sum_steps", lambda l: real(l)[:-1])
+    prm, s, lay, outs, y2, ops = run_he(prm, lay, seed=2)
+    with pytest.raises(AssertionError):
+        check_outputs(prm, s, lay, outs, y2)
