@@ -1,0 +1,46 @@
+"""The benchmark's bookkeeping on the CPU: the algorithmic byte and product counts behind the
+roofline figures, the derived integer-multiply peak, and the aggregate rate of replicas."""
+import argparse
+
+import pytest
+
+import bench
+
+N, L, K, DNUM = 1 << 15, 12, 3, 4          # the bench ring: 12 + 3 primes, digits of 3 primes
+
+
+def test_layer_algorithmic_bytes():
+    # 24 Galois keys of [4 digits][2][15 limbs][N] words, 64 inputs and 64 x 5 outputs of
+    # [2][12][N] words, 8 bytes a word
+    keys = 24 * 4 * 2 * 15 * N * 8
+    ct = 2 * 12 * N * 8
+    assert keys == 754_974_720 and ct == 6_291_456
+    assert bench.layer_algorithmic_bytes(64, 5, 24) == keys + 64 * ct + 64 * 5 * ct == 3_170_893_824
+
+
+def test_tap_kernel_products_and_roofline():
+    # per image, limb of Q u P and coefficient: 2 dnum = 8 products for each of the 24 rotated
+    # taps and 2 r = 4 for each of the 25 taps: 292
+    args = argparse.Namespace(pack="dp_shift_ext")
+    roof = bench.taps_roofline({"taps": (8.6513, 1)}, args, 64, 24)
+    assert roof["products_per_launch"] == 64 * N * 15 * 292 == 9_185_525_760
+    assert roof["launch_us"] == pytest.approx(8651.3)
+    assert roof["achieved"] == pytest.approx(9_185_525_760 / 8.6513e-3 / 1e12)
+    assert roof["frac"] == pytest.approx(roof["achieved"] / roof["peak"])
+    assert roof["traffic"] == 3_415_376_896 + 990_737_152
+    assert bench.taps_roofline({"taps": (1.0, 1)}, argparse.Namespace(pack="dp_shift"), 64, 24) is None
+
+
+def test_integer_peak():
+    # 152 SMs x 64 multiply-adds per clock / 8 per 64 x 64 -> 128-bit product x 2070 MHz
+    assert bench.mul64_peak_per_s(2070.0) == pytest.approx(2.51712e12)
+
+
+def test_whole_job_rate_is_the_sum_over_replicas():
+    # every rank does the same units; the time is the slowest rank's
+    assert bench.whole_job_rate(64 * 24 * 100, 4, 1588.4) == pytest.approx(4 * 64 * 24 * 100 / 1.5884)
+
+
+def test_workload_name_names_the_packing():
+    assert "dp_shift_ext" in bench.workload_name(argparse.Namespace(pack="dp_shift_ext"))
+    assert "N=2^15" in bench.workload_name(argparse.Namespace(pack="dp_dot"))
