@@ -42,3 +42,28 @@ def test_binding_refuses_to_run_without_gpu(libhe):
         pytest.skip("a GPU is present")
     with pytest.raises(RuntimeError):
         libhe.Context(log_n=10, n_q=2, n_p=1, alpha=1)
+
+
+def header_constants():
+    """Every NAME = value inside the header's enums and its #define'd int32 constants."""
+    text = open(os.path.join(ROOT, "include", "he.h")).read()
+    out = {}
+    for body in re.findall(r"enum\s*\{([^}]*)\}", text):
+        for name, val in re.findall(r"(HE_[A-Z0-9_]+)\s*=\s*(-?\d+)", body):
+            out[name] = int(val)
+    for name, val in re.findall(r"#define\s+(HE_[A-Z0-9_]+)\s+\(\(int32_t\)(0x[0-9a-fA-F]+)\)", text):
+        v = int(val, 16)
+        out[name] = v - (1 << 32) if v >= 1 << 31 else v
+    return out
+
+
+def test_binding_constants_match_the_header(libhe):
+    consts = header_constants()
+    assert {"HE_OK", "HE_ETIMEOUT", "HE_NTT", "HE_DP_DP", "HE_ROW_SWAP", "HE_RELIN_KEY"} <= set(consts)
+    for name, val in consts.items():
+        if name.startswith("HE_PHASE_") or name == "HE_N_PHASES":
+            continue
+        assert getattr(libhe, name) == val, name
+    # phase indices: the binding's names follow the header's order
+    phases = sorted((v, n) for n, v in consts.items() if n.startswith("HE_PHASE_"))
+    assert [n[len("HE_PHASE_"):].lower() for _, n in phases] == list(libhe.Context.PHASES[:len(phases)])
