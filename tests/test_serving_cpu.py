@@ -1,7 +1,8 @@
 """The serving scheduler's host logic with a fake executor and a fake clock (no GPU): every
-request completes, admission never exceeds the memory budget, batches hold one ring and at
-most max_batch requests, each ring is served oldest first, and requests that arrive while a
-batch runs are batched into the next one."""
+request completes, admission never exceeds the memory budget (a request larger than the
+whole budget is refused), batches hold one ring and at most max_batch requests, no ring runs
+more batches than it has workers, each ring is served oldest first, requests that arrive
+while a batch runs are batched into the next one, and arrivals are seeded."""
 from paper_2102_03494_gb300.serving import Request, Scheduler, latency_stats, poisson_arrivals
 
 
@@ -82,3 +83,37 @@ def test_continuous_batching_picks_up_late_arrivals():
     assert joined_late > 0
     stats = latency_stats(done)
     assert stats["requests"] == 200 and stats["p99_ms"] >= stats["p50_ms"] > 0
+
+
+def test_a_request_larger_than_the_budget_is_refused():
+    import pytest
+    clock, log = Clock(), []
+    rings = {"large": FakeRing("large", 1, 0.05, 400, clock, log)}
+    sched = Scheduler(rings, max_batch=4, memory_budget=300, clock=clock)
+    with pytest.raises(ValueError):
+        sched.submit(Request(rid=0, ring="large", t_arrive=0.0))
+
+
+def test_no_ring_runs_more_batches_than_it_has_workers():
+    done, log, peak, sched = run()
+    durations = {"small": 0.02, "large": 0.05}
+    workers = {"small": 2, "large": 1}
+    for ring in ("small", "large"):
+        spans = [(t, t + durations[ring]) for (r, w, rids, t) in log if r == ring]
+        for t0, _ in spans:
+            running = sum(1 for a, b in spans if a <= t0 < b)
+            assert running <= workers[ring], (ring, t0, running)
+        # each worker index is used by at most one batch at a time
+        for w in range(workers[ring]):
+            mine = sorted(t for (r, ww, rids, t) in log if r == ring and ww == w)
+            assert all(b - a >= durations[ring] - 1e-9 for a, b in zip(mine, mine[1:]))
+
+
+def test_poisson_arrivals_are_seeded_and_follow_the_mix():
+    a = poisson_arrivals(seed=7, rate=100.0, count=2000, mix={"x": 0.6, "y": 0.4})
+    b = poisson_arrivals(seed=7, rate=100.0, count=2000, mix={"x": 0.6, "y": 0.4})
+    assert [(r.ring, r.t_arrive) for r in a] == [(r.ring, r.t_arrive) for r in b]
+    share = sum(r.ring == "x" for r in a) / len(a)
+    assert 0.55 < share < 0.65
+    mean_gap = a[-1].t_arrive / len(a)
+    assert 0.009 < mean_gap < 0.011                  # rate 100 per second
