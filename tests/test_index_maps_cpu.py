@@ -1,0 +1,54 @@
+"""The index map the kernels use for the automorphism in the NTT domain, restated here and
+checked against the oracle (CPU, no GPU).
+
+The library's forward NTT leaves position p holding a(psi^(2 brv(p) + 1)).  X -> X^g then
+moves the value at odd power e to e g mod 2N, so the rotated polynomial's position p reads the
+input's position perm_g(p) = brv(((2 brv(p) + 1) g mod 2N - 1) / 2) (perm_of / perm_src in the
+CUDA sources).  The fused tap kernel also relies on perm_g mapping every aligned block of 2^k
+positions onto one aligned block of 2^k positions."""
+import numpy as np
+import pytest
+
+from oracle import bfv, params, ring
+
+
+def brv(x, bits):
+    return int(format(x, f"0{bits}b")[::-1], 2) if bits else 0
+
+
+def perm(p, g, log_n):
+    n2 = 2 << log_n
+    e = (2 * brv(p, log_n) + 1) * g % n2
+    return brv((e - 1) // 2, log_n)
+
+
+def galois_elements(log_n):
+    n = 1 << log_n
+    return [pow(5, k, 2 * n) for k in (1, 2, 3, 7, n // 2 - 1)] + [2 * n - 1]
+
+
+@pytest.mark.parametrize("log_n", [4, 6, 9])
+def test_perm_matches_the_oracle_automorphism_in_the_ntt_domain(log_n):
+    prm = params.Params(log_n=log_n, n_q=1, n_p=1, alpha=1)
+    q, n = prm.q[0], prm.n
+    rng = np.random.default_rng(log_n)
+    a = rng.integers(0, q, n, dtype=np.uint64)
+    order = [brv(p, log_n) for p in range(n)]
+    x = ring.neg_eval(a, q, prm.psi[q])[order]           # NTT order: position p
+    for g in galois_elements(log_n):
+        b = bfv.automorphism(a[None, :], g, [q])[0]
+        y = ring.neg_eval(b, q, prm.psi[q])[order]
+        assert (y == x[[perm(p, g, log_n) for p in range(n)]]).all(), g
+
+
+@pytest.mark.parametrize("log_n", [4, 7, 10])
+def test_perm_maps_aligned_blocks_onto_aligned_blocks(log_n):
+    n = 1 << log_n
+    for g in galois_elements(log_n):
+        pm = [perm(p, g, log_n) for p in range(n)]
+        assert sorted(pm) == list(range(n))                  # a permutation
+        for k in range(log_n + 1):
+            size = 1 << k
+            for a0 in range(0, n, size):
+                blocks = {pm[p] // size for p in range(a0, a0 + size)}
+                assert len(blocks) == 1, (g, k, a0)
