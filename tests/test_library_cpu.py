@@ -67,3 +67,7 @@ def test_binding_constants_match_the_header(libhe):
     # phase indices: the binding's names follow the header's order
     phases = sorted((v, n) for n, v in consts.items() if n.startswith("HE_PHASE_"))
     assert [n[len("HE_PHASE_"):].lower() for _, n in phases] == list(libhe.Context.PHASES[:len(phases)])
+
+
+def test_binding_declares_a_signature_for_every_entry_point(libhe):
+    assert set(libhe._SIGS) == set(declared_entry_points())
