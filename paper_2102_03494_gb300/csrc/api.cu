@@ -4,6 +4,7 @@
 // 2N-th root of a modulus m is x^((m-1)/2N) for the smallest quadratic non-residue x (for
 // the plaintext modulus this root fixes the slot encoding).  Error sampler table: exact
 // 128-bit fixed point (120 fractional bits).
+#include <nvtx3/nvToolsExt.h>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -588,7 +589,13 @@ extern "C" void he_gaussian_table(uint64_t out[20]) { he_cdt_compute(out); }
 
 extern "C" uint64_t he_launch_count(const he_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
+static const char* const kPhaseNames[HE_N_PHASES] = {"encode", "modup", "taps", "moddown",
+                                                     "rotate", "restore", "multiply", "phase7"};
+
 void phase_begin(he_ctx* ctx, int phase) {
+    if (ctx->nvtx_open) nvtxRangeEnd(ctx->nvtx_id);       // a phase left by an error return
+    ctx->nvtx_id = nvtxRangeStartA(phase >= 0 && phase < HE_N_PHASES ? kPhaseNames[phase] : "phase");
+    ctx->nvtx_open = true;
     if (!ctx->timing) return;
     he_ctx::PhaseSpan sp{phase, nullptr, nullptr};
     for (cudaEvent_t* e : {&sp.a, &sp.b}) {
@@ -605,6 +612,10 @@ void phase_begin(he_ctx* ctx, int phase) {
 }
 
 void phase_end(he_ctx* ctx) {
+    if (ctx->nvtx_open) {
+        nvtxRangeEnd(ctx->nvtx_id);
+        ctx->nvtx_open = false;
+    }
     if (!ctx->timing || ctx->spans.empty()) return;
     cudaEventRecord(ctx->spans.back().b, ctx->stream);
 }

@@ -220,6 +220,10 @@ struct he_ctx {
     Staging staging;
     uint64_t ops[4] = {0, 0, 0, 0};     // MulPC, AddCC, Rot, KeySwitch
     uint64_t launches = 0;              // kernels launched by this context
+    // NVTX range of the phase in progress (shown by profilers that record NVTX; a no-op
+    // otherwise)
+    uint64_t nvtx_id = 0;
+    bool nvtx_open = false;
     // optional per-phase timing (CUDA events on the context stream, summed on request)
     bool timing = false;
     struct PhaseSpan {
