@@ -277,6 +277,8 @@ def run(args):
     ctx.he_set_phase_timing(False)
     launches = ctx.he_launch_count() - l0
     ms = ev0.elapsed_time(ev1)
+    ctx.he_check()                        # raises if a bounded device wait ran out
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
 
     # end to end through the same API with host buffers: every step copies its encrypted
     # inputs host -> device from pinned memory, runs the layer and copies every output
@@ -378,7 +380,7 @@ def run(args):
     ctx.he_graph_free(gid)
     ctx.he_ffconv_plan_free(plan)
 
-    roof = taps_roofline(phases, args, B, n_rot)
+    roof = taps_roofline(phases, args, B, n_rot, sms)
     if roof is not None:          # the measured multiply-accumulate rate, for context
         chain, cols = ctx.he_probe_int_mac()
         roof["probe_mul64_per_s"] = {"carry_chain_T": chain / 1e12, "column_sums_T": cols / 1e12,
@@ -468,20 +470,21 @@ def measured_peaks():
 
 
 # DRAM bytes (read + write) of one k_ks_mac_ext launch, from one ncu capture of the current
-# kernel version at the bench shape (profiles/k_ks_mac_ext_n15.md); cleared when the kernel
-# changes and until it is captured again.
+# kernel version at the bench shape; cleared when the kernel changes and until it is captured
+# again.
 KS_MAC_EXT_TRAFFIC = {64: 3415376896 + 990737152}
 
 
-# 64 x 64 -> 128-bit products per second of the GPU's integer multiplier: 152 SMs x 64 32-bit
-# multiply-adds per clock x clock / 8.  A 64 x 64 -> 128-bit product is four 32 x 32 -> 64-bit
-# partial products, and each of those is two multiply-add instructions (its low and its high
-# word), so it takes at least 8 of the SM's 64 multiply-add issue slots per clock.
-def mul64_peak_per_s(sm_mhz):
-    return 152 * 64 / 8 * sm_mhz * 1e6
+# 64 x 64 -> 128-bit products per second of the GPU's integer multiplier: SMs (152 on GB300)
+# x 64 32-bit multiply-adds per clock x clock / 8.  A 64 x 64 -> 128-bit product is four
+# 32 x 32 -> 64-bit partial products, and each of those is two multiply-add instructions (its
+# low and its high word), so it takes at least 8 of the SM's 64 multiply-add issue slots per
+# clock.
+def mul64_peak_per_s(sm_mhz, sms=152):
+    return sms * 64 / 8 * sm_mhz * 1e6
 
 
-def taps_roofline(phases, args, B, n_rot):
+def taps_roofline(phases, args, B, n_rot, sms=152):
     """Roofline of the dominant kernel, the extended-basis tap MAC (k_ks_mac_ext), from its
     CUDA-event time inside the timed region.  Algorithmic work: per image, ciphertext-basis
     limb and coefficient, 2 dnum products for the key inner product of each rotated tap and
@@ -493,14 +496,14 @@ def taps_roofline(phases, args, B, n_rot):
     products = B * N * LK * (n_rot * 2 * dnum + taps * 2 * r)
     sec = ms / 1000.0 / spans
     pk = measured_peaks()
-    peak = mul64_peak_per_s(pk["sm_max_mhz"]) / 1e12
+    peak = mul64_peak_per_s(pk["sm_max_mhz"], sms) / 1e12
     achieved = products / sec / 1e12
     return {"kernel": "k_ks_mac_ext", "bound": "alu", "achieved": achieved, "peak": peak,
             "unit": "T mul64/s", "frac": achieved / peak,
             "traffic": KS_MAC_EXT_TRAFFIC.get(B) if args.pack == "dp_shift_ext" else None,
             "launch_us": sec * 1e6, "products_per_launch": products,
-            "peak_note": "152 SMs x 64 IMAD/clk / 8 per 64x64->128-bit product (4 partial "
-                         "products, low and high word each) x max SM clock of "
+            "peak_note": f"{sms} SMs (device attribute) x 64 IMAD/clk / 8 per 64x64->128-bit "
+                         "product (4 partial products, low and high word each) x max SM clock of "
                          f"MEASURED_PEAKS ({pk['src']})"}
 
 

@@ -35,7 +35,9 @@ enum {
     HE_ENOMEM = -2,   /* device allocation failed */
     HE_ENOKEY = -3,   /* a rotation needs a Galois key that is not loaded */
     HE_ECUDA = -4,    /* a CUDA call or kernel launch failed */
-    HE_ETIMEOUT = -5  /* a bounded device-side wait ran out (reported by the next call) */
+    HE_ETIMEOUT = -5  /* a bounded device-side wait ran out: reported by he_check and by the
+                         synchronising calls that check the device error word (he_decrypt,
+                         he_phase_times, he_ffconv_graph_create) */
 };
 
 enum { HE_COEFF = 0, HE_NTT = 1 };            /* representation of a ciphertext's limbs */
@@ -175,7 +177,9 @@ int he_rotate(he_ctx* ctx, const he_ct* in, int32_t step, he_ct* out);
  * primes; larger parameter sets are rejected with HE_EINVAL and a message giving the size
  * needed).  The first call on a device looks up the array's device address, so make it
  * before any stream capture.  All calls share the array: calls that overlap on the GPU race
- * on it and must be serialised by the caller.  Calls cudaMalloc/cudaFree never. */
+ * on it and must be serialised by the caller.  Calls cudaMalloc/cudaFree never; refused
+ * (HE_EINVAL) while a graph is being recorded, because recording would allocate the graph's
+ * own pointer tables. */
 int he_rotate_noalloc(he_ctx* ctx, const he_ct* in, int32_t step, he_ct* out);
 /* The same rotation applied to n ciphertexts in one batch (one key read per launch). */
 int he_rotate_batch(he_ctx* ctx, const he_ct* in, int n, int32_t step, he_ct* out);
@@ -390,6 +394,22 @@ int he_deep_batch(he_ctx* ctx, const he_ct* in, int B, const he_mc_conv* convs, 
  * more digits (else 256), split log2 N1 = floor(log2 N / 2).  Uses the context scratch;
  * synchronises the stream. */
 int he_autotune(he_ctx* ctx, int batch, int force_tile, double* ms_out);
+
+/* ---- failure detection ------------------------------------------------------------ */
+
+/* Waits for the context's stream, then reports HE_ECUDA if a kernel failed, HE_ETIMEOUT if a
+ * bounded device-side wait of a kernel enqueued since the last check ran out (the results of
+ * that work are unusable; the error word is cleared, so the next check starts afresh), else
+ * HE_OK.  The only device-side waits are the fused tap kernel's waits on its shared-memory
+ * stages (he_ffconv_layer with HE_DP_SHIFT_EXT and the network and multi-ciphertext calls
+ * built on it).  Refused while recording.  Synchronous. */
+int he_check(he_ctx* ctx);
+/* Test hook for the path above (no counterpart in the paper): the fused tap kernel's compute
+ * warps report their wait for a stage's operands (error bit set) once it has polled `polls`
+ * times, then keep waiting up to the full bound (2^20 polls), so copies and results stay in
+ * step and only the report is forced.  polls = 0 reports every such wait; polls < 0 restores
+ * the default (reports only at the full bound).  Refused while recording. */
+int he_set_wait_report(he_ctx* ctx, int polls);
 
 /* ---- primitives for measurement --------------------------------------------------- */
 

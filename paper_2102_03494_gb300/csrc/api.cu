@@ -239,6 +239,13 @@ int check_device_error(he_ctx* ctx) {
     return HE_OK;
 }
 
+extern "C" int he_check(he_ctx* ctx) {
+    if (!ctx) return HE_EINVAL;
+    HE_NOT_RECORDING(ctx, "he_check");
+    HE_CHECK_CUDA(ctx, cudaGetLastError());
+    return check_device_error(ctx);
+}
+
 int he_launch_check(he_ctx* ctx, const char* what) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)

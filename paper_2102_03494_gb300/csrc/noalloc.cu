@@ -50,6 +50,9 @@ static size_t align_words(size_t n) { return (n + 31) & ~(size_t)31; }   // 256-
 
 extern "C" int he_rotate_noalloc(he_ctx* ctx, const he_ct* in, int32_t step, he_ct* out) {
     if (!ctx) return HE_EINVAL;
+    // while a graph is recorded the pointer tables below would go to buffers the graph
+    // allocates, and a replay would share the static array with later calls: refused
+    HE_NOT_RECORDING(ctx, "he_rotate_noalloc");
     int rc = check_ct(ctx, in, ctx->L, HE_NTT, "he_rotate_noalloc input");
     if (!rc) rc = check_ct(ctx, out, ctx->L, -1, "he_rotate_noalloc output");
     if (rc) return rc;

@@ -56,8 +56,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return done != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kWaitSpins; ++i)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          uint32_t polls = kWaitSpins) {
+    for (uint32_t i = 0; i < polls; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -172,7 +173,8 @@ __global__ void __launch_bounds__(TILE + 32, min_ctas(DNUM, TILE))
 k_ks_mac_ext_bulk(const uint64_t* __restrict__ D, const uint64_t* __restrict__ XPg,
                   const uint64_t* __restrict__ pts, TapTable tt, int c_lo, int c_cnt, int B,
                   uint64_t* __restrict__ A, int L, int K, int logN,
-                  const ModConst* __restrict__ mods, int* __restrict__ err) {
+                  const ModConst* __restrict__ mods, int* __restrict__ err,
+                  uint32_t report_polls) {
     using S = Stage<DNUM, TILE>;
     constexpr int kTile = S::T;
     constexpr int kComputeWarps = kTile / 32;
@@ -224,7 +226,12 @@ k_ks_mac_ext_bulk(const uint64_t* __restrict__ D, const uint64_t* __restrict__ X
         for (int t = 0; t < tt.n; ++t) {
             const int s = t % kStages;
             const uint64_t* st = smem + s * S::WORDS;
-            ok &= mbar_wait(&full[s], (uint32_t)(t / kStages) & 1u);
+            // a wait longer than report_polls is reported (error bit) and then goes on with
+            // the full bound, so the warp stays in step with the producer's stages
+            if (!mbar_wait(&full[s], (uint32_t)(t / kStages) & 1u, report_polls)) {
+                ok = false;
+                mbar_wait(&full[s], (uint32_t)(t / kStages) & 1u);
+            }
             uint64_t x[2][2];
             if (!tt.key[t]) {
 #pragma unroll
@@ -322,7 +329,8 @@ void launch_bulk(he_ctx* c, const uint64_t* D, const uint64_t* XP, const uint64_
     }
     const dim3 grid((B + 1) / 2, c->N / TILE, c->L + c->K);
     k_ks_mac_ext_bulk<DNUM, TILE><<<grid, TILE + 32, smem, c->stream>>>(
-        D, XP, pts, tt, c_lo, cnt, B, A, c->L, c->K, c->logN, c->d_mod, c->d_err);
+        D, XP, pts, tt, c_lo, cnt, B, A, c->L, c->K, c->logN, c->d_mod, c->d_err,
+        c->wait_report >= 0 ? (uint32_t)c->wait_report : kWaitSpins);
 }
 
 template <int TILE>
@@ -470,4 +478,11 @@ extern "C" int he_autotune(he_ctx* ctx, int batch, int force_tile, double* ms_ou
         ms_out[1] = ms[1];
     }
     return he_launch_check(ctx, "he_autotune");
+}
+
+extern "C" int he_set_wait_report(he_ctx* ctx, int polls) {
+    if (!ctx) return HE_EINVAL;
+    HE_NOT_RECORDING(ctx, "he_set_wait_report");
+    ctx->wait_report = polls < 0 ? -1 : polls;
+    return HE_OK;
 }

@@ -91,6 +91,8 @@ _SIGS = {
     "he_net_required_steps": ([_P, ctypes.POINTER(HeNet), _I32P, ctypes.c_int], ctypes.c_int),
     "he_autotune": ([_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "he_probe_int_mac": ([_P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "he_check": ([_P], ctypes.c_int),
+    "he_set_wait_report": ([_P, ctypes.c_int], ctypes.c_int),
     "he_mc_conv_batch": ([_P, _CTP, ctypes.c_int, _I32P, _I32P, ctypes.POINTER(HeMcConv), _CTP],
                          ctypes.c_int),
     "he_rotate_sum_batch": ([_P, _CTP, ctypes.c_int, _I32P, ctypes.c_int], ctypes.c_int),
@@ -419,6 +421,15 @@ class Context:
         out = (ctypes.c_double * 2)()
         self._ck(lib().he_probe_int_mac(self.h, out), "he_probe_int_mac")
         return float(out[0]), float(out[1])
+
+    def he_check(self):
+        """Wait for the stream; raise HeError (HE_ETIMEOUT) if a bounded device wait ran out
+        since the last check, or HE_ECUDA if a kernel failed."""
+        self._ck(lib().he_check(self.h), "he_check")
+
+    def he_set_wait_report(self, polls):
+        """Test hook: polls before the tap kernel reports a stage wait (-1: the default)."""
+        self._ck(lib().he_set_wait_report(self.h, int(polls)), "he_set_wait_report")
 
     # ---- deeper networks (several ciphertexts per tensor)
     @staticmethod

@@ -230,7 +230,7 @@ class GpuRing:
                 res = [o.clone() for o in outs] if self.keep_results else None
                 ev = torch.cuda.Event()
                 ev.record(self.streams[worker])
-            return (ev, res)
+            return (ev, res, worker)
         with torch.cuda.stream(self.streams[worker]):
             # allocated (and zero-filled) on the worker's stream, ordered before the layer
             outs = [ctx.new_ct() for _ in range(len(requests) * self.O_c)]
@@ -238,12 +238,14 @@ class GpuRing:
                                         outs)
             ev = torch.cuda.Event()
             ev.record(self.streams[worker])
-        return (ev, outs)
+        return (ev, outs, worker)
 
     def done(self, handle):
         return handle[0].query()
 
     def results(self, handle, requests):
+        # the worker's stream is idle here: report a device wait that ran out (HE_ETIMEOUT)
+        self.ctx[handle[2]].he_check()
         outs = handle[1]
         for i, r in enumerate(requests):
             r.result = outs[i * self.O_c:(i + 1) * self.O_c] if self.keep_results else None
@@ -377,12 +379,13 @@ class _NetWorkers:
                 self._call(ctx, cts, outs)
             ev = torch.cuda.Event()
             ev.record(self.streams[worker])
-        return (ev, outs)
+        return (ev, outs, worker)
 
     def done(self, handle):
         return handle[0].query()
 
     def results(self, handle, requests):
+        self.ctx[handle[2]].he_check()           # as GpuRing.results
         for i, r in enumerate(requests):
             r.result = [handle[1][i]] if self.keep_results else None
 

@@ -54,3 +54,24 @@ def test_rotate_noalloc_refuses_parameters_beyond_its_scratch():
     with pytest.raises(he.HeError) as e:
         ctx.he_rotate_noalloc(ct, 1, ctx.new_ct())
     assert e.value.code == he.HE_EINVAL and "bytes of scratch" in str(e.value)
+
+
+def test_rotate_noalloc_is_refused_while_recording():
+    """Recording would give the graph pointer tables of its own (allocated) and a replay would
+    share the static array with later calls, so the entry point refuses to be recorded."""
+    from paper_2102_03494_gb300 import he
+    from tests.gpu_common import make_ctx
+
+    prm = params.cfg_small_layer()
+    ctx = make_ctx(prm)
+    sk = ctx.he_keygen_secret(5)
+    ctx.he_keygen_galois(sk, 6, [3])
+    ct = ctx.he_encrypt(sk, np.zeros(prm.n, dtype=np.int64), 3)
+    out = ctx.new_ct()
+    ctx.he_rotate_noalloc(ct, 3, out)          # the first call (address set-up) before recording
+    ctx.he_graph_begin(share_scratch=True)
+    a, b = ctx.ct_struct(ct), ctx.ct_struct(out)
+    rc = he.lib().he_rotate_noalloc(ctx.h, ctypes.byref(a), 3, ctypes.byref(b))
+    assert rc == he.HE_EINVAL and b"recording" in he.lib().he_last_error(ctx.h)
+    with pytest.raises(he.HeError):            # the refusal spoils the recording
+        ctx.he_graph_end()
