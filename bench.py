@@ -38,6 +38,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--pack", default="dp_shift_ext", choices=["dp_shift", "dp_shift_ext", "dp_dot"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-baseline-child", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the short network runs reported under 'also'")
     ap.add_argument("--serving-layers", action="store_true",
@@ -79,22 +80,81 @@ def dist_env():
 
 # ---------------------------------------------------------------- CPU oracle sample
 
-def oracle_sample(n_steps=2, seed=0):
-    """Time the oracle's hoisted rotations of one ciphertext at the bench's ring (one ModUp,
-    n_steps key switches).  Returns (seconds, rotations, description)."""
-    import numpy as np
-    from oracle import bfv, encoder, params
+_ORACLE = {}
+
+
+def _oracle_layer_setup():
+    """Per-process, untimed set-up of the oracle's layer: the ring, the secret and the layer's
+    24 Galois keys (seeds of rank 0's GPU arm), the weights."""
+    from oracle import bfv, ffconv, params
+    from paper_2102_03494_gb300 import workloads
+    if _ORACLE:
+        return _ORACLE
     prm = params.Params(log_n=LOG_N, n_q=N_Q, n_p=N_P, alpha=ALPHA)
-    s = bfv.keygen_secret(prm, seed + 1)
-    steps = [1, 28][:n_steps]
-    keys = {bfv.galois_of(st, prm.n): bfv.galois_key(prm, s, bfv.galois_of(st, prm.n), seed + 2)
-            for st in steps}
-    v = np.random.default_rng(seed).integers(0, prm.t, prm.n)
-    ct = bfv.encrypt(prm, s, encoder.encode(v, prm), seed + 3)
+    shape = workloads.MNIST_LAYER
+    lay = ffconv.Layout(*shape.astuple(), pack="dp_shift_ext")
+    s = bfv.keygen_secret(prm, 1000)
+    steps = ffconv.required_steps(lay, prm.n)
+    keys = {}
+    for st in steps:
+        g = bfv.galois_of(st, prm.n)
+        keys[g] = bfv.galois_key(prm, s, g, 2000)
+    W1, W2 = workloads.weights(0, shape)
+    _ORACLE.update(prm=prm, shape=shape, lay=lay, s=s, keys=keys, W1=W1, W2=W2, n_rot=len(steps))
+    return _ORACLE
+
+
+def oracle_layer_step(i):
+    """One image's encrypted FFConv layer by the oracle, under the GPU arm's schedule
+    (DP_SHIFT_EXT at N = 2^15, 12 + 3 primes): image i of the GPU arm's batch, encrypted
+    (untimed), then the layer timed.  Returns (seconds, hoisted rotations of the image)."""
+    from oracle import bfv, encoder, ffconv
+    from paper_2102_03494_gb300 import workloads
+    o = _oracle_layer_setup()
+    prm, lay = o["prm"], o["lay"]
+    x = workloads.images(0, o["shape"], 64)[i % 64]
+    ct = bfv.encrypt(prm, o["s"], encoder.encode(ffconv.input_slots(x, lay, prm.n), prm), 3000 + i % 64)
     t0 = time.perf_counter()
-    bfv.rotate_hoisted(prm, ct, steps, keys)
-    dt = time.perf_counter() - t0
-    return dt, len(steps), f"oracle hoisted rotation of 1 ciphertext by {len(steps)} steps at N=2^15, L=12, K=3"
+    ffconv.he_layer(prm, ct, o["W1"], o["W2"], lay, o["keys"])
+    return time.perf_counter() - t0, o["n_rot"]
+
+
+ORACLE_UNIT_DESC = ("the oracle's encrypted FFConv layer of one image under the same schedule "
+                    "(DP_SHIFT_EXT: ModUp, 24 hoisted rotations key-switched in Q u P, 50 tap "
+                    "plaintext products, ModDown per channel, ConvPack restore), N=2^15, L=12, K=3, "
+                    "the GPU arm's inputs and seeds")
+
+
+def cpu_baseline_child():
+    """The single-core baseline, run in its own process (started before the GPU work and
+    overlapping it on another host core): one image's layer, timed once."""
+    dt, n = oracle_layer_step(0)
+    print(json.dumps({"seconds": dt, "rotations": n}))
+
+
+def start_cpu_baseline():
+    """Starts cpu_baseline_child on one host core; returns the process (or None)."""
+    try:
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1")
+        return subprocess.Popen([sys.executable, os.path.abspath(__file__), "--cpu-baseline-child"],
+                                stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env)
+    except OSError:
+        return None
+
+
+def finish_cpu_baseline(proc, timeout=900):
+    if proc is None:
+        return {"error": "could not start the oracle process"}
+    try:
+        out, err = proc.communicate(timeout=timeout)
+        rec = json.loads(out.strip().splitlines()[-1])
+    except Exception as e:                 # noqa: BLE001 -- reported in the line
+        proc.kill()
+        return {"error": f"{type(e).__name__}: {e}"[:300]}
+    return {"value": rec["rotations"] / rec["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "ms_per_image": 1000.0 * rec["seconds"],
+            "sample": ORACLE_UNIT_DESC + "; one image, run once on one host core (key generation "
+                      "and encryption untimed), overlapping the GPU arm on another core"}
 
 
 def copy_bandwidth(stream, nbytes=1 << 29):
@@ -122,15 +182,21 @@ def workload_name(args):
             "N=2^15, 12x50-bit q, 3x60-bit p, alpha=3")
 
 
-def _reference_sample(i):
-    """One reference step: the oracle's hoisted rotation of one ciphertext (seeded by i)."""
-    return oracle_sample(n_steps=1, seed=i)
+def _reference_init():
+    """Pool initializer: the untimed per-worker set-up (keys), before any step."""
+    _oracle_layer_setup()
+
+
+def _reference_step(i):
+    return oracle_layer_step(i)
 
 
 def run_reference(args):
-    """The CPU oracle as it stands, one sample per step, the samples spread over the host's
-    cores (a spawned process pool; no GPU is touched).  value = the aggregate rate of those
-    cores: rotations / (sum of the samples' rotation times / workers)."""
+    """The CPU oracle as it stands, on the GPU arm's unit: every step is one image's encrypted
+    FFConv layer (DP_SHIFT_EXT, N = 2^15), the steps spread over the host's cores by a spawned
+    process pool (no GPU is touched).  Each worker generates its keys before the warm-up; the
+    warm-up runs one layer on every worker; the timed region is the wall time of the K steps.
+    value = 24 K / wall, ms_per_step = wall / K."""
     import multiprocessing as mp
     rank, _, world = dist_env()
     if rank != 0:
@@ -140,27 +206,29 @@ def run_reference(args):
     except AttributeError:
         avail = os.cpu_count() or 1
     workers = max(1, min(16, avail, args.steps))
-    with mp.get_context("spawn").Pool(workers) as pool:
-        pool.map(_reference_sample, range(args.warmup), chunksize=1)
+    with mp.get_context("spawn").Pool(workers, initializer=_reference_init) as pool:
+        # at least one warm-up layer per worker (one wave: they run side by side)
+        pool.map(_reference_step, range(max(args.warmup, workers)), chunksize=1)
         t0 = time.perf_counter()
-        res = pool.map(_reference_sample, range(args.warmup, args.warmup + args.steps), chunksize=1)
+        res = pool.map(_reference_step, range(args.steps), chunksize=1)
         wall = time.perf_counter() - t0
-    rots = sum(n for _, n, _ in res)
-    busy = sum(dt for dt, _, _ in res)
-    value = rots * workers / busy
-    desc = res[0][2]
+    rots = sum(n for _, n in res)
+    value = rots / wall
+    per_image = statistics.mean(dt for dt, _ in res)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * busy / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * wall / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
             "config": {"workload": workload_name(args), "batch_per_gpu": args.batch,
                        "parallelism": f"replicas x{world} (rank 0 times the oracle)",
-                       "sample": "each step: the oracle's hoisted rotation of one layer input "
-                                 "(one ModUp, one key switch), the unit the metric counts"},
+                       "same_config": True,
+                       "sample": "each step: " + ORACLE_UNIT_DESC,
+                       "ms_per_image": 1000.0 * per_image,
+                       "workers": workers},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
-                             "sample": f"{desc}, {args.steps} samples on {workers} host cores "
-                                       f"(rotation time only; {wall:.1f} s wall with key generation "
-                                       "and encryption of each sample)"},
+                             "sample": f"{args.steps} steps of {ORACLE_UNIT_DESC}, on {workers} host "
+                                       f"cores side by side ({wall:.1f} s wall; "
+                                       f"{1000.0 * per_image:.0f} ms per image per core)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -221,6 +289,8 @@ def run(args):
     from paper_2102_03494_gb300 import he, workloads
 
     rank, local, world = dist_env()
+    # the single-core oracle baseline runs beside the GPU work, started before any GPU call
+    cpu_proc = start_cpu_baseline() if world == 1 and not args.no_cpu_baseline else None
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -248,7 +318,8 @@ def run(args):
         slots[: x.size] = x.reshape(-1)
         cts.append(ctx.he_encrypt(sk, slots, 3000 + b))
     outs = [ctx.new_ct() for _ in range(B * shape.O_c)]
-    tile_ms = ctx.he_autotune(B)          # untimed: picks the tap-kernel tile for this batch
+    tuned = ctx.he_autotune(B)            # untimed: picks the NTT split and the tap kernel's
+                                          # tile and arithmetic for this batch
     torch.cuda.synchronize()
 
     def layer():
@@ -403,9 +474,7 @@ def run(args):
                        "layer_ms_per_image": ms / args.steps / B, "hoisted_rotations_per_image": n_rot,
                        "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (keys 755 MB + ModUp digits per step)",
-                       "autotune": {"tap_tile_ms": {"128": tile_ms[0], "256": tile_ms[1]},
-                                    "tap_tile": 128 if tile_ms[0] <= tile_ms[1] else 256,
-                                    "ntt_log2_n1": tile_ms[3], "ntt_ms": tile_ms[2]}},
+                       "autotune": tuned},
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": B * ct_bytes,
                     "d2h_bytes_per_step": B * shape.O_c * ct_bytes, "ms_per_step": ms_e2e / args.steps,
                     "note": "pinned host buffers, one copy per direction and step; copies of "
@@ -428,10 +497,8 @@ def run(args):
                           "frac": layer_bytes / (ms / args.steps / 1000.0) / 1e9 / peaks["hbm_gbs"],
                           "note": "keys read once per batch + input and output ciphertexts; "
                                   "the layer is bound by 64-bit modular products, not HBM"}}
-    if world == 1 and not args.no_cpu_baseline:
-        dt, n, desc = oracle_sample(n_steps=2)
-        line["cpu_baseline"] = {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": desc}
+    if cpu_proc is not None:
+        line["cpu_baseline"] = finish_cpu_baseline(cpu_proc)
     if world == 1 and not args.no_extra:
         line["also"] = extra_workloads()
     print(json.dumps(line))
@@ -805,6 +872,8 @@ def run_net(args):
     from paper_2102_03494_gb300 import he, workloads
 
     rank, local, world = dist_env()
+    # the single-core oracle baseline runs beside the GPU work, started before any GPU call
+    cpu_proc = start_cpu_baseline() if world == 1 and not args.no_cpu_baseline else None
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -1005,6 +1074,9 @@ def run_deep(args):
 
 def main():
     args = parse()
+    if args.cpu_baseline_child:
+        cpu_baseline_child()
+        return
     if args.impl == "reference":
         run_reference(args)
         return

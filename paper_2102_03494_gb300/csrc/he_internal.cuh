@@ -180,6 +180,7 @@ struct he_ctx {
     Arena net;                          // ciphertexts between the layers of he_net_batch
     int tap_tile = 0;                   // tap kernel tile chosen by he_autotune (0: default)
     int ntt_s1 = 0;                     // NTT split log2 N1 chosen by he_autotune (0: default)
+    int tap_arith = 1;                  // tap kernel products: 0 carry chains, 1 30-bit columns
     int wait_report = -1;               // he_set_wait_report: polls before a stage wait is
                                         // reported in the tap kernel (-1: the full bound)
     struct LayerPlan {                  // he_ffconv_plan: weights and encoded W1 plaintexts

@@ -166,10 +166,342 @@ __device__ __forceinline__ void issue_tap(uint64_t* st, uint64_t* bar, int t, co
 
 // CTAs per SM the register budget is sized for: at 128-coefficient tiles with up to four key
 // digits the three stages take 54 KB, so four CTAs (4 x 5 warps) fit; 94 registers a thread.
-constexpr int min_ctas(int dnum, int tile) { return tile == 128 && dnum <= 4 ? 4 : 1; }
+constexpr int min_ctas(int dnum, int tile, int arith) {
+    return tile == 128 && dnum <= 4 ? (arith ? 3 : 4) : 1;
+}
 
+// Compute warps, carry-chain arithmetic: every 64 x 64-bit product is added into a 128-bit
+// sum by mac128; each tap's key inner product is reduced by Montgomery (REDC, 2^-64).
 template <int DNUM, int TILE>
-__global__ void __launch_bounds__(TILE + 32, min_ctas(DNUM, TILE))
+__device__ __forceinline__ bool compute_chain(const uint64_t* __restrict__ smem, uint64_t* full, uint64_t* empty,
+                                   const uint64_t* __restrict__ XPg, const TapTable& tt, int c_lo,
+                                   int c_cnt, uint64_t* __restrict__ A, int b0, int nb, int l, int L,
+                                   int n0, size_t LN, size_t LNq, int N, int logN, const ModConst& M,
+                                   uint32_t report_polls) {
+    using S = Stage<DNUM, TILE>;
+    constexpr int kTile = S::T;
+    const int tid = threadIdx.x;
+    const bool qlimb = l < L;
+    bool ok = true;
+    const uint64_t q = M.q, qi = M.qinv_neg;
+    const int n = n0 + tid;
+    // unreduced sums of at most HE_MAX_TAPS products below q^2 each: < 64 q^2 < 2^126
+    U128 a128[2][2][2];
+#pragma unroll
+    for (int ib = 0; ib < 2; ++ib)
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int k = 0; k < 2; ++k) a128[ib][c][k] = U128{0, 0};
+    for (int t = 0; t < tt.n; ++t) {
+        const int s = t % kStages;
+        const uint64_t* st = smem + s * S::WORDS;
+        // a wait longer than report_polls is reported (error bit) and then goes on with
+        // the full bound, so the warp stays in step with the producer's stages
+        if (!mbar_wait(&full[s], (uint32_t)(t / kStages) & 1u, report_polls)) {
+            ok = false;
+            mbar_wait(&full[s], (uint32_t)(t / kStages) & 1u);
+        }
+        uint64_t x[2][2];
+        if (!tt.key[t]) {
+#pragma unroll
+            for (int ib = 0; ib < 2; ++ib) {
+                x[ib][0] = (qlimb && ib < nb) ? st[S::XP + (ib * 2) * kTile + tid] : 0;
+                x[ib][1] = (qlimb && ib < nb) ? st[S::XP + (ib * 2 + 1) * kTile + tid] : 0;
+            }
+        } else {
+            const uint32_t pn = perm_of((uint32_t)n, tt.g[t], logN);
+            const int loc = (int)(pn & (kTile - 1));
+            uint64_t xp[2] = {0, 0};                  // (P c0)[perm_g(n)] of each image
+            if (qlimb) {
+#pragma unroll
+                for (int ib = 0; ib < 2; ++ib)
+                    if (ib < nb)
+                        xp[ib] = __ldg(XPg + ((size_t)(b0 + ib) * tt.n_sub + tt.sub[t]) * 2 * LNq +
+                                       (size_t)l * N + pn);
+            }
+            uint64_t kv[DNUM][2];
+#pragma unroll
+            for (int j = 0; j < DNUM; ++j) {
+                kv[j][0] = st[S::KEYS + (2 * j) * kTile + tid];
+                kv[j][1] = st[S::KEYS + (2 * j + 1) * kTile + tid];
+            }
+#pragma unroll
+            for (int ib = 0; ib < 2; ++ib) {
+                if (ib >= nb) {
+                    x[ib][0] = x[ib][1] = 0;
+                    continue;
+                }
+                U128 s0{0, 0}, s1{0, 0};
+#pragma unroll
+                for (int j = 0; j < DNUM; ++j) {
+                    const uint64_t d = st[S::DIG + (ib * DNUM + j) * kTile + loc];
+                    mac128(s0, d, kv[j][0]);
+                    mac128(s1, d, kv[j][1]);
+                }
+                s0.hi += xp[ib];                      // + (P c0) 2^64 (zero on P limbs)
+                x[ib][0] = redc_w(s0, q, qi);
+                x[ib][1] = redc(s1, q, qi);
+            }
+        }
+        const uint64_t p0 = st[S::PTS + tid];
+        const uint64_t p1 = c_cnt > 1 ? st[S::PTS + kTile + tid] : 0;
+        __syncwarp();
+        if ((tid & 31) == 0) mbar_arrive(&empty[s]);   // this warp's last read of stage s
+#pragma unroll
+        for (int ib = 0; ib < 2; ++ib)
+#pragma unroll
+            for (int k = 0; k < 2; ++k) mac128(a128[ib][0][k], x[ib][k], p0);
+        if (c_cnt > 1) {                 // uniform over the launch: one channel skips this
+#pragma unroll
+            for (int ib = 0; ib < 2; ++ib)
+#pragma unroll
+                for (int k = 0; k < 2; ++k) mac128(a128[ib][1][k], x[ib][k], p1);
+        }
+    }
+    if (ok) {
+#pragma unroll
+        for (int ib = 0; ib < 2; ++ib) {
+            if (ib >= nb) break;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                if (c >= c_cnt) break;
+                uint64_t* ab = A + (((size_t)(b0 + ib) * tt.r + c_lo + c) * 2) * LN + (size_t)l * N + n;
+                ab[0] = reduce_sum(a128[ib][c][0], q, qi);
+                ab[LN] = reduce_sum(a128[ib][c][1], q, qi);
+            }
+        }
+    }
+    return ok;
+}
+
+// ---- column arithmetic ----------------------------------------------------------------------
+// A residue x < 2^60 is split as x = x0 + x1 2^30 (x0, x1 < 2^30).  The product of two such
+// residues is four 32 x 32 -> 64-bit partial products (one mad.wide.u32 each) summed into three
+// 64-bit columns: V = c0 + c1 2^30 + c2 2^60 with c0 += x0 y0, c1 += x0 y1 + x1 y0, c2 += x1 y1.
+// No carry chain: the columns have headroom (each partial product is below 2^60) and are
+// normalised (fold) before they could overflow.
+constexpr uint32_t kM30 = (1u << 30) - 1;
+
+struct Cols {
+    uint64_t c0, c1, c2;
+};
+
+__device__ __forceinline__ void madw(uint64_t& acc, uint32_t a, uint32_t b) {
+    asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
+}
+
+__device__ __forceinline__ void cmac(Cols& a, uint32_t x0, uint32_t x1, uint32_t y0, uint32_t y1) {
+    madw(a.c0, x0, y0);
+    madw(a.c1, x0, y1);
+    madw(a.c1, x1, y0);
+    madw(a.c2, x1, y1);
+}
+
+__device__ __forceinline__ uint32_t lo30(uint64_t x) { return (uint32_t)x & kM30; }
+__device__ __forceinline__ uint32_t hi30(uint64_t x) { return (uint32_t)(x >> 30); }
+
+// Carries c0 -> c1 -> c2 and reduces c2 modulo q (c2 counts multiples of 2^60, so c2 mod q
+// changes V by a multiple of q): afterwards c0, c1 < 2^30 + 2^34 and c2 < 2^60 + 16 (2^60 - q).
+__device__ __forceinline__ void fold(Cols& a, uint64_t q) {
+    a.c1 += a.c0 >> 30;
+    a.c0 &= kM30;
+    a.c2 += a.c1 >> 30;
+    a.c1 &= kM30;
+    a.c2 -= (a.c2 >> 60) * q;
+}
+
+// Montgomery reduction by 2^60 in two 30-bit steps: returns r = (V + m q) / 2^60 = V 2^-60
+// mod q, with r < V / 2^60 + q.  qi = -q^-1 mod 2^32 (only its low 30 bits matter).
+// Requires c0 + 2^60 and c1 + 2^60 + 2^34 and c2 + 2^60 + 2^34 below 2^64.
+__device__ __forceinline__ uint64_t mont60(Cols a, uint32_t q0, uint32_t q1, uint32_t qi) {
+    uint32_t m = ((uint32_t)a.c0 * qi) & kM30;
+    madw(a.c0, m, q0);                       // now a multiple of 2^30
+    madw(a.c1, m, q1);
+    a.c1 += a.c0 >> 30;
+    m = ((uint32_t)a.c1 * qi) & kM30;
+    madw(a.c1, m, q0);
+    madw(a.c2, m, q1);
+    return a.c2 + (a.c1 >> 30);
+}
+
+// x < 2^63 -> x mod q for q >= 2^55.  near60 (q > 2^63 / 9, as the special primes just below
+// 2^60 are): x - floor(x / 2^60) q is below 2^60 + 7 (2^60 - q) < 2q, then one conditional
+// subtraction; otherwise (x < 2^8 q) conditional subtractions of q 2^7 .. q.
+__device__ __forceinline__ uint64_t below_q(uint64_t x, uint64_t q, bool near60) {
+    if (near60) {
+        x -= (x >> 60) * q;
+        return x >= q ? x - q : x;
+    }
+#pragma unroll
+    for (int i = 7; i >= 0; --i) {
+        const uint64_t m = q << i;
+        x = x >= m ? x - m : x;
+    }
+    return x;
+}
+
+// 16 x mod q for x < q: a shift when 16 q < 2^60 (q < 2^56), else four modular doublings.
+__device__ __forceinline__ uint64_t times16(uint64_t x, uint64_t q, bool small) {
+    if (small) return x << 4;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) x = add_mod(x, x, q);
+    return x;
+}
+
+// The tap sums' final reduction: V (normalised columns) -> V 2^-68 mod q in [0, q).
+__device__ __forceinline__ uint64_t finish_cols(Cols a, uint64_t q, uint64_t qinv_neg,
+                                                uint32_t q0, uint32_t q1, bool small, bool near60) {
+    fold(a, q);
+    uint64_t r = mont60(a, q0, q1, (uint32_t)qinv_neg);   // < 2^62
+    if (small) {
+        while (r >= q) r -= q;                 // r < 2^56 + q: a few subtractions at most
+    } else {
+        r = below_q(r, q, near60);
+    }
+    // times 2^-8: (r + m q) / 2^8 with m = -r q^-1 mod 2^8, below (q + 255 q) / 2^8 = q
+    const uint64_t m = (r * qinv_neg) & 255u;
+    U128 x{r, 0};
+    mac128(x, m, q);
+    return (x.lo >> 8) | (x.hi << 56);
+}
+
+// Compute warps, column arithmetic.  The keys are in Montgomery form (k 2^64), so a tap's key
+// inner product reduced by mont60 is 16 (sum_j D_j k_j) mod q (the sum times 2^64 - 60); the
+// P c0 term is brought to the same factor, and so is the key-less tap's P x.  The plaintexts
+// are in Montgomery form too (p 2^64): the tap sums then carry 2^(4 + 64), and finish_cols
+// divides by 2^68 (mont60 and one 8-bit step), giving exactly the chain version's residues.
+// Operand bounds: keys, digits, P x and plaintexts are below q; x' (a tap's reduced value) is
+// kept below 2^60 so that its halves are 30-bit.
+template <int DNUM, int TILE>
+__device__ __forceinline__ bool compute_cols(const uint64_t* __restrict__ smem, uint64_t* full, uint64_t* empty,
+                                   const uint64_t* __restrict__ XPg, const TapTable& tt, int c_lo,
+                                   int c_cnt, uint64_t* __restrict__ A, int b0, int nb, int l, int L,
+                                   int n0, size_t LN, size_t LNq, int N, int logN, const ModConst& M,
+                                   uint32_t report_polls) {
+    using S = Stage<DNUM, TILE>;
+    constexpr int kTile = S::T;
+    const int tid = threadIdx.x;
+    const bool qlimb = l < L;
+    const uint64_t q = M.q;
+    const uint32_t q0 = lo30(q), q1 = hi30(q), qi = (uint32_t)M.qinv_neg;
+    const bool small = (q >> 55) == 0;        // q < 2^55: x' = r + 16 P c0 stays below 2^60
+    const bool near60 = q > (1ull << 63) / 9;
+    const int n = n0 + tid;
+    bool ok = true;
+    Cols acc[2][2][2];
+#pragma unroll
+    for (int ib = 0; ib < 2; ++ib)
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int k = 0; k < 2; ++k) acc[ib][c][k] = Cols{0, 0, 0};
+    for (int t = 0; t < tt.n; ++t) {
+        const int s = t % kStages;
+        const uint64_t* st = smem + s * S::WORDS;
+        if (!mbar_wait(&full[s], (uint32_t)(t / kStages) & 1u, report_polls)) {
+            ok = false;
+            mbar_wait(&full[s], (uint32_t)(t / kStages) & 1u);
+        }
+        uint64_t x[2][2];                              // x' of each image and polynomial
+        if (!tt.key[t]) {
+#pragma unroll
+            for (int ib = 0; ib < 2; ++ib)
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+                    x[ib][k] = (qlimb && ib < nb)
+                                   ? times16(st[S::XP + (ib * 2 + k) * kTile + tid], q, small)
+                                   : 0;
+        } else {
+            const uint32_t pn = perm_of((uint32_t)n, tt.g[t], logN);
+            const int loc = (int)(pn & (kTile - 1));
+            uint64_t xp[2] = {0, 0};                   // (P c0)[perm_g(n)] of each image
+            if (qlimb) {
+#pragma unroll
+                for (int ib = 0; ib < 2; ++ib)
+                    if (ib < nb)
+                        xp[ib] = __ldg(XPg + ((size_t)(b0 + ib) * tt.n_sub + tt.sub[t]) * 2 * LNq +
+                                       (size_t)l * N + pn);
+            }
+            uint32_t k0[DNUM][2], k1[DNUM][2];
+#pragma unroll
+            for (int j = 0; j < DNUM; ++j)
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const uint64_t kv = st[S::KEYS + (2 * j + k) * kTile + tid];
+                    k0[j][k] = lo30(kv);
+                    k1[j][k] = hi30(kv);
+                }
+#pragma unroll
+            for (int ib = 0; ib < 2; ++ib) {
+                if (ib >= nb) {
+                    x[ib][0] = x[ib][1] = 0;
+                    continue;
+                }
+                Cols s0{0, 0, 0}, s1{0, 0, 0};
+#pragma unroll
+                for (int j = 0; j < DNUM; ++j) {
+                    const uint64_t d = st[S::DIG + (ib * DNUM + j) * kTile + loc];
+                    const uint32_t d0 = lo30(d), d1 = hi30(d);
+                    cmac(s0, d0, d1, k0[j][0], k1[j][0]);
+                    cmac(s1, d0, d1, k0[j][1], k1[j][1]);
+                    if ((j & 3) == 3 && j + 1 < DNUM) {  // four digits: c1 < 2^63
+                        fold(s0, q);
+                        fold(s1, q);
+                    }
+                }
+                uint64_t r0 = mont60(s0, q0, q1, qi), r1 = mont60(s1, q0, q1, qi);
+                if (small) {                           // r < 2^56: no reduction needed
+                    r0 += xp[ib] << 4;                 // + 16 (P c0), zero on special primes
+                } else {
+                    r0 = below_q(r0, q, near60);
+                    r1 = below_q(r1, q, near60);
+                    if (xp[ib]) r0 = add_mod(r0, times16(xp[ib], q, false), q);
+                }
+                x[ib][0] = r0;
+                x[ib][1] = r1;
+            }
+        }
+        const uint64_t pa = st[S::PTS + tid];
+        const uint64_t pb = c_cnt > 1 ? st[S::PTS + kTile + tid] : 0;
+        __syncwarp();
+        if ((tid & 31) == 0) mbar_arrive(&empty[s]);   // this warp's last read of stage s
+        const uint32_t pa0 = lo30(pa), pa1 = hi30(pa), pb0 = lo30(pb), pb1 = hi30(pb);
+#pragma unroll
+        for (int ib = 0; ib < 2; ++ib)
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const uint32_t x0 = lo30(x[ib][k]), x1 = hi30(x[ib][k]);
+                cmac(acc[ib][0][k], x0, x1, pa0, pa1);
+                if (c_cnt > 1) cmac(acc[ib][1][k], x0, x1, pb0, pb1);
+            }
+        if ((t & 3) == 3) {                            // every four taps: c1 < 2^63 + 2^34
+#pragma unroll
+            for (int ib = 0; ib < 2; ++ib)
+#pragma unroll
+                for (int c = 0; c < 2; ++c)
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) fold(acc[ib][c][k], q);
+        }
+    }
+    if (ok) {
+#pragma unroll
+        for (int ib = 0; ib < 2; ++ib) {
+            if (ib >= nb) break;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                if (c >= c_cnt) break;
+                uint64_t* ab = A + (((size_t)(b0 + ib) * tt.r + c_lo + c) * 2) * LN + (size_t)l * N + n;
+                ab[0] = finish_cols(acc[ib][c][0], q, M.qinv_neg, q0, q1, small, near60);
+                ab[LN] = finish_cols(acc[ib][c][1], q, M.qinv_neg, q0, q1, small, near60);
+            }
+        }
+    }
+    return ok;
+}
+
+template <int DNUM, int TILE, int ARITH>
+__global__ void __launch_bounds__(TILE + 32, min_ctas(DNUM, TILE, ARITH))
 k_ks_mac_ext_bulk(const uint64_t* __restrict__ D, const uint64_t* __restrict__ XPg,
                   const uint64_t* __restrict__ pts, TapTable tt, int c_lo, int c_cnt, int B,
                   uint64_t* __restrict__ A, int L, int K, int logN,
@@ -211,97 +543,12 @@ k_ks_mac_ext_bulk(const uint64_t* __restrict__ D, const uint64_t* __restrict__ X
             issue_tap<DNUM, TILE>(smem + s * S::WORDS, &full[s], t, tt, D, XPg, pts, c_lo, c_cnt,
                                   b0, nb, l, L, n0, LN, N, logN);
         }
+    } else if (ARITH == 0) {
+        ok = compute_chain<DNUM, TILE>(smem, full, empty, XPg, tt, c_lo, c_cnt, A, b0, nb, l, L, n0,
+                                       LN, LNq, N, logN, mods[l], report_polls);
     } else {
-        const ModConst M = mods[l];
-        const uint64_t q = M.q, qi = M.qinv_neg;
-        const int n = n0 + tid;
-        // unreduced sums of at most HE_MAX_TAPS products below q^2 each: < 64 q^2 < 2^126
-        U128 a128[2][2][2];
-#pragma unroll
-        for (int ib = 0; ib < 2; ++ib)
-#pragma unroll
-            for (int c = 0; c < 2; ++c)
-#pragma unroll
-                for (int k = 0; k < 2; ++k) a128[ib][c][k] = U128{0, 0};
-        for (int t = 0; t < tt.n; ++t) {
-            const int s = t % kStages;
-            const uint64_t* st = smem + s * S::WORDS;
-            // a wait longer than report_polls is reported (error bit) and then goes on with
-            // the full bound, so the warp stays in step with the producer's stages
-            if (!mbar_wait(&full[s], (uint32_t)(t / kStages) & 1u, report_polls)) {
-                ok = false;
-                mbar_wait(&full[s], (uint32_t)(t / kStages) & 1u);
-            }
-            uint64_t x[2][2];
-            if (!tt.key[t]) {
-#pragma unroll
-                for (int ib = 0; ib < 2; ++ib) {
-                    x[ib][0] = (qlimb && ib < nb) ? st[S::XP + (ib * 2) * kTile + tid] : 0;
-                    x[ib][1] = (qlimb && ib < nb) ? st[S::XP + (ib * 2 + 1) * kTile + tid] : 0;
-                }
-            } else {
-                const uint32_t pn = perm_of((uint32_t)n, tt.g[t], logN);
-                const int loc = (int)(pn & (kTile - 1));
-                uint64_t xp[2] = {0, 0};                  // (P c0)[perm_g(n)] of each image
-                if (qlimb) {
-#pragma unroll
-                    for (int ib = 0; ib < 2; ++ib)
-                        if (ib < nb)
-                            xp[ib] = __ldg(XPg + ((size_t)(b0 + ib) * tt.n_sub + tt.sub[t]) * 2 * LNq +
-                                           (size_t)l * N + pn);
-                }
-                uint64_t kv[DNUM][2];
-#pragma unroll
-                for (int j = 0; j < DNUM; ++j) {
-                    kv[j][0] = st[S::KEYS + (2 * j) * kTile + tid];
-                    kv[j][1] = st[S::KEYS + (2 * j + 1) * kTile + tid];
-                }
-#pragma unroll
-                for (int ib = 0; ib < 2; ++ib) {
-                    if (ib >= nb) {
-                        x[ib][0] = x[ib][1] = 0;
-                        continue;
-                    }
-                    U128 s0{0, 0}, s1{0, 0};
-#pragma unroll
-                    for (int j = 0; j < DNUM; ++j) {
-                        const uint64_t d = st[S::DIG + (ib * DNUM + j) * kTile + loc];
-                        mac128(s0, d, kv[j][0]);
-                        mac128(s1, d, kv[j][1]);
-                    }
-                    s0.hi += xp[ib];                      // + (P c0) 2^64 (zero on P limbs)
-                    x[ib][0] = redc_w(s0, q, qi);
-                    x[ib][1] = redc(s1, q, qi);
-                }
-            }
-            const uint64_t p0 = st[S::PTS + tid];
-            const uint64_t p1 = c_cnt > 1 ? st[S::PTS + kTile + tid] : 0;
-            __syncwarp();
-            if ((tid & 31) == 0) mbar_arrive(&empty[s]);   // this warp's last read of stage s
-#pragma unroll
-            for (int ib = 0; ib < 2; ++ib)
-#pragma unroll
-                for (int k = 0; k < 2; ++k) mac128(a128[ib][0][k], x[ib][k], p0);
-            if (c_cnt > 1) {                 // uniform over the launch: one channel skips this
-#pragma unroll
-                for (int ib = 0; ib < 2; ++ib)
-#pragma unroll
-                    for (int k = 0; k < 2; ++k) mac128(a128[ib][1][k], x[ib][k], p1);
-            }
-        }
-        if (ok) {
-#pragma unroll
-            for (int ib = 0; ib < 2; ++ib) {
-                if (ib >= nb) break;
-#pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    if (c >= c_cnt) break;
-                    uint64_t* ab = A + (((size_t)(b0 + ib) * tt.r + c_lo + c) * 2) * LN + (size_t)l * N + n;
-                    ab[0] = reduce_sum(a128[ib][c][0], q, qi);
-                    ab[LN] = reduce_sum(a128[ib][c][1], q, qi);
-                }
-            }
-        }
+        ok = compute_cols<DNUM, TILE>(smem, full, empty, XPg, tt, c_lo, c_cnt, A, b0, nb, l, L, n0,
+                                      LN, LNq, N, logN, mods[l], report_polls);
     }
     if (!ok) atomicOr(err, 1);
     __syncthreads();
@@ -315,7 +562,7 @@ k_ks_mac_ext_bulk(const uint64_t* __restrict__ D, const uint64_t* __restrict__ X
     }
 }
 
-template <int DNUM, int TILE>
+template <int DNUM, int TILE, int ARITH>
 void launch_bulk(he_ctx* c, const uint64_t* D, const uint64_t* XP, const uint64_t* pts,
                  const TapTable& tt, uint64_t* A, int B, int c_lo, int cnt) {
     const size_t smem = (size_t)kStages * Stage<DNUM, TILE>::WORDS * 8;
@@ -323,28 +570,28 @@ void launch_bulk(he_ctx* c, const uint64_t* D, const uint64_t* XP, const uint64_
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-        cudaFuncSetAttribute(k_ks_mac_ext_bulk<DNUM, TILE>,
+        cudaFuncSetAttribute(k_ks_mac_ext_bulk<DNUM, TILE, ARITH>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
     const dim3 grid((B + 1) / 2, c->N / TILE, c->L + c->K);
-    k_ks_mac_ext_bulk<DNUM, TILE><<<grid, TILE + 32, smem, c->stream>>>(
+    k_ks_mac_ext_bulk<DNUM, TILE, ARITH><<<grid, TILE + 32, smem, c->stream>>>(
         D, XP, pts, tt, c_lo, cnt, B, A, c->L, c->K, c->logN, c->d_mod, c->d_err,
         c->wait_report >= 0 ? (uint32_t)c->wait_report : kWaitSpins);
 }
 
-template <int TILE>
+template <int TILE, int ARITH>
 void launch_bulk_tile(he_ctx* c, const uint64_t* D, const uint64_t* XP, const uint64_t* pts,
                       const TapTable& tt, uint64_t* A, int B, int c_lo, int cnt) {
     switch (c->dnum) {
-        case 1: launch_bulk<1, TILE>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
-        case 2: launch_bulk<2, TILE>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
-        case 3: launch_bulk<3, TILE>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
-        case 4: launch_bulk<4, TILE>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
-        case 5: launch_bulk<5, TILE>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
-        case 6: launch_bulk<6, TILE>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
-        case 7: launch_bulk<7, TILE>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
-        default: launch_bulk<8, TILE>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
+        case 1: launch_bulk<1, TILE, ARITH>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
+        case 2: launch_bulk<2, TILE, ARITH>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
+        case 3: launch_bulk<3, TILE, ARITH>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
+        case 4: launch_bulk<4, TILE, ARITH>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
+        case 5: launch_bulk<5, TILE, ARITH>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
+        case 6: launch_bulk<6, TILE, ARITH>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
+        case 7: launch_bulk<7, TILE, ARITH>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
+        default: launch_bulk<8, TILE, ARITH>(c, D, XP, pts, tt, A, B, c_lo, cnt); break;
     }
 }
 
@@ -358,8 +605,14 @@ void launch_ks_mac_ext_bulk(he_ctx* c, const uint64_t* D, const uint64_t* XP, co
     for (int c_lo = 0; c_lo < tt.r; c_lo += 2) {
         ++c->launches;
         const int cnt = tt.r - c_lo < 2 ? tt.r - c_lo : 2;
-        if (tile == 128) launch_bulk_tile<128>(c, D, XP, pts, tt, A, B, c_lo, cnt);
-        else launch_bulk_tile<256>(c, D, XP, pts, tt, A, B, c_lo, cnt);
+        const bool cols = c->tap_arith != 0;
+        if (tile == 128) {
+            if (cols) launch_bulk_tile<128, 1>(c, D, XP, pts, tt, A, B, c_lo, cnt);
+            else launch_bulk_tile<128, 0>(c, D, XP, pts, tt, A, B, c_lo, cnt);
+        } else {
+            if (cols) launch_bulk_tile<256, 1>(c, D, XP, pts, tt, A, B, c_lo, cnt);
+            else launch_bulk_tile<256, 0>(c, D, XP, pts, tt, A, B, c_lo, cnt);
+        }
     }
 }
 
@@ -420,8 +673,11 @@ extern "C" int he_autotune(he_ctx* ctx, int batch, int force_tile, double* ms_ou
     int rc = tune_ntt(ctx, batch, &ntt_ms);
     if (rc) return rc;
     if (ms_out) {
-        ms_out[2] = ntt_ms;
-        ms_out[3] = ctx->ntt_s1;
+        for (int i = 0; i < HE_TUNE_REPORT_LEN; ++i) ms_out[i] = 0.0;
+        ms_out[4] = ntt_ms;
+        ms_out[5] = ctx->ntt_s1;
+        ms_out[6] = default_tile(ctx->dnum);
+        ms_out[7] = ctx->tap_arith;
     }
     if (!tapmac_bulk_supported(ctx)) return HE_OK;        // no tile to choose
     const int L = ctx->L, LK = L + ctx->K, dn = ctx->dnum, taps = 25, r = 2;
@@ -454,13 +710,16 @@ extern "C" int he_autotune(he_ctx* ctx, int batch, int force_tile, double* ms_ou
         tt.key[t] = t ? Kb : nullptr;
         tt.g[t] = t ? galois_elt(ctx, t) : 1u;
     }
+    // every (tile, arithmetic) pair, timed on the same operands
     const int tiles[2] = {128, 256};
-    double ms[2] = {0, 0};
+    double ms[4] = {0, 0, 0, 0};
     cudaEvent_t e0, e1;
     HE_CHECK_CUDA(ctx, cudaEventCreate(&e0));
     HE_CHECK_CUDA(ctx, cudaEventCreate(&e1));
-    for (int v = 0; v < 2; ++v) {
-        ctx->tap_tile = tiles[v];
+    int best = 0;
+    for (int v = 0; v < 4; ++v) {
+        ctx->tap_tile = tiles[v >> 1];
+        ctx->tap_arith = v & 1;
         launch_ks_mac_ext_bulk(ctx, D, XP, P, tt, A, batch);          // warm-up
         cudaEventRecord(e0, ctx->stream);
         for (int rep = 0; rep < 3; ++rep) launch_ks_mac_ext_bulk(ctx, D, XP, P, tt, A, batch);
@@ -469,13 +728,16 @@ extern "C" int he_autotune(he_ctx* ctx, int batch, int force_tile, double* ms_ou
         float t = 0.f;
         cudaEventElapsedTime(&t, e0, e1);
         ms[v] = t / 3.0;
+        if (ms[v] < ms[best]) best = v;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    ctx->tap_tile = ms[0] <= ms[1] ? tiles[0] : tiles[1];
+    ctx->tap_tile = tiles[best >> 1];
+    ctx->tap_arith = best & 1;
     if (ms_out) {
-        ms_out[0] = ms[0];
-        ms_out[1] = ms[1];
+        for (int v = 0; v < 4; ++v) ms_out[v] = ms[v];
+        ms_out[6] = ctx->tap_tile;
+        ms_out[7] = ctx->tap_arith;
     }
     return he_launch_check(ctx, "he_autotune");
 }
@@ -485,4 +747,38 @@ extern "C" int he_set_wait_report(he_ctx* ctx, int polls) {
     HE_NOT_RECORDING(ctx, "he_set_wait_report");
     ctx->wait_report = polls < 0 ? -1 : polls;
     return HE_OK;
+}
+
+extern "C" int he_tune_set(he_ctx* ctx, int knob, int value) {
+    if (!ctx) return HE_EINVAL;
+    HE_NOT_RECORDING(ctx, "he_tune_set");
+    switch (knob) {
+        case HE_TUNE_TAP_TILE:
+            if (value != -1 && value != 128 && value != 256)
+                return he_fail(ctx, HE_EINVAL, "he_tune_set: the tap tile is 128 or 256");
+            ctx->tap_tile = value < 0 ? 0 : value;
+            return HE_OK;
+        case HE_TUNE_TAP_ARITH:
+            if (value < -1 || value > 1)
+                return he_fail(ctx, HE_EINVAL, "he_tune_set: tap arithmetic is 0 (chains) or 1 (columns)");
+            ctx->tap_arith = value < 0 ? 1 : value;
+            return HE_OK;
+        case HE_TUNE_NTT_SPLIT:
+            if (value != -1 && (value < 1 || value >= ctx->logN))
+                return he_fail(ctx, HE_EINVAL, "he_tune_set: NTT split log2 N1 out of range");
+            ctx->ntt_s1 = value < 0 ? 0 : value;
+            return HE_OK;
+        default:
+            return he_fail(ctx, HE_EINVAL, "he_tune_set: unknown knob");
+    }
+}
+
+extern "C" int he_tune_get(he_ctx* ctx, int knob, int* value) {
+    if (!ctx || !value) return HE_EINVAL;
+    switch (knob) {
+        case HE_TUNE_TAP_TILE: *value = ctx->tap_tile ? ctx->tap_tile : default_tile(ctx->dnum); return HE_OK;
+        case HE_TUNE_TAP_ARITH: *value = ctx->tap_arith; return HE_OK;
+        case HE_TUNE_NTT_SPLIT: *value = ctx->ntt_s1 ? ctx->ntt_s1 : ctx->logN / 2; return HE_OK;
+        default: return he_fail(ctx, HE_EINVAL, "he_tune_get: unknown knob");
+    }
 }

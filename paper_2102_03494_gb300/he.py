@@ -14,6 +14,8 @@ HE_OK, HE_EINVAL, HE_ENOMEM, HE_ENOKEY, HE_ECUDA, HE_ETIMEOUT = 0, -1, -2, -3, -
 HE_COEFF, HE_NTT = 0, 1
 HE_DP_DOT, HE_DP_SHIFT, HE_DP_SHIFT_EXT, HE_CP_CP, HE_DP_DP = 0, 1, 2, 3, 4
 HE_ROW_SWAP = 0x7FFFFFFF
+HE_TUNE_TAP_TILE, HE_TUNE_TAP_ARITH, HE_TUNE_NTT_SPLIT = 0, 1, 2
+HE_TUNE_REPORT_LEN = 16
 HE_RELIN_KEY = -0x80000000
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -92,6 +94,8 @@ _SIGS = {
     "he_autotune": ([_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "he_probe_int_mac": ([_P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "he_check": ([_P], ctypes.c_int),
+    "he_tune_set": ([_P, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "he_tune_get": ([_P, ctypes.c_int, _I32P], ctypes.c_int),
     "he_set_wait_report": ([_P, ctypes.c_int], ctypes.c_int),
     "he_mc_conv_batch": ([_P, _CTP, ctypes.c_int, _I32P, _I32P, ctypes.POINTER(HeMcConv), _CTP],
                          ctypes.c_int),
@@ -410,11 +414,23 @@ class Context:
         return outs
 
     def he_autotune(self, batch, force_tile=0):
-        """Tune the NTT split and the tap-kernel tile by timing (force_tile 128 / 256 only
-        sets the tile); returns (tap ms with tile 128, with 256, NTT ms, chosen log2 N1)."""
-        ms = (ctypes.c_double * 4)()
+        """Tune the NTT split and the tap kernel's tile and arithmetic by timing (force_tile
+        128 / 256 only sets the tile).  Returns the report as a dict: tap-kernel ms per launch
+        by (tile, arithmetic), the NTT ms and split, and the choices."""
+        ms = (ctypes.c_double * HE_TUNE_REPORT_LEN)()
         self._ck(lib().he_autotune(self.h, batch, force_tile, ms), "he_autotune")
-        return float(ms[0]), float(ms[1]), float(ms[2]), int(ms[3])
+        return {"tap_ms": {"128_chains": ms[0], "128_columns": ms[1], "256_chains": ms[2],
+                           "256_columns": ms[3]},
+                "ntt_ms": ms[4], "ntt_log2_n1": int(ms[5]), "tap_tile": int(ms[6]),
+                "tap_arith": "columns" if int(ms[7]) else "chains"}
+
+    def he_tune_set(self, knob, value):
+        self._ck(lib().he_tune_set(self.h, knob, int(value)), "he_tune_set")
+
+    def he_tune_get(self, knob):
+        v = (ctypes.c_int32 * 1)()
+        self._ck(lib().he_tune_get(self.h, knob, v), "he_tune_get")
+        return int(v[0])
 
     def he_probe_int_mac(self):
         """Measured 64 x 64 -> 128-bit products/s: (carry chain, 32-bit column sums)."""

@@ -12,7 +12,8 @@ def need_gpu():
 def make_ctx(prm):
     from paper_2102_03494_gb300 import he
     need_gpu()
-    ctx = he.Context(log_n=prm.log_n, n_q=prm.n_q, n_p=prm.n_p, alpha=prm.alpha, t=prm.t)
+    ctx = he.Context(log_n=prm.log_n, n_q=prm.n_q, n_p=prm.n_p, alpha=prm.alpha, t=prm.t,
+                     q_bits=prm.q_bits, p_bits=prm.p_bits)
     assert ctx.he_get_moduli() == prm.q + prm.p + [prm.t]
     return ctx
 

@@ -255,27 +255,57 @@ def test_captured_layer_replays_bit_exact(pack):
     ctx.he_graph_free(gid3)
 
 
-def test_autotuned_tap_tile_keeps_the_bits():
-    """he_autotune times the two tap-kernel tiles and keeps one; either forced tile gives the
-    oracle's bits."""
+def test_autotuned_tap_tile_and_arithmetic_keep_the_bits():
+    """he_autotune times the tap kernel's tiles and arithmetic variants and keeps one pair;
+    every forced pair gives the oracle's bits."""
+    from paper_2102_03494_gb300 import he
     prm = params.Params(log_n=10, n_q=4, n_p=2, alpha=2)
     shape = workloads.LayerShape(2, 6, 6, 3, 1, 1, 3, 2)
     lay_o, s, steps, keys, blob, xs, W1, W2, cts = setup_layer(prm, shape, "dp_shift_ext", seed=9, B=3)
     ctx = make_ctx(prm)
     lay = ctx.layout(*shape.astuple(), pack="dp_shift_ext")
     ctx.he_load_keys(blob, gpu_steps(steps))
-    t128, t256, t_ntt, s1 = ctx.he_autotune(3)
-    assert t128 > 0 and t256 > 0 and t_ntt > 0 and 1 <= s1 < prm.log_n
+    rep = ctx.he_autotune(3)
+    assert all(v > 0 for v in rep["tap_ms"].values()) and rep["ntt_ms"] > 0
+    assert 1 <= rep["ntt_log2_n1"] < prm.log_n and rep["tap_tile"] in (128, 256)
+    assert ctx.he_tune_get(he.HE_TUNE_TAP_TILE) == rep["tap_tile"]
     want = [ffconv.he_layer(prm, c, W1, W2, lay_o, keys) for c in cts]
     for tile in (128, 256):
-        ctx.he_autotune(3, force_tile=tile)
-        outs = ctx.he_ffconv_layer_batch([upload_ntt(ctx, c) for c in cts], W1, W2, lay)
-        for b in range(3):
-            for c in range(shape.O_c):
-                assert (download_coeff(ctx, outs[b * shape.O_c + c]) == want[b][c].stack()).all()
-    from paper_2102_03494_gb300 import he
+        for arith in (0, 1):
+            ctx.he_autotune(3, force_tile=tile)
+            ctx.he_tune_set(he.HE_TUNE_TAP_ARITH, arith)
+            outs = ctx.he_ffconv_layer_batch([upload_ntt(ctx, c) for c in cts], W1, W2, lay)
+            for b in range(3):
+                for c in range(shape.O_c):
+                    assert (download_coeff(ctx, outs[b * shape.O_c + c]) == want[b][c].stack()).all()
     with pytest.raises(he.HeError):
         ctx.he_autotune(3, force_tile=64)
+    with pytest.raises(he.HeError):
+        ctx.he_tune_set(he.HE_TUNE_TAP_ARITH, 2)
+
+
+@pytest.mark.parametrize("q_bits,p_bits,n_q,n_p,alpha",
+                         [(58, 57, 3, 2, 1), (60, 59, 3, 2, 1), (50, 60, 6, 1, 1), (52, 56, 5, 1, 1)],
+                         ids=["q58-p57", "q60-p59", "six-digits", "five-digits-p56"])
+def test_tap_kernel_on_wide_primes_and_many_digits(q_bits, p_bits, n_q, n_p, alpha):
+    """The tap kernel's column arithmetic has separate branches for ciphertext primes of 55 bits
+    or more (no lazy sums), for special primes not just below 2^60 and for keys of more than
+    four digits (a mid-sum normalisation); each gives the oracle's bits, as do the carry
+    chains."""
+    from paper_2102_03494_gb300 import he
+    prm = params.Params(log_n=9, n_q=n_q, n_p=n_p, alpha=alpha, q_bits=q_bits, p_bits=p_bits)
+    shape = SMALL[0]
+    lay_o, s, steps, keys, blob, xs, W1, W2, cts = setup_layer(prm, shape, "dp_shift_ext", seed=5, B=2)
+    ctx = make_ctx(prm)
+    ctx.he_load_keys(blob, gpu_steps(steps))
+    lay = ctx.layout(*shape.astuple(), pack="dp_shift_ext")
+    want = [ffconv.he_layer(prm, c, W1, W2, lay_o, keys) for c in cts]
+    for arith in (1, 0):
+        ctx.he_tune_set(he.HE_TUNE_TAP_ARITH, arith)
+        outs = ctx.he_ffconv_layer_batch([upload_ntt(ctx, c) for c in cts], W1, W2, lay)
+        for b in range(2):
+            for c in range(shape.O_c):
+                assert (download_coeff(ctx, outs[b * shape.O_c + c]) == want[b][c].stack()).all()
 
 
 @pytest.mark.parametrize("B", [1, 2])
