@@ -37,6 +37,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--pack", default="dp_shift_ext", choices=["dp_shift", "dp_shift_ext", "dp_dot"])
+    ap.add_argument("--tap-arith", default="auto", choices=["auto", "chains", "columns"],
+                    help="force the fused tap kernel's arithmetic after autotuning")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-baseline-child", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-extra", action="store_true",
@@ -44,8 +46,18 @@ def parse():
     ap.add_argument("--serving-layers", action="store_true",
                     help="serving loop over single FFConv layers (28 x 28 at N = 2^14, 3 x 32 x 32 "
                          "at N = 2^15) instead of whole networks")
+    ap.add_argument("--sweep", nargs="?", const="full", default=None, choices=["full", "short"],
+                    help="batched primitive sweep (NTT, automorphism, plain and hoisted rotations "
+                         "over B, N, L); 'short' = N=2^15, L=16, B in {16, 256}")
     ap.add_argument("--packing", action="store_true",
                     help="Table IX: the packing variants on WideNet's factorized second layer")
+    ap.add_argument("--serving-rates", default="20,60,120,240",
+                    help="offered request rates (per second) of --serving")
+    ap.add_argument("--serving-count", type=int, default=0,
+                    help="requests per rate of --serving (0: 3 s of arrivals, 60 .. 480)")
+    ap.add_argument("--single", action="store_true",
+                    help="one-image latency of the 1x28x28 layer at N=8192, 3+1 primes, for the "
+                         "DP_DOT, DP_SHIFT and DP_SHIFT_EXT schedules")
     ap.add_argument("--serving", action="store_true",
                     help="run the serving loop (mixed rings, Poisson arrivals) instead")
     ap.add_argument("--net", action="store_true",
@@ -320,6 +332,9 @@ def run(args):
     outs = [ctx.new_ct() for _ in range(B * shape.O_c)]
     tuned = ctx.he_autotune(B)            # untimed: picks the NTT split and the tap kernel's
                                           # tile and arithmetic for this batch
+    if args.tap_arith != "auto":
+        ctx.he_tune_set(he.HE_TUNE_TAP_ARITH, 1 if args.tap_arith == "columns" else 0)
+        tuned["tap_arith"] = args.tap_arith + " (forced)"
     torch.cuda.synchronize()
 
     def layer():
@@ -505,26 +520,37 @@ def run(args):
 
 
 def extra_workloads():
-    """Short runs of the two network workloads (their own modes, in child processes on the same
-    GPU), summarised beside the layer line; failures are reported, not raised."""
+    """Short runs of the other workloads (their own modes, in child processes on the same GPU),
+    summarised beside the layer line; failures are reported, not raised."""
     out = {}
     for key, flags in (("network_n14_b64", ["--net", "--steps", "3", "--warmup", "2"]),
                        ("deep_3x32x32_n15_b16", ["--deep", "--deep-ranks", "8", "--steps", "2",
-                                                 "--warmup", "1"])):
+                                                 "--warmup", "1"]),
+                       ("single_request_n13", ["--single", "--steps", "50", "--warmup", "3"]),
+                       ("sweep_n15_l16", ["--sweep", "short"]),
+                       ("serving_mix", ["--serving", "--serving-rates", "60,120",
+                                        "--serving-count", "120"])):
         try:
             res = subprocess.run([sys.executable, os.path.abspath(__file__)] + flags,
-                                 capture_output=True, text=True, timeout=600)
+                                 capture_output=True, text=True, timeout=900)
             rec = json.loads(res.stdout.strip().splitlines()[-1])
-            keep = {k: rec[k] for k in ("metric", "value", "unit", "ms_per_step") if k in rec}
-            keep["batch"] = rec.get("config", {}).get("batch_per_gpu")
-            if "ops_per_image" in rec:
-                keep["ops_per_image"] = rec["ops_per_image"]
-            if "variants" in rec:
-                keep["ops_per_image"] = rec["variants"][0]["ops_per_image"]
-            keep["clocks"] = rec.get("clocks")
-            out[key] = keep
         except Exception as e:             # noqa: BLE001 -- reported in the line
             out[key] = {"error": f"{type(e).__name__}: {e}"[:300]}
+            continue
+        if key in ("single_request_n13", "sweep_n15_l16"):
+            out[key] = rec
+            continue
+        if key == "serving_mix":
+            out[key] = {k: rec.get(k) for k in ("metric", "mix", "workload", "served", "rates")}
+            continue
+        keep = {k: rec[k] for k in ("metric", "value", "unit", "ms_per_step") if k in rec}
+        keep["batch"] = rec.get("config", {}).get("batch_per_gpu")
+        if "ops_per_image" in rec:
+            keep["ops_per_image"] = rec["ops_per_image"]
+        if "variants" in rec:
+            keep["ops_per_image"] = rec["variants"][0]["ops_per_image"]
+        keep["clocks"] = rec.get("clocks")
+        out[key] = keep
     return out
 
 
@@ -675,8 +701,8 @@ def run_serving(args):
            "served": "batches replayed as recorded CUDA graphs (one per worker and batch size)",
            "served_calls": "the same scheduler, batches run as library calls",
            "rates": []}
-    for rate in (20.0, 60.0, 120.0, 240.0):
-        count = int(max(60, min(rate * 3, 480)))
+    for rate in [float(v) for v in args.serving_rates.split(",")]:
+        count = args.serving_count or int(max(60, min(rate * 3, 480)))
         served_calls, _ = serve(rate, count, False)
         served, by_ring = serve(rate, count, True)
         # the plain form: one request per call in arrival order on one stream
@@ -972,7 +998,7 @@ def run_net(args):
                     "h2d_bytes_per_step": B * ct_bytes, "d2h_bytes_per_step": B * ct_bytes,
                     "ms_per_step": ms_e2e / args.steps},
             "gpu_launches": launches, "clocks": clk,
-            "autotune": {"tap_tile_ms": tuned[:2], "ntt_log2_n1": tuned[3]},
+            "autotune": tuned,
             "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items() if v[1]}}
     print(json.dumps(line))
 
@@ -1067,8 +1093,247 @@ def run_deep(args):
                                    "128 -> x^2 -> sum pool -> FC 128->10, N=2^15, 12x50-bit q, "
                                    "3x60-bit p, alpha=3; value = rank 8",
                        "batch_per_gpu": B, "galois_keys": len(steps) - 1},
-            "autotune": {"tap_tile_ms": tuned[:2], "ntt_log2_n1": tuned[3]},
+            "autotune": tuned,
             "clocks": clk, "variants": variants}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------- single request, N = 8192
+
+def run_single(args):
+    """The plain single-request layer: one encrypted 1 x 28 x 28 image (pixels uniform in
+    [0, 255], seed 0), the 5 x 5 stride-2 pad-1 low-rank convolution to r = 2 channels and the
+    1 x 1 restore to 5 channels (weights uniform in [-8, 8]), RNS-BFV N = 8192, t = 65537,
+    3 x 50-bit q, one 60-bit special prime, digits of one prime; one image per call.  For each
+    W1 schedule -- DP_DOT (the paper's DensePack: per output a plaintext product and a
+    rotate-and-sum, Sec. 3.2 / Table I), DP_SHIFT and DP_SHIFT_EXT (hoisted filter taps) --
+    the call's latency by CUDA events (warm-up, then --steps calls, an event pair each), the
+    rotations per call, and the DP_SHIFT_EXT call with the weights resident (a layer plan)
+    and replayed as a recorded CUDA graph."""
+    import numpy as np
+    import torch
+
+    from paper_2102_03494_gb300 import he, workloads
+
+    torch.cuda.set_device(0)
+    shape = workloads.MNIST_LAYER
+    stream = torch.cuda.Stream()
+    ctx = he.Context(log_n=13, n_q=3, n_p=1, alpha=1, stream=stream)
+    N = ctx.N
+    sk = ctx.he_keygen_secret(1)
+    x = workloads.image(0, shape)
+    W1, W2 = workloads.weights(0, shape)
+    slots = np.zeros(N, dtype=np.int64)
+    slots[: x.size] = x.reshape(-1)
+    ct = ctx.he_encrypt(sk, slots, 3)
+    clocks = ClockSampler(0)
+    clocks.start()
+    res = {}
+
+    def latency(fn, n):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(n)]
+        torch.cuda.synchronize()
+        for a, b in evs:
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = sorted(a.elapsed_time(b) for a, b in evs)
+        return {"ms_mean": statistics.mean(ms), "ms_p50": ms[len(ms) // 2],
+                "ms_p99": ms[min(len(ms) - 1, int(0.99 * len(ms)))], "calls": n}
+
+    for pack in ("dp_dot", "dp_shift", "dp_shift_ext"):
+        lay = ctx.layout(*shape.astuple(), pack=pack)
+        ctx.he_keygen_galois(sk, 2, ctx.he_ffconv_required_steps(lay))
+        outs = [ctx.new_ct() for _ in range(shape.O_c)]
+        ctx.he_reset_op_counts()
+        ctx.he_ffconv_layer_batch([ct], W1, W2, lay, outs)
+        ops = ctx.he_op_counts()
+        n = max(5, min(args.steps, 20 if pack == "dp_dot" else 200))
+        res[pack] = dict(latency(lambda: ctx.he_ffconv_layer_batch([ct], W1, W2, lay, outs), n),
+                         ops_per_call=ops)
+        if pack == "dp_shift_ext":
+            plan = ctx.he_ffconv_plan(W1, W2, lay)
+            res[pack]["weights_resident"] = latency(
+                lambda: ctx.he_ffconv_layer_planned(plan, [ct], lay, outs), n)
+            gid, _ = ctx.he_ffconv_graph_create(plan, [ct], lay, outs)
+            res[pack]["graph_replay"] = latency(lambda: ctx.he_graph_launch(gid), n)
+            ctx.he_graph_free(gid)
+            ctx.he_ffconv_plan_free(plan)
+    ctx.he_check()
+    clk = clocks.stop()
+    print(json.dumps({"metric": "single-request encrypted FFConv layer latency (ms) at N=8192",
+                      "unit": "ms", "higher_is_better": False, "dtype": "u64", "data": "synthetic",
+                      "config": {"workload": "1x28x28 -> 5x5 s2 p1 (r=2) -> 1x1 (5 ch), N=8192, "
+                                             "t=65537, 3x50-bit q + 1x60-bit p, alpha=1, batch 1"},
+                      "schedules": res, "clocks": clk}))
+
+
+# ---------------------------------------------------------------- primitive sweep
+
+# The primitive sweep's grid: ring sizes, ciphertext primes L -> (special primes K, digit
+# width alpha = K), batch sizes and hoisted step counts.
+SWEEP_LOG_N = (13, 14, 15, 16)
+SWEEP_L = {3: 1, 8: 2, 16: 4, 24: 6}
+SWEEP_B = (1, 16, 256, 1024)
+SWEEP_H = (8, 24)
+SWEEP_MAX_KEYS = 64
+SWEEP_MEM_LIMIT = 150 << 30
+L2_BYTES = 129 << 20
+
+
+def sweep_point_bytes(log_n, L, K, B, h):
+    """Device bytes a sweep point holds: the B input and B output ciphertexts, the hoisted
+    outputs of up to 8 ciphertexts (reused), the Galois keys and the rotation scratch."""
+    N = 1 << log_n
+    ct = 2 * L * N * 8
+    dnum = -(-L // K)
+    key = 16 * dnum * (L + K) * N
+    n_keys = min(max(B, h), SWEEP_MAX_KEYS)
+    scratch = min(B, 64) * (L + dnum * (L + K) + 2 * (L + K) + 2 * L) * N * 8
+    return 2 * B * ct + 8 * h * ct + n_keys * key + scratch
+
+
+def run_sweep(args):
+    """Batched primitive sweep: negacyclic NTT and inverse NTT, the Galois automorphism, plain
+    key-switched rotations (ciphertexts grouped by Galois key, one batched call per key) and
+    hoisted rotations (h steps per ciphertext sharing one ModUp), over batch sizes, ring sizes
+    and prime counts.  Ciphertexts hold residues uniform modulo each prime; steps are uniform
+    in [1, N/2); min(B, 64) distinct Galois keys (max(h, min(B, 64)) for the hoisted points),
+    generated on the device, each ciphertext taking one of them uniformly.  Every op is timed
+    by CUDA events on the library's stream: two warm-up calls, then enough repetitions for
+    about 0.3 s (3 .. 20); points whose inputs are smaller than L2 flush it (a 256 MiB write,
+    outside the timed events) before every repetition.  Points above 150 GB are skipped."""
+    import numpy as np
+    import torch
+
+    from paper_2102_03494_gb300 import he
+
+    torch.cuda.set_device(0)
+    short = args.sweep == "short"
+    grid_n = (15,) if short else SWEEP_LOG_N
+    grid_l = (16,) if short else tuple(SWEEP_L)
+    grid_b = (16, 256) if short else SWEEP_B
+    stream = torch.cuda.Stream()
+    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peaks = measured_peaks()
+    clocks = ClockSampler(0)
+    clocks.start()
+    points = []
+
+    def timed(fn, flush):
+        for _ in range(2):
+            fn()
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        first = e0.elapsed_time(e1)
+        reps = int(max(3, min(20, 300.0 / max(first, 1e-3))))
+        total = 0.0
+        for _ in range(reps):
+            if flush:
+                with torch.cuda.stream(stream):
+                    flush_buf.zero_()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+        return total / reps, reps
+
+    for log_n in grid_n:
+        N = 1 << log_n
+        for L in grid_l:
+            K = SWEEP_L[L]
+            todo = [B for B in grid_b
+                    if sweep_point_bytes(log_n, L, K, B, max(SWEEP_H)) <= SWEEP_MEM_LIMIT]
+            for B in grid_b:
+                if B not in todo:
+                    points.append({"log_n": log_n, "L": L, "K": K, "B": B, "skipped":
+                                   f"needs {sweep_point_bytes(log_n, L, K, B, max(SWEEP_H)) / 1e9:.0f} GB "
+                                   "on the device, above the 150 GB bound"})
+            if not todo:
+                continue
+            ctx = he.Context(log_n=log_n, n_q=L, n_p=K, alpha=K, stream=stream)
+            rng = np.random.default_rng(1000 * log_n + L)
+            n_keys = min(max(max(todo), max(SWEEP_H)), SWEEP_MAX_KEYS)
+            steps = [int(x) for x in rng.choice(np.arange(1, N // 2), n_keys, replace=False)]
+            sk = ctx.he_keygen_secret(7)
+            ctx.he_keygen_galois(sk, 8, steps)
+            ctx.he_autotune(min(max(todo), 64))
+            moduli = ctx.he_get_moduli()[:L]
+            dnum = -(-L // K)
+            for B in todo:
+                torch.cuda.synchronize()
+                with torch.cuda.stream(stream):
+                    X = torch.empty((B, 2, L, N), dtype=torch.int64, device="cuda")
+                    for l, q in enumerate(moduli):
+                        X[:, :, l, :].random_(0, q)       # uniform residues below q_l
+                    Y = torch.empty_like(X)
+                ins, outs = list(X), list(Y)
+                ct_bytes = 2 * L * N * 8
+                flush = B * ct_bytes < 2 * L2_BYTES
+                pt = {"log_n": log_n, "L": L, "K": K, "alpha": K, "B": B,
+                      "l2": "flushed before every repetition" if flush else "inputs larger than L2"}
+                # NTT / inverse NTT of all 2 B polynomials' limbs
+                ms, reps = timed(lambda: ctx.he_ntt(X, 2 * B, L), flush)
+                pt["ntt_limbs_per_s"] = 2 * B * L / (ms / 1e3)
+                pt["ntt_butterflies_T_per_s"] = 2 * B * L * (N // 2) * log_n / (ms / 1e3) / 1e12
+                ms, reps = timed(lambda: ctx.he_ntt(X, 2 * B, L, inverse=True), flush)
+                pt["intt_limbs_per_s"] = 2 * B * L / (ms / 1e3)
+                # automorphism: read and write every word once
+                ms, reps = timed(lambda: ctx.he_automorphism(ins, steps[0], outs), flush)
+                gbs = 2 * B * ct_bytes / (ms / 1e3) / 1e9
+                pt["automorphism_gbs"] = gbs
+                pt["automorphism_hbm_frac"] = gbs / peaks["hbm_gbs"]
+                # plain rotations, grouped by key
+                nk = min(B, SWEEP_MAX_KEYS)
+                owner = rng.integers(0, nk, B)
+                groups = [(steps[k], [i for i in range(B) if owner[i] == k]) for k in range(nk)]
+                groups = [(st, idx) for st, idx in groups if idx]
+
+                def plain():
+                    for st, idx in groups:
+                        ctx.he_rotate_batch([ins[i] for i in idx], st, [outs[i] for i in idx])
+
+                ms, reps = timed(plain, flush)
+                pt["rotations_per_s"] = B / (ms / 1e3)
+                key_bytes = 16 * dnum * (L + K) * N
+                pt["rotation_gbs_algorithmic"] = (2 * B * ct_bytes + len(groups) * key_bytes) / (ms / 1e3) / 1e9
+                # hoisted: h steps per ciphertext, one ModUp each, outputs reused by every 8th
+                for h in SWEEP_H:
+                    hk = min(max(B, h), SWEEP_MAX_KEYS)
+                    mine = [[steps[int(k)] for k in rng.choice(hk, h, replace=False)] for _ in range(B)]
+                    with torch.cuda.stream(stream):
+                        pool = [list(ctx.new_ct(count=h)) for _ in range(min(B, 8))]
+
+                    def hoisted():
+                        for i in range(B):
+                            ctx.he_rotate_hoisted(ins[i], mine[i], pool[i % len(pool)])
+
+                    ms, reps = timed(hoisted, flush)
+                    pt[f"hoisted_h{h}_rotations_per_s"] = B * h / (ms / 1e3)
+                    del pool
+                ctx.he_check()
+                points.append(pt)
+                del X, Y, ins, outs
+            ctx.close()
+            torch.cuda.empty_cache()
+    clk = clocks.stop()
+    line = {"metric": "batched primitive sweep: NTT/INTT limbs/s, automorphism GB/s, plain and "
+                      "hoisted key-switched rotations/s",
+            "unit": "per point", "n_gpus": 1, "data": "synthetic (uniform residues)",
+            "dtype": "u64", "grid": "short" if short else "full",
+            "config": {"primes": "50-bit q, 60-bit p, alpha = K", "hbm_peak_gbs": peaks["hbm_gbs"],
+                       "sms": sms},
+            "points": points, "clocks": clk}
     print(json.dumps(line))
 
 
@@ -1079,6 +1344,12 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.sweep:
+        run_sweep(args)
+        return
+    if args.single:
+        run_single(args)
         return
     if args.packing:
         run_packing(args)

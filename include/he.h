@@ -181,6 +181,12 @@ int he_rotate(he_ctx* ctx, const he_ct* in, int32_t step, he_ct* out);
  * (HE_EINVAL) while a graph is being recorded, because recording would allocate the graph's
  * own pointer tables. */
 int he_rotate_noalloc(he_ctx* ctx, const he_ct* in, int32_t step, he_ct* out);
+/* The Galois automorphism X -> X^(5^step) (X -> X^(2N-1) for HE_ROW_SWAP) on both polynomials
+ * of n ciphertexts, without key switching (the step the paper's rotation starts with, Sec.
+ * 3.2): out[i] decrypts under s(X^g) to the rotated slots.  NTT domain, any level; out[i]
+ * must not alias in[i].  Ciphertexts stored back to back (in and out alike) take one launch.
+ * No key needed. */
+int he_automorphism(he_ctx* ctx, const he_ct* in, int n, int32_t step, he_ct* out);
 /* The same rotation applied to n ciphertexts in one batch (one key read per launch). */
 int he_rotate_batch(he_ctx* ctx, const he_ct* in, int n, int32_t step, he_ct* out);
 /* h rotations of one ciphertext sharing one ModUp of c1 (hoisting): outs[i] = rotation by
@@ -428,6 +434,11 @@ int he_set_wait_report(he_ctx* ctx, int polls);
  * the 32-bit multiply-add carry chain the kernels use, out[1] = products/s with 30-bit limbs
  * summed into 64-bit column accumulators.  Uses the context stream and scratch; synchronous. */
 int he_probe_int_mac(he_ctx* ctx, double* out);
+/* The same probe per form and per instruction (n doubles, up to 6): out[0] carry-chain
+ * products/s, out[1] column products/s, out[2] products/s with three 32 x 32 -> 64-bit
+ * products each (Karatsuba on 30-bit halves), out[3] mad.lo.u32/s, out[4] mad.hi.u32/s,
+ * out[5] mad.wide.u32/s (eight independent accumulators per thread).  Synchronous. */
+int he_probe_int_ops(he_ctx* ctx, double* out, int n);
 
 /* Negacyclic NTT (inverse = 0) or inverse NTT (inverse = 1) in place on `n_items` blocks of
  * n_limbs limbs each (device [n_items][n_limbs][N]); limb i uses the i-th ciphertext prime

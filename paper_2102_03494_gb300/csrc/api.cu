@@ -471,6 +471,7 @@ extern "C" int he_ctx_create(const he_params* p, void* stream, he_ctx** out) {
         M.r2 = h_mulmod(r1, r1, q);
         M.n_inv = h_inv((uint64_t)N % q, q);
         M.n_inv_sh = h_shoup(M.n_inv, q).ws;
+        M.one_sh = h_shoup(1, q).ws;
         if (m == c->L + c->K && !c->batching) continue;   // t without a 2N-th root
         uint64_t psi = root_2n(q, two_n), psi_inv = h_inv(psi, q);
         for (int k = 0; k < N; ++k) {

@@ -225,6 +225,36 @@ extern "C" int he_rotate_batch(he_ctx* ctx, const he_ct* in, int n, int32_t step
     return rotate_contig(ctx, X, n, g, nullptr, outs, b, chunk);
 }
 
+extern "C" int he_automorphism(he_ctx* ctx, const he_ct* in, int n, int32_t step, he_ct* out) {
+    if (!ctx || !in || !out || n < 1)
+        return ctx ? he_fail(ctx, HE_EINVAL, "he_automorphism: arguments") : HE_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        int rc = check_ct(ctx, &in[i], 0, HE_NTT, "he_automorphism input");
+        if (!rc) rc = check_ct(ctx, &out[i], (int)in[i].n_limbs, -1, "he_automorphism output");
+        if (rc) return rc;
+        if (in[i].data == out[i].data)
+            return he_fail(ctx, HE_EINVAL, "he_automorphism: input and output must not alias");
+    }
+    const uint32_t g = galois_elt(ctx, step);
+    const size_t N = ctx->N, lv = in[0].n_limbs, poly = lv * N;
+    // ciphertexts stored back to back (inputs and outputs alike, one level): one launch over
+    // all 2 n polynomials; otherwise one launch per ciphertext
+    bool contig = true;
+    for (int i = 0; i < n && contig; ++i)
+        contig = in[i].n_limbs == lv && in[i].data == in[0].data + 2 * poly * i &&
+                 out[i].data == out[0].data + 2 * poly * i;
+    if (contig) {
+        launch_automorph(ctx, in[0].data, poly, out[0].data, poly, 2 * n, (int)lv, g);
+    } else {
+        for (int i = 0; i < n; ++i) {
+            const size_t p = (size_t)in[i].n_limbs * N;
+            launch_automorph(ctx, in[i].data, p, out[i].data, p, 2, (int)in[i].n_limbs, g);
+        }
+    }
+    for (int i = 0; i < n; ++i) out[i].domain = HE_NTT;
+    return he_launch_check(ctx, "he_automorphism");
+}
+
 extern "C" int he_rotate(he_ctx* ctx, const he_ct* in, int32_t step, he_ct* out) {
     return he_rotate_batch(ctx, in, 1, step, out);
 }

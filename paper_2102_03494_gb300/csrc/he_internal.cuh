@@ -26,6 +26,7 @@ struct ModConst {
     uint64_t r2;         // 2^128 mod q (to Montgomery form via REDC(x r2))
     uint64_t n_inv;      // N^-1 mod q
     uint64_t n_inv_sh;   // its Shoup companion
+    uint64_t one_sh;     // floor(2^64 / q): Shoup companion of 1 (x mod q for any 64-bit x)
 };
 
 struct ShoupPair {
@@ -78,6 +79,18 @@ __device__ __forceinline__ uint64_t mul_shoup(uint64_t x, uint64_t w, uint64_t w
 __device__ __forceinline__ uint64_t mul_shoup_lazy(uint64_t x, uint64_t w, uint64_t ws,
                                                    uint64_t q) {
     uint64_t h = mulhi64(x, ws);
+    return x * w - h * q;
+}
+
+// Same with the high product estimated from three of the four partial products:
+// h' = x1 w1 + hi(x0 w1) + hi(x1 w0) is floor(x ws / 2^64) minus 0, 1 or 2 (the dropped low
+// halves and hi(x0 w0) carry at most 2 into bit 64), so x w - h' q lies in [0, 4q).
+__device__ __forceinline__ uint64_t mul_shoup_approx(uint64_t x, uint64_t w, uint64_t ws,
+                                                     uint64_t q) {
+    const uint32_t x0 = (uint32_t)x, x1 = (uint32_t)(x >> 32);
+    const uint32_t w0 = (uint32_t)ws, w1 = (uint32_t)(ws >> 32);
+    uint64_t h = (uint64_t)__umulhi(x0, w1) + __umulhi(x1, w0);
+    h += (uint64_t)x1 * w1;
     return x * w - h * q;
 }
 

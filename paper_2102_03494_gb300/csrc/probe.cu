@@ -66,6 +66,66 @@ __global__ void __launch_bounds__(256) k_probe_cols(const uint64_t* __restrict__
     out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = r;
 }
 
+// Karatsuba form: a b = a0 b0 + ((a0 + a1)(b0 + b1) - a0 b0 - a1 b1) 2^30 + a1 b1 2^60, three
+// 32 x 32 -> 64-bit products per 64-bit product; the middle column is formed from the three
+// sums once, at the end.
+__global__ void __launch_bounds__(256) k_probe_kara(const uint64_t* __restrict__ in,
+                                                    uint64_t* __restrict__ out, int iters) {
+    uint32_t x0[kAcc], x1[kAcc], y0[kAcc], y1[kAcc];
+    uint64_t c0[kAcc], cm[kAcc], c2[kAcc];
+    const uint64_t m60 = (1ull << 60) - 1;
+#pragma unroll
+    for (int a = 0; a < kAcc; ++a) {
+        const uint64_t xv = (in[a] + threadIdx.x) & m60, yv = in[kAcc + a] & m60;
+        x0[a] = (uint32_t)(xv & 0x3fffffff);
+        x1[a] = (uint32_t)(xv >> 30);
+        y0[a] = (uint32_t)(yv & 0x3fffffff);
+        y1[a] = (uint32_t)(yv >> 30);
+        c0[a] = cm[a] = c2[a] = 0;
+    }
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int a = 0; a < kAcc; ++a) {
+            const uint32_t xs = x0[a] + x1[a], ys = y0[a] + y1[a];
+            c0[a] += (uint64_t)x0[a] * y0[a];
+            cm[a] += (uint64_t)xs * ys;
+            c2[a] += (uint64_t)x1[a] * y1[a];
+            x0[a] = (x0[a] + y0[a]) & 0x3fffffff;
+        }
+    }
+    uint64_t r = 0;
+#pragma unroll
+    for (int a = 0; a < kAcc; ++a) r ^= c0[a] ^ (cm[a] - c0[a] - c2[a]) ^ c2[a];
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = r;
+}
+
+// Single-instruction streams: eight independent accumulators per thread, each step one
+// instruction of the kind measured (op 0: mad.lo.u32, 1: mad.hi.u32, 2: mad.wide.u32).
+template <int OP>
+__global__ void __launch_bounds__(256) k_probe_op(const uint64_t* __restrict__ in,
+                                                  uint64_t* __restrict__ out, int iters) {
+    uint32_t acc[kAcc], b[kAcc];
+    uint64_t w[kAcc];
+#pragma unroll
+    for (int a = 0; a < kAcc; ++a) {
+        acc[a] = (uint32_t)in[a] + threadIdx.x;
+        b[a] = (uint32_t)in[kAcc + a] | 1u;
+        w[a] = in[a] ^ threadIdx.x;
+    }
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int a = 0; a < kAcc; ++a) {
+            if (OP == 0) asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(acc[a]) : "r"(b[a]), "r"(b[(a + 1) % kAcc]));
+            if (OP == 1) asm volatile("mad.hi.u32 %0, %0, %1, %2;" : "+r"(acc[a]) : "r"(b[a]), "r"(b[(a + 1) % kAcc]));
+            if (OP == 2) asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(w[a]) : "r"(acc[a]), "r"(b[a]));
+        }
+    }
+    uint64_t r = 0;
+#pragma unroll
+    for (int a = 0; a < kAcc; ++a) r ^= acc[a] ^ w[a];
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = r;
+}
+
 }  // namespace
 
 extern "C" int he_probe_int_mac(he_ctx* ctx, double* out) {
@@ -108,4 +168,51 @@ extern "C" int he_probe_int_mac(he_ctx* ctx, double* out) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return he_launch_check(ctx, "he_probe_int_mac");
+}
+
+extern "C" int he_probe_int_ops(he_ctx* ctx, double* out, int n) {
+    if (!ctx || !out || n < 1) return HE_EINVAL;
+    HE_NOT_RECORDING(ctx, "he_probe_int_ops");
+    int sms = 0, dev = 0;
+    HE_CHECK_CUDA(ctx, cudaGetDevice(&dev));
+    HE_CHECK_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = sms * 8, threads = 256, iters = 4096;
+    int rc = arena_reserve(ctx, 2 * kAcc + (size_t)blocks * threads + 64);
+    if (rc) return rc;
+    arena_reset(ctx);
+    uint64_t* in = arena_take(ctx, 2 * kAcc);
+    uint64_t* o = arena_take(ctx, (size_t)blocks * threads);
+    uint64_t h[2 * kAcc];
+    for (int i = 0; i < 2 * kAcc; ++i) h[i] = (0x0123456789abcdefull * (i + 1)) & ((1ull << 59) - 1);
+    HE_CHECK_CUDA(ctx, cudaMemcpyAsync(in, h, sizeof(h), cudaMemcpyHostToDevice, ctx->stream));
+    cudaEvent_t e0, e1;
+    HE_CHECK_CUDA(ctx, cudaEventCreate(&e0));
+    HE_CHECK_CUDA(ctx, cudaEventCreate(&e1));
+    const double per = (double)blocks * threads * iters * kAcc;
+    const int nv = n < 6 ? n : 6;
+    for (int v = 0; v < nv; ++v) {
+        auto launch = [&]() {
+            ++ctx->launches;
+            switch (v) {
+                case 0: k_probe_chain<<<blocks, threads, 0, ctx->stream>>>(in, o, iters); break;
+                case 1: k_probe_cols<<<blocks, threads, 0, ctx->stream>>>(in, o, iters); break;
+                case 2: k_probe_kara<<<blocks, threads, 0, ctx->stream>>>(in, o, iters); break;
+                case 3: k_probe_op<0><<<blocks, threads, 0, ctx->stream>>>(in, o, iters); break;
+                case 4: k_probe_op<1><<<blocks, threads, 0, ctx->stream>>>(in, o, iters); break;
+                default: k_probe_op<2><<<blocks, threads, 0, ctx->stream>>>(in, o, iters); break;
+            }
+        };
+        launch();
+        launch();
+        cudaEventRecord(e0, ctx->stream);
+        for (int rep = 0; rep < 5; ++rep) launch();
+        cudaEventRecord(e1, ctx->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        out[v] = per * 5 / (ms / 1e3);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return he_launch_check(ctx, "he_probe_int_ops");
 }

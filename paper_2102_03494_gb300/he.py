@@ -81,6 +81,7 @@ _SIGS = {
     "he_rotate": ([_P, _CTP, ctypes.c_int32, _CTP], ctypes.c_int),
     "he_rotate_noalloc": ([_P, _CTP, ctypes.c_int32, _CTP], ctypes.c_int),
     "he_rotate_batch": ([_P, _CTP, ctypes.c_int, ctypes.c_int32, _CTP], ctypes.c_int),
+    "he_automorphism": ([_P, _CTP, ctypes.c_int, ctypes.c_int32, _CTP], ctypes.c_int),
     "he_rotate_hoisted": ([_P, _CTP, _I32P, ctypes.c_int, _CTP], ctypes.c_int),
     "he_mul_plain_acc": ([_P, _CTP, _P, ctypes.c_int, _CTP], ctypes.c_int),
     "he_add": ([_P, _CTP, _CTP, _CTP], ctypes.c_int),
@@ -93,6 +94,7 @@ _SIGS = {
     "he_net_required_steps": ([_P, ctypes.POINTER(HeNet), _I32P, ctypes.c_int], ctypes.c_int),
     "he_autotune": ([_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "he_probe_int_mac": ([_P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "he_probe_int_ops": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int], ctypes.c_int),
     "he_check": ([_P], ctypes.c_int),
     "he_tune_set": ([_P, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "he_tune_get": ([_P, ctypes.c_int, _I32P], ctypes.c_int),
@@ -336,6 +338,12 @@ class Context:
         self._ck(lib().he_rotate_batch(self.h, ia, len(cts), step, oa), "he_rotate_batch")
         return outs
 
+    def he_automorphism(self, cts, step, outs=None):
+        outs = [self.new_ct() for _ in cts] if outs is None else outs
+        ia, oa = self.ct_array(cts), self.ct_array(outs)
+        self._ck(lib().he_automorphism(self.h, ia, len(cts), step, oa), "he_automorphism")
+        return outs
+
     def he_rotate_hoisted(self, ct, steps, outs=None):
         outs = [self.new_ct() for _ in steps] if outs is None else outs
         a = self.ct_struct(ct)
@@ -446,6 +454,14 @@ class Context:
     def he_set_wait_report(self, polls):
         """Test hook: polls before the tap kernel reports a stage wait (-1: the default)."""
         self._ck(lib().he_set_wait_report(self.h, int(polls)), "he_set_wait_report")
+
+    def he_probe_int_ops(self):
+        """Rates per second: carry-chain, column and Karatsuba products; mad.lo / mad.hi /
+        mad.wide.u32 instructions."""
+        out = (ctypes.c_double * 6)()
+        self._ck(lib().he_probe_int_ops(self.h, out, 6), "he_probe_int_ops")
+        return dict(zip(("chain", "columns", "karatsuba", "mad_lo", "mad_hi", "mad_wide"),
+                        (float(v) for v in out)))
 
     # ---- deeper networks (several ciphertexts per tensor)
     @staticmethod

@@ -240,3 +240,31 @@ def test_sweep_rotations_are_bit_exact(cfg):
     hs = ctx.he_rotate_hoisted(ds[1], steps)
     for o, w in zip(hs, bfv.rotate_hoisted(prm, cts[1], steps, keys)):
         assert (download_coeff(ctx, o) == w.stack()).all()
+
+
+@pytest.mark.parametrize("cfg", [(9, 3, 1, 1), (13, 3, 1, 1), (15, 16, 4, 4), (16, 24, 6, 6)])
+def test_automorphism_is_bit_exact(cfg):
+    """he_automorphism (X -> X^g on both polynomials, no key switch) against the oracle's
+    coefficient-domain automorphism, for ciphertexts stored back to back (one launch) and
+    apart (a launch each), with a random step and the row swap."""
+    from paper_2102_03494_gb300 import he
+    prm = params.Params(log_n=cfg[0], n_q=cfg[1], n_p=cfg[2], alpha=cfg[3])
+    ctx = make_ctx(prm)
+    rng = np.random.default_rng(cfg[0] + 100)
+    cts = [bfv.Ct(*[np.stack([rng.integers(0, q, prm.n, dtype=np.uint64) for q in prm.q])
+                    for _ in range(2)]) for _ in range(3)]
+    step = int(rng.integers(1, prm.n // 2))
+    block = ctx.new_ct(count=3)
+    for i, c in enumerate(cts):
+        block[i].copy_(upload_ntt(ctx, c))
+    for st, g in ((step, bfv.galois_of(step, prm.n)), (he.HE_ROW_SWAP, 2 * prm.n - 1)):
+        outs = ctx.he_automorphism(list(block), st, outs=list(ctx.new_ct(count=3)))
+        apart = ctx.he_automorphism([block[2], block[0]], st)
+        for i, c in enumerate(cts):
+            want = np.stack([bfv.automorphism(c.c0, g, prm.q), bfv.automorphism(c.c1, g, prm.q)])
+            assert (download_coeff(ctx, outs[i]) == want).all()
+        for o, i in zip(apart, (2, 0)):
+            want = np.stack([bfv.automorphism(cts[i].c0, g, prm.q), bfv.automorphism(cts[i].c1, g, prm.q)])
+            assert (download_coeff(ctx, o) == want).all()
+    with pytest.raises(he.HeError):
+        ctx.he_automorphism([block[0]], 1, outs=[block[0]])
