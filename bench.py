@@ -37,7 +37,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--pack", default="dp_shift_ext", choices=["dp_shift", "dp_shift_ext", "dp_dot"])
-    ap.add_argument("--tap-arith", default="auto", choices=["auto", "chains", "columns"],
+    ap.add_argument("--tap-arith", default="auto", choices=["auto", "chains", "columns", "products"],
                     help="force the fused tap kernel's arithmetic after autotuning")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-baseline-child", action="store_true", help=argparse.SUPPRESS)
@@ -333,7 +333,7 @@ def run(args):
     tuned = ctx.he_autotune(B)            # untimed: picks the NTT split and the tap kernel's
                                           # tile and arithmetic for this batch
     if args.tap_arith != "auto":
-        ctx.he_tune_set(he.HE_TUNE_TAP_ARITH, 1 if args.tap_arith == "columns" else 0)
+        ctx.he_tune_set(he.HE_TUNE_TAP_ARITH, ("chains", "columns", "products").index(args.tap_arith))
         tuned["tap_arith"] = args.tap_arith + " (forced)"
     torch.cuda.synchronize()
 
@@ -466,11 +466,13 @@ def run(args):
     ctx.he_graph_free(gid)
     ctx.he_ffconv_plan_free(plan)
 
-    roof = taps_roofline(phases, args, B, n_rot, sms)
-    if roof is not None:          # the measured multiply-accumulate rate, for context
-        chain, cols = ctx.he_probe_int_mac()
-        roof["probe_mul64_per_s"] = {"carry_chain_T": chain / 1e12, "column_sums_T": cols / 1e12,
-                                     "frac_of_carry_chain": roof["achieved"] / (chain / 1e12)}
+    roof = taps_roofline(phases, args, B, n_rot, sms, tuned["tap_arith"])
+    if roof is not None:          # the measured multiply-accumulate rates, for context
+        probe = ctx.he_probe_int_ops()
+        clk = measured_peaks()["sm_max_mhz"] * 1e6
+        roof["probe"] = {"mul64_T_per_s": {k: probe[k] / 1e12 for k in ("chain", "columns", "karatsuba")},
+                         "per_clock_per_sm": {k: probe[k] / (sms * clk)
+                                              for k in ("mad_lo", "mad_hi", "mad_wide")}}
     layer_bytes = layer_algorithmic_bytes(B, shape.O_c, n_rot)
     peaks = measured_peaks()
 
@@ -562,26 +564,26 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "src": "fallback"}
 
 
-# DRAM bytes (read + write) of one k_ks_mac_ext launch, from one ncu capture of the current
-# kernel version at the bench shape; cleared when the kernel changes and until it is captured
-# again.
-KS_MAC_EXT_TRAFFIC = {64: 3415376896 + 990737152}
+# DRAM bytes (read + write) of the tap phase per batch of 64, from one ncu capture of the
+# current kernels (scaled from a smaller batch); None until captured for this version.
+TAPS_TRAFFIC = {}
 
 
 # 64 x 64 -> 128-bit products per second of the GPU's integer multiplier: SMs (152 on GB300)
-# x 64 32-bit multiply-adds per clock x clock / 8.  A 64 x 64 -> 128-bit product is four
-# 32 x 32 -> 64-bit partial products, and each of those is two multiply-add instructions (its
-# low and its high word), so it takes at least 8 of the SM's 64 multiply-add issue slots per
-# clock.
+# x 64 32-bit multiply-adds per clock x clock / 4.  A 64 x 64 -> 128-bit product is four
+# 32 x 32 -> 64-bit partial products, and mad.wide.u32 forms one of them (both words) in a
+# single multiply-add issue slot: the in-library probe (he_probe_int_ops) measures mad.wide.u32
+# at 59 and mad.lo.u32 at 63 per clock and SM, mad.hi.u32 at 27 (half rate).
 def mul64_peak_per_s(sm_mhz, sms=152):
-    return sms * 64 / 8 * sm_mhz * 1e6
+    return sms * 64 / 4 * sm_mhz * 1e6
 
 
-def taps_roofline(phases, args, B, n_rot, sms=152):
-    """Roofline of the dominant kernel, the extended-basis tap MAC (k_ks_mac_ext), from its
-    CUDA-event time inside the timed region.  Algorithmic work: per image, ciphertext-basis
-    limb and coefficient, 2 dnum products for the key inner product of each rotated tap and
-    2 r products for the plaintext product of every tap."""
+def taps_roofline(phases, args, B, n_rot, sms=152, arith="chains"):
+    """Roofline of the dominant phase, the extended-basis tap MAC (the fused tap kernel; with
+    the precomputed products also their preparation and the special-prime limbs' chain
+    kernel), from its CUDA-event time inside the timed region.  Algorithmic work: per image,
+    limb of Q u P and coefficient, 2 dnum products for the key inner product of each rotated
+    tap and 2 r products for the plaintext product of every tap."""
     ms, spans = phases["taps"]
     if not spans or args.pack != "dp_shift_ext":
         return None
@@ -591,13 +593,15 @@ def taps_roofline(phases, args, B, n_rot, sms=152):
     pk = measured_peaks()
     peak = mul64_peak_per_s(pk["sm_max_mhz"], sms) / 1e12
     achieved = products / sec / 1e12
-    return {"kernel": "k_ks_mac_ext", "bound": "alu", "achieved": achieved, "peak": peak,
-            "unit": "T mul64/s", "frac": achieved / peak,
-            "traffic": KS_MAC_EXT_TRAFFIC.get(B) if args.pack == "dp_shift_ext" else None,
-            "launch_us": sec * 1e6, "products_per_launch": products,
-            "peak_note": f"{sms} SMs (device attribute) x 64 IMAD/clk / 8 per 64x64->128-bit "
-                         "product (4 partial products, low and high word each) x max SM clock of "
-                         f"MEASURED_PEAKS ({pk['src']})"}
+    kernels = {"chains": "k_ks_mac_ext_bulk (carry chains)",
+               "columns": "k_ks_mac_ext_bulk (30-bit columns)",
+               "products": "k_pk_prep + k_tap_pk (q limbs) + k_ks_mac_ext_bulk (p limbs)"}
+    return {"kernel": kernels.get(arith.split(" ")[0], arith), "bound": "alu",
+            "achieved": achieved, "peak": peak, "unit": "T mul64/s", "frac": achieved / peak,
+            "traffic": TAPS_TRAFFIC.get(B), "launch_us": sec * 1e6, "products_per_launch": products,
+            "peak_note": f"{sms} SMs (device attribute) x 64 multiply-add issue slots per clock / 4 "
+                         "mad.wide.u32 per 64x64->128-bit product x max SM clock of MEASURED_PEAKS "
+                         f"({pk['src']}); derived, probe-checked (he_probe_int_ops)"}
 
 
 def layer_algorithmic_bytes(B, O_c, n_rot):

@@ -297,6 +297,25 @@ int net_reserve(he_ctx* ctx, size_t n_u64) {
     return HE_OK;
 }
 
+int pk_reserve(he_ctx* ctx, size_t n_u64) {
+    const size_t bytes = n_u64 * 8 + 4096;
+    if (bytes <= ctx->pk.cap) return HE_OK;
+    if (ctx->rec) return refuse_growth(ctx);
+    if (ctx->pk.base) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->pk.base);
+        ctx->pk.base = nullptr;
+        ctx->pk.cap = 0;
+    }
+    if (cudaMalloc(&ctx->pk.base, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return he_fail(ctx, HE_ENOMEM, "tap product buffer allocation failed");
+    }
+    ctx->pk.cap = bytes;
+    ++ctx->pk_epoch;
+    return HE_OK;
+}
+
 void arena_reset(he_ctx* ctx) { ctx->arena.used = 0; }
 
 uint64_t* arena_take(he_ctx* ctx, size_t n_u64) {
@@ -395,7 +414,7 @@ static void free_ctx(he_ctx* c) {
     void* ptrs[] = {c->d_mod, c->d_tw_fwd, c->d_tw_inv, c->d_slot_pos, c->d_cdt,
                     c->d_modup_inv, c->d_modup_c, c->d_md_inv, c->d_md_c, c->d_md_pinv,
                     c->d_rs_inv, c->d_pmodq, c->arena.base, c->staging.dev, c->d_err,
-                    c->d_mult_tab, c->net.base};
+                    c->d_mult_tab, c->net.base, c->pk.base};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& kv : c->keys)

@@ -53,6 +53,7 @@ static int begin_recording(he_ctx* ctx, int own, const Arena* adopt_saved) {
     }
     r->g.arena_epoch = ctx->arena_epoch;
     r->g.net_epoch = ctx->net_epoch;
+    r->g.pk_epoch = ctx->pk_epoch;
     // on failure below only the fresh arena of own == 1 is undone; otherwise the context's
     // arena is left as it is (the caller of own == 2 still holds its saved one)
     if (cudaStreamCreateWithFlags(&r->cs, cudaStreamNonBlocking) != cudaSuccess) {
@@ -194,6 +195,8 @@ extern "C" int he_graph_launch(he_ctx* ctx, int32_t graph) {
         return he_fail(ctx, HE_EINVAL, "he_graph_launch: the context scratch was reallocated since recording");
     if (g.net_epoch != ctx->net_epoch)
         return he_fail(ctx, HE_EINVAL, "he_graph_launch: the network buffer was reallocated since recording");
+    if (g.pk_epoch != ctx->pk_epoch)
+        return he_fail(ctx, HE_EINVAL, "he_graph_launch: the tap product buffer was reallocated since recording");
     HE_CHECK_CUDA(ctx, cudaGraphLaunch(g.exec, ctx->stream));
     ctx->launches += g.launches;
     for (int i = 0; i < 4; ++i) ctx->ops[i] += g.ops[i];

@@ -191,9 +191,11 @@ struct he_ctx {
     std::map<uint32_t, GaloisKey> keys; // by Galois element
     Arena arena;
     Arena net;                          // ciphertexts between the layers of he_net_batch
+    Arena pk;                           // the tap kernel's plaintext x key products (tapmac.cu)
     int tap_tile = 0;                   // tap kernel tile chosen by he_autotune (0: default)
     int ntt_s1 = 0;                     // NTT split log2 N1 chosen by he_autotune (0: default)
-    int tap_arith = 1;                  // tap kernel products: 0 carry chains, 1 30-bit columns
+    int tap_arith = 0;                  // tap kernel: 0 carry chains, 1 30-bit columns,
+                                        // 2 precomputed plaintext x key products
     int wait_report = -1;               // he_set_wait_report: polls before a stage wait is
                                         // reported in the tap kernel (-1: the full bound)
     struct LayerPlan {                  // he_ffconv_plan: weights and encoded W1 plaintexts
@@ -206,6 +208,7 @@ struct he_ctx {
     uint64_t keys_epoch = 0;            // bumped whenever a resident key is dropped
     uint64_t arena_epoch = 0;           // bumped whenever the scratch arena is reallocated
     uint64_t net_epoch = 0;             // bumped whenever the network buffer is reallocated
+    uint64_t pk_epoch = 0;              // bumped whenever the tap products buffer is reallocated
     struct LayerGraph {                 // a recorded sequence of library calls (graph.cu)
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
@@ -213,6 +216,7 @@ struct he_ctx {
         bool shared = false;            // recorded on the context's scratch
         uint64_t arena_epoch = 0;       // ... at this generation of it
         uint64_t net_epoch = 0;         // network buffer generation at recording
+        uint64_t pk_epoch = 0;          // tap products buffer generation at recording
         uint64_t keys_epoch = 0;
         std::vector<void*> allocs;      // small tables uploaded while recording
         std::vector<int32_t> plans;     // layer plans the recorded calls use
@@ -279,6 +283,8 @@ void arena_reset(he_ctx* ctx);
 int arena_reserve(he_ctx* ctx, size_t n_u64);
 // The context's buffer for a network's activations (grow-only, like the arena).
 int net_reserve(he_ctx* ctx, size_t n_u64);
+// The tap kernel's buffer of plaintext x key products (grow-only, like the arena).
+int pk_reserve(he_ctx* ctx, size_t n_u64);
 
 uint32_t galois_elt(const he_ctx* ctx, int32_t step);
 // Phase timing: phase_begin/phase_end bracket work of one phase (HE_PHASE_*) with events on

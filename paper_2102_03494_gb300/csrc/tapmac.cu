@@ -500,13 +500,284 @@ __device__ __forceinline__ bool compute_cols(const uint64_t* __restrict__ smem, 
     return ok;
 }
 
+// ---- precomputed plaintext x key products (the ciphertext-prime limbs) ---------------------
+// For a limb whose prime is below 2^50 the tap sum is rewritten with the products
+// PK[c][t][j][k] = pt[c][t] key_t[j][k] (per coefficient, Montgomery form, computed once per
+// launch from the resident keys and the layer's plaintexts):
+//   acc_k[c] = sum_t ( sum_j D_j[perm_t(n)] PK[c][t][j][k] + [k = 0] (P c0)[perm_t(n)] pt[c][t] )
+// (the key-less centre tap: (P c_k)[n] pt[c][0]).  Every term is a product of two residues
+// below 2^50, split at bit 25 into halves below 2^25: four mad.wide.u32 add it into three
+// 64-bit columns V = c0 + c1 2^25 + c2 2^50, each partial product below 2^50.  With at most
+// (8 + 1) 64 = 576 terms per sum the columns stay below 2^61 and V below 576 q^2 < q 2^64, so
+// the whole sum is reduced once, by one Montgomery reduction (REDC, 2^-64) at the end, which
+// removes the single 2^64 factor every term carries.  No reduction per tap.
+constexpr uint32_t kM25 = (1u << 25) - 1;
+constexpr int kPkTile = 128;                          // coefficients per CTA
+constexpr int kPkImages = 4;                          // images per CTA, two per thread
+
+__device__ __forceinline__ uint64_t split25(uint64_t x) {   // x < 2^50 -> lo | hi << 32
+    return (x & kM25) | ((x >> 25) << 32);
+}
+
+__global__ void k_pk_prep(const uint64_t* __restrict__ pts, TapTable tt, int c_lo, int dnum,
+                          uint64_t* __restrict__ PK, int L, int K, int logN,
+                          const ModConst* __restrict__ mods) {
+    const int N = 1 << logN;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int l = blockIdx.y;
+    int z = blockIdx.z;                               // ((c t + t) dnum + j) 2 + k
+    const int k = z & 1;
+    z >>= 1;
+    const int j = z % dnum;
+    z /= dnum;
+    const int t = z % tt.n, c = z / tt.n;
+    const uint64_t* key = tt.key[t];
+    if (!key) return;
+    const size_t LN = (size_t)(L + K) * N;
+    const ModConst M = mods[l];
+    U128 x{0, 0};
+    mac128(x, pts[((size_t)(c_lo + c) * tt.n + t) * LN + (size_t)l * N + n],
+           key[(size_t)(2 * j + k) * LN + (size_t)l * N + n]);
+    PK[(size_t)blockIdx.z * L * N + (size_t)l * N + n] = split25(redc(x, M.q, M.qinv_neg));
+}
+
+template <int DNUM>
+struct PkStage {
+    static constexpr int T = kPkTile;
+    static constexpr int PK = 0;                                   // [2 c][DNUM][2 k][T]
+    static constexpr int PT = 2 * DNUM * 2 * T;                    // [2 c][T]
+    static constexpr int DIG = PT + 2 * T;                         // [4 img][DNUM][T]
+    static constexpr int XP = DIG;                                 // key-less: [4 img][2 k][T]
+    static constexpr int WORDS = DIG + (kPkImages * DNUM > 8 ? kPkImages * DNUM : 8) * T;
+    static constexpr int STAGES = DNUM <= 4 ? 3 : 2;
+};
+
+template <int DNUM>
+__device__ __forceinline__ void issue_pk_tap(uint64_t* st, uint64_t* bar, int t, const TapTable& tt,
+                                             const uint64_t* __restrict__ D,
+                                             const uint64_t* __restrict__ XPg,
+                                             const uint64_t* __restrict__ PK,
+                                             const uint64_t* __restrict__ pts, int c_lo,
+                                             int c_cnt, int b0, int nb, int l, int L, int n0,
+                                             size_t LN, int N, int logN) {
+    using S = PkStage<DNUM>;
+    constexpr int T = S::T;
+    const int lane = threadIdx.x & 31;
+    const bool keyed = tt.key[t] != nullptr;
+    const uint32_t row = T * 8;
+    const int src0 = keyed ? (int)(perm_of((uint32_t)n0, tt.g[t], logN) & ~(uint32_t)(T - 1)) : n0;
+    const int npk = keyed ? c_cnt * DNUM * 2 : 0;
+    const int npt = c_cnt;
+    const int ndig = keyed ? nb * DNUM : nb * 2;     // digit rows, or P x rows of the centre tap
+    const int total = npk + npt + ndig;
+    if (lane == 0) mbar_expect_tx(bar, (uint32_t)total * row);
+    __syncwarp();
+    const size_t LNq = (size_t)L * N;
+    for (int i = lane; i < total; i += 32) {
+        uint64_t* dst;
+        const uint64_t* src;
+        if (i < npk) {                                // i = (c DNUM + j) 2 + k
+            dst = st + S::PK + i * T;
+            src = PK + ((size_t)(i / (2 * DNUM)) * tt.n * DNUM * 2 + (size_t)t * DNUM * 2 +
+                        i % (2 * DNUM)) * LNq + (size_t)l * N + n0;
+        } else if (i < npk + npt) {
+            const int c = i - npk;
+            dst = st + S::PT + c * T;
+            src = pts + ((size_t)(c_lo + c) * tt.n + t) * LN + (size_t)l * N + n0;
+        } else if (keyed) {
+            const int q = i - npk - npt, ib = q / DNUM, j = q - ib * DNUM;
+            const size_t it = (size_t)(b0 + ib) * tt.n_sub + tt.sub[t];
+            dst = st + S::DIG + (ib * DNUM + j) * T;
+            src = D + (it * DNUM + j) * LN + (size_t)l * N + src0;
+        } else {
+            const int q = i - npk - npt, ib = q >> 1, k = q & 1;
+            const size_t it = (size_t)(b0 + ib) * tt.n_sub + tt.sub[t];
+            dst = st + S::XP + (ib * 2 + k) * T;
+            src = XPg + (it * 2 + k) * LNq + (size_t)l * N + n0;
+        }
+        bulk_copy(dst, src, row, bar);
+    }
+}
+
+__device__ __forceinline__ void cmac25(Cols& a, uint32_t x0, uint32_t x1, uint32_t y0, uint32_t y1) {
+    madw(a.c0, x0, y0);
+    madw(a.c1, x0, y1);
+    madw(a.c1, x1, y0);
+    madw(a.c2, x1, y1);
+}
+
+// V = c0 + c1 2^25 + c2 2^50 (< q 2^64) -> V 2^-64 mod q.
+__device__ __forceinline__ uint64_t finish25(const Cols& a, uint64_t q, uint64_t qinv_neg) {
+    U128 v{a.c0, 0};
+    uint64_t lo = a.c1 << 25, hi = a.c1 >> 39;
+    v.lo += lo;
+    v.hi += hi + (v.lo < lo);
+    lo = a.c2 << 50;
+    hi = a.c2 >> 14;
+    v.lo += lo;
+    v.hi += hi + (v.lo < lo);
+    return redc(v, q, qinv_neg);
+}
+
+// One CTA: 128 coefficients of one ciphertext-prime limb for four images; compute thread
+// tid < 256 holds coefficient n0 + (tid mod 128) of images 2 (tid / 128) and 2 (tid / 128) + 1.
+// The last warp stages every tap's rows (PK, plaintexts, the digits of the permuted block or
+// the centre tap's P x rows) with bulk copies, as in k_ks_mac_ext_bulk.
+template <int DNUM>
+__global__ void __launch_bounds__(2 * kPkTile + 32, DNUM <= 4 ? 2 : 1)
+k_tap_pk(const uint64_t* __restrict__ D, const uint64_t* __restrict__ XPg,
+         const uint64_t* __restrict__ PK, const uint64_t* __restrict__ pts, TapTable tt, int c_lo,
+         int c_cnt, int B, uint64_t* __restrict__ A, int L, int K, int logN,
+         const ModConst* __restrict__ mods, int* __restrict__ err, uint32_t report_polls) {
+    using S = PkStage<DNUM>;
+    constexpr int T = S::T;
+    constexpr int kSt = S::STAGES;
+    constexpr int kComputeWarps = 2 * T / 32;
+    extern __shared__ __align__(128) uint64_t smem[];
+    __shared__ __align__(8) uint64_t full[kSt], empty[kSt];
+    const int N = 1 << logN;
+    const int tid = threadIdx.x;
+    const int n0 = blockIdx.y * T;
+    const int l = blockIdx.z;
+    const int b0 = blockIdx.x * kPkImages;
+    const int nb = B - b0 < kPkImages ? B - b0 : kPkImages;
+    const size_t LN = (size_t)(L + K) * N;
+    const size_t LNq = (size_t)L * N;
+    if (tid == 0) {
+        for (int s = 0; s < kSt; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kComputeWarps);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    bool ok = true;
+    if (tid >= 2 * T) {                               // the producer warp
+        for (int t = 0; t < tt.n; ++t) {
+            const int s = t % kSt;
+            if (t >= kSt) {
+                ok &= mbar_wait(&empty[s], (uint32_t)((t / kSt) - 1) & 1u);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            }
+            issue_pk_tap<DNUM>(smem + s * S::WORDS, &full[s], t, tt, D, XPg, PK, pts, c_lo, c_cnt,
+                               b0, nb, l, L, n0, LN, N, logN);
+        }
+    } else {
+        const ModConst M = mods[l];
+        const int col = tid & (T - 1);
+        const int n = n0 + col;
+        const int i0 = 2 * (tid / T);                 // this thread's first image in the CTA
+        Cols acc[2][2][2];
+#pragma unroll
+        for (int ii = 0; ii < 2; ++ii)
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int k = 0; k < 2; ++k) acc[ii][c][k] = Cols{0, 0, 0};
+        for (int t = 0; t < tt.n; ++t) {
+            const int s = t % kSt;
+            const uint64_t* st = smem + s * S::WORDS;
+            if (!mbar_wait(&full[s], (uint32_t)(t / kSt) & 1u, report_polls)) {
+                ok = false;
+                mbar_wait(&full[s], (uint32_t)(t / kSt) & 1u);
+            }
+            if (tt.key[t]) {
+                const uint32_t pn = perm_of((uint32_t)n, tt.g[t], logN);
+                const int loc = (int)(pn & (T - 1));
+                uint32_t d0[2][DNUM], d1[2][DNUM], x0[2], x1[2];
+#pragma unroll
+                for (int ii = 0; ii < 2; ++ii) {
+                    const int ib = i0 + ii;
+                    const bool live = ib < nb;
+                    uint64_t xp = 0;
+                    if (live)
+                        xp = __ldg(XPg + ((size_t)(b0 + ib) * tt.n_sub + tt.sub[t]) * 2 * LNq +
+                                   (size_t)l * N + pn);
+                    x0[ii] = (uint32_t)xp & kM25;
+                    x1[ii] = (uint32_t)(xp >> 25);
+#pragma unroll
+                    for (int j = 0; j < DNUM; ++j) {
+                        const uint64_t d = live ? st[S::DIG + (ib * DNUM + j) * T + loc] : 0;
+                        d0[ii][j] = (uint32_t)d & kM25;
+                        d1[ii][j] = (uint32_t)(d >> 25);
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    if (c >= c_cnt) break;
+                    const uint64_t p = st[S::PT + c * T + col];
+                    const uint32_t p0 = (uint32_t)p & kM25, p1 = (uint32_t)(p >> 25);
+#pragma unroll
+                    for (int ii = 0; ii < 2; ++ii) cmac25(acc[ii][c][0], x0[ii], x1[ii], p0, p1);
+#pragma unroll
+                    for (int j = 0; j < DNUM; ++j)
+#pragma unroll
+                        for (int k = 0; k < 2; ++k) {
+                            const uint64_t w = st[S::PK + ((c * DNUM + j) * 2 + k) * T + col];
+                            const uint32_t w0 = (uint32_t)w, w1 = (uint32_t)(w >> 32);
+#pragma unroll
+                            for (int ii = 0; ii < 2; ++ii)
+                                cmac25(acc[ii][c][k], d0[ii][j], d1[ii][j], w0, w1);
+                        }
+                }
+            } else {
+                uint32_t x0[2][2], x1[2][2];
+#pragma unroll
+                for (int ii = 0; ii < 2; ++ii)
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        const int ib = i0 + ii;
+                        const uint64_t x = ib < nb ? st[S::XP + (ib * 2 + k) * T + col] : 0;
+                        x0[ii][k] = (uint32_t)x & kM25;
+                        x1[ii][k] = (uint32_t)(x >> 25);
+                    }
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    if (c >= c_cnt) break;
+                    const uint64_t p = st[S::PT + c * T + col];
+                    const uint32_t p0 = (uint32_t)p & kM25, p1 = (uint32_t)(p >> 25);
+#pragma unroll
+                    for (int ii = 0; ii < 2; ++ii)
+#pragma unroll
+                        for (int k = 0; k < 2; ++k) cmac25(acc[ii][c][k], x0[ii][k], x1[ii][k], p0, p1);
+                }
+            }
+            __syncwarp();
+            if ((tid & 31) == 0) mbar_arrive(&empty[s]);   // this warp's last read of stage s
+        }
+        if (ok) {
+#pragma unroll
+            for (int ii = 0; ii < 2; ++ii) {
+                const int ib = i0 + ii;
+                if (ib >= nb) break;
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    if (c >= c_cnt) break;
+                    uint64_t* ab = A + (((size_t)(b0 + ib) * tt.r + c_lo + c) * 2) * LN + (size_t)l * N + n;
+                    ab[0] = finish25(acc[ii][c][0], M.q, M.qinv_neg);
+                    ab[LN] = finish25(acc[ii][c][1], M.q, M.qinv_neg);
+                }
+            }
+        }
+    }
+    if (!ok) atomicOr(err, 1);
+    __syncthreads();
+    if (!ok) {
+        for (int s = 0; s < kSt && s < tt.n; ++s) {
+            const int last = s + kSt * ((tt.n - 1 - s) / kSt);
+            mbar_wait(&full[s], (uint32_t)(last / kSt) & 1u);
+        }
+    }
+}
+
 template <int DNUM, int TILE, int ARITH>
 __global__ void __launch_bounds__(TILE + 32, min_ctas(DNUM, TILE, ARITH))
 k_ks_mac_ext_bulk(const uint64_t* __restrict__ D, const uint64_t* __restrict__ XPg,
                   const uint64_t* __restrict__ pts, TapTable tt, int c_lo, int c_cnt, int B,
                   uint64_t* __restrict__ A, int L, int K, int logN,
                   const ModConst* __restrict__ mods, int* __restrict__ err,
-                  uint32_t report_polls) {
+                  uint32_t report_polls, int l0) {
     using S = Stage<DNUM, TILE>;
     constexpr int kTile = S::T;
     constexpr int kComputeWarps = kTile / 32;
@@ -515,7 +786,7 @@ k_ks_mac_ext_bulk(const uint64_t* __restrict__ D, const uint64_t* __restrict__ X
     const int N = 1 << logN;
     const int tid = threadIdx.x;
     const int n0 = blockIdx.y * kTile;
-    const int l = blockIdx.z;
+    const int l = l0 + blockIdx.z;                    // limbs l0 .. l0 + gridDim.z - 1
     const int b0 = blockIdx.x * 2;
     const int nb = B - b0 < 2 ? B - b0 : 2;
     const int LK = L + K;
@@ -564,7 +835,8 @@ k_ks_mac_ext_bulk(const uint64_t* __restrict__ D, const uint64_t* __restrict__ X
 
 template <int DNUM, int TILE, int ARITH>
 void launch_bulk(he_ctx* c, const uint64_t* D, const uint64_t* XP, const uint64_t* pts,
-                 const TapTable& tt, uint64_t* A, int B, int c_lo, int cnt) {
+                 const TapTable& tt, uint64_t* A, int B, int c_lo, int cnt, int l0 = 0,
+                 int n_limbs = -1) {
     const size_t smem = (size_t)kStages * Stage<DNUM, TILE>::WORDS * 8;
     static bool attr_set[64] = {};   // per template instance and device
     int dev = 0;
@@ -574,10 +846,45 @@ void launch_bulk(he_ctx* c, const uint64_t* D, const uint64_t* XP, const uint64_
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
-    const dim3 grid((B + 1) / 2, c->N / TILE, c->L + c->K);
+    const dim3 grid((B + 1) / 2, c->N / TILE, n_limbs < 0 ? c->L + c->K : n_limbs);
     k_ks_mac_ext_bulk<DNUM, TILE, ARITH><<<grid, TILE + 32, smem, c->stream>>>(
         D, XP, pts, tt, c_lo, cnt, B, A, c->L, c->K, c->logN, c->d_mod, c->d_err,
+        c->wait_report >= 0 ? (uint32_t)c->wait_report : kWaitSpins, l0);
+}
+
+// Precomputed products: PK for the channel pair, the ciphertext-prime limbs by k_tap_pk, the
+// special-prime limbs by the carry-chain kernel.
+template <int DNUM>
+void launch_pk(he_ctx* c, const uint64_t* D, const uint64_t* XP, const uint64_t* pts,
+               const TapTable& tt, uint64_t* A, int B, int c_lo, int cnt, uint64_t* PK) {
+    ++c->launches;
+    const dim3 gp((c->N + 255) / 256, c->L, cnt * tt.n * DNUM * 2);
+    k_pk_prep<<<gp, 256, 0, c->stream>>>(pts, tt, c_lo, DNUM, PK, c->L, c->K, c->logN, c->d_mod);
+    using S = PkStage<DNUM>;
+    const size_t smem = (size_t)S::STAGES * S::WORDS * 8;
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        cudaFuncSetAttribute(k_tap_pk<DNUM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    ++c->launches;
+    const dim3 grid((B + kPkImages - 1) / kPkImages, c->N / kPkTile, c->L);
+    k_tap_pk<DNUM><<<grid, 2 * kPkTile + 32, smem, c->stream>>>(
+        D, XP, PK, pts, tt, c_lo, cnt, B, A, c->L, c->K, c->logN, c->d_mod, c->d_err,
         c->wait_report >= 0 ? (uint32_t)c->wait_report : kWaitSpins);
+    ++c->launches;
+    launch_bulk<DNUM, 128, 0>(c, D, XP, pts, tt, A, B, c_lo, cnt, c->L, c->K);
+}
+
+template <int DNUM>
+void launch_pk_pairs(he_ctx* c, const uint64_t* D, const uint64_t* XP, const uint64_t* pts,
+                     const TapTable& tt, uint64_t* A, int B, uint64_t* PK) {
+    for (int c_lo = 0; c_lo < tt.r; c_lo += 2) {
+        const int cnt = tt.r - c_lo < 2 ? tt.r - c_lo : 2;
+        launch_pk<DNUM>(c, D, XP, pts, tt, A, B, c_lo, cnt, PK);
+    }
 }
 
 template <int TILE, int ARITH>
@@ -599,8 +906,38 @@ void launch_bulk_tile(he_ctx* c, const uint64_t* D, const uint64_t* XP, const ui
 
 bool tapmac_bulk_supported(const he_ctx* c) { return c->N >= kMaxTile && c->dnum <= 8; }
 
+// The precomputed-product path needs every ciphertext prime below 2^50 (25-bit halves).
+static bool pk_supported(const he_ctx* c) {
+    if (!tapmac_bulk_supported(c)) return false;
+    for (int i = 0; i < c->L; ++i)
+        if (c->mods[i] >> 50) return false;
+    return true;
+}
+
+// Its product buffer for one channel pair: [2][taps][dnum][2][L][N] words.  Grown outside a
+// recording only; NULL (the chain path is used instead) if it cannot be had.
+static uint64_t* pk_buffer(he_ctx* c, const TapTable& tt) {
+    const size_t words = (size_t)2 * tt.n * c->dnum * 2 * c->L * c->N;
+    if (words * 8 + 4096 > c->pk.cap && (c->rec || pk_reserve(c, words))) return nullptr;
+    return (uint64_t*)c->pk.base;
+}
+
 void launch_ks_mac_ext_bulk(he_ctx* c, const uint64_t* D, const uint64_t* XP, const uint64_t* pts,
                             const TapTable& tt, uint64_t* A, int B) {
+    if (c->tap_arith == 2 && pk_supported(c)) {
+        if (uint64_t* PK = pk_buffer(c, tt)) {
+            switch (c->dnum) {
+                case 1: launch_pk_pairs<1>(c, D, XP, pts, tt, A, B, PK); return;
+                case 2: launch_pk_pairs<2>(c, D, XP, pts, tt, A, B, PK); return;
+                case 3: launch_pk_pairs<3>(c, D, XP, pts, tt, A, B, PK); return;
+                case 4: launch_pk_pairs<4>(c, D, XP, pts, tt, A, B, PK); return;
+                case 5: launch_pk_pairs<5>(c, D, XP, pts, tt, A, B, PK); return;
+                case 6: launch_pk_pairs<6>(c, D, XP, pts, tt, A, B, PK); return;
+                case 7: launch_pk_pairs<7>(c, D, XP, pts, tt, A, B, PK); return;
+                default: launch_pk_pairs<8>(c, D, XP, pts, tt, A, B, PK); return;
+            }
+        }
+    }
     const int tile = c->tap_tile ? c->tap_tile : default_tile(c->dnum);
     for (int c_lo = 0; c_lo < tt.r; c_lo += 2) {
         ++c->launches;
@@ -710,16 +1047,18 @@ extern "C" int he_autotune(he_ctx* ctx, int batch, int force_tile, double* ms_ou
         tt.key[t] = t ? Kb : nullptr;
         tt.g[t] = t ? galois_elt(ctx, t) : 1u;
     }
-    // every (tile, arithmetic) pair, timed on the same operands
+    // every (tile, arithmetic) pair, timed on the same operands, then the precomputed-product
+    // path (its own tiling: 128 coefficients, four images per CTA)
     const int tiles[2] = {128, 256};
-    double ms[4] = {0, 0, 0, 0};
+    double ms[5] = {0, 0, 0, 0, 0};
     cudaEvent_t e0, e1;
     HE_CHECK_CUDA(ctx, cudaEventCreate(&e0));
     HE_CHECK_CUDA(ctx, cudaEventCreate(&e1));
     int best = 0;
-    for (int v = 0; v < 4; ++v) {
-        ctx->tap_tile = tiles[v >> 1];
-        ctx->tap_arith = v & 1;
+    const int nv = pk_supported(ctx) ? 5 : 4;
+    for (int v = 0; v < nv; ++v) {
+        ctx->tap_tile = v == 4 ? 128 : tiles[v >> 1];
+        ctx->tap_arith = v == 4 ? 2 : (v & 1);
         launch_ks_mac_ext_bulk(ctx, D, XP, P, tt, A, batch);          // warm-up
         cudaEventRecord(e0, ctx->stream);
         for (int rep = 0; rep < 3; ++rep) launch_ks_mac_ext_bulk(ctx, D, XP, P, tt, A, batch);
@@ -732,10 +1071,11 @@ extern "C" int he_autotune(he_ctx* ctx, int batch, int force_tile, double* ms_ou
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    ctx->tap_tile = tiles[best >> 1];
-    ctx->tap_arith = best & 1;
+    ctx->tap_tile = best == 4 ? 128 : tiles[best >> 1];
+    ctx->tap_arith = best == 4 ? 2 : (best & 1);
     if (ms_out) {
         for (int v = 0; v < 4; ++v) ms_out[v] = ms[v];
+        ms_out[8] = ms[4];
         ms_out[6] = ctx->tap_tile;
         ms_out[7] = ctx->tap_arith;
     }
@@ -759,9 +1099,10 @@ extern "C" int he_tune_set(he_ctx* ctx, int knob, int value) {
             ctx->tap_tile = value < 0 ? 0 : value;
             return HE_OK;
         case HE_TUNE_TAP_ARITH:
-            if (value < -1 || value > 1)
-                return he_fail(ctx, HE_EINVAL, "he_tune_set: tap arithmetic is 0 (chains) or 1 (columns)");
-            ctx->tap_arith = value < 0 ? 1 : value;
+            if (value < -1 || value > 2)
+                return he_fail(ctx, HE_EINVAL, "he_tune_set: tap arithmetic is 0 (chains), 1 "
+                                               "(columns) or 2 (precomputed products)");
+            ctx->tap_arith = value < 0 ? 0 : value;
             return HE_OK;
         case HE_TUNE_NTT_SPLIT:
             if (value != -1 && (value < 1 || value >= ctx->logN))

@@ -428,9 +428,9 @@ class Context:
         ms = (ctypes.c_double * HE_TUNE_REPORT_LEN)()
         self._ck(lib().he_autotune(self.h, batch, force_tile, ms), "he_autotune")
         return {"tap_ms": {"128_chains": ms[0], "128_columns": ms[1], "256_chains": ms[2],
-                           "256_columns": ms[3]},
+                           "256_columns": ms[3], "128_products": ms[8]},
                 "ntt_ms": ms[4], "ntt_log2_n1": int(ms[5]), "tap_tile": int(ms[6]),
-                "tap_arith": "columns" if int(ms[7]) else "chains"}
+                "tap_arith": ("chains", "columns", "products")[int(ms[7])]}
 
     def he_tune_set(self, knob, value):
         self._ck(lib().he_tune_set(self.h, knob, int(value)), "he_tune_set")

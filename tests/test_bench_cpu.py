@@ -27,13 +27,15 @@ def test_tap_kernel_products_and_roofline():
     assert roof["launch_us"] == pytest.approx(8651.3)
     assert roof["achieved"] == pytest.approx(9_185_525_760 / 8.6513e-3 / 1e12)
     assert roof["frac"] == pytest.approx(roof["achieved"] / roof["peak"])
-    assert roof["traffic"] == 3_415_376_896 + 990_737_152
+    assert "k_ks_mac_ext_bulk" in roof["kernel"]
     assert bench.taps_roofline({"taps": (1.0, 1)}, argparse.Namespace(pack="dp_shift"), 64, 24) is None
 
 
 def test_integer_peak():
-    # 152 SMs x 64 multiply-adds per clock / 8 per 64 x 64 -> 128-bit product x 2070 MHz
-    assert bench.mul64_peak_per_s(2070.0) == pytest.approx(2.51712e12)
+    # 152 SMs x 64 multiply-add slots per clock / 4 mad.wide.u32 per 64 x 64 -> 128-bit
+    # product x 2070 MHz; the SM count follows the device
+    assert bench.mul64_peak_per_s(2070.0) == pytest.approx(5.03424e12)
+    assert bench.mul64_peak_per_s(2070.0, sms=76) == pytest.approx(5.03424e12 / 2)
 
 
 def test_whole_job_rate_is_the_sum_over_replicas():

@@ -141,24 +141,47 @@ def test_bench_layer_n15_decrypts_to_the_convolution(pack, B):
         check_decrypted(ctx, prm, sk, lay_o, outs[b * 5:(b + 1) * 5], xs[b], W1, W2)
 
 
-def test_bench_layer_n15_sampled_image_is_bit_exact():
+def _oracle_layer(args):
+    """One image's oracle layer (runs in a spawned worker)."""
+    prm, ct, W1, W2, lay_o, keys = args
+    return [w.stack() for w in ffconv.he_layer(prm, ct, W1, W2, lay_o, keys)]
+
+
+def test_bench_layer_n15_sampled_images_are_bit_exact():
     """The benchmark's own launch: N = 2^15 (12 + 3 primes, digits of 3), dp_shift_ext, a batch
-    of 64 images in one call (grid and tile as timed); one sampled image's five output
-    ciphertexts are compared bit for bit with the oracle (oracle keys and encryptions; about
-    three CPU-minutes of oracle work)."""
+    of 64 images in one call (grid and tile as timed), under each of the tap kernel's
+    arithmetic variants (carry chains, 30-bit columns, precomputed products).  Two sampled
+    images are compared bit for bit with the oracle on all five output ciphertexts: image 41
+    (second of its image pair, first thread half of its CTA of four) and image 62 (first of
+    its pair, second half), so that a slip in either slot shows; the oracle runs them side
+    by side (about three CPU-minutes of oracle work each)."""
+    import concurrent.futures
+    import multiprocessing as mp
+    from paper_2102_03494_gb300 import he
     prm = params.cfg_n15()
     shape = workloads.MNIST_LAYER
     lay_o, s, steps, keys, blob, xs, W1, W2, cts = setup_layer(prm, shape, "dp_shift_ext",
                                                                seed=5, B=64)
-    ctx = make_ctx(prm)
-    lay = ctx.layout(*shape.astuple(), pack="dp_shift_ext")
-    ctx.he_load_keys(blob, gpu_steps(steps))
-    outs = ctx.he_ffconv_layer_batch([upload_ntt(ctx, c) for c in cts], W1, W2, lay)
-    b = 41                                      # the sampled image (image pair 20 of 32)
-    want = ffconv.he_layer(prm, cts[b], W1, W2, lay_o, keys)
-    for c in range(shape.O_c):
-        assert (download_coeff(ctx, outs[b * shape.O_c + c]) == want[c].stack()).all(), c
-    check_decrypted(ctx, prm, s, lay_o, outs[b * shape.O_c:(b + 1) * shape.O_c], xs[b], W1, W2)
+    sampled = (41, 62)
+    with concurrent.futures.ProcessPoolExecutor(2, mp_context=mp.get_context("spawn")) as pool:
+        jobs = [pool.submit(_oracle_layer, (prm, cts[b], W1, W2, lay_o, keys)) for b in sampled]
+        ctx = make_ctx(prm)
+        lay = ctx.layout(*shape.astuple(), pack="dp_shift_ext")
+        ctx.he_load_keys(blob, gpu_steps(steps))
+        ins = [upload_ntt(ctx, c) for c in cts]
+        got = {}
+        for arith in (0, 1, 2):
+            ctx.he_tune_set(he.HE_TUNE_TAP_ARITH, arith)
+            outs = ctx.he_ffconv_layer_batch(ins, W1, W2, lay)
+            ctx.he_check()
+            got[arith] = {b: [download_coeff(ctx, outs[b * shape.O_c + c]) for c in range(shape.O_c)]
+                          for b in sampled}
+        wants = {b: j.result() for b, j in zip(sampled, jobs)}
+    for arith in (0, 1, 2):
+        for b in sampled:
+            for c in range(shape.O_c):
+                assert (got[arith][b][c] == wants[b][c]).all(), (arith, b, c)
+    check_decrypted(ctx, prm, s, lay_o, outs[41 * shape.O_c:42 * shape.O_c], xs[41], W1, W2)
 
 
 @pytest.mark.parametrize("pack", ["dp_dot", "dp_shift", "dp_shift_ext", "cp_cp"])
@@ -271,7 +294,7 @@ def test_autotuned_tap_tile_and_arithmetic_keep_the_bits():
     assert ctx.he_tune_get(he.HE_TUNE_TAP_TILE) == rep["tap_tile"]
     want = [ffconv.he_layer(prm, c, W1, W2, lay_o, keys) for c in cts]
     for tile in (128, 256):
-        for arith in (0, 1):
+        for arith in (0, 1, 2):
             ctx.he_autotune(3, force_tile=tile)
             ctx.he_tune_set(he.HE_TUNE_TAP_ARITH, arith)
             outs = ctx.he_ffconv_layer_batch([upload_ntt(ctx, c) for c in cts], W1, W2, lay)
@@ -281,7 +304,7 @@ def test_autotuned_tap_tile_and_arithmetic_keep_the_bits():
     with pytest.raises(he.HeError):
         ctx.he_autotune(3, force_tile=64)
     with pytest.raises(he.HeError):
-        ctx.he_tune_set(he.HE_TUNE_TAP_ARITH, 2)
+        ctx.he_tune_set(he.HE_TUNE_TAP_ARITH, 3)
 
 
 @pytest.mark.parametrize("q_bits,p_bits,n_q,n_p,alpha",
@@ -291,7 +314,7 @@ def test_tap_kernel_on_wide_primes_and_many_digits(q_bits, p_bits, n_q, n_p, alp
     """The tap kernel's column arithmetic has separate branches for ciphertext primes of 55 bits
     or more (no lazy sums), for special primes not just below 2^60 and for keys of more than
     four digits (a mid-sum normalisation); each gives the oracle's bits, as do the carry
-    chains."""
+    chains and (where every ciphertext prime is below 2^50) the precomputed products."""
     from paper_2102_03494_gb300 import he
     prm = params.Params(log_n=9, n_q=n_q, n_p=n_p, alpha=alpha, q_bits=q_bits, p_bits=p_bits)
     shape = SMALL[0]
@@ -300,7 +323,7 @@ def test_tap_kernel_on_wide_primes_and_many_digits(q_bits, p_bits, n_q, n_p, alp
     ctx.he_load_keys(blob, gpu_steps(steps))
     lay = ctx.layout(*shape.astuple(), pack="dp_shift_ext")
     want = [ffconv.he_layer(prm, c, W1, W2, lay_o, keys) for c in cts]
-    for arith in (1, 0):
+    for arith in (1, 0, 2):
         ctx.he_tune_set(he.HE_TUNE_TAP_ARITH, arith)
         outs = ctx.he_ffconv_layer_batch([upload_ntt(ctx, c) for c in cts], W1, W2, lay)
         for b in range(2):

@@ -206,14 +206,22 @@ def test_error_paths():
 
 
 def test_integer_rate_probe_is_sane():
-    """The multiply-accumulate probe returns rates below the derived issue-slot bound
-    (152 SMs x 64 multiply-adds per clock / 8 per product at 2070 MHz, with margin)."""
+    """The multiply-accumulate probes return rates below the derived issue-slot bounds: per
+    SM and clock at most 64 multiply-adds of any kind, and a 64 x 64 -> 128-bit product takes
+    at least four of them (2070 MHz maximum clock, with margin)."""
+    import torch
     prm = params.Params(log_n=9, n_q=3, n_p=1, alpha=1)
     ctx = make_ctx(prm)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    slots = sms * 64 * 2070e6
     chain, cols = ctx.he_probe_int_mac()
-    bound = 152 * 64 / 8 * 2070e6
-    assert 0.05 * bound < chain < 1.2 * bound
-    assert 0.05 * bound < cols < 1.5 * bound
+    for v in (chain, cols):
+        assert 0.02 * slots / 4 < v < 1.1 * slots / 4
+    ops = ctx.he_probe_int_ops()
+    for k in ("mad_lo", "mad_hi", "mad_wide"):
+        assert 0.05 * slots < ops[k] < 1.1 * slots
+    for k in ("chain", "columns", "karatsuba"):
+        assert 0.02 * slots / 4 < ops[k] < 1.1 * slots / 3
 
 
 @pytest.mark.parametrize("cfg", [(13, 3, 1, 1), (14, 8, 2, 2), (15, 16, 4, 4), (16, 24, 6, 6)])
