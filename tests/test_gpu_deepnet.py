@@ -49,8 +49,11 @@ def encrypt_tensor(prm, s, x, shape, seed):
     return [encrypt_slots(prm, s, v, seed + i) for i, v in enumerate(deepnet.pack_tensor(x, shape, prm.n))]
 
 
-def test_layers_are_bit_exact(small):
+@pytest.mark.parametrize("arith", [0, 2], ids=["chains", "products"])
+def test_layers_are_bit_exact(small, arith):
     prm, ctx, s, keys, rlk = small
+    from paper_2102_03494_gb300 import he as _he
+    ctx.he_tune_set(_he.HE_TUNE_TAP_ARITH, arith)   # the tap kernel's arithmetic (same bits)
     w = deepnet.rand_weights(SHAPE, 3)
     convs = gpu_convs(ctx, SHAPE)
     rng = np.random.default_rng(4)
@@ -102,9 +105,12 @@ def test_pool_and_classifier_are_bit_exact(small):
         assert (download_coeff(ctx, got[b]) == want.stack()).all(), b
 
 
-def test_network_is_bit_exact(small):
+@pytest.mark.parametrize("arith", [0, 2], ids=["chains", "products"])
+def test_network_is_bit_exact(small, arith):
     from paper_2102_03494_gb300 import he
     prm, ctx, s, keys, rlk = small
+    from paper_2102_03494_gb300 import he as _he
+    ctx.he_tune_set(_he.HE_TUNE_TAP_ARITH, arith)   # the tap kernel's arithmetic (same bits)
     w = deepnet.rand_weights(SHAPE, 6)
     convs = gpu_convs(ctx, SHAPE)
     steps = ctx.he_deep_required_steps(convs, SHAPE.n_cls)

@@ -71,9 +71,12 @@ def test_multiply_batch_is_bit_exact(small):
 
 @pytest.mark.parametrize("m,n_in,per,spread", [(20, 108, 1024, True), (4, 20, 32, False),
                                                (100, 300, 1024, True), (1, 7, 8, False)])
-def test_fc_layer_is_bit_exact(small, m, n_in, per, spread):
+@pytest.mark.parametrize("arith", [0, 2], ids=["chains", "products"])
+def test_fc_layer_is_bit_exact(small, m, n_in, per, spread, arith):
     """spread: sparse positions over a whole row (period N/2); else dense, repeating."""
     prm, ctx, s, keys, rlk = small
+    from paper_2102_03494_gb300 import he as _he
+    ctx.he_tune_set(_he.HE_TUNE_TAP_ARITH, arith)   # the tap kernel's arithmetic (same bits)
     half = prm.n // 2
     rng = np.random.default_rng(m + n_in)
     pos = (sorted(rng.choice(per, size=n_in, replace=False).tolist()) if spread
@@ -111,8 +114,11 @@ def test_combine_is_bit_exact(small):
         assert (download_coeff(ctx, got[b]) == want.stack()).all(), b
 
 
-def test_network_is_bit_exact(small):
+@pytest.mark.parametrize("arith", [0, 2], ids=["chains", "products"])
+def test_network_is_bit_exact(small, arith):
     prm, ctx, s, keys, rlk = small
+    from paper_2102_03494_gb300 import he as _he
+    ctx.he_tune_set(_he.HE_TUNE_TAP_ARITH, arith)   # the tap kernel's arithmetic (same bits)
     imgs, cts = [], []
     for b in range(2):
         x, W1, W2, F1, F2 = rand_net(SMALL, M1, M2, seed=7)      # shared weights
