@@ -790,7 +790,6 @@ k_ks_mac_ext_bulk(const uint64_t* __restrict__ D, const uint64_t* __restrict__ X
     const int b0 = blockIdx.x * 2;
     const int nb = B - b0 < 2 ? B - b0 : 2;
     const int LK = L + K;
-    const bool qlimb = l < L;
     const size_t LN = (size_t)LK * N;
     const size_t LNq = (size_t)L * N;
     if (tid == 0) {
