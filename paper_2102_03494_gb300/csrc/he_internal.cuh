@@ -47,28 +47,26 @@ __device__ __forceinline__ uint64_t sub_mod(uint64_t a, uint64_t b, uint64_t q) 
 __device__ __forceinline__ uint64_t neg_mod(uint64_t a, uint64_t q) { return a ? q - a : 0; }
 
 // High 64 bits of a 64 x 64-bit product from 32-bit partial products in one carry chain (the
-// low word of a0 b0 cannot carry: it is never added to).  Operands and result pass as 64-bit
-// registers and are split into 32-bit halves inside the block, so no moves are needed to
-// pack and unpack them around it.
+// low word of a0 b0 cannot carry: it is never added to).
+#pragma nv_diag_suppress 550   // c1 below is written by the chain and read only through carries
 __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) {
-    uint64_t r;
-    asm("{\n\t.reg .u32 a0, a1, b0, b1, c1, c2, c3;\n\t"
-        "mov.b64 {a0, a1}, %1;\n\t"
-        "mov.b64 {b0, b1}, %2;\n\t"
-        "mul.hi.u32 c1, a0, b0;\n\t"
-        "mul.lo.u32 c2, a1, b1;\n\t"
-        "mul.hi.u32 c3, a1, b1;\n\t"
-        "mad.lo.cc.u32 c1, a0, b1, c1;\n\t"
-        "madc.hi.cc.u32 c2, a0, b1, c2;\n\t"
-        "addc.u32 c3, c3, 0;\n\t"
-        "mad.lo.cc.u32 c1, a1, b0, c1;\n\t"
-        "madc.hi.cc.u32 c2, a1, b0, c2;\n\t"
-        "addc.u32 c3, c3, 0;\n\t"
-        "mov.b64 %0, {c2, c3};\n\t}"
-        : "=l"(r)
-        : "l"(a), "l"(b));
-    return r;   // c1 (bits 32..63) only feeds the carries
+    const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32);
+    const uint32_t b0 = (uint32_t)b, b1 = (uint32_t)(b >> 32);
+    uint32_t c1, c2, c3;
+    asm("mul.hi.u32 %0, %3, %5;\n\t"
+        "mul.lo.u32 %1, %4, %6;\n\t"
+        "mul.hi.u32 %2, %4, %6;\n\t"
+        "mad.lo.cc.u32 %0, %3, %6, %0;\n\t"
+        "madc.hi.cc.u32 %1, %3, %6, %1;\n\t"
+        "addc.u32 %2, %2, 0;\n\t"
+        "mad.lo.cc.u32 %0, %4, %5, %0;\n\t"
+        "madc.hi.cc.u32 %1, %4, %5, %1;\n\t"
+        "addc.u32 %2, %2, 0;"
+        : "=&r"(c1), "=&r"(c2), "=&r"(c3)
+        : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
+    return ((uint64_t)c3 << 32) | c2;   // c1 (bits 32..63) only feeds the carries
 }
+#pragma nv_diag_default 550
 
 // x * w mod q, x any 64-bit value, w < q, ws = floor(w 2^64 / q).
 __device__ __forceinline__ uint64_t mul_shoup(uint64_t x, uint64_t w, uint64_t ws, uint64_t q) {
@@ -198,6 +196,7 @@ struct he_ctx {
     Arena pk;                           // the tap kernel's plaintext x key products (tapmac.cu)
     int tap_tile = 0;                   // tap kernel tile chosen by he_autotune (0: default)
     int ntt_s1 = 0;                     // NTT split log2 N1 chosen by he_autotune (0: default)
+    int ntt_radix = 0;                  // NTT rounds of up to 2^ntt_radix points (0: 3, radix 8)
     int tap_arith = 0;                  // tap kernel: 0 carry chains, 1 30-bit columns,
                                         // 2 precomputed plaintext x key products
     int wait_report = -1;               // he_set_wait_report: polls before a stage wait is

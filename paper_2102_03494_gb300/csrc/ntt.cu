@@ -15,7 +15,14 @@
 // elements of a group share all index bits except the round's K stage bits.  Rounds exchange
 // through shared memory; the first round reads global memory directly and the last writes it.
 // Butterflies use Harvey's lazy reduction: forward values stay in [0, 4q), inverse values in
-// [0, 2q), and are brought to [0, q) at the end (moduli below 2^62).
+// [0, 2q), and are brought to [0, q) at the end (moduli below 2^62).  Forward transforms of a
+// modulus below 2^57 ("small") skip the per-butterfly reduction altogether and estimate the
+// Shoup quotient from three partial products: each stage adds less than 4q to a value, so
+// after at most 16 stages every value stays below 4q + 64q < 2^64, and the pass's last write
+// reduces it exactly (conditional subtractions of 64q, 32q, ..., q).  The output is the same
+// residue in [0, q).
+// Rounds hold up to 2^K elements per group with K <= the context's radix cap (log2 of 2, 4 or
+// 8; the autotuner picks it).
 #include "he_internal.cuh"
 
 namespace {
@@ -28,6 +35,16 @@ __device__ __forceinline__ void bfly_ct(uint64_t& X, uint64_t& Y, const ShoupPai
     uint64_t t = mul_shoup_lazy(Y, W.w, W.ws, q);    // [0, 2q)
     X = x + t;                                       // [0, 4q)
     Y = x - t + q2;                                  // (0, 4q)
+}
+
+// Forward butterfly without reduction (small moduli): t in [0, 4q), X + t and X - t + 4q grow
+// by less than 4q per stage.
+__device__ __forceinline__ void bfly_ct_small(uint64_t& X, uint64_t& Y, const ShoupPair& W,
+                                              uint64_t q, uint64_t q4) {
+    const uint64_t t = mul_shoup_approx(Y, W.w, W.ws, q);
+    const uint64_t x = X;
+    X = x + t;
+    Y = x - t + q4;
 }
 
 __device__ __forceinline__ void bfly_gs(uint64_t& X, uint64_t& Y, const ShoupPair& W, uint64_t q,
@@ -43,7 +60,7 @@ __device__ __forceinline__ void bfly_gs(uint64_t& X, uint64_t& Y, const ShoupPai
 // group g at x[g * 2^K + m].  Twiddle of stage ee for element m of a group whose block index
 // is `hi` (plus the block offset `toff` of the row pass): psi^brv(2^s + toff 2^ee + hi 2^ee
 // + (m >> (K - ee))).
-template <int K, bool INV>
+template <int K, bool INV, bool SMALL>
 __device__ __forceinline__ void round_bflies(uint64_t (&x)[8], const int (&hi)[8 >> K], int s0,
                                              int toff, const ShoupPair* __restrict__ w,
                                              uint64_t q, uint64_t q2) {
@@ -61,6 +78,7 @@ __device__ __forceinline__ void round_bflies(uint64_t (&x)[8], const int (&hi)[8
                 if (m & d) continue;
                 const ShoupPair W = w[(1 << s) + (base_hi << ee) + (m >> (K - ee))];
                 if (INV) bfly_gs(x[g * M + m], x[g * M + m + d], W, q, q2);
+                else if (SMALL) bfly_ct_small(x[g * M + m], x[g * M + m + d], W, q, 2 * q2);
                 else bfly_ct(x[g * M + m], x[g * M + m + d], W, q, q2);
             }
         }
@@ -70,7 +88,7 @@ __device__ __forceinline__ void round_bflies(uint64_t (&x)[8], const int (&hi)[8
 // One round of the column pass.  Element m of group Gi: column c = Gi mod cols, row
 // hi (tlow 2^K) + m tlow + lo with (hi, lo) = divmod(Gi / cols, tlow).  cols = 2^lc and
 // tlow = 2^(s1 - e0 - K), so the divisions are shifts.
-template <int K, bool INV>
+template <int K, bool INV, bool SMALL>
 __device__ __forceinline__ void col_round(uint64_t (&x)[8], uint64_t* sm, uint64_t* __restrict__ a,
                                           bool first, bool last, int e0, int s1, int N2, int lo0,
                                           int lc, const ShoupPair* __restrict__ w,
@@ -102,7 +120,7 @@ __device__ __forceinline__ void col_round(uint64_t (&x)[8], uint64_t* sm, uint64
         for (int i = 0; i < 8; ++i) x[i] = sm[off[i]];
     }
     const uint64_t q = Mc.q, q2 = 2 * q;
-    round_bflies<K, INV>(x, hi, e0, 0, w, q, q2);
+    round_bflies<K, INV, SMALL>(x, hi, e0, 0, w, q, q2);
     if (last) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -120,7 +138,7 @@ __device__ __forceinline__ void col_round(uint64_t (&x)[8], uint64_t* sm, uint64
 
 // One round of the row pass.  Element m of group Gi: block b = Gi / (N2 >> K) of the tile,
 // local index hi (tlow 2^K) + m tlow + lo.
-template <int K, bool INV>
+template <int K, bool INV, bool SMALL>
 __device__ __forceinline__ void row_round(uint64_t (&x)[8], uint64_t* sm, uint64_t* __restrict__ a,
                                           bool first, bool last, int e0, int s1, int s2, int blk0,
                                           const ShoupPair* __restrict__ w, const ModConst& Mc) {
@@ -158,12 +176,18 @@ __device__ __forceinline__ void row_round(uint64_t (&x)[8], uint64_t* sm, uint64
     int hh[8 >> K];
 #pragma unroll
     for (int g = 0; g < (8 >> K); ++g) hh[g] = ((blk0 + blk[g]) << e0) + hi[g];
-    round_bflies<K, INV>(x, hh, s1 + e0, 0, w, q, q2);
+    round_bflies<K, INV, SMALL>(x, hh, s1 + e0, 0, w, q, q2);
     if (last) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             uint64_t v = x[i];
-            if (!INV) {
+            if (!INV && SMALL) {                        // v < 68 q: subtract 64 q, ..., q
+#pragma unroll
+                for (int sh = 6; sh >= 0; --sh) {
+                    const uint64_t m = q << sh;
+                    v = v >= m ? v - m : v;
+                }
+            } else if (!INV) {
                 v = v >= q2 ? v - q2 : v;
                 v = v >= q ? v - q : v;
             }
@@ -177,62 +201,81 @@ __device__ __forceinline__ void row_round(uint64_t (&x)[8], uint64_t* sm, uint64
 }
 
 // Rounds of a pass of 2^lg points: forward e0 = 0, 3, 6, ...; inverse from the top down.
-__device__ __forceinline__ void round_of(int r, int lg, bool inv, int& e0, int& K) {
+__device__ __forceinline__ void round_of(int r, int lg, bool inv, int kmax, int& e0, int& K) {
     if (!inv) {
-        e0 = 3 * r;
-        K = min(3, lg - e0);
+        e0 = kmax * r;
+        K = min(kmax, lg - e0);
     } else {
-        const int top = lg - 3 * r;
-        K = min(3, top);
+        const int top = lg - kmax * r;
+        K = min(kmax, top);
         e0 = top - K;
     }
 }
 
-template <bool INV>
+template <bool INV, bool SMALL, int KMAX>
+__device__ __forceinline__ void ntt_cols_body(uint64_t* __restrict__ a, uint64_t* sm, int logN,
+                                              int s1, int lc, int lo0,
+                                              const ShoupPair* __restrict__ w, const ModConst& Mc) {
+    const int N2 = (1 << logN) >> s1;
+    const int nr = (s1 + KMAX - 1) / KMAX;
+    uint64_t x[8];
+    for (int r = 0; r < nr; ++r) {
+        int e0, K;
+        round_of(r, s1, INV, KMAX, e0, K);
+        const bool first = r == 0, last = r == nr - 1;
+        if (KMAX == 3 && K == 3) col_round<3, INV, SMALL>(x, sm, a, first, last, e0, s1, N2, lo0, lc, w, Mc);
+        else if (K == 2) col_round<2, INV, SMALL>(x, sm, a, first, last, e0, s1, N2, lo0, lc, w, Mc);
+        else col_round<1, INV, SMALL>(x, sm, a, first, last, e0, s1, N2, lo0, lc, w, Mc);
+    }
+}
+
+template <bool INV, bool SMALL, int KMAX>
+__device__ __forceinline__ void ntt_rows_body(uint64_t* __restrict__ a, uint64_t* sm, int logN,
+                                              int s1, int blk0,
+                                              const ShoupPair* __restrict__ w, const ModConst& Mc) {
+    const int s2 = logN - s1;
+    const int nr = (s2 + KMAX - 1) / KMAX;
+    uint64_t x[8];
+    for (int r = 0; r < nr; ++r) {
+        int e0, K;
+        round_of(r, s2, INV, KMAX, e0, K);
+        const bool first = r == 0, last = r == nr - 1;
+        if (KMAX == 3 && K == 3) row_round<3, INV, SMALL>(x, sm, a, first, last, e0, s1, s2, blk0, w, Mc);
+        else if (K == 2) row_round<2, INV, SMALL>(x, sm, a, first, last, e0, s1, s2, blk0, w, Mc);
+        else row_round<1, INV, SMALL>(x, sm, a, first, last, e0, s1, s2, blk0, w, Mc);
+    }
+}
+
+// The forward transform of a modulus below 2^57 takes the unreduced butterflies (SMALL, see
+// the header); the launcher splits a launch's limbs by that test.
+bool small_mod(uint64_t q) { return (q >> 57) == 0; }
+
+template <bool INV, bool SMALL, int KMAX>
 __global__ void __launch_bounds__(256, 4)
 k_ntt_cols(uint64_t* __restrict__ data, size_t item_stride, int mod_off, int logN, int s1, int lc,
            const ModConst* __restrict__ mods, const ShoupPair* __restrict__ tw) {
     __shared__ uint64_t sm[kTile];
-    const int N = 1 << logN, N2 = N >> s1;
+    const int N = 1 << logN;
     const int mod = mod_off + blockIdx.y;
     const ModConst Mc = mods[mod];
     const ShoupPair* w = tw + (size_t)mod * N;
     uint64_t* a = data + blockIdx.z * item_stride + (size_t)blockIdx.y * N;
     const int lo0 = blockIdx.x << lc;
-    const int nr = (s1 + 2) / 3;
-    uint64_t x[8];
-    for (int r = 0; r < nr; ++r) {
-        int e0, K;
-        round_of(r, s1, INV, e0, K);
-        const bool first = r == 0, last = r == nr - 1;
-        if (K == 3) col_round<3, INV>(x, sm, a, first, last, e0, s1, N2, lo0, lc, w, Mc);
-        else if (K == 2) col_round<2, INV>(x, sm, a, first, last, e0, s1, N2, lo0, lc, w, Mc);
-        else col_round<1, INV>(x, sm, a, first, last, e0, s1, N2, lo0, lc, w, Mc);
-    }
+    ntt_cols_body<INV, SMALL, KMAX>(a, sm, logN, s1, lc, lo0, w, Mc);
 }
 
-template <bool INV>
+template <bool INV, bool SMALL, int KMAX>
 __global__ void __launch_bounds__(256, 4)
 k_ntt_rows(uint64_t* __restrict__ data, size_t item_stride, int mod_off, int logN, int s1, int blocks,
            const ModConst* __restrict__ mods, const ShoupPair* __restrict__ tw) {
     __shared__ uint64_t sm[kTile];
     const int N = 1 << logN;
-    const int s2 = logN - s1;
     const int mod = mod_off + blockIdx.y;
     const ModConst Mc = mods[mod];
     const ShoupPair* w = tw + (size_t)mod * N;
     uint64_t* a = data + blockIdx.z * item_stride + (size_t)blockIdx.y * N;
     const int blk0 = blockIdx.x * blocks;
-    const int nr = (s2 + 2) / 3;
-    uint64_t x[8];
-    for (int r = 0; r < nr; ++r) {
-        int e0, K;
-        round_of(r, s2, INV, e0, K);
-        const bool first = r == 0, last = r == nr - 1;
-        if (K == 3) row_round<3, INV>(x, sm, a, first, last, e0, s1, s2, blk0, w, Mc);
-        else if (K == 2) row_round<2, INV>(x, sm, a, first, last, e0, s1, s2, blk0, w, Mc);
-        else row_round<1, INV>(x, sm, a, first, last, e0, s1, s2, blk0, w, Mc);
-    }
+    ntt_rows_body<INV, SMALL, KMAX>(a, sm, logN, s1, blk0, w, Mc);
 }
 
 struct Split {
@@ -295,26 +338,51 @@ int ntt_split_candidates(int logN, int* out, int cap) {
     return n;
 }
 
+template <bool INV, bool SMALL, int KMAX>
+void launch_pass_pair(he_ctx* ctx, const Split& sp, uint64_t* d, int items, size_t item_stride,
+                      int rows, int mod) {
+    dim3 gc(sp.col_ctas, rows, items), gr(sp.row_ctas, rows, items);
+    ctx->launches += 2;
+    const ShoupPair* tw = INV ? ctx->d_tw_inv : ctx->d_tw_fwd;
+    if (!INV) {
+        k_ntt_cols<INV, SMALL, KMAX><<<gc, sp.col_threads, 0, ctx->stream>>>(
+            d, item_stride, mod, ctx->logN, sp.s1, sp.lc, ctx->d_mod, tw);
+        k_ntt_rows<INV, SMALL, KMAX><<<gr, sp.row_threads, 0, ctx->stream>>>(
+            d, item_stride, mod, ctx->logN, sp.s1, sp.blocks, ctx->d_mod, tw);
+    } else {
+        k_ntt_rows<INV, SMALL, KMAX><<<gr, sp.row_threads, 0, ctx->stream>>>(
+            d, item_stride, mod, ctx->logN, sp.s1, sp.blocks, ctx->d_mod, tw);
+        k_ntt_cols<INV, SMALL, KMAX><<<gc, sp.col_threads, 0, ctx->stream>>>(
+            d, item_stride, mod, ctx->logN, sp.s1, sp.lc, ctx->d_mod, tw);
+    }
+}
+
 void ntt_forward(he_ctx* ctx, uint64_t* data, int items, size_t item_stride, int rows,
                  int mod_off) {
     if (items <= 0 || rows <= 0) return;
-    ctx->launches += 2;
     const Split sp = split_of(ctx->logN, ctx->ntt_s1);
-    dim3 gc(sp.col_ctas, rows, items), gr(sp.row_ctas, rows, items);
-    k_ntt_cols<false><<<gc, sp.col_threads, 0, ctx->stream>>>(
-        data, item_stride, mod_off, ctx->logN, sp.s1, sp.lc, ctx->d_mod, ctx->d_tw_fwd);
-    k_ntt_rows<false><<<gr, sp.row_threads, 0, ctx->stream>>>(
-        data, item_stride, mod_off, ctx->logN, sp.s1, sp.blocks, ctx->d_mod, ctx->d_tw_fwd);
+    const bool r4 = ctx->ntt_radix == 2;
+    // runs of limbs of one kind (moduli below 2^57 or not), one launch pair each
+    for (int r0 = 0; r0 < rows;) {
+        const bool small = small_mod(ctx->mods[mod_off + r0]);
+        int r1 = r0 + 1;
+        while (r1 < rows && small_mod(ctx->mods[mod_off + r1]) == small) ++r1;
+        uint64_t* d = data + (size_t)r0 * ctx->N;
+        if (small) {
+            if (r4) launch_pass_pair<false, true, 2>(ctx, sp, d, items, item_stride, r1 - r0, mod_off + r0);
+            else launch_pass_pair<false, true, 3>(ctx, sp, d, items, item_stride, r1 - r0, mod_off + r0);
+        } else {
+            if (r4) launch_pass_pair<false, false, 2>(ctx, sp, d, items, item_stride, r1 - r0, mod_off + r0);
+            else launch_pass_pair<false, false, 3>(ctx, sp, d, items, item_stride, r1 - r0, mod_off + r0);
+        }
+        r0 = r1;
+    }
 }
 
 void ntt_inverse(he_ctx* ctx, uint64_t* data, int items, size_t item_stride, int rows,
                  int mod_off) {
     if (items <= 0 || rows <= 0) return;
-    ctx->launches += 2;
     const Split sp = split_of(ctx->logN, ctx->ntt_s1);
-    dim3 gc(sp.col_ctas, rows, items), gr(sp.row_ctas, rows, items);
-    k_ntt_rows<true><<<gr, sp.row_threads, 0, ctx->stream>>>(
-        data, item_stride, mod_off, ctx->logN, sp.s1, sp.blocks, ctx->d_mod, ctx->d_tw_inv);
-    k_ntt_cols<true><<<gc, sp.col_threads, 0, ctx->stream>>>(
-        data, item_stride, mod_off, ctx->logN, sp.s1, sp.lc, ctx->d_mod, ctx->d_tw_inv);
+    if (ctx->ntt_radix == 2) launch_pass_pair<true, false, 2>(ctx, sp, data, items, item_stride, rows, mod_off);
+    else launch_pass_pair<true, false, 3>(ctx, sp, data, items, item_stride, rows, mod_off);
 }

@@ -969,9 +969,11 @@ static int tune_ntt(he_ctx* ctx, int batch, double* best_ms) {
     HE_CHECK_CUDA(ctx, cudaEventCreate(&e0));
     HE_CHECK_CUDA(ctx, cudaEventCreate(&e1));
     double best = 1e30;
-    int best_s1 = cand[0];
-    for (int c = 0; c < nc; ++c) {
+    int best_s1 = cand[0], best_radix = 3;
+    for (int v = 0; v < 2 * nc; ++v) {                 // every split at radix 8, then radix 4
+        const int c = v % nc;
         ctx->ntt_s1 = cand[c];
+        ctx->ntt_radix = v < nc ? 3 : 2;
         ntt_forward(ctx, X, (int)items, (size_t)ctx->L * ctx->N, ctx->L, 0);     // warm-up
         ntt_inverse(ctx, X, (int)items, (size_t)ctx->L * ctx->N, ctx->L, 0);
         cudaEventRecord(e0, ctx->stream);
@@ -986,11 +988,13 @@ static int tune_ntt(he_ctx* ctx, int batch, double* best_ms) {
         if (t / 3.0 < best) {
             best = t / 3.0;
             best_s1 = cand[c];
+            best_radix = ctx->ntt_radix;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->ntt_s1 = best_s1;
+    ctx->ntt_radix = best_radix;
     *best_ms = best;
     return he_launch_check(ctx, "he_autotune");
 }
@@ -1012,6 +1016,7 @@ extern "C" int he_autotune(he_ctx* ctx, int batch, int force_tile, double* ms_ou
         for (int i = 0; i < HE_TUNE_REPORT_LEN; ++i) ms_out[i] = 0.0;
         ms_out[4] = ntt_ms;
         ms_out[5] = ctx->ntt_s1;
+        ms_out[9] = 1 << ctx->ntt_radix;
         ms_out[6] = default_tile(ctx->dnum);
         ms_out[7] = ctx->tap_arith;
     }
@@ -1108,6 +1113,11 @@ extern "C" int he_tune_set(he_ctx* ctx, int knob, int value) {
                 return he_fail(ctx, HE_EINVAL, "he_tune_set: NTT split log2 N1 out of range");
             ctx->ntt_s1 = value < 0 ? 0 : value;
             return HE_OK;
+        case HE_TUNE_NTT_RADIX:
+            if (value != -1 && value != 2 && value != 4 && value != 8)
+                return he_fail(ctx, HE_EINVAL, "he_tune_set: NTT radix is 2, 4 or 8");
+            ctx->ntt_radix = value < 0 ? 0 : (value == 8 ? 3 : value == 4 ? 2 : 1);
+            return HE_OK;
         default:
             return he_fail(ctx, HE_EINVAL, "he_tune_set: unknown knob");
     }
@@ -1119,6 +1129,7 @@ extern "C" int he_tune_get(he_ctx* ctx, int knob, int* value) {
         case HE_TUNE_TAP_TILE: *value = ctx->tap_tile ? ctx->tap_tile : default_tile(ctx->dnum); return HE_OK;
         case HE_TUNE_TAP_ARITH: *value = ctx->tap_arith; return HE_OK;
         case HE_TUNE_NTT_SPLIT: *value = ctx->ntt_s1 ? ctx->ntt_s1 : ctx->logN / 2; return HE_OK;
+        case HE_TUNE_NTT_RADIX: *value = 1 << (ctx->ntt_radix ? ctx->ntt_radix : 3); return HE_OK;
         default: return he_fail(ctx, HE_EINVAL, "he_tune_get: unknown knob");
     }
 }
