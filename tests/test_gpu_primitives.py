@@ -20,14 +20,22 @@ def brv(x, bits):
     return int(format(x, f"0{bits}b")[::-1], 2)
 
 
+@pytest.mark.parametrize("radix", [8, 4, 2])
 @pytest.mark.parametrize("cfg", [(6, 2, 1, 1), (9, 3, 1, 1), (13, 3, 1, 1), (14, 6, 2, 2),
                                  (15, 12, 3, 3), (16, 24, 6, 6)])
-def test_ntt_matches_oracle_evaluation(cfg):
+def test_ntt_matches_oracle_evaluation(cfg, radix):
+    """Forward / inverse NTT against the oracle's evaluation at the odd powers of psi, at every
+    radix the autotuner may pick; the second item holds q - 1 everywhere (the largest growth
+    of the unreduced forward butterflies used below 2^57)."""
     import torch
+    from paper_2102_03494_gb300 import he
     prm = params.Params(log_n=cfg[0], n_q=cfg[1], n_p=cfg[2], alpha=cfg[3])
     ctx = make_ctx(prm)
+    ctx.he_tune_set(he.HE_TUNE_NTT_RADIX, radix)
+    assert ctx.he_tune_get(he.HE_TUNE_NTT_RADIX) == radix
     items = 2
     a = np.stack([np.stack([np.random.default_rng(100 * i + l).integers(0, q, prm.n, dtype=np.uint64)
+                            if i == 0 else np.full(prm.n, q - 1, dtype=np.uint64)
                             for l, q in enumerate(prm.qp)]) for i in range(items)])
     d = ctx.from_numpy(a)
     ctx.he_ntt(d, items, len(prm.qp), inverse=False)
