@@ -395,12 +395,14 @@ def run(args):
     load(0)
     for i in range(args.steps):
         k = i & 1
-        if i + 1 < args.steps:
-            load(k ^ 1)
         stream.wait_event(ev_in[k])
         stream.wait_event(ev_out[k])                       # outputs two steps back copied out
         ctx.he_ffconv_layer_batch(sets[k][0], W1, W2, lay, sets[k][1])
         ev_used[k].record(stream)
+        # the next step's inputs: enqueued after the layer, so that the layer's own small
+        # uploads are not queued behind this large copy on the host-to-device copy engine
+        if i + 1 < args.steps:
+            load(k ^ 1)
         with torch.cuda.stream(down):
             down.wait_event(ev_used[k])
             h_out.copy_(blocks[k][1], non_blocking=True)
