@@ -392,7 +392,10 @@ int he_deep_batch(he_ctx* ctx, const he_ct* in, int B, const he_mc_conv* convs, 
 /* Autotuner of implementation parameters (no counterpart in the paper; results never depend
  * on them): (1) the split N = N1 N2 of the two-pass NTT and its radix (rounds of up to 8 or
  * up to 4 points per thread group), timing forward + inverse transforms of `batch`
- * ciphertexts for each candidate pair; (2) the fused tap kernel's tile (128 or 256
+ * ciphertexts for each candidate pair; (1b) the limb groups of the ModUp / ModDown base
+ * conversions (a thread converts all target limbs of a digit, half of them or a quarter: 1,
+ * 2 or 4 groups across the grid), timed on `batch` ciphertexts; (2) the fused tap kernel's
+ * tile (128 or 256
  * coefficients per CTA) and its arithmetic -- 0: 64 x 64-bit products in 32-bit multiply-add
  * carry chains; 1: 30-bit halves summed into 64-bit columns; 2: the plaintext x key products
  * precomputed per launch and every tap summed unreduced in 25-bit-split columns (ciphertext
@@ -403,7 +406,8 @@ int he_deep_batch(he_ctx* ctx, const he_ct* in, int B, const he_mc_conv* convs, 
  * [0..3] tap-kernel ms per launch for (tile 128, chains), (128, columns), (256, chains),
  * (256, columns); [4] the NTT time of the chosen split and [5] its log2 N1; [6] the chosen
  * tile; [7] the chosen arithmetic; [8] the precomputed-product path's ms (0 where it does not
- * apply); [9] the chosen NTT radix (8 or 4); the rest 0.  Without a call: tile 128 for keys of four or more digits (else 256),
+ * apply); [9] the chosen NTT radix (8 or 4); [10..12] the conversions' ms with 1, 2 and 4
+ * limb groups and [13] the chosen number; the rest 0.  Without a call: tile 128 for keys of four or more digits (else 256),
  * carry chains, split log2 N1 = floor(log2 N / 2).  Uses the context scratch; synchronises
  * the stream. */
 #define HE_TUNE_REPORT_LEN 16
@@ -411,10 +415,17 @@ int he_autotune(he_ctx* ctx, int batch, int force_tile, double* ms_out);
 /* Tuning knobs, set by hand (value -1 restores the default) or read back: HE_TUNE_TAP_TILE
  * (128 or 256), HE_TUNE_TAP_ARITH (0 chains, 1 columns, 2 precomputed products),
  * HE_TUNE_NTT_SPLIT (log2 N1, 1 .. log2 N - 1), HE_TUNE_NTT_RADIX (2, 4 or 8: the most points
- * a thread group transforms per round).  Results never depend on them.  he_tune_set is
+ * a thread group transforms per round), HE_TUNE_LIMB_GROUPS (1, 2 or 4).  Results never
+ * depend on them.  he_tune_set is
  * refused while recording.  The precomputed products take a grow-only buffer of 16 x taps x
  * dnum x n_q x N bytes, allocated at the first call that needs it (not while recording). */
-enum { HE_TUNE_TAP_TILE = 0, HE_TUNE_TAP_ARITH = 1, HE_TUNE_NTT_SPLIT = 2, HE_TUNE_NTT_RADIX = 3 };
+enum {
+    HE_TUNE_TAP_TILE = 0,
+    HE_TUNE_TAP_ARITH = 1,
+    HE_TUNE_NTT_SPLIT = 2,
+    HE_TUNE_NTT_RADIX = 3,
+    HE_TUNE_LIMB_GROUPS = 4
+};
 int he_tune_set(he_ctx* ctx, int knob, int value);
 int he_tune_get(he_ctx* ctx, int knob, int* value);
 

@@ -197,6 +197,8 @@ struct he_ctx {
     int tap_tile = 0;                   // tap kernel tile chosen by he_autotune (0: default)
     int ntt_s1 = 0;                     // NTT split log2 N1 chosen by he_autotune (0: default)
     int ntt_radix = 0;                  // NTT rounds of up to 2^ntt_radix points (0: 3, radix 8)
+    int limb_groups = 0;                // ModUp / ModDown conversions: target limbs split in
+                                        // this many groups across the grid (0: 1)
     int tap_arith = 0;                  // tap kernel: 0 carry chains, 1 30-bit columns,
                                         // 2 precomputed plaintext x key products
     int wait_report = -1;               // he_set_wait_report: polls before a stage wait is

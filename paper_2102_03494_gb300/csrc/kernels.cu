@@ -59,12 +59,15 @@ __global__ void k_modup(const uint64_t* __restrict__ x_coeff, size_t xc_stride,
                         const uint64_t* __restrict__ x_ntt, size_t xn_stride, uint32_t g_own,
                         uint64_t* __restrict__ out, size_t out_stride, int L, int K, int alpha,
                         int logN, const ModConst* __restrict__ mods,
-                        const ShoupPair* __restrict__ inv, const ShoupPair* __restrict__ cst) {
+                        const ShoupPair* __restrict__ inv, const ShoupPair* __restrict__ cst,
+                        int groups) {
     const int N = 1 << logN;
     const int n = blockIdx.y * blockDim.x + threadIdx.x;
     if (n >= N) return;
-    const int j = blockIdx.z;
+    const int j = blockIdx.z / groups;       // digit; the target limbs are split in `groups`
+    const int grp = blockIdx.z - j * groups;
     const int LK = L + K;
+    const int l_lo = grp * LK / groups, l_hi = (grp + 1) * LK / groups;
     const int i0 = j * alpha;
     const int i1 = min(i0 + alpha, L);
     const uint64_t* xc = x_coeff + blockIdx.x * xc_stride;
@@ -81,7 +84,7 @@ __global__ void k_modup(const uint64_t* __restrict__ x_coeff, size_t xc_stride,
         }
     }
     const uint32_t src = perm_src(n, g_own, logN);
-    for (int l = 0; l < LK; ++l) {
+    for (int l = l_lo; l < l_hi; ++l) {
         if (l >= i0 && l < i1) {
             o[(size_t)l * N + n] = xn[(size_t)l * N + src];
             continue;
@@ -131,11 +134,13 @@ __global__ void k_moddown_conv(const uint64_t* __restrict__ u, size_t u_stride,
                                uint64_t* __restrict__ v, size_t v_stride, int L, int K,
                                int logN, const ModConst* __restrict__ mods,
                                const ShoupPair* __restrict__ inv,
-                               const ShoupPair* __restrict__ cst) {
+                               const ShoupPair* __restrict__ cst, int groups) {
     const int N = 1 << logN;
     const int n = blockIdx.y * blockDim.x + threadIdx.x;
     if (n >= N) return;
-    const int k = blockIdx.z;  // polynomial 0 or 1
+    const int k = blockIdx.z / groups;       // polynomial 0 or 1; its limbs split in `groups`
+    const int grp = blockIdx.z - k * groups;
+    const int i_lo = grp * L / groups, i_hi = (grp + 1) * L / groups;
     const int LK = L + K;
     const uint64_t* ub = u + blockIdx.x * u_stride + (size_t)k * LK * N + (size_t)L * N;
     uint64_t y[8];                           // K <= 8; constant indices keep y in registers
@@ -148,7 +153,7 @@ __global__ void k_moddown_conv(const uint64_t* __restrict__ u, size_t u_stride,
         }
     }
     uint64_t* vb = v + blockIdx.x * v_stride + (size_t)k * L * N;
-    for (int i = 0; i < L; ++i) {
+    for (int i = i_lo; i < i_hi; ++i) {
         const uint64_t qi = mods[i].q;
         uint64_t acc = 0;
 #pragma unroll
@@ -782,9 +787,10 @@ void launch_automorph(he_ctx* c, const uint64_t* in, size_t in_stride, uint64_t*
 void launch_modup(he_ctx* c, const uint64_t* x_coeff, size_t xc_stride, const uint64_t* x_ntt,
                   size_t xn_stride, uint32_t g_own, uint64_t* out, size_t out_stride, int items) {
     ++c->launches;
-    k_modup<<<grid_nx(items, c->N, c->dnum), 256, 0, c->stream>>>(
+    const int g = c->limb_groups > 0 ? c->limb_groups : 1;
+    k_modup<<<grid_nx(items, c->N, c->dnum * g), 256, 0, c->stream>>>(
         x_coeff, xc_stride, x_ntt, xn_stride, g_own, out, out_stride, c->L, c->K, c->alpha,
-        c->logN, c->d_mod, c->d_modup_inv, c->d_modup_c);
+        c->logN, c->d_mod, c->d_modup_inv, c->d_modup_c, g);
 }
 
 void launch_ks_inner(he_ctx* c, const uint64_t* D, size_t d_stride, const uint64_t* key,
@@ -797,8 +803,9 @@ void launch_ks_inner(he_ctx* c, const uint64_t* D, size_t d_stride, const uint64
 void launch_moddown_conv(he_ctx* c, const uint64_t* u, size_t u_stride, uint64_t* v,
                          size_t v_stride, int items) {
     ++c->launches;
-    k_moddown_conv<<<grid_nx(items, c->N, 2), 256, 0, c->stream>>>(
-        u, u_stride, v, v_stride, c->L, c->K, c->logN, c->d_mod, c->d_md_inv, c->d_md_c);
+    const int g = c->limb_groups > 0 ? c->limb_groups : 1;
+    k_moddown_conv<<<grid_nx(items, c->N, 2 * g), 256, 0, c->stream>>>(
+        u, u_stride, v, v_stride, c->L, c->K, c->logN, c->d_mod, c->d_md_inv, c->d_md_c, g);
 }
 
 void launch_ks_combine(he_ctx* c, const uint64_t* u, size_t u_stride, const uint64_t* v,

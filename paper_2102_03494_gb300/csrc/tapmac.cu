@@ -675,9 +675,25 @@ k_tap_pk(const uint64_t* __restrict__ D, const uint64_t* __restrict__ XPg,
             for (int c = 0; c < 2; ++c)
 #pragma unroll
                 for (int k = 0; k < 2; ++k) acc[ii][c][k] = Cols{0, 0, 0};
+        // (P c0)[perm_t(n)] of this thread's images, loaded one keyed tap ahead of its use
+        auto load_xp = [&](int t, uint64_t (&xp)[2]) {
+            const uint32_t pn = perm_of((uint32_t)n, tt.g[t], logN);
+#pragma unroll
+            for (int ii = 0; ii < 2; ++ii) {
+                const int ib = i0 + ii;
+                xp[ii] = (tt.key[t] && ib < nb)
+                             ? __ldg(XPg + ((size_t)(b0 + ib) * tt.n_sub + tt.sub[t]) * 2 * LNq +
+                                     (size_t)l * N + pn)
+                             : 0;
+            }
+        };
+        uint64_t xp_next[2];
+        load_xp(0, xp_next);
         for (int t = 0; t < tt.n; ++t) {
             const int s = t % kSt;
             const uint64_t* st = smem + s * S::WORDS;
+            const uint64_t xp_cur[2] = {xp_next[0], xp_next[1]};
+            if (t + 1 < tt.n) load_xp(t + 1, xp_next);
             if (!mbar_wait(&full[s], (uint32_t)(t / kSt) & 1u, report_polls)) {
                 ok = false;
                 mbar_wait(&full[s], (uint32_t)(t / kSt) & 1u);
@@ -690,10 +706,7 @@ k_tap_pk(const uint64_t* __restrict__ D, const uint64_t* __restrict__ XPg,
                 for (int ii = 0; ii < 2; ++ii) {
                     const int ib = i0 + ii;
                     const bool live = ib < nb;
-                    uint64_t xp = 0;
-                    if (live)
-                        xp = __ldg(XPg + ((size_t)(b0 + ib) * tt.n_sub + tt.sub[t]) * 2 * LNq +
-                                   (size_t)l * N + pn);
+                    const uint64_t xp = xp_cur[ii];
                     x0[ii] = (uint32_t)xp & kM25;
                     x1[ii] = (uint32_t)(xp >> 25);
 #pragma unroll
@@ -999,6 +1012,50 @@ static int tune_ntt(he_ctx* ctx, int batch, double* best_ms) {
     return he_launch_check(ctx, "he_autotune");
 }
 
+// Limb groups of the ModUp / ModDown base conversions: both conversions timed on synthetic
+// operands of `batch` ciphertexts with the target limbs split over 1, 2 and 4 groups.
+static int tune_limb_groups(he_ctx* ctx, int batch, double* ms) {
+    const size_t N = ctx->N, L = ctx->L, LK = ctx->L + ctx->K, dn = ctx->dnum;
+    const size_t nX = (size_t)batch * 2 * L * N, nD = (size_t)batch * dn * LK * N,
+                 nU = (size_t)batch * 2 * LK * N, nV = (size_t)batch * 2 * L * N;
+    int rc = arena_reserve(ctx, nX + nD + nU + nV + 32 * 4);
+    if (rc) return rc;
+    arena_reset(ctx);
+    uint64_t* X = arena_take(ctx, nX);
+    uint64_t* D = arena_take(ctx, nD);
+    uint64_t* U = arena_take(ctx, nU);
+    uint64_t* V = arena_take(ctx, nV);
+    for (int b = 0; b < batch; ++b) {
+        launch_uniform(ctx, he_stream_state(0x6c696d62ull, 2 * b), X + (size_t)b * 2 * L * N, (int)L, 0, 0);
+        launch_uniform(ctx, he_stream_state(0x6c696d62ull, 2 * b + 1), U + (size_t)b * 2 * LK * N, (int)LK, 0, 0);
+    }
+    cudaEvent_t e0, e1;
+    HE_CHECK_CUDA(ctx, cudaEventCreate(&e0));
+    HE_CHECK_CUDA(ctx, cudaEventCreate(&e1));
+    const int cand[3] = {1, 2, 4};
+    int best = 0;
+    for (int v = 0; v < 3; ++v) {
+        ctx->limb_groups = cand[v];
+        auto run = [&]() {
+            launch_modup(ctx, X, 2 * L * N, X + L * N, 2 * L * N, 1u, D, dn * LK * N, batch);
+            launch_moddown_conv(ctx, U, 2 * LK * N, V, 2 * L * N, batch);
+        };
+        run();
+        cudaEventRecord(e0, ctx->stream);
+        for (int rep = 0; rep < 3; ++rep) run();
+        cudaEventRecord(e1, ctx->stream);
+        cudaEventSynchronize(e1);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        ms[v] = t / 3.0;
+        if (ms[v] < ms[best]) best = v;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->limb_groups = cand[best];
+    return he_launch_check(ctx, "he_autotune");
+}
+
 extern "C" int he_autotune(he_ctx* ctx, int batch, int force_tile, double* ms_out) {
     if (!ctx) return HE_EINVAL;
     HE_NOT_RECORDING(ctx, "he_autotune");
@@ -1009,14 +1066,17 @@ extern "C" int he_autotune(he_ctx* ctx, int batch, int force_tile, double* ms_ou
         return HE_OK;
     }
     if (batch < 1 || batch > 1024) return he_fail(ctx, HE_EINVAL, "he_autotune: batch out of range");
-    double ntt_ms = 0;
+    double ntt_ms = 0, lg_ms[3] = {0, 0, 0};
     int rc = tune_ntt(ctx, batch, &ntt_ms);
     if (rc) return rc;
+    if ((rc = tune_limb_groups(ctx, batch, lg_ms))) return rc;
     if (ms_out) {
         for (int i = 0; i < HE_TUNE_REPORT_LEN; ++i) ms_out[i] = 0.0;
         ms_out[4] = ntt_ms;
         ms_out[5] = ctx->ntt_s1;
         ms_out[9] = 1 << ctx->ntt_radix;
+        for (int v = 0; v < 3; ++v) ms_out[10 + v] = lg_ms[v];
+        ms_out[13] = ctx->limb_groups;
         ms_out[6] = default_tile(ctx->dnum);
         ms_out[7] = ctx->tap_arith;
     }
@@ -1118,6 +1178,11 @@ extern "C" int he_tune_set(he_ctx* ctx, int knob, int value) {
                 return he_fail(ctx, HE_EINVAL, "he_tune_set: NTT radix is 2, 4 or 8");
             ctx->ntt_radix = value < 0 ? 0 : (value == 8 ? 3 : value == 4 ? 2 : 1);
             return HE_OK;
+        case HE_TUNE_LIMB_GROUPS:
+            if (value != -1 && value != 1 && value != 2 && value != 4)
+                return he_fail(ctx, HE_EINVAL, "he_tune_set: limb groups are 1, 2 or 4");
+            ctx->limb_groups = value < 0 ? 0 : value;
+            return HE_OK;
         default:
             return he_fail(ctx, HE_EINVAL, "he_tune_set: unknown knob");
     }
@@ -1130,6 +1195,7 @@ extern "C" int he_tune_get(he_ctx* ctx, int knob, int* value) {
         case HE_TUNE_TAP_ARITH: *value = ctx->tap_arith; return HE_OK;
         case HE_TUNE_NTT_SPLIT: *value = ctx->ntt_s1 ? ctx->ntt_s1 : ctx->logN / 2; return HE_OK;
         case HE_TUNE_NTT_RADIX: *value = 1 << (ctx->ntt_radix ? ctx->ntt_radix : 3); return HE_OK;
+        case HE_TUNE_LIMB_GROUPS: *value = ctx->limb_groups ? ctx->limb_groups : 1; return HE_OK;
         default: return he_fail(ctx, HE_EINVAL, "he_tune_get: unknown knob");
     }
 }

@@ -14,7 +14,7 @@ HE_OK, HE_EINVAL, HE_ENOMEM, HE_ENOKEY, HE_ECUDA, HE_ETIMEOUT = 0, -1, -2, -3, -
 HE_COEFF, HE_NTT = 0, 1
 HE_DP_DOT, HE_DP_SHIFT, HE_DP_SHIFT_EXT, HE_CP_CP, HE_DP_DP = 0, 1, 2, 3, 4
 HE_ROW_SWAP = 0x7FFFFFFF
-HE_TUNE_TAP_TILE, HE_TUNE_TAP_ARITH, HE_TUNE_NTT_SPLIT, HE_TUNE_NTT_RADIX = 0, 1, 2, 3
+HE_TUNE_TAP_TILE, HE_TUNE_TAP_ARITH, HE_TUNE_NTT_SPLIT, HE_TUNE_NTT_RADIX, HE_TUNE_LIMB_GROUPS = 0, 1, 2, 3, 4
 HE_TUNE_REPORT_LEN = 16
 HE_RELIN_KEY = -0x80000000
 
@@ -430,7 +430,8 @@ class Context:
         return {"tap_ms": {"128_chains": ms[0], "128_columns": ms[1], "256_chains": ms[2],
                            "256_columns": ms[3], "128_products": ms[8]},
                 "ntt_ms": ms[4], "ntt_log2_n1": int(ms[5]), "ntt_radix": int(ms[9]),
-                "tap_tile": int(ms[6]),
+                "conversion_ms": {"1": ms[10], "2": ms[11], "4": ms[12]},
+                "limb_groups": int(ms[13]), "tap_tile": int(ms[6]),
                 "tap_arith": ("chains", "columns", "products")[int(ms[7])]}
 
     def he_tune_set(self, knob, value):
