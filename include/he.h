@@ -107,9 +107,7 @@ int he_get_moduli(const he_ctx* ctx, uint64_t* out, int cap);
  * out[2] rotations, out[3] key switches (Table I's counted operations). */
 void he_op_counts(const he_ctx* ctx, uint64_t out[4]);
 void he_reset_op_counts(he_ctx* ctx);
-/* Number of CUDA kernels this context has launched since creation (a diagnostic); the small
- * copy kernels that move the library's own argument tables to the device are uploads and are
- * not counted. */
+/* Number of CUDA kernels this context has launched since creation (a diagnostic). */
 uint64_t he_launch_count(const he_ctx* ctx);
 /* Phase timing (a diagnostic).  While enabled, he_ffconv_layer(_batch) brackets each phase
  * with CUDA events on the context stream: HE_PHASE_ENCODE (plaintexts from the weights),

@@ -360,6 +360,7 @@ const void* upload_small(he_ctx* ctx, const void* src, size_t bytes) {
     const size_t words = (bytes + 7) / 8;             // the slot holds whole words
     if (words) {
         const int grid = (int)std::min<size_t>(64, (words + 1023) / 1024);
+        ++ctx->launches;
         k_copy_words<<<grid, 256, 0, ctx->stream>>>((uint64_t*)d,
                                                     (const uint64_t*)(st.host_dev + (size_t)slot * st.slot_bytes),
                                                     words);
