@@ -5,7 +5,6 @@
 // the plaintext modulus this root fixes the slot encoding).  Error sampler table: exact
 // 128-bit fixed point (120 fractional bits).
 #include <nvtx3/nvToolsExt.h>
-#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -327,17 +326,8 @@ uint64_t* arena_take(he_ctx* ctx, size_t n_u64) {
     return p;
 }
 
-// Copies n words from a pinned host slot (read through its device mapping) to device memory.
-__global__ void k_copy_words(uint64_t* __restrict__ dst, const uint64_t* __restrict__ src, size_t n) {
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        dst[i] = src[i];
-}
-
 // Small host->device uploads go through a ring of pinned staging slots so that they stay
-// asynchronous; a slot is reused only after the copy that last read it has executed.  The
-// copy is a small kernel reading the slot's device mapping, not a copy-engine transfer: a
-// large host-to-device copy the caller has queued (the next batch's inputs, on another
-// stream) then never holds up a library call waiting for its tables.
+// asynchronous; a slot is reused only after the copy that last read it has executed.
 const void* upload_small(he_ctx* ctx, const void* src, size_t bytes) {
     if (ctx->rec) {                              // recording a graph: a buffer the graph owns
         void* d = nullptr;
@@ -357,15 +347,8 @@ const void* upload_small(he_ctx* ctx, const void* src, size_t bytes) {
     char* h = st.host + (size_t)slot * st.slot_bytes;
     char* d = st.dev + (size_t)slot * st.slot_bytes;
     memcpy(h, src, bytes);
-    const size_t words = (bytes + 7) / 8;             // the slot holds whole words
-    if (words) {
-        const int grid = (int)std::min<size_t>(64, (words + 1023) / 1024);
-        ++ctx->launches;
-        k_copy_words<<<grid, 256, 0, ctx->stream>>>((uint64_t*)d,
-                                                    (const uint64_t*)(st.host_dev + (size_t)slot * st.slot_bytes),
-                                                    words);
-        if (cudaGetLastError() != cudaSuccess) return nullptr;
-    }
+    if (cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+        return nullptr;
     cudaEventRecord(st.ev[slot], ctx->stream);
     return d;
 }
@@ -591,8 +574,7 @@ extern "C" int he_ctx_create(const he_params* p, void* stream, he_ctx** out) {
         return HE_ENOMEM;
     }
     Staging& st = c->staging;
-    if (cudaHostAlloc((void**)&st.host, st.slot_bytes * st.n_slots, cudaHostAllocMapped) != cudaSuccess ||
-        cudaHostGetDevicePointer((void**)&st.host_dev, st.host, 0) != cudaSuccess ||
+    if (cudaMallocHost((void**)&st.host, st.slot_bytes * st.n_slots) != cudaSuccess ||
         cudaMalloc((void**)&st.dev, st.slot_bytes * st.n_slots) != cudaSuccess) {
         cudaGetLastError();
         free_ctx(c);

@@ -154,7 +154,6 @@ struct Staging {
     int n_slots = kSlots;
     int next = 0;
     char* host = nullptr;
-    char* host_dev = nullptr;     // the pinned slots' device mapping
     char* dev = nullptr;
     cudaEvent_t ev[kSlots] = {};
 };
