@@ -25,6 +25,7 @@
 // one ModDown per (image, channel) follows.  Per image this replaces d^2 - 1 ModDowns (2K
 // inverse and 2L forward transforms each) with r of them.
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include "eval.cuh"
@@ -154,9 +155,19 @@ std::vector<int32_t> layer_steps(const he_layout& y, const LayoutInfo& li) {
 
 // DP_SHIFT: plaintext (c', i, j) holds W1[c', ci, i, j] at slot ci*B_c + (s oh) I_w + s ow for
 // every output position whose input pixel (s oh + i - pad, s ow + j - pad) is inside.
-__global__ void k_dp_shift_slots(const int32_t* __restrict__ w1, int I_c, int I_h, int I_w, int d,
+// Low-rank weights small enough to travel as a kernel parameter: the slot kernels then read
+// them from parameter space, and the layer needs no upload before its first kernel (an upload
+// there would wait behind any large host-to-device copy the caller has queued).
+constexpr int kW1Inline = 1024;
+struct W1Inline {
+    int32_t w[kW1Inline];
+};
+
+__global__ void k_dp_shift_slots(const int32_t* __restrict__ w1_dev, const __grid_constant__ W1Inline w1i,
+                                 int I_c, int I_h, int I_w, int d,
                                  int s, int pad, int r, int O_h, int O_w, int B_c, int logN,
                                  int64_t* __restrict__ out) {
+    const int32_t* w1 = w1_dev ? w1_dev : w1i.w;
     const int N = 1 << logN;
     const int pt = blockIdx.x;  // (c' * d + i) * d + j
     const int j = pt % d, i = (pt / d) % d, cp = pt / (d * d);
@@ -173,9 +184,11 @@ __global__ void k_dp_shift_slots(const int32_t* __restrict__ w1, int I_c, int I_
 
 // DP_DOT: plaintext (c', o) (index c' S + o) is filter c' zero-padded at output o; plaintext
 // r S + o is the one-hot mask of slot o.
-__global__ void k_dp_dot_slots(const int32_t* __restrict__ w1, int I_c, int I_h, int I_w, int d,
+__global__ void k_dp_dot_slots(const int32_t* __restrict__ w1_dev, const __grid_constant__ W1Inline w1i,
+                               int I_c, int I_h, int I_w, int d,
                                int s, int pad, int r, int O_w, int S, int logN,
                                int64_t* __restrict__ out) {
+    const int32_t* w1 = w1_dev ? w1_dev : w1i.w;
     const int N = 1 << logN;
     const int pt = blockIdx.x;
     if (pt >= r * S) {
@@ -451,15 +464,22 @@ static int encode_w1(he_ctx* ctx, const he_layout& y, const LayoutInfo& li,
     const int pt_rows = y.pack == HE_DP_SHIFT_EXT ? LK : ctx->L;
     const int n_pt = dot ? r * li.S + li.S : r * li.taps;
     const size_t w1n = (size_t)r * y.I_c * y.d * y.d;
-    const int32_t* d_w1 = (const int32_t*)upload_small(ctx, lowrank_w, w1n * 4);
-    if (!d_w1) return he_fail(ctx, HE_EINVAL, "he_ffconv_layer: W1 too large for staging");
+    // up to kW1Inline weights travel inline with the launch; larger sets are uploaded
+    W1Inline w1i;
+    const int32_t* d_w1 = nullptr;
+    if (w1n <= (size_t)kW1Inline) {
+        memcpy(w1i.w, lowrank_w, w1n * 4);
+    } else {
+        d_w1 = (const int32_t*)upload_small(ctx, lowrank_w, w1n * 4);
+        if (!d_w1) return he_fail(ctx, HE_EINVAL, "he_ffconv_layer: W1 too large for staging");
+    }
     HE_CHECK_CUDA(ctx, cudaMemsetAsync(slots, 0, (size_t)n_pt * N * 8, ctx->stream));
     ++ctx->launches;
     if (dot)
-        k_dp_dot_slots<<<dim3(n_pt, 1), 256, 0, ctx->stream>>>(d_w1, y.I_c, y.I_h, y.I_w, y.d, y.stride,
+        k_dp_dot_slots<<<dim3(n_pt, 1), 256, 0, ctx->stream>>>(d_w1, w1i, y.I_c, y.I_h, y.I_w, y.d, y.stride,
                                                                y.pad, r, li.O_w, li.S, ctx->logN, slots);
     else
-        k_dp_shift_slots<<<dim3(n_pt, 4), 256, 0, ctx->stream>>>(d_w1, y.I_c, y.I_h, y.I_w, y.d,
+        k_dp_shift_slots<<<dim3(n_pt, 4), 256, 0, ctx->stream>>>(d_w1, w1i, y.I_c, y.I_h, y.I_w, y.d,
                                                                  y.stride, y.pad, r, li.O_h, li.O_w,
                                                                  li.B_c, ctx->logN, slots);
     encode_device(ctx, slots, n_pt, tmp, pts, 1, pt_rows);
