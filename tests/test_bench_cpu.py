@@ -46,3 +46,30 @@ def test_whole_job_rate_is_the_sum_over_replicas():
 def test_workload_name_names_the_packing():
     assert "dp_shift_ext" in bench.workload_name(argparse.Namespace(pack="dp_shift_ext"))
     assert "N=2^15" in bench.workload_name(argparse.Namespace(pack="dp_dot"))
+
+
+def test_sweep_point_bytes_and_bound():
+    # B input and B output ciphertexts of [2][L][N] words, 8 reused hoisted output sets of h
+    # ciphertexts, min(max(B, h), 64) keys of [dnum][2][L + K][N] words, the rotation scratch
+    n, L, K, B, h = 1 << 16, 24, 6, 1024, 24
+    ct = 2 * L * n * 8
+    key = 16 * 4 * (L + K) * n
+    scratch = 64 * (L + 4 * (L + K) + 2 * (L + K) + 2 * L) * n * 8
+    assert bench.sweep_point_bytes(16, L, K, B, h) == 2 * B * ct + 8 * h * ct + 64 * key + scratch
+    # every point of the grid fits the 150 GB bound (none is skipped)
+    for log_n in bench.SWEEP_LOG_N:
+        for L, K in bench.SWEEP_L.items():
+            for B in bench.SWEEP_B:
+                assert bench.sweep_point_bytes(log_n, L, K, B, max(bench.SWEEP_H)) <= bench.SWEEP_MEM_LIMIT
+
+
+def test_reference_step_runs_the_oracle_layer(monkeypatch):
+    """One reference step is one image's DP_SHIFT_EXT layer by the oracle (a small ring here)."""
+    monkeypatch.setattr(bench, "LOG_N", 11)          # 28 x 28 = 784 slots fit a row of N/2
+    monkeypatch.setattr(bench, "N_Q", 3)
+    monkeypatch.setattr(bench, "N_P", 1)
+    monkeypatch.setattr(bench, "ALPHA", 1)
+    monkeypatch.setattr(bench, "_ORACLE", {})
+    dt, n_rot = bench.oracle_layer_step(3)
+    assert dt > 0 and n_rot == 24
+    assert bench._ORACLE["lay"].pack == "dp_shift_ext"
