@@ -60,26 +60,23 @@ __device__ __forceinline__ void bfly_gs(uint64_t& X, uint64_t& Y, const ShoupPai
 // group g at x[g * 2^K + m].  Twiddle of stage ee for element m of a group whose block index
 // is `hi` (plus the block offset `toff` of the row pass): psi^brv(2^s + toff 2^ee + hi 2^ee
 // + (m >> (K - ee))).
-// LOCAL (the row pass): w holds only this CTA's twiddles, stage s0 + ee of `smb` blocks at
-// smb (2^(s0 + ee) - 1), and hi counts from the CTA's first block.
-template <int K, bool INV, bool SMALL, bool LOCAL>
+template <int K, bool INV, bool SMALL>
 __device__ __forceinline__ void round_bflies(uint64_t (&x)[8], const int (&hi)[8 >> K], int s0,
-                                             int smb, const ShoupPair* __restrict__ w,
+                                             int toff, const ShoupPair* __restrict__ w,
                                              uint64_t q, uint64_t q2) {
     constexpr int M = 1 << K;
 #pragma unroll
     for (int g = 0; g < (8 >> K); ++g) {
-        const int base_hi = hi[g];
+        const int base_hi = toff + hi[g];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int ee = INV ? (K - 1 - k) : k;
             const int d = 1 << (K - 1 - ee);
             const int s = s0 + ee;
-            const int stage_base = LOCAL ? smb * ((1 << s) - 1) : (1 << s);
 #pragma unroll
             for (int m = 0; m < M; ++m) {
                 if (m & d) continue;
-                const ShoupPair W = w[stage_base + (base_hi << ee) + (m >> (K - ee))];
+                const ShoupPair W = w[(1 << s) + (base_hi << ee) + (m >> (K - ee))];
                 if (INV) bfly_gs(x[g * M + m], x[g * M + m + d], W, q, q2);
                 else if (SMALL) bfly_ct_small(x[g * M + m], x[g * M + m + d], W, q, 2 * q2);
                 else bfly_ct(x[g * M + m], x[g * M + m + d], W, q, q2);
@@ -123,7 +120,7 @@ __device__ __forceinline__ void col_round(uint64_t (&x)[8], uint64_t* sm, uint64
         for (int i = 0; i < 8; ++i) x[i] = sm[off[i]];
     }
     const uint64_t q = Mc.q, q2 = 2 * q;
-    round_bflies<K, INV, SMALL, false>(x, hi, e0, 0, w, q, q2);
+    round_bflies<K, INV, SMALL>(x, hi, e0, 0, w, q, q2);
     if (last) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -144,8 +141,7 @@ __device__ __forceinline__ void col_round(uint64_t (&x)[8], uint64_t* sm, uint64
 template <int K, bool INV, bool SMALL>
 __device__ __forceinline__ void row_round(uint64_t (&x)[8], uint64_t* sm, uint64_t* __restrict__ a,
                                           bool first, bool last, int e0, int s1, int s2, int blk0,
-                                          int blocks, const ShoupPair* __restrict__ w,
-                                          const ModConst& Mc) {
+                                          const ShoupPair* __restrict__ w, const ModConst& Mc) {
     constexpr int M = 1 << K;
     const int N2 = 1 << s2;
     const int ltl = s2 - e0 - K, tlow = 1 << ltl;
@@ -175,12 +171,12 @@ __device__ __forceinline__ void row_round(uint64_t (&x)[8], uint64_t* sm, uint64
         for (int i = 0; i < 8; ++i) x[i] = sm[off[i]];
     }
     const uint64_t q = Mc.q, q2 = 2 * q;
-    // twiddles of the CTA's `blocks` blocks, staged in shared memory (w): block b's offset at
-    // stage e0 + ee is b 2^(e0 + ee), folded into hi as b 2^e0 + hi.
+    // twiddle offset of block (blk0 + b) at stage s1 + e0 + ee is (blk0 + b) 2^(e0 + ee):
+    // fold it into hi as (blk0 + b) 2^e0 + hi.
     int hh[8 >> K];
 #pragma unroll
-    for (int g = 0; g < (8 >> K); ++g) hh[g] = (blk[g] << e0) + hi[g];
-    round_bflies<K, INV, SMALL, true>(x, hh, e0, blocks, w, q, q2);
+    for (int g = 0; g < (8 >> K); ++g) hh[g] = ((blk0 + blk[g]) << e0) + hi[g];
+    round_bflies<K, INV, SMALL>(x, hh, s1 + e0, 0, w, q, q2);
     if (last) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -235,7 +231,7 @@ __device__ __forceinline__ void ntt_cols_body(uint64_t* __restrict__ a, uint64_t
 
 template <bool INV, bool SMALL, int KMAX>
 __device__ __forceinline__ void ntt_rows_body(uint64_t* __restrict__ a, uint64_t* sm, int logN,
-                                              int s1, int blk0, int blocks,
+                                              int s1, int blk0,
                                               const ShoupPair* __restrict__ w, const ModConst& Mc) {
     const int s2 = logN - s1;
     const int nr = (s2 + KMAX - 1) / KMAX;
@@ -244,9 +240,9 @@ __device__ __forceinline__ void ntt_rows_body(uint64_t* __restrict__ a, uint64_t
         int e0, K;
         round_of(r, s2, INV, KMAX, e0, K);
         const bool first = r == 0, last = r == nr - 1;
-        if (KMAX == 3 && K == 3) row_round<3, INV, SMALL>(x, sm, a, first, last, e0, s1, s2, blk0, blocks, w, Mc);
-        else if (K == 2) row_round<2, INV, SMALL>(x, sm, a, first, last, e0, s1, s2, blk0, blocks, w, Mc);
-        else row_round<1, INV, SMALL>(x, sm, a, first, last, e0, s1, s2, blk0, blocks, w, Mc);
+        if (KMAX == 3 && K == 3) row_round<3, INV, SMALL>(x, sm, a, first, last, e0, s1, s2, blk0, w, Mc);
+        else if (K == 2) row_round<2, INV, SMALL>(x, sm, a, first, last, e0, s1, s2, blk0, w, Mc);
+        else row_round<1, INV, SMALL>(x, sm, a, first, last, e0, s1, s2, blk0, w, Mc);
     }
 }
 
@@ -259,16 +255,13 @@ __global__ void __launch_bounds__(256, 4)
 k_ntt_cols(uint64_t* __restrict__ data, size_t item_stride, int mod_off, int logN, int s1, int lc,
            const ModConst* __restrict__ mods, const ShoupPair* __restrict__ tw) {
     __shared__ uint64_t sm[kTile];
-    __shared__ ShoupPair tws[kTile];                  // twiddles of stages < s1: entries < 2^s1
     const int N = 1 << logN;
     const int mod = mod_off + blockIdx.y;
     const ModConst Mc = mods[mod];
     const ShoupPair* w = tw + (size_t)mod * N;
-    for (int i = threadIdx.x; i < (1 << s1); i += blockDim.x) tws[i] = w[i];
-    __syncthreads();
     uint64_t* a = data + blockIdx.z * item_stride + (size_t)blockIdx.y * N;
     const int lo0 = blockIdx.x << lc;
-    ntt_cols_body<INV, SMALL, KMAX>(a, sm, logN, s1, lc, lo0, tws, Mc);
+    ntt_cols_body<INV, SMALL, KMAX>(a, sm, logN, s1, lc, lo0, w, Mc);
 }
 
 template <bool INV, bool SMALL, int KMAX>
@@ -276,24 +269,13 @@ __global__ void __launch_bounds__(256, 4)
 k_ntt_rows(uint64_t* __restrict__ data, size_t item_stride, int mod_off, int logN, int s1, int blocks,
            const ModConst* __restrict__ mods, const ShoupPair* __restrict__ tw) {
     __shared__ uint64_t sm[kTile];
-    // the twiddles of this CTA's blocks: stage s1 + e holds, for blocks blk0 .. blk0 + blocks - 1,
-    // the contiguous entries 2^(s1 + e) + blk0 2^e + i, i < blocks 2^e; staged at
-    // blocks (2^e - 1) + i (fewer than blocks 2^s2 <= kTile in all)
-    __shared__ ShoupPair tws[kTile];
     const int N = 1 << logN;
     const int mod = mod_off + blockIdx.y;
     const ModConst Mc = mods[mod];
     const ShoupPair* w = tw + (size_t)mod * N;
-    const int blk0 = blockIdx.x * blocks;
-    const int s2 = logN - s1;
-    for (int e = 0; e < s2; ++e) {
-        const ShoupPair* src = w + (1 << (s1 + e)) + ((size_t)blk0 << e);
-        ShoupPair* dst = tws + blocks * ((1 << e) - 1);
-        for (int i = threadIdx.x; i < (blocks << e); i += blockDim.x) dst[i] = src[i];
-    }
-    __syncthreads();
     uint64_t* a = data + blockIdx.z * item_stride + (size_t)blockIdx.y * N;
-    ntt_rows_body<INV, SMALL, KMAX>(a, sm, logN, s1, blk0, blocks, tws, Mc);
+    const int blk0 = blockIdx.x * blocks;
+    ntt_rows_body<INV, SMALL, KMAX>(a, sm, logN, s1, blk0, w, Mc);
 }
 
 struct Split {
