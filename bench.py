@@ -574,9 +574,10 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "src": "fallback"}
 
 
-# DRAM bytes (read + write) of the tap phase per batch of 64, from one ncu capture of the
-# current kernels (scaled from a smaller batch); None until captured for this version.
-TAPS_TRAFFIC = {}
+# DRAM bytes (read + write) of one carry-chain tap launch at batch 64, from one ncu capture of
+# the current kernel (dram__bytes_read.sum 3.53 GB + dram__bytes_write.sum 0.990 GB, one pass);
+# cleared whenever the kernel changes until it is captured again.
+TAPS_TRAFFIC = {("chains", 64): 3.53e9 + 0.98959e9}
 
 
 # 64 x 64 -> 128-bit products per second of the GPU's integer multiplier: SMs (152 on GB300)
@@ -608,7 +609,8 @@ def taps_roofline(phases, args, B, n_rot, sms=152, arith="chains"):
                "products": "k_pk_prep + k_tap_pk (q limbs) + k_ks_mac_ext_bulk (p limbs)"}
     return {"kernel": kernels.get(arith.split(" ")[0], arith), "bound": "alu",
             "achieved": achieved, "peak": peak, "unit": "T mul64/s", "frac": achieved / peak,
-            "traffic": TAPS_TRAFFIC.get(B), "launch_us": sec * 1e6, "products_per_launch": products,
+            "traffic": TAPS_TRAFFIC.get((arith.split(" ")[0], B)), "launch_us": sec * 1e6,
+            "products_per_launch": products,
             "peak_note": f"{sms} SMs (device attribute) x 64 multiply-add issue slots per clock / 4 "
                          "mad.wide.u32 per 64x64->128-bit product x max SM clock of MEASURED_PEAKS "
                          f"({pk['src']}); derived, probe-checked (he_probe_int_ops)"}

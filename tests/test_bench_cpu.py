@@ -28,6 +28,9 @@ def test_tap_kernel_products_and_roofline():
     assert roof["achieved"] == pytest.approx(9_185_525_760 / 8.6513e-3 / 1e12)
     assert roof["frac"] == pytest.approx(roof["achieved"] / roof["peak"])
     assert "k_ks_mac_ext_bulk" in roof["kernel"]
+    # the DRAM capture belongs to the carry-chain kernel at batch 64 only
+    assert roof["traffic"] == pytest.approx(4.51959e9)
+    assert bench.taps_roofline({"taps": (1.0, 1)}, args, 64, 24, arith="columns")["traffic"] is None
     assert bench.taps_roofline({"taps": (1.0, 1)}, argparse.Namespace(pack="dp_shift"), 64, 24) is None
 
 
