@@ -476,7 +476,8 @@ def run(args):
         clk = measured_peaks()["sm_max_mhz"] * 1e6
         roof["probe"] = {"mul64_T_per_s": {k: probe[k] / 1e12 for k in ("chain", "columns", "karatsuba")},
                          "per_clock_per_sm": {k: probe[k] / (sms * clk)
-                                              for k in ("mad_lo", "mad_hi", "mad_wide")}}
+                                              for k in ("mad_lo", "mad_hi", "mad_wide")},
+                         "read_gbs": ctx.he_probe_mem()}
     layer_bytes = layer_algorithmic_bytes(B, shape.O_c, n_rot)
     peaks = measured_peaks()
 

@@ -457,6 +457,10 @@ int he_probe_int_mac(he_ctx* ctx, double* out);
  * products each (Karatsuba on 30-bit halves), out[3] mad.lo.u32/s, out[4] mad.hi.u32/s,
  * out[5] mad.wide.u32/s (eight independent accumulators per thread).  Synchronous. */
 int he_probe_int_ops(he_ctx* ctx, double* out, int n);
+/* Read bandwidth in GB/s (n doubles, up to 2): out[0] of a 32 MiB buffer that stays in L2,
+ * out[1] of a 2 GiB buffer read from HBM (16-byte loads bypassing L1, all SMs).  Uses the
+ * context stream and scratch; synchronous. */
+int he_probe_mem(he_ctx* ctx, double* out, int n);
 
 /* Negacyclic NTT (inverse = 0) or inverse NTT (inverse = 1) in place on `n_items` blocks of
  * n_limbs limbs each (device [n_items][n_limbs][N]); limb i uses the i-th ciphertext prime

@@ -126,6 +126,20 @@ __global__ void __launch_bounds__(256) k_probe_op(const uint64_t* __restrict__ i
     out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = r;
 }
 
+// Read bandwidth: every thread streams 16-byte loads that bypass L1 (ld.global.cg) over a
+// buffer, `reps` times; a buffer that fits in L2 measures L2, a larger one HBM.
+__global__ void __launch_bounds__(256) k_probe_read(const uint4* __restrict__ in, size_t n16,
+                                                    int reps, uint64_t* __restrict__ out) {
+    uint32_t acc = 0;
+    for (int r = 0; r < reps; ++r)
+        for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16;
+             i += (size_t)gridDim.x * blockDim.x) {
+            const uint4 v = __ldcg(in + i);
+            acc ^= v.x ^ v.y ^ v.z ^ v.w;
+        }
+    if (acc == 0x9e3779b9u) out[0] = acc;           // keeps the loads live
+}
+
 }  // namespace
 
 extern "C" int he_probe_int_mac(he_ctx* ctx, double* out) {
@@ -215,4 +229,39 @@ extern "C" int he_probe_int_ops(he_ctx* ctx, double* out, int n) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return he_launch_check(ctx, "he_probe_int_ops");
+}
+
+extern "C" int he_probe_mem(he_ctx* ctx, double* out, int n) {
+    if (!ctx || !out || n < 1) return HE_EINVAL;
+    HE_NOT_RECORDING(ctx, "he_probe_mem");
+    int sms = 0, dev = 0;
+    HE_CHECK_CUDA(ctx, cudaGetDevice(&dev));
+    HE_CHECK_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const size_t sizes[2] = {(size_t)32 << 20, (size_t)2 << 30};   // bytes: L2-resident, HBM
+    const int reps[2] = {40, 2};
+    int rc = arena_reserve(ctx, sizes[1] / 8 + 64);
+    if (rc) return rc;
+    arena_reset(ctx);
+    uint64_t* buf = arena_take(ctx, sizes[1] / 8);
+    uint64_t* sink = arena_take(ctx, 8);
+    HE_CHECK_CUDA(ctx, cudaMemsetAsync(buf, 1, sizes[1], ctx->stream));
+    cudaEvent_t e0, e1;
+    HE_CHECK_CUDA(ctx, cudaEventCreate(&e0));
+    HE_CHECK_CUDA(ctx, cudaEventCreate(&e1));
+    const int nv = n < 2 ? n : 2;
+    for (int v = 0; v < nv; ++v) {
+        const size_t n16 = sizes[v] / 16;
+        k_probe_read<<<sms * 8, 256, 0, ctx->stream>>>((const uint4*)buf, n16, 1, sink);   // warm
+        cudaEventRecord(e0, ctx->stream);
+        k_probe_read<<<sms * 8, 256, 0, ctx->stream>>>((const uint4*)buf, n16, reps[v], sink);
+        cudaEventRecord(e1, ctx->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        out[v] = (double)sizes[v] * reps[v] / (ms / 1e3) / 1e9;
+        ctx->launches += 2;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return he_launch_check(ctx, "he_probe_mem");
 }

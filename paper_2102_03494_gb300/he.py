@@ -95,6 +95,7 @@ _SIGS = {
     "he_autotune": ([_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "he_probe_int_mac": ([_P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "he_probe_int_ops": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int], ctypes.c_int),
+    "he_probe_mem": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int], ctypes.c_int),
     "he_check": ([_P], ctypes.c_int),
     "he_tune_set": ([_P, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "he_tune_get": ([_P, ctypes.c_int, _I32P], ctypes.c_int),
@@ -464,6 +465,12 @@ class Context:
         self._ck(lib().he_probe_int_ops(self.h, out, 6), "he_probe_int_ops")
         return dict(zip(("chain", "columns", "karatsuba", "mad_lo", "mad_hi", "mad_wide"),
                         (float(v) for v in out)))
+
+    def he_probe_mem(self):
+        """Read GB/s of an L2-resident buffer and of an HBM-sized one."""
+        out = (ctypes.c_double * 2)()
+        self._ck(lib().he_probe_mem(self.h, out, 2), "he_probe_mem")
+        return {"l2_read_gbs": float(out[0]), "hbm_read_gbs": float(out[1])}
 
     # ---- deeper networks (several ciphertexts per tensor)
     @staticmethod

@@ -230,6 +230,8 @@ def test_integer_rate_probe_is_sane():
         assert 0.05 * slots < ops[k] < 1.1 * slots
     for k in ("chain", "columns", "karatsuba"):
         assert 0.02 * slots / 4 < ops[k] < 1.1 * slots / 3
+    mem = ctx.he_probe_mem()          # L2-resident reads outrun HBM reads; HBM below 8 TB/s
+    assert 500 < mem["hbm_read_gbs"] < 8000 and mem["l2_read_gbs"] > mem["hbm_read_gbs"]
 
 
 @pytest.mark.parametrize("cfg", [(13, 3, 1, 1), (14, 8, 2, 2), (15, 16, 4, 4), (16, 24, 6, 6)])
