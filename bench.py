@@ -1200,22 +1200,34 @@ SWEEP_MEM_LIMIT = 150 << 30
 L2_BYTES = 129 << 20
 
 
+SWEEP_HOIST_OUT_BYTES = 16 << 30
+
+
+def sweep_hoist_batch(log_n, L, h):
+    """Ciphertexts per batched hoisted call in the sweep: as many whose h outputs fit 16 GiB,
+    between 8 and 64 (the output sets are reused from call to call)."""
+    ct = 2 * L * (1 << log_n) * 8
+    return max(8, min(64, SWEEP_HOIST_OUT_BYTES // (h * ct)))
+
+
 def sweep_point_bytes(log_n, L, K, B, h):
     """Device bytes a sweep point holds: the B input and B output ciphertexts, the hoisted
-    outputs of up to 8 ciphertexts (reused), the Galois keys and the rotation scratch."""
+    outputs of one batched call (reused), the Galois keys and the rotation scratch."""
     N = 1 << log_n
     ct = 2 * L * N * 8
     dnum = -(-L // K)
     key = 16 * dnum * (L + K) * N
     n_keys = min(max(B, h), SWEEP_MAX_KEYS)
     scratch = min(B, 64) * (L + dnum * (L + K) + 2 * (L + K) + 2 * L) * N * 8
-    return 2 * B * ct + 8 * h * ct + n_keys * key + scratch
+    hoist = min(B, sweep_hoist_batch(log_n, L, h)) * h * ct
+    return 2 * B * ct + hoist + n_keys * key + scratch
 
 
 def run_sweep(args):
     """Batched primitive sweep: negacyclic NTT and inverse NTT, the Galois automorphism, plain
     key-switched rotations (ciphertexts grouped by Galois key, one batched call per key) and
-    hoisted rotations (h steps per ciphertext sharing one ModUp), over batch sizes, ring sizes
+    hoisted rotations (h steps per ciphertext sharing one ModUp; ciphertexts grouped by step
+    set, batched calls of up to 8 .. 64 of them), over batch sizes, ring sizes
     and prime counts.  Ciphertexts hold residues uniform modulo each prime; steps are uniform
     in [1, N/2); min(B, 64) distinct Galois keys (max(h, min(B, 64)) for the hoisted points),
     generated on the device, each ciphertext taking one of them uniformly.  Every op is timed
@@ -1322,19 +1334,30 @@ def run_sweep(args):
                 pt["rotations_per_s"] = B / (ms / 1e3)
                 key_bytes = 16 * dnum * (L + K) * N
                 pt["rotation_gbs_algorithmic"] = (2 * B * ct_bytes + len(groups) * key_bytes) / (ms / 1e3) / 1e9
-                # hoisted: h steps per ciphertext, one ModUp each, outputs reused by every 8th
+                # hoisted: ciphertexts grouped by step set (one set of h steps per h of the
+                # keys), one ModUp per ciphertext, batched calls of up to P ciphertexts of one
+                # group, the P h output ciphertexts reused from call to call
                 for h in SWEEP_H:
                     hk = min(max(B, h), SWEEP_MAX_KEYS)
-                    mine = [[steps[int(k)] for k in rng.choice(hk, h, replace=False)] for _ in range(B)]
+                    sets = [[steps[int(k)] for k in rng.choice(hk, h, replace=False)]
+                            for _ in range(max(1, hk // h))]
+                    owner = rng.integers(0, len(sets), B)
+                    P = min(B, sweep_hoist_batch(log_n, L, h))
+                    calls = []
+                    for g, st in enumerate(sets):
+                        idx = [i for i in range(B) if owner[i] == g]
+                        calls += [(st, [ins[i] for i in idx[j:j + P]])
+                                  for j in range(0, len(idx), P)]
                     with torch.cuda.stream(stream):
-                        pool = [list(ctx.new_ct(count=h)) for _ in range(min(B, 8))]
+                        pool = list(ctx.new_ct(count=P * h))
 
                     def hoisted():
-                        for i in range(B):
-                            ctx.he_rotate_hoisted(ins[i], mine[i], pool[i % len(pool)])
+                        for st, cts in calls:
+                            ctx.he_rotate_hoisted_batch(cts, st, pool[:len(cts) * h])
 
                     ms, reps = timed(hoisted, flush)
                     pt[f"hoisted_h{h}_rotations_per_s"] = B * h / (ms / 1e3)
+                    pt[f"hoisted_h{h}_calls"] = len(calls)
                     del pool
                 ctx.he_check()
                 points.append(pt)

@@ -193,6 +193,12 @@ int he_rotate_batch(he_ctx* ctx, const he_ct* in, int n, int32_t step, he_ct* ou
  * steps[i].  Its ciphertext bits differ from he_rotate's (the lift happens before the
  * automorphism); both decrypt identically. */
 int he_rotate_hoisted(he_ctx* ctx, const he_ct* in, const int32_t* steps, int h, he_ct* outs);
+/* The same for n ciphertexts rotated by the same h steps: outs[i h + s] = rotation of in[i] by
+ * steps[s], each output bit-identical to he_rotate_hoisted's.  The ciphertexts go through the
+ * key switch in batches (one ModUp per ciphertext, each step's key read once per batch).  No
+ * output may alias an input (HE_EINVAL). */
+int he_rotate_hoisted_batch(he_ctx* ctx, const he_ct* in, int n, const int32_t* steps, int h,
+                            he_ct* outs);
 /* MulPC + AddCC (Table I): acc += sum_i cts[i] * pts[i], pts device [n][level][N] NTT domain
  * (e.g. from he_encode).  acc and cts in the NTT domain, same level. */
 int he_mul_plain_acc(he_ctx* ctx, const he_ct* cts, const uint64_t* pts, int n, he_ct* acc);

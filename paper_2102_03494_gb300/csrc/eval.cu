@@ -7,6 +7,7 @@
 //            out = ((u_Q - NTT(v)) P^-1 + perm_g(c0), (u_Q - NTT(v)) P^-1)
 //   hoisted: D_j = ModUp_j(INTT(c1)) once; per step u = sum_j perm_g(D_j) * key_j, same tail.
 #include <algorithm>
+#include <unordered_set>
 #include <vector>
 
 #include "eval.cuh"
@@ -283,6 +284,48 @@ int rotate_hoisted_contig(he_ctx* c, const uint64_t* X, int items, const std::ve
     c->ops[2] += (uint64_t)items * gs.size();
     c->ops[3] += (uint64_t)items * gs.size();
     return he_launch_check(c, "hoisted rotation");
+}
+
+extern "C" int he_rotate_hoisted_batch(he_ctx* ctx, const he_ct* in, int n, const int32_t* steps,
+                                       int h, he_ct* outs) {
+    if (!ctx || !in || !steps || !outs || n < 1 || h < 1)
+        return ctx ? he_fail(ctx, HE_EINVAL, "he_rotate_hoisted_batch: arguments") : HE_EINVAL;
+    std::vector<uint32_t> gs(h);
+    for (int s = 0; s < h; ++s) gs[s] = galois_elt(ctx, steps[s]);
+    // inputs are gathered chunk by chunk, so an output written for one chunk must not be a
+    // later chunk's input
+    std::unordered_set<const uint64_t*> ins;
+    for (int i = 0; i < n; ++i) ins.insert(in[i].data);
+    for (size_t j = 0; j < (size_t)n * h; ++j)
+        if (ins.count(outs[j].data))
+            return he_fail(ctx, HE_EINVAL, "he_rotate_hoisted_batch: an output aliases an input");
+    for (int i = 0; i < n; ++i) {
+        int rc = check_ct(ctx, &in[i], ctx->L, HE_NTT, "he_rotate_hoisted_batch input");
+        if (rc) return rc;
+        for (int s = 0; s < h; ++s)
+            if ((rc = check_ct(ctx, &outs[(size_t)i * h + s], ctx->L, -1, "he_rotate_hoisted_batch output")))
+                return rc;
+    }
+    const size_t ct = 2 * (size_t)ctx->L * ctx->N;
+    const int chunk = std::min(n, rotation_chunk(ctx));
+    int rc = arena_reserve(ctx, chunk * ct + chunk * rot_scratch_per_item(ctx) + 64);
+    if (rc) return rc;
+    arena_reset(ctx);
+    uint64_t* X = arena_take(ctx, chunk * ct);
+    RotBufs b = rot_bufs_take(ctx, chunk);
+    for (int i0 = 0; i0 < n; i0 += chunk) {
+        const int items = std::min(chunk, n - i0);
+        if ((rc = gather_inputs(ctx, in + i0, items, X))) return rc;
+        std::vector<uint64_t*> o((size_t)h * items);   // step-major, as rotate_hoisted_contig takes them
+        for (int it = 0; it < items; ++it)
+            for (int s = 0; s < h; ++s) {
+                he_ct& oc = outs[(size_t)(i0 + it) * h + s];
+                o[(size_t)s * items + it] = oc.data;
+                oc.domain = HE_NTT;
+            }
+        if ((rc = rotate_hoisted_contig(ctx, X, items, gs, o, b))) return rc;
+    }
+    return HE_OK;
 }
 
 extern "C" int he_rotate_hoisted(he_ctx* ctx, const he_ct* in, const int32_t* steps, int h,

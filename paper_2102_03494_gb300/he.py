@@ -83,6 +83,7 @@ _SIGS = {
     "he_rotate_batch": ([_P, _CTP, ctypes.c_int, ctypes.c_int32, _CTP], ctypes.c_int),
     "he_automorphism": ([_P, _CTP, ctypes.c_int, ctypes.c_int32, _CTP], ctypes.c_int),
     "he_rotate_hoisted": ([_P, _CTP, _I32P, ctypes.c_int, _CTP], ctypes.c_int),
+    "he_rotate_hoisted_batch": ([_P, _CTP, ctypes.c_int, _I32P, ctypes.c_int, _CTP], ctypes.c_int),
     "he_mul_plain_acc": ([_P, _CTP, _P, ctypes.c_int, _CTP], ctypes.c_int),
     "he_add": ([_P, _CTP, _CTP, _CTP], ctypes.c_int),
     "he_rescale": ([_P, _CTP, _CTP], ctypes.c_int),
@@ -351,6 +352,15 @@ class Context:
         st, pst = _i32(steps)
         oa = self.ct_array(outs)
         self._ck(lib().he_rotate_hoisted(self.h, ctypes.byref(a), pst, len(st), oa), "he_rotate_hoisted")
+        return outs
+
+    def he_rotate_hoisted_batch(self, cts, steps, outs=None):
+        """outs[i * h + s]: cts[i] rotated by steps[s] (one ModUp per ciphertext)."""
+        outs = [self.new_ct() for _ in range(len(cts) * len(steps))] if outs is None else outs
+        ia, oa = self.ct_array(cts), self.ct_array(outs)
+        st, pst = _i32(steps)
+        self._ck(lib().he_rotate_hoisted_batch(self.h, ia, len(cts), pst, len(st), oa),
+                 "he_rotate_hoisted_batch")
         return outs
 
     def he_mul_plain_acc(self, cts, pts, acc):

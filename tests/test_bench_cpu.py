@@ -52,13 +52,21 @@ def test_workload_name_names_the_packing():
 
 
 def test_sweep_point_bytes_and_bound():
-    # B input and B output ciphertexts of [2][L][N] words, 8 reused hoisted output sets of h
-    # ciphertexts, min(max(B, h), 64) keys of [dnum][2][L + K][N] words, the rotation scratch
+    # B input and B output ciphertexts of [2][L][N] words, the reused outputs of one batched
+    # hoisted call (P ciphertexts x h), min(max(B, h), 64) keys of [dnum][2][L + K][N] words,
+    # the rotation scratch
     n, L, K, B, h = 1 << 16, 24, 6, 1024, 24
     ct = 2 * L * n * 8
     key = 16 * 4 * (L + K) * n
     scratch = 64 * (L + 4 * (L + K) + 2 * (L + K) + 2 * L) * n * 8
-    assert bench.sweep_point_bytes(16, L, K, B, h) == 2 * B * ct + 8 * h * ct + 64 * key + scratch
+    P = (16 << 30) // (h * ct)                     # 28 ciphertexts' outputs fit 16 GiB
+    assert P == 28 and bench.sweep_hoist_batch(16, L, h) == P
+    assert bench.sweep_point_bytes(16, L, K, B, h) == 2 * B * ct + P * h * ct + 64 * key + scratch
+    # the batch stays within 8 .. 64 ciphertexts and below B
+    assert bench.sweep_hoist_batch(13, 3, 8) == 64
+    assert bench.sweep_point_bytes(13, 3, 1, 1, 8) == (2 * 2 * 3 * 8192 * 8 + 8 * 2 * 3 * 8192 * 8
+                                                       + 8 * 16 * 3 * 4 * 8192
+                                                       + (3 + 3 * 4 + 2 * 4 + 6) * 8192 * 8)
     # every point of the grid fits the 150 GB bound (none is skipped)
     for log_n in bench.SWEEP_LOG_N:
         for L, K in bench.SWEEP_L.items():

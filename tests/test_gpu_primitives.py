@@ -123,6 +123,13 @@ def test_rotations_are_bit_exact(name):
     hs = ctx.he_rotate_hoisted(ds[1], gpu_steps(steps))
     for o, w in zip(hs, bfv.rotate_hoisted(prm, cts[1], steps, keys)):
         assert (download_coeff(ctx, o) == w.stack()).all()
+    # batched hoisted: outs[i h + s] is ciphertext i rotated by step s
+    hb = ctx.he_rotate_hoisted_batch(ds, gpu_steps(steps))
+    for i, c in enumerate(cts):
+        for j, w in enumerate(bfv.rotate_hoisted(prm, c, steps, keys)):
+            assert (download_coeff(ctx, hb[i * len(steps) + j]) == w.stack()).all(), (i, j)
+    with pytest.raises(RuntimeError):               # an output aliasing an input is refused
+        ctx.he_rotate_hoisted_batch(ds[:2], gpu_steps(steps[:1]), [ctx.new_ct(), ds[0]])
     # decrypted slots shift as the paper's rotation does
     half = prm.n // 2
     v = encoder.decode(bfv.decrypt(prm, s, cts[1]), prm)
@@ -258,6 +265,16 @@ def test_sweep_rotations_are_bit_exact(cfg):
     hs = ctx.he_rotate_hoisted(ds[1], steps)
     for o, w in zip(hs, bfv.rotate_hoisted(prm, cts[1], steps, keys)):
         assert (download_coeff(ctx, o) == w.stack()).all()
+    # the batched hoisted call over more ciphertexts than one key-switching chunk holds (about
+    # 1 GiB of scratch: 8 ciphertexts at N = 2^16 with 24 + 6 primes) equals one call per
+    # ciphertext, bit for bit
+    import torch
+    more = ds + [torch.randint_like(ds[0], 0, 1 << 40) for _ in range(8)]   # residues < 2^40 < q
+    torch.cuda.synchronize()
+    hb = ctx.he_rotate_hoisted_batch(more, steps)
+    for i, m in enumerate(more):
+        for j, o in enumerate(ctx.he_rotate_hoisted(m, steps)):
+            assert torch.equal(hb[i * 2 + j], o), (i, j)
 
 
 @pytest.mark.parametrize("cfg", [(9, 3, 1, 1), (13, 3, 1, 1), (15, 16, 4, 4), (16, 24, 6, 6)])
