@@ -491,6 +491,12 @@ extern "C" int he_ctx_create(const he_params* p, void* stream, he_ctx** out) {
         M.n_inv = h_inv((uint64_t)N % q, q);
         M.n_inv_sh = h_shoup(M.n_inv, q).ws;
         M.one_sh = h_shoup(1, q).ws;
+        if ((q >> 57) == 0) {
+            const int b = 64 - __builtin_clzll(q);
+            M.red_sh = (uint16_t)std::max(b - 25, 0);
+            M.red_t = (uint16_t)(31 + b - M.red_sh);
+            M.red_r = (uint32_t)(((u128)1 << (31 + b)) / q);
+        }
         if (m == c->L + c->K && !c->batching) continue;   // t without a 2N-th root
         uint64_t psi = root_2n(q, two_n), psi_inv = h_inv(psi, q);
         for (int k = 0; k < N; ++k) {

@@ -27,6 +27,10 @@ struct ModConst {
     uint64_t n_inv;      // N^-1 mod q
     uint64_t n_inv_sh;   // its Shoup companion
     uint64_t one_sh;     // floor(2^64 / q): Shoup companion of 1 (x mod q for any 64-bit x)
+    // quotient estimate for values below 2^(b + 7), b = bit length of q <= 57 (reduce_small):
+    // red_r = floor(2^(31 + b) / q), red_sh = max(b - 25, 0), red_t = 31 + b - red_sh
+    uint32_t red_r;
+    uint16_t red_sh, red_t;
 };
 
 struct ShoupPair {
@@ -42,6 +46,17 @@ __device__ __forceinline__ uint64_t add_mod(uint64_t a, uint64_t b, uint64_t q) 
 
 __device__ __forceinline__ uint64_t sub_mod(uint64_t a, uint64_t b, uint64_t q) {
     return a >= b ? a - b : a + q - b;
+}
+
+// v mod q for v < 2^(b + 7) (b = bit length of q, at most 57).  With vh = floor(v / 2^sh)
+// (below 2^32) the estimate k = floor(vh red_r / 2^t) satisfies floor(v/q) - 1 <= k <=
+// floor(v/q): each truncation costs less than 2^-24 of a quotient unit.  So v - k q lies in
+// [0, 2q) and one conditional subtraction finishes.
+__device__ __forceinline__ uint64_t reduce_small(uint64_t v, const ModConst& M) {
+    const uint32_t vh = (uint32_t)(v >> M.red_sh);
+    const uint32_t k = (uint32_t)(((uint64_t)vh * M.red_r) >> M.red_t);
+    const uint64_t r = v - (uint64_t)k * M.q;
+    return r >= M.q ? r - M.q : r;
 }
 
 __device__ __forceinline__ uint64_t neg_mod(uint64_t a, uint64_t q) { return a ? q - a : 0; }

@@ -19,8 +19,8 @@
 // modulus below 2^57 ("small") skip the per-butterfly reduction altogether and estimate the
 // Shoup quotient from three partial products: each stage adds less than 4q to a value, so
 // after at most 16 stages every value stays below 4q + 64q < 2^64, and the pass's last write
-// reduces it exactly (conditional subtractions of 64q, 32q, ..., q).  The output is the same
-// residue in [0, q).
+// reduces it exactly (a 32-bit quotient estimate and one conditional subtraction,
+// reduce_small).  The output is the same residue in [0, q).
 // Rounds hold up to 2^K elements per group with K <= the context's radix cap (log2 of 2, 4 or
 // 8; the autotuner picks it).
 #include "he_internal.cuh"
@@ -181,12 +181,8 @@ __device__ __forceinline__ void row_round(uint64_t (&x)[8], uint64_t* sm, uint64
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             uint64_t v = x[i];
-            if (!INV && SMALL) {                        // v < 68 q: subtract 64 q, ..., q
-#pragma unroll
-                for (int sh = 6; sh >= 0; --sh) {
-                    const uint64_t m = q << sh;
-                    v = v >= m ? v - m : v;
-                }
+            if (!INV && SMALL) {                        // v < 68 q < 2^(b + 7)
+                v = reduce_small(v, Mc);
             } else if (!INV) {
                 v = v >= q2 ? v - q2 : v;
                 v = v >= q ? v - q : v;
