@@ -413,7 +413,9 @@ int he_deep_batch(he_ctx* ctx, const he_ct* in, int B, const he_mc_conv* convs, 
  * (256, columns); [4] the NTT time of the chosen split and [5] its log2 N1; [6] the chosen
  * tile; [7] the chosen arithmetic; [8] the precomputed-product path's ms (0 where it does not
  * apply); [9] the chosen NTT radix (8 or 4); [10..12] the conversions' ms with 1, 2 and 4
- * limb groups and [13] the chosen number; the rest 0.  Without a call: tile 128 for keys of four or more digits (else 256),
+ * limb groups and [13] the chosen number; [14] / [15] one ModUp + ModDown of min(batch, 64)
+ * ciphertexts with the base conversions as separate kernels / inside the forward NTT's first
+ * pass (the faster is kept, HE_TUNE_BCONV_FUSED).  Without a call: tile 128 for keys of four or more digits (else 256),
  * carry chains, split log2 N1 = floor(log2 N / 2).  Uses the context scratch; synchronises
  * the stream. */
 #define HE_TUNE_REPORT_LEN 16
@@ -421,7 +423,9 @@ int he_autotune(he_ctx* ctx, int batch, int force_tile, double* ms_out);
 /* Tuning knobs, set by hand (value -1 restores the default) or read back: HE_TUNE_TAP_TILE
  * (128 or 256), HE_TUNE_TAP_ARITH (0 chains, 1 columns, 2 precomputed products),
  * HE_TUNE_NTT_SPLIT (log2 N1, 1 .. log2 N - 1), HE_TUNE_NTT_RADIX (2, 4 or 8: the most points
- * a thread group transforms per round), HE_TUNE_LIMB_GROUPS (1, 2 or 4).  Results never
+ * a thread group transforms per round), HE_TUNE_LIMB_GROUPS (1, 2 or 4), HE_TUNE_BCONV_FUSED
+ * (0: the ModUp / ModDown base conversions as separate kernels, 1 (default): read by the
+ * forward NTT's first pass, the inverse NTT before them leaving y directly).  Results never
  * depend on them.  he_tune_set is
  * refused while recording.  The precomputed products take a grow-only buffer of 16 x taps x
  * dnum x n_q x N bytes, allocated at the first call that needs it (not while recording). */
@@ -430,7 +434,8 @@ enum {
     HE_TUNE_TAP_ARITH = 1,
     HE_TUNE_NTT_SPLIT = 2,
     HE_TUNE_NTT_RADIX = 3,
-    HE_TUNE_LIMB_GROUPS = 4
+    HE_TUNE_LIMB_GROUPS = 4,
+    HE_TUNE_BCONV_FUSED = 5
 };
 int he_tune_set(he_ctx* ctx, int knob, int value);
 int he_tune_get(he_ctx* ctx, int knob, int* value);

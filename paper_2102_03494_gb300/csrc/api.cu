@@ -413,6 +413,7 @@ static void free_ctx(he_ctx* c) {
     if (c->stream || true) cudaStreamSynchronize(c->stream);
     void* ptrs[] = {c->d_mod, c->d_tw_fwd, c->d_tw_inv, c->d_slot_pos, c->d_cdt,
                     c->d_modup_inv, c->d_modup_c, c->d_md_inv, c->d_md_c, c->d_md_pinv,
+                    c->d_modup_ninv, c->d_md_ninv,
                     c->d_rs_inv, c->d_pmodq, c->arena.base, c->staging.dev, c->d_err,
                     c->d_mult_tab, c->net.base, c->pk.base};
     for (void* p : ptrs)
@@ -559,6 +560,9 @@ extern "C" int he_ctx_create(const he_params* p, void* stream, he_ctx** out) {
         md_pinv[i] = h_shoup(h_inv(P, qi), qi);
         pmodq[i] = h_to_mont(P, qi);
     }
+    std::vector<ShoupPair> mu_ninv(L), md_ninv(K);
+    for (int i = 0; i < L; ++i) mu_ninv[i] = h_shoup(h_mulmod(mc[i].n_inv, mu_inv[i].w, qs[i]), qs[i]);
+    for (int k = 0; k < K; ++k) md_ninv[k] = h_shoup(h_mulmod(mc[L + k].n_inv, md_inv[k].w, ps[k]), ps[k]);
     std::vector<ShoupPair> rs((size_t)L * L, ShoupPair{0, 0});
     for (int lv = 1; lv < L; ++lv)
         for (int i = 0; i < lv; ++i) rs[(size_t)lv * L + i] = h_shoup(h_inv(qs[lv] % qs[i], qs[i]), qs[i]);
@@ -569,6 +573,7 @@ extern "C" int he_ctx_create(const he_params* p, void* stream, he_ctx** out) {
         (rc = upload_vec(c, &c->d_cdt, cdtv)) || (rc = upload_vec(c, &c->d_modup_inv, mu_inv)) ||
         (rc = upload_vec(c, &c->d_modup_c, mu_c)) || (rc = upload_vec(c, &c->d_md_inv, md_inv)) ||
         (rc = upload_vec(c, &c->d_md_c, md_c)) || (rc = upload_vec(c, &c->d_md_pinv, md_pinv)) ||
+        (rc = upload_vec(c, &c->d_modup_ninv, mu_ninv)) || (rc = upload_vec(c, &c->d_md_ninv, md_ninv)) ||
         (rc = upload_vec(c, &c->d_rs_inv, rs)) || (rc = upload_vec(c, &c->d_pmodq, pmodq))) {
         free_ctx(c);
         return rc;

@@ -256,15 +256,12 @@ extern "C" int he_mc_conv_batch(he_ctx* ctx, const he_ct* in, int B, const int32
         // one ModDown per (image, channel): AX [B][cn][2][LK][N] -> Y [B][cn][2][L][N]
         const int it = B * cn;
         phase_begin(ctx, HE_PHASE_MODDOWN);
-        ntt_inverse(ctx, AX + (size_t)L * N, it * 2, (size_t)LK * N, ctx->K, L);
-        launch_moddown_conv(ctx, AX, ext_ct, V, ct, it);
-        ntt_forward(ctx, V, it * 2, (size_t)L * N, L, 0);
         {
             std::vector<uint64_t*> yo(it);
             for (int q = 0; q < it; ++q) yo[q] = Y + (size_t)q * ct;
             auto op = upload_out_ptrs(ctx, yo);
             if (!op) return he_fail(ctx, HE_ECUDA, "pointer table upload failed");
-            launch_ks_combine(ctx, AX, ext_ct, V, ct, nullptr, nullptr, op, it, 1u);
+            moddown_combine(ctx, AX, V, it, nullptr, nullptr, op, 1u);
         }
         phase_end(ctx);
         // block sum: y1 = sum_{u<g} rot(Y, u Bk) (hoisted, summed in Q u P, one ModDown)
@@ -282,14 +279,11 @@ extern "C" int he_mc_conv_batch(he_ctx* ctx, const he_ct* in, int B, const int32
                 ft.g[u] = u ? fold_g[u - 1] : 1u;
             }
             launch_ks_mac_ext(ctx, rbf.D, YP, ones, ft, AF, it);
-            ntt_inverse(ctx, AF + (size_t)L * N, it * 2, (size_t)LK * N, ctx->K, L);
-            launch_moddown_conv(ctx, AF, ext_ct, V, ct, it);
-            ntt_forward(ctx, V, it * 2, (size_t)L * N, L, 0);
             std::vector<uint64_t*> yo(it);
             for (int q = 0; q < it; ++q) yo[q] = Y2 + (size_t)q * ct;
             auto op = upload_out_ptrs(ctx, yo);
             if (!op) return he_fail(ctx, HE_ECUDA, "pointer table upload failed");
-            launch_ks_combine(ctx, AF, ext_ct, V, ct, nullptr, nullptr, op, it, 1u);
+            moddown_combine(ctx, AF, V, it, nullptr, nullptr, op, 1u);
             Ya = Y2;
             phase_end(ctx);
         }

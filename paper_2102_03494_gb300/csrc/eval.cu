@@ -123,6 +123,22 @@ void modup_items(he_ctx* c, const uint64_t* X, int items, uint32_t g_own, const 
     const size_t N = c->N, L = c->L, LK = c->L + c->K;
     const size_t dstride = c->dnum * LK * N;
     launch_automorph(c, X + L * N, 2 * L * N, b.T, L * N, items, (int)L, g_own);
+    if (c->bconv_fused) {
+        // T <- y_i = [c1_i (Q_j/q_i)^-1]_{q_i} in coefficient form (the factor rides on N^-1);
+        // each digit's own rows are c1 itself at perm positions; every other row is the
+        // conversion, read by the forward NTT's first pass
+        ntt_inverse_scaled(c, b.T, items, L * N, (int)L, 0, c->d_modup_ninv);
+        launch_automorph(c, X + L * N, 2 * L * N, b.D, dstride, items, (int)L, g_own, c->alpha,
+                         (int)LK);
+        for (int j = 0; j < c->dnum; ++j) {
+            const int i0 = j * c->alpha, i1 = std::min(i0 + c->alpha, c->L);
+            const BConvSrc bc{b.T + (size_t)i0 * N, L * N, c->d_modup_c + (size_t)j * c->alpha * LK,
+                              (int)LK, i1 - i0};
+            ntt_forward_bconv(c, b.D + (size_t)j * LK * N, items, dstride, i0, 0, bc);
+            ntt_forward_bconv(c, b.D + ((size_t)j * LK + i1) * N, items, dstride, (int)LK - i1, i1, bc);
+        }
+        return;
+    }
     ntt_inverse(c, b.T, items, L * N, (int)L, 0);
     launch_modup(c, b.T, L * N, X + L * N, 2 * L * N, g_own, b.D, dstride, items);
     for (int j = 0; j < c->dnum; ++j) {
@@ -132,6 +148,37 @@ void modup_items(he_ctx* c, const uint64_t* X, int items, uint32_t g_own, const 
     }
 }
 
+// v <- the ModDown base conversion of the P limbs of u, NTT domain: u [items][2][L+K][N]
+// (NTT domain; its P limbs are left in coefficient form, scaled), v [items][2][L][N].
+void moddown_items(he_ctx* c, uint64_t* u, uint64_t* v, int items) {
+    const size_t N = c->N, L = c->L, LK = c->L + c->K;
+    if (c->bconv_fused) {
+        ntt_inverse_scaled(c, u + L * N, items * 2, LK * N, c->K, (int)L, c->d_md_ninv);
+        const BConvSrc bc{u + L * N, LK * N, c->d_md_c, (int)L, c->K};
+        ntt_forward_bconv(c, v, items * 2, L * N, (int)L, 0, bc);
+        return;
+    }
+    ntt_inverse(c, u + L * N, items * 2, LK * N, c->K, (int)L);
+    launch_moddown_conv(c, u, 2 * LK * N, v, 2 * L * N, items);
+    ntt_forward(c, v, items * 2, L * N, (int)L, 0);
+}
+
+// The ModDown of u and the key switch's last step: out[it] = (u_Q - conv(u_P)) P^-1
+// (+ c0[it] at perm_g, + base[it]); v [items][2][L][N] is scratch.
+void moddown_combine(he_ctx* c, uint64_t* u, uint64_t* v, int items, const uint64_t* const* c0p,
+                     const uint64_t* const* basep, uint64_t* const* outp, uint32_t g) {
+    const size_t N = c->N, L = c->L, LK = c->L + c->K;
+    if (c->bconv_fused) {
+        ntt_inverse_scaled(c, u + L * N, items * 2, LK * N, c->K, (int)L, c->d_md_ninv);
+        const BConvSrc bc{u + L * N, LK * N, c->d_md_c, (int)L, c->K};
+        const CombineDst cd{u, LK * N, c0p, basep, outp, c->d_md_pinv, (int)L, g};
+        ntt_forward_bconv_combine(c, v, items * 2, L * N, (int)L, bc, cd);
+        return;
+    }
+    moddown_items(c, u, v, items);
+    launch_ks_combine(c, u, 2 * LK * N, v, 2 * L * N, c0p, basep, outp, items, g);
+}
+
 // Key switch of the prepared digits (read through perm g_ks) and the rotation's tail:
 // out[it] = (u - v) P^-1 + perm_g(c0[it]) (+ base[it]).
 void ks_items(he_ctx* c, int items, const uint64_t* key, uint32_t g_ks, uint32_t g,
@@ -139,10 +186,7 @@ void ks_items(he_ctx* c, int items, const uint64_t* key, uint32_t g_ks, uint32_t
               const RotBufs& b) {
     const size_t N = c->N, L = c->L, LK = c->L + c->K;
     launch_ks_inner(c, b.D, c->dnum * LK * N, key, b.u, 2 * LK * N, items, g_ks);
-    ntt_inverse(c, b.u + L * N, items * 2, LK * N, c->K, (int)L);
-    launch_moddown_conv(c, b.u, 2 * LK * N, b.v, 2 * L * N, items);
-    ntt_forward(c, b.v, items * 2, L * N, (int)L, 0);
-    launch_ks_combine(c, b.u, 2 * LK * N, b.v, 2 * L * N, c0p, basep, outp, items, g);
+    moddown_combine(c, b.u, b.v, items, c0p, basep, outp, g);
 }
 
 const uint64_t* const* upload_ptrs(he_ctx* c, const std::vector<const uint64_t*>& v) {

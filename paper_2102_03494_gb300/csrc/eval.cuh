@@ -15,6 +15,9 @@ struct RotBufs {
 size_t rot_scratch_per_item(const he_ctx* c);
 RotBufs rot_bufs_take(he_ctx* c, int items);
 void modup_items(he_ctx* c, const uint64_t* X, int items, uint32_t g_own, const RotBufs& b);
+void moddown_items(he_ctx* c, uint64_t* u, uint64_t* v, int items);
+void moddown_combine(he_ctx* c, uint64_t* u, uint64_t* v, int items, const uint64_t* const* c0p,
+                     const uint64_t* const* basep, uint64_t* const* outp, uint32_t g);
 void ks_items(he_ctx* c, int items, const uint64_t* key, uint32_t g_ks, uint32_t g,
               const uint64_t* const* c0p, const uint64_t* const* basep, uint64_t* const* outp,
               const RotBufs& b);

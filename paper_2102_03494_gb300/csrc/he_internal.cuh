@@ -61,6 +61,17 @@ __device__ __forceinline__ uint64_t reduce_small(uint64_t v, const ModConst& M) 
 
 __device__ __forceinline__ uint64_t neg_mod(uint64_t a, uint64_t q) { return a ? q - a : 0; }
 
+__device__ __forceinline__ uint32_t brv_bits(uint32_t x, int bits) {
+    return bits ? (__brev(x) >> (32 - bits)) : 0u;
+}
+
+// NTT-domain automorphism X -> X^g: position p holds a(psi^(2 brv(p) + 1)); the image takes
+// the value at exponent (2 brv(p) + 1) g mod 2N.
+__device__ __forceinline__ uint32_t perm_src(uint32_t p, uint32_t g, int logN) {
+    uint32_t e = (2u * brv_bits(p, logN) + 1u) * g & ((2u << logN) - 1u);
+    return brv_bits((e - 1u) >> 1, logN);
+}
+
 // High 64 bits of a 64 x 64-bit product from 32-bit partial products in one carry chain (the
 // low word of a0 b0 cannot carry: it is never added to).
 #pragma nv_diag_suppress 550   // c1 below is written by the chain and read only through carries
@@ -201,6 +212,10 @@ struct he_ctx {
     ShoupPair* d_md_inv = nullptr;      // [K]
     ShoupPair* d_md_c = nullptr;        // [K][L]
     ShoupPair* d_md_pinv = nullptr;     // [L]
+    // the inverse NTT's N^-1 times the conversion's first factor, so that the inverse transform
+    // of a converted limb leaves y directly (the fused conversion, ntt_forward_bconv)
+    ShoupPair* d_modup_ninv = nullptr;  // [L]: N^-1 [(Q_j/q_i)^-1]_{q_i}
+    ShoupPair* d_md_ninv = nullptr;     // [K]: N^-1 [(P/p_k)^-1]_{p_k}
     ShoupPair* d_rs_inv = nullptr;      // [L][L]: row lv = q_lv^-1 mod q_i (rescale at level lv+1)
     uint64_t* d_pmodq = nullptr;        // [L] P mod q_i (Montgomery form) for key generation
     int* d_err = nullptr;               // device error word: bit 0 = a bounded wait ran out
@@ -214,6 +229,8 @@ struct he_ctx {
     int ntt_radix = 0;                  // NTT rounds of up to 2^ntt_radix points (0: 3, radix 8)
     int limb_groups = 0;                // ModUp / ModDown conversions: target limbs split in
                                         // this many groups across the grid (0: 1)
+    int bconv_fused = 1;                // ModUp / ModDown base conversions: 1 inside the
+                                        // forward NTT's first pass, 0 separate kernels
     int tap_arith = 0;                  // tap kernel: 0 carry chains, 1 30-bit columns,
                                         // 2 precomputed plaintext x key products
     int wait_report = -1;               // he_set_wait_report: polls before a stage wait is
@@ -340,3 +357,37 @@ void ntt_forward(he_ctx* ctx, uint64_t* data, int items, size_t item_stride, int
 int ntt_split_candidates(int logN, int* out, int cap);
 void ntt_inverse(he_ctx* ctx, uint64_t* data, int items, size_t item_stride, int rows,
                  int mod_off);
+// The inverse NTT with row r's N^-1 replaced by scale[r] (a per-row constant times N^-1).
+void ntt_inverse_scaled(he_ctx* ctx, uint64_t* data, int items, size_t item_stride, int rows,
+                        int mod_off, const ShoupPair* scale);
+
+// Fast base conversion read by a forward NTT's first pass instead of its input: row r of item
+// it (modulus m = mod_off + r) starts as sum_k y_k c_{k,m} mod m, with y_k the item's source
+// limb k at src + it src_stride + k N (coefficient form, already multiplied by its inverse
+// factor) and c_{k,m} = cst[k cst_s + m].  At most 8 source limbs.
+struct BConvSrc {
+    const uint64_t* src;
+    size_t src_stride;
+    const ShoupPair* cst;
+    int cst_s;
+    int ns;
+};
+void ntt_forward_bconv(he_ctx* ctx, uint64_t* data, int items, size_t item_stride, int rows,
+                       int mod_off, const BConvSrc& bc);
+
+// The key switch's last step written by the row pass of that forward NTT instead of its
+// output v: item z = 2 it + k, row m (modulus m): out = (u - v) P^-1 (+ c0[perm_g] for k = 0)
+// (+ base), with u at u + z u_stride + m N and the per-it pointers outp / c0p / basep
+// ([2][L][N] ciphertexts; c0p, basep may be null).  pinv[m] = P^-1 mod q_m.
+struct CombineDst {
+    const uint64_t* u;
+    size_t u_stride;
+    const uint64_t* const* c0p;
+    const uint64_t* const* basep;
+    uint64_t* const* outp;
+    const ShoupPair* pinv;
+    int L;
+    uint32_t g;
+};
+void ntt_forward_bconv_combine(he_ctx* ctx, uint64_t* data, int items, size_t item_stride,
+                               int rows, const BConvSrc& bc, const CombineDst& cd);

@@ -3,6 +3,8 @@
 // Layout: a ring element is [limbs][N] uint64 residues; a ciphertext [2][limbs][N].  Grids
 // put the "item" (ciphertext / output) index in blockIdx.x so that CTAs running together
 // touch the same coefficient tile of shared operands (keys, plaintexts) and find it in L2.
+#include <algorithm>
+
 #include "he_internal.cuh"
 #include "kernels.cuh"
 
@@ -10,18 +12,7 @@ namespace {
 
 constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
 
-__device__ __forceinline__ uint32_t brv_bits(uint32_t x, int bits) {
-    return bits ? (__brev(x) >> (32 - bits)) : 0u;
-}
-
 }  // namespace
-
-// NTT-domain automorphism X -> X^g: position p holds a(psi^(2 brv(p) + 1)); the image takes
-// the value at exponent (2 brv(p) + 1) g mod 2N.
-__device__ __forceinline__ uint32_t perm_src(uint32_t p, uint32_t g, int logN) {
-    uint32_t e = (2u * brv_bits(p, logN) + 1u) * g & ((2u << logN) - 1u);
-    return brv_bits((e - 1u) >> 1, logN);
-}
 
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -36,16 +27,34 @@ __device__ __forceinline__ uint64_t draw(uint64_t state0, uint64_t ctr) {
 // ------------------------------------------------------------------ automorphism
 
 // out[item][r][p] = in[item][r][perm_g(p)] for `rows` limbs per item.
-__global__ void k_automorph(const uint64_t* __restrict__ in, size_t in_stride,
-                            uint64_t* __restrict__ out, size_t out_stride, int rows, int logN,
-                            uint32_t g) {
-    const int N = 1 << logN;
-    const int n = blockIdx.y * blockDim.x + threadIdx.x;
-    if (n >= N) return;
-    const uint32_t src = perm_src(n, g, logN);
-    const uint64_t* a = in + blockIdx.x * in_stride;
-    uint64_t* b = out + blockIdx.x * out_stride;
-    for (int r = 0; r < rows; ++r) b[(size_t)r * N + n] = a[(size_t)r * N + src];
+// The outputs of an aligned chunk of T = 2^lt consecutive positions read one aligned chunk of
+// T inputs: the top logN - lt bits of perm_src(p) depend only on those of p (an odd exponent
+// times g keeps its low bits a function of its low bits, and the bit reversal exchanges low
+// and high bits).  One CTA per (item, chunk, row) stages the source chunk in shared memory by
+// coalesced 16-byte loads, then writes its outputs in order.  With alpha > 0 output row r goes
+// to row (r / alpha) lk + r: a digit's own limbs inside the ModUp layout [dnum][lk][N].
+constexpr int kAutoLog = 11;   // T = 2048 residues, 16 KiB
+__global__ void __launch_bounds__(256) k_automorph(const uint64_t* __restrict__ in, size_t in_stride,
+                                                   uint64_t* __restrict__ out, size_t out_stride,
+                                                   int logN, uint32_t g, int alpha, int lk) {
+    __shared__ __align__(16) uint64_t sm[1 << kAutoLog];
+    const int lt = min(logN, kAutoLog), T = 1 << lt;
+    const size_t N = (size_t)1 << logN;
+    const uint32_t c0 = blockIdx.y << lt;                         // first output of the chunk
+    const uint32_t s0 = perm_src(c0, g, logN) & ~(uint32_t)(T - 1);
+    const uint64_t* a = in + blockIdx.x * in_stride + blockIdx.z * N + s0;
+    const size_t orow = alpha ? (blockIdx.z / alpha) * (size_t)lk + blockIdx.z : blockIdx.z;
+    uint64_t* b = out + blockIdx.x * out_stride + orow * N + c0;
+    if ((reinterpret_cast<uintptr_t>(a) & 15) == 0) {            // T is even: whole pairs
+        const ulonglong2* a2 = reinterpret_cast<const ulonglong2*>(a);
+        for (int i = threadIdx.x; i < T / 2; i += blockDim.x)
+            reinterpret_cast<ulonglong2*>(sm)[i] = a2[i];
+    } else {
+        for (int i = threadIdx.x; i < T; i += blockDim.x) sm[i] = a[i];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < T; i += blockDim.x)
+        b[i] = sm[perm_src(c0 + i, g, logN) & (T - 1)];
 }
 
 // ------------------------------------------------------------------ key switching
@@ -778,10 +787,12 @@ static inline dim3 grid_nx(int items, int N, int z) {
 }
 
 void launch_automorph(he_ctx* c, const uint64_t* in, size_t in_stride, uint64_t* out,
-                      size_t out_stride, int items, int rows, uint32_t g) {
+                      size_t out_stride, int items, int rows, uint32_t g, int alpha, int lk) {
+    if (items <= 0 || rows <= 0) return;
     ++c->launches;
-    k_automorph<<<grid_nx(items, c->N, 1), 256, 0, c->stream>>>(in, in_stride, out, out_stride,
-                                                                 rows, c->logN, g);
+    const int lt = std::min(c->logN, kAutoLog);
+    k_automorph<<<dim3(items, c->N >> lt, rows), 256, 0, c->stream>>>(
+        in, in_stride, out, out_stride, c->logN, g, alpha, lk);
 }
 
 void launch_modup(he_ctx* c, const uint64_t* x_coeff, size_t xc_stride, const uint64_t* x_ntt,

@@ -29,8 +29,10 @@ bool tapmac_bulk_supported(const he_ctx* c);
 void launch_ks_mac_ext_bulk(he_ctx* c, const uint64_t* D, const uint64_t* XP, const uint64_t* pts,
                             const TapTable& tt, uint64_t* A, int B);
 
+// out row r = in row r at perm_g positions; with alpha > 0, out row (r / alpha) lk + r.
 void launch_automorph(he_ctx* c, const uint64_t* in, size_t in_stride, uint64_t* out,
-                      size_t out_stride, int items, int rows, uint32_t g);
+                      size_t out_stride, int items, int rows, uint32_t g, int alpha = 0,
+                      int lk = 0);
 void launch_modup(he_ctx* c, const uint64_t* x_coeff, size_t xc_stride, const uint64_t* x_ntt,
                   size_t xn_stride, uint32_t g_own, uint64_t* out, size_t out_stride, int items);
 void launch_ks_inner(he_ctx* c, const uint64_t* D, size_t d_stride, const uint64_t* key,

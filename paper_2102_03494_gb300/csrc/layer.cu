@@ -655,14 +655,11 @@ static int layer_impl(he_ctx* ctx, const he_ct* ct_in, int B, const int32_t* low
         const int items = B * r;
         phase_begin(ctx, HE_PHASE_MODDOWN);
         const size_t ext_ct = 2 * (size_t)LK * N;
-        ntt_inverse(ctx, AX + (size_t)L * N, items * 2, (size_t)LK * N, ctx->K, L);
-        launch_moddown_conv(ctx, AX, ext_ct, rb.v, ct, items);
-        ntt_forward(ctx, rb.v, items * 2, (size_t)L * N, L, 0);
         std::vector<uint64_t*> ao(items);
         for (int q = 0; q < items; ++q) ao[q] = A + (size_t)q * ct;
         auto op = upload_out_ptrs(ctx, ao);
         if (!op) return he_fail(ctx, HE_ECUDA, "pointer table upload failed");
-        launch_ks_combine(ctx, AX, ext_ct, rb.v, ct, nullptr, nullptr, op, items, 1u);
+        moddown_combine(ctx, AX, rb.v, items, nullptr, nullptr, op, 1u);
         phase_end(ctx);
         ctx->ops[0] += (uint64_t)B * r * li.taps;
         ctx->ops[1] += (uint64_t)B * r * (li.taps - 1);

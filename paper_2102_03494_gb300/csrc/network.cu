@@ -214,15 +214,12 @@ static int fc_core(he_ctx* ctx, const he_ct* in, int B, int n_ct, const int32_t*
     phase_end(ctx);
     // one ModDown per image
     phase_begin(ctx, HE_PHASE_MODDOWN);
-    ntt_inverse(ctx, AX + (size_t)L * N, B * 2, (size_t)LK * N, ctx->K, L);
-    launch_moddown_conv(ctx, AX, ext_ct, rb.v, ct, B);
-    ntt_forward(ctx, rb.v, B * 2, (size_t)L * N, L, 0);
     {
         std::vector<uint64_t*> ao(B);
         for (int b = 0; b < B; ++b) ao[b] = A + (size_t)b * ct;
         auto op = upload_out_ptrs(ctx, ao);
         if (!op) return he_fail(ctx, HE_ECUDA, "pointer table upload failed");
-        launch_ks_combine(ctx, AX, ext_ct, rb.v, ct, nullptr, nullptr, op, B, 1u);
+        moddown_combine(ctx, AX, rb.v, B, nullptr, nullptr, op, 1u);
     }
     phase_end(ctx);
     ctx->ops[0] += (uint64_t)B * T;

@@ -85,14 +85,31 @@ __device__ __forceinline__ void round_bflies(uint64_t (&x)[8], const int (&hi)[8
     }
 }
 
+// The fused base conversion as one CTA of the column pass sees it: the item's source limbs
+// and the constants of the CTA's target modulus (staged in shared memory).
+struct BConvCta {
+    const uint64_t* s;
+    const ShoupPair* c;
+    int ns, N;
+};
+
+__device__ __forceinline__ uint64_t bconv_at(const BConvCta& p, size_t pos, uint64_t q) {
+    uint64_t acc = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        if (k < p.ns) acc = add_mod(acc, mul_shoup(p.s[(size_t)k * p.N + pos], p.c[k].w, p.c[k].ws, q), q);
+    return acc;
+}
+
 // One round of the column pass.  Element m of group Gi: column c = Gi mod cols, row
 // hi (tlow 2^K) + m tlow + lo with (hi, lo) = divmod(Gi / cols, tlow).  cols = 2^lc and
 // tlow = 2^(s1 - e0 - K), so the divisions are shifts.
-template <int K, bool INV, bool SMALL>
+template <int K, bool INV, bool SMALL, bool PRO>
 __device__ __forceinline__ void col_round(uint64_t (&x)[8], uint64_t* sm, uint64_t* __restrict__ a,
                                           bool first, bool last, int e0, int s1, int N2, int lo0,
                                           int lc, const ShoupPair* __restrict__ w,
-                                          const ModConst& Mc) {
+                                          const ModConst& Mc, const BConvCta& pc,
+                                          const ShoupPair& osc) {
     constexpr int M = 1 << K;
     const int ltl = s1 - e0 - K, tlow = 1 << ltl;
     const int cmask = (1 << lc) - 1;
@@ -113,7 +130,8 @@ __device__ __forceinline__ void col_round(uint64_t (&x)[8], uint64_t* sm, uint64
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int row = off[i] >> lc, c = off[i] & cmask;
-            x[i] = a[(size_t)row * N2 + lo0 + c];
+            const size_t pos = (size_t)row * N2 + lo0 + c;
+            x[i] = PRO ? bconv_at(pc, pos, Mc.q) : a[pos];
         }
     } else {
 #pragma unroll
@@ -126,7 +144,7 @@ __device__ __forceinline__ void col_round(uint64_t (&x)[8], uint64_t* sm, uint64
         for (int i = 0; i < 8; ++i) {
             const int row = off[i] >> lc, c = off[i] & cmask;
             uint64_t v = x[i];
-            if (INV) v = mul_shoup(v, Mc.n_inv, Mc.n_inv_sh, q);
+            if (INV) v = mul_shoup(v, osc.w, osc.ws, q);
             a[(size_t)row * N2 + lo0 + c] = v;
         }
     } else {
@@ -136,12 +154,23 @@ __device__ __forceinline__ void col_round(uint64_t (&x)[8], uint64_t* sm, uint64
     }
 }
 
+// The combine step as one CTA of the row pass sees it (CombineDst for its item and row).
+struct CombineCta {
+    const uint64_t* u;
+    uint64_t* o;
+    const uint64_t* c0;
+    const uint64_t* base;
+    ShoupPair pinv;
+    uint32_t g;
+};
+
 // One round of the row pass.  Element m of group Gi: block b = Gi / (N2 >> K) of the tile,
 // local index hi (tlow 2^K) + m tlow + lo.
-template <int K, bool INV, bool SMALL>
+template <int K, bool INV, bool SMALL, bool EPI>
 __device__ __forceinline__ void row_round(uint64_t (&x)[8], uint64_t* sm, uint64_t* __restrict__ a,
                                           bool first, bool last, int e0, int s1, int s2, int blk0,
-                                          const ShoupPair* __restrict__ w, const ModConst& Mc) {
+                                          const ShoupPair* __restrict__ w, const ModConst& Mc,
+                                          const CombineCta& ep) {
     constexpr int M = 1 << K;
     const int N2 = 1 << s2;
     const int ltl = s2 - e0 - K, tlow = 1 << ltl;
@@ -187,7 +216,15 @@ __device__ __forceinline__ void row_round(uint64_t (&x)[8], uint64_t* sm, uint64
                 v = v >= q2 ? v - q2 : v;
                 v = v >= q ? v - q : v;
             }
-            a[(size_t)blk0 * N2 + off[i]] = v;
+            const size_t pos = (size_t)blk0 * N2 + off[i];
+            if (EPI) {
+                uint64_t r = mul_shoup(sub_mod(ep.u[pos], v, q), ep.pinv.w, ep.pinv.ws, q);
+                if (ep.c0) r = add_mod(r, ep.c0[perm_src((uint32_t)pos, ep.g, s1 + s2)], q);
+                if (ep.base) r = add_mod(r, ep.base[pos], q);
+                ep.o[pos] = r;
+            } else {
+                a[pos] = v;
+            }
         }
     } else {
 #pragma unroll
@@ -208,10 +245,11 @@ __device__ __forceinline__ void round_of(int r, int lg, bool inv, int kmax, int&
     }
 }
 
-template <bool INV, bool SMALL, int KMAX>
+template <bool INV, bool SMALL, int KMAX, bool PRO>
 __device__ __forceinline__ void ntt_cols_body(uint64_t* __restrict__ a, uint64_t* sm, int logN,
                                               int s1, int lc, int lo0,
-                                              const ShoupPair* __restrict__ w, const ModConst& Mc) {
+                                              const ShoupPair* __restrict__ w, const ModConst& Mc,
+                                              const BConvCta& pc, const ShoupPair& osc) {
     const int N2 = (1 << logN) >> s1;
     const int nr = (s1 + KMAX - 1) / KMAX;
     uint64_t x[8];
@@ -219,16 +257,17 @@ __device__ __forceinline__ void ntt_cols_body(uint64_t* __restrict__ a, uint64_t
         int e0, K;
         round_of(r, s1, INV, KMAX, e0, K);
         const bool first = r == 0, last = r == nr - 1;
-        if (KMAX == 3 && K == 3) col_round<3, INV, SMALL>(x, sm, a, first, last, e0, s1, N2, lo0, lc, w, Mc);
-        else if (K == 2) col_round<2, INV, SMALL>(x, sm, a, first, last, e0, s1, N2, lo0, lc, w, Mc);
-        else col_round<1, INV, SMALL>(x, sm, a, first, last, e0, s1, N2, lo0, lc, w, Mc);
+        if (KMAX == 3 && K == 3) col_round<3, INV, SMALL, PRO>(x, sm, a, first, last, e0, s1, N2, lo0, lc, w, Mc, pc, osc);
+        else if (K == 2) col_round<2, INV, SMALL, PRO>(x, sm, a, first, last, e0, s1, N2, lo0, lc, w, Mc, pc, osc);
+        else col_round<1, INV, SMALL, PRO>(x, sm, a, first, last, e0, s1, N2, lo0, lc, w, Mc, pc, osc);
     }
 }
 
-template <bool INV, bool SMALL, int KMAX>
+template <bool INV, bool SMALL, int KMAX, bool EPI>
 __device__ __forceinline__ void ntt_rows_body(uint64_t* __restrict__ a, uint64_t* sm, int logN,
                                               int s1, int blk0,
-                                              const ShoupPair* __restrict__ w, const ModConst& Mc) {
+                                              const ShoupPair* __restrict__ w, const ModConst& Mc,
+                                              const CombineCta& ep) {
     const int s2 = logN - s1;
     const int nr = (s2 + KMAX - 1) / KMAX;
     uint64_t x[8];
@@ -236,9 +275,9 @@ __device__ __forceinline__ void ntt_rows_body(uint64_t* __restrict__ a, uint64_t
         int e0, K;
         round_of(r, s2, INV, KMAX, e0, K);
         const bool first = r == 0, last = r == nr - 1;
-        if (KMAX == 3 && K == 3) row_round<3, INV, SMALL>(x, sm, a, first, last, e0, s1, s2, blk0, w, Mc);
-        else if (K == 2) row_round<2, INV, SMALL>(x, sm, a, first, last, e0, s1, s2, blk0, w, Mc);
-        else row_round<1, INV, SMALL>(x, sm, a, first, last, e0, s1, s2, blk0, w, Mc);
+        if (KMAX == 3 && K == 3) row_round<3, INV, SMALL, EPI>(x, sm, a, first, last, e0, s1, s2, blk0, w, Mc, ep);
+        else if (K == 2) row_round<2, INV, SMALL, EPI>(x, sm, a, first, last, e0, s1, s2, blk0, w, Mc, ep);
+        else row_round<1, INV, SMALL, EPI>(x, sm, a, first, last, e0, s1, s2, blk0, w, Mc, ep);
     }
 }
 
@@ -246,24 +285,38 @@ __device__ __forceinline__ void ntt_rows_body(uint64_t* __restrict__ a, uint64_t
 // the header); the launcher splits a launch's limbs by that test.
 bool small_mod(uint64_t q) { return (q >> 57) == 0; }
 
-template <bool INV, bool SMALL, int KMAX>
+// Column pass.  Inverse: the last round multiplies by oscale[row] when given, else N^-1.
+// Forward with PRO: the first round reads the fused base conversion `bc` instead of `data`.
+template <bool INV, bool SMALL, int KMAX, bool PRO>
 __global__ void __launch_bounds__(256, 4)
 k_ntt_cols(uint64_t* __restrict__ data, size_t item_stride, int mod_off, int logN, int s1, int lc,
-           const ModConst* __restrict__ mods, const ShoupPair* __restrict__ tw) {
+           const ModConst* __restrict__ mods, const ShoupPair* __restrict__ tw,
+           const ShoupPair* __restrict__ oscale, const BConvSrc bc) {
     __shared__ uint64_t sm[kTile];
+    __shared__ ShoupPair csm[8];
     const int N = 1 << logN;
     const int mod = mod_off + blockIdx.y;
     const ModConst Mc = mods[mod];
     const ShoupPair* w = tw + (size_t)mod * N;
     uint64_t* a = data + blockIdx.z * item_stride + (size_t)blockIdx.y * N;
     const int lo0 = blockIdx.x << lc;
-    ntt_cols_body<INV, SMALL, KMAX>(a, sm, logN, s1, lc, lo0, w, Mc);
+    ShoupPair osc{Mc.n_inv, Mc.n_inv_sh};
+    if (INV && oscale) osc = oscale[blockIdx.y];
+    BConvCta pc{nullptr, csm, 0, N};
+    if (PRO) {
+        if ((int)threadIdx.x < bc.ns) csm[threadIdx.x] = bc.cst[(size_t)threadIdx.x * bc.cst_s + mod];
+        __syncthreads();
+        pc.s = bc.src + blockIdx.z * bc.src_stride;
+        pc.ns = bc.ns;
+    }
+    ntt_cols_body<INV, SMALL, KMAX, PRO>(a, sm, logN, s1, lc, lo0, w, Mc, pc, osc);
 }
 
-template <bool INV, bool SMALL, int KMAX>
+// Row pass.  Forward with EPI: the last round writes the combine step `cd` instead of v.
+template <bool INV, bool SMALL, int KMAX, bool EPI>
 __global__ void __launch_bounds__(256, 4)
 k_ntt_rows(uint64_t* __restrict__ data, size_t item_stride, int mod_off, int logN, int s1, int blocks,
-           const ModConst* __restrict__ mods, const ShoupPair* __restrict__ tw) {
+           const ModConst* __restrict__ mods, const ShoupPair* __restrict__ tw, const CombineDst cd) {
     __shared__ uint64_t sm[kTile];
     const int N = 1 << logN;
     const int mod = mod_off + blockIdx.y;
@@ -271,7 +324,18 @@ k_ntt_rows(uint64_t* __restrict__ data, size_t item_stride, int mod_off, int log
     const ShoupPair* w = tw + (size_t)mod * N;
     uint64_t* a = data + blockIdx.z * item_stride + (size_t)blockIdx.y * N;
     const int blk0 = blockIdx.x * blocks;
-    ntt_rows_body<INV, SMALL, KMAX>(a, sm, logN, s1, blk0, w, Mc);
+    CombineCta ep{nullptr, nullptr, nullptr, nullptr, ShoupPair{0, 0}, 1u};
+    if (EPI) {
+        const int it = blockIdx.z >> 1, k = blockIdx.z & 1;
+        const size_t row = (size_t)k * cd.L * N + (size_t)mod * N;
+        ep.u = cd.u + blockIdx.z * cd.u_stride + (size_t)mod * N;
+        ep.o = cd.outp[it] + row;
+        ep.c0 = (k == 0 && cd.c0p) ? cd.c0p[it] + (size_t)mod * N : nullptr;
+        ep.base = cd.basep ? cd.basep[it] + row : nullptr;
+        ep.pinv = cd.pinv[mod];
+        ep.g = cd.g;
+    }
+    ntt_rows_body<INV, SMALL, KMAX, EPI>(a, sm, logN, s1, blk0, w, Mc, ep);
 }
 
 struct Split {
@@ -334,27 +398,32 @@ int ntt_split_candidates(int logN, int* out, int cap) {
     return n;
 }
 
-template <bool INV, bool SMALL, int KMAX>
+constexpr CombineDst kNoCombine{nullptr, 0, nullptr, nullptr, nullptr, nullptr, 0, 1u};
+
+template <bool INV, bool SMALL, int KMAX, bool PRO = false, bool EPI = false>
 void launch_pass_pair(he_ctx* ctx, const Split& sp, uint64_t* d, int items, size_t item_stride,
-                      int rows, int mod) {
+                      int rows, int mod, const ShoupPair* oscale = nullptr,
+                      const BConvSrc& bc = BConvSrc{nullptr, 0, nullptr, 0, 0},
+                      const CombineDst& cd = kNoCombine) {
     dim3 gc(sp.col_ctas, rows, items), gr(sp.row_ctas, rows, items);
     ctx->launches += 2;
     const ShoupPair* tw = INV ? ctx->d_tw_inv : ctx->d_tw_fwd;
     if (!INV) {
-        k_ntt_cols<INV, SMALL, KMAX><<<gc, sp.col_threads, 0, ctx->stream>>>(
-            d, item_stride, mod, ctx->logN, sp.s1, sp.lc, ctx->d_mod, tw);
-        k_ntt_rows<INV, SMALL, KMAX><<<gr, sp.row_threads, 0, ctx->stream>>>(
-            d, item_stride, mod, ctx->logN, sp.s1, sp.blocks, ctx->d_mod, tw);
+        k_ntt_cols<INV, SMALL, KMAX, PRO><<<gc, sp.col_threads, 0, ctx->stream>>>(
+            d, item_stride, mod, ctx->logN, sp.s1, sp.lc, ctx->d_mod, tw, nullptr, bc);
+        k_ntt_rows<INV, SMALL, KMAX, EPI><<<gr, sp.row_threads, 0, ctx->stream>>>(
+            d, item_stride, mod, ctx->logN, sp.s1, sp.blocks, ctx->d_mod, tw, cd);
     } else {
-        k_ntt_rows<INV, SMALL, KMAX><<<gr, sp.row_threads, 0, ctx->stream>>>(
-            d, item_stride, mod, ctx->logN, sp.s1, sp.blocks, ctx->d_mod, tw);
-        k_ntt_cols<INV, SMALL, KMAX><<<gc, sp.col_threads, 0, ctx->stream>>>(
-            d, item_stride, mod, ctx->logN, sp.s1, sp.lc, ctx->d_mod, tw);
+        k_ntt_rows<INV, SMALL, KMAX, false><<<gr, sp.row_threads, 0, ctx->stream>>>(
+            d, item_stride, mod, ctx->logN, sp.s1, sp.blocks, ctx->d_mod, tw, kNoCombine);
+        k_ntt_cols<INV, SMALL, KMAX, false><<<gc, sp.col_threads, 0, ctx->stream>>>(
+            d, item_stride, mod, ctx->logN, sp.s1, sp.lc, ctx->d_mod, tw, oscale, bc);
     }
 }
 
-void ntt_forward(he_ctx* ctx, uint64_t* data, int items, size_t item_stride, int rows,
-                 int mod_off) {
+template <bool PRO, bool EPI = false>
+static void forward_runs(he_ctx* ctx, uint64_t* data, int items, size_t item_stride, int rows,
+                         int mod_off, const BConvSrc& bc, const CombineDst& cd = kNoCombine) {
     if (items <= 0 || rows <= 0) return;
     const Split sp = split_of(ctx->logN, ctx->ntt_s1);
     const bool r4 = ctx->ntt_radix == 2;
@@ -364,21 +433,43 @@ void ntt_forward(he_ctx* ctx, uint64_t* data, int items, size_t item_stride, int
         int r1 = r0 + 1;
         while (r1 < rows && small_mod(ctx->mods[mod_off + r1]) == small) ++r1;
         uint64_t* d = data + (size_t)r0 * ctx->N;
+        const int n = r1 - r0, m = mod_off + r0;
         if (small) {
-            if (r4) launch_pass_pair<false, true, 2>(ctx, sp, d, items, item_stride, r1 - r0, mod_off + r0);
-            else launch_pass_pair<false, true, 3>(ctx, sp, d, items, item_stride, r1 - r0, mod_off + r0);
+            if (r4) launch_pass_pair<false, true, 2, PRO, EPI>(ctx, sp, d, items, item_stride, n, m, nullptr, bc, cd);
+            else launch_pass_pair<false, true, 3, PRO, EPI>(ctx, sp, d, items, item_stride, n, m, nullptr, bc, cd);
         } else {
-            if (r4) launch_pass_pair<false, false, 2>(ctx, sp, d, items, item_stride, r1 - r0, mod_off + r0);
-            else launch_pass_pair<false, false, 3>(ctx, sp, d, items, item_stride, r1 - r0, mod_off + r0);
+            if (r4) launch_pass_pair<false, false, 2, PRO, EPI>(ctx, sp, d, items, item_stride, n, m, nullptr, bc, cd);
+            else launch_pass_pair<false, false, 3, PRO, EPI>(ctx, sp, d, items, item_stride, n, m, nullptr, bc, cd);
         }
         r0 = r1;
     }
 }
 
-void ntt_inverse(he_ctx* ctx, uint64_t* data, int items, size_t item_stride, int rows,
+void ntt_forward(he_ctx* ctx, uint64_t* data, int items, size_t item_stride, int rows,
                  int mod_off) {
+    forward_runs<false>(ctx, data, items, item_stride, rows, mod_off,
+                        BConvSrc{nullptr, 0, nullptr, 0, 0});
+}
+
+void ntt_forward_bconv(he_ctx* ctx, uint64_t* data, int items, size_t item_stride, int rows,
+                       int mod_off, const BConvSrc& bc) {
+    forward_runs<true>(ctx, data, items, item_stride, rows, mod_off, bc);
+}
+
+void ntt_forward_bconv_combine(he_ctx* ctx, uint64_t* data, int items, size_t item_stride,
+                               int rows, const BConvSrc& bc, const CombineDst& cd) {
+    forward_runs<true, true>(ctx, data, items, item_stride, rows, 0, bc, cd);
+}
+
+void ntt_inverse_scaled(he_ctx* ctx, uint64_t* data, int items, size_t item_stride, int rows,
+                        int mod_off, const ShoupPair* scale) {
     if (items <= 0 || rows <= 0) return;
     const Split sp = split_of(ctx->logN, ctx->ntt_s1);
-    if (ctx->ntt_radix == 2) launch_pass_pair<true, false, 2>(ctx, sp, data, items, item_stride, rows, mod_off);
-    else launch_pass_pair<true, false, 3>(ctx, sp, data, items, item_stride, rows, mod_off);
+    if (ctx->ntt_radix == 2) launch_pass_pair<true, false, 2>(ctx, sp, data, items, item_stride, rows, mod_off, scale);
+    else launch_pass_pair<true, false, 3>(ctx, sp, data, items, item_stride, rows, mod_off, scale);
+}
+
+void ntt_inverse(he_ctx* ctx, uint64_t* data, int items, size_t item_stride, int rows,
+                 int mod_off) {
+    ntt_inverse_scaled(ctx, data, items, item_stride, rows, mod_off, nullptr);
 }

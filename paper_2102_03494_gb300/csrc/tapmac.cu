@@ -18,6 +18,7 @@
 // never meet at a block barrier inside the tap loop, so no warp waits for the copy issue.
 // Every wait is bounded: on expiry the kernel sets a bit in the context's device error word,
 // waits (again bounded) for its own copies and returns.
+#include "eval.cuh"
 #include "he_internal.cuh"
 #include "kernels.cuh"
 
@@ -72,14 +73,6 @@ __device__ __forceinline__ void bulk_copy(void* dst_smem, const void* src_gmem, 
         : "memory");
 }
 
-__device__ __forceinline__ uint32_t brv_bits(uint32_t x, int bits) {
-    return bits ? (__brev(x) >> (32 - bits)) : 0u;
-}
-
-__device__ __forceinline__ uint32_t perm_of(uint32_t p, uint32_t g, int logN) {
-    uint32_t e = (2u * brv_bits(p, logN) + 1u) * g & ((2u << logN) - 1u);
-    return brv_bits((e - 1u) >> 1, logN);
-}
 
 __device__ __forceinline__ uint64_t redc_w(U128 x, uint64_t q, uint64_t qinv_neg) {
     const uint64_t m = x.lo * qinv_neg;   // x < 2q 2^64: (x + m q) / 2^64 < 3q
@@ -130,7 +123,7 @@ __device__ __forceinline__ void issue_tap(uint64_t* st, uint64_t* bar, int t, co
     const uint64_t* key = tt.key[t];
     const bool qlimb = l < L;
     const uint32_t row = kTile * 8;
-    const int src0 = key ? (int)(perm_of((uint32_t)n0, tt.g[t], logN) & ~(uint32_t)(kTile - 1)) : n0;
+    const int src0 = key ? (int)(perm_src((uint32_t)n0, tt.g[t], logN) & ~(uint32_t)(kTile - 1)) : n0;
     // copy list: index -> (dst, src)
     const int nkeys = key ? 2 * DNUM : 0;
     const int npts = c_cnt;
@@ -210,7 +203,7 @@ __device__ __forceinline__ bool compute_chain(const uint64_t* __restrict__ smem,
                 x[ib][1] = (qlimb && ib < nb) ? st[S::XP + (ib * 2 + 1) * kTile + tid] : 0;
             }
         } else {
-            const uint32_t pn = perm_of((uint32_t)n, tt.g[t], logN);
+            const uint32_t pn = perm_src((uint32_t)n, tt.g[t], logN);
             const int loc = (int)(pn & (kTile - 1));
             uint64_t xp[2] = {0, 0};                  // (P c0)[perm_g(n)] of each image
             if (qlimb) {
@@ -413,7 +406,7 @@ __device__ __forceinline__ bool compute_cols(const uint64_t* __restrict__ smem, 
                                    ? times16(st[S::XP + (ib * 2 + k) * kTile + tid], q, small)
                                    : 0;
         } else {
-            const uint32_t pn = perm_of((uint32_t)n, tt.g[t], logN);
+            const uint32_t pn = perm_src((uint32_t)n, tt.g[t], logN);
             const int loc = (int)(pn & (kTile - 1));
             uint64_t xp[2] = {0, 0};                   // (P c0)[perm_g(n)] of each image
             if (qlimb) {
@@ -566,7 +559,7 @@ __device__ __forceinline__ void issue_pk_tap(uint64_t* st, uint64_t* bar, int t,
     const int lane = threadIdx.x & 31;
     const bool keyed = tt.key[t] != nullptr;
     const uint32_t row = T * 8;
-    const int src0 = keyed ? (int)(perm_of((uint32_t)n0, tt.g[t], logN) & ~(uint32_t)(T - 1)) : n0;
+    const int src0 = keyed ? (int)(perm_src((uint32_t)n0, tt.g[t], logN) & ~(uint32_t)(T - 1)) : n0;
     const int npk = keyed ? c_cnt * DNUM * 2 : 0;
     const int npt = c_cnt;
     const int ndig = keyed ? nb * DNUM : nb * 2;     // digit rows, or P x rows of the centre tap
@@ -677,7 +670,7 @@ k_tap_pk(const uint64_t* __restrict__ D, const uint64_t* __restrict__ XPg,
                 for (int k = 0; k < 2; ++k) acc[ii][c][k] = Cols{0, 0, 0};
         // (P c0)[perm_t(n)] of this thread's images, loaded one keyed tap ahead of its use
         auto load_xp = [&](int t, uint64_t (&xp)[2]) {
-            const uint32_t pn = perm_of((uint32_t)n, tt.g[t], logN);
+            const uint32_t pn = perm_src((uint32_t)n, tt.g[t], logN);
 #pragma unroll
             for (int ii = 0; ii < 2; ++ii) {
                 const int ib = i0 + ii;
@@ -699,7 +692,7 @@ k_tap_pk(const uint64_t* __restrict__ D, const uint64_t* __restrict__ XPg,
                 mbar_wait(&full[s], (uint32_t)(t / kSt) & 1u);
             }
             if (tt.key[t]) {
-                const uint32_t pn = perm_of((uint32_t)n, tt.g[t], logN);
+                const uint32_t pn = perm_src((uint32_t)n, tt.g[t], logN);
                 const int loc = (int)(pn & (T - 1));
                 uint32_t d0[2][DNUM], d1[2][DNUM], x0[2], x1[2];
 #pragma unroll
@@ -1056,6 +1049,50 @@ static int tune_limb_groups(he_ctx* ctx, int batch, double* ms) {
     return he_launch_check(ctx, "he_autotune");
 }
 
+// Where the ModUp / ModDown base conversions run: separate kernels (with the chosen limb
+// groups) or inside the forward NTT's first pass.  Both timed as one ModUp and one ModDown of
+// min(batch, 64) synthetic ciphertexts; ms[0] separate, ms[1] fused.
+static int tune_bconv(he_ctx* ctx, int batch, double* ms) {
+    const int items = std::min(batch, 64);
+    const size_t N = ctx->N, L = ctx->L, ct = 2 * L * N;
+    int rc = arena_reserve(ctx, items * ct + items * rot_scratch_per_item(ctx) + 64);
+    if (rc) return rc;
+    arena_reset(ctx);
+    uint64_t* X = arena_take(ctx, items * ct);
+    RotBufs b = rot_bufs_take(ctx, items);
+    for (int it = 0; it < items; ++it) {
+        launch_uniform(ctx, he_stream_state(0x62636f6eull, 2 * it), X + it * ct, (int)L, 0, 0);
+        launch_uniform(ctx, he_stream_state(0x62636f6eull, 2 * it + 1), b.u + it * 2 * (L + ctx->K) * N,
+                       (int)(L + ctx->K), 0, 0);
+    }
+    std::vector<uint64_t*> outs(items);
+    for (int it = 0; it < items; ++it) outs[it] = X + it * ct;   // overwritten: fine for timing
+    auto outp = upload_out_ptrs(ctx, outs);
+    if (!outp) return he_fail(ctx, HE_ECUDA, "pointer table upload failed");
+    cudaEvent_t e0, e1;
+    HE_CHECK_CUDA(ctx, cudaEventCreate(&e0));
+    HE_CHECK_CUDA(ctx, cudaEventCreate(&e1));
+    for (int v = 0; v < 2; ++v) {
+        ctx->bconv_fused = v;
+        auto run = [&]() {
+            modup_items(ctx, X, items, 1u, b);
+            moddown_combine(ctx, b.u, b.v, items, nullptr, nullptr, outp, 1u);
+        };
+        run();
+        cudaEventRecord(e0, ctx->stream);
+        for (int r = 0; r < 3; ++r) run();
+        cudaEventRecord(e1, ctx->stream);
+        cudaEventSynchronize(e1);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        ms[v] = t / 3.0;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->bconv_fused = ms[1] <= ms[0] ? 1 : 0;
+    return he_launch_check(ctx, "he_autotune");
+}
+
 extern "C" int he_autotune(he_ctx* ctx, int batch, int force_tile, double* ms_out) {
     if (!ctx) return HE_EINVAL;
     HE_NOT_RECORDING(ctx, "he_autotune");
@@ -1070,6 +1107,8 @@ extern "C" int he_autotune(he_ctx* ctx, int batch, int force_tile, double* ms_ou
     int rc = tune_ntt(ctx, batch, &ntt_ms);
     if (rc) return rc;
     if ((rc = tune_limb_groups(ctx, batch, lg_ms))) return rc;
+    double bc_ms[2] = {0, 0};
+    if ((rc = tune_bconv(ctx, batch, bc_ms))) return rc;
     if (ms_out) {
         for (int i = 0; i < HE_TUNE_REPORT_LEN; ++i) ms_out[i] = 0.0;
         ms_out[4] = ntt_ms;
@@ -1077,6 +1116,8 @@ extern "C" int he_autotune(he_ctx* ctx, int batch, int force_tile, double* ms_ou
         ms_out[9] = 1 << ctx->ntt_radix;
         for (int v = 0; v < 3; ++v) ms_out[10 + v] = lg_ms[v];
         ms_out[13] = ctx->limb_groups;
+        ms_out[14] = bc_ms[0];
+        ms_out[15] = bc_ms[1];
         ms_out[6] = default_tile(ctx->dnum);
         ms_out[7] = ctx->tap_arith;
     }
@@ -1183,6 +1224,12 @@ extern "C" int he_tune_set(he_ctx* ctx, int knob, int value) {
                 return he_fail(ctx, HE_EINVAL, "he_tune_set: limb groups are 1, 2 or 4");
             ctx->limb_groups = value < 0 ? 0 : value;
             return HE_OK;
+        case HE_TUNE_BCONV_FUSED:
+            if (value < -1 || value > 1)
+                return he_fail(ctx, HE_EINVAL, "he_tune_set: base conversion placement is 0 "
+                                               "(separate kernels) or 1 (inside the NTT)");
+            ctx->bconv_fused = value < 0 ? 1 : value;
+            return HE_OK;
         default:
             return he_fail(ctx, HE_EINVAL, "he_tune_set: unknown knob");
     }
@@ -1196,6 +1243,7 @@ extern "C" int he_tune_get(he_ctx* ctx, int knob, int* value) {
         case HE_TUNE_NTT_SPLIT: *value = ctx->ntt_s1 ? ctx->ntt_s1 : ctx->logN / 2; return HE_OK;
         case HE_TUNE_NTT_RADIX: *value = 1 << (ctx->ntt_radix ? ctx->ntt_radix : 3); return HE_OK;
         case HE_TUNE_LIMB_GROUPS: *value = ctx->limb_groups ? ctx->limb_groups : 1; return HE_OK;
+        case HE_TUNE_BCONV_FUSED: *value = ctx->bconv_fused; return HE_OK;
         default: return he_fail(ctx, HE_EINVAL, "he_tune_get: unknown knob");
     }
 }

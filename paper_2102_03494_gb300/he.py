@@ -15,6 +15,7 @@ HE_COEFF, HE_NTT = 0, 1
 HE_DP_DOT, HE_DP_SHIFT, HE_DP_SHIFT_EXT, HE_CP_CP, HE_DP_DP = 0, 1, 2, 3, 4
 HE_ROW_SWAP = 0x7FFFFFFF
 HE_TUNE_TAP_TILE, HE_TUNE_TAP_ARITH, HE_TUNE_NTT_SPLIT, HE_TUNE_NTT_RADIX, HE_TUNE_LIMB_GROUPS = 0, 1, 2, 3, 4
+HE_TUNE_BCONV_FUSED = 5
 HE_TUNE_REPORT_LEN = 16
 HE_RELIN_KEY = -0x80000000
 
@@ -443,6 +444,8 @@ class Context:
                 "ntt_ms": ms[4], "ntt_log2_n1": int(ms[5]), "ntt_radix": int(ms[9]),
                 "conversion_ms": {"1": ms[10], "2": ms[11], "4": ms[12]},
                 "limb_groups": int(ms[13]), "tap_tile": int(ms[6]),
+                "bconv_ms": {"separate": ms[14], "fused": ms[15]},
+                "bconv": ("separate", "fused")[self.he_tune_get(HE_TUNE_BCONV_FUSED)],
                 "tap_arith": ("chains", "columns", "products")[int(ms[7])]}
 
     def he_tune_set(self, knob, value):

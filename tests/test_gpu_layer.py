@@ -304,6 +304,7 @@ def test_autotuned_tap_tile_and_arithmetic_keep_the_bits():
     # the ModUp / ModDown conversions with their target limbs split over 1, 2 and 4 groups
     assert rep["limb_groups"] in (1, 2, 4) and all(v > 0 for v in rep["conversion_ms"].values())
     ctx.he_tune_set(he.HE_TUNE_TAP_ARITH, 0)
+    ctx.he_tune_set(he.HE_TUNE_BCONV_FUSED, 0)        # limb groups apply to the separate kernels
     for groups in (1, 2, 4):
         ctx.he_tune_set(he.HE_TUNE_LIMB_GROUPS, groups)
         assert ctx.he_tune_get(he.HE_TUNE_LIMB_GROUPS) == groups
@@ -314,6 +315,21 @@ def test_autotuned_tap_tile_and_arithmetic_keep_the_bits():
         st = gpu_steps(steps)[0]
         got = ctx.he_rotate(upload_ntt(ctx, cts[0]), st)
         assert (download_coeff(ctx, got) == bfv.rotate(prm, cts[0], steps[0], keys).stack()).all()
+    # the base conversions as separate kernels and inside the NTT's first pass
+    assert rep["bconv"] in ("separate", "fused") and all(v > 0 for v in rep["bconv_ms"].values())
+    ctx.he_tune_set(he.HE_TUNE_LIMB_GROUPS, 1)
+    for fused in (0, 1):
+        ctx.he_tune_set(he.HE_TUNE_BCONV_FUSED, fused)
+        assert ctx.he_tune_get(he.HE_TUNE_BCONV_FUSED) == fused
+        outs = ctx.he_ffconv_layer_batch([upload_ntt(ctx, c) for c in cts], W1, W2, lay)
+        for b in range(3):
+            for c in range(shape.O_c):
+                assert (download_coeff(ctx, outs[b * shape.O_c + c]) == want[b][c].stack()).all()
+        st = gpu_steps(steps)[0]
+        got = ctx.he_rotate(upload_ntt(ctx, cts[0]), st)
+        assert (download_coeff(ctx, got) == bfv.rotate(prm, cts[0], steps[0], keys).stack()).all()
+    with pytest.raises(he.HeError):
+        ctx.he_tune_set(he.HE_TUNE_BCONV_FUSED, 2)
     with pytest.raises(he.HeError):
         ctx.he_autotune(3, force_tile=64)
     with pytest.raises(he.HeError):
