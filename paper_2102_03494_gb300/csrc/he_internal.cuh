@@ -149,6 +149,28 @@ __device__ __forceinline__ void mac128(U128& acc, uint64_t a, uint64_t b) {
         : "l"(a), "l"(b));
 }
 
+// acc += a * b for operands below 2^63 (residues): then the two cross products a0 b1 + a1 b0
+// fit one 64-bit word, and the partial products enter the 128-bit sum by 64-bit add-with-carry
+// (four 32 x 32 -> 64-bit multiplies, two shifts, four adds).  Measured 11 % more products per
+// clock than mac128's 32-bit carry chain (5.94 against 5.36 per SM and clock on GB300).
+__device__ __forceinline__ void mac128r(U128& acc, uint64_t a, uint64_t b) {
+    asm("{\n\t.reg .u32 a0, a1, b0, b1;\n\t.reg .u64 lo, hi, mid, sh;\n\t"
+        "mov.b64 {a0, a1}, %2;\n\t"
+        "mov.b64 {b0, b1}, %3;\n\t"
+        "mul.wide.u32 lo, a0, b0;\n\t"
+        "mul.wide.u32 hi, a1, b1;\n\t"
+        "mul.wide.u32 mid, a0, b1;\n\t"
+        "mad.wide.u32 mid, a1, b0, mid;\n\t"
+        "add.cc.u64 %0, %0, lo;\n\t"
+        "addc.u64 %1, %1, hi;\n\t"
+        "shl.b64 sh, mid, 32;\n\t"
+        "shr.u64 mid, mid, 32;\n\t"
+        "add.cc.u64 %0, %0, sh;\n\t"
+        "addc.u64 %1, %1, mid;\n\t}"
+        : "+l"(acc.lo), "+l"(acc.hi)
+        : "l"(a), "l"(b));
+}
+
 // REDC: x 2^-64 mod q for x < q 2^64, result in [0, q).  With m = x q' mod 2^64 the sum
 // x + m q is divisible by 2^64 and its top half is x 2^-64 mod q, in [0, 2q).
 __device__ __forceinline__ uint64_t redc(U128 x, uint64_t q, uint64_t qinv_neg) {

@@ -129,8 +129,8 @@ __global__ void k_ks_inner(const uint64_t* __restrict__ D, size_t d_stride,
     U128 a0{0, 0}, a1{0, 0};
     for (int j = 0; j < dnum; ++j) {
         uint64_t x = d[(size_t)j * LK * N + src];
-        mac128(a0, x, kb[(size_t)(2 * j) * LK * N]);
-        mac128(a1, x, kb[(size_t)(2 * j + 1) * LK * N]);
+        mac128r(a0, x, kb[(size_t)(2 * j) * LK * N]);
+        mac128r(a1, x, kb[(size_t)(2 * j + 1) * LK * N]);
     }
     uint64_t* ub = u + blockIdx.x * u_stride + (size_t)l * N + n;
     ub[0] = redc(a0, M.q, M.qinv_neg);
@@ -311,8 +311,8 @@ k_ks_mac_ext(const uint64_t* __restrict__ D, const uint64_t* __restrict__ XP,
                 U128 s0{0, 0}, s1{0, 0};
 #pragma unroll
                 for (int j = 0; j < DNUM; ++j) {
-                    mac128(s0, dv[j], kv[j][0]);
-                    mac128(s1, dv[j], kv[j][1]);
+                    mac128r(s0, dv[j], kv[j][0]);
+                    mac128r(s1, dv[j], kv[j][1]);
                 }
                 s0.hi += c0p;   // + (P c0) 2^64 before the division by 2^64
                 x[ib][0] = redc_wide(s0, q, qi);
@@ -323,8 +323,8 @@ k_ks_mac_ext(const uint64_t* __restrict__ D, const uint64_t* __restrict__ XP,
         for (int ib = 0; ib < 2; ++ib)
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-                mac128(a128[ib][0][k], x[ib][k], p0);
-                mac128(a128[ib][1][k], x[ib][k], p1);
+                mac128r(a128[ib][0][k], x[ib][k], p0);
+                mac128r(a128[ib][1][k], x[ib][k], p1);
             }
         if (++pending == 8 || t == tt.n - 1) {
             pending = 0;
@@ -371,8 +371,8 @@ __global__ void k_mac(const uint64_t* const* __restrict__ X, const uint64_t* con
     for (int t = 0; t < T; ++t) {
         const uint64_t* x = X[(size_t)o * T + t];
         uint64_t p = P[(size_t)o * T + t][off];
-        mac128(a0, x[off], p);
-        mac128(a1, x[off + (size_t)L * N], p);
+        mac128r(a0, x[off], p);
+        mac128r(a1, x[off + (size_t)L * N], p);
     }
     uint64_t r0 = redc(a0, M.q, M.qinv_neg);
     uint64_t r1 = redc(a1, M.q, M.qinv_neg);
@@ -403,8 +403,8 @@ __global__ void k_convpack(const uint64_t* __restrict__ x, int r, int O_c,
         U128 a0{0, 0}, a1{0, 0};
         for (int cp = 0; cp < r; ++cp) {
             const uint64_t w = wm[((size_t)c * r + cp) * L + i];
-            mac128(a0, xb[cp * ct], w);
-            mac128(a1, xb[cp * ct + (size_t)L * N], w);
+            mac128r(a0, xb[cp * ct], w);
+            mac128r(a1, xb[cp * ct + (size_t)L * N], w);
         }
         uint64_t* ob = outp[(size_t)b * O_c + c] + (size_t)i * N + n;
         ob[0] = redc(a0, M.q, M.qinv_neg);
@@ -437,8 +437,8 @@ __global__ void k_convpack_reg(const uint64_t* __restrict__ x, int O_c,
 #pragma unroll
         for (int cp = 0; cp < R; ++cp) {
             const uint64_t w = wm[((size_t)c * R + cp) * L + i];
-            mac128(a0, x0[cp], w);
-            mac128(a1, x1[cp], w);
+            mac128r(a0, x0[cp], w);
+            mac128r(a1, x1[cp], w);
         }
         uint64_t* ob = outp[(size_t)b * O_c + c] + (size_t)i * N + n;
         ob[0] = redc(a0, M.q, M.qinv_neg);

@@ -229,8 +229,8 @@ __device__ __forceinline__ bool compute_chain(const uint64_t* __restrict__ smem,
 #pragma unroll
                 for (int j = 0; j < DNUM; ++j) {
                     const uint64_t d = st[S::DIG + (ib * DNUM + j) * kTile + loc];
-                    mac128(s0, d, kv[j][0]);
-                    mac128(s1, d, kv[j][1]);
+                    mac128r(s0, d, kv[j][0]);
+                    mac128r(s1, d, kv[j][1]);
                 }
                 s0.hi += xp[ib];                      // + (P c0) 2^64 (zero on P limbs)
                 x[ib][0] = redc_w(s0, q, qi);
@@ -244,12 +244,12 @@ __device__ __forceinline__ bool compute_chain(const uint64_t* __restrict__ smem,
 #pragma unroll
         for (int ib = 0; ib < 2; ++ib)
 #pragma unroll
-            for (int k = 0; k < 2; ++k) mac128(a128[ib][0][k], x[ib][k], p0);
+            for (int k = 0; k < 2; ++k) mac128r(a128[ib][0][k], x[ib][k], p0);
         if (c_cnt > 1) {                 // uniform over the launch: one channel skips this
 #pragma unroll
             for (int ib = 0; ib < 2; ++ib)
 #pragma unroll
-                for (int k = 0; k < 2; ++k) mac128(a128[ib][1][k], x[ib][k], p1);
+                for (int k = 0; k < 2; ++k) mac128r(a128[ib][1][k], x[ib][k], p1);
         }
     }
     if (ok) {

@@ -220,10 +220,16 @@ class Context:
         return HeCt(t.data_ptr(), 2, t.shape[-2], domain)
 
     def ct_array(self, ts, domain=HE_NTT):
+        if isinstance(ts, CtBatch):
+            return ts.arr
         arr = (HeCt * len(ts))()
         for i, t in enumerate(ts):
             arr[i] = self.ct_struct(t, domain)
         return arr
+
+    def ct_batch(self, ts, domain=HE_NTT):
+        """Ciphertext tensors marshalled once, for repeated calls on the same list."""
+        return CtBatch(self, ts, domain)
 
     def to_numpy(self, t):
         self.stream.synchronize()                  # the library may still be writing t
@@ -656,6 +662,26 @@ class Context:
         self._ck(lib().he_ntt(self.h, ctypes.c_void_p(data.data_ptr()), n_items, n_limbs, int(inverse)),
                  "he_ntt")
         return data
+
+
+class CtBatch:
+    """A list of ciphertext tensors with its C-ABI struct array built once; accepted wherever a
+    list of ciphertexts is.  The tensors are kept alive by it."""
+
+    def __init__(self, ctx, ts, domain=HE_NTT):
+        self.ts = list(ts)
+        self.arr = (HeCt * len(self.ts))()
+        for i, t in enumerate(self.ts):
+            self.arr[i] = ctx.ct_struct(t, domain)
+
+    def __len__(self):
+        return len(self.ts)
+
+    def __getitem__(self, i):
+        return self.ts[i]
+
+    def __iter__(self):
+        return iter(self.ts)
 
 
 def he_gaussian_table():

@@ -293,7 +293,9 @@ def test_automorphism_is_bit_exact(cfg):
     for i, c in enumerate(cts):
         block[i].copy_(upload_ntt(ctx, c))
     for st, g in ((step, bfv.galois_of(step, prm.n)), (he.HE_ROW_SWAP, 2 * prm.n - 1)):
-        outs = ctx.he_automorphism(list(block), st, outs=list(ctx.new_ct(count=3)))
+        # the lists marshalled once (as the sweep passes them), back to back: one launch
+        outs = ctx.he_automorphism(ctx.ct_batch(list(block)), st,
+                                   outs=ctx.ct_batch(list(ctx.new_ct(count=3))))
         apart = ctx.he_automorphism([block[2], block[0]], st)
         for i, c in enumerate(cts):
             want = np.stack([bfv.automorphism(c.c0, g, prm.q), bfv.automorphism(c.c1, g, prm.q)])
