@@ -80,6 +80,20 @@ def max_over_ranks(values, device):
     return [float(v) for v in t.tolist()]
 
 
+def check_line(line):
+    """The bench line's contract keys and their types (raises ValueError on a malformed line)."""
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "dtype", "config", "e2e", "gpu_launches", "clocks"):
+        if k not in line:
+            raise ValueError(f"bench line without {k!r}")
+    clk = line["clocks"]
+    if not isinstance(clk, dict) or not {"sm_mhz", "sm_max_mhz", "reasons"} <= set(clk):
+        raise ValueError(f"bench line clocks must be an object with sm_mhz, sm_max_mhz, reasons: {clk!r}")
+    if not isinstance(line["e2e"], dict) or "value" not in line["e2e"]:
+        raise ValueError("bench line e2e must be an object with a value")
+    return line
+
+
 def whole_job_rate(units_per_rank, world, ms_max):
     """Units processed by all replicas per second, timed by the slowest replica."""
     return world * units_per_rank / (ms_max / 1000.0)
@@ -473,9 +487,9 @@ def run(args):
     roof = taps_roofline(phases, args, B, n_rot, sms, tuned["tap_arith"])
     if roof is not None:          # the measured multiply-accumulate rates, for context
         probe = ctx.he_probe_int_ops()
-        clk = measured_peaks()["sm_max_mhz"] * 1e6
+        clk_hz = measured_peaks()["sm_max_mhz"] * 1e6
         roof["probe"] = {"mul64_T_per_s": {k: probe[k] / 1e12 for k in ("chain", "columns", "karatsuba")},
-                         "per_clock_per_sm": {k: probe[k] / (sms * clk)
+                         "per_clock_per_sm": {k: probe[k] / (sms * clk_hz)
                                               for k in ("mad_lo", "mad_hi", "mad_wide")},
                          "read_gbs": ctx.he_probe_mem()}
     layer_bytes = layer_algorithmic_bytes(B, shape.O_c, n_rot)
@@ -523,7 +537,7 @@ def run(args):
         line["also"] = extra_workloads(cpu_proc)
     if cpu_proc is not None:
         line["cpu_baseline"] = finish_cpu_baseline(cpu_proc)
-    print(json.dumps(line))
+    print(json.dumps(check_line(line)))
 
 
 def extra_workloads(cpu_proc=None):

@@ -93,14 +93,6 @@ struct BConvCta {
     int ns, N;
 };
 
-__device__ __forceinline__ uint64_t bconv_at(const BConvCta& p, size_t pos, uint64_t q) {
-    uint64_t acc = 0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-        if (k < p.ns) acc = add_mod(acc, mul_shoup(p.s[(size_t)k * p.N + pos], p.c[k].w, p.c[k].ws, q), q);
-    return acc;
-}
-
 // One round of the column pass.  Element m of group Gi: column c = Gi mod cols, row
 // hi (tlow 2^K) + m tlow + lo with (hi, lo) = divmod(Gi / cols, tlow).  cols = 2^lc and
 // tlow = 2^(s1 - e0 - K), so the divisions are shifts.
@@ -126,12 +118,27 @@ __device__ __forceinline__ void col_round(uint64_t (&x)[8], uint64_t* sm, uint64
         for (int m = 0; m < M; ++m)
             off[g * M + m] = ((((hi[g] << K) + m) << ltl) + lo) << lc | c;
     }
-    if (first) {
+    if (first && PRO) {
+        // source limb by source limb, the thread's eight loads in flight together
+        const uint64_t q = Mc.q;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (k >= pc.ns) break;
+            const uint64_t* sk = pc.s + (size_t)k * pc.N + lo0;
+            const ShoupPair ck = pc.c[k];
+            uint64_t v[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[i] = sk[(size_t)(off[i] >> lc) * N2 + (off[i] & cmask)];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) x[i] = add_mod(x[i], mul_shoup(v[i], ck.w, ck.ws, q), q);
+        }
+    } else if (first) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int row = off[i] >> lc, c = off[i] & cmask;
-            const size_t pos = (size_t)row * N2 + lo0 + c;
-            x[i] = PRO ? bconv_at(pc, pos, Mc.q) : a[pos];
+            x[i] = a[(size_t)row * N2 + lo0 + c];
         }
     } else {
 #pragma unroll

@@ -84,3 +84,17 @@ def test_reference_step_runs_the_oracle_layer(monkeypatch):
     dt, n_rot = bench.oracle_layer_step(3)
     assert dt > 0 and n_rot == 24
     assert bench._ORACLE["lay"].pack == "dp_shift_ext"
+
+
+def test_bench_line_contract_is_checked():
+    """The main line carries clocks as an object (sm_mhz, sm_max_mhz, reasons) and e2e as one;
+    a line whose clocks became a bare number is refused before it is printed."""
+    line = {"metric": "m", "value": 1.0, "unit": "u", "n_gpus": 1, "steps": 2, "warmup": 3,
+            "ms_per_step": 1.0, "higher_is_better": True, "dtype": "u64", "config": {},
+            "e2e": {"value": 1.0}, "gpu_launches": 4,
+            "clocks": {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []}}
+    assert bench.check_line(line) is line
+    with pytest.raises(ValueError):
+        bench.check_line(dict(line, clocks=2.07e9))
+    with pytest.raises(ValueError):
+        bench.check_line({k: v for k, v in line.items() if k != "e2e"})
