@@ -76,7 +76,11 @@ __device__ __forceinline__ void round_bflies(uint64_t (&x)[8], const int (&hi)[8
 #pragma unroll
             for (int m = 0; m < M; ++m) {
                 if (m & d) continue;
-                const ShoupPair W = w[(1 << s) + (base_hi << ee) + (m >> (K - ee))];
+                // one 16-byte load per pair (the tables are 16-byte aligned): half the L1
+                // wavefronts of two 8-byte loads
+                const ulonglong2 tw = __ldg(reinterpret_cast<const ulonglong2*>(w) +
+                                            ((1 << s) + (base_hi << ee) + (m >> (K - ee))));
+                const ShoupPair W{tw.x, tw.y};
                 if (INV) bfly_gs(x[g * M + m], x[g * M + m + d], W, q, q2);
                 else if (SMALL) bfly_ct_small(x[g * M + m], x[g * M + m + d], W, q, 2 * q2);
                 else bfly_ct(x[g * M + m], x[g * M + m + d], W, q, q2);
@@ -319,9 +323,11 @@ k_ntt_cols(uint64_t* __restrict__ data, size_t item_stride, int mod_off, int log
     ntt_cols_body<INV, SMALL, KMAX, PRO>(a, sm, logN, s1, lc, lo0, w, Mc, pc, osc);
 }
 
-// Row pass.  Forward with EPI: the last round writes the combine step `cd` instead of v.
+// Row pass.  Forward with EPI: the last round writes the combine step `cd` instead of v.  The
+// unreduced forward rounds hold more live values: three CTAs per SM leave them in registers
+// (measured faster than four with spills).
 template <bool INV, bool SMALL, int KMAX, bool EPI>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, (SMALL && !INV) ? 3 : 4)
 k_ntt_rows(uint64_t* __restrict__ data, size_t item_stride, int mod_off, int logN, int s1, int blocks,
            const ModConst* __restrict__ mods, const ShoupPair* __restrict__ tw, const CombineDst cd) {
     __shared__ uint64_t sm[kTile];
