@@ -165,6 +165,13 @@ __device__ __forceinline__ void col_round(uint64_t (&x)[8], uint64_t* sm, uint64
     }
 }
 
+// Shared-memory index of the row pass: word w goes to w ^ ((w >> 4) & 15), a permutation inside
+// each row of 16 words (128 bytes, the 32 banks).  The later rounds' strided patterns (groups of
+// 4 consecutive words 32 words apart, or words 4 apart) otherwise fall on 4 of the 16 bank
+// pairs, 8-way conflicts; swizzled, every pattern of the pass spreads a warp's 32 words over all
+// 16 pairs, two each (the minimum two wavefronts of a 64-bit access).
+__device__ __forceinline__ int swz(int w) { return w ^ ((w >> 4) & 15); }
+
 // The combine step as one CTA of the row pass sees it (CombineDst for its item and row).
 struct CombineCta {
     const uint64_t* u;
@@ -208,7 +215,7 @@ __device__ __forceinline__ void row_round(uint64_t (&x)[8], uint64_t* sm, uint64
         for (int i = 0; i < 8; ++i) x[i] = a[(size_t)blk0 * N2 + off[i]];
     } else {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) x[i] = sm[off[i]];
+        for (int i = 0; i < 8; ++i) x[i] = sm[swz(off[i])];
     }
     const uint64_t q = Mc.q, q2 = 2 * q;
     // twiddle offset of block (blk0 + b) at stage s1 + e0 + ee is (blk0 + b) 2^(e0 + ee):
@@ -239,7 +246,7 @@ __device__ __forceinline__ void row_round(uint64_t (&x)[8], uint64_t* sm, uint64
         }
     } else {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) sm[off[i]] = x[i];
+        for (int i = 0; i < 8; ++i) sm[swz(off[i])] = x[i];
         __syncthreads();
     }
 }
