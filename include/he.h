@@ -422,7 +422,7 @@ int he_deep_batch(he_ctx* ctx, const he_ct* in, int B, const he_mc_conv* convs, 
 int he_autotune(he_ctx* ctx, int batch, int force_tile, double* ms_out);
 /* Tuning knobs, set by hand (value -1 restores the default) or read back: HE_TUNE_TAP_TILE
  * (128 or 256), HE_TUNE_TAP_ARITH (0 chains, 1 columns, 2 precomputed products),
- * HE_TUNE_NTT_SPLIT (log2 N1, 1 .. log2 N - 1), HE_TUNE_NTT_RADIX (2, 4 or 8: the most points
+ * HE_TUNE_NTT_SPLIT (log2 N1, 1 .. log2 N - 1), HE_TUNE_NTT_RADIX (4 or 8: the most points
  * a thread group transforms per round), HE_TUNE_LIMB_GROUPS (1, 2 or 4), HE_TUNE_BCONV_FUSED
  * (0: the ModUp / ModDown base conversions as separate kernels, 1 (default): read by the
  * forward NTT's first pass, the inverse NTT before them leaving y directly).  Results never

@@ -411,7 +411,7 @@ static void free_ctx(he_ctx* c) {
     if (!c) return;
     recording_abort(c);
     if (c->stream || true) cudaStreamSynchronize(c->stream);
-    void* ptrs[] = {c->d_mod, c->d_tw_fwd, c->d_tw_inv, c->d_slot_pos, c->d_cdt,
+    void* ptrs[] = {c->d_mod, c->d_tw_fwd, c->d_tw_inv, c->d_tw_fwd_rows, c->d_slot_pos, c->d_cdt,
                     c->d_modup_inv, c->d_modup_c, c->d_md_inv, c->d_md_c, c->d_md_pinv,
                     c->d_modup_ninv, c->d_md_ninv,
                     c->d_rs_inv, c->d_pmodq, c->arena.base, c->staging.dev, c->d_err,
@@ -569,7 +569,8 @@ extern "C" int he_ctx_create(const he_params* p, void* stream, he_ctx** out) {
 
     int rc = HE_OK;
     if ((rc = upload_vec(c, &c->d_mod, mc)) || (rc = upload_vec(c, &c->d_tw_fwd, twf)) ||
-        (rc = upload_vec(c, &c->d_tw_inv, twi)) || (rc = upload_vec(c, &c->d_slot_pos, pos)) ||
+        (rc = upload_vec(c, &c->d_tw_inv, twi)) || (rc = upload_vec(c, &c->d_tw_fwd_rows, twf)) ||
+        (rc = upload_vec(c, &c->d_slot_pos, pos)) ||
         (rc = upload_vec(c, &c->d_cdt, cdtv)) || (rc = upload_vec(c, &c->d_modup_inv, mu_inv)) ||
         (rc = upload_vec(c, &c->d_modup_c, mu_c)) || (rc = upload_vec(c, &c->d_md_inv, md_inv)) ||
         (rc = upload_vec(c, &c->d_md_c, md_c)) || (rc = upload_vec(c, &c->d_md_pinv, md_pinv)) ||
@@ -592,6 +593,7 @@ extern "C" int he_ctx_create(const he_params* p, void* stream, he_ctx** out) {
         return HE_ENOMEM;
     }
     for (int i = 0; i < st.n_slots; ++i) cudaEventCreateWithFlags(&st.ev[i], cudaEventDisableTiming);
+    ntt_prepare(c);                             // row-pass twiddle order of the default split
     *out = c;
     return HE_OK;
 }

@@ -225,6 +225,10 @@ struct he_ctx {
     ModConst* d_mod = nullptr;          // [n_mod]
     ShoupPair* d_tw_fwd = nullptr;      // [n_mod][N]: psi^brv(k)
     ShoupPair* d_tw_inv = nullptr;      // [n_mod][N]: psi^-brv(k)
+    // d_tw_fwd with each forward row-pass stage reordered so that a round's lanes read
+    // consecutive entries (ntt.cu ensure_row_tables); valid for the split and radix cap here
+    ShoupPair* d_tw_fwd_rows = nullptr;
+    int tw_rows_s1 = -1, tw_rows_k = -1;
     int32_t* d_slot_pos = nullptr;      // [N]: NTT position of each slot (mod t, root zeta)
     uint64_t* d_cdt = nullptr;          // [20] sampler thresholds
     // ModUp: y_i = x_i [(Q_j/q_i)^-1]_{q_i};  then sum_i y_i [Q_j/q_i]_{p_l}
@@ -375,6 +379,9 @@ void he_cdt_compute(uint64_t out[20]);
 // `rows` consecutive limbs; limb r of a block uses modulus index mod_off + r.
 void ntt_forward(he_ctx* ctx, uint64_t* data, int items, size_t item_stride, int rows,
                  int mod_off);
+// Brings the row-pass twiddle tables to the context's split and radix cap; called wherever
+// those change (never while recording).
+void ntt_prepare(he_ctx* ctx);
 // Splits log2 N1 of the two-pass NTT worth timing for this ring (the default first).
 int ntt_split_candidates(int logN, int* out, int cap);
 void ntt_inverse(he_ctx* ctx, uint64_t* data, int items, size_t item_stride, int rows,

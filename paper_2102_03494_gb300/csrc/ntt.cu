@@ -56,11 +56,26 @@ __device__ __forceinline__ void bfly_gs(uint64_t& X, uint64_t& Y, const ShoupPai
     Y = mul_shoup_lazy(d, W.w, W.ws, q);             // [0, 2q)
 }
 
+// Inverse butterfly for q < 2^61: values kept in [0, 4q) (8q < 2^64), the Shoup product
+// estimated from three partial products ([0, 4q) for any 64-bit input).  The pass's last
+// product by N^-1 is a full Shoup product and brings every value to [0, q).
+__device__ __forceinline__ void bfly_gs_small(uint64_t& X, uint64_t& Y, const ShoupPair& W,
+                                              uint64_t q, uint64_t q4) {
+    uint64_t s = X + Y;                              // < 8q
+    s = s >= q4 ? s - q4 : s;                        // [0, 4q)
+    const uint64_t d = X - Y + q4;                   // (0, 8q)
+    X = s;
+    Y = mul_shoup_approx(d, W.w, W.ws, q);           // [0, 4q)
+}
+
 // Butterflies of one round on the thread's 8 registers: (8 >> K) groups of 2^K elements,
 // group g at x[g * 2^K + m].  Twiddle of stage ee for element m of a group whose block index
 // is `hi` (plus the block offset `toff` of the row pass): psi^brv(2^s + toff 2^ee + hi 2^ee
 // + (m >> (K - ee))).
-template <int K, bool INV, bool SMALL>
+// ROWT (the forward row pass): the reordered table, where stage s's entry (base, j) sits at
+// 2^s + j 2^s0 + base (s0 the round's first stage): lanes with consecutive groups read
+// consecutive entries.  (The inverse row pass measured slower with its own reordered table.)
+template <int K, bool INV, bool SMALL, bool ROWT = false>
 __device__ __forceinline__ void round_bflies(uint64_t (&x)[8], const int (&hi)[8 >> K], int s0,
                                              int toff, const ShoupPair* __restrict__ w,
                                              uint64_t q, uint64_t q2) {
@@ -78,10 +93,12 @@ __device__ __forceinline__ void round_bflies(uint64_t (&x)[8], const int (&hi)[8
                 if (m & d) continue;
                 // one 16-byte load per pair (the tables are 16-byte aligned): half the L1
                 // wavefronts of two 8-byte loads
-                const ulonglong2 tw = __ldg(reinterpret_cast<const ulonglong2*>(w) +
-                                            ((1 << s) + (base_hi << ee) + (m >> (K - ee))));
+                const int ti = ROWT ? (1 << s) + ((m >> (K - ee)) << s0) + base_hi
+                                    : (1 << s) + (base_hi << ee) + (m >> (K - ee));
+                const ulonglong2 tw = __ldg(reinterpret_cast<const ulonglong2*>(w) + ti);
                 const ShoupPair W{tw.x, tw.y};
-                if (INV) bfly_gs(x[g * M + m], x[g * M + m + d], W, q, q2);
+                if (INV && SMALL) bfly_gs_small(x[g * M + m], x[g * M + m + d], W, q, 2 * q2);
+                else if (INV) bfly_gs(x[g * M + m], x[g * M + m + d], W, q, q2);
                 else if (SMALL) bfly_ct_small(x[g * M + m], x[g * M + m + d], W, q, 2 * q2);
                 else bfly_ct(x[g * M + m], x[g * M + m + d], W, q, q2);
             }
@@ -210,9 +227,14 @@ __device__ __forceinline__ void row_round(uint64_t (&x)[8], uint64_t* sm, uint64
         for (int m = 0; m < M; ++m)
             off[g * M + m] = (b << s2) + ((((hi[g] << K) + m) << ltl) | lo);
     }
+    // The forward pass ends with its shortest strides (a thread's 2^K residues adjacent): its
+    // last round leaves through shared memory, so that global memory is written in whole lines
+    // (the same staging at the inverse pass's start measured slower).
+    const int tile = nthr * 8;
+    uint64_t* at = a + (size_t)blk0 * N2;
     if (first) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) x[i] = a[(size_t)blk0 * N2 + off[i]];
+        for (int i = 0; i < 8; ++i) x[i] = at[off[i]];
     } else {
 #pragma unroll
         for (int i = 0; i < 8; ++i) x[i] = sm[swz(off[i])];
@@ -223,18 +245,25 @@ __device__ __forceinline__ void row_round(uint64_t (&x)[8], uint64_t* sm, uint64
     int hh[8 >> K];
 #pragma unroll
     for (int g = 0; g < (8 >> K); ++g) hh[g] = ((blk0 + blk[g]) << e0) + hi[g];
-    round_bflies<K, INV, SMALL>(x, hh, s1 + e0, 0, w, q, q2);
-    if (last) {
+    round_bflies<K, INV, SMALL, !INV>(x, hh, s1 + e0, 0, w, q, q2);
+    if (last && !INV) {
+        // reduced values back to the locations this thread read (no other thread reads them
+        // in this round), then the tile leaves in order
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             uint64_t v = x[i];
-            if (!INV && SMALL) {                        // v < 68 q < 2^(b + 7)
+            if (SMALL) {                                // v < 68 q < 2^(b + 7)
                 v = reduce_small(v, Mc);
-            } else if (!INV) {
+            } else {
                 v = v >= q2 ? v - q2 : v;
                 v = v >= q ? v - q : v;
             }
-            const size_t pos = (size_t)blk0 * N2 + off[i];
+            sm[swz(off[i])] = v;
+        }
+        __syncthreads();
+        for (int i = tid; i < tile; i += nthr) {
+            const uint64_t v = sm[swz(i)];
+            const size_t pos = (size_t)blk0 * N2 + i;
             if (EPI) {
                 uint64_t r = mul_shoup(sub_mod(ep.u[pos], v, q), ep.pinv.w, ep.pinv.ws, q);
                 if (ep.c0) r = add_mod(r, ep.c0[perm_src((uint32_t)pos, ep.g, s1 + s2)], q);
@@ -244,6 +273,9 @@ __device__ __forceinline__ void row_round(uint64_t (&x)[8], uint64_t* sm, uint64
                 a[pos] = v;
             }
         }
+    } else if (last) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) at[off[i]] = x[i];
     } else {
 #pragma unroll
         for (int i = 0; i < 8; ++i) sm[swz(off[i])] = x[i];
@@ -302,6 +334,8 @@ __device__ __forceinline__ void ntt_rows_body(uint64_t* __restrict__ a, uint64_t
 // The forward transform of a modulus below 2^57 takes the unreduced butterflies (SMALL, see
 // the header); the launcher splits a launch's limbs by that test.
 bool small_mod(uint64_t q) { return (q >> 57) == 0; }
+// The inverse transform of a modulus below 2^61 keeps its values in [0, 4q) (bfly_gs_small).
+bool small_inv_mod(uint64_t q) { return (q >> 61) == 0; }
 
 // Column pass.  Inverse: the last round multiplies by oscale[row] when given, else N^-1.
 // Forward with PRO: the first round reads the fused base conversion `bc` instead of `data`.
@@ -418,6 +452,50 @@ int ntt_split_candidates(int logN, int* out, int cap) {
     return n;
 }
 
+namespace {
+
+// Forward row table from the standard one: entry e of stage s >= s1 (offset o = e - 2^s,
+// o = base 2^ee + j with ee = (s - s1) mod kmax, the stage's place in its round) moves to
+// 2^s + j 2^(s - ee) + base; stages below s1 are copied.
+__global__ void k_row_table(const ShoupPair* __restrict__ fwd, ShoupPair* __restrict__ fwd_r,
+                            int logN, int s1, int kmax, size_t total) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const size_t N = (size_t)1 << logN, base_m = i - (i & (N - 1));
+    const int e = (int)(i & (N - 1));
+    if (e < (1 << s1)) {
+        fwd_r[i] = fwd[i];
+        return;
+    }
+    const int s = 31 - __clz(e), o = e - (1 << s), ee = (s - s1) % kmax;
+    const int b = o >> ee, j = o & ((1 << ee) - 1);
+    fwd_r[base_m + (1 << s) + ((size_t)j << (s - ee)) + b] = fwd[i];
+}
+
+// Rebuilds the row table for a split and radix cap it was not made for.  ntt_prepare does
+// it wherever those change; a transform that still finds them stale rebuilds them, except
+// while recording (the rebuild would enter the graph), where the recording is spoiled.
+void ensure_row_tables(he_ctx* ctx, int s1, int kmax) {
+    if (ctx->tw_rows_s1 == s1 && ctx->tw_rows_k == kmax) return;
+    if (ctx->rec) {
+        he_fail(ctx, HE_EINVAL, "NTT twiddle order changed while recording");
+        return;
+    }
+    const size_t total = (size_t)ctx->n_mod * ctx->N;
+    ++ctx->launches;
+    k_row_table<<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(
+        ctx->d_tw_fwd, ctx->d_tw_fwd_rows, ctx->logN, s1, kmax, total);
+    ctx->tw_rows_s1 = s1;
+    ctx->tw_rows_k = kmax;
+}
+
+}  // namespace
+
+void ntt_prepare(he_ctx* ctx) {
+    const Split sp = split_of(ctx->logN, ctx->ntt_s1);
+    ensure_row_tables(ctx, sp.s1, ctx->ntt_radix == 2 ? 2 : 3);
+}
+
 constexpr CombineDst kNoCombine{nullptr, 0, nullptr, nullptr, nullptr, nullptr, 0, 1u};
 
 template <bool INV, bool SMALL, int KMAX, bool PRO = false, bool EPI = false>
@@ -426,16 +504,18 @@ void launch_pass_pair(he_ctx* ctx, const Split& sp, uint64_t* d, int items, size
                       const BConvSrc& bc = BConvSrc{nullptr, 0, nullptr, 0, 0},
                       const CombineDst& cd = kNoCombine) {
     dim3 gc(sp.col_ctas, rows, items), gr(sp.row_ctas, rows, items);
+    ensure_row_tables(ctx, sp.s1, KMAX);
     ctx->launches += 2;
     const ShoupPair* tw = INV ? ctx->d_tw_inv : ctx->d_tw_fwd;
+    const ShoupPair* twr = INV ? ctx->d_tw_inv : ctx->d_tw_fwd_rows;
     if (!INV) {
         k_ntt_cols<INV, SMALL, KMAX, PRO><<<gc, sp.col_threads, 0, ctx->stream>>>(
             d, item_stride, mod, ctx->logN, sp.s1, sp.lc, ctx->d_mod, tw, nullptr, bc);
         k_ntt_rows<INV, SMALL, KMAX, EPI><<<gr, sp.row_threads, 0, ctx->stream>>>(
-            d, item_stride, mod, ctx->logN, sp.s1, sp.blocks, ctx->d_mod, tw, cd);
+            d, item_stride, mod, ctx->logN, sp.s1, sp.blocks, ctx->d_mod, twr, cd);
     } else {
         k_ntt_rows<INV, SMALL, KMAX, false><<<gr, sp.row_threads, 0, ctx->stream>>>(
-            d, item_stride, mod, ctx->logN, sp.s1, sp.blocks, ctx->d_mod, tw, kNoCombine);
+            d, item_stride, mod, ctx->logN, sp.s1, sp.blocks, ctx->d_mod, twr, kNoCombine);
         k_ntt_cols<INV, SMALL, KMAX, false><<<gc, sp.col_threads, 0, ctx->stream>>>(
             d, item_stride, mod, ctx->logN, sp.s1, sp.lc, ctx->d_mod, tw, oscale, bc);
     }
@@ -485,8 +565,23 @@ void ntt_inverse_scaled(he_ctx* ctx, uint64_t* data, int items, size_t item_stri
                         int mod_off, const ShoupPair* scale) {
     if (items <= 0 || rows <= 0) return;
     const Split sp = split_of(ctx->logN, ctx->ntt_s1);
-    if (ctx->ntt_radix == 2) launch_pass_pair<true, false, 2>(ctx, sp, data, items, item_stride, rows, mod_off, scale);
-    else launch_pass_pair<true, false, 3>(ctx, sp, data, items, item_stride, rows, mod_off, scale);
+    const bool r4 = ctx->ntt_radix == 2;
+    for (int r0 = 0; r0 < rows;) {                   // runs of limbs of one kind
+        const bool small = small_inv_mod(ctx->mods[mod_off + r0]);
+        int r1 = r0 + 1;
+        while (r1 < rows && small_inv_mod(ctx->mods[mod_off + r1]) == small) ++r1;
+        uint64_t* d = data + (size_t)r0 * ctx->N;
+        const int n = r1 - r0, m = mod_off + r0;
+        const ShoupPair* sc = scale ? scale + r0 : nullptr;
+        if (small) {
+            if (r4) launch_pass_pair<true, true, 2>(ctx, sp, d, items, item_stride, n, m, sc);
+            else launch_pass_pair<true, true, 3>(ctx, sp, d, items, item_stride, n, m, sc);
+        } else {
+            if (r4) launch_pass_pair<true, false, 2>(ctx, sp, d, items, item_stride, n, m, sc);
+            else launch_pass_pair<true, false, 3>(ctx, sp, d, items, item_stride, n, m, sc);
+        }
+        r0 = r1;
+    }
 }
 
 void ntt_inverse(he_ctx* ctx, uint64_t* data, int items, size_t item_stride, int rows,

@@ -980,6 +980,7 @@ static int tune_ntt(he_ctx* ctx, int batch, double* best_ms) {
         const int c = v % nc;
         ctx->ntt_s1 = cand[c];
         ctx->ntt_radix = v < nc ? 3 : 2;
+        ntt_prepare(ctx);
         ntt_forward(ctx, X, (int)items, (size_t)ctx->L * ctx->N, ctx->L, 0);     // warm-up
         ntt_inverse(ctx, X, (int)items, (size_t)ctx->L * ctx->N, ctx->L, 0);
         cudaEventRecord(e0, ctx->stream);
@@ -1001,6 +1002,7 @@ static int tune_ntt(he_ctx* ctx, int batch, double* best_ms) {
     cudaEventDestroy(e1);
     ctx->ntt_s1 = best_s1;
     ctx->ntt_radix = best_radix;
+    ntt_prepare(ctx);
     *best_ms = best;
     return he_launch_check(ctx, "he_autotune");
 }
@@ -1213,11 +1215,13 @@ extern "C" int he_tune_set(he_ctx* ctx, int knob, int value) {
             if (value != -1 && (value < 1 || value >= ctx->logN))
                 return he_fail(ctx, HE_EINVAL, "he_tune_set: NTT split log2 N1 out of range");
             ctx->ntt_s1 = value < 0 ? 0 : value;
+            ntt_prepare(ctx);
             return HE_OK;
         case HE_TUNE_NTT_RADIX:
-            if (value != -1 && value != 2 && value != 4 && value != 8)
-                return he_fail(ctx, HE_EINVAL, "he_tune_set: NTT radix is 2, 4 or 8");
-            ctx->ntt_radix = value < 0 ? 0 : (value == 8 ? 3 : value == 4 ? 2 : 1);
+            if (value != -1 && value != 4 && value != 8)
+                return he_fail(ctx, HE_EINVAL, "he_tune_set: NTT radix is 4 or 8");
+            ctx->ntt_radix = value < 0 ? 0 : (value == 8 ? 3 : 2);
+            ntt_prepare(ctx);
             return HE_OK;
         case HE_TUNE_LIMB_GROUPS:
             if (value != -1 && value != 1 && value != 2 && value != 4)
