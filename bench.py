@@ -55,6 +55,9 @@ def parse():
                     help="offered request rates (per second) of --serving")
     ap.add_argument("--serving-count", type=int, default=0,
                     help="requests per rate of --serving (0: 3 s of arrivals, 60 .. 480)")
+    ap.add_argument("--ntt", action="store_true",
+                    help="forward and inverse NTT of 64 ciphertexts' c1 (64 x 12 limbs) at N=2^15, "
+                         "default split and radix (the case the NTT profiles capture)")
     ap.add_argument("--single", action="store_true",
                     help="one-image latency of the 1x28x28 layer at N=8192, 3+1 primes, for the "
                          "DP_DOT, DP_SHIFT and DP_SHIFT_EXT schedules")
@@ -488,7 +491,8 @@ def run(args):
     if roof is not None:          # the measured multiply-accumulate rates, for context
         probe = ctx.he_probe_int_ops()
         clk_hz = measured_peaks()["sm_max_mhz"] * 1e6
-        roof["probe"] = {"mul64_T_per_s": {k: probe[k] / 1e12 for k in ("chain", "columns", "karatsuba")},
+        roof["probe"] = {"mul64_T_per_s": {k: probe[k] / 1e12
+                                           for k in ("chain", "chain_wide", "columns", "karatsuba")},
                          "per_clock_per_sm": {k: probe[k] / (sms * clk_hz)
                                               for k in ("mad_lo", "mad_hi", "mad_wide")},
                          "read_gbs": ctx.he_probe_mem()}
@@ -1201,6 +1205,47 @@ def run_single(args):
                       "schedules": res, "clocks": clk}))
 
 
+# ---------------------------------------------------------------- NTT alone
+
+def run_ntt(args):
+    """Forward and inverse negacyclic NTT of 64 x 12 limbs at N = 2^15 (the c1 limbs of a
+    batch-64 layer input), the context's default split and radix: one untimed pair first (the
+    pair an ncu capture of `-k regex:k_ntt -c 4` sees), then 20 timed pairs by CUDA events."""
+    import torch
+
+    from paper_2102_03494_gb300 import he
+
+    torch.cuda.set_device(0)
+    ctx = he.Context(log_n=LOG_N, n_q=N_Q, n_p=N_P, alpha=ALPHA)
+    N, items, L = 1 << LOG_N, 64, N_Q
+    moduli = ctx.he_get_moduli()[:L]
+    with torch.cuda.stream(ctx.stream):
+        X = torch.empty((items, L, N), dtype=torch.int64, device="cuda")
+        for l, q in enumerate(moduli):
+            X[:, l].random_(0, q)                       # uniform residues below q_l
+    ctx.he_ntt(X, items, L)
+    ctx.he_ntt(X, items, L, inverse=True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    fwd, inv = [], []
+    for _ in range(20):
+        ev[0].record(ctx.stream)
+        ctx.he_ntt(X, items, L)
+        ev[1].record(ctx.stream)
+        ctx.he_ntt(X, items, L, inverse=True)
+        ev[2].record(ctx.stream)
+        ev[2].synchronize()
+        fwd.append(ev[0].elapsed_time(ev[1]))
+        inv.append(ev[1].elapsed_time(ev[2]))
+    ctx.he_check()
+    bfly = items * L * (N // 2) * LOG_N
+    f, i = statistics.median(fwd), statistics.median(inv)
+    print(json.dumps({"metric": "negacyclic NTT / inverse NTT, 64 x 12 limbs at N=2^15",
+                      "unit": "ms", "forward_ms": f, "inverse_ms": i,
+                      "forward_T_butterflies_per_s": bfly / f / 1e9,
+                      "inverse_T_butterflies_per_s": bfly / i / 1e9,
+                      "data": "synthetic (uniform residues)", "dtype": "u64"}))
+
+
 # ---------------------------------------------------------------- primitive sweep
 
 # The primitive sweep's grid: ring sizes, ciphertext primes L -> (special primes K, digit
@@ -1405,6 +1450,9 @@ def main():
         return
     if args.sweep:
         run_sweep(args)
+        return
+    if args.ntt:
+        run_ntt(args)
         return
     if args.single:
         run_single(args)

@@ -466,7 +466,9 @@ int he_probe_int_mac(he_ctx* ctx, double* out);
 /* The same probe per form and per instruction (n doubles, up to 6): out[0] carry-chain
  * products/s, out[1] column products/s, out[2] products/s with three 32 x 32 -> 64-bit
  * products each (Karatsuba on 30-bit halves), out[3] mad.lo.u32/s, out[4] mad.hi.u32/s,
- * out[5] mad.wide.u32/s (eight independent accumulators per thread).  Synchronous. */
+ * out[5] mad.wide.u32/s (eight independent accumulators per thread), out[6] products/s of the
+ * 64-bit add-with-carry form for operands below 2^63 (the kernels' residue products).
+ * Synchronous. */
 int he_probe_int_ops(he_ctx* ctx, double* out, int n);
 /* Read bandwidth in GB/s (n doubles, up to 2): out[0] of a 32 MiB buffer that stays in L2,
  * out[1] of a 2 GiB buffer read from HBM (16-byte loads bypassing L1, all SMs).  Uses the

@@ -1,8 +1,10 @@
 // probe.cu -- microbenchmark of the GPU's 64 x 64 -> 128-bit multiply-accumulate rate, the
 // operation the key-switch, plaintext-product and base-conversion kernels are built from.
 //
-// Two forms, registers only, eight independent accumulators per thread:
-//   chain: mac128 (he_internal.cuh), the 32-bit multiply-add carry chain the kernels use;
+// The forms, registers only, eight independent accumulators per thread:
+//   chain: mac128 (he_internal.cuh), the 32-bit multiply-add carry chain of the Montgomery
+//          reductions; chain_wide: mac128r, the 64-bit add-with-carry form of the residue
+//          products in the tap, inner-product and MAC kernels;
 //   cols:  the same product as four 32 x 32 -> 64-bit partial products summed into three
 //          64-bit column accumulators (operands below 2^60 split at bit 30), no carry chain.
 // Each iteration also advances one operand (so nothing is loop-invariant); every thread
@@ -13,6 +15,9 @@ namespace {
 
 constexpr int kAcc = 8;
 
+// WIDE: mac128r (64-bit add-with-carry of four 32 x 32 -> 64-bit products, operands below
+// 2^63, the form the tap, inner-product and MAC kernels use); else mac128.
+template <bool WIDE>
 __global__ void __launch_bounds__(256) k_probe_chain(const uint64_t* __restrict__ in,
                                                      uint64_t* __restrict__ out, int iters) {
     uint64_t x[kAcc], y[kAcc];
@@ -26,8 +31,9 @@ __global__ void __launch_bounds__(256) k_probe_chain(const uint64_t* __restrict_
     for (int i = 0; i < iters; ++i) {
 #pragma unroll
         for (int a = 0; a < kAcc; ++a) {
-            mac128(acc[a], x[a], y[a]);
-            x[a] += y[a];
+            if (WIDE) mac128r(acc[a], x[a], y[a]);
+            else mac128(acc[a], x[a], y[a]);
+            x[a] ^= (uint32_t)i;                  // stays below 2^60 (low word only)
         }
     }
     uint64_t r = 0;
@@ -164,13 +170,13 @@ extern "C" int he_probe_int_mac(he_ctx* ctx, double* out) {
     for (int v = 0; v < 2; ++v) {
         for (int rep = 0; rep < 2; ++rep) {                       // warm-up
             ++ctx->launches;
-            if (v == 0) k_probe_chain<<<blocks, threads, 0, ctx->stream>>>(in, o, iters);
+            if (v == 0) k_probe_chain<false><<<blocks, threads, 0, ctx->stream>>>(in, o, iters);
             else k_probe_cols<<<blocks, threads, 0, ctx->stream>>>(in, o, iters);
         }
         cudaEventRecord(e0, ctx->stream);
         for (int rep = 0; rep < 5; ++rep) {
             ++ctx->launches;
-            if (v == 0) k_probe_chain<<<blocks, threads, 0, ctx->stream>>>(in, o, iters);
+            if (v == 0) k_probe_chain<false><<<blocks, threads, 0, ctx->stream>>>(in, o, iters);
             else k_probe_cols<<<blocks, threads, 0, ctx->stream>>>(in, o, iters);
         }
         cudaEventRecord(e1, ctx->stream);
@@ -203,17 +209,19 @@ extern "C" int he_probe_int_ops(he_ctx* ctx, double* out, int n) {
     HE_CHECK_CUDA(ctx, cudaEventCreate(&e0));
     HE_CHECK_CUDA(ctx, cudaEventCreate(&e1));
     const double per = (double)blocks * threads * iters * kAcc;
-    const int nv = n < 6 ? n : 6;
+    const int nv = n < 7 ? n : 7;
     for (int v = 0; v < nv; ++v) {
         auto launch = [&]() {
             ++ctx->launches;
             switch (v) {
-                case 0: k_probe_chain<<<blocks, threads, 0, ctx->stream>>>(in, o, iters); break;
+                case 0: k_probe_chain<false><<<blocks, threads, 0, ctx->stream>>>(in, o, iters); break;
+                case 6: k_probe_chain<true><<<blocks, threads, 0, ctx->stream>>>(in, o, iters); break;
                 case 1: k_probe_cols<<<blocks, threads, 0, ctx->stream>>>(in, o, iters); break;
                 case 2: k_probe_kara<<<blocks, threads, 0, ctx->stream>>>(in, o, iters); break;
                 case 3: k_probe_op<0><<<blocks, threads, 0, ctx->stream>>>(in, o, iters); break;
                 case 4: k_probe_op<1><<<blocks, threads, 0, ctx->stream>>>(in, o, iters); break;
-                default: k_probe_op<2><<<blocks, threads, 0, ctx->stream>>>(in, o, iters); break;
+                case 5: k_probe_op<2><<<blocks, threads, 0, ctx->stream>>>(in, o, iters); break;
+                default: break;
             }
         };
         launch();

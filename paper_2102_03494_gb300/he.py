@@ -479,11 +479,11 @@ class Context:
 
     def he_probe_int_ops(self):
         """Rates per second: carry-chain, column and Karatsuba products; mad.lo / mad.hi /
-        mad.wide.u32 instructions."""
-        out = (ctypes.c_double * 6)()
-        self._ck(lib().he_probe_int_ops(self.h, out, 6), "he_probe_int_ops")
-        return dict(zip(("chain", "columns", "karatsuba", "mad_lo", "mad_hi", "mad_wide"),
-                        (float(v) for v in out)))
+        mad.wide.u32 instructions; products of the 64-bit add-with-carry residue form."""
+        out = (ctypes.c_double * 7)()
+        self._ck(lib().he_probe_int_ops(self.h, out, 7), "he_probe_int_ops")
+        return dict(zip(("chain", "columns", "karatsuba", "mad_lo", "mad_hi", "mad_wide",
+                         "chain_wide"), (float(v) for v in out)))
 
     def he_probe_mem(self):
         """Read GB/s of an L2-resident buffer and of an HBM-sized one."""

@@ -247,7 +247,7 @@ def test_integer_rate_probe_is_sane():
     ops = ctx.he_probe_int_ops()
     for k in ("mad_lo", "mad_hi", "mad_wide"):
         assert 0.05 * slots < ops[k] < 1.1 * slots
-    for k in ("chain", "columns", "karatsuba"):
+    for k in ("chain", "chain_wide", "columns", "karatsuba"):
         assert 0.02 * slots / 4 < ops[k] < 1.1 * slots / 3
     mem = ctx.he_probe_mem()          # L2-resident reads outrun HBM reads; HBM below 8 TB/s
     assert 500 < mem["hbm_read_gbs"] < 8000 and mem["l2_read_gbs"] > mem["hbm_read_gbs"]
