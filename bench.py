@@ -594,9 +594,10 @@ def measured_peaks():
 
 
 # DRAM bytes (read + write) of one carry-chain tap launch at batch 64, from one ncu capture of
-# the current kernel (dram__bytes_read.sum 3.53 GB + dram__bytes_write.sum 0.990 GB, one pass);
-# cleared whenever the kernel changes until it is captured again.
-TAPS_TRAFFIC = {("chains", 64): 3.53e9 + 0.98959e9}
+# the current kernel (the 64-bit add-with-carry residue products: dram__bytes_read.sum
+# 3.545 GB + dram__bytes_write.sum 0.989 GB, one pass); cleared whenever the kernel changes
+# until it is captured again.
+TAPS_TRAFFIC = {("chains", 64): 3.544969984e9 + 0.989202176e9}
 
 
 # 64 x 64 -> 128-bit products per second of the GPU's integer multiplier: SMs (152 on GB300)
